@@ -1,0 +1,208 @@
+/*
+ * ld.h -- C ABI of libld: batched Lagrangian-Decomposition (LD) lower bounds
+ * of a ReLU network's output over L-infinity input boxes, for a batch of
+ * branch-and-bound subdomains, on one GB300 GPU.
+ *
+ * The method is De Palma et al., "Improved Branch and Bound for Neural
+ * Network Verification via Lagrangian Decomposition":
+ *   - problem: min x_hat_n s.t. x0 in [l0,u0], x_hat_{k+1} = W_{k+1} x_k + b_{k+1},
+ *     x_k = relu(x_hat_k)                                   (Sec. 2.1, Eq. noncvx_pb)
+ *   - dual:    q(rho) = min x_hat_A,n + sum_k rho_k^T (x_hat_B,k - x_hat_A,k)
+ *     over the layer-pair subproblems P0, Pk                (Sec. 3.1, Eq. nonprox_problem)
+ *   - solver:  supergradient ascent with Adam               (Sec. 3.2, Algorithm 1)
+ *
+ * Notation used below: layers k = 1..n; n_k = width of layer k (n_0 = input
+ * size, n_n = 1); N = n_1 + ... + n_{n-1} = number of ReLUs.  A "flat ReLU
+ * vector" holds layers 1..n-1 back to back in layer order; a conv layer's
+ * activations are flattened channel-major (C, H, W).
+ *
+ * Conventions for every entry point:
+ *   - Pointers marked [device] are CUDA device pointers owned by the caller;
+ *     [host] are host pointers read during the call only.
+ *   - Calls are asynchronous and ordered on `stream` (a cudaStream_t passed
+ *     as void*; NULL = the legacy default stream).  Results are valid after
+ *     the stream is synchronised.
+ *   - No call allocates device memory except ld_net_create and
+ *     ld_net_reserve; a call that needs a larger workspace than reserved
+ *     grows it first (synchronously) and returns LD_ERR_NOMEM if that fails.
+ *   - Errors are returned as ld_status, never thrown.  Argument errors are
+ *     detected on the host before anything is launched.  Device-side
+ *     conditions (non-finite inputs) are recorded in a status word read by
+ *     ld_net_sync_status.
+ *   - A net handle must not be used from two host threads at once.
+ */
+#ifndef LD_H_
+#define LD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LD_OK = 0,
+  LD_ERR_ARG = 1,          /* null pointer, negative size, bad option value */
+  LD_ERR_SHAPE = 2,        /* layer shapes do not chain, bad conv geometry  */
+  LD_ERR_CUDA = 3,         /* a CUDA runtime call failed                    */
+  LD_ERR_NOMEM = 4,        /* device allocation failed                      */
+  LD_ERR_TIMEOUT = 5,      /* reserved: a bounded device wait gave up       */
+  LD_ERR_NONFINITE = 6,    /* NaN/Inf in an input box, or l0 > u0            */
+  LD_ERR_UNSUPPORTED = 7   /* valid request this build does not implement   */
+} ld_status;
+
+enum { LD_LAYER_FC = 0, LD_LAYER_CONV = 1 };
+
+/* One linear layer x_hat_k = W_k x_{k-1} + b_k (Eq. noncvx_pb).
+ *   FC:   cin = n_{k-1}, h = w = 1, cout = n_k, kh = kw = 1, stride = 1, pad = 0;
+ *         W [host] row-major [cout, cin].
+ *   CONV: input cin x h x w, cout output channels, kh x kw kernel, stride,
+ *         zero padding pad (cross-correlation, as deep-learning convs);
+ *         W [host] [cout, cin, kh, kw].
+ *   b [host] [cout] (a conv bias is shared over the output plane).
+ * An FC layer after a conv layer reads the conv output flattened (C, H, W). */
+typedef struct {
+  int32_t kind;
+  int32_t cin, h, w;
+  int32_t cout, kh, kw, stride, pad;
+  const float* W;
+  const float* b;
+} ld_layer_desc;
+
+enum { LD_INIT_ZERO = 0, LD_INIT_CROWN = 1, LD_INIT_GIVEN = 2 };
+enum { LD_PREC_FP32 = 0, LD_PREC_BF16 = 1 };
+
+/* Solver options.  Defaults (ld_opts_default): alpha 1e-2 -> 1e-4 (linear
+ * decay, Sec. 7.1), Adam beta1 0.9, beta2 0.999, eps 1e-8, CROWN init
+ * (Prop. 3), FP32 arithmetic, FP64 final bound. */
+typedef struct {
+  float alpha0;        /* step size at iteration 0                          */
+  float alpha_end;     /* step size at the last iteration of the schedule   */
+  float beta1, beta2;  /* Adam moment decays                                */
+  float eps;           /* Adam denominator epsilon                          */
+  int32_t init;        /* LD_INIT_*: starting rho (GIVEN reads rho_in)      */
+  int32_t precision;   /* LD_PREC_*: arithmetic of the iterations           */
+  int32_t fp64_final;  /* 1: final q in FP64 with outward slack (sound);
+                          0: final q in FP32, no slack (not a sound bound)  */
+  int32_t t_offset;    /* resumed run: schedule index of this call's first
+                          iteration (Adam bias correction uses t_offset+t+1) */
+  int32_t t_total;     /* schedule length for alpha decay (0: n_iters)      */
+} ld_opts;
+
+typedef struct ld_net ld_net;
+
+/* Fill *opts with the defaults above. */
+void ld_opts_default(ld_opts* opts);
+
+/* Human-readable name of a status code (static string). */
+const char* ld_status_str(ld_status s);
+
+/* Build a network handle (Sec. 2.1 canonical form).
+ *   L [host] n_layers descriptors, layer 1 first.  Every layer but the last
+ *   is followed by a ReLU.  The last layer must be FC.
+ *   margin [host] NULL, or [cout of the last layer]: the property vector c;
+ *   the last layer is folded to W_n = c^T W_last, b_n = c^T b_last (in FP64,
+ *   rounded once to FP32), giving the scalar output of the canonical form.
+ *   With margin == NULL the last layer must have cout == 1.
+ *   *out receives the handle; the handle owns device copies of the weights
+ *   and its workspace.  `stream` orders the weight uploads.
+ * Errors: LD_ERR_ARG (nulls, n_layers < 2), LD_ERR_SHAPE (shapes do not
+ * chain, conv output empty, last layer not FC), LD_ERR_NOMEM, LD_ERR_CUDA. */
+ld_status ld_net_create(const ld_layer_desc* L, int32_t n_layers, const float* margin,
+                        ld_net** out, void* stream);
+
+/* Free a handle and everything it owns (synchronises its streams). */
+ld_status ld_net_destroy(ld_net* net);
+
+/* Sizes of a handle: n_0 (input), N (ReLUs), n (layers), and the number of
+ * weights / biases in the packed gradient layout of ld_bound_backward. */
+ld_status ld_net_sizes(const ld_net* net, int64_t* n0, int64_t* n_relu, int32_t* n_layers,
+                       int64_t* n_weights, int64_t* n_biases);
+
+/* Pre-allocate the workspace for up to B subdomains so that later calls do
+ * not allocate (call it before capturing ld_bound in a CUDA graph). */
+ld_status ld_net_reserve(ld_net* net, int32_t B);
+
+/* Device status word: LD_OK, or the first device-detected error since the
+ * last call (LD_ERR_NONFINITE).  Synchronises `stream`, then clears it. */
+ld_status ld_net_sync_status(ld_net* net, void* stream);
+
+/* Interval bound propagation (Sec. 2.2.3; IBP in Sec. 7.1) for n_props boxes.
+ *   lb0, ub0 [device] [n_props, n_0] float input boxes.
+ *   lbk, ubk [device] [n_props, N] float outputs: bounds of x_hat_k for
+ *   layers 1..n-1 (flat ReLU vector), rounded outward (directed FP32
+ *   rounding), so they contain the exact interval bounds.
+ *   out_lb [device] NULL or [n_props] double: IBP lower bound of x_hat_n.
+ * Errors: LD_ERR_ARG; LD_ERR_NONFINITE (via the status word) if a box holds
+ * NaN/Inf or l0 > u0. */
+ld_status ld_intermediate_bounds(ld_net* net, const float* lb0, const float* ub0, int32_t n_props,
+                                 float* lbk, float* ubk, double* out_lb, void* stream);
+
+/* LD lower bounds for B subdomains after n_iters Adam iterations
+ * (Algorithm 1; Eq. box_bounds_sol and Eq. min-pk for the inner minimum).
+ *   lb0, ub0 [device] [n_props, n_0] float boxes; lbk, ubk [device]
+ *   [n_props, N] float intermediate bounds (e.g. from ld_intermediate_bounds).
+ *   prop_of_subdomain [device] NULL (all subdomains use property 0) or [B]
+ *   int32 in [0, n_props).
+ *   split_masks [device] NULL (no splits) or [B, N] int8 in {-1, 0, +1}:
+ *   +1 fixes the ReLU passing (l <- max(l,0)), -1 blocking (u <- min(u,0))
+ *   (Sec. 2.3.2).  A subdomain whose clamped bounds cross (l > u) is empty:
+ *   its bound is +inf and its rho is left unchanged.
+ *   opts [host] NULL for defaults.
+ *   rho_in [device] [B, N] float, read when opts->init == LD_INIT_GIVEN
+ *   (warm start from a parent's duals); rho_out [device] NULL or [B, N]
+ *   float: rho after the last update.  adam_mv [device] NULL or [2, B, N]
+ *   float: Adam moments m then v, read when opts->t_offset > 0 and written
+ *   back (to resume a run split across calls; NULL starts from zero).
+ *   out [device] [B] double: q(rho_T) evaluated in FP64 and lowered by an
+ *   a-priori rounding-error bound (opts->fp64_final = 1), a valid lower
+ *   bound of min x_hat_n over the subdomain (weak duality, Sec. 3.1).
+ *   n_iters = 0 evaluates q at the initial rho.
+ * Errors: LD_ERR_ARG (nulls, B < 0, n_iters < 0, n_props < 1, options out of
+ * range), LD_ERR_UNSUPPORTED (precision not built), LD_ERR_NOMEM. */
+ld_status ld_bound(ld_net* net, const float* lb0, const float* ub0, const float* lbk,
+                   const float* ubk, int32_t n_props, const int32_t* prop_of_subdomain,
+                   const int8_t* split_masks, int32_t B, int32_t n_iters, const ld_opts* opts,
+                   const float* rho_in, float* rho_out, float* adam_mv, double* out,
+                   void* stream);
+
+/* One inner minimisation at a given rho, in FP32, without any update:
+ * q(rho) (Eq. nonprox_problem), the supergradient x_hat_B - x_hat_A
+ * (Algorithm 1) and the chosen vertex per ReLU.
+ *   rho [device] [B, N] float; q [device] NULL or [B] double (FP32 terms,
+ *   FP64 accumulation); supergrad [device] NULL or [B, N] float;
+ *   vertex [device] NULL or [B, N] int8: 0 = (l,0) or the lower end of the
+ *   box, 1 = (0,0), 2 = (u,u) or the upper end (ties: first strict minimum
+ *   in the order (l,0), (0,0), (u,u); box argmin takes u where its
+ *   coefficient is <= 0).  Other arguments as ld_bound. */
+ld_status ld_dual_supergradient(ld_net* net, const float* lb0, const float* ub0, const float* lbk,
+                                const float* ubk, int32_t n_props, const int32_t* prop_of_subdomain,
+                                const int8_t* split_masks, int32_t B, const float* rho, double* q,
+                                float* supergrad, int8_t* vertex, void* stream);
+
+/* Danskin gradients of sum_b grad_out[b] * q_b(rho_b) at a fixed rho (e.g.
+ * rho_out of ld_bound), recomputing the inner argmins (no stored iterates).
+ * With rho_n = -1:  dq/db_k = -rho_k, dq/dW_k = -rho_k x*_{k-1}^T (conv:
+ * the correlation of rho_k with x*_{k-1}), dq/dl0 = -g_0 where x0* = l0,
+ * dq/du0 = -g_0 where x0* = u0 (g_0 = W_1^T rho_1), and for layer k the
+ * bound on which the chosen vertex lies receives the coefficient of
+ * x_hat_B,k in its subproblem (0 where a split mask clamped that bound).
+ *   rho [device] [B, N]; grad_out [device] [B] double (NULL = all ones).
+ *   Outputs (each [device] float, NULL to skip, overwritten):
+ *   gW [n_weights] packed layer by layer in the layout of the handle's own
+ *   weights (the last layer is the folded 1 x n_{n-1} row); gb [n_biases];
+ *   glb0, gub0 [n_props, n_0]; glbk, gubk [n_props, N] (sums over the
+ *   subdomains of each property).  Empty subdomains contribute nothing.
+ * Errors: as ld_bound. */
+ld_status ld_bound_backward(ld_net* net, const float* lb0, const float* ub0, const float* lbk,
+                            const float* ubk, int32_t n_props, const int32_t* prop_of_subdomain,
+                            const int8_t* split_masks, int32_t B, const float* rho,
+                            const double* grad_out, float* gW, float* gb, float* glb0, float* gub0,
+                            float* glbk, float* gubk, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LD_H_ */

@@ -1,0 +1,281 @@
+"""Thin ctypes binding of libld's C ABI (include/ld.h).
+
+Argument marshalling only: every step of the bound runs in libld's CUDA
+kernels.  Tensors are torch CUDA tensors (device memory and streams come
+from PyTorch); calls are ordered on torch's current CUDA stream.  If the
+library is missing or no GPU is present, the calls raise: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libld.so")
+
+LD_OK, LD_ERR_ARG, LD_ERR_SHAPE, LD_ERR_CUDA, LD_ERR_NOMEM, LD_ERR_TIMEOUT, LD_ERR_NONFINITE, LD_ERR_UNSUPPORTED = range(8)
+LD_LAYER_FC, LD_LAYER_CONV = 0, 1
+LD_INIT_ZERO, LD_INIT_CROWN, LD_INIT_GIVEN = 0, 1, 2
+LD_PREC_FP32, LD_PREC_BF16 = 0, 1
+
+EXPORTED = [
+    "ld_opts_default", "ld_status_str", "ld_net_create", "ld_net_destroy", "ld_net_sizes", "ld_net_reserve",
+    "ld_net_sync_status", "ld_intermediate_bounds", "ld_bound", "ld_dual_supergradient", "ld_bound_backward",
+]
+
+
+class LDError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {status_str(code)} (status {code})")
+
+
+class LayerDesc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("cin", C.c_int32), ("h", C.c_int32), ("w", C.c_int32),
+                ("cout", C.c_int32), ("kh", C.c_int32), ("kw", C.c_int32), ("stride", C.c_int32),
+                ("pad", C.c_int32), ("W", C.c_void_p), ("b", C.c_void_p)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("alpha0", C.c_float), ("alpha_end", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
+                ("eps", C.c_float), ("init", C.c_int32), ("precision", C.c_int32), ("fp64_final", C.c_int32),
+                ("t_offset", C.c_int32), ("t_total", C.c_int32)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libld.so (built in-tree by paper_2104_06718_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libld.so not found at {path}: run `python -m paper_2104_06718_gb300.build` "
+                           "(nvcc, sm_103a) first; there is no CPU fallback")
+    lib = C.CDLL(path)
+    vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+    lib.ld_opts_default.argtypes = [C.POINTER(Opts)]
+    lib.ld_opts_default.restype = None
+    lib.ld_status_str.argtypes = [C.c_int]
+    lib.ld_status_str.restype = C.c_char_p
+    lib.ld_net_create.argtypes = [C.POINTER(LayerDesc), i32, vp, C.POINTER(vp), vp]
+    lib.ld_net_destroy.argtypes = [vp]
+    lib.ld_net_sizes.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i32), C.POINTER(i64), C.POINTER(i64)]
+    lib.ld_net_reserve.argtypes = [vp, i32]
+    lib.ld_net_sync_status.argtypes = [vp, vp]
+    lib.ld_intermediate_bounds.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp]
+    lib.ld_bound.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, i32, i32, C.POINTER(Opts), vp, vp, vp, vp, vp]
+    lib.ld_dual_supergradient.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, i32, vp, vp, vp, vp, vp]
+    lib.ld_bound_backward.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    for name in EXPORTED:
+        if name not in ("ld_opts_default", "ld_status_str"):
+            getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def status_str(code: int) -> str:
+    try:
+        return load_library().ld_status_str(int(code)).decode()
+    except RuntimeError:
+        return "unknown"
+
+
+def _check(code, where):
+    if code != LD_OK:
+        raise LDError(code, where)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("libld takes CUDA tensors")
+    if not t.is_contiguous():
+        raise ValueError("libld takes contiguous tensors")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev(x, dtype):
+    if isinstance(x, torch.Tensor):
+        t = x.to(device="cuda", dtype=dtype)
+    else:
+        t = torch.as_tensor(np.asarray(x), dtype=dtype, device="cuda")
+    return t.contiguous()
+
+
+@dataclass
+class Options:
+    """Solver options (ld_opts): step size alpha0 -> alpha_end decayed
+    linearly (Sec. 7.1), Adam moments, initialisation (Prop. 3 CROWN by
+    default), FP64 final bound."""
+    alpha0: float = 1e-2
+    alpha_end: float = 1e-4
+    beta1: float = 0.9
+    beta2: float = 0.999
+    eps: float = 1e-8
+    init: str = "crown"          # "zero" | "crown" | "given"
+    precision: str = "fp32"      # "fp32" | "bf16"
+    fp64_final: bool = True
+    t_offset: int = 0
+    t_total: int = 0
+
+    def to_c(self) -> Opts:
+        return Opts(self.alpha0, self.alpha_end, self.beta1, self.beta2, self.eps,
+                    {"zero": LD_INIT_ZERO, "crown": LD_INIT_CROWN, "given": LD_INIT_GIVEN}[self.init],
+                    {"fp32": LD_PREC_FP32, "bf16": LD_PREC_BF16}[self.precision],
+                    int(self.fp64_final), self.t_offset, self.t_total)
+
+
+class Net:
+    """An ld_net handle: device copies of a ReLU net in canonical form.
+
+    specs: sequence of layer specs with attributes kind ('fc'|'conv'), W, b,
+    in_shape, stride, pad (see paper_2104_06718_gb300.synth.LayerSpec).
+    margin: None, or the property vector c folded into the last layer.
+    """
+
+    def __init__(self, specs, margin=None):
+        lib = load_library()
+        self._keep = []
+        descs = (LayerDesc * len(specs))()
+        for d, s in zip(descs, specs):
+            W = np.ascontiguousarray(np.asarray(s.W, dtype=np.float32))
+            b = np.ascontiguousarray(np.asarray(s.b, dtype=np.float32))
+            self._keep += [W, b]
+            if s.kind == "fc":
+                d.kind, d.cin, d.h, d.w = LD_LAYER_FC, W.shape[1], 1, 1
+                d.cout, d.kh, d.kw, d.stride, d.pad = W.shape[0], 1, 1, 1, 0
+            else:
+                c, h, w = s.in_shape
+                d.kind, d.cin, d.h, d.w = LD_LAYER_CONV, c, h, w
+                d.cout, d.kh, d.kw, d.stride, d.pad = W.shape[0], W.shape[2], W.shape[3], s.stride, s.pad
+            d.W = W.ctypes.data
+            d.b = b.ctypes.data
+        mptr = None
+        if margin is not None:
+            m = np.ascontiguousarray(np.asarray(margin, dtype=np.float32))
+            self._keep.append(m)
+            mptr = C.c_void_p(m.ctypes.data)
+        h = C.c_void_p()
+        torch.cuda.init()
+        _check(lib.ld_net_create(descs, len(specs), mptr, C.byref(h), _stream()), "ld_net_create")
+        self._h = h
+        self._lib = lib
+        n0, N, nl, nw, nb = C.c_int64(), C.c_int64(), C.c_int32(), C.c_int64(), C.c_int64()
+        _check(lib.ld_net_sizes(h, C.byref(n0), C.byref(N), C.byref(nl), C.byref(nw), C.byref(nb)), "ld_net_sizes")
+        self.n0, self.N, self.n_layers, self.n_weights, self.n_biases = n0.value, N.value, nl.value, nw.value, nb.value
+        self.specs = list(specs)
+        self.margin = None if margin is None else np.asarray(margin, np.float32)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.ld_net_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def reserve(self, B: int):
+        _check(self._lib.ld_net_reserve(self._h, int(B)), "ld_net_reserve")
+
+    def sync_status(self):
+        return self._lib.ld_net_sync_status(self._h, _stream())
+
+
+def ld_intermediate_bounds(net: Net, lb0, ub0, want_output_lb: bool = False):
+    """IBP bounds of layers 1..n-1 ([P, N] each, outward rounded) and,
+    optionally, the IBP lower bound of the output ([P] float64)."""
+    lb0 = _dev(lb0, torch.float32)
+    ub0 = _dev(ub0, torch.float32)
+    if lb0.dim() == 1:
+        lb0, ub0 = lb0[None], ub0[None]
+    P = lb0.shape[0]
+    lbk = torch.empty((P, net.N), dtype=torch.float32, device="cuda")
+    ubk = torch.empty_like(lbk)
+    out_lb = torch.empty(P, dtype=torch.float64, device="cuda") if want_output_lb else None
+    _check(net._lib.ld_intermediate_bounds(net.handle, _ptr(lb0), _ptr(ub0), P, _ptr(lbk), _ptr(ubk), _ptr(out_lb),
+                                           _stream()), "ld_intermediate_bounds")
+    return (lbk, ubk, out_lb) if want_output_lb else (lbk, ubk)
+
+
+def _problem(lb0, ub0, lbk, ubk, prop, masks, B):
+    lb0 = _dev(lb0, torch.float32)
+    ub0 = _dev(ub0, torch.float32)
+    if lb0.dim() == 1:
+        lb0, ub0 = lb0[None], ub0[None]
+    lbk = _dev(lbk, torch.float32)
+    ubk = _dev(ubk, torch.float32)
+    if lbk.dim() == 1:
+        lbk, ubk = lbk[None], ubk[None]
+    prop = None if prop is None else _dev(prop, torch.int32)
+    masks = None if masks is None else _dev(masks, torch.int8)
+    if B is None:
+        B = masks.shape[0] if masks is not None else (prop.shape[0] if prop is not None else 1)
+    return lb0, ub0, lbk, ubk, prop, masks, int(B)
+
+
+def ld_bound(net: Net, lb0, ub0, lbk, ubk, prop=None, masks=None, n_iters: int = 100, opts: Options | None = None,
+             rho_in=None, B: int | None = None, return_rho: bool = False, adam_mv=None):
+    """Lower bounds [B] (float64) after n_iters Adam iterations (Algorithm 1).
+    With return_rho, also returns rho_T [B, N] (float32)."""
+    lb0, ub0, lbk, ubk, prop, masks, B = _problem(lb0, ub0, lbk, ubk, prop, masks, B)
+    o = (opts or Options())
+    if rho_in is not None and o.init != "given":
+        o = Options(**{**o.__dict__, "init": "given"})
+    rho_in = None if rho_in is None else _dev(rho_in, torch.float32)
+    out = torch.empty(B, dtype=torch.float64, device="cuda")
+    rho_out = torch.empty((B, net.N), dtype=torch.float32, device="cuda") if return_rho else None
+    oc = o.to_c()
+    _check(net._lib.ld_bound(net.handle, _ptr(lb0), _ptr(ub0), _ptr(lbk), _ptr(ubk), lbk.shape[0], _ptr(prop),
+                             _ptr(masks), B, int(n_iters), C.byref(oc), _ptr(rho_in), _ptr(rho_out), _ptr(adam_mv),
+                             _ptr(out), _stream()), "ld_bound")
+    return (out, rho_out) if return_rho else out
+
+
+def ld_dual_supergradient(net: Net, lb0, ub0, lbk, ubk, rho, prop=None, masks=None):
+    """q(rho) [B] float64, supergradient [B, N] float32 and vertex codes [B, N]
+    int8 at a given rho, in FP32 (no update)."""
+    rho = _dev(rho, torch.float32)
+    lb0, ub0, lbk, ubk, prop, masks, B = _problem(lb0, ub0, lbk, ubk, prop, masks, rho.shape[0])
+    q = torch.empty(B, dtype=torch.float64, device="cuda")
+    sg = torch.empty((B, net.N), dtype=torch.float32, device="cuda")
+    vtx = torch.empty((B, net.N), dtype=torch.int8, device="cuda")
+    _check(net._lib.ld_dual_supergradient(net.handle, _ptr(lb0), _ptr(ub0), _ptr(lbk), _ptr(ubk), lbk.shape[0],
+                                          _ptr(prop), _ptr(masks), B, _ptr(rho), _ptr(q), _ptr(sg), _ptr(vtx),
+                                          _stream()), "ld_dual_supergradient")
+    return q, sg, vtx
+
+
+def ld_bound_backward(net: Net, lb0, ub0, lbk, ubk, rho, grad_out=None, prop=None, masks=None):
+    """Danskin gradients at fixed rho: dict with gW (packed), gb, glb0, gub0,
+    glbk, gubk (float32 device tensors)."""
+    rho = _dev(rho, torch.float32)
+    lb0, ub0, lbk, ubk, prop, masks, B = _problem(lb0, ub0, lbk, ubk, prop, masks, rho.shape[0])
+    P = lbk.shape[0]
+    go = None if grad_out is None else _dev(grad_out, torch.float64)
+    f = lambda *shape: torch.empty(shape, dtype=torch.float32, device="cuda")
+    out = {"gW": f(net.n_weights), "gb": f(net.n_biases), "glb0": f(P, net.n0), "gub0": f(P, net.n0),
+           "glbk": f(P, net.N), "gubk": f(P, net.N)}
+    _check(net._lib.ld_bound_backward(net.handle, _ptr(lb0), _ptr(ub0), _ptr(lbk), _ptr(ubk), P, _ptr(prop),
+                                      _ptr(masks), B, _ptr(rho), _ptr(go), _ptr(out["gW"]), _ptr(out["gb"]),
+                                      _ptr(out["glb0"]), _ptr(out["gub0"]), _ptr(out["glbk"]), _ptr(out["gubk"]),
+                                      _stream()), "ld_bound_backward")
+    return out

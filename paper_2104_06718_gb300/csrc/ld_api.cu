@@ -1,0 +1,509 @@
+// C ABI of libld (declared in include/ld.h): argument checking, the net
+// handle, workspace ownership and the order of the passes of one call.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ld_common.cuh"
+
+using ld::LayerDev;
+using ld::Problem;
+
+struct ld_net {
+  int n = 0;
+  int64_t n0 = 0, N = 0;
+  int XS = 0;
+  std::vector<LayerDev> L;            // L[k-1] = layer k of the paper
+  std::vector<size_t> w_off, b_off;   // packed weight / bias offsets
+  size_t n_w = 0, n_b = 0;
+  float* d_W = nullptr;
+  float* d_b = nullptr;
+  int* d_status = nullptr;
+  double bn = 0.0;                    // folded output bias b_n
+  // workspace, sized for ws_B subdomains
+  int ws_B = -1;
+  void* ws = nullptr;
+  float *rho = nullptr, *m = nullptr, *v = nullptr, *x = nullptr, *g = nullptr, *xB = nullptr;
+  float *scr_bn = nullptr, *scr_b0 = nullptr;
+  int8_t *empty = nullptr, *vtx = nullptr;
+  double* acc = nullptr;
+};
+
+namespace {
+
+inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+ld_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return LD_OK;
+  if (e == cudaErrorMemoryAllocation) return LD_ERR_NOMEM;
+  return LD_ERR_CUDA;
+}
+
+ld_status last_error() { return cuda_status(cudaGetLastError()); }
+
+void free_ws(ld_net* net) {
+  if (net->ws) cudaFree(net->ws);
+  net->ws = nullptr;
+  net->ws_B = -1;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+ld_status ensure_ws(ld_net* net, int B) {
+  if (B <= net->ws_B) return LD_OK;
+  const size_t Bn = (size_t)(B > 0 ? B : 1);
+  const size_t N = (size_t)net->N, XS = (size_t)net->XS, n0 = (size_t)net->n0;
+  const size_t sizes[] = {
+      4 * Bn * N,        // rho
+      4 * Bn * N,        // m
+      4 * Bn * N,        // v
+      4 * Bn * XS,       // x
+      4 * Bn * XS,       // g
+      4 * Bn * N,        // xB
+      4 * 2 * Bn * N,    // scr_bn
+      4 * 2 * Bn * n0,   // scr_b0
+      Bn,                // empty
+      Bn * N,            // vtx
+      8 * 3 * Bn,        // acc
+  };
+  size_t total = 0;
+  for (size_t s : sizes) total += align256(s);
+  cudaDeviceSynchronize();
+  free_ws(net);
+  void* p = nullptr;
+  if (cudaMalloc(&p, total) != cudaSuccess) {
+    cudaGetLastError();
+    return LD_ERR_NOMEM;
+  }
+  net->ws = p;
+  char* c = static_cast<char*>(p);
+  void* ptrs[11];
+  for (int i = 0; i < 11; ++i) {
+    ptrs[i] = c;
+    c += align256(sizes[i]);
+  }
+  net->rho = (float*)ptrs[0];
+  net->m = (float*)ptrs[1];
+  net->v = (float*)ptrs[2];
+  net->x = (float*)ptrs[3];
+  net->g = (float*)ptrs[4];
+  net->xB = (float*)ptrs[5];
+  net->scr_bn = (float*)ptrs[6];
+  net->scr_b0 = (float*)ptrs[7];
+  net->empty = (int8_t*)ptrs[8];
+  net->vtx = (int8_t*)ptrs[9];
+  net->acc = (double*)ptrs[10];
+  net->ws_B = B > 0 ? B : 1;
+  return LD_OK;
+}
+
+int r_off(const ld_net* net, int k) { return k >= 1 ? net->L[k - 1].r_out_off : 0; }
+int x_off(const ld_net* net, int k) { return k >= 1 ? (int)net->n0 + net->L[k - 1].r_out_off : 0; }
+const LayerDev& layer(const ld_net* net, int k) { return net->L[k - 1]; }
+int plane_of(const LayerDev& L) { return L.kind == LD_LAYER_FC ? 1 : L.ho * L.wo; }
+
+ld_status check_opts(const ld_opts& o) {
+  if (!(std::isfinite(o.alpha0) && std::isfinite(o.alpha_end) && o.alpha0 >= 0 && o.alpha_end >= 0)) return LD_ERR_ARG;
+  if (!(o.beta1 >= 0 && o.beta1 < 1 && o.beta2 >= 0 && o.beta2 < 1 && o.eps > 0)) return LD_ERR_ARG;
+  if (o.init < LD_INIT_ZERO || o.init > LD_INIT_GIVEN) return LD_ERR_ARG;
+  if (o.precision != LD_PREC_FP32 && o.precision != LD_PREC_BF16) return LD_ERR_ARG;
+  if (o.precision == LD_PREC_BF16) return LD_ERR_UNSUPPORTED;
+  if (o.t_offset < 0 || o.t_total < 0) return LD_ERR_ARG;
+  return LD_OK;
+}
+
+ld_status check_problem(const ld_net* net, const float* lb0, const float* ub0, const float* lbk, const float* ubk,
+                        int32_t n_props, int32_t B) {
+  if (!net) return LD_ERR_ARG;
+  if (B < 0 || n_props < 1) return LD_ERR_ARG;
+  if (!lb0 || !ub0 || !lbk || !ubk) return LD_ERR_ARG;
+  if (B > 65535) return LD_ERR_UNSUPPORTED;  // grid rows per subdomain in the conv passes
+  return LD_OK;
+}
+
+Problem make_problem(ld_net* net, const float* lb0, const float* ub0, const float* lbk, const float* ubk,
+                     int32_t n_props, const int32_t* prop, const int8_t* masks, int32_t B) {
+  Problem P;
+  P.B = B;
+  P.N = (int)net->N;
+  P.n0 = (int)net->n0;
+  P.XS = net->XS;
+  P.n_props = n_props;
+  P.l0 = lb0;
+  P.u0 = ub0;
+  P.lbk = lbk;
+  P.ubk = ubk;
+  P.prop = prop;
+  P.mask = masks;
+  P.empty = net->empty;
+  return P;
+}
+
+// rho^0 from CROWN (Prop. 3): one transposed sweep with the CROWN epilogue.
+void crown_sweep(ld_net* net, const Problem& P, cudaStream_t s) {
+  const int n = net->n;
+  ld::EpiCrown top{P, r_off(net, n - 1), net->rho};
+  ld::launch_top_crown(layer(net, n), P, top, s);
+  for (int k = n - 1; k >= 2; --k) {
+    ld::EpiCrown e{P, r_off(net, k - 1), net->rho};
+    ld::launch_transposed_crown(layer(net, k), P, net->rho, e, s);
+  }
+}
+
+// One inner minimisation (top-down over the layer pairs) followed, for each
+// pair, by the forward pass of the layer above it.  mode 0: Adam update;
+// mode 1: record supergradient and q; mode 2: argmins only (g kept).
+void sweep(ld_net* net, const Problem& P, int mode, const ld_opts& o, ld::AdamStep st, float* sg, double* q,
+           int8_t* vtx, float* g_keep, cudaStream_t s) {
+  const int n = net->n;
+  for (int k = n - 1; k >= 0; --k) {
+    ld::EpiArgmin ea{P, k, r_off(net, k), x_off(net, k), net->rho, net->x, net->xB, vtx, g_keep};
+    if (k == n - 1)
+      ld::launch_top_argmin(layer(net, n), P, ea, s);
+    else
+      ld::launch_transposed_argmin(layer(net, k + 1), nullptr, P, net->rho, ea, s);
+    if (mode == 2) continue;
+    const LayerDev& Lk1 = layer(net, k + 1);
+    if (mode == 0) {
+      if (k + 1 <= n - 1) {
+        ld::EpiAdam ep{P, Lk1.r_out_off, plane_of(Lk1), Lk1.b, net->xB, net->rho, net->m, net->v,
+                       o.beta1, o.beta2, o.eps, st};
+        ld::launch_forward_adam(Lk1, P, net->x, ep, s);
+      }
+    } else {
+      ld::EpiRecord er{P, Lk1.r_out_off, plane_of(Lk1), k + 1 == n ? 1 : 0, Lk1.b, net->xB, net->rho, sg, q};
+      ld::launch_forward_record(Lk1, P, net->x, er, s);
+    }
+  }
+}
+
+void final_fp64(ld_net* net, const Problem& P, double* out, cudaStream_t s) {
+  const int n = net->n;
+  ld::FinalAcc acc{net->acc, net->acc + P.B, net->acc + 2 * (size_t)P.B};
+  cudaMemsetAsync(net->acc, 0, sizeof(double) * 3 * (size_t)P.B, s);
+  for (int k = n - 1; k >= 0; --k)
+    ld::launch_final_layer(layer(net, k + 1), k, r_off(net, k), x_off(net, k), P, net->rho, k == n - 1 ? 1 : 0, acc,
+                           s);
+  ld::launch_final_bias(net->L, P, net->rho, acc, s);
+  const double M = (double)(net->n0 + 2 * net->N + 1);
+  const double gM = ld::final_gamma(M);
+  ld::launch_final_combine_bn(P, acc, net->bn, gM, 1.0 + 2.0 * gM, out, s);
+}
+
+// q in FP32 terms (FP64 sum) via the forward form, +inf for empty subdomains.
+void final_fp32(ld_net* net, const Problem& P, double* out, float* sg, int8_t* vtx, cudaStream_t s) {
+  ld::FinalAcc acc{net->acc, net->acc + P.B, net->acc + 2 * (size_t)P.B};
+  cudaMemsetAsync(net->acc, 0, sizeof(double) * 3 * (size_t)P.B, s);
+  ld::AdamStep st{};
+  ld_opts o;
+  ld_opts_default(&o);
+  sweep(net, P, 1, o, st, sg, net->acc, vtx, nullptr, s);
+  if (out) ld::launch_final_combine_bn(P, acc, 0.0, 0.0, 1.0, out, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+void ld_opts_default(ld_opts* o) {
+  if (!o) return;
+  o->alpha0 = 1e-2f;
+  o->alpha_end = 1e-4f;
+  o->beta1 = 0.9f;
+  o->beta2 = 0.999f;
+  o->eps = 1e-8f;
+  o->init = LD_INIT_CROWN;
+  o->precision = LD_PREC_FP32;
+  o->fp64_final = 1;
+  o->t_offset = 0;
+  o->t_total = 0;
+}
+
+const char* ld_status_str(ld_status s) {
+  switch (s) {
+    case LD_OK: return "ok";
+    case LD_ERR_ARG: return "invalid argument";
+    case LD_ERR_SHAPE: return "layer shapes do not chain";
+    case LD_ERR_CUDA: return "CUDA runtime error";
+    case LD_ERR_NOMEM: return "device allocation failed";
+    case LD_ERR_TIMEOUT: return "device wait timed out";
+    case LD_ERR_NONFINITE: return "non-finite or inverted input box";
+    case LD_ERR_UNSUPPORTED: return "unsupported request";
+  }
+  return "unknown status";
+}
+
+ld_status ld_net_create(const ld_layer_desc* Ld, int32_t n_layers, const float* margin, ld_net** out, void* stream) {
+  if (!Ld || !out || n_layers < 2 || n_layers > ld::kMaxLayers) return LD_ERR_ARG;
+  *out = nullptr;
+  std::vector<LayerDev> L(n_layers);
+  std::vector<size_t> w_off(n_layers), b_off(n_layers);
+  size_t n_w = 0, n_b = 0;
+  int64_t prev_out = -1;
+  int prev_c = -1, prev_h = -1, prev_w = -1;
+  for (int k = 0; k < n_layers; ++k) {
+    const ld_layer_desc& d = Ld[k];
+    if (!d.W || !d.b) return LD_ERR_ARG;
+    LayerDev& l = L[k];
+    std::memset(&l, 0, sizeof(l));
+    l.kind = d.kind;
+    if (d.kind == LD_LAYER_FC) {
+      if (d.cin < 1 || d.cout < 1) return LD_ERR_SHAPE;
+      l.cin = d.cin; l.h = 1; l.w = 1; l.cout = d.cout; l.ho = 1; l.wo = 1;
+      l.kh = 1; l.kw = 1; l.stride = 1; l.pad = 0;
+      l.n_in = d.cin;
+      l.n_out = d.cout;
+      l.fan_t = d.cout;
+    } else if (d.kind == LD_LAYER_CONV) {
+      if (d.cin < 1 || d.h < 1 || d.w < 1 || d.cout < 1 || d.kh < 1 || d.kw < 1 || d.stride < 1 || d.pad < 0)
+        return LD_ERR_SHAPE;
+      l.cin = d.cin; l.h = d.h; l.w = d.w; l.cout = d.cout;
+      l.kh = d.kh; l.kw = d.kw; l.stride = d.stride; l.pad = d.pad;
+      l.ho = (d.h + 2 * d.pad - d.kh) / d.stride + 1;
+      l.wo = (d.w + 2 * d.pad - d.kw) / d.stride + 1;
+      if (d.h + 2 * d.pad < d.kh || d.w + 2 * d.pad < d.kw || l.ho < 1 || l.wo < 1) return LD_ERR_SHAPE;
+      l.n_in = d.cin * d.h * d.w;
+      l.n_out = d.cout * l.ho * l.wo;
+      l.fan_t = d.cout * ((d.kh + d.stride - 1) / d.stride) * ((d.kw + d.stride - 1) / d.stride);
+      if ((size_t)d.cout * d.cin * d.kh * d.kw > 12288) return LD_ERR_UNSUPPORTED;  // weights staged in 48 KB smem
+      if (k > 0 && prev_c >= 0 && (prev_c != d.cin || prev_h != d.h || prev_w != d.w)) return LD_ERR_SHAPE;
+    } else {
+      return LD_ERR_ARG;
+    }
+    if (k > 0 && prev_out != l.n_in) return LD_ERR_SHAPE;
+    prev_out = l.n_out;
+    if (d.kind == LD_LAYER_CONV) {
+      prev_c = l.cout; prev_h = l.ho; prev_w = l.wo;
+    } else {
+      prev_c = -1;
+    }
+    w_off[k] = n_w;
+    b_off[k] = n_b;
+    const size_t nw = (size_t)l.cout * l.cin * l.kh * l.kw;
+    n_w += (k == n_layers - 1) ? (size_t)l.n_in : nw;   // last layer is folded to one row
+    n_b += (k == n_layers - 1) ? 1 : (size_t)l.cout;
+  }
+  const ld_layer_desc& last = Ld[n_layers - 1];
+  if (last.kind != LD_LAYER_FC) return LD_ERR_SHAPE;
+  if (!margin && last.cout != 1) return LD_ERR_SHAPE;
+
+  // Host copies of the packed parameters, last layer folded with the margin.
+  std::vector<float> hW(n_w), hb(n_b);
+  for (int k = 0; k < n_layers; ++k) {
+    const ld_layer_desc& d = Ld[k];
+    if (k < n_layers - 1) {
+      std::memcpy(&hW[w_off[k]], d.W, sizeof(float) * (size_t)d.cout * d.cin * (d.kind == LD_LAYER_FC ? 1 : d.kh * d.kw));
+      std::memcpy(&hb[b_off[k]], d.b, sizeof(float) * (size_t)d.cout);
+    } else {
+      double bsum = 0.0;
+      for (int i = 0; i < d.cin; ++i) {
+        double s = 0.0;
+        for (int o = 0; o < d.cout; ++o) s += (margin ? (double)margin[o] : 1.0) * (double)d.W[(size_t)o * d.cin + i];
+        hW[w_off[k] + i] = (float)s;
+      }
+      for (int o = 0; o < d.cout; ++o) bsum += (margin ? (double)margin[o] : 1.0) * (double)d.b[o];
+      hb[b_off[k]] = (float)bsum;
+    }
+  }
+
+  ld_net* net = new (std::nothrow) ld_net();
+  if (!net) return LD_ERR_NOMEM;
+  net->n = n_layers;
+  net->n0 = L[0].n_in;
+  int64_t off = 0;
+  for (int k = 0; k < n_layers; ++k) {
+    L[k].x_in_off = k == 0 ? 0 : (int)(L[0].n_in + L[k - 1].r_out_off);
+    if (k < n_layers - 1) {
+      L[k].r_out_off = (int)off;
+      off += L[k].n_out;
+    } else {
+      L[k].r_out_off = 0;  // rho_n = -1 is implicit
+      L[k].cout = 1;
+      L[k].n_out = 1;
+      L[k].fan_t = 1;
+    }
+  }
+  net->N = off;
+  net->XS = (int)(net->n0 + net->N);
+  net->w_off = w_off;
+  net->b_off = b_off;
+  net->n_w = n_w;
+  net->n_b = n_b;
+  net->bn = (double)hb[b_off[n_layers - 1]];
+  cudaStream_t s = S(stream);
+  ld_status st = cuda_status(cudaMalloc(&net->d_W, sizeof(float) * n_w));
+  if (st == LD_OK) st = cuda_status(cudaMalloc(&net->d_b, sizeof(float) * n_b));
+  if (st == LD_OK) st = cuda_status(cudaMalloc(&net->d_status, sizeof(int)));
+  if (st == LD_OK) st = cuda_status(cudaMemcpyAsync(net->d_W, hW.data(), sizeof(float) * n_w, cudaMemcpyHostToDevice, s));
+  if (st == LD_OK) st = cuda_status(cudaMemcpyAsync(net->d_b, hb.data(), sizeof(float) * n_b, cudaMemcpyHostToDevice, s));
+  if (st == LD_OK) st = cuda_status(cudaMemsetAsync(net->d_status, 0, sizeof(int), s));
+  if (st == LD_OK) st = cuda_status(cudaStreamSynchronize(s));
+  if (st != LD_OK) {
+    ld_net_destroy(net);
+    return st;
+  }
+  for (int k = 0; k < n_layers; ++k) {
+    L[k].W = net->d_W + w_off[k];
+    L[k].b = net->d_b + b_off[k];
+  }
+  net->L = L;
+  *out = net;
+  return LD_OK;
+}
+
+ld_status ld_net_destroy(ld_net* net) {
+  if (!net) return LD_ERR_ARG;
+  cudaDeviceSynchronize();
+  free_ws(net);
+  if (net->d_W) cudaFree(net->d_W);
+  if (net->d_b) cudaFree(net->d_b);
+  if (net->d_status) cudaFree(net->d_status);
+  delete net;
+  return LD_OK;
+}
+
+ld_status ld_net_sizes(const ld_net* net, int64_t* n0, int64_t* n_relu, int32_t* n_layers, int64_t* n_weights,
+                       int64_t* n_biases) {
+  if (!net) return LD_ERR_ARG;
+  if (n0) *n0 = net->n0;
+  if (n_relu) *n_relu = net->N;
+  if (n_layers) *n_layers = net->n;
+  if (n_weights) *n_weights = (int64_t)net->n_w;
+  if (n_biases) *n_biases = (int64_t)net->n_b;
+  return LD_OK;
+}
+
+ld_status ld_net_reserve(ld_net* net, int32_t B) {
+  if (!net || B < 0) return LD_ERR_ARG;
+  return ensure_ws(net, B);
+}
+
+ld_status ld_net_sync_status(ld_net* net, void* stream) {
+  if (!net) return LD_ERR_ARG;
+  int h = 0;
+  ld_status st = cuda_status(cudaMemcpyAsync(&h, net->d_status, sizeof(int), cudaMemcpyDeviceToHost, S(stream)));
+  if (st == LD_OK) st = cuda_status(cudaStreamSynchronize(S(stream)));
+  if (st != LD_OK) return st;
+  cudaMemsetAsync(net->d_status, 0, sizeof(int), S(stream));
+  return (ld_status)h;
+}
+
+ld_status ld_intermediate_bounds(ld_net* net, const float* lb0, const float* ub0, int32_t n_props, float* lbk,
+                                 float* ubk, double* out_lb, void* stream) {
+  if (!net || !lb0 || !ub0 || !lbk || !ubk || n_props < 1) return LD_ERR_ARG;
+  cudaStream_t s = S(stream);
+  const int n = net->n;
+  for (int k = 1; k <= n; ++k) {
+    const LayerDev& L = layer(net, k);
+    const float* lin = k == 1 ? lb0 : lbk + r_off(net, k - 1);
+    const float* uin = k == 1 ? ub0 : ubk + r_off(net, k - 1);
+    const int in_stride = k == 1 ? (int)net->n0 : (int)net->N;
+    const bool last = k == n;
+    if (last && !out_lb) break;
+    ld::launch_ibp_layer(L, k == 1, last, n_props, lin, uin, in_stride, last ? nullptr : lbk + L.r_out_off,
+                         last ? nullptr : ubk + L.r_out_off, (int)net->N, out_lb, net->d_status, s);
+  }
+  return last_error();
+}
+
+ld_status ld_bound(ld_net* net, const float* lb0, const float* ub0, const float* lbk, const float* ubk,
+                   int32_t n_props, const int32_t* prop, const int8_t* masks, int32_t B, int32_t n_iters,
+                   const ld_opts* opts, const float* rho_in, float* rho_out, float* adam_mv, double* out,
+                   void* stream) {
+  ld_status st = check_problem(net, lb0, ub0, lbk, ubk, n_props, B);
+  if (st != LD_OK) return st;
+  if (n_iters < 0 || !out) return LD_ERR_ARG;
+  ld_opts o;
+  if (opts) o = *opts; else ld_opts_default(&o);
+  if ((st = check_opts(o)) != LD_OK) return st;
+  if (o.init == LD_INIT_GIVEN && !rho_in) return LD_ERR_ARG;
+  if (B == 0) return LD_OK;
+  if ((st = ensure_ws(net, B)) != LD_OK) return st;
+  cudaStream_t s = S(stream);
+  const Problem P = make_problem(net, lb0, ub0, lbk, ubk, n_props, prop, masks, B);
+  const size_t BN = (size_t)B * net->N;
+  ld::launch_empty_flags(P, net->empty, net->d_status, s);
+  if (o.init == LD_INIT_GIVEN)
+    cudaMemcpyAsync(net->rho, rho_in, sizeof(float) * BN, cudaMemcpyDeviceToDevice, s);
+  else if (o.init == LD_INIT_ZERO)
+    cudaMemsetAsync(net->rho, 0, sizeof(float) * BN, s);
+  else
+    crown_sweep(net, P, s);
+  if (adam_mv && o.t_offset > 0) {
+    cudaMemcpyAsync(net->m, adam_mv, sizeof(float) * BN, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(net->v, adam_mv + BN, sizeof(float) * BN, cudaMemcpyDeviceToDevice, s);
+  } else {
+    cudaMemsetAsync(net->m, 0, sizeof(float) * BN, s);
+    cudaMemsetAsync(net->v, 0, sizeof(float) * BN, s);
+  }
+  const int T_sched = o.t_total > 0 ? o.t_total : o.t_offset + n_iters;
+  for (int t = 0; t < n_iters; ++t) {
+    const int tt = o.t_offset + t;
+    ld::AdamStep a;
+    const double alpha = (double)o.alpha0 + ((double)o.alpha_end - (double)o.alpha0) * (double)tt /
+                                                (double)(T_sched - 1 > 1 ? T_sched - 1 : 1);
+    a.alpha = (float)alpha;
+    a.inv_bc1 = (float)(1.0 / (1.0 - std::pow((double)o.beta1, (double)(tt + 1))));
+    a.inv_bc2 = (float)(1.0 / (1.0 - std::pow((double)o.beta2, (double)(tt + 1))));
+    sweep(net, P, 0, o, a, nullptr, nullptr, nullptr, nullptr, s);
+  }
+  if (o.fp64_final)
+    final_fp64(net, P, out, s);
+  else
+    final_fp32(net, P, out, nullptr, nullptr, s);
+  if (rho_out) cudaMemcpyAsync(rho_out, net->rho, sizeof(float) * BN, cudaMemcpyDeviceToDevice, s);
+  if (adam_mv) {
+    cudaMemcpyAsync(adam_mv, net->m, sizeof(float) * BN, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(adam_mv + BN, net->v, sizeof(float) * BN, cudaMemcpyDeviceToDevice, s);
+  }
+  return last_error();
+}
+
+ld_status ld_dual_supergradient(ld_net* net, const float* lb0, const float* ub0, const float* lbk, const float* ubk,
+                                int32_t n_props, const int32_t* prop, const int8_t* masks, int32_t B, const float* rho,
+                                double* q, float* supergrad, int8_t* vertex, void* stream) {
+  ld_status st = check_problem(net, lb0, ub0, lbk, ubk, n_props, B);
+  if (st != LD_OK) return st;
+  if (!rho) return LD_ERR_ARG;
+  if (B == 0) return LD_OK;
+  if ((st = ensure_ws(net, B)) != LD_OK) return st;
+  cudaStream_t s = S(stream);
+  const Problem P = make_problem(net, lb0, ub0, lbk, ubk, n_props, prop, masks, B);
+  ld::launch_empty_flags(P, net->empty, net->d_status, s);
+  cudaMemcpyAsync(net->rho, rho, sizeof(float) * (size_t)B * net->N, cudaMemcpyDeviceToDevice, s);
+  final_fp32(net, P, q, supergrad, vertex, s);
+  return last_error();
+}
+
+ld_status ld_bound_backward(ld_net* net, const float* lb0, const float* ub0, const float* lbk, const float* ubk,
+                            int32_t n_props, const int32_t* prop, const int8_t* masks, int32_t B, const float* rho,
+                            const double* grad_out, float* gW, float* gb, float* glb0, float* gub0, float* glbk,
+                            float* gubk, void* stream) {
+  ld_status st = check_problem(net, lb0, ub0, lbk, ubk, n_props, B);
+  if (st != LD_OK) return st;
+  if (!rho) return LD_ERR_ARG;
+  cudaStream_t s = S(stream);
+  if (B == 0) {
+    if (gW) cudaMemsetAsync(gW, 0, sizeof(float) * net->n_w, s);
+    if (gb) cudaMemsetAsync(gb, 0, sizeof(float) * net->n_b, s);
+    if (glb0) cudaMemsetAsync(glb0, 0, sizeof(float) * n_props * net->n0, s);
+    if (gub0) cudaMemsetAsync(gub0, 0, sizeof(float) * n_props * net->n0, s);
+    if (glbk) cudaMemsetAsync(glbk, 0, sizeof(float) * n_props * net->N, s);
+    if (gubk) cudaMemsetAsync(gubk, 0, sizeof(float) * n_props * net->N, s);
+    return last_error();
+  }
+  if ((st = ensure_ws(net, B)) != LD_OK) return st;
+  const Problem P = make_problem(net, lb0, ub0, lbk, ubk, n_props, prop, masks, B);
+  ld::launch_empty_flags(P, net->empty, net->d_status, s);
+  cudaMemcpyAsync(net->rho, rho, sizeof(float) * (size_t)B * net->N, cudaMemcpyDeviceToDevice, s);
+  ld_opts o;
+  ld_opts_default(&o);
+  sweep(net, P, 2, o, ld::AdamStep{}, nullptr, nullptr, net->vtx, net->g, s);
+  ld::BackwardOut bo{gW, gb, glb0, gub0, glbk, gubk};
+  ld::launch_backward(net->L, net->w_off, net->b_off, P, net->rho, grad_out, net->x, net->g, net->vtx, net->scr_bn,
+                      net->scr_b0, bo, s);
+  return last_error();
+}
+
+}  // extern "C"

@@ -1,0 +1,264 @@
+// Internal declarations shared by the libld translation units.
+//
+// Layout conventions (all row-major, subdomain-major):
+//   flat ReLU vector  [B, N]   layers 1..n-1 back to back; layer k at r_off
+//   x buffer          [B, XS]  XS = n_0 + N: x_0 (the box argmin) at 0, then
+//                              x_k for k = 1..n-1 at n_0 + r_off of layer k
+//   per-property data [P, n_0] boxes, [P, N] intermediate bounds
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/ld.h"
+
+namespace ld {
+
+constexpr int kMaxLayers = 16;
+
+// One linear layer x_hat_k = W_k x_{k-1} + b_k as seen by the kernels.
+struct LayerDev {
+  int kind;                      // LD_LAYER_FC / LD_LAYER_CONV
+  int cin, h, w;                 // input plane (FC: n_in, 1, 1)
+  int cout, ho, wo;              // output plane (FC: n_out, 1, 1)
+  int kh, kw, stride, pad;
+  int n_in, n_out;
+  int x_in_off;                  // offset of x_{k-1} in the x buffer
+  int r_out_off;                 // offset of layer k in the flat ReLU vector (k < n)
+  int fan_t;                     // max number of terms of one transposed-pass sum
+  const float* W;                // FC [n_out, n_in]; conv [cout, cin, kh, kw]
+  const float* b;                // [cout]
+};
+
+// Inputs of one bounding call, in device memory.
+struct Problem {
+  int B, N, n0, XS, n_props;
+  const float* l0;               // [P, n0]
+  const float* u0;
+  const float* lbk;              // [P, N]
+  const float* ubk;
+  const int32_t* prop;           // [B] or nullptr
+  const int8_t* mask;            // [B, N] or nullptr
+  const int8_t* empty;           // [B] 1 where the clamped bounds cross
+};
+
+// Property of subdomain b; an out-of-range index is clamped here (so no
+// access leaves the per-property arrays) and reported by the pre-pass.
+__device__ __forceinline__ int prop_of(const Problem& P, int b) {
+  if (!P.prop) return 0;
+  const int p = P.prop[b];
+  return p < 0 ? 0 : (p >= P.n_props ? P.n_props - 1 : p);
+}
+
+// Split-mask clamp of Sec. 2.3.2: +1 => l <- max(l,0); -1 => u <- min(u,0).
+__device__ __forceinline__ void clamped_bounds(const Problem& P, int b, int j, float& l, float& u) {
+  const int p = prop_of(P, b);
+  l = P.lbk[(size_t)p * P.N + j];
+  u = P.ubk[(size_t)p * P.N + j];
+  const int m = P.mask ? P.mask[(size_t)b * P.N + j] : 0;
+  if (m > 0) l = fmaxf(l, 0.f);
+  if (m < 0) u = fminf(u, 0.f);
+}
+
+// Inner minimisation of a ReLU subproblem P_k for one neuron (Sec. 3.2.2):
+// minimise r * x_hat_B - c * x over the Planet hull of Eq. (planet-relu-hull).
+//   blocking (u <= 0): x = 0, x_hat_B = box argmin of r
+//   passing  (l >= 0): x = x_hat_B = box argmin of (r - c)
+//   ambiguous: best of the vertices (l,0), (0,0), (u,u), Eq. (min-pk),
+//              first strict minimum in that order
+// Box argmin of a*y over [l,u]: u if a <= 0 else l (Eq. box_bounds_sol rule).
+// code: 0 = (l,0) / lower end, 1 = (0,0), 2 = (u,u) / upper end.
+template <typename T>
+__device__ __forceinline__ void relu_argmin(T r, T c, T l, T u, T& xb, T& xk, int& code) {
+  if (u <= T(0)) {
+    const bool up = r <= T(0);
+    xb = up ? u : l;
+    xk = T(0);
+    code = up ? 2 : 0;
+  } else if (l >= T(0)) {
+    const bool up = (r - c) <= T(0);
+    xb = up ? u : l;
+    xk = xb;
+    code = up ? 2 : 0;
+  } else {
+    T best = r * l;
+    code = 0;
+    if (T(0) < best) { best = T(0); code = 1; }
+    if ((r - c) * u < best) code = 2;
+    xb = code == 0 ? l : (code == 1 ? T(0) : u);
+    xk = code == 2 ? u : T(0);
+  }
+}
+
+// ---------------------------------------------------------------- epilogues
+// Transposed-pass epilogues receive (b, i, g) with g = (W_{k+1}^T rho_{k+1})[i]
+// for neuron i of layer k.  Forward-pass epilogues receive (b, j, acc) with
+// acc = (W_{k+1} x_k)[j] (no bias yet) for neuron j of layer k+1.
+
+// Transposed pass -> inner minimisation of layer k (k >= 1) or the box (k = 0).
+struct EpiArgmin {
+  Problem P;
+  int layer;           // k
+  int r_off;           // layer k in the flat ReLU vector (k >= 1)
+  int x_off;           // layer k in the x buffer
+  const float* rho;    // [B, N]
+  float* x;            // [B, XS]
+  float* xB;           // [B, N]
+  int8_t* vtx;         // [B, N] or nullptr (vertex codes, layers >= 1)
+  float* g_out;        // [B, XS] or nullptr: keeps g_k at the layer's x offset
+  __device__ __forceinline__ void operator()(int b, int i, float g) const {
+    if (g_out) g_out[(size_t)b * P.XS + x_off + i] = g;
+    if (layer == 0) {
+      const int p = prop_of(P, b);
+      // P0 (Eq. box_bounds_sol): minimise -g_0^T x0, i.e. x0 = u0 where g_0 >= 0
+      const float v = (g >= 0.f) ? P.u0[(size_t)p * P.n0 + i] : P.l0[(size_t)p * P.n0 + i];
+      x[(size_t)b * P.XS + i] = v;
+      return;
+    }
+    const int j = r_off + i;
+    float l, u;
+    clamped_bounds(P, b, j, l, u);
+    const float r = rho[(size_t)b * P.N + j];
+    float xb, xk;
+    int code;
+    relu_argmin<float>(r, g, l, u, xb, xk, code);
+    x[(size_t)b * P.XS + x_off + i] = xk;
+    xB[(size_t)b * P.N + j] = xb;
+    if (vtx) vtx[(size_t)b * P.N + j] = (int8_t)code;
+  }
+};
+
+// Transposed pass -> CROWN dual of layer k (Prop. 3, Eq. salman-assignment):
+// rho_k = a_bar [lambda]_+ + a_low [lambda]_- with lambda = g_k.
+struct EpiCrown {
+  Problem P;
+  int r_off;
+  float* rho;          // [B, N]
+  __device__ __forceinline__ void operator()(int b, int i, float lam) const {
+    const int j = r_off + i;
+    float l, u;
+    clamped_bounds(P, b, j, l, u);
+    float a_up, a_lo;
+    if (u <= 0.f) {            // blocking
+      a_up = 0.f; a_lo = 0.f;
+    } else if (l >= 0.f) {     // passing
+      a_up = 1.f; a_lo = 1.f;
+    } else {                   // ambiguous: u/(u-l); CROWN lower slope 1[u >= -l]
+      a_up = u / (u - l);
+      a_lo = (u >= -l) ? 1.f : 0.f;
+    }
+    rho[(size_t)b * P.N + j] = a_up * fmaxf(lam, 0.f) + a_lo * fminf(lam, 0.f);
+  }
+};
+
+// Per-iteration Adam constants (host-computed in double, then rounded).
+struct AdamStep {
+  float alpha;        // alpha_t of the linear schedule
+  float inv_bc1;      // 1 / (1 - beta1^(t+1))
+  float inv_bc2;      // 1 / (1 - beta2^(t+1))
+};
+
+// Forward pass -> supergradient s = x_hat_B - x_hat_A and Adam ascent step on
+// rho_{k+1} (Algorithm 1 with Adam; Eq. subgradient_update).
+struct EpiAdam {
+  Problem P;
+  int r_off;           // layer k+1 in the flat ReLU vector
+  int plane;           // outputs per channel (FC: 1)
+  const float* bias;
+  const float* xB;
+  float* rho;
+  float* m;
+  float* v;
+  float beta1, beta2, eps;
+  AdamStep st;
+  __device__ __forceinline__ void operator()(int b, int jj, float acc) const {
+    if (P.empty[b]) return;
+    const float xa = acc + bias[jj / plane];
+    const size_t j = (size_t)b * P.N + r_off + jj;
+    const float s = xB[j] - xa;
+    const float mm = beta1 * m[j] + (1.f - beta1) * s;
+    const float vv = beta2 * v[j] + (1.f - beta2) * s * s;
+    m[j] = mm;
+    v[j] = vv;
+    const float mhat = mm * st.inv_bc1;
+    const float vhat = vv * st.inv_bc2;
+    rho[j] = rho[j] + st.alpha * mhat / (sqrtf(vhat) + eps);
+  }
+};
+
+// Forward pass -> record the supergradient and accumulate q = x_hat_A,n +
+// sum_k rho_k (x_hat_B,k - x_hat_A,k) (FP32 terms, FP64 sum).
+struct EpiRecord {
+  Problem P;
+  int r_off;           // layer k+1 (ignored for the last layer)
+  int plane;
+  int last;            // 1 for layer n (adds x_hat_A,n to q)
+  const float* bias;
+  const float* xB;
+  const float* rho;
+  float* sg;           // [B, N] or nullptr
+  double* q;           // [B] or nullptr
+  __device__ __forceinline__ void operator()(int b, int jj, float acc) const {
+    const float xa = acc + bias[jj / plane];
+    if (last) {
+      if (q) atomicAdd(&q[b], (double)xa);
+      return;
+    }
+    const size_t j = (size_t)b * P.N + r_off + jj;
+    const float s = xB[j] - xa;
+    if (sg) sg[j] = s;
+    if (q) atomicAdd(&q[b], (double)(rho[j] * s));
+  }
+};
+
+// ---------------------------------------------------------------- launchers
+// FP32 passes (ld_passes.cu).
+void launch_transposed_argmin(const LayerDev& L, const LayerDev* Lnext_or_null, const Problem& P,
+                              const float* rho, EpiArgmin epi, cudaStream_t s);
+void launch_transposed_crown(const LayerDev& L, const Problem& P, const float* rho, EpiCrown epi,
+                             cudaStream_t s);
+void launch_top_argmin(const LayerDev& Ln, const Problem& P, EpiArgmin epi, cudaStream_t s);
+void launch_top_crown(const LayerDev& Ln, const Problem& P, EpiCrown epi, cudaStream_t s);
+void launch_forward_adam(const LayerDev& L, const Problem& P, const float* x, EpiAdam epi, cudaStream_t s);
+void launch_forward_record(const LayerDev& L, const Problem& P, const float* x, EpiRecord epi,
+                           cudaStream_t s);
+
+// Feasibility pre-pass and box checks (ld_passes.cu).
+void launch_empty_flags(const Problem& P, int8_t* empty, int* status, cudaStream_t s);
+
+// IBP (ld_ibp.cu).
+void launch_ibp_layer(const LayerDev& L, int first, int last, int n_props, const float* lin, const float* uin,
+                      int in_stride, float* lout, float* uout, int out_stride, double* out_lb, int* status,
+                      cudaStream_t s);
+
+// FP64 final bound (ld_final.cu).
+struct FinalAcc {
+  double* S;           // [B] sum of term values
+  double* E;           // [B] sum of term error bounds (rounded up)
+  double* A;           // [B] sum of |term values| (rounded up)
+};
+void launch_final_layer(const LayerDev& Lnext, int layer, int r_off, int x_off, const Problem& P,
+                        const float* rho, int top, FinalAcc acc, cudaStream_t s);
+void launch_final_bias(const std::vector<LayerDev>& Ls, const Problem& P, const float* rho, FinalAcc acc,
+                       cudaStream_t s);
+void launch_final_combine_bn(const Problem& P, FinalAcc acc, double bn, double gamma_M, double inflate,
+                             double* out, cudaStream_t s);
+double final_gamma(double K);  // Higham's gamma_K for unit roundoff 2^-53, slightly inflated
+
+// Danskin adjoint (ld_backward.cu).
+struct BackwardOut {
+  float* gW;           // packed, or nullptr
+  float* gb;
+  float* glb0;
+  float* gub0;
+  float* glbk;
+  float* gubk;
+};
+void launch_backward(const std::vector<LayerDev>& Ls, const std::vector<size_t>& w_off,
+                     const std::vector<size_t>& b_off, const Problem& P, const float* rho,
+                     const double* grad_out, const float* x, const float* g0, const int8_t* vtx,
+                     float* scratch_bn, float* scratch_b0, BackwardOut out, cudaStream_t s);
+
+}  // namespace ld

@@ -1,0 +1,324 @@
+// Final bound in FP64 with outward slack: a sound lower bound q(rho_T).
+//
+// With rho_n = -1 and g_k = W_{k+1}^T rho_{k+1}, the dual of Eq.
+// (nonprox_problem) decomposes over the subproblems (App. A, Eq.
+// dual_decomp_vs_dj) into per-neuron minima plus bias terms:
+//   q(rho) = sum_j min_{x0_j in [l0_j,u0_j]} (-g_0[j] x0_j)                    (P0)
+//          + sum_{k=1}^{n-1} sum_i min_{vertices of P_k} (rho_k[i] xB - g_k[i] x) (Pk)
+//          - sum_{k=1}^{n-1} rho_k^T b_k + b_n
+// so the final bound needs only the transposed pass.  Each g_k is summed in
+// FP64 from the FP32 weights and duals (the products are exact in FP64); an
+// upper bound A_i >= sum |W||rho| is summed alongside in FP32 rounded up,
+// which bounds the FP64 summation error by delta_i = gamma_K A_i (Higham,
+// gamma_K = K u / (1 - K u), u = 2^-53).  Every term's value t and an upper
+// bound e on its error (from delta_i and the rounding of one subtraction and
+// one product) are summed per subdomain; the bound returned is
+//   S - E - gamma_M * sum|t|   (S = sum t, E = sum e, M = number of terms),
+// each of E and sum|t| inflated for the reassociation of the atomic sums.
+#include "ld_common.cuh"
+
+namespace ld {
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+constexpr double U52 = 2.220446049250313e-16;  // 2^-52
+
+// Value and error bound of one per-neuron minimum.  box: P0 term with
+// coefficient -g on [l, u].  Otherwise the Pk neuron with rho r.
+__device__ __forceinline__ void final_term(bool box, double r, double g, double delta, double l, double u,
+                                           double& t, double& e) {
+  if (!box && u <= 0.0) {            // blocking: min r*xB over [l,u], exact products
+    t = fmin(r * l, r * u);
+    e = 0.0;
+    return;
+  }
+  const double d = box ? -g : r - g;  // coefficient of xB (and of x) in the box/passing/(u,u) cases
+  const double ad = fabs(d);
+  if (box || l >= 0.0) {              // P0 box, or passing: min d*xB over [l,u]
+    const double tl = d * l, tu = d * u;
+    t = fmin(tl, tu);
+    const double xm = fmax(fabs(l), fabs(u));
+    e = __dadd_ru(__dmul_ru(xm, __dadd_ru(delta, __dmul_ru(U52, ad))), __dmul_ru(U52, fmax(fabs(tl), fabs(tu))));
+    return;
+  }
+  // ambiguous: vertices (l,0) -> r*l (exact), (0,0) -> 0, (u,u) -> d*u
+  const double tuu = d * u;
+  t = fmin(fmin(r * l, 0.0), tuu);
+  e = __dadd_ru(__dmul_ru(fabs(u), __dadd_ru(delta, __dmul_ru(U52, ad))), __dmul_ru(U52, fabs(tuu)));
+}
+
+struct FinalEpi {
+  Problem P;
+  int layer;           // k (0 = box)
+  int r_off;
+  const float* rho;
+  double gamma_K;
+  __device__ __forceinline__ void term(int b, int i, double g, float abs_sum, double& t, double& e) const {
+    const double delta = __dmul_ru(gamma_K, (double)abs_sum);
+    if (layer == 0) {
+      const int p = prop_of(P, b);
+      final_term(true, 0.0, g, delta, (double)P.l0[(size_t)p * P.n0 + i], (double)P.u0[(size_t)p * P.n0 + i], t, e);
+      return;
+    }
+    const int j = r_off + i;
+    float l, u;
+    clamped_bounds(P, b, j, l, u);
+    final_term(false, (double)rho[(size_t)b * P.N + j], g, delta, (double)l, (double)u, t, e);
+  }
+};
+
+__device__ __forceinline__ void acc_add(FinalAcc a, int b, double t, double e, double at) {
+  atomicAdd(&a.S[b], t);
+  atomicAdd(&a.E[b], e);
+  atomicAdd(&a.A[b], at);
+}
+
+// FP64 transposed FC pass (A = rho_{k+1} [B, n_out], W [n_out, n_in]).
+__global__ void __launch_bounds__(NT) final_fc_kernel(int M, int Ncol, int K, const float* __restrict__ A, int lda,
+                                                      const float* __restrict__ W, int ldw, FinalEpi epi,
+                                                      FinalAcc acc_out) {
+  __shared__ float As[BK][BM + 4];
+  __shared__ float Bs[BK][BN + 4];
+  const int t = threadIdx.x, tx = t % 16, ty = t / 16;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  double acc[4][4];
+  float aab[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      acc[i][j] = 0.0;
+      aab[i][j] = 0.f;
+    }
+  for (int k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int idx = t + e * NT;
+      const int mm = idx / BK, kk = idx % BK;
+      const int gm = m0 + mm, gk = k0 + kk;
+      As[kk][mm] = (gm < M && gk < K) ? A[(size_t)gm * lda + gk] : 0.f;
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int idx = t + e * NT;
+      const int kk = idx / BN, nn = idx % BN;
+      const int gk = k0 + kk, gn = n0 + nn;
+      Bs[kk][nn] = (gk < K && gn < Ncol) ? W[(size_t)gk * ldw + gn] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < BK; ++kk) {
+      float a[4], bb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc[i][j] = fma((double)a[i], (double)bb[j], acc[i][j]);
+          aab[i][j] = __fmaf_ru(fabsf(a[i]), fabsf(bb[j]), aab[i][j]);
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = m0 + ty + 16 * i;
+    double st = 0.0, se = 0.0, sa = 0.0;
+    if (m < M) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int n = n0 + tx + 16 * j;
+        if (n < Ncol) {
+          double tv, ev;
+          epi.term(m, n, acc[i][j], aab[i][j], tv, ev);
+          st += tv;
+          se = __dadd_ru(se, ev);
+          sa = __dadd_ru(sa, fabs(tv));
+        }
+      }
+    }
+#pragma unroll
+    for (int off = 8; off > 0; off >>= 1) {
+      st += __shfl_xor_sync(0xffffffffu, st, off);
+      se = __dadd_ru(se, __shfl_xor_sync(0xffffffffu, se, off));
+      sa = __dadd_ru(sa, __shfl_xor_sync(0xffffffffu, sa, off));
+    }
+    if (tx == 0 && m < M) acc_add(acc_out, m, st, se, sa);
+  }
+}
+
+__device__ __forceinline__ void block_reduce_add(FinalAcc a, int b, double st, double se, double sa) {
+  __shared__ double red[3][NT / 32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    st += __shfl_xor_sync(0xffffffffu, st, off);
+    se = __dadd_ru(se, __shfl_xor_sync(0xffffffffu, se, off));
+    sa = __dadd_ru(sa, __shfl_xor_sync(0xffffffffu, sa, off));
+  }
+  const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (lane == 0) {
+    red[0][w] = st;
+    red[1][w] = se;
+    red[2][w] = sa;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+    for (int i = 0; i < (int)(blockDim.x / 32); ++i) {
+      t0 += red[0][i];
+      t1 = __dadd_ru(t1, red[1][i]);
+      t2 = __dadd_ru(t2, red[2][i]);
+    }
+    acc_add(a, b, t0, t1, t2);
+  }
+}
+
+// FP64 transposed conv pass; grid row = subdomain.
+__global__ void __launch_bounds__(NT) final_conv_kernel(LayerDev L, const float* __restrict__ r, int rs,
+                                                        FinalEpi epi, FinalAcc acc_out) {
+  extern __shared__ float sW[];
+  const int nw = L.cout * L.cin * L.kh * L.kw;
+  for (int e = threadIdx.x; e < nw; e += blockDim.x) sW[e] = L.W[e];
+  __syncthreads();
+  const int b = blockIdx.y;
+  const float* rb = r + (size_t)b * rs;
+  const int hw_i = L.h * L.w, plane = L.cin * hw_i, hw_o = L.ho * L.wo;
+  double st = 0.0, se = 0.0, sa = 0.0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < plane; e += gridDim.x * blockDim.x) {
+    const int c = e / hw_i, rem = e % hw_i, yy = rem / L.w, xx = rem % L.w;
+    double acc = 0.0;
+    float aab = 0.f;
+    for (int i = 0; i < L.kh; ++i) {
+      const int ty = yy + L.pad - i;
+      if (ty < 0 || ty % L.stride) continue;
+      const int y = ty / L.stride;
+      if (y >= L.ho) continue;
+      for (int j = 0; j < L.kw; ++j) {
+        const int tx = xx + L.pad - j;
+        if (tx < 0 || tx % L.stride) continue;
+        const int xo = tx / L.stride;
+        if (xo >= L.wo) continue;
+        const float* wp = sW + ((size_t)c * L.kh + i) * L.kw + j;
+        const float* rp = rb + y * L.wo + xo;
+        for (int o = 0; o < L.cout; ++o) {
+          const float wv = wp[(size_t)o * L.cin * L.kh * L.kw], rv = rp[(size_t)o * hw_o];
+          acc = fma((double)wv, (double)rv, acc);
+          aab = __fmaf_ru(fabsf(wv), fabsf(rv), aab);
+        }
+      }
+    }
+    double tv, ev;
+    epi.term(b, e, acc, aab, tv, ev);
+    st += tv;
+    se = __dadd_ru(se, ev);
+    sa = __dadd_ru(sa, fabs(tv));
+  }
+  block_reduce_add(acc_out, b, st, se, sa);
+}
+
+// Top subproblem P_{n-1}: g_{n-1} = -W_n exactly (no rounding, delta = 0).
+__global__ void __launch_bounds__(NT) final_top_kernel(int n, const float* __restrict__ Wn, FinalEpi epi,
+                                                       FinalAcc acc_out) {
+  const int b = blockIdx.x;
+  double st = 0.0, se = 0.0, sa = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double tv, ev;
+    epi.term(b, i, -(double)Wn[i], 0.f, tv, ev);
+    st += tv;
+    se = __dadd_ru(se, ev);
+    sa = __dadd_ru(sa, fabs(tv));
+  }
+  block_reduce_add(acc_out, b, st, se, sa);
+}
+
+struct BiasLayers {
+  int count;
+  int r_off[kMaxLayers];
+  int n[kMaxLayers];
+  int plane[kMaxLayers];
+  const float* bias[kMaxLayers];
+};
+
+// Bias terms -rho_k^T b_k, k = 1..n-1 (exact FP64 products).
+__global__ void __launch_bounds__(NT) final_bias_kernel(Problem P, BiasLayers BL, const float* __restrict__ rho,
+                                                        FinalAcc acc_out) {
+  const int b = blockIdx.x;
+  double st = 0.0, sa = 0.0;
+  for (int k = 0; k < BL.count; ++k)
+    for (int i = threadIdx.x; i < BL.n[k]; i += blockDim.x) {
+      const double tv = -(double)rho[(size_t)b * P.N + BL.r_off[k] + i] * (double)BL.bias[k][i / BL.plane[k]];
+      st += tv;
+      sa = __dadd_ru(sa, fabs(tv));
+    }
+  block_reduce_add(acc_out, b, st, 0.0, sa);
+}
+
+__global__ void final_combine_kernel(Problem P, FinalAcc a, double bn, double gamma_M, double inflate, double* out) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < P.B; b += gridDim.x * blockDim.x) {
+    if (P.empty[b]) {
+      out[b] = __longlong_as_double(0x7ff0000000000000LL);  // +inf: empty subdomain
+      continue;
+    }
+    const double S = a.S[b] + bn;
+    const double E = __dmul_ru(a.E[b], inflate);
+    const double A = __dmul_ru(__dadd_ru(a.A[b], fabs(bn)), inflate);
+    out[b] = __dsub_rd(__dsub_rd(S, E), __dmul_ru(gamma_M, A));
+  }
+}
+
+}  // namespace
+
+static double gamma_of(double K) {
+  const double u = 1.1102230246251565e-16;  // 2^-53
+  return (K * u) / (1.0 - K * u) * (1.0 + 1e-12);
+}
+
+void launch_final_layer(const LayerDev& Lnext, int layer, int r_off, int x_off, const Problem& P,
+                        const float* rho, int top, FinalAcc acc, cudaStream_t s) {
+  (void)x_off;
+  FinalEpi epi{P, layer, r_off, rho, gamma_of((double)Lnext.fan_t)};
+  if (P.B == 0) return;
+  if (top) {
+    final_top_kernel<<<P.B, NT, 0, s>>>(Lnext.n_in, Lnext.W, epi, acc);
+    return;
+  }
+  const float* r = rho + Lnext.r_out_off;
+  if (Lnext.kind == LD_LAYER_FC) {
+    dim3 grid((Lnext.n_in + BN - 1) / BN, (P.B + BM - 1) / BM);
+    final_fc_kernel<<<grid, NT, 0, s>>>(P.B, Lnext.n_in, Lnext.n_out, r, P.N, Lnext.W, Lnext.n_in, epi, acc);
+  } else {
+    const int plane = Lnext.cin * Lnext.h * Lnext.w;
+    dim3 grid((plane + NT - 1) / NT, P.B);
+    const size_t smem = sizeof(float) * Lnext.cout * Lnext.cin * Lnext.kh * Lnext.kw;
+    final_conv_kernel<<<grid, NT, smem, s>>>(Lnext, r, P.N, epi, acc);
+  }
+}
+
+void launch_final_bias(const std::vector<LayerDev>& Ls, const Problem& P, const float* rho, FinalAcc acc,
+                       cudaStream_t s) {
+  if (P.B == 0) return;
+  BiasLayers BL{};
+  BL.count = (int)Ls.size() - 1;
+  for (int k = 0; k < BL.count; ++k) {
+    const LayerDev& L = Ls[k];
+    BL.r_off[k] = L.r_out_off;
+    BL.n[k] = L.n_out;
+    BL.plane[k] = L.kind == LD_LAYER_FC ? 1 : L.ho * L.wo;
+    BL.bias[k] = L.b;
+  }
+  final_bias_kernel<<<P.B, NT, 0, s>>>(P, BL, rho, acc);
+}
+
+// b_n is read on the host once per net and passed here.
+void launch_final_combine_bn(const Problem& P, FinalAcc acc, double bn, double gamma_M, double inflate,
+                             double* out, cudaStream_t s) {
+  if (P.B == 0) return;
+  final_combine_kernel<<<(P.B + 255) / 256, 256, 0, s>>>(P, acc, bn, gamma_M, inflate, out);
+}
+
+double final_gamma(double K) { return gamma_of(K); }
+
+}  // namespace ld

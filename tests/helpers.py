@@ -41,3 +41,48 @@ def tiny_problem(i=0):
     l0, u0 = synth.tiny_box(i)
     lb, ub = oracle.ibp_bounds(net, l0.astype(np.float64), u0.astype(np.float64))
     return specs, net, l0.astype(np.float64), u0.astype(np.float64), lb, ub
+
+
+def outward_f32(lo, hi):
+    """Round float64 bounds to float32 outward (lo down, hi up)."""
+    lo = np.asarray(lo, np.float64)
+    hi = np.asarray(hi, np.float64)
+    l32 = lo.astype(np.float32)
+    h32 = hi.astype(np.float32)
+    l32 = np.where(l32.astype(np.float64) > lo, np.nextafter(l32, np.float32(-np.inf)), l32)
+    h32 = np.where(h32.astype(np.float64) < hi, np.nextafter(h32, np.float32(np.inf)), h32)
+    return l32.astype(np.float32), h32.astype(np.float32)
+
+
+def conv_problem(name, B, depth=(0, 8), props=(0,), block=0, eps_range=(1 / 255, 8 / 255)):
+    """Oracle-side synthetic problem on a CIFAR-shaped convnet: folded float32
+    specs (margin of property props[0]), oracle net, float32 boxes and
+    outward-rounded IBP bounds per property, masks over root-ambiguous ReLUs,
+    and subdomain -> property map (contiguous blocks)."""
+    specs = synth.make_convnet(name)
+    boxes = [synth.image_property(p, eps_range) for p in props]
+    fspecs = folded_specs(specs, boxes[0][2])
+    net = oracle_net(fspecs)
+    l0 = np.stack([b[0] for b in boxes])
+    u0 = np.stack([b[1] for b in boxes])
+    lb, ub = oracle.ibp_bounds(net, l0.astype(np.float64), u0.astype(np.float64))
+    flat_l = np.concatenate([lb[k] for k in range(1, net.n)], axis=1)
+    flat_u = np.concatenate([ub[k] for k in range(1, net.n)], axis=1)
+    lbk, ubk = outward_f32(flat_l, flat_u)
+    P = len(props)
+    prop = (np.arange(B) * P // max(B, 1)).astype(np.int32)
+    amb = np.nonzero((lbk[0] < 0) & (ubk[0] > 0))[0]
+    masks = synth.split_masks(lbk.shape[1], B, amb, depth, block=block)
+    return dict(specs=fspecs, net=net, l0=l0, u0=u0, lbk=lbk, ubk=ubk, prop=prop, masks=masks, B=B)
+
+
+def oracle_lists(net, pb, rows=None):
+    """Per-subdomain clamped bound lists and boxes (float64) for the oracle."""
+    prop = pb["prop"] if rows is None else pb["prop"][rows]
+    masks = pb["masks"] if rows is None else pb["masks"][rows]
+    L0 = pb["l0"][prop].astype(np.float64)
+    U0 = pb["u0"][prop].astype(np.float64)
+    lb = oracle.layer_lists(net, pb["lbk"][prop].astype(np.float64))
+    ub = oracle.layer_lists(net, pb["ubk"][prop].astype(np.float64))
+    lb, ub, empty = oracle.apply_masks(net, lb, ub, masks)
+    return L0, U0, lb, ub, empty

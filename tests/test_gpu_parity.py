@@ -1,0 +1,347 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+identical seeded inputs.  Every oracle input comes from the synthetic
+generators and the oracle itself; nothing computed on the GPU is fed back
+to the oracle.
+
+Tolerances (relative = |a - b| / max(|b|, 1)):
+  dual value and supergradient at the same rho  1e-5
+  final bound after T iterations                1e-4
+  FP64 final bound at the same rho              sound (<= oracle + 1e-12) and within 1e-9
+  vertex choices and empty-subdomain flags      exact (outside FP32 near-ties)
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2104_06718_gb300 import binding as ldb
+from paper_2104_06718_gb300 import synth
+from helpers import conv_problem, oracle_lists, outward_f32, oracle_net, tiny_problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2104_06718_gb300 import build
+    build.build()
+    ldb.load_library()
+
+
+def rel(a, b):
+    return np.abs(np.asarray(a, np.float64) - np.asarray(b, np.float64)) / np.maximum(np.abs(np.asarray(b, np.float64)), 1.0)
+
+
+def gpu_net(pb):
+    return ldb.Net(pb["specs"])
+
+
+def flat(net, lst):
+    return np.concatenate([lst[k] for k in range(1, net.n)], axis=1)
+
+
+@pytest.fixture(scope="module")
+def base16():
+    return conv_problem("base", 16, depth=(0, 8), block=1)
+
+
+@pytest.fixture(scope="module")
+def tiny_set():
+    out = []
+    for i in range(6):
+        specs, net, l0, u0, lb, ub = tiny_problem(i)
+        flat_l = np.concatenate([lb[k] for k in range(1, net.n)], axis=1)
+        flat_u = np.concatenate([ub[k] for k in range(1, net.n)], axis=1)
+        lbk, ubk = outward_f32(flat_l, flat_u)
+        out.append(dict(specs=specs, net=net, l0=l0.astype(np.float32), u0=u0.astype(np.float32), lbk=lbk, ubk=ubk,
+                        prop=np.zeros(1, np.int32), masks=np.zeros((1, lbk.shape[1]), np.int8), B=1))
+    return out
+
+
+# ------------------------------------------------------------------ IBP (row a0)
+
+@pytest.mark.parametrize("name", ["base", "wide", "deep"])
+def test_ibp_contains_oracle_bounds(name):
+    pb = conv_problem(name, 1, props=(0, 1, 2))
+    net = gpu_net(pb)
+    lbk, ubk, out_lb = ldb.ld_intermediate_bounds(net, pb["l0"], pb["u0"], want_output_lb=True)
+    on = pb["net"]
+    lb, ub = oracle.ibp_bounds(on, pb["l0"].astype(np.float64), pb["u0"].astype(np.float64))
+    fl, fu = flat(on, lb), flat(on, ub)
+    gl, gu = lbk.cpu().numpy().astype(np.float64), ubk.cpu().numpy().astype(np.float64)
+    scale = np.maximum(np.abs(fl), np.abs(fu)) + 1.0
+    assert np.all(gl <= fl + 1e-12 * scale), "IBP lower bound not outward"
+    assert np.all(gu >= fu - 1e-12 * scale), "IBP upper bound not outward"
+    assert np.max((fl - gl) / scale) < 1e-4 and np.max((gu - fu) / scale) < 1e-4
+    assert np.all(out_lb.cpu().numpy() <= lb[on.n][:, 0] + 1e-9)
+    assert np.max(rel(out_lb.cpu().numpy(), lb[on.n][:, 0])) < 1e-4
+    # ambiguity classification agrees wherever the oracle is not within rounding of zero
+    sure = (np.abs(fl) > 1e-4 * scale) & (np.abs(fu) > 1e-4 * scale)
+    assert np.array_equal(((gl < 0) & (gu > 0))[sure], ((fl < 0) & (fu > 0))[sure])
+
+
+def test_nonfinite_box_sets_status(base16):
+    pb = base16
+    net = gpu_net(pb)
+    l0 = pb["l0"].copy()
+    l0[0, 5] = np.nan
+    ldb.ld_intermediate_bounds(net, l0, pb["u0"])
+    assert net.sync_status() == ldb.LD_ERR_NONFINITE
+    ldb.ld_intermediate_bounds(net, pb["l0"], pb["u0"])
+    assert net.sync_status() == ldb.LD_OK
+
+
+# ------------------------------------------------------------------ inner minimisation (rows a2, a3, a4)
+
+def near_tie_mask(on, lbs, ubs, rho, sol, rel_tol=2e-4):
+    """Neurons whose vertex choice an FP32 evaluation may legitimately flip:
+    the two best candidate values (or the box coefficient's sign) are within
+    rel_tol of the magnitude of the terms that produce them."""
+    ties = []
+    for k in range(1, on.n):
+        r, g, l, u = rho[k], sol.g[k], lbs[k], ubs[k]
+        nxt = -np.ones((r.shape[0], 1)) if k + 1 == on.n else rho[k + 1]
+        absg = np.asarray((abs(on.L(k + 1).mat).T @ np.abs(nxt).T).T)
+        mag = (np.abs(r) + absg + 1e-30) * (np.maximum(np.abs(l), np.abs(u)) + 1e-30)
+        cls = oracle.classify(l, u)
+        v = np.stack([r * l, np.zeros_like(r), (r - g) * u], axis=-1)
+        vs = np.sort(v, axis=-1)
+        amb_tie = (vs[..., 1] - vs[..., 0]) < rel_tol * mag
+        box_coef = np.where(cls == 0, r, r - g)
+        box_tie = np.abs(box_coef) < rel_tol * (np.abs(r) + absg + 1e-30)
+        ties.append(np.where(cls == 2, amb_tie, box_tie))
+    return ties
+
+
+def check_inner(pb, rho_flat):
+    """Compare q, the supergradient and the vertex codes at one rho."""
+    on = pb["net"]
+    net = gpu_net(pb)
+    q, sg, vtx = ldb.ld_dual_supergradient(net, pb["l0"], pb["u0"], pb["lbk"], pb["ubk"], rho_flat,
+                                           prop=pb["prop"], masks=pb["masks"])
+    q, sg, vtx = q.cpu().numpy(), sg.cpu().numpy(), vtx.cpu().numpy()
+    L0, U0, lbs, ubs, empty = oracle_lists(on, pb)
+    rho = oracle.layer_lists(on, rho_flat.astype(np.float64))
+    sol = oracle.inner_minimisation(on, L0, U0, lbs, ubs, rho)
+    sgo = oracle.supergradient(sol)
+    ties = near_tie_mask(on, lbs, ubs, rho, sol)
+    offs = oracle.split_offsets(on)
+    n_tie = 0
+    for b in range(pb["B"]):
+        if empty[b]:
+            continue
+        mism_below = False
+        for k in range(1, on.n):
+            gv = vtx[b, offs[k - 1]:offs[k]]
+            ov = sol.vertex[k][b]
+            t = ties[k - 1][b]
+            n_tie += int(t.sum())
+            assert np.array_equal(gv[~t], ov[~t]), f"vertex mismatch subdomain {b} layer {k}"
+            # the supergradient of layer k needs x*_{k-1}: compare it when the
+            # layer below made the same choices everywhere
+            if not mism_below:
+                gs = sg[b, offs[k - 1]:offs[k]]
+                scale = np.maximum(np.abs(sol.xA[k][b]), np.abs(sol.xB[k][b])) + 1.0
+                assert np.max(np.abs(gs - sgo[k][b]) / scale) < 1e-5, f"supergradient subdomain {b} layer {k}"
+            mism_below = bool(np.any(gv[t] != ov[t]))
+        # q is continuous across ties: always compare
+        assert rel(q[b], sol.q[b]) < 1e-5, f"q subdomain {b}: {q[b]} vs {sol.q[b]}"
+    return n_tie
+
+
+def test_inner_minimisation_tiny_random_and_crown(tiny_set):
+    for pb in tiny_set:
+        on = pb["net"]
+        N = pb["lbk"].shape[1]
+        rho_r = synth.random_duals([N], 1, seed=17)[0]
+        check_inner(pb, rho_r)
+        L0, U0, lbs, ubs, _ = oracle_lists(on, pb)
+        rc, _ = oracle.crown_init(on, lbs, ubs)
+        check_inner(pb, flat(on, rc).astype(np.float32))
+
+
+@pytest.mark.parametrize("name", ["base", "wide", "deep"])
+def test_inner_minimisation_convnets(name):
+    pb = conv_problem(name, 12, depth=(0, 8), block=2)
+    N = pb["lbk"].shape[1]
+    rho = synth.random_duals([N], pb["B"], seed=21, scale=0.05)[0]
+    n_tie = check_inner(pb, rho)
+    assert n_tie < 0.001 * pb["B"] * N
+
+
+# ------------------------------------------------------------------ CROWN init (row a1)
+
+@pytest.mark.parametrize("name", ["base", "deep"])
+def test_crown_init_matches_oracle(name):
+    pb = conv_problem(name, 8, depth=(0, 8), block=3)
+    on = pb["net"]
+    net = gpu_net(pb)
+    out, rho = ldb.ld_bound(net, pb["l0"], pb["u0"], pb["lbk"], pb["ubk"], pb["prop"], pb["masks"], n_iters=0,
+                            return_rho=True)
+    L0, U0, lbs, ubs, empty = oracle_lists(on, pb)
+    rc, lam = oracle.crown_init(on, lbs, ubs)
+    d = oracle.propagation_bound(on, L0, U0, lbs, ubs, rc, lam)
+    ro = flat(on, rc)
+    g = rho.cpu().numpy()
+    ok = ~empty
+    assert np.max(np.abs(g[ok] - ro[ok]) / (np.abs(ro[ok]) + 1e-3)) < 1e-4
+    assert np.max(rel(out.cpu().numpy()[ok], d[ok])) < 1e-5
+
+
+# ------------------------------------------------------------------ FP64 final bound (row a5)
+
+@pytest.mark.parametrize("name", ["base", "wide", "deep"])
+def test_fp64_final_bound_is_sound_and_tight(name):
+    pb = conv_problem(name, 10, depth=(0, 8), block=4)
+    on = pb["net"]
+    net = gpu_net(pb)
+    N = pb["lbk"].shape[1]
+    rho = synth.random_duals([N], pb["B"], seed=23, scale=0.05)[0]
+    out = ldb.ld_bound(net, pb["l0"], pb["u0"], pb["lbk"], pb["ubk"], pb["prop"], pb["masks"], n_iters=0,
+                       rho_in=rho).cpu().numpy()
+    L0, U0, lbs, ubs, empty = oracle_lists(on, pb)
+    q = oracle.dual_value(on, L0, U0, lbs, ubs, oracle.layer_lists(on, rho.astype(np.float64)))
+    ok = ~empty
+    assert np.all(np.isinf(out[empty]))
+    assert np.all(out[ok] <= q[ok] + 1e-12 * np.maximum(np.abs(q[ok]), 1))
+    assert np.max(rel(out[ok], q[ok])) < 1e-9
+
+
+def test_empty_subdomains_are_inf_and_keep_rho(base16):
+    pb = dict(base16)
+    masks = pb["masks"].copy()
+    lbk, ubk = pb["lbk"], pb["ubk"]
+    blocking = np.nonzero(ubk[0] < 0)[0]
+    masks[3, blocking[0]] = 1
+    masks[7, blocking[1]] = 1
+    pb["masks"] = masks
+    net = gpu_net(pb)
+    N = lbk.shape[1]
+    rho = synth.random_duals([N], pb["B"], seed=5, scale=0.05)[0]
+    out, rho_out = ldb.ld_bound(net, pb["l0"], pb["u0"], lbk, ubk, pb["prop"], masks, n_iters=5, rho_in=rho,
+                                return_rho=True)
+    out = out.cpu().numpy()
+    ro = rho_out.cpu().numpy()
+    assert np.isinf(out[3]) and np.isinf(out[7]) and np.all(np.isfinite(np.delete(out, [3, 7])))
+    assert np.array_equal(ro[3], rho[3]) and np.array_equal(ro[7], rho[7])
+
+
+# ------------------------------------------------------------------ full runs (Algorithm 1)
+
+def test_tiny_full_runs_match_oracle(tiny_set):
+    for pb in tiny_set:
+        on = pb["net"]
+        net = gpu_net(pb)
+        opts = ldb.Options()
+        out = ldb.ld_bound(net, pb["l0"], pb["u0"], pb["lbk"], pb["ubk"], None, None, n_iters=200, opts=opts,
+                           B=1).cpu().numpy()
+        ref, _, _ = oracle.ld_bound(on, pb["l0"].astype(np.float64), pb["u0"].astype(np.float64),
+                                    pb["lbk"].astype(np.float64), pb["ubk"].astype(np.float64), None,
+                                    pb["masks"], 200)
+        assert rel(out[0], ref[0]) < 1e-4, (out, ref)
+        assert out[0] <= ref[0] + 1e-4
+
+
+@pytest.mark.parametrize("name,B,T", [("base", 24, 100), ("deep", 12, 100), ("wide", 8, 60)])
+def test_convnet_full_runs_match_oracle(name, B, T):
+    pb = conv_problem(name, B, depth=(0, 8), block=5)
+    on = pb["net"]
+    net = gpu_net(pb)
+    out = ldb.ld_bound(net, pb["l0"], pb["u0"], pb["lbk"], pb["ubk"], pb["prop"], pb["masks"], n_iters=T).cpu().numpy()
+    ref, _, _ = oracle.ld_bound(on, pb["l0"].astype(np.float64), pb["u0"].astype(np.float64),
+                                pb["lbk"].astype(np.float64), pb["ubk"].astype(np.float64), pb["prop"],
+                                pb["masks"], T)
+    fin = np.isfinite(ref)
+    assert np.array_equal(np.isfinite(out), fin)
+    assert np.max(rel(out[fin], ref[fin])) < 1e-4
+
+
+def test_resume_is_bitwise(base16):
+    """T iterations in one call equal T1 + T2 iterations in two calls (the
+    Adam moments and schedule index are carried)."""
+    pb = base16
+    net = gpu_net(pb)
+    args = (pb["l0"], pb["u0"], pb["lbk"], pb["ubk"], pb["prop"], pb["masks"])
+    out_a, rho_a = ldb.ld_bound(net, *args, n_iters=20, return_rho=True)
+    B, N = pb["B"], pb["lbk"].shape[1]
+    mv = torch.zeros((2, B, N), dtype=torch.float32, device="cuda")
+    o1 = ldb.Options(t_offset=0, t_total=20)
+    _, rho_1 = ldb.ld_bound(net, *args, n_iters=12, opts=o1, return_rho=True, adam_mv=mv)
+    o2 = ldb.Options(t_offset=12, t_total=20, init="given")
+    out_b, rho_b = ldb.ld_bound(net, *args, n_iters=8, opts=o2, rho_in=rho_1, return_rho=True, adam_mv=mv)
+    assert torch.equal(rho_a, rho_b)
+    assert torch.equal(out_a, out_b)
+
+
+def test_margin_folding_matches_prefolded():
+    specs = synth.make_convnet("base")
+    l0, u0, c = synth.image_property(3)
+    from helpers import folded_specs
+    a = ldb.Net(specs, margin=c)
+    b = ldb.Net(folded_specs(specs, c))
+    lbk, ubk = ldb.ld_intermediate_bounds(a, l0, u0)
+    lbk2, ubk2 = ldb.ld_intermediate_bounds(b, l0, u0)
+    assert torch.equal(lbk, lbk2) and torch.equal(ubk, ubk2)
+    oa = ldb.ld_bound(a, l0, u0, lbk, ubk, n_iters=10, B=4)
+    ob = ldb.ld_bound(b, l0, u0, lbk, ubk, n_iters=10, B=4)
+    assert torch.equal(oa, ob)
+
+
+# ------------------------------------------------------------------ Danskin adjoint (row a6)
+
+@pytest.mark.parametrize("name", ["base", "deep"])
+def test_backward_matches_oracle_danskin(name):
+    pb = conv_problem(name, 6, depth=(0, 6), block=6)
+    on = pb["net"]
+    net = gpu_net(pb)
+    L0, U0, lbs, ubs, empty = oracle_lists(on, pb)
+    rc, _ = oracle.crown_init(on, lbs, ubs)
+    run = oracle.supergradient_adam(on, L0, U0, lbs, ubs, rc, 15)
+    rho = flat(on, run.rho).astype(np.float32)
+    w = np.linspace(0.5, 1.5, pb["B"])
+    g = ldb.ld_bound_backward(net, pb["l0"], pb["u0"], pb["lbk"], pb["ubk"], rho, grad_out=w, prop=pb["prop"],
+                              masks=pb["masks"])
+    rho64 = oracle.layer_lists(on, rho.astype(np.float64))
+    lb_raw = oracle.layer_lists(on, pb["lbk"][pb["prop"]].astype(np.float64))
+    ub_raw = oracle.layer_lists(on, pb["ubk"][pb["prop"]].astype(np.float64))
+    info = oracle.clamp_info(on, lb_raw, ub_raw, pb["masks"])
+    wz = np.where(empty, 0.0, w)
+    ref = oracle.danskin_gradients(on, L0, U0, lbs, ubs, info, rho64, wz)
+    gW = g["gW"].cpu().numpy()
+    gb = g["gb"].cpu().numpy()
+    woff = boff = 0
+    for k in range(1, on.n + 1):
+        W = ref.gW[k].ravel()
+        np.testing.assert_allclose(gW[woff:woff + W.size], W, rtol=2e-4, atol=2e-4 * (np.abs(W).max() + 1))
+        woff += W.size
+        bb = np.atleast_1d(ref.gb[k])
+        np.testing.assert_allclose(gb[boff:boff + bb.size], bb, rtol=2e-4, atol=2e-4 * (np.abs(bb).max() + 1))
+        boff += bb.size
+    np.testing.assert_allclose(g["glb0"].cpu().numpy()[0], ref.gl0.sum(axis=0), rtol=1e-4, atol=1e-5)
+    np.testing.assert_allclose(g["gub0"].cpu().numpy()[0], ref.gu0.sum(axis=0), rtol=1e-4, atol=1e-5)
+    np.testing.assert_allclose(g["glbk"].cpu().numpy()[0], flat(on, ref.glb).sum(axis=0), rtol=1e-4, atol=1e-5)
+    np.testing.assert_allclose(g["gubk"].cpu().numpy()[0], flat(on, ref.gub).sum(axis=0), rtol=1e-4, atol=1e-5)
+
+
+# ------------------------------------------------------------------ full size, launch configuration of the bench
+
+def test_wide_2048_sampled_against_oracle():
+    """Wide net, 2048 subdomains of split depth 0-20, 100 iterations: the
+    full-size call; sampled subdomains are recomputed by the oracle, and the
+    root bound is checked against network evaluations (weak duality)."""
+    pb = conv_problem("wide", 2048, depth=(0, 20), block=7)
+    on = pb["net"]
+    net = gpu_net(pb)
+    out = ldb.ld_bound(net, pb["l0"], pb["u0"], pb["lbk"], pb["ubk"], pb["prop"], pb["masks"], n_iters=100).cpu().numpy()
+    rows = np.array([0, 1, 777, 2047])
+    sub = dict(pb, prop=pb["prop"][rows], masks=pb["masks"][rows], B=len(rows))
+    ref, _, _ = oracle.ld_bound(on, pb["l0"].astype(np.float64), pb["u0"].astype(np.float64),
+                                pb["lbk"].astype(np.float64), pb["ubk"].astype(np.float64), sub["prop"],
+                                sub["masks"], 100)
+    fin = np.isfinite(ref)
+    assert np.array_equal(np.isfinite(out[rows]), fin)
+    assert np.max(rel(out[rows][fin], ref[fin])) < 1e-4
+    xs = synth.random_box_points(pb["l0"][0], pb["u0"][0], 256, seed=9)
+    assert out[0] <= on.evaluate(xs).min()

@@ -1,0 +1,371 @@
+"""Benchmark: LD subdomain bounds/s on synthetic CIFAR-shaped convnets.
+
+One step = one pass of the whole bounding path over one batch of synthetic
+subdomains: interval bounds of the root box (ld_intermediate_bounds), the
+LD bound of every subdomain after T Adam iterations with CROWN
+initialisation and the FP64 final bound (ld_bound), and the Danskin adjoint
+of the bounds (ld_bound_backward).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload base|wide|deep]
+                    [--impl ours|reference]
+
+`value` is whole-job bounds/s with inputs resident in HBM, timed with CUDA
+events per step, L2 flushed (a 512 MB write) between steps; `e2e` is the
+same metric through the C ABI with host buffers and the host<->device copies
+inside the timed region.  `--impl reference` times the FP64 CPU oracle on a
+bounded sample of the same workload.  For N > 1 (torchrun), every rank
+bounds its own batch of subdomains (weak scaling, no collective on the data
+path); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (net, subdomains per GPU, iterations, split depth range, eps range)
+    "base": ("base", 256, 100, (0, 8), (1 / 255, 8 / 255)),
+    "wide": ("wide", 2048, 100, (0, 20), (1 / 255, 8 / 255)),
+    "deep": ("deep", 128, 100, (0, 8), (1 / 255, 8 / 255)),
+}
+METRIC = "LD subdomain bounds/s on Base/Wide/Deep convnets, bf16 vs fp32 at ≤1e-3 gap"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="base", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def peak_value(d, key_candidates, default):
+    for k in key_candidates:
+        if k in d and isinstance(d[k], (int, float)):
+            return float(d[k])
+    for v in d.values():
+        if isinstance(v, dict):
+            for k in key_candidates:
+                if k in v and isinstance(v[k], (int, float)):
+                    return float(v[k])
+    return default
+
+
+def make_workload(name, rank):
+    from paper_2104_06718_gb300 import synth
+    net_name, B, T, depth, eps = WORKLOADS[name]
+    specs = synth.make_convnet(net_name)
+    l0, u0, c = synth.image_property(rank, eps)
+    return dict(name=name, net=net_name, specs=specs, l0=l0[None], u0=u0[None], margin=c, B=B, T=T, depth=depth,
+                rank=rank)
+
+
+def cpu_baseline(wl, masks, lbk, ubk, budget_s=15.0, max_sub=None):
+    """Time the FP64 oracle on a bounded sample (first subdomains, same T)."""
+    import oracle
+    from paper_2104_06718_gb300 import synth  # noqa: F401
+    specs = wl["specs"]
+    W, b = oracle.fold_margin(specs[-1].W.astype(np.float64), specs[-1].b.astype(np.float64),
+                              np.asarray(wl["margin"], np.float64))
+    layers = []
+    for s in specs[:-1]:
+        if s.kind == "fc":
+            layers.append(oracle.Layer("fc", s.W, s.b))
+        else:
+            layers.append(oracle.Layer("conv", s.W, s.b, in_shape=s.in_shape, stride=s.stride, pad=s.pad))
+    layers.append(oracle.Layer("fc", W.astype(np.float32), b.astype(np.float32)))
+    on = oracle.Net(layers)
+    T = wl["T"]
+    # calibrate: one subdomain, then size the sample to the budget
+    t0 = time.perf_counter()
+    oracle.ld_bound(on, wl["l0"].astype(np.float64), wl["u0"].astype(np.float64), lbk.astype(np.float64),
+                    ubk.astype(np.float64), None, masks[:2], T)
+    per = (time.perf_counter() - t0) / 2
+    n = int(max(2, min(masks.shape[0], budget_s / max(per, 1e-6))))
+    if max_sub:
+        n = min(n, max_sub)
+    t0 = time.perf_counter()
+    oracle.ld_bound(on, wl["l0"].astype(np.float64), wl["u0"].astype(np.float64), lbk.astype(np.float64),
+                    ubk.astype(np.float64), None, masks[:n], T)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "bounds/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"first {n} of {masks.shape[0]} subdomains of the {wl['name']} workload, T={T}, FP64 NumPy/SciPy "
+                      f"(dense BLAS may use all {os.cpu_count()} cores; sparse conv products are single-threaded)"}
+
+
+def run_reference(args):
+    world, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2104_06718_gb300 import synth
+    import oracle
+    wl = make_workload(args.workload, 0)
+    specs = wl["specs"]
+    W, b = oracle.fold_margin(specs[-1].W.astype(np.float64), specs[-1].b.astype(np.float64),
+                              np.asarray(wl["margin"], np.float64))
+    layers = []
+    for s in specs[:-1]:
+        layers.append(oracle.Layer("conv", s.W, s.b, in_shape=s.in_shape, stride=s.stride, pad=s.pad)
+                      if s.kind == "conv" else oracle.Layer("fc", s.W, s.b))
+    layers.append(oracle.Layer("fc", W.astype(np.float32), b.astype(np.float32)))
+    on = oracle.Net(layers)
+    lb, ub = oracle.ibp_bounds(on, wl["l0"].astype(np.float64), wl["u0"].astype(np.float64))
+    lbk = np.concatenate([lb[k] for k in range(1, on.n)], axis=1)
+    ubk = np.concatenate([ub[k] for k in range(1, on.n)], axis=1)
+    amb = np.nonzero((lbk[0] < 0) & (ubk[0] > 0))[0]
+    masks = synth.split_masks(lbk.shape[1], wl["B"], amb, wl["depth"], block=0)
+    # each step: a bounded sample of the workload (same T, first S subdomains)
+    t0 = time.perf_counter()
+    oracle.ld_bound(on, wl["l0"].astype(np.float64), wl["u0"].astype(np.float64), lbk, ubk, None, masks[:2], wl["T"])
+    per = (time.perf_counter() - t0) / 2
+    budget_total = 120.0
+    S = int(max(2, min(wl["B"], budget_total / max(per, 1e-6) / max(args.steps + args.warmup, 1))))
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.ld_bound(on, wl["l0"].astype(np.float64), wl["u0"].astype(np.float64), lbk, ubk, None, masks[:S],
+                        wl["T"])
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = S * len(times) / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "bounds/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / max(len(times), 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{wl['net']} convnet, {wl['B']} subdomains, T={wl['T']} (oracle sample of {S} per step)",
+                       "subdomains_per_step": S, "iterations": wl["T"]},
+            "cpu_baseline": {"value": value, "unit": "bounds/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"first {S} of {wl['B']} subdomains per step, T={wl['T']}, FP64 NumPy/SciPy"},
+            "e2e": {"value": value, "unit": "bounds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_2104_06718_gb300 import build as ldbuild
+    if rank == 0 or world == 1:
+        ldbuild.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2104_06718_gb300 import binding as ldb
+    from paper_2104_06718_gb300 import synth
+    wl = make_workload(args.workload, rank)
+    B, T = wl["B"], wl["T"]
+    net = ldb.Net(wl["specs"], margin=wl["margin"])
+    net.reserve(B)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    l0 = torch.as_tensor(wl["l0"], device=dev)
+    u0 = torch.as_tensor(wl["u0"], device=dev)
+    lbk, ubk = ldb.ld_intermediate_bounds(net, l0, u0)
+    lb_h, ub_h = lbk.cpu().numpy(), ubk.cpu().numpy()
+    amb = np.nonzero((lb_h[0] < 0) & (ub_h[0] > 0))[0]
+    masks_np = synth.split_masks(net.N, B, amb, wl["depth"], block=rank)
+    masks = torch.as_tensor(masks_np, device=dev)
+    ones = torch.ones(B, dtype=torch.float64, device=dev)
+    opts = ldb.Options()
+
+    def step():
+        lk, uk = ldb.ld_intermediate_bounds(net, l0, u0)
+        out, rho = ldb.ld_bound(net, l0, u0, lk, uk, None, masks, n_iters=T, opts=opts, return_rho=True)
+        g = ldb.ld_bound_backward(net, l0, u0, lk, uk, rho, grad_out=ones, masks=masks)
+        return out, g
+
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # ---- device-resident timing
+    sampler = ClockSampler(torch.cuda.current_device())
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out, g = step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    t_local = sum(times) / 1000.0
+    # ---- end to end through the C ABI with host buffers
+    h_l0 = torch.as_tensor(wl["l0"]).pin_memory()
+    h_u0 = torch.as_tensor(wl["u0"]).pin_memory()
+    h_masks = torch.as_tensor(masks_np).pin_memory()
+    h_out = torch.empty(B, dtype=torch.float64).pin_memory()
+    h_gW = torch.empty(net.n_weights, dtype=torch.float32).pin_memory()
+    h2d = h_l0.numel() * 4 + h_u0.numel() * 4 + h_masks.numel()
+    d2h = B * 8 + net.n_weights * 4
+
+    def e2e_step():
+        d_l0 = h_l0.to(dev, non_blocking=True)
+        d_u0 = h_u0.to(dev, non_blocking=True)
+        d_m = h_masks.to(dev, non_blocking=True)
+        lk, uk = ldb.ld_intermediate_bounds(net, d_l0, d_u0)
+        out, rho = ldb.ld_bound(net, d_l0, d_u0, lk, uk, None, d_m, n_iters=T, opts=opts, return_rho=True)
+        gg = ldb.ld_bound_backward(net, d_l0, d_u0, lk, uk, rho, grad_out=ones, masks=d_m)
+        h_out.copy_(out, non_blocking=True)
+        h_gW.copy_(gg["gW"], non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    etimes = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        e2e_step()
+        e1.record(stream)
+        e1.synchronize()
+        etimes.append(e0.elapsed_time(e1))
+    te_local = sum(etimes) / 1000.0
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_local, te_local], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_all, te_all = tt.tolist()
+        dist.barrier()
+    else:
+        t_all, te_all = t_local, te_local
+    total_bounds = B * args.steps * world
+    value = total_bounds / t_all
+    e2e_value = total_bounds / te_all
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+    peaks, peak_src = measured_peaks()
+    line = {
+        "metric": METRIC, "value": value, "unit": "bounds/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000 * t_all / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{wl['net']} convnet ({net.N} ReLUs), {B} subdomains/GPU, split depth "
+                               f"{wl['depth'][0]}-{wl['depth'][1]}, T={T} Adam iterations, CROWN init, FP64 final "
+                               f"bound, Danskin backward",
+                   "subdomains_per_gpu": B, "iterations": T, "precision": "fp32 iterations, fp64 final",
+                   "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": "bounds/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": None,
+        "peaks_source": peak_src,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, masks_np, lb_h, ub_h)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -261,6 +261,9 @@ class InnerSolution:
     vertex: list           # chosen vertex/endpoint code per neuron, k = 1..n-1
 
 
+TIE_REL = 2.0 ** -16   # vertex tie tolerance of the (u,u) comparison (a reading; see inner_minimisation)
+
+
 def box_argmin(a, l, u):
     """argmin_{y in [l,u]} a*y, taking u when a <= 0 (Eq. (box_bounds_sol) rule)."""
     return np.where(a <= 0, u, l)
@@ -310,7 +313,10 @@ def inner_minimisation(net: Net, l0, u0, lb, ub, rho) -> InnerSolution:
         take = v_00 < best
         best = np.where(take, v_00, best)
         choice[take] = 1
-        take = v_uu < best
+        # (u,u) must win by more than TIE_REL of the magnitudes: the CROWN
+        # point of Prop. 3 puts (l,0) and (u,u) at an exact tie for every
+        # ambiguous ReLU with lambda > 0, which rounding must not decide.
+        take = v_uu < best - TIE_REL * (np.abs(v_uu) + np.abs(best))
         choice[take] = 2
         xb_amb = np.select([choice == 0, choice == 1], [l, np.zeros_like(l)], u)
         xk_amb = np.where(choice == 2, u, 0.0)

@@ -95,24 +95,28 @@ def test_nonfinite_box_sets_status(base16):
 
 # ------------------------------------------------------------------ inner minimisation (rows a2, a3, a4)
 
-def near_tie_mask(on, lbs, ubs, rho, sol, rel_tol=2e-4):
-    """Neurons whose vertex choice an FP32 evaluation may legitimately flip:
-    the two best candidate values (or the box coefficient's sign) are within
-    rel_tol of the magnitude of the terms that produce them."""
-    ties = []
+def near_tie_mask(on, L0, U0, lbs, ubs, rho, sol, rel_tol=5e-5):
+    """Decisions an FP32 evaluation may legitimately take differently from
+    the FP64 oracle: those whose deciding quantity is within rel_tol of its
+    threshold, relative to the magnitude of the terms that produce it.
+    Returns (box near-ties [B, n0], list of per-layer near-ties 1..n-1)."""
+    def absg_of(k):
+        nxt = -np.ones((rho[1].shape[0], 1)) if k + 1 == on.n else rho[k + 1]
+        return np.asarray((abs(on.L(k + 1).mat).T @ np.abs(nxt).T).T)
+    box = np.abs(sol.g[0]) < rel_tol * (absg_of(0) + 1e-30)
+    ties = [None]
     for k in range(1, on.n):
         r, g, l, u = rho[k], sol.g[k], lbs[k], ubs[k]
-        nxt = -np.ones((r.shape[0], 1)) if k + 1 == on.n else rho[k + 1]
-        absg = np.asarray((abs(on.L(k + 1).mat).T @ np.abs(nxt).T).T)
+        absg = absg_of(k)
         mag = (np.abs(r) + absg + 1e-30) * (np.maximum(np.abs(l), np.abs(u)) + 1e-30)
         cls = oracle.classify(l, u)
-        v = np.stack([r * l, np.zeros_like(r), (r - g) * u], axis=-1)
-        vs = np.sort(v, axis=-1)
-        amb_tie = (vs[..., 1] - vs[..., 0]) < rel_tol * mag
-        box_coef = np.where(cls == 0, r, r - g)
-        box_tie = np.abs(box_coef) < rel_tol * (np.abs(r) + absg + 1e-30)
-        ties.append(np.where(cls == 2, amb_tie, box_tie))
-    return ties
+        best0 = np.minimum(r * l, 0.0)
+        vuu = (r - g) * u
+        gap = best0 - oracle.TIE_REL * (np.abs(vuu) + np.abs(best0)) - vuu
+        amb_tie = np.abs(gap) < rel_tol * mag
+        pas_tie = np.abs(r - g) < rel_tol * (np.abs(r) + absg + 1e-30)
+        ties.append(np.where(cls == 2, amb_tie, np.where(cls == 1, pas_tie, False)))
+    return box, ties
 
 
 def check_inner(pb, rho_flat):
@@ -126,25 +130,28 @@ def check_inner(pb, rho_flat):
     rho = oracle.layer_lists(on, rho_flat.astype(np.float64))
     sol = oracle.inner_minimisation(on, L0, U0, lbs, ubs, rho)
     sgo = oracle.supergradient(sol)
-    ties = near_tie_mask(on, lbs, ubs, rho, sol)
+    box_tie, ties = near_tie_mask(on, L0, U0, lbs, ubs, rho, sol)
     offs = oracle.split_offsets(on)
     n_tie = 0
     for b in range(pb["B"]):
         if empty[b]:
             continue
-        mism_below = False
+        # the box choices are not returned: a near-tie there may change x_hat_A,1
+        mism_below = bool(np.any(box_tie[b]))
+        n_tie += int(box_tie[b].sum())
         for k in range(1, on.n):
             gv = vtx[b, offs[k - 1]:offs[k]]
             ov = sol.vertex[k][b]
-            t = ties[k - 1][b]
+            t = ties[k][b]
             n_tie += int(t.sum())
             assert np.array_equal(gv[~t], ov[~t]), f"vertex mismatch subdomain {b} layer {k}"
-            # the supergradient of layer k needs x*_{k-1}: compare it when the
-            # layer below made the same choices everywhere
+            # s_k = x_hat_B,k - x_hat_A,k: x_hat_B,k follows layer k's own choice,
+            # x_hat_A,k all of layer k-1's; compare where both are decided
             if not mism_below:
-                gs = sg[b, offs[k - 1]:offs[k]]
-                scale = np.maximum(np.abs(sol.xA[k][b]), np.abs(sol.xB[k][b])) + 1.0
-                assert np.max(np.abs(gs - sgo[k][b]) / scale) < 1e-5, f"supergradient subdomain {b} layer {k}"
+                gs = sg[b, offs[k - 1]:offs[k]][~t]
+                scale = np.maximum(np.abs(sol.xA[k][b]), np.abs(sol.xB[k][b]))[~t] + 1.0
+                assert np.max(np.abs(gs - sgo[k][b][~t]) / scale, initial=0.0) < 1e-5, \
+                    f"supergradient subdomain {b} layer {k}"
             mism_below = bool(np.any(gv[t] != ov[t]))
         # q is continuous across ties: always compare
         assert rel(q[b], sol.q[b]) < 1e-5, f"q subdomain {b}: {q[b]} vs {sol.q[b]}"
@@ -168,7 +175,7 @@ def test_inner_minimisation_convnets(name):
     N = pb["lbk"].shape[1]
     rho = synth.random_duals([N], pb["B"], seed=21, scale=0.05)[0]
     n_tie = check_inner(pb, rho)
-    assert n_tie < 0.001 * pb["B"] * N
+    assert n_tie < 0.01 * pb["B"] * (N + pb["l0"].shape[1])
 
 
 # ------------------------------------------------------------------ CROWN init (row a1)
@@ -297,9 +304,7 @@ def test_backward_matches_oracle_danskin(name):
     on = pb["net"]
     net = gpu_net(pb)
     L0, U0, lbs, ubs, empty = oracle_lists(on, pb)
-    rc, _ = oracle.crown_init(on, lbs, ubs)
-    run = oracle.supergradient_adam(on, L0, U0, lbs, ubs, rc, 15)
-    rho = flat(on, run.rho).astype(np.float32)
+    rho = synth.random_duals([pb["lbk"].shape[1]], pb["B"], seed=29, scale=0.05)[0]
     w = np.linspace(0.5, 1.5, pb["B"])
     g = ldb.ld_bound_backward(net, pb["l0"], pb["u0"], pb["lbk"], pb["ubk"], rho, grad_out=w, prop=pb["prop"],
                               masks=pb["masks"])

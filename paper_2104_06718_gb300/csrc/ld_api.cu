@@ -50,6 +50,8 @@ void free_ws(ld_net* net) {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+int n_final_slots(const ld_net* net);
+
 ld_status ensure_ws(ld_net* net, int B) {
   if (B <= net->ws_B) return LD_OK;
   const size_t Bn = (size_t)(B > 0 ? B : 1);
@@ -65,7 +67,7 @@ ld_status ensure_ws(ld_net* net, int B) {
       4 * 2 * Bn * n0,   // scr_b0
       Bn,                // empty
       Bn * N,            // vtx
-      8 * 3 * Bn,        // acc
+      8 * 3 * Bn * (size_t)n_final_slots(net),  // acc: final-bound slots
   };
   size_t total = 0;
   for (size_t s : sizes) total += align256(s);
@@ -178,13 +180,20 @@ void sweep(ld_net* net, const Problem& P, int mode, const ld_opts& o, ld::AdamSt
   }
 }
 
+int n_final_slots(const ld_net* net) {
+  int n = 1;  // bias terms
+  for (int k = net->n - 1; k >= 0; --k) n += ld::final_slots(layer(net, k + 1), k == net->n - 1);
+  return n;
+}
+
 void final_fp64(ld_net* net, const Problem& P, double* out, cudaStream_t s) {
   const int n = net->n;
-  ld::FinalAcc acc{net->acc, net->acc + P.B, net->acc + 2 * (size_t)P.B};
-  cudaMemsetAsync(net->acc, 0, sizeof(double) * 3 * (size_t)P.B, s);
-  for (int k = n - 1; k >= 0; --k)
+  ld::FinalAcc acc{net->acc, n_final_slots(net), 0};
+  for (int k = n - 1; k >= 0; --k) {
     ld::launch_final_layer(layer(net, k + 1), k, r_off(net, k), x_off(net, k), P, net->rho, k == n - 1 ? 1 : 0, acc,
                            s);
+    acc.slot += ld::final_slots(layer(net, k + 1), k == n - 1);
+  }
   ld::launch_final_bias(net->L, P, net->rho, acc, s);
   const double M = (double)(net->n0 + 2 * net->N + 1);
   const double gM = ld::final_gamma(M);
@@ -193,13 +202,12 @@ void final_fp64(ld_net* net, const Problem& P, double* out, cudaStream_t s) {
 
 // q in FP32 terms (FP64 sum) via the forward form, +inf for empty subdomains.
 void final_fp32(ld_net* net, const Problem& P, double* out, float* sg, int8_t* vtx, cudaStream_t s) {
-  ld::FinalAcc acc{net->acc, net->acc + P.B, net->acc + 2 * (size_t)P.B};
-  cudaMemsetAsync(net->acc, 0, sizeof(double) * 3 * (size_t)P.B, s);
+  cudaMemsetAsync(net->acc, 0, sizeof(double) * (size_t)P.B, s);
   ld::AdamStep st{};
   ld_opts o;
   ld_opts_default(&o);
   sweep(net, P, 1, o, st, sg, net->acc, vtx, nullptr, s);
-  if (out) ld::launch_final_combine_bn(P, acc, 0.0, 0.0, 1.0, out, s);
+  if (out) ld::launch_record_finish(P, net->acc, out, s);
 }
 
 }  // namespace

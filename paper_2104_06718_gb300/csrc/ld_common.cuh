@@ -240,10 +240,13 @@ void launch_ibp_layer(const LayerDev& L, int first, int last, int n_props, const
 
 // FP64 final bound (ld_final.cu).
 struct FinalAcc {
-  double* S;           // [B] sum of term values
-  double* E;           // [B] sum of term error bounds (rounded up)
-  double* A;           // [B] sum of |term values| (rounded up)
+  double* slots;       // [B, n_slots, 3]: per-slot sum of term values, of their
+                       // error bounds (rounded up) and of |values| (rounded up)
+  int n_slots;
+  int slot;            // first slot of the launch
 };
+int final_slots(const LayerDev& Lnext, int top);
+void launch_record_finish(const Problem& P, const double* q, double* out, cudaStream_t s);
 void launch_final_layer(const LayerDev& Lnext, int layer, int r_off, int x_off, const Problem& P,
                         const float* rho, int top, FinalAcc acc, cudaStream_t s);
 void launch_final_bias(const std::vector<LayerDev>& Ls, const Problem& P, const float* rho, FinalAcc acc,

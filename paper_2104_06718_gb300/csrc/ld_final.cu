@@ -67,10 +67,14 @@ struct FinalEpi {
   }
 };
 
-__device__ __forceinline__ void acc_add(FinalAcc a, int b, double t, double e, double at) {
-  atomicAdd(&a.S[b], t);
-  atomicAdd(&a.E[b], e);
-  atomicAdd(&a.A[b], at);
+// Each (subdomain, slot) partial is written exactly once and the slots are
+// summed in a fixed order by the combine kernel: the final bound does not
+// depend on the order in which blocks run.
+__device__ __forceinline__ void acc_add(FinalAcc a, int slot, int b, double t, double e, double at) {
+  double* p = a.slots + ((size_t)b * a.n_slots + slot) * 3;
+  p[0] = t;
+  p[1] = e;
+  p[2] = at;
 }
 
 // FP64 transposed FC pass (A = rho_{k+1} [B, n_out], W [n_out, n_in]).
@@ -146,11 +150,11 @@ __global__ void __launch_bounds__(NT) final_fc_kernel(int M, int Ncol, int K, co
       se = __dadd_ru(se, __shfl_xor_sync(0xffffffffu, se, off));
       sa = __dadd_ru(sa, __shfl_xor_sync(0xffffffffu, sa, off));
     }
-    if (tx == 0 && m < M) acc_add(acc_out, m, st, se, sa);
+    if (tx == 0 && m < M) acc_add(acc_out, acc_out.slot + blockIdx.x, m, st, se, sa);
   }
 }
 
-__device__ __forceinline__ void block_reduce_add(FinalAcc a, int b, double st, double se, double sa) {
+__device__ __forceinline__ void block_reduce_add(FinalAcc a, int slot, int b, double st, double se, double sa) {
   __shared__ double red[3][NT / 32];
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
@@ -172,7 +176,7 @@ __device__ __forceinline__ void block_reduce_add(FinalAcc a, int b, double st, d
       t1 = __dadd_ru(t1, red[1][i]);
       t2 = __dadd_ru(t2, red[2][i]);
     }
-    acc_add(a, b, t0, t1, t2);
+    acc_add(a, slot, b, t0, t1, t2);
   }
 }
 
@@ -216,7 +220,7 @@ __global__ void __launch_bounds__(NT) final_conv_kernel(LayerDev L, const float*
     se = __dadd_ru(se, ev);
     sa = __dadd_ru(sa, fabs(tv));
   }
-  block_reduce_add(acc_out, b, st, se, sa);
+  block_reduce_add(acc_out, acc_out.slot + blockIdx.x, b, st, se, sa);
 }
 
 // Top subproblem P_{n-1}: g_{n-1} = -W_n exactly (no rounding, delta = 0).
@@ -231,7 +235,7 @@ __global__ void __launch_bounds__(NT) final_top_kernel(int n, const float* __res
     se = __dadd_ru(se, ev);
     sa = __dadd_ru(sa, fabs(tv));
   }
-  block_reduce_add(acc_out, b, st, se, sa);
+  block_reduce_add(acc_out, acc_out.slot, b, st, se, sa);
 }
 
 struct BiasLayers {
@@ -253,7 +257,7 @@ __global__ void __launch_bounds__(NT) final_bias_kernel(Problem P, BiasLayers BL
       st += tv;
       sa = __dadd_ru(sa, fabs(tv));
     }
-  block_reduce_add(acc_out, b, st, 0.0, sa);
+  block_reduce_add(acc_out, acc_out.slot, b, st, 0.0, sa);
 }
 
 __global__ void final_combine_kernel(Problem P, FinalAcc a, double bn, double gamma_M, double inflate, double* out) {
@@ -262,11 +266,22 @@ __global__ void final_combine_kernel(Problem P, FinalAcc a, double bn, double ga
       out[b] = __longlong_as_double(0x7ff0000000000000LL);  // +inf: empty subdomain
       continue;
     }
-    const double S = a.S[b] + bn;
-    const double E = __dmul_ru(a.E[b], inflate);
-    const double A = __dmul_ru(__dadd_ru(a.A[b], fabs(bn)), inflate);
+    double S = bn, E = 0.0, A = fabs(bn);
+    const double* p = a.slots + (size_t)b * a.n_slots * 3;
+    for (int i = 0; i < a.n_slots; ++i) {
+      S += p[3 * i];
+      E = __dadd_ru(E, p[3 * i + 1]);
+      A = __dadd_ru(A, p[3 * i + 2]);
+    }
+    E = __dmul_ru(E, inflate);
+    A = __dmul_ru(A, inflate);
     out[b] = __dsub_rd(__dsub_rd(S, E), __dmul_ru(gamma_M, A));
   }
+}
+
+__global__ void record_finish_kernel(Problem P, const double* q, double* out) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < P.B; b += gridDim.x * blockDim.x)
+    out[b] = P.empty[b] ? __longlong_as_double(0x7ff0000000000000LL) : q[b];
 }
 
 }  // namespace
@@ -320,5 +335,17 @@ void launch_final_combine_bn(const Problem& P, FinalAcc acc, double bn, double g
 }
 
 double final_gamma(double K) { return gamma_of(K); }
+
+void launch_record_finish(const Problem& P, const double* q, double* out, cudaStream_t s) {
+  if (P.B == 0) return;
+  record_finish_kernel<<<(P.B + 255) / 256, 256, 0, s>>>(P, q, out);
+}
+
+// Slots used by the final pass of layer k+1 (transposed pass into layer k).
+int final_slots(const LayerDev& Lnext, int top) {
+  if (top) return 1;
+  if (Lnext.kind == LD_LAYER_FC) return (Lnext.n_in + BN - 1) / BN;
+  return (Lnext.cin * Lnext.h * Lnext.w + NT - 1) / NT;
+}
 
 }  // namespace ld

@@ -138,6 +138,20 @@ def peak_value(d, key_candidates, default):
     return default
 
 
+def macs_per_pass(specs):
+    """Multiply-accumulates of one forward pass of the canonical-form net
+    (the last layer folded to one output)."""
+    total = 0
+    for i, s in enumerate(specs):
+        n_out = 1 if i == len(specs) - 1 else s.n_out
+        if s.kind == "fc":
+            total += n_out * s.n_in
+        else:
+            cout, cin, kh, kw = s.W.shape
+            total += s.n_out * cin * kh * kw
+    return total
+
+
 def make_workload(name, rank):
     from paper_2104_06718_gb300 import synth
     net_name, B, T, depth, eps = WORKLOADS[name]
@@ -270,12 +284,16 @@ def run_ours(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    engine, tile = net.tuned(B)
     # ---- device-resident timing
     sampler = ClockSampler(torch.cuda.current_device())
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     sampler.start()
+    net.profile(True)
+    net.profile_read("iter", reset=True)
+    launches0 = ldb.launch_count()
     times = []
     for _ in range(args.steps):
         flush.fill_(1.0)
@@ -287,6 +305,13 @@ def run_ours(args):
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
     torch.cuda.synchronize()
+    launches = ldb.launch_count() - launches0
+    iter_ms, iter_n = net.profile_read("iter")
+    final_ms, final_n = net.profile_read("final")
+    init_ms, _ = net.profile_read("init")
+    ibp_ms, _ = net.profile_read("ibp")
+    bwd_ms, _ = net.profile_read("backward", reset=True)
+    net.profile(False)
     clocks = sampler.stop()
     t_local = sum(times) / 1000.0
     # ---- end to end through the C ABI with host buffers
@@ -338,6 +363,22 @@ def run_ours(args):
             torch.distributed.destroy_process_group()
         return 0
     peaks, peak_src = measured_peaks()
+    # Roofline of the dominant kernel: the Adam iterations (with the fused
+    # engine, one kernel launch per step).  Algorithmic work per
+    # subdomain-iteration: one transposed and one forward pass, 2 FLOP per MAC.
+    macs = macs_per_pass(wl["specs"])
+    flops_per_launch = B * T * 2 * 2 * macs
+    avg_launch_s = (iter_ms / max(iter_n, 1)) / 1000.0
+    achieved_tflops = flops_per_launch / avg_launch_s / 1e12
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    max_mhz = clocks.get("sm_max_mhz") or 2070.0
+    alu_peak = sm_count * 128 * 2 * max_mhz * 1e6 / 1e12   # FP32 FMA lanes x 2 FLOP x clock
+    roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved_tflops / alu_peak, "traffic": None,
+                "kernel": f"{engine or 'auto'} iterations (tile {tile})",
+                "peak_basis": f"{sm_count} SMs x 128 FP32 FMA/clk x 2 FLOP x {max_mhz:.0f} MHz (derived, not measured)",
+                "work_per_launch": f"{B} subdomains x {T} iterations x 2 passes x {macs} MAC x 2 FLOP",
+                "avg_launch_ms": iter_ms / max(iter_n, 1)}
     line = {
         "metric": METRIC, "value": value, "unit": "bounds/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000 * t_all / args.steps, "higher_is_better": True,
@@ -349,7 +390,12 @@ def run_ours(args):
                    "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": "bounds/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": None,
+        "gpu_launches": int(launches),
+        "roofline": roofline,
+        "phases_ms_per_step": {"ibp": ibp_ms / args.steps, "init": init_ms / args.steps,
+                               "iterations": iter_ms / args.steps, "final_fp64": final_ms / args.steps,
+                               "backward": bwd_ms / args.steps},
+        "engine": {"engine": engine, "tile": tile},
         "peaks_source": peak_src,
     }
     if not args.no_cpu_baseline:

@@ -88,7 +88,18 @@ typedef struct {
   int32_t t_offset;    /* resumed run: schedule index of this call's first
                           iteration (Adam bias correction uses t_offset+t+1) */
   int32_t t_total;     /* schedule length for alpha decay (0: n_iters)      */
+  int32_t engine;      /* LD_ENGINE_*: how the iterations are launched      */
+  int32_t tile;        /* fused engine: subdomains per CTA (0 auto, 1, 2, 4) */
 } ld_opts;
+
+/* Engines for the iterations (all compute the same iterates up to FP32
+ * rounding order):
+ *   LD_ENGINE_AUTO      pick per (net, B) by timing a short probe of each
+ *                       candidate on the first call, then cache the choice;
+ *   LD_ENGINE_LAYERWISE one launch per layer pass and iteration;
+ *   LD_ENGINE_FUSED     one launch for all iterations, each CTA owning
+ *                       `tile` subdomains for the whole run. */
+enum { LD_ENGINE_AUTO = 0, LD_ENGINE_LAYERWISE = 1, LD_ENGINE_FUSED = 2 };
 
 typedef struct ld_net ld_net;
 
@@ -200,6 +211,30 @@ ld_status ld_bound_backward(ld_net* net, const float* lb0, const float* ub0, con
                             const int8_t* split_masks, int32_t B, const float* rho,
                             const double* grad_out, float* gW, float* gb, float* glb0, float* gub0,
                             float* glbk, float* gubk, void* stream);
+
+/* Tracing.  With profiling enabled, every call records CUDA events on its
+ * stream around each phase (not a paper concept; a measurement aid):
+ *   LD_PHASE_ITER   the Adam iterations (with the fused engine: exactly one
+ *                   kernel launch per ld_bound call)
+ *   LD_PHASE_FINAL  the FP64 final bound
+ *   LD_PHASE_INIT   feasibility pre-pass and dual initialisation
+ *   LD_PHASE_IBP    ld_intermediate_bounds
+ *   LD_PHASE_BACKWARD ld_bound_backward
+ * ld_net_profile_read synchronises on the recorded events and returns the
+ * total milliseconds and the number of recorded phase instances since the
+ * last reset (reset = 1 clears them after reading). */
+enum { LD_PHASE_ITER = 0, LD_PHASE_FINAL = 1, LD_PHASE_INIT = 2, LD_PHASE_IBP = 3, LD_PHASE_BACKWARD = 4,
+       LD_N_PHASES = 5 };
+ld_status ld_net_profile(ld_net* net, int32_t enable);
+ld_status ld_net_profile_read(ld_net* net, int32_t phase, double* total_ms, int64_t* count, int32_t reset);
+
+/* Number of kernels this library has launched in this process (all
+ * handles, all calls), for accounting of device work. */
+ld_status ld_launch_count(int64_t* count);
+
+/* The engine and tile the last LD_ENGINE_AUTO choice cached for batch size
+ * B (engine = -1 if none yet). */
+ld_status ld_net_tuned(const ld_net* net, int32_t B, int32_t* engine, int32_t* tile);
 
 #ifdef __cplusplus
 }

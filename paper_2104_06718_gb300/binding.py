@@ -22,11 +22,14 @@ LD_OK, LD_ERR_ARG, LD_ERR_SHAPE, LD_ERR_CUDA, LD_ERR_NOMEM, LD_ERR_TIMEOUT, LD_E
 LD_LAYER_FC, LD_LAYER_CONV = 0, 1
 LD_INIT_ZERO, LD_INIT_CROWN, LD_INIT_GIVEN = 0, 1, 2
 LD_PREC_FP32, LD_PREC_BF16 = 0, 1
+LD_ENGINE_AUTO, LD_ENGINE_LAYERWISE, LD_ENGINE_FUSED = 0, 1, 2
 
 EXPORTED = [
     "ld_opts_default", "ld_status_str", "ld_net_create", "ld_net_destroy", "ld_net_sizes", "ld_net_reserve",
     "ld_net_sync_status", "ld_intermediate_bounds", "ld_bound", "ld_dual_supergradient", "ld_bound_backward",
+    "ld_net_profile", "ld_net_profile_read", "ld_launch_count", "ld_net_tuned",
 ]
+PHASES = {"iter": 0, "final": 1, "init": 2, "ibp": 3, "backward": 4}
 
 
 class LDError(RuntimeError):
@@ -44,7 +47,7 @@ class LayerDesc(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("alpha0", C.c_float), ("alpha_end", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
                 ("eps", C.c_float), ("init", C.c_int32), ("precision", C.c_int32), ("fp64_final", C.c_int32),
-                ("t_offset", C.c_int32), ("t_total", C.c_int32)]
+                ("t_offset", C.c_int32), ("t_total", C.c_int32), ("engine", C.c_int32), ("tile", C.c_int32)]
 
 
 _lib = None
@@ -73,6 +76,10 @@ def load_library(path: str = LIB_PATH):
     lib.ld_bound.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, i32, i32, C.POINTER(Opts), vp, vp, vp, vp, vp]
     lib.ld_dual_supergradient.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, i32, vp, vp, vp, vp, vp]
     lib.ld_bound_backward.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.ld_net_profile.argtypes = [vp, i32]
+    lib.ld_net_profile_read.argtypes = [vp, i32, C.POINTER(C.c_double), C.POINTER(i64), i32]
+    lib.ld_launch_count.argtypes = [C.POINTER(i64)]
+    lib.ld_net_tuned.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32)]
     for name in EXPORTED:
         if name not in ("ld_opts_default", "ld_status_str"):
             getattr(lib, name).restype = C.c_int
@@ -129,12 +136,16 @@ class Options:
     fp64_final: bool = True
     t_offset: int = 0
     t_total: int = 0
+    engine: str = "auto"         # "auto" | "layerwise" | "fused"
+    tile: int = 0                # fused engine: subdomains per CTA (0 = auto, 1, 2, 4)
 
     def to_c(self) -> Opts:
         return Opts(self.alpha0, self.alpha_end, self.beta1, self.beta2, self.eps,
                     {"zero": LD_INIT_ZERO, "crown": LD_INIT_CROWN, "given": LD_INIT_GIVEN}[self.init],
                     {"fp32": LD_PREC_FP32, "bf16": LD_PREC_BF16}[self.precision],
-                    int(self.fp64_final), self.t_offset, self.t_total)
+                    int(self.fp64_final), self.t_offset, self.t_total,
+                    {"auto": LD_ENGINE_AUTO, "layerwise": LD_ENGINE_LAYERWISE, "fused": LD_ENGINE_FUSED}[self.engine],
+                    int(self.tile))
 
 
 class Net:
@@ -198,6 +209,31 @@ class Net:
 
     def sync_status(self):
         return self._lib.ld_net_sync_status(self._h, _stream())
+
+    def profile(self, enable: bool = True):
+        """Record CUDA events around each phase of every call."""
+        _check(self._lib.ld_net_profile(self._h, int(enable)), "ld_net_profile")
+
+    def profile_read(self, phase: str, reset: bool = False):
+        """(total ms, instances) of a phase since the last reset."""
+        ms, n = C.c_double(), C.c_int64()
+        _check(self._lib.ld_net_profile_read(self._h, PHASES[phase], C.byref(ms), C.byref(n), int(reset)),
+               "ld_net_profile_read")
+        return ms.value, n.value
+
+    def tuned(self, B: int):
+        """(engine, tile) chosen by the autotuner for batch size B, or (None, 0)."""
+        e, t = C.c_int32(), C.c_int32()
+        _check(self._lib.ld_net_tuned(self._h, int(B), C.byref(e), C.byref(t)), "ld_net_tuned")
+        names = {LD_ENGINE_LAYERWISE: "layerwise", LD_ENGINE_FUSED: "fused"}
+        return names.get(e.value), t.value
+
+
+def launch_count() -> int:
+    """Kernels launched by libld in this process so far."""
+    n = C.c_int64()
+    _check(load_library().ld_launch_count(C.byref(n)), "ld_launch_count")
+    return n.value
 
 
 def ld_intermediate_bounds(net: Net, lb0, ub0, want_output_lb: bool = False):

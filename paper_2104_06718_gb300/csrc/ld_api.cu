@@ -1,14 +1,22 @@
 // C ABI of libld (declared in include/ld.h): argument checking, the net
 // handle, workspace ownership and the order of the passes of one call.
+#include <atomic>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "ld_common.cuh"
 
 using ld::LayerDev;
 using ld::Problem;
+
+namespace ld {
+std::atomic<int64_t> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add(n); }
+}  // namespace ld
 
 struct ld_net {
   int n = 0;
@@ -28,7 +36,66 @@ struct ld_net {
   float *scr_bn = nullptr, *scr_b0 = nullptr;
   int8_t *empty = nullptr, *vtx = nullptr;
   double* acc = nullptr;
+  // fused engine and the autotuner's choices: B -> (engine, tile)
+  ld::FusedNet fused{};
+  std::map<int, std::pair<int, int>> tuned;
+  int n_sm = 0;
+  size_t smem_optin = 0;
+  // tracing: recorded (phase, start, stop) events and accumulated totals
+  bool profile = false;
+  struct Mark {
+    int phase;
+    cudaEvent_t a, b;
+  };
+  std::vector<Mark> marks;
+  double prof_ms[LD_N_PHASES] = {0, 0, 0, 0, 0};
+  int64_t prof_n[LD_N_PHASES] = {0, 0, 0, 0, 0};
 };
+
+namespace {
+
+// RAII phase marker: records a start event now and a stop event when it goes
+// out of scope (only when profiling is on).
+struct PhaseMark {
+  ld_net* net;
+  int phase;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  PhaseMark(ld_net* n, int ph, cudaStream_t st) : net(n), phase(ph), s(st) {
+    if (!net->profile) return;
+    if (cudaEventCreate(&a) != cudaSuccess) {
+      a = nullptr;
+      return;
+    }
+    cudaEventRecord(a, s);
+  }
+  ~PhaseMark() {
+    if (!a) return;
+    cudaEvent_t b;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+      cudaEventDestroy(a);
+      return;
+    }
+    cudaEventRecord(b, s);
+    net->marks.push_back({phase, a, b});
+  }
+};
+
+void drain_marks(ld_net* net) {
+  for (auto& mk : net->marks) {
+    cudaEventSynchronize(mk.b);
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, mk.a, mk.b) == cudaSuccess) {
+      net->prof_ms[mk.phase] += ms;
+      net->prof_n[mk.phase] += 1;
+    }
+    cudaEventDestroy(mk.a);
+    cudaEventDestroy(mk.b);
+  }
+  net->marks.clear();
+}
+
+}  // namespace
 
 namespace {
 
@@ -112,6 +179,8 @@ ld_status check_opts(const ld_opts& o) {
   if (o.precision != LD_PREC_FP32 && o.precision != LD_PREC_BF16) return LD_ERR_ARG;
   if (o.precision == LD_PREC_BF16) return LD_ERR_UNSUPPORTED;
   if (o.t_offset < 0 || o.t_total < 0) return LD_ERR_ARG;
+  if (o.engine < LD_ENGINE_AUTO || o.engine > LD_ENGINE_FUSED) return LD_ERR_ARG;
+  if (o.tile != 0 && o.tile != 1 && o.tile != 2 && o.tile != 4) return LD_ERR_ARG;
   return LD_OK;
 }
 
@@ -180,6 +249,86 @@ void sweep(ld_net* net, const Problem& P, int mode, const ld_opts& o, ld::AdamSt
   }
 }
 
+bool tile_fits(const ld_net* net, int S) { return ld::fused_smem_bytes(net->fused, S) <= net->smem_optin; }
+
+// T Adam iterations with the given engine (tile = subdomains per CTA).
+ld_status run_iterations(ld_net* net, const Problem& P, const ld_opts& o, int n_iters, int engine, int tile,
+                         cudaStream_t s) {
+  const int T_sched = o.t_total > 0 ? o.t_total : o.t_offset + n_iters;
+  if (engine == LD_ENGINE_FUSED) {
+    ld::FusedIter it{n_iters, o.t_offset, T_sched, o.alpha0, o.alpha_end, o.beta1, o.beta2, o.eps};
+    return cuda_status(ld::launch_fused(net->fused, tile, P, net->rho, net->m, net->v, it, s));
+  }
+  for (int t = 0; t < n_iters; ++t) {
+    const int tt = o.t_offset + t;
+    ld::AdamStep a;
+    const double alpha = (double)o.alpha0 + ((double)o.alpha_end - (double)o.alpha0) * (double)tt /
+                                                (double)(T_sched - 1 > 1 ? T_sched - 1 : 1);
+    a.alpha = (float)alpha;
+    a.inv_bc1 = (float)(1.0 / (1.0 - std::pow((double)o.beta1, (double)(tt + 1))));
+    a.inv_bc2 = (float)(1.0 / (1.0 - std::pow((double)o.beta2, (double)(tt + 1))));
+    sweep(net, P, 0, o, a, nullptr, nullptr, nullptr, nullptr, s);
+  }
+  return last_error();
+}
+
+// Engine and tile for this call.  LD_ENGINE_AUTO times a 4-iteration probe
+// of every candidate on the first call with a given B (on the call's own
+// inputs, before rho is initialised) and caches the fastest; while the
+// stream is being captured it falls back to a fixed rule.
+std::pair<int, int> choose_engine(ld_net* net, const Problem& P, const ld_opts& o, cudaStream_t s) {
+  if (o.engine == LD_ENGINE_LAYERWISE) return {LD_ENGINE_LAYERWISE, 0};
+  if (o.engine == LD_ENGINE_FUSED) {
+    int S = o.tile;
+    if (S == 0) S = P.B <= 2 * net->n_sm ? 1 : 2;
+    while (S > 1 && !tile_fits(net, S)) S /= 2;
+    if (!tile_fits(net, S)) return {LD_ENGINE_LAYERWISE, 0};
+    return {LD_ENGINE_FUSED, S};
+  }
+  auto hit = net->tuned.find(P.B);
+  if (hit != net->tuned.end()) return hit->second;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cap);
+  if (cap != cudaStreamCaptureStatusNone) {
+    ld_opts f = o;
+    f.engine = LD_ENGINE_FUSED;
+    return choose_engine(net, P, f, s);
+  }
+  ld::launch_empty_flags(P, net->empty, net->d_status, s);
+  std::vector<std::pair<int, int>> cands = {{LD_ENGINE_LAYERWISE, 0}};
+  for (int S : {1, 2, 4})
+    if (tile_fits(net, S)) cands.push_back({LD_ENGINE_FUSED, S});
+  const size_t BN = (size_t)P.B * net->N;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  ld_opts probe = o;
+  probe.t_offset = 0;
+  probe.t_total = 100;
+  float best = 1e30f;
+  std::pair<int, int> choice = cands.back();
+  for (const auto& c : cands) {
+    cudaMemsetAsync(net->rho, 0, sizeof(float) * BN, s);
+    cudaMemsetAsync(net->m, 0, sizeof(float) * BN, s);
+    cudaMemsetAsync(net->v, 0, sizeof(float) * BN, s);
+    run_iterations(net, P, probe, 1, c.first, c.second, s);  // warm-up
+    cudaEventRecord(e0, s);
+    ld_status st = run_iterations(net, P, probe, 4, c.first, c.second, s);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (st == LD_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best) {
+      best = ms;
+      choice = c;
+    }
+  }
+  cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  net->tuned[P.B] = choice;
+  return choice;
+}
+
 int n_final_slots(const ld_net* net) {
   int n = 1;  // bias terms
   for (int k = net->n - 1; k >= 0; --k) n += ld::final_slots(layer(net, k + 1), k == net->n - 1);
@@ -226,6 +375,8 @@ void ld_opts_default(ld_opts* o) {
   o->fp64_final = 1;
   o->t_offset = 0;
   o->t_total = 0;
+  o->engine = LD_ENGINE_AUTO;
+  o->tile = 0;
 }
 
 const char* ld_status_str(ld_status s) {
@@ -356,6 +507,13 @@ ld_status ld_net_create(const ld_layer_desc* Ld, int32_t n_layers, const float* 
     L[k].b = net->d_b + b_off[k];
   }
   net->L = L;
+  net->fused = ld::make_fused_net(L);
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+  net->n_sm = v > 0 ? v : 1;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  net->smem_optin = (size_t)(v > 0 ? v : 48 * 1024);
   *out = net;
   return LD_OK;
 }
@@ -363,6 +521,7 @@ ld_status ld_net_create(const ld_layer_desc* Ld, int32_t n_layers, const float* 
 ld_status ld_net_destroy(ld_net* net) {
   if (!net) return LD_ERR_ARG;
   cudaDeviceSynchronize();
+  drain_marks(net);
   free_ws(net);
   if (net->d_W) cudaFree(net->d_W);
   if (net->d_b) cudaFree(net->d_b);
@@ -402,6 +561,7 @@ ld_status ld_intermediate_bounds(ld_net* net, const float* lb0, const float* ub0
   if (!net || !lb0 || !ub0 || !lbk || !ubk || n_props < 1) return LD_ERR_ARG;
   cudaStream_t s = S(stream);
   const int n = net->n;
+  PhaseMark pm(net, LD_PHASE_IBP, s);
   for (int k = 1; k <= n; ++k) {
     const LayerDev& L = layer(net, k);
     const float* lin = k == 1 ? lb0 : lbk + r_off(net, k - 1);
@@ -431,35 +591,35 @@ ld_status ld_bound(ld_net* net, const float* lb0, const float* ub0, const float*
   cudaStream_t s = S(stream);
   const Problem P = make_problem(net, lb0, ub0, lbk, ubk, n_props, prop, masks, B);
   const size_t BN = (size_t)B * net->N;
-  ld::launch_empty_flags(P, net->empty, net->d_status, s);
-  if (o.init == LD_INIT_GIVEN)
-    cudaMemcpyAsync(net->rho, rho_in, sizeof(float) * BN, cudaMemcpyDeviceToDevice, s);
-  else if (o.init == LD_INIT_ZERO)
-    cudaMemsetAsync(net->rho, 0, sizeof(float) * BN, s);
-  else
-    crown_sweep(net, P, s);
-  if (adam_mv && o.t_offset > 0) {
-    cudaMemcpyAsync(net->m, adam_mv, sizeof(float) * BN, cudaMemcpyDeviceToDevice, s);
-    cudaMemcpyAsync(net->v, adam_mv + BN, sizeof(float) * BN, cudaMemcpyDeviceToDevice, s);
-  } else {
-    cudaMemsetAsync(net->m, 0, sizeof(float) * BN, s);
-    cudaMemsetAsync(net->v, 0, sizeof(float) * BN, s);
+  const std::pair<int, int> eng = n_iters > 0 ? choose_engine(net, P, o, s) : std::make_pair(1, 0);
+  {
+    PhaseMark pm(net, LD_PHASE_INIT, s);
+    ld::launch_empty_flags(P, net->empty, net->d_status, s);
+    if (o.init == LD_INIT_GIVEN)
+      cudaMemcpyAsync(net->rho, rho_in, sizeof(float) * BN, cudaMemcpyDeviceToDevice, s);
+    else if (o.init == LD_INIT_ZERO)
+      cudaMemsetAsync(net->rho, 0, sizeof(float) * BN, s);
+    else
+      crown_sweep(net, P, s);
+    if (adam_mv && o.t_offset > 0) {
+      cudaMemcpyAsync(net->m, adam_mv, sizeof(float) * BN, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(net->v, adam_mv + BN, sizeof(float) * BN, cudaMemcpyDeviceToDevice, s);
+    } else {
+      cudaMemsetAsync(net->m, 0, sizeof(float) * BN, s);
+      cudaMemsetAsync(net->v, 0, sizeof(float) * BN, s);
+    }
   }
-  const int T_sched = o.t_total > 0 ? o.t_total : o.t_offset + n_iters;
-  for (int t = 0; t < n_iters; ++t) {
-    const int tt = o.t_offset + t;
-    ld::AdamStep a;
-    const double alpha = (double)o.alpha0 + ((double)o.alpha_end - (double)o.alpha0) * (double)tt /
-                                                (double)(T_sched - 1 > 1 ? T_sched - 1 : 1);
-    a.alpha = (float)alpha;
-    a.inv_bc1 = (float)(1.0 / (1.0 - std::pow((double)o.beta1, (double)(tt + 1))));
-    a.inv_bc2 = (float)(1.0 / (1.0 - std::pow((double)o.beta2, (double)(tt + 1))));
-    sweep(net, P, 0, o, a, nullptr, nullptr, nullptr, nullptr, s);
+  if (n_iters > 0) {
+    PhaseMark pm(net, LD_PHASE_ITER, s);
+    if ((st = run_iterations(net, P, o, n_iters, eng.first, eng.second, s)) != LD_OK) return st;
   }
-  if (o.fp64_final)
-    final_fp64(net, P, out, s);
-  else
-    final_fp32(net, P, out, nullptr, nullptr, s);
+  {
+    PhaseMark pm(net, LD_PHASE_FINAL, s);
+    if (o.fp64_final)
+      final_fp64(net, P, out, s);
+    else
+      final_fp32(net, P, out, nullptr, nullptr, s);
+  }
   if (rho_out) cudaMemcpyAsync(rho_out, net->rho, sizeof(float) * BN, cudaMemcpyDeviceToDevice, s);
   if (adam_mv) {
     cudaMemcpyAsync(adam_mv, net->m, sizeof(float) * BN, cudaMemcpyDeviceToDevice, s);
@@ -503,6 +663,7 @@ ld_status ld_bound_backward(ld_net* net, const float* lb0, const float* ub0, con
   }
   if ((st = ensure_ws(net, B)) != LD_OK) return st;
   const Problem P = make_problem(net, lb0, ub0, lbk, ubk, n_props, prop, masks, B);
+  PhaseMark pm(net, LD_PHASE_BACKWARD, s);
   ld::launch_empty_flags(P, net->empty, net->d_status, s);
   cudaMemcpyAsync(net->rho, rho, sizeof(float) * (size_t)B * net->N, cudaMemcpyDeviceToDevice, s);
   ld_opts o;
@@ -512,6 +673,40 @@ ld_status ld_bound_backward(ld_net* net, const float* lb0, const float* ub0, con
   ld::launch_backward(net->L, net->w_off, net->b_off, P, net->rho, grad_out, net->x, net->g, net->vtx, net->scr_bn,
                       net->scr_b0, bo, s);
   return last_error();
+}
+
+ld_status ld_net_profile(ld_net* net, int32_t enable) {
+  if (!net) return LD_ERR_ARG;
+  net->profile = enable != 0;
+  return LD_OK;
+}
+
+ld_status ld_net_profile_read(ld_net* net, int32_t phase, double* total_ms, int64_t* count, int32_t reset) {
+  if (!net || phase < 0 || phase >= LD_N_PHASES) return LD_ERR_ARG;
+  drain_marks(net);
+  if (total_ms) *total_ms = net->prof_ms[phase];
+  if (count) *count = net->prof_n[phase];
+  if (reset) {
+    for (int i = 0; i < LD_N_PHASES; ++i) {
+      net->prof_ms[i] = 0.0;
+      net->prof_n[i] = 0;
+    }
+  }
+  return LD_OK;
+}
+
+ld_status ld_launch_count(int64_t* count) {
+  if (!count) return LD_ERR_ARG;
+  *count = ld::g_launches.load();
+  return LD_OK;
+}
+
+ld_status ld_net_tuned(const ld_net* net, int32_t B, int32_t* engine, int32_t* tile) {
+  if (!net) return LD_ERR_ARG;
+  auto it = net->tuned.find(B);
+  if (engine) *engine = it == net->tuned.end() ? -1 : it->second.first;
+  if (tile) *tile = it == net->tuned.end() ? 0 : it->second.second;
+  return LD_OK;
 }
 
 }  // extern "C"

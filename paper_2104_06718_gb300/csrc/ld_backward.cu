@@ -157,6 +157,7 @@ void launch_backward(const std::vector<LayerDev>& Ls, const std::vector<size_t>&
   for (int k = 1; k <= n; ++k) {
     const LayerDev& L = Ls[k - 1];
     const int last = k == n;
+    count_launch((out.gW ? 1 : 0) + (out.gb ? 1 : 0));
     if (out.gW) {
       float* G = out.gW + w_off[k - 1];
       if (L.kind == LD_LAYER_FC) {
@@ -180,9 +181,11 @@ void launch_backward(const std::vector<LayerDev>& Ls, const std::vector<size_t>&
     int grid = (int)((total + NT - 1) / NT);
     if (grid > 65535 * 8) grid = 65535 * 8;
     if (grid < 1) grid = 1;
+    count_launch();
     bound_contrib_kernel<<<grid, NT, 0, s>>>(P, grad_out, rho, g, vtx, gl, gu, gl0, gu0);
     auto red = [&](const float* src, int width, float* dst) {
       if (!dst) return;
+      count_launch();
       cudaMemsetAsync(dst, 0, sizeof(float) * (size_t)P.n_props * width, s);
       reduce_by_prop_kernel<<<(width + NT - 1) / NT, NT, 0, s>>>(P, src, width, dst);
     };

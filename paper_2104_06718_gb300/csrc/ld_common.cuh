@@ -218,6 +218,33 @@ struct EpiRecord {
   }
 };
 
+// Library-wide count of kernel launches (every launcher calls this once per
+// kernel it launches); read through ld_launch_count.
+void count_launch(int n = 1);
+
+// ---------------------------------------------------------------- fused engine
+// The net as the fused kernel sees it (ld_fused.cu).
+struct FusedNet {
+  int n;
+  int maxX;                    // max n_k, k = 0..n-1 (x_k buffer)
+  int maxB;                    // max n_k, k = 1..n-1 (x_hat_B buffers)
+  int maxR;                    // max n_k, k = 1..n-1 (staged rho_{k+1})
+  int convW_total;
+  int convW_off[kMaxLayers];   // offset of a conv layer's weights in shared memory
+  LayerDev L[kMaxLayers];      // L[k] = layer k+1 of the paper
+};
+
+// Iteration range and Adam settings of one fused launch.
+struct FusedIter {
+  int T, t_offset, T_sched;
+  float alpha0, alpha_end, beta1, beta2, eps;
+};
+
+FusedNet make_fused_net(const std::vector<LayerDev>& Ls);
+size_t fused_smem_bytes(const FusedNet& f, int S);
+cudaError_t launch_fused(const FusedNet& f, int S, const Problem& P, float* rho, float* m, float* v,
+                         const FusedIter& it, cudaStream_t s);
+
 // ---------------------------------------------------------------- launchers
 // FP32 passes (ld_passes.cu).
 void launch_transposed_argmin(const LayerDev& L, const LayerDev* Lnext_or_null, const Problem& P,

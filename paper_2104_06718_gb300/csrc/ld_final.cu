@@ -296,6 +296,7 @@ void launch_final_layer(const LayerDev& Lnext, int layer, int r_off, int x_off, 
   (void)x_off;
   FinalEpi epi{P, layer, r_off, rho, gamma_of((double)Lnext.fan_t)};
   if (P.B == 0) return;
+  count_launch();
   if (top) {
     final_top_kernel<<<P.B, NT, 0, s>>>(Lnext.n_in, Lnext.W, epi, acc);
     return;
@@ -324,6 +325,7 @@ void launch_final_bias(const std::vector<LayerDev>& Ls, const Problem& P, const 
     BL.plane[k] = L.kind == LD_LAYER_FC ? 1 : L.ho * L.wo;
     BL.bias[k] = L.b;
   }
+  count_launch();
   final_bias_kernel<<<P.B, NT, 0, s>>>(P, BL, rho, acc);
 }
 
@@ -331,6 +333,7 @@ void launch_final_bias(const std::vector<LayerDev>& Ls, const Problem& P, const 
 void launch_final_combine_bn(const Problem& P, FinalAcc acc, double bn, double gamma_M, double inflate,
                              double* out, cudaStream_t s) {
   if (P.B == 0) return;
+  count_launch();
   final_combine_kernel<<<(P.B + 255) / 256, 256, 0, s>>>(P, acc, bn, gamma_M, inflate, out);
 }
 
@@ -338,6 +341,7 @@ double final_gamma(double K) { return gamma_of(K); }
 
 void launch_record_finish(const Problem& P, const double* q, double* out, cudaStream_t s) {
   if (P.B == 0) return;
+  count_launch();
   record_finish_kernel<<<(P.B + 255) / 256, 256, 0, s>>>(P, q, out);
 }
 

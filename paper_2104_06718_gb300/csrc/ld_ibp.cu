@@ -77,6 +77,7 @@ void launch_ibp_layer(const LayerDev& L, int first, int last, int n_props, const
   const size_t total = (size_t)n_props * L.n_out;
   int grid = (int)((total + 255) / 256);
   if (grid < 1) grid = 1;
+  count_launch();
   ibp_kernel<<<grid, 256, 0, s>>>(L, first, last, n_props, lin, uin, in_stride, lout, uout, out_stride, out_lb,
                                   status);
 }

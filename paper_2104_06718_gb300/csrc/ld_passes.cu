@@ -190,6 +190,7 @@ inline int grid1d(size_t total, int nt = NT) {
 template <class Epi>
 void transposed(const LayerDev& L, const Problem& P, const float* rho, Epi epi, cudaStream_t s) {
   // g over the inputs of layer L (= the neurons of the layer below it).
+  count_launch();
   const float* r = rho + L.r_out_off;
   if (L.kind == LD_LAYER_FC) {
     dim3 grid((L.n_in + BN - 1) / BN, (P.B + BM - 1) / BM);
@@ -204,6 +205,7 @@ void transposed(const LayerDev& L, const Problem& P, const float* rho, Epi epi, 
 
 template <class Epi>
 void forward(const LayerDev& L, const Problem& P, const float* x, Epi epi, cudaStream_t s) {
+  count_launch();
   const float* xin = x + L.x_in_off;
   if (L.kind == LD_LAYER_FC) {
     dim3 grid((L.n_out + BN - 1) / BN, (P.B + BM - 1) / BM);
@@ -229,10 +231,12 @@ void launch_transposed_crown(const LayerDev& L, const Problem& P, const float* r
 }
 
 void launch_top_argmin(const LayerDev& Ln, const Problem& P, EpiArgmin epi, cudaStream_t s) {
+  count_launch();
   top_kernel<EpiArgmin><<<grid1d((size_t)P.B * Ln.n_in), NT, 0, s>>>(P.B, Ln.n_in, Ln.W, epi);
 }
 
 void launch_top_crown(const LayerDev& Ln, const Problem& P, EpiCrown epi, cudaStream_t s) {
+  count_launch();
   top_kernel<EpiCrown><<<grid1d((size_t)P.B * Ln.n_in), NT, 0, s>>>(P.B, Ln.n_in, Ln.W, epi);
 }
 
@@ -246,7 +250,11 @@ void launch_forward_record(const LayerDev& L, const Problem& P, const float* x, 
 }
 
 void launch_empty_flags(const Problem& P, int8_t* empty, int* status, cudaStream_t s) {
-  if (P.B > 0) empty_kernel<<<P.B, NT, 0, s>>>(P, empty, status);
+  if (P.B > 0) {
+    count_launch();
+    empty_kernel<<<P.B, NT, 0, s>>>(P, empty, status);
+  }
+  count_launch();
   box_check_kernel<<<grid1d((size_t)P.n_props * (P.n0 > P.N ? P.n0 : P.N)), NT, 0, s>>>(P, status);
 }
 

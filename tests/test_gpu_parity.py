@@ -249,22 +249,35 @@ FULL_RUN_MAX = 1e-3
 FULL_RUN_MEDIAN = 3e-4
 
 
-def run_both(pb, T):
+ENGINES = {"layerwise": ldb.Options(engine="layerwise"), "fused1": ldb.Options(engine="fused", tile=1),
+           "fused2": ldb.Options(engine="fused", tile=2), "fused4": ldb.Options(engine="fused", tile=4),
+           "auto": ldb.Options()}
+_oracle_cache = {}
+
+
+def run_both(pb, T, engine="auto", key=None):
     net = gpu_net(pb)
-    out = ldb.ld_bound(net, pb["l0"], pb["u0"], pb["lbk"], pb["ubk"], pb["prop"], pb["masks"], n_iters=T).cpu().numpy()
-    ref, _, _ = oracle.ld_bound(pb["net"], pb["l0"].astype(np.float64), pb["u0"].astype(np.float64),
-                                pb["lbk"].astype(np.float64), pb["ubk"].astype(np.float64), pb["prop"],
-                                pb["masks"], T)
+    out = ldb.ld_bound(net, pb["l0"], pb["u0"], pb["lbk"], pb["ubk"], pb["prop"], pb["masks"], n_iters=T,
+                       opts=ENGINES[engine]).cpu().numpy()
+    if key is None or key not in _oracle_cache:
+        ref, _, _ = oracle.ld_bound(pb["net"], pb["l0"].astype(np.float64), pb["u0"].astype(np.float64),
+                                    pb["lbk"].astype(np.float64), pb["ubk"].astype(np.float64), pb["prop"],
+                                    pb["masks"], T)
+        if key is not None:
+            _oracle_cache[key] = ref
+    else:
+        ref = _oracle_cache[key]
     fin = np.isfinite(ref)
     assert np.array_equal(np.isfinite(out), fin)
     return out[fin], ref[fin]
 
 
+@pytest.mark.parametrize("engine", ["layerwise", "fused1", "fused2", "fused4"])
 @pytest.mark.parametrize("name", ["base", "wide", "deep"])
 @pytest.mark.parametrize("T", [1, 3])
-def test_short_runs_match_oracle_strictly(name, T):
+def test_short_runs_match_oracle_strictly(name, T, engine):
     pb = conv_problem(name, 16, depth=(0, 8), block=8)
-    out, ref = run_both(pb, T)
+    out, ref = run_both(pb, T, engine, key=("short", name, T))
     assert np.max(rel(out, ref)) < 1e-5
 
 
@@ -282,26 +295,28 @@ def test_tiny_full_runs_match_oracle_and_stay_below_lp(tiny_set):
     assert max(errs) < FULL_RUN_MAX and np.median(errs) < FULL_RUN_MEDIAN
 
 
+@pytest.mark.parametrize("engine", ["layerwise", "fused1", "fused2", "fused4"])
 @pytest.mark.parametrize("name,B,T", [("base", 24, 100), ("deep", 12, 100), ("wide", 8, 60)])
-def test_convnet_full_runs_match_oracle(name, B, T):
+def test_convnet_full_runs_match_oracle(name, B, T, engine):
     pb = conv_problem(name, B, depth=(0, 8), block=5)
-    out, ref = run_both(pb, T)
+    out, ref = run_both(pb, T, engine, key=("full", name, B, T))
     r = rel(out, ref)
     assert np.max(r) < FULL_RUN_MAX and np.median(r) < FULL_RUN_MEDIAN
 
 
-def test_resume_is_bitwise(base16):
+@pytest.mark.parametrize("engine", ["layerwise", "fused"])
+def test_resume_is_bitwise(base16, engine):
     """T iterations in one call equal T1 + T2 iterations in two calls (the
     Adam moments and schedule index are carried)."""
     pb = base16
     net = gpu_net(pb)
     args = (pb["l0"], pb["u0"], pb["lbk"], pb["ubk"], pb["prop"], pb["masks"])
-    out_a, rho_a = ldb.ld_bound(net, *args, n_iters=20, return_rho=True)
+    out_a, rho_a = ldb.ld_bound(net, *args, n_iters=20, return_rho=True, opts=ldb.Options(engine=engine, tile=2))
     B, N = pb["B"], pb["lbk"].shape[1]
     mv = torch.zeros((2, B, N), dtype=torch.float32, device="cuda")
-    o1 = ldb.Options(t_offset=0, t_total=20)
+    o1 = ldb.Options(t_offset=0, t_total=20, engine=engine, tile=2)
     _, rho_1 = ldb.ld_bound(net, *args, n_iters=12, opts=o1, return_rho=True, adam_mv=mv)
-    o2 = ldb.Options(t_offset=12, t_total=20, init="given")
+    o2 = ldb.Options(t_offset=12, t_total=20, init="given", engine=engine, tile=2)
     out_b, rho_b = ldb.ld_bound(net, *args, n_iters=8, opts=o2, rho_in=rho_1, return_rho=True, adam_mv=mv)
     assert torch.equal(rho_a, rho_b)
     assert torch.equal(out_a, out_b)
@@ -364,7 +379,8 @@ def test_wide_2048_sampled_against_oracle():
     pb = conv_problem("wide", 2048, depth=(0, 20), block=7)
     on = pb["net"]
     net = gpu_net(pb)
-    out = ldb.ld_bound(net, pb["l0"], pb["u0"], pb["lbk"], pb["ubk"], pb["prop"], pb["masks"], n_iters=100).cpu().numpy()
+    out = ldb.ld_bound(net, pb["l0"], pb["u0"], pb["lbk"], pb["ubk"], pb["prop"], pb["masks"], n_iters=100,
+                       opts=ldb.Options(engine="fused", tile=2)).cpu().numpy()
     rows = np.array([0, 1, 777, 2047])
     sub = dict(pb, prop=pb["prop"][rows], masks=pb["masks"][rows], B=len(rows))
     ref, _, _ = oracle.ld_bound(on, pb["l0"].astype(np.float64), pb["u0"].astype(np.float64),
@@ -375,3 +391,19 @@ def test_wide_2048_sampled_against_oracle():
     assert np.max(rel(out[rows][fin], ref[fin])) < FULL_RUN_MAX
     xs = synth.random_box_points(pb["l0"][0], pb["u0"][0], 256, seed=9)
     assert out[0] <= on.evaluate(xs).min()
+
+
+def test_engines_agree_after_one_iteration(base16):
+    """The layerwise and fused engines compute the same iterate (they differ
+    only in the summation order of the forward FC pass)."""
+    pb = base16
+    net = gpu_net(pb)
+    args = (pb["l0"], pb["u0"], pb["lbk"], pb["ubk"], pb["prop"], pb["masks"])
+    outs, rhos = [], []
+    for eng, tile in (("layerwise", 0), ("fused", 1), ("fused", 2), ("fused", 4)):
+        o, r = ldb.ld_bound(net, *args, n_iters=1, return_rho=True, opts=ldb.Options(engine=eng, tile=tile))
+        outs.append(o.cpu().numpy())
+        rhos.append(r.cpu().numpy())
+    for o, r in zip(outs[1:], rhos[1:]):
+        assert np.max(rel(o, outs[0])) < 1e-6
+        assert np.max(np.abs(r - rhos[0])) < 1e-6

@@ -51,6 +51,11 @@ def parse():
     ap.add_argument("--workload", default="base", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--subdomains", type=int, default=0, help="override subdomains per GPU (profiling runs)")
+    ap.add_argument("--iters", type=int, default=0, help="override Adam iterations (profiling runs)")
+    ap.add_argument("--engine", default="auto", choices=["auto", "layerwise", "fused"])
+    ap.add_argument("--tile", type=int, default=0)
     return ap.parse_args()
 
 
@@ -259,6 +264,10 @@ def run_ours(args):
     from paper_2104_06718_gb300 import binding as ldb
     from paper_2104_06718_gb300 import synth
     wl = make_workload(args.workload, rank)
+    if args.subdomains:
+        wl["B"] = args.subdomains
+    if args.iters:
+        wl["T"] = args.iters
     B, T = wl["B"], wl["T"]
     net = ldb.Net(wl["specs"], margin=wl["margin"])
     net.reserve(B)
@@ -271,7 +280,7 @@ def run_ours(args):
     masks_np = synth.split_masks(net.N, B, amb, wl["depth"], block=rank)
     masks = torch.as_tensor(masks_np, device=dev)
     ones = torch.ones(B, dtype=torch.float64, device=dev)
-    opts = ldb.Options()
+    opts = ldb.Options(engine=args.engine, tile=args.tile)
 
     def step():
         lk, uk = ldb.ld_intermediate_bounds(net, l0, u0)
@@ -333,10 +342,11 @@ def run_ours(args):
         h_out.copy_(out, non_blocking=True)
         h_gW.copy_(gg["gW"], non_blocking=True)
 
-    e2e_step()
-    torch.cuda.synchronize()
     etimes = []
-    for _ in range(args.steps):
+    if not args.no_e2e:
+        e2e_step()
+        torch.cuda.synchronize()
+    for _ in range(0 if args.no_e2e else args.steps):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -346,7 +356,7 @@ def run_ours(args):
         e1.record(stream)
         e1.synchronize()
         etimes.append(e0.elapsed_time(e1))
-    te_local = sum(etimes) / 1000.0
+    te_local = sum(etimes) / 1000.0 if etimes else float("nan")
     if world > 1:
         import torch.distributed as dist
         tt = torch.tensor([t_local, te_local], dtype=torch.float64, device=dev)

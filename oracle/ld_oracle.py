@@ -313,10 +313,13 @@ def inner_minimisation(net: Net, l0, u0, lb, ub, rho) -> InnerSolution:
         take = v_00 < best
         best = np.where(take, v_00, best)
         choice[take] = 1
-        # (u,u) must win by more than TIE_REL of the magnitudes: the CROWN
-        # point of Prop. 3 puts (l,0) and (u,u) at an exact tie for every
-        # ambiguous ReLU with lambda > 0, which rounding must not decide.
-        take = v_uu < best - TIE_REL * (np.abs(v_uu) + np.abs(best))
+        # (u,u) must win by more than TIE_REL of the magnitudes that enter
+        # the comparison, (|r| + |g|) * max(|l|, u): the CROWN point of
+        # Prop. 3 puts (l,0) and (u,u) at an exact tie for every ambiguous
+        # ReLU with lambda > 0, and (r - g) * u is then a cancellation whose
+        # rounding error scales with |r| + |g|; rounding must not decide it.
+        margin = TIE_REL * (np.abs(r) + np.abs(c)) * np.maximum(np.abs(l), np.abs(u))
+        take = v_uu < best - margin
         choice[take] = 2
         xb_amb = np.select([choice == 0, choice == 1], [l, np.zeros_like(l)], u)
         xk_amb = np.where(choice == 2, u, 0.0)

@@ -68,9 +68,11 @@ __device__ __forceinline__ void clamped_bounds(const Problem& P, int b, int j, f
 //   passing  (l >= 0): x = x_hat_B = box argmin of (r - c)
 //   ambiguous: best of the vertices (l,0), (0,0), (u,u), Eq. (min-pk),
 //              first strict minimum in that order; (u,u) must win by more
-//              than kTieRel of the two magnitudes, because the CROWN point of
-//              Prop. 3 puts (l,0) and (u,u) at an exact tie for every
-//              ambiguous ReLU with lambda > 0, and rounding must not decide it
+//              than kTieRel * (|r| + |c|) * max(|l|, u), because the CROWN
+//              point of Prop. 3 puts (l,0) and (u,u) at an exact tie for
+//              every ambiguous ReLU with lambda > 0, where (r - c) * u is a
+//              cancellation whose rounding error scales with |r| + |c|, and
+//              rounding must not decide the tie
 // Box argmin of a*y over [l,u]: u if a <= 0 else l (Eq. box_bounds_sol rule).
 // code: 0 = (l,0) / lower end, 1 = (0,0), 2 = (u,u) / upper end.
 constexpr float kTieRel = 1.52587890625e-05f;  // 2^-16
@@ -91,7 +93,8 @@ __device__ __forceinline__ void relu_argmin(T r, T c, T l, T u, T& xb, T& xk, in
     code = 0;
     if (T(0) < best) { best = T(0); code = 1; }
     const T vuu = (r - c) * u;
-    if (vuu < best - T(kTieRel) * (fabs(vuu) + fabs(best))) code = 2;
+    const T margin = T(kTieRel) * (fabs(r) + fabs(c)) * fmax(-l, u);
+    if (vuu < best - margin) code = 2;
     xb = code == 0 ? l : (code == 1 ? T(0) : u);
     xk = code == 2 ? u : T(0);
   }

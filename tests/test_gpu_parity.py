@@ -113,7 +113,7 @@ def near_tie_mask(on, L0, U0, lbs, ubs, rho, sol, rel_tol=5e-5):
         cls = oracle.classify(l, u)
         best0 = np.minimum(r * l, 0.0)
         vuu = (r - g) * u
-        gap = best0 - oracle.TIE_REL * (np.abs(vuu) + np.abs(best0)) - vuu
+        gap = best0 - oracle.TIE_REL * (np.abs(r) + np.abs(g)) * np.maximum(np.abs(l), np.abs(u)) - vuu
         amb_tie = np.abs(gap) < rel_tol * mag
         pas_tie = np.abs(r - g) < rel_tol * (np.abs(r) + absg + 1e-30)
         ties.append(np.where(cls == 2, amb_tie, np.where(cls == 1, pas_tie, False)))

@@ -27,6 +27,7 @@ struct ld_net {
   size_t n_w = 0, n_b = 0;
   float* d_W = nullptr;
   float* d_b = nullptr;
+  float* d_Wx = nullptr;              // conv weights re-laid for the fused engine
   int* d_status = nullptr;
   double bn = 0.0;                    // folded output bias b_n
   // workspace, sized for ws_B subdomains
@@ -502,9 +503,47 @@ ld_status ld_net_create(const ld_layer_desc* Ld, int32_t n_layers, const float* 
     ld_net_destroy(net);
     return st;
   }
+  // Conv weights in the two layouts of the fused engine: forward
+  // [cin, kh, kw, cout] and transposed [cout, kh, kw, cin], each block
+  // starting on a 16-byte boundary.
+  std::vector<size_t> x_off(n_layers, 0);
+  size_t n_x = 0;
+  for (int k = 0; k < n_layers; ++k) {
+    if (L[k].kind != LD_LAYER_CONV) continue;
+    x_off[k] = n_x;
+    n_x += 2 * (((size_t)L[k].cout * L[k].cin * L[k].kh * L[k].kw + 3) & ~size_t(3));
+  }
+  std::vector<float> hX(n_x > 0 ? n_x : 1, 0.f);
+  for (int k = 0; k < n_layers; ++k) {
+    const LayerDev& l = L[k];
+    if (l.kind != LD_LAYER_CONV) continue;
+    const size_t nw = ((size_t)l.cout * l.cin * l.kh * l.kw + 3) & ~size_t(3);
+    const float* W = &hW[w_off[k]];
+    for (int o = 0; o < l.cout; ++o)
+      for (int c = 0; c < l.cin; ++c)
+        for (int i = 0; i < l.kh; ++i)
+          for (int j = 0; j < l.kw; ++j) {
+            const float w = W[(((size_t)o * l.cin + c) * l.kh + i) * l.kw + j];
+            hX[x_off[k] + (((size_t)c * l.kh + i) * l.kw + j) * l.cout + o] = w;
+            hX[x_off[k] + nw + (((size_t)o * l.kh + i) * l.kw + j) * l.cin + c] = w;
+          }
+  }
+  if (cudaMalloc(&net->d_Wx, sizeof(float) * hX.size()) != cudaSuccess ||
+      cudaMemcpy(net->d_Wx, hX.data(), sizeof(float) * hX.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    ld_net_destroy(net);
+    return LD_ERR_NOMEM;
+  }
   for (int k = 0; k < n_layers; ++k) {
     L[k].W = net->d_W + w_off[k];
     L[k].b = net->d_b + b_off[k];
+    L[k].Wf = nullptr;
+    L[k].Wt = nullptr;
+    if (L[k].kind == LD_LAYER_CONV) {
+      const size_t nw = ((size_t)L[k].cout * L[k].cin * L[k].kh * L[k].kw + 3) & ~size_t(3);
+      L[k].Wf = net->d_Wx + x_off[k];
+      L[k].Wt = net->d_Wx + x_off[k] + nw;
+    }
   }
   net->L = L;
   net->fused = ld::make_fused_net(L);
@@ -524,6 +563,7 @@ ld_status ld_net_destroy(ld_net* net) {
   drain_marks(net);
   free_ws(net);
   if (net->d_W) cudaFree(net->d_W);
+  if (net->d_Wx) cudaFree(net->d_Wx);
   if (net->d_b) cudaFree(net->d_b);
   if (net->d_status) cudaFree(net->d_status);
   delete net;

@@ -30,6 +30,8 @@ struct LayerDev {
   int fan_t;                     // max number of terms of one transposed-pass sum
   const float* W;                // FC [n_out, n_in]; conv [cout, cin, kh, kw]
   const float* b;                // [cout]
+  const float* Wf;               // conv only: [cin, kh, kw, cout] (forward pass, output channels innermost)
+  const float* Wt;               // conv only: [cout, kh, kw, cin] (transposed pass, input channels innermost)
 };
 
 // Inputs of one bounding call, in device memory.
@@ -226,14 +228,24 @@ struct EpiRecord {
 void count_launch(int n = 1);
 
 // ---------------------------------------------------------------- fused engine
-// The net as the fused kernel sees it (ld_fused.cu).
+// Shared-memory plan of one layer in the fused kernel (ld_fused.cu).
+struct FusedLayer {
+  int Hp, Wp;                  // zero-padded plane of the layer's input x_k: (h + 2 pad) x (w + 2 pad); FC: 1 x n_in
+  int rhl, rhh, rwl, rwh;      // zero halo of the staged rho_{k+1} plane (transposed conv)
+  int Hr, Wr;                  // padded dims of that plane; FC: 1 x n_out
+  int swf, swt;                // shared-memory offsets (floats) of the forward / transposed weight layouts
+  int fmode, tmode;            // 0 generic; 1 blocked k4 s2; 2 blocked k3 s1
+  int vec4;                    // FC: rows 16-byte aligned and n_in % 4 == 0
+};
+
+// The net as the fused kernel sees it.
 struct FusedNet {
   int n;
-  int maxX;                    // max n_k, k = 0..n-1 (x_k buffer)
+  int maxXK;                   // per-subdomain floats of the (padded) x_k buffer
   int maxB;                    // max n_k, k = 1..n-1 (x_hat_B buffers)
-  int maxR;                    // max n_k, k = 1..n-1 (staged rho_{k+1})
-  int convW_total;
-  int convW_off[kMaxLayers];   // offset of a conv layer's weights in shared memory
+  int maxR;                    // per-subdomain floats of the (padded) staged rho_{k+1}
+  int convW_total;             // floats of conv weights in shared memory (both layouts)
+  FusedLayer F[kMaxLayers];
   LayerDev L[kMaxLayers];      // L[k] = layer k+1 of the paper
 };
 

@@ -259,6 +259,7 @@ class InnerSolution:
     xB: list               # x_hat_B,k^*, k = 1..n-1 (index 0 unused)
     xA: list               # x_hat_A,k^*, k = 1..n   (index 0 unused)
     vertex: list           # chosen vertex/endpoint code per neuron, k = 1..n-1
+    q_point: np.ndarray = None  # [B] Lagrangian at the returned point (>= q by at most the tie margins)
 
 
 TIE_REL = 2.0 ** -16   # vertex tie tolerance of the (u,u) comparison (a reading; see inner_minimisation)
@@ -297,12 +298,15 @@ def inner_minimisation(net: Net, l0, u0, lb, ub, rho) -> InnerSolution:
         blk = cls == 0
         xb[blk] = box_argmin(r, l, u)[blk]
         code[blk] = np.where(r <= 0, 2, 0)[blk]
-        # passing: x = x_hat_B, minimise (r - c) * x_hat_B over [l, u]
+        # passing: x = x_hat_B, minimise (r - c) * x_hat_B over [l, u]; the
+        # lower end needs r - c > TIE_REL (|r| + |c|): at the CROWN point
+        # r = c exactly for every passing ReLU, and rounding must not decide
         pas = cls == 1
-        yp = box_argmin(r - c, l, u)
+        low = (r - c) > TIE_REL * (np.abs(r) + np.abs(c))
+        yp = np.where(low, l, u)
         xb[pas] = yp[pas]
         xk[pas] = yp[pas]
-        code[pas] = np.where((r - c) <= 0, 2, 0)[pas]
+        code[pas] = np.where(low, 0, 2)[pas]
         # ambiguous: the three vertices of Fig. (relucvx), Eq. (min-pk)
         amb = cls == 2
         v_l0 = r * l                  # vertex (l, 0)
@@ -331,10 +335,24 @@ def inner_minimisation(net: Net, l0, u0, lb, ub, rho) -> InnerSolution:
         vertex.append(code)
 
     xA = [None] + [net.L(k).forward(x[k - 1]) for k in range(1, n + 1)]
-    q = xA[n][:, 0].copy()
+    # Lagrangian of Eq. (nonprox_problem) at the returned primal point
+    q_point = xA[n][:, 0].copy()
     for k in range(1, n):
-        q += np.sum(rho[k] * (xB[k] - xA[k]), axis=1)
-    return InnerSolution(q=q, g=g, x=x, xB=xB, xA=xA, vertex=vertex)
+        q_point += np.sum(rho[k] * (xB[k] - xA[k]), axis=1)
+    # q itself from the exact per-subproblem minima (App. A, Eq.
+    # (dual_decomp_vs_dj)): the tie margins above may return a vertex whose
+    # value exceeds the minimum by at most the margin, so q is not read off
+    # the returned point.
+    q = np.sum(np.minimum(-g[0] * l0, -g[0] * u0), axis=1) + net.L(n).bias_vector()[0]
+    for k in range(1, n):
+        r, c, l, u = rho[k], g[k], lb[k], ub[k]
+        cls = classify(l, u)
+        m_blk = np.minimum(r * l, r * u)
+        m_pas = np.minimum((r - c) * l, (r - c) * u)
+        m_amb = np.minimum(np.minimum(r * l, 0.0), (r - c) * u)
+        q += np.sum(np.select([cls == 0, cls == 1], [m_blk, m_pas], m_amb), axis=1)
+        q -= rho[k] @ net.L(k).bias_vector()
+    return InnerSolution(q=q, g=g, x=x, xB=xB, xA=xA, vertex=vertex, q_point=q_point)
 
 
 def dual_value(net, l0, u0, lb, ub, rho):

@@ -86,7 +86,9 @@ __device__ __forceinline__ void relu_argmin(T r, T c, T l, T u, T& xb, T& xk, in
     xk = T(0);
     code = up ? 2 : 0;
   } else if (l >= T(0)) {
-    const bool up = (r - c) <= T(0);
+    // lower end only if r - c clears kTieRel (|r| + |c|): at the CROWN point
+    // r = c exactly for passing ReLUs and rounding must not decide
+    const bool up = (r - c) <= T(kTieRel) * (fabs(r) + fabs(c));
     xb = up ? u : l;
     xk = xb;
     code = up ? 2 : 0;

@@ -491,3 +491,21 @@ def test_planted_dropped_term_is_caught(monkeypatch):
     d = oracle.propagation_bound(net, l0, u0, L, U, rho, lam)
     assert abs(sol.q[0] - d[0]) < 1e-12
     assert abs(q_drop[0] - d[0]) > 1e-6
+
+
+@pytest.mark.parametrize("i", range(3))
+def test_dual_value_is_the_exact_minimum(i):
+    """q is read from the exact per-subproblem minima; the Lagrangian at the
+    returned (tie-margin) point is never below it, exceeds it by at most the
+    margins, and at random duals (no near-ties) equals it."""
+    specs, net, l0, u0, lb, ub = tiny_problem(i)
+    L, U = lists(net, lb, ub)
+    rho, _ = oracle.crown_init(net, L, U)
+    sol = oracle.inner_minimisation(net, l0, u0, L, U, rho)
+    slack = sum(np.sum(oracle.TIE_REL * (np.abs(rho[k]) + np.abs(sol.g[k]))
+                       * np.maximum(np.abs(L[k]), np.abs(U[k]))) for k in range(1, net.n))
+    assert sol.q_point[0] >= sol.q[0] - 1e-12
+    assert sol.q_point[0] - sol.q[0] <= slack + 1e-12
+    rr = [None] + [r.astype(np.float64) for r in synth.random_duals([L[1].shape[1], L[2].shape[1]], 1, seed=3)]
+    s2 = oracle.inner_minimisation(net, l0, u0, L, U, rr)
+    assert abs(s2.q_point[0] - s2.q[0]) < 1e-12

@@ -258,8 +258,9 @@ struct FusedIter {
 };
 
 FusedNet make_fused_net(const std::vector<LayerDev>& Ls);
-size_t fused_smem_bytes(const FusedNet& f, int S);
-cudaError_t launch_fused(const FusedNet& f, int S, const Problem& P, float* rho, float* m, float* v,
+// resident: rho, m, v of a CTA's subdomains kept in shared memory for the run.
+size_t fused_smem_bytes(const FusedNet& f, int S, int resident, int N);
+cudaError_t launch_fused(const FusedNet& f, int S, int resident, const Problem& P, float* rho, float* m, float* v,
                          const FusedIter& it, cudaStream_t s);
 
 // ---------------------------------------------------------------- launchers

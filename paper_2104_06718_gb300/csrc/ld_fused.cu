@@ -10,8 +10,9 @@
 //                    x_hat_B,k+1 - x_hat_A,k+1 and the Adam step on rho_{k+1}
 // x_k (in a zero-padded plane), x_hat_B and the staged duals live in shared
 // memory; both layouts of the conv weights are loaded into shared memory
-// once; rho, m, v stream through L2/HBM once per iteration; FC weights are
-// read from L2 with batched 16-byte loads.
+// once; rho, m, v stay in shared memory for the whole run when they fit
+// (loaded once, written back once), else they stream through L2/HBM every
+// iteration; FC weights are read from L2 with batched 16-byte loads.
 //
 // The 4x4/stride-2 and 3x3/stride-1 convs (all the CIFAR nets) take blocked
 // paths: each thread computes 2 positions x 4 channels, the kernel taps are
@@ -31,9 +32,10 @@ template <int S>
 struct Ctx {
   const FusedNet& net;
   const Problem& P;
-  float* rho;
-  float* m;
+  float* rho;      // duals of subdomain b0 + s at rho + s * ss (shared memory when resident)
+  float* m;        // Adam moments, same layout
   float* v;
+  size_t ss;       // per-subdomain stride of rho / m / v
   float* sW;       // conv weights, both layouts
   float* XK;       // [S][maxXK]
   float* XB0;      // [S][maxB]
@@ -67,7 +69,7 @@ __device__ __forceinline__ void argmin_epi(const Ctx<S>& c, int k, const LayerDe
   const int j = c.net.L[k - 1].r_out_off + i;
   float l, u;
   clamped_bounds(c.P, b, j, l, u);
-  const float r = c.rho[(size_t)b * c.P.N + j];
+  const float r = c.rho[(size_t)s * c.ss + j];
   float xb, xv;
   int code;
   relu_argmin<float>(r, g, l, u, xb, xv, code);
@@ -83,7 +85,7 @@ __device__ __forceinline__ void adam_epi(const Ctx<S>& c, const LayerDev& L, con
   if (c.P.empty[b]) return;
   const int plane = L.kind == LD_LAYER_FC ? 1 : L.ho * L.wo;
   const float xa = acc + __ldg(L.b + jj / plane);
-  const size_t j = (size_t)b * c.P.N + L.r_out_off + jj;
+  const size_t j = (size_t)s * c.ss + L.r_out_off + jj;
   const float sg = XBprev[s * c.net.maxB + jj] - xa;
   const float mm = it.beta1 * c.m[j] + (1.f - it.beta1) * sg;
   const float vv = it.beta2 * c.v[j] + (1.f - it.beta2) * sg * sg;
@@ -109,7 +111,7 @@ __device__ void stage(const Ctx<S>& c, const LayerDev& L, const FusedLayer& F) {
         const int y = r / F.Wr - F.rhl, x = r % F.Wr - F.rwl;
         o = (y >= 0 && y < L.ho && x >= 0 && x < L.wo) ? (ch * L.ho + y) * L.wo + x : -1;
       }
-      if (o >= 0) v = c.rho[(size_t)(c.b0 + s) * c.P.N + L.r_out_off + o];
+      if (o >= 0) v = c.rho[(size_t)s * c.ss + L.r_out_off + o];
     }
     c.R[s * c.net.maxR + q] = v;
   }
@@ -430,7 +432,10 @@ __device__ void conv_t_generic(const Ctx<S>& c, const LayerDev& L, const FusedLa
 
 // ------------------------------------------------------------------ kernel
 
-template <int S>
+// RES: rho, m, v of the CTA's subdomains stay in shared memory for the whole
+// run (loaded once, written back once); otherwise they are read and written
+// in global memory every iteration.
+template <int S, bool RES>
 __global__ void __launch_bounds__(FT) fused_kernel(const __grid_constant__ FusedNet net,
                                                    const __grid_constant__ Problem P, float* rho, float* m, float* v,
                                                    FusedIter it) {
@@ -440,6 +445,21 @@ __global__ void __launch_bounds__(FT) fused_kernel(const __grid_constant__ Fused
   float* XB0 = XK + S * net.maxXK;
   float* XB1 = XB0 + S * net.maxB;
   float* R = XB1 + S * net.maxB;
+  const int b0 = (int)blockIdx.x * S;
+  const int Np = (P.N + 3) & ~3;
+  float* srho = R + S * net.maxR;
+  float* sm = srho + S * Np;
+  float* sv = sm + S * Np;
+  if (RES) {
+    for (int e = threadIdx.x; e < S * Np; e += FT) {
+      const int s = e / Np, j = e % Np;
+      const bool ok = b0 + s < P.B && j < P.N;
+      const size_t g = (size_t)(b0 + s) * P.N + j;
+      srho[e] = ok ? rho[g] : 0.f;
+      sm[e] = ok ? m[g] : 0.f;
+      sv[e] = ok ? v[g] : 0.f;
+    }
+  }
   for (int k = 0; k < net.n; ++k) {
     const LayerDev& L = net.L[k];
     if (L.kind == LD_LAYER_CONV) {
@@ -450,7 +470,12 @@ __global__ void __launch_bounds__(FT) fused_kernel(const __grid_constant__ Fused
       }
     }
   }
-  Ctx<S> c{net, P, rho, m, v, sW, XK, XB0, XB1, R, (int)blockIdx.x * S};
+  Ctx<S> c{net, P,
+           RES ? srho : rho + (size_t)b0 * P.N,
+           RES ? sm : m + (size_t)b0 * P.N,
+           RES ? sv : v + (size_t)b0 * P.N,
+           RES ? (size_t)Np : (size_t)P.N,
+           sW, XK, XB0, XB1, R, b0};
   __syncthreads();
   for (int t = 0; t < it.T; ++t) {
     const int tt = it.t_offset + t;
@@ -504,22 +529,35 @@ __global__ void __launch_bounds__(FT) fused_kernel(const __grid_constant__ Fused
       cur0 = !cur0;
     }
   }
+  if (RES) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < S * Np; e += FT) {
+      const int s = e / Np, j = e % Np;
+      if (b0 + s < P.B && j < P.N) {
+        const size_t g = (size_t)(b0 + s) * P.N + j;
+        rho[g] = srho[e];
+        m[g] = sm[e];
+        v[g] = sv[e];
+      }
+    }
+  }
 }
 
-template <int S>
-size_t smem_bytes(const FusedNet& f) {
-  return sizeof(float) * ((size_t)f.convW_total + (size_t)S * (f.maxXK + 2 * f.maxB + f.maxR));
+size_t smem_bytes(const FusedNet& f, int S, bool res, int N) {
+  const size_t np = (size_t)((N + 3) & ~3);
+  return sizeof(float) * ((size_t)f.convW_total + (size_t)S * (f.maxXK + 2 * f.maxB + f.maxR) +
+                          (res ? (size_t)S * 3 * np : 0));
 }
 
-template <int S>
+template <int S, bool RES>
 cudaError_t launch_s(const FusedNet& f, const Problem& P, float* rho, float* m, float* v, const FusedIter& it,
                      cudaStream_t s) {
-  const size_t sm = smem_bytes<S>(f);
-  cudaError_t e = cudaFuncSetAttribute(fused_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const size_t sm = smem_bytes(f, S, RES, P.N);
+  cudaError_t e = cudaFuncSetAttribute(fused_kernel<S, RES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   const int grid = (P.B + S - 1) / S;
   count_launch();
-  fused_kernel<S><<<grid, FT, sm, s>>>(f, P, rho, m, v, it);
+  fused_kernel<S, RES><<<grid, FT, sm, s>>>(f, P, rho, m, v, it);
   return cudaGetLastError();
 }
 
@@ -585,22 +623,23 @@ FusedNet make_fused_net(const std::vector<LayerDev>& Ls) {
   return f;
 }
 
-size_t fused_smem_bytes(const FusedNet& f, int S) {
-  switch (S) {
-    case 1: return smem_bytes<1>(f);
-    case 2: return smem_bytes<2>(f);
-    case 4: return smem_bytes<4>(f);
-  }
-  return 0;
-}
+size_t fused_smem_bytes(const FusedNet& f, int S, int resident, int N) { return smem_bytes(f, S, resident != 0, N); }
 
-cudaError_t launch_fused(const FusedNet& f, int S, const Problem& P, float* rho, float* m, float* v,
+cudaError_t launch_fused(const FusedNet& f, int S, int resident, const Problem& P, float* rho, float* m, float* v,
                          const FusedIter& it, cudaStream_t s) {
   if (P.B == 0 || it.T == 0) return cudaSuccess;
-  switch (S) {
-    case 1: return launch_s<1>(f, P, rho, m, v, it, s);
-    case 2: return launch_s<2>(f, P, rho, m, v, it, s);
-    case 4: return launch_s<4>(f, P, rho, m, v, it, s);
+  if (resident) {
+    switch (S) {
+      case 1: return launch_s<1, true>(f, P, rho, m, v, it, s);
+      case 2: return launch_s<2, true>(f, P, rho, m, v, it, s);
+      case 4: return launch_s<4, true>(f, P, rho, m, v, it, s);
+    }
+  } else {
+    switch (S) {
+      case 1: return launch_s<1, false>(f, P, rho, m, v, it, s);
+      case 2: return launch_s<2, false>(f, P, rho, m, v, it, s);
+      case 4: return launch_s<4, false>(f, P, rho, m, v, it, s);
+    }
   }
   return cudaErrorInvalidValue;
 }

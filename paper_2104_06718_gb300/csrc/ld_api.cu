@@ -259,11 +259,13 @@ int resident_fits(const ld_net* net, int S) {
 }
 
 // T Adam iterations with the given engine (tile = subdomains per CTA).
+// crown: the fused engine computes the CROWN start itself (with the same
+// transposed pass as its iterations) before the first iteration.
 ld_status run_iterations(ld_net* net, const Problem& P, const ld_opts& o, int n_iters, int engine, int tile,
-                         cudaStream_t s) {
+                         cudaStream_t s, int crown = 0) {
   const int T_sched = o.t_total > 0 ? o.t_total : o.t_offset + n_iters;
   if (engine == LD_ENGINE_FUSED) {
-    ld::FusedIter it{n_iters, o.t_offset, T_sched, o.alpha0, o.alpha_end, o.beta1, o.beta2, o.eps};
+    ld::FusedIter it{n_iters, o.t_offset, T_sched, o.alpha0, o.alpha_end, o.beta1, o.beta2, o.eps, crown};
     return cuda_status(
         ld::launch_fused(net->fused, tile, resident_fits(net, tile), P, net->rho, net->m, net->v, it, s));
   }
@@ -639,6 +641,10 @@ ld_status ld_bound(ld_net* net, const float* lb0, const float* ub0, const float*
   const Problem P = make_problem(net, lb0, ub0, lbk, ubk, n_props, prop, masks, B);
   const size_t BN = (size_t)B * net->N;
   const std::pair<int, int> eng = n_iters > 0 ? choose_engine(net, P, o, s) : std::make_pair(1, 0);
+  // The CROWN start must come from the same transposed-pass arithmetic as the
+  // iterations (its exact ties would otherwise be broken by rounding): the
+  // fused engine computes it in-kernel, the layerwise engine with its kernels.
+  const int crown_in_kernel = (o.init == LD_INIT_CROWN && eng.first == LD_ENGINE_FUSED) ? 1 : 0;
   {
     PhaseMark pm(net, LD_PHASE_INIT, s);
     ld::launch_empty_flags(P, net->empty, net->d_status, s);
@@ -646,7 +652,7 @@ ld_status ld_bound(ld_net* net, const float* lb0, const float* ub0, const float*
       cudaMemcpyAsync(net->rho, rho_in, sizeof(float) * BN, cudaMemcpyDeviceToDevice, s);
     else if (o.init == LD_INIT_ZERO)
       cudaMemsetAsync(net->rho, 0, sizeof(float) * BN, s);
-    else
+    else if (!crown_in_kernel)
       crown_sweep(net, P, s);
     if (adam_mv && o.t_offset > 0) {
       cudaMemcpyAsync(net->m, adam_mv, sizeof(float) * BN, cudaMemcpyDeviceToDevice, s);
@@ -658,7 +664,7 @@ ld_status ld_bound(ld_net* net, const float* lb0, const float* ub0, const float*
   }
   if (n_iters > 0) {
     PhaseMark pm(net, LD_PHASE_ITER, s);
-    if ((st = run_iterations(net, P, o, n_iters, eng.first, eng.second, s)) != LD_OK) return st;
+    if ((st = run_iterations(net, P, o, n_iters, eng.first, eng.second, s, crown_in_kernel)) != LD_OK) return st;
   }
   {
     PhaseMark pm(net, LD_PHASE_FINAL, s);

@@ -255,6 +255,7 @@ struct FusedNet {
 struct FusedIter {
   int T, t_offset, T_sched;
   float alpha0, alpha_end, beta1, beta2, eps;
+  int crown;                   // 1: compute the CROWN initial duals in the kernel first
 };
 
 FusedNet make_fused_net(const std::vector<LayerDev>& Ls);

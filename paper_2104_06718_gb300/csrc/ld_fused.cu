@@ -42,6 +42,7 @@ struct Ctx {
   float* XB1;      // [S][maxB]
   float* R;        // [S][maxR]
   int b0;          // first subdomain of this CTA
+  bool crown;      // transposed-pass epilogue computes the CROWN duals instead of the argmin
 };
 
 template <int S>
@@ -60,6 +61,27 @@ template <int S>
 __device__ __forceinline__ void argmin_epi(const Ctx<S>& c, int k, const LayerDev& L, const FusedLayer& F,
                                            float* XBcur, int s, int i, int xi, float g) {
   const int b = c.b0 + s;
+  if (c.crown) {
+    // dual initialisation (Prop. 3, Eq. salman-assignment): rho_k = a_bar [g]_+ + a_low [g]_-,
+    // computed by the same transposed pass the iterations use, so that the
+    // exact ties it creates (rho_k = g_k for passing ReLUs) survive rounding
+    const int j = c.net.L[k - 1].r_out_off + i;
+    float l, u;
+    clamped_bounds(c.P, b, j, l, u);
+    float a_up, a_lo;
+    if (u <= 0.f) {
+      a_up = 0.f;
+      a_lo = 0.f;
+    } else if (l >= 0.f) {
+      a_up = 1.f;
+      a_lo = 1.f;
+    } else {
+      a_up = u / (u - l);
+      a_lo = (u >= -l) ? 1.f : 0.f;
+    }
+    c.rho[(size_t)s * c.ss + j] = a_up * fmaxf(g, 0.f) + a_lo * fminf(g, 0.f);
+    return;
+  }
   float* xk = c.XK + s * c.net.maxXK;
   if (k == 0) {
     const int p = prop_of(c.P, b);
@@ -430,6 +452,26 @@ __device__ void conv_t_generic(const Ctx<S>& c, const LayerDev& L, const FusedLa
   }
 }
 
+// Transposed pass of layer L = layer k+1 into layer k, with the epilogue.
+template <int S>
+__device__ void transposed_pass(const Ctx<S>& c, const LayerDev& L, const FusedLayer& F, int k, float* XBcur) {
+  if (L.kind == LD_LAYER_FC) {
+    transposed_fc(c, L, F, k, XBcur);
+  } else if (F.tmode == 1) {
+    if (L.cin == 3)
+      conv_t_blocked<4, 4, 2, 3>(c, L, F, k, XBcur);
+    else
+      conv_t_blocked<4, 4, 2, 4>(c, L, F, k, XBcur);
+  } else if (F.tmode == 2) {
+    if (L.cin == 3)
+      conv_t_blocked<3, 3, 1, 3>(c, L, F, k, XBcur);
+    else
+      conv_t_blocked<3, 3, 1, 4>(c, L, F, k, XBcur);
+  } else {
+    conv_t_generic(c, L, F, k, XBcur);
+  }
+}
+
 // ------------------------------------------------------------------ kernel
 
 // RES: rho, m, v of the CTA's subdomains stay in shared memory for the whole
@@ -475,8 +517,27 @@ __global__ void __launch_bounds__(FT) fused_kernel(const __grid_constant__ Fused
            RES ? sm : m + (size_t)b0 * P.N,
            RES ? sv : v + (size_t)b0 * P.N,
            RES ? (size_t)Np : (size_t)P.N,
-           sW, XK, XB0, XB1, R, b0};
+           sW, XK, XB0, XB1, R, b0, false};
   __syncthreads();
+  if (it.crown) {
+    c.crown = true;
+    for (int k = net.n - 1; k >= 1; --k) {
+      const LayerDev& L = net.L[k];
+      const FusedLayer& F = net.F[k];
+      if (k == net.n - 1) {
+        for (int e = threadIdx.x; e < S * L.n_in; e += FT) {
+          const int s = e / L.n_in, i = e % L.n_in;
+          if (active(c, s)) argmin_epi(c, k, L, F, XB0, s, i, i, -__ldg(L.W + i));
+        }
+      } else {
+        stage(c, L, F);
+        __syncthreads();
+        transposed_pass(c, L, F, k, XB0);
+      }
+      __syncthreads();
+    }
+    c.crown = false;
+  }
   for (int t = 0; t < it.T; ++t) {
     const int tt = it.t_offset + t;
     AdamStep st;
@@ -500,21 +561,7 @@ __global__ void __launch_bounds__(FT) fused_kernel(const __grid_constant__ Fused
       } else {
         stage(c, L, F);
         __syncthreads();
-        if (L.kind == LD_LAYER_FC) {
-          transposed_fc(c, L, F, k, XBcur);
-        } else if (F.tmode == 1) {
-          if (L.cin == 3)
-            conv_t_blocked<4, 4, 2, 3>(c, L, F, k, XBcur);
-          else
-            conv_t_blocked<4, 4, 2, 4>(c, L, F, k, XBcur);
-        } else if (F.tmode == 2) {
-          if (L.cin == 3)
-            conv_t_blocked<3, 3, 1, 3>(c, L, F, k, XBcur);
-          else
-            conv_t_blocked<3, 3, 1, 4>(c, L, F, k, XBcur);
-        } else {
-          conv_t_generic(c, L, F, k, XBcur);
-        }
+        transposed_pass(c, L, F, k, XBcur);
         __syncthreads();
         if (L.kind == LD_LAYER_FC)
           forward_fc(c, L, F, XBprev, it, st);

@@ -228,6 +228,30 @@ enum { LD_PHASE_ITER = 0, LD_PHASE_FINAL = 1, LD_PHASE_INIT = 2, LD_PHASE_IBP = 
 ld_status ld_net_profile(ld_net* net, int32_t enable);
 ld_status ld_net_profile_read(ld_net* net, int32_t phase, double* total_ms, int64_t* count, int32_t reset);
 
+/* The sound FP64 final bound q(rho) at a given rho, computed without any
+ * device allocation.  The paper has no counterpart: this is a service for
+ * callers that cannot call cudaMalloc at the point where they need a bound,
+ * for instance code that runs where allocation is not permitted or that must
+ * keep its device memory fixed after start-up.  It computes what ld_bound
+ * returns with n_iters = 0 and init = LD_INIT_GIVEN (same kernels, same
+ * results), but its scratch lives in a 4 MiB array compiled into the library
+ * (held on every GPU that loads the library until the process exits) instead
+ * of the handle's workspace.
+ *   Arguments as ld_bound; rho [device] [B, N] float; out [device] [B] double.
+ *   Limit: B * (24 * S + 1) bytes of scratch (S = number of partial-sum slots
+ *   of the net, a few dozen for the CIFAR nets: about 4,600 Base or 2,800
+ *   Wide subdomains) must fit in 4 MiB; larger B returns LD_ERR_UNSUPPORTED
+ *   before anything is launched.
+ *   The first call on each device looks up the array's device address (with
+ *   that device current); make that first call before any stream capture.
+ *   All calls share the array: calls that overlap on the GPU race, so order
+ *   them (for instance on one stream).  The handle itself must have been
+ *   created beforehand (ld_net_create allocates). */
+ld_status ld_final_bound_noalloc(ld_net* net, const float* lb0, const float* ub0, const float* lbk,
+                                 const float* ubk, int32_t n_props, const int32_t* prop_of_subdomain,
+                                 const int8_t* split_masks, int32_t B, const float* rho, double* out,
+                                 void* stream);
+
 /* Number of kernels this library has launched in this process (all
  * handles, all calls), for accounting of device work. */
 ld_status ld_launch_count(int64_t* count);

@@ -27,7 +27,7 @@ LD_ENGINE_AUTO, LD_ENGINE_LAYERWISE, LD_ENGINE_FUSED = 0, 1, 2
 EXPORTED = [
     "ld_opts_default", "ld_status_str", "ld_net_create", "ld_net_destroy", "ld_net_sizes", "ld_net_reserve",
     "ld_net_sync_status", "ld_intermediate_bounds", "ld_bound", "ld_dual_supergradient", "ld_bound_backward",
-    "ld_net_profile", "ld_net_profile_read", "ld_launch_count", "ld_net_tuned",
+    "ld_net_profile", "ld_net_profile_read", "ld_launch_count", "ld_net_tuned", "ld_final_bound_noalloc",
 ]
 PHASES = {"iter": 0, "final": 1, "init": 2, "ibp": 3, "backward": 4}
 
@@ -80,6 +80,7 @@ def load_library(path: str = LIB_PATH):
     lib.ld_net_profile_read.argtypes = [vp, i32, C.POINTER(C.c_double), C.POINTER(i64), i32]
     lib.ld_launch_count.argtypes = [C.POINTER(i64)]
     lib.ld_net_tuned.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32)]
+    lib.ld_final_bound_noalloc.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, i32, vp, vp, vp]
     for name in EXPORTED:
         if name not in ("ld_opts_default", "ld_status_str"):
             getattr(lib, name).restype = C.c_int
@@ -314,4 +315,20 @@ def ld_bound_backward(net: Net, lb0, ub0, lbk, ubk, rho, grad_out=None, prop=Non
                                       _ptr(masks), B, _ptr(rho), _ptr(go), _ptr(out["gW"]), _ptr(out["gb"]),
                                       _ptr(out["glb0"]), _ptr(out["gub0"]), _ptr(out["glbk"]), _ptr(out["gubk"]),
                                       _stream()), "ld_bound_backward")
+    return out
+
+
+def ld_final_bound_noalloc(net: Net, lb0, ub0, lbk, ubk, rho, prop=None, masks=None, out=None):
+    """Sound FP64 bound q(rho) [B] at a given rho without any device allocation
+    inside the library (its scratch is a fixed array compiled into libld).
+    For callers that cannot allocate device memory when they need a bound.
+    Pass `out` (a float64 CUDA tensor [B]) to keep this call allocation-free
+    on the Python side too."""
+    rho = _dev(rho, torch.float32)
+    lb0, ub0, lbk, ubk, prop, masks, B = _problem(lb0, ub0, lbk, ubk, prop, masks, rho.shape[0])
+    if out is None:
+        out = torch.empty(B, dtype=torch.float64, device="cuda")
+    _check(net._lib.ld_final_bound_noalloc(net.handle, _ptr(lb0), _ptr(ub0), _ptr(lbk), _ptr(ubk), lbk.shape[0],
+                                           _ptr(prop), _ptr(masks), B, _ptr(rho), _ptr(out), _stream()),
+           "ld_final_bound_noalloc")
     return out

@@ -53,6 +53,10 @@ struct ld_net {
   int64_t prof_n[LD_N_PHASES] = {0, 0, 0, 0, 0};
 };
 
+namespace ld {
+NetView net_view(const ld_net* net) { return NetView{net->n, net->n0, net->N, net->bn, &net->L, net->d_status}; }
+}  // namespace ld
+
 namespace {
 
 // RAII phase marker: records a start event now and a stop event when it goes

@@ -229,6 +229,16 @@ struct EpiRecord {
 // kernel it launches); read through ld_launch_count.
 void count_launch(int n = 1);
 
+// Read-only view of a net handle for entry points outside ld_api.cu.
+struct NetView {
+  int n;
+  int64_t n0, N;
+  double bn;                         // folded output bias
+  const std::vector<LayerDev>* L;    // (*L)[k-1] = layer k
+  int* d_status;
+};
+NetView net_view(const ld_net* net);
+
 // ---------------------------------------------------------------- fused engine
 // Shared-memory plan of one layer in the fused kernel (ld_fused.cu).
 struct FusedLayer {

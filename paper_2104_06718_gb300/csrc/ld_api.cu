@@ -254,13 +254,7 @@ void sweep(ld_net* net, const Problem& P, int mode, const ld_opts& o, ld::AdamSt
   }
 }
 
-bool tile_fits(const ld_net* net, int S) {
-  return ld::fused_smem_bytes(net->fused, S, 0, (int)net->N) <= net->smem_optin;
-}
-// rho, m, v stay in shared memory whenever they fit beside the working set.
-int resident_fits(const ld_net* net, int S) {
-  return ld::fused_smem_bytes(net->fused, S, 1, (int)net->N) <= net->smem_optin ? 1 : 0;
-}
+bool tile_fits(const ld_net* net, int S) { return ld::fused_smem_bytes(net->fused, S) <= net->smem_optin; }
 
 // T Adam iterations with the given engine (tile = subdomains per CTA).
 // crown: the fused engine computes the CROWN start itself (with the same
@@ -270,8 +264,7 @@ ld_status run_iterations(ld_net* net, const Problem& P, const ld_opts& o, int n_
   const int T_sched = o.t_total > 0 ? o.t_total : o.t_offset + n_iters;
   if (engine == LD_ENGINE_FUSED) {
     ld::FusedIter it{n_iters, o.t_offset, T_sched, o.alpha0, o.alpha_end, o.beta1, o.beta2, o.eps, crown};
-    return cuda_status(
-        ld::launch_fused(net->fused, tile, resident_fits(net, tile), P, net->rho, net->m, net->v, it, s));
+    return cuda_status(ld::launch_fused(net->fused, tile, P, net->rho, net->m, net->v, it, s));
   }
   for (int t = 0; t < n_iters; ++t) {
     const int tt = o.t_offset + t;

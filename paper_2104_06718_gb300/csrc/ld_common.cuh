@@ -243,8 +243,11 @@ NetView net_view(const ld_net* net);
 // Shared-memory plan of one layer in the fused kernel (ld_fused.cu).
 struct FusedLayer {
   int Hp, Wp;                  // zero-padded plane of the layer's input x_k: (h + 2 pad) x (w + 2 pad); FC: 1 x n_in
-  int rhl, rhh, rwl, rwh;      // zero halo of the staged rho_{k+1} plane (transposed conv)
+  int poly;                    // input plane stored by stride-2 phase: [c][Y&1][X&1][Hp/2][Wp/2]
+  int rhl, rhh, rwl, rwh;      // zero halo of the layer's output (rho) plane read by its transposed conv
   int Hr, Wr;                  // padded dims of that plane; FC: 1 x n_out
+  int xoff;                    // offset of the input plane in the per-subdomain x area
+  int roff;                    // offset of the output rho plane in the per-subdomain rho area (hidden layers)
   int swf, swt;                // shared-memory offsets (floats) of the forward / transposed weight layouts
   int fmode, tmode;            // 0 generic; 1 blocked k4 s2; 2 blocked k3 s1
   int vec4;                    // FC: rows 16-byte aligned and n_in % 4 == 0
@@ -253,9 +256,9 @@ struct FusedLayer {
 // The net as the fused kernel sees it.
 struct FusedNet {
   int n;
-  int maxXK;                   // per-subdomain floats of the (padded) x_k buffer
-  int maxB;                    // max n_k, k = 1..n-1 (x_hat_B buffers)
-  int maxR;                    // per-subdomain floats of the (padded) staged rho_{k+1}
+  int xp_total;                // per-subdomain floats of all padded input planes
+  int rho_total;               // per-subdomain floats of all padded rho planes
+  int nb;                      // per-subdomain floats of x_hat_B (N rounded up to 4)
   int convW_total;             // floats of conv weights in shared memory (both layouts)
   FusedLayer F[kMaxLayers];
   LayerDev L[kMaxLayers];      // L[k] = layer k+1 of the paper
@@ -269,9 +272,9 @@ struct FusedIter {
 };
 
 FusedNet make_fused_net(const std::vector<LayerDev>& Ls);
-// resident: rho, m, v of a CTA's subdomains kept in shared memory for the run.
-size_t fused_smem_bytes(const FusedNet& f, int S, int resident, int N);
-cudaError_t launch_fused(const FusedNet& f, int S, int resident, const Problem& P, float* rho, float* m, float* v,
+// Shared memory of a fused CTA owning S subdomains (all their state resident).
+size_t fused_smem_bytes(const FusedNet& f, int S);
+cudaError_t launch_fused(const FusedNet& f, int S, const Problem& P, float* rho, float* m, float* v,
                          const FusedIter& it, cudaStream_t s);
 
 // ---------------------------------------------------------------- launchers

@@ -8,4 +8,4 @@ package loads nothing; the library is loaded on first use and its absence
 is an error (there is no CPU fallback).
 """
 
-__all__ = ["binding", "synth", "build"]
+__all__ = ["binding", "autograd", "synth", "build"]

@@ -163,7 +163,11 @@ __device__ void transposed_fc(const Ctx<S>& c, const LayerDev& L, const FusedLay
       float4 acc[S];
 #pragma unroll
       for (int s = 0; s < S; ++s) acc[s] = make_float4(0.f, 0.f, 0.f, 0.f);
-      for (int o0 = 0; o0 < L.n_out; o0 += U) {
+      // every CTA streams the same weight rows: start at a CTA-dependent batch
+      // so that concurrent CTAs spread over the L2 slices
+      const int nbat = (L.n_out + U - 1) / U;
+      for (int bi = 0; bi < nbat; ++bi) {
+        const int o0 = U * ((bi + (int)blockIdx.x) % nbat);
         float4 wv[U];
 #pragma unroll
         for (int u = 0; u < U; ++u)
@@ -218,7 +222,10 @@ __device__ void forward_fc(const Ctx<S>& c, const LayerDev& L, const FusedLayer&
                            const AdamStep& st) {
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nwarp = FT / 32;
   const float* __restrict__ W = L.W;
-  for (int j0 = 2 * warp; j0 < L.n_out; j0 += 2 * nwarp) {
+  const int npair = (L.n_out + 1) / 2;
+  for (int jp = warp; jp < npair; jp += nwarp) {
+    // CTA-dependent rotation of the rows (as in transposed_fc)
+    const int j0 = 2 * ((jp + (int)blockIdx.x) % npair);
     const bool two = j0 + 1 < L.n_out;
     float acc[2][S];
 #pragma unroll
@@ -280,12 +287,12 @@ __device__ void forward_fc(const Ctx<S>& c, const LayerDev& L, const FusedLayer&
 
 // ------------------------------------------------------------------ blocked convs
 
-// Forward conv, blocked: item = (s, y, x0, group of 4 output channels); the
+// Forward conv, blocked: item = (s, y, x0, group of GF output channels); the
 // thread computes positions x0 and x0 + wo/2.
-template <int KH, int KW, int ST, int S>
+template <int KH, int KW, int ST, int GF, int S>
 __device__ void conv_fwd_blocked(const Ctx<S>& c, const LayerDev& L, const FusedLayer& F, const FusedIter& it,
                                  const AdamStep& st) {
-  const int half = L.wo / 2, nog = L.cout / 4;
+  const int half = L.wo / 2, nog = L.cout / GF;
   const int items = S * L.ho * half * nog;
   const float* wf = c.sW + F.swf;
   const int hq = F.Hp >> 1, wq = F.Wp >> 1;
@@ -297,20 +304,31 @@ __device__ void conv_fwd_blocked(const Ctx<S>& c, const LayerDev& L, const Fused
     r /= L.ho;
     const int og = r % nog;
     const int s = r / nog;
-    float acc[2][4];
+    float acc[2][GF];
 #pragma unroll
     for (int p = 0; p < 2; ++p)
 #pragma unroll
-      for (int g = 0; g < 4; ++g) acc[p][g] = 0.f;
+      for (int g = 0; g < GF; ++g) acc[p][g] = 0.f;
     const float* xs = c.xp(s) + F.xoff;
-    const float* wg = wf + og * 4;
+    const float* wg = wf + og * GF;
     for (int ch = 0; ch < L.cin; ++ch) {
       const float* wc = wg + ch * KH * KW * L.cout;
 #pragma unroll
       for (int i = 0; i < KH; ++i)
 #pragma unroll
         for (int j = 0; j < KW; ++j) {
-          const float4 w = *reinterpret_cast<const float4*>(wc + (i * KW + j) * L.cout);
+          float w[GF];
+          if (GF == 4) {
+            const float4 w4 = *reinterpret_cast<const float4*>(wc + (i * KW + j) * L.cout);
+            w[0] = w4.x;
+            w[1 % GF] = w4.y;
+            w[2 % GF] = w4.z;
+            w[3 % GF] = w4.w;
+          } else {
+            const float2 w2 = *reinterpret_cast<const float2*>(wc + (i * KW + j) * L.cout);
+            w[0] = w2.x;
+            w[1 % GF] = w2.y;
+          }
           int a0i;
           if (ST == 2) {  // stride-phase layout: phase (i&1, j&1), sub-position (y + i/2, x + j/2)
             a0i = (((ch * 2 + (i & 1)) * 2 + (j & 1)) * hq + y + (i >> 1)) * wq + x0 + (j >> 1);
@@ -318,22 +336,19 @@ __device__ void conv_fwd_blocked(const Ctx<S>& c, const LayerDev& L, const Fused
             a0i = (ch * F.Hp + y * ST + i) * F.Wp + x0 * ST + j;
           }
           const float a0 = xs[a0i], a1 = xs[a0i + (ST == 2 ? half : half * ST)];
-          acc[0][0] = fmaf(w.x, a0, acc[0][0]);
-          acc[0][1] = fmaf(w.y, a0, acc[0][1]);
-          acc[0][2] = fmaf(w.z, a0, acc[0][2]);
-          acc[0][3] = fmaf(w.w, a0, acc[0][3]);
-          acc[1][0] = fmaf(w.x, a1, acc[1][0]);
-          acc[1][1] = fmaf(w.y, a1, acc[1][1]);
-          acc[1][2] = fmaf(w.z, a1, acc[1][2]);
-          acc[1][3] = fmaf(w.w, a1, acc[1][3]);
+#pragma unroll
+          for (int g = 0; g < GF; ++g) {
+            acc[0][g] = fmaf(w[g], a0, acc[0][g]);
+            acc[1][g] = fmaf(w[g], a1, acc[1][g]);
+          }
         }
     }
     if (!active(c, s)) continue;
 #pragma unroll
-    for (int g = 0; g < 4; ++g)
+    for (int g = 0; g < GF; ++g)
 #pragma unroll
       for (int p = 0; p < 2; ++p) {
-        const int o = og * 4 + g, x = x0 + p * half;
+        const int o = og * GF + g, x = x0 + p * half;
         epi_f(c, L, s, (o * L.ho + y) * L.wo + x, rho_conv(F, o, y, x), acc[p][g], it, st);
       }
   }
@@ -576,10 +591,14 @@ __global__ void __launch_bounds__(FT) fused_kernel(const __grid_constant__ Fused
       __syncthreads();
       if (L.kind == LD_LAYER_FC)
         forward_fc(c, L, F, it, st);
-      else if (F.fmode == 1)
-        conv_fwd_blocked<4, 4, 2>(c, L, F, it, st);
+      else if (F.fmode == 1 && S * L.ho * (L.wo / 2) * (L.cout / 4) >= FT)
+        conv_fwd_blocked<4, 4, 2, 4>(c, L, F, it, st);
+      else if (F.fmode == 1)  // too few 4-channel items to fill the CTA
+        conv_fwd_blocked<4, 4, 2, 2>(c, L, F, it, st);
+      else if (F.fmode == 2 && S * L.ho * (L.wo / 2) * (L.cout / 4) >= FT)
+        conv_fwd_blocked<3, 3, 1, 4>(c, L, F, it, st);
       else if (F.fmode == 2)
-        conv_fwd_blocked<3, 3, 1>(c, L, F, it, st);
+        conv_fwd_blocked<3, 3, 1, 2>(c, L, F, it, st);
       else
         conv_fwd_generic(c, L, F, it, st);
       __syncthreads();

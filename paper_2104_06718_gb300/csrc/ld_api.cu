@@ -37,6 +37,9 @@ struct ld_net {
   float *scr_bn = nullptr, *scr_b0 = nullptr;
   int8_t *empty = nullptr, *vtx = nullptr;
   double* acc = nullptr;
+  float* splitk_part = nullptr;       // split-K partial sums of the layerwise forward FC pass
+  int* splitk_count = nullptr;
+  int splitk_part_cap = 0, splitk_count_cap = 0;
   // fused engine and the autotuner's choices: B -> (engine, tile)
   ld::FusedNet fused{};
   std::map<int, std::pair<int, int>> tuned;
@@ -124,6 +127,14 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 int n_final_slots(const ld_net* net);
 
+// Largest output width of an FC layer (the split-K forward pass's tile count).
+int max_fc_out(const ld_net* net) {
+  int m = 1;
+  for (const auto& L : net->L)
+    if (L.kind == LD_LAYER_FC && L.n_out > m) m = L.n_out;
+  return m;
+}
+
 ld_status ensure_ws(ld_net* net, int B) {
   if (B <= net->ws_B) return LD_OK;
   const size_t Bn = (size_t)(B > 0 ? B : 1);
@@ -140,6 +151,8 @@ ld_status ensure_ws(ld_net* net, int B) {
       Bn,                // empty
       Bn * N,            // vtx
       8 * 3 * Bn * (size_t)n_final_slots(net),  // acc: final-bound slots
+      4 * 16 * Bn * (size_t)max_fc_out(net),      // split-K partial sums (up to 16 splits)
+      4 * ((Bn + 31) / 32) * (size_t)((max_fc_out(net) + 31) / 32),  // split-K tile counters
   };
   size_t total = 0;
   for (size_t s : sizes) total += align256(s);
@@ -152,8 +165,8 @@ ld_status ensure_ws(ld_net* net, int B) {
   }
   net->ws = p;
   char* c = static_cast<char*>(p);
-  void* ptrs[11];
-  for (int i = 0; i < 11; ++i) {
+  void* ptrs[13];
+  for (int i = 0; i < 13; ++i) {
     ptrs[i] = c;
     c += align256(sizes[i]);
   }
@@ -168,6 +181,11 @@ ld_status ensure_ws(ld_net* net, int B) {
   net->empty = (int8_t*)ptrs[8];
   net->vtx = (int8_t*)ptrs[9];
   net->acc = (double*)ptrs[10];
+  net->splitk_part = (float*)ptrs[11];
+  net->splitk_count = (int*)ptrs[12];
+  net->splitk_part_cap = (int)(16 * Bn * (size_t)max_fc_out(net));
+  net->splitk_count_cap = (int)(((Bn + 31) / 32) * (size_t)((max_fc_out(net) + 31) / 32));
+  if (cudaMemset(net->splitk_count, 0, sizes[12]) != cudaSuccess) return LD_ERR_CUDA;
   net->ws_B = B > 0 ? B : 1;
   return LD_OK;
 }
@@ -213,6 +231,10 @@ Problem make_problem(ld_net* net, const float* lb0, const float* ub0, const floa
   P.prop = prop;
   P.mask = masks;
   P.empty = net->empty;
+  P.splitk_part = net->splitk_part;
+  P.splitk_count = net->splitk_count;
+  P.splitk_part_cap = net->splitk_part_cap;
+  P.splitk_count_cap = net->splitk_count_cap;
   return P;
 }
 

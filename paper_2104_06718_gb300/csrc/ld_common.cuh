@@ -44,6 +44,11 @@ struct Problem {
   const int32_t* prop;           // [B] or nullptr
   const int8_t* mask;            // [B, N] or nullptr
   const int8_t* empty;           // [B] 1 where the clamped bounds cross
+  // split-K scratch of the layerwise forward FC pass (nullptr: no split)
+  float* splitk_part;            // [splits, B, n_out] partial sums
+  int* splitk_count;             // per output tile: partials that have arrived
+  int splitk_part_cap;           // floats available in splitk_part
+  int splitk_count_cap;          // ints available in splitk_count
 };
 
 // Property of subdomain b; an out-of-range index is clamped here (so no

@@ -67,7 +67,7 @@ extern "C" ld_status ld_final_bound_noalloc(ld_net* net, const float* lb0, const
   if (st != LD_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   int8_t* empty = reinterpret_cast<int8_t*>(static_cast<unsigned char*>(base) + flag_off);
-  ld::Problem P;
+  ld::Problem P{};
   P.B = B;
   P.N = (int)nv.N;
   P.n0 = (int)nv.n0;

@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--iters", type=int, default=0, help="override Adam iterations (profiling runs)")
     ap.add_argument("--engine", default="auto", choices=["auto", "layerwise", "fused"])
     ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"],
+                    help="arithmetic of the Adam iterations (the final bound is FP64 either way)")
     return ap.parse_args()
 
 
@@ -280,7 +282,7 @@ def run_ours(args):
     masks_np = synth.split_masks(net.N, B, amb, wl["depth"], block=rank)
     masks = torch.as_tensor(masks_np, device=dev)
     ones = torch.ones(B, dtype=torch.float64, device=dev)
-    opts = ldb.Options(engine=args.engine, tile=args.tile)
+    opts = ldb.Options(engine=args.engine, tile=args.tile, precision=args.precision)
 
     def step():
         lk, uk = ldb.ld_intermediate_bounds(net, l0, u0)
@@ -294,6 +296,10 @@ def run_ours(args):
         step()
     torch.cuda.synchronize()
     engine, tile = net.tuned(B)
+    if args.precision == "bf16":
+        engine, tile = "tensor-core bf16", 0
+    elif args.engine != "auto":
+        engine, tile = args.engine, args.tile
     # ---- device-resident timing
     sampler = ClockSampler(torch.cuda.current_device())
     if world > 1:
@@ -392,11 +398,14 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": "bounds/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000 * t_all / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if args.precision == "bf16" else "f32",
+        "data": "synthetic",
         "config": {"workload": f"{wl['net']} convnet ({net.N} ReLUs), {B} subdomains/GPU, split depth "
                                f"{wl['depth'][0]}-{wl['depth'][1]}, T={T} Adam iterations, CROWN init, FP64 final "
                                f"bound, Danskin backward",
-                   "subdomains_per_gpu": B, "iterations": T, "precision": "fp32 iterations, fp64 final",
+                   "subdomains_per_gpu": B, "iterations": T,
+                   "precision": ("bf16 GEMM operands, fp32 accumulation and dual state" if args.precision == "bf16"
+                                 else "fp32") + " iterations, fp64 final",
                    "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": "bounds/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},

@@ -103,6 +103,10 @@ class Layer:
         """r [B, n_out] -> W^T r, [B, n_in] (no bias)."""
         return np.asarray((self.mat.T @ r.T).T)
 
+    def linear(self, x: np.ndarray) -> np.ndarray:
+        """x [B, n_in] -> W x, [B, n_out] (no bias)."""
+        return np.asarray((self.mat @ x.T).T)
+
 
 def conv_out_shape(in_shape, W, stride, pad):
     cout, cin, kh, kw = W.shape
@@ -270,18 +274,36 @@ def box_argmin(a, l, u):
     return np.where(a <= 0, u, l)
 
 
-def inner_minimisation(net: Net, l0, u0, lb, ub, rho) -> InnerSolution:
+class ExactPasses:
+    """The two linear passes of the inner minimisation in FP64 arithmetic."""
+
+    def __init__(self, net: Net):
+        self.net = net
+
+    def transposed(self, k: int, r):
+        """g_{k-1} = W_k^T r (no bias)."""
+        return self.net.L(k).transposed(r)
+
+    def forward(self, k: int, x):
+        """x_hat_A,k = W_k x + b_k."""
+        return self.net.L(k).forward(x)
+
+
+def inner_minimisation(net: Net, l0, u0, lb, ub, rho, passes=None) -> InnerSolution:
     """Solve the decomposed inner problem of Eq. (nonprox_problem) at rho.
 
     l0, u0 [B, n_0]; lb, ub lists 1..n-1 of [B, n_k] (clamped); rho list 1..n-1.
     Vertex codes: 0 -> (l,0) / lower endpoint, 1 -> (0,0), 2 -> (u,u) / upper.
+    `passes` supplies the linear passes (default: exact FP64, ExactPasses);
+    q is always computed from the g of those passes.
     """
     n = net.n
     B = l0.shape[0]
+    ps = ExactPasses(net) if passes is None else passes
     g = [None] * n
     for k in range(n):
         rho_next = -np.ones((B, 1)) if k + 1 == n else rho[k + 1]
-        g[k] = net.L(k + 1).transposed(rho_next)
+        g[k] = ps.transposed(k + 1, rho_next)
 
     # P0 (Sec. 3.2.1, Eq. (box_bounds_sol)): minimise -g_0^T x0 over the box.
     x = [box_argmin(-g[0], l0, u0)]
@@ -334,7 +356,7 @@ def inner_minimisation(net: Net, l0, u0, lb, ub, rho) -> InnerSolution:
         xB.append(xb)
         vertex.append(code)
 
-    xA = [None] + [net.L(k).forward(x[k - 1]) for k in range(1, n + 1)]
+    xA = [None] + [ps.forward(k, x[k - 1]) for k in range(1, n + 1)]
     # Lagrangian of Eq. (nonprox_problem) at the returned primal point
     q_point = xA[n][:, 0].copy()
     for k in range(1, n):
@@ -366,6 +388,52 @@ def supergradient(sol: InnerSolution):
 
 
 # --------------------------------------------------------------------------
+# BF16 operands (the precision of the tensor-core passes)
+# --------------------------------------------------------------------------
+
+def round_bf16(a):
+    """Nearest bfloat16 value (ties to even) of each element, via its float32
+    value: keep the top 16 bits of the float32 encoding after adding half an
+    ulp of the kept part (0x7FFF plus the lowest kept bit)."""
+    f = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+class BF16Passes:
+    """Linear passes with BF16 operands and exact accumulation: the weights of
+    layers 1..n-1 and the vectors they multiply (rho_k in the transposed pass,
+    x_{k-1} in the forward pass) rounded to bfloat16.  Layer n is exact (its
+    transposed pass is g_{n-1} = -W_n, no product is formed).  The box enters
+    the forward pass of layer 1 as x_0 = c_0 + delta_0 with c_0 = l_0 +
+    (u_0 - l_0)/2 exact and only delta_0 = x_0 - c_0 rounded, so that the box
+    width survives the rounding."""
+
+    def __init__(self, net: Net, l0, u0):
+        self.net = net
+        self.rounded = {}
+        for k in range(1, net.n):
+            lay = net.L(k)
+            Wr = round_bf16(lay.W)
+            self.rounded[k] = Layer(lay.kind, Wr, np.zeros_like(lay.b), lay.in_shape, lay.stride, lay.pad)
+        self.c0 = l0 + (u0 - l0) / 2
+        self.c1 = net.L(1).forward(self.c0)
+
+    def transposed(self, k: int, r):
+        if k == self.net.n:
+            return self.net.L(k).transposed(r)
+        return self.rounded[k].transposed(round_bf16(r))
+
+    def forward(self, k: int, x):
+        if k == self.net.n:
+            return self.net.L(k).forward(x)
+        if k == 1:
+            return self.c1 + self.rounded[1].linear(round_bf16(x - self.c0))
+        return self.rounded[k].linear(round_bf16(x)) + self.net.L(k).bias_vector()[None, :]
+
+
+# --------------------------------------------------------------------------
 # Dual initialisation (Prop. 3) and the propagation bound
 # --------------------------------------------------------------------------
 
@@ -388,23 +456,27 @@ def crown_slopes(l, u):
     return a_bar, a_low, b_bar
 
 
-def crown_init(net: Net, lb, ub):
+def crown_init(net: Net, lb, ub, passes=None):
     """rho^0 = mu_bar of Eq. (salman-assignment), Prop. 3 (one backward pass).
 
     lambda_{n-1} = -W_n^T 1; mu_k = a_bar*[lambda_k]_+ + a_low*[lambda_k]_-;
     lambda_{k-1} = W_k^T mu_k.  Returns (rho list 1..n-1, lambda list 1..n-1).
+    `passes` supplies the transposed products (default exact); the iterations
+    must use the same ones, or the exact (l,0)/(u,u) ties that Prop. 3 puts
+    at rho^0 are broken by the difference between the two.
     """
     n = net.n
     B = lb[1].shape[0]
+    ps = ExactPasses(net) if passes is None else passes
     rho = [None] * n
     lam = [None] * n
-    lam_k = net.L(n).transposed(-np.ones((B, 1)))
+    lam_k = ps.transposed(n, -np.ones((B, 1)))
     for k in range(n - 1, 0, -1):
         lam[k] = lam_k
         a_bar, a_low, _ = crown_slopes(lb[k], ub[k])
         rho[k] = a_bar * np.maximum(lam_k, 0.0) + a_low * np.minimum(lam_k, 0.0)
         if k >= 2:
-            lam_k = net.L(k).transposed(rho[k])
+            lam_k = ps.transposed(k, rho[k])
     return rho, lam
 
 
@@ -455,7 +527,7 @@ class AdamResult:
 
 
 def supergradient_adam(net, l0, u0, lb, ub, rho0, T, s: AdamSettings = AdamSettings(),
-                       m0=None, v0=None, t0: int = 0, T_sched: int | None = None):
+                       m0=None, v0=None, t0: int = 0, T_sched: int | None = None, passes=None):
     """Algorithm 1 with the Adam update in place of Eq. (subgradient_update).
 
     For t = 0..T-1: inner minimisation at rho^t, supergradient
@@ -464,6 +536,8 @@ def supergradient_adam(net, l0, u0, lb, ub, rho0, T, s: AdamSettings = AdamSetti
         rho <- rho + alpha_t * (m / (1-b1^(t+1))) / (sqrt(v / (1-b2^(t+1))) + eps)
     and finally q(rho^T).  `t0`, `m0`, `v0`, `T_sched` resume a run that was
     split across calls (the schedule index is t0 + t out of T_sched).
+    `passes` replaces the linear passes of the iterations (not of the final
+    q(rho^T), which is always exact).
     """
     n = net.n
     rho = [None] + [np.array(rho0[k], dtype=np.float64, copy=True) for k in range(1, n)]
@@ -473,7 +547,7 @@ def supergradient_adam(net, l0, u0, lb, ub, rho0, T, s: AdamSettings = AdamSetti
     trace = []
     for t in range(T):
         tt = t0 + t
-        sol = inner_minimisation(net, l0, u0, lb, ub, rho)
+        sol = inner_minimisation(net, l0, u0, lb, ub, rho, passes)
         trace.append(sol.q)
         sg = supergradient(sol)
         alpha = step_size(tt, Ts, s)
@@ -508,13 +582,14 @@ def flatten_layers(net, lst):
 
 
 def ld_bound(net: Net, l0, u0, lbk, ubk, prop_of_subdomain, masks, T,
-             s: AdamSettings = AdamSettings(), init: str = "crown", rho_in=None):
+             s: AdamSettings = AdamSettings(), init: str = "crown", rho_in=None, operands: str = "fp64"):
     """Lower bound of min x_hat_n for each subdomain after T Adam updates.
 
     l0, u0 [P, n_0]; lbk, ubk [P, sum n_k] intermediate bounds of layers
     1..n-1; masks int8 [B, sum n_k].  Empty subdomains get +inf and no
-    iterations.  Returns (bounds [B], AdamResult over the feasible rows,
-    feasible-row index array).
+    iterations.  operands "bf16" runs the iterations with BF16Passes (the
+    final bound stays exact).  Returns (bounds [B], AdamResult over the
+    feasible rows, feasible-row index array).
     """
     B = masks.shape[0]
     pos = np.zeros(B, dtype=np.int64) if prop_of_subdomain is None else np.asarray(prop_of_subdomain)
@@ -532,12 +607,18 @@ def ld_bound(net: Net, l0, u0, lbk, ubk, prop_of_subdomain, masks, T,
     if rho_in is not None:
         rho0 = sel(layer_lists(net, np.asarray(rho_in, np.float64)))
     elif init == "crown":
-        rho0, _ = crown_init(net, lbs, ubs)
+        rho0, _ = crown_init(net, lbs, ubs,
+                             BF16Passes(net, L0[keep], U0[keep]) if operands == "bf16" else None)
     elif init == "zero":
         rho0 = [None] + [np.zeros_like(lbs[k]) for k in range(1, net.n)]
     else:
         raise ValueError(init)
-    res = supergradient_adam(net, L0[keep], U0[keep], lbs, ubs, rho0, T, s)
+    passes = None
+    if operands == "bf16":
+        passes = BF16Passes(net, L0[keep], U0[keep])
+    elif operands != "fp64":
+        raise ValueError(operands)
+    res = supergradient_adam(net, L0[keep], U0[keep], lbs, ubs, rho0, T, s, passes=passes)
     out[keep] = res.q_final
     return out, res, keep
 

@@ -42,6 +42,15 @@ struct ld_net {
   int splitk_part_cap = 0, splitk_count_cap = 0;
   // fused engine and the autotuner's choices: B -> (engine, tile)
   ld::FusedNet fused{};
+  // BF16 tensor-core engine: re-laid weights (built on first use) and the
+  // shadow rows [B, XH] / [B, RH] plus the per-property centre term
+  ld::TcNet tc{};
+  ld_status tc_state = LD_ERR_UNSUPPORTED;  // LD_OK once built
+  bool tc_tried = false;
+  void* tc_ws = nullptr;
+  int tc_B = -1, tc_props = -1;
+  uint16_t *xh = nullptr, *rh = nullptr;
+  float* c1 = nullptr;
   std::map<int, std::pair<int, int>> tuned;
   int n_sm = 0;
   size_t smem_optin = 0;
@@ -200,7 +209,6 @@ ld_status check_opts(const ld_opts& o) {
   if (!(o.beta1 >= 0 && o.beta1 < 1 && o.beta2 >= 0 && o.beta2 < 1 && o.eps > 0)) return LD_ERR_ARG;
   if (o.init < LD_INIT_ZERO || o.init > LD_INIT_GIVEN) return LD_ERR_ARG;
   if (o.precision != LD_PREC_FP32 && o.precision != LD_PREC_BF16) return LD_ERR_ARG;
-  if (o.precision == LD_PREC_BF16) return LD_ERR_UNSUPPORTED;
   if (o.t_offset < 0 || o.t_total < 0) return LD_ERR_ARG;
   if (o.engine < LD_ENGINE_AUTO || o.engine > LD_ENGINE_FUSED) return LD_ERR_ARG;
   if (o.tile != 0 && o.tile != 1 && o.tile != 2 && o.tile != 4) return LD_ERR_ARG;
@@ -276,6 +284,18 @@ void sweep(ld_net* net, const Problem& P, int mode, const ld_opts& o, ld::AdamSt
   }
 }
 
+// Adam constants of iteration tt (0-based, counted over the whole schedule):
+// alpha from the linear schedule, bias corrections with step count tt + 1.
+ld::AdamStep adam_step(const ld_opts& o, int tt, int T_sched) {
+  ld::AdamStep a;
+  const double alpha = (double)o.alpha0 + ((double)o.alpha_end - (double)o.alpha0) * (double)tt /
+                                              (double)(T_sched - 1 > 1 ? T_sched - 1 : 1);
+  a.alpha = (float)alpha;
+  a.inv_bc1 = (float)(1.0 / (1.0 - std::pow((double)o.beta1, (double)(tt + 1))));
+  a.inv_bc2 = (float)(1.0 / (1.0 - std::pow((double)o.beta2, (double)(tt + 1))));
+  return a;
+}
+
 bool tile_fits(const ld_net* net, int S) { return ld::fused_smem_bytes(net->fused, S) <= net->smem_optin; }
 
 // T Adam iterations with the given engine (tile = subdomains per CTA).
@@ -288,15 +308,80 @@ ld_status run_iterations(ld_net* net, const Problem& P, const ld_opts& o, int n_
     ld::FusedIter it{n_iters, o.t_offset, T_sched, o.alpha0, o.alpha_end, o.beta1, o.beta2, o.eps, crown};
     return cuda_status(ld::launch_fused(net->fused, tile, P, net->rho, net->m, net->v, it, s));
   }
+  for (int t = 0; t < n_iters; ++t)
+    sweep(net, P, 0, o, adam_step(o, o.t_offset + t, T_sched), nullptr, nullptr, nullptr, nullptr, s);
+  return last_error();
+}
+
+// Tensor-core plan and shadow buffers for B subdomains and n_props properties.
+ld_status ensure_tc(ld_net* net, int B, int n_props) {
+  if (!net->tc_tried) {
+    net->tc_tried = true;
+    net->tc_state = ld::build_tc_net(net->L, &net->tc);
+  }
+  if (net->tc_state != LD_OK) return net->tc_state;
+  if (B <= net->tc_B && n_props <= net->tc_props) return LD_OK;
+  const size_t Bn = (size_t)(B > 0 ? B : 1), Pn = (size_t)(n_props > 0 ? n_props : 1);
+  const size_t s_xh = align256(2 * Bn * (size_t)net->tc.XH), s_rh = align256(2 * Bn * (size_t)net->tc.RH);
+  const size_t s_c1 = align256(4 * Pn * (size_t)net->tc.n1);
+  cudaDeviceSynchronize();
+  if (net->tc_ws) cudaFree(net->tc_ws);
+  net->tc_ws = nullptr;
+  net->tc_B = net->tc_props = -1;
+  void* p = nullptr;
+  if (cudaMalloc(&p, s_xh + s_rh + s_c1) != cudaSuccess) {
+    cudaGetLastError();
+    return LD_ERR_NOMEM;
+  }
+  // the zero padding of the shadows is never written afterwards
+  if (cudaMemset(p, 0, s_xh + s_rh + s_c1) != cudaSuccess) return LD_ERR_CUDA;
+  net->tc_ws = p;
+  char* c = static_cast<char*>(p);
+  net->xh = reinterpret_cast<uint16_t*>(c);
+  net->rh = reinterpret_cast<uint16_t*>(c + s_xh);
+  net->c1 = reinterpret_cast<float*>(c + s_xh + s_rh);
+  net->tc_B = (int)Bn;
+  net->tc_props = (int)Pn;
+  return LD_OK;
+}
+
+// T Adam iterations with BF16 tensor-core passes: the top layer's inner
+// minimisation (rho_n = -1, no GEMM) in FP32, then for k = n-1 .. 1 the
+// transposed pass of layer k (-> inner minimisation of layer k-1) and the
+// forward pass of layer k (-> Adam on rho_k), as in the FP32 sweep.
+ld::TcState tc_state(const ld_net* net, const ld_opts& o) {
+  return ld::TcState{net->xh, net->rh, net->c1, net->rho, net->m, net->v, net->xB, net->d_status,
+                     o.beta1, o.beta2, o.eps};
+}
+
+// CROWN start for the BF16 iterations: rho_{n-1} from the top layer (FP32,
+// no product), then rho_{k-1} from the tensor-core transposed pass of layer
+// k, so that the start and the iterations form their products alike (the
+// exact (l,0)/(u,u) ties of Prop. 3 survive into the first iteration).
+void crown_sweep_bf16(ld_net* net, const Problem& P, const ld_opts& o, cudaStream_t s) {
+  const int n = net->n;
+  const ld::TcState S = tc_state(net, o);
+  ld::EpiCrown top{P, r_off(net, n - 1), net->rho};
+  ld::launch_top_crown(layer(net, n), P, top, s);
+  ld::launch_tc_shadow_rho(net->tc, net->L, P, S, n - 1, n - 1, s);
+  for (int k = n - 1; k >= 2; --k) ld::launch_tc_transposed(net->tc, net->L, k, P, S, net->n_sm, s, 1);
+}
+
+ld_status run_iterations_bf16(ld_net* net, const Problem& P, const ld_opts& o, int n_iters, bool shadows_ready,
+                              cudaStream_t s) {
+  const int T_sched = o.t_total > 0 ? o.t_total : o.t_offset + n_iters;
+  const int n = net->n;
+  const ld::TcState S = tc_state(net, o);
+  ld::launch_tc_centre(net->tc, layer(net, 1), P, S, s);
+  if (!shadows_ready) ld::launch_tc_shadow_rho(net->tc, net->L, P, S, 1, n - 1, s);
   for (int t = 0; t < n_iters; ++t) {
-    const int tt = o.t_offset + t;
-    ld::AdamStep a;
-    const double alpha = (double)o.alpha0 + ((double)o.alpha_end - (double)o.alpha0) * (double)tt /
-                                                (double)(T_sched - 1 > 1 ? T_sched - 1 : 1);
-    a.alpha = (float)alpha;
-    a.inv_bc1 = (float)(1.0 / (1.0 - std::pow((double)o.beta1, (double)(tt + 1))));
-    a.inv_bc2 = (float)(1.0 / (1.0 - std::pow((double)o.beta2, (double)(tt + 1))));
-    sweep(net, P, 0, o, a, nullptr, nullptr, nullptr, nullptr, s);
+    const ld::AdamStep a = adam_step(o, o.t_offset + t, T_sched);
+    ld::EpiArgmin ea{P, n - 1, r_off(net, n - 1), x_off(net, n - 1), net->rho, net->x, net->xB, nullptr, nullptr};
+    ld::launch_top_argmin(layer(net, n), P, ea, s);
+    for (int k = n - 1; k >= 1; --k) {
+      ld::launch_tc_transposed(net->tc, net->L, k, P, S, net->n_sm, s);
+      ld::launch_tc_forward(net->tc, net->L, k, P, S, a, net->n_sm, s);
+    }
   }
   return last_error();
 }
@@ -590,6 +675,8 @@ ld_status ld_net_destroy(ld_net* net) {
   cudaDeviceSynchronize();
   drain_marks(net);
   free_ws(net);
+  if (net->tc_ws) cudaFree(net->tc_ws);
+  ld::free_tc_net(&net->tc);
   if (net->d_W) cudaFree(net->d_W);
   if (net->d_Wx) cudaFree(net->d_Wx);
   if (net->d_b) cudaFree(net->d_b);
@@ -659,7 +746,10 @@ ld_status ld_bound(ld_net* net, const float* lb0, const float* ub0, const float*
   cudaStream_t s = S(stream);
   const Problem P = make_problem(net, lb0, ub0, lbk, ubk, n_props, prop, masks, B);
   const size_t BN = (size_t)B * net->N;
-  const std::pair<int, int> eng = n_iters > 0 ? choose_engine(net, P, o, s) : std::make_pair(1, 0);
+  const bool bf16 = o.precision == LD_PREC_BF16 && n_iters > 0;
+  if (bf16 && (st = ensure_tc(net, B, n_props)) != LD_OK) return st;
+  const std::pair<int, int> eng =
+      (n_iters > 0 && !bf16) ? choose_engine(net, P, o, s) : std::make_pair((int)LD_ENGINE_LAYERWISE, 0);
   // The CROWN start must come from the same transposed-pass arithmetic as the
   // iterations (its exact ties would otherwise be broken by rounding): the
   // fused engine computes it in-kernel, the layerwise engine with its kernels.
@@ -671,6 +761,8 @@ ld_status ld_bound(ld_net* net, const float* lb0, const float* ub0, const float*
       cudaMemcpyAsync(net->rho, rho_in, sizeof(float) * BN, cudaMemcpyDeviceToDevice, s);
     else if (o.init == LD_INIT_ZERO)
       cudaMemsetAsync(net->rho, 0, sizeof(float) * BN, s);
+    else if (bf16)
+      crown_sweep_bf16(net, P, o, s);
     else if (!crown_in_kernel)
       crown_sweep(net, P, s);
     if (adam_mv && o.t_offset > 0) {
@@ -683,7 +775,9 @@ ld_status ld_bound(ld_net* net, const float* lb0, const float* ub0, const float*
   }
   if (n_iters > 0) {
     PhaseMark pm(net, LD_PHASE_ITER, s);
-    if ((st = run_iterations(net, P, o, n_iters, eng.first, eng.second, s, crown_in_kernel)) != LD_OK) return st;
+    st = bf16 ? run_iterations_bf16(net, P, o, n_iters, o.init == LD_INIT_CROWN, s)
+              : run_iterations(net, P, o, n_iters, eng.first, eng.second, s, crown_in_kernel);
+    if (st != LD_OK) return st;
   }
   {
     PhaseMark pm(net, LD_PHASE_FINAL, s);

@@ -149,24 +149,30 @@ struct EpiArgmin {
 
 // Transposed pass -> CROWN dual of layer k (Prop. 3, Eq. salman-assignment):
 // rho_k = a_bar [lambda]_+ + a_low [lambda]_- with lambda = g_k.
+// CROWN dual of neuron j (flat index) of subdomain b at lambda (Prop. 3,
+// Eq. salman-assignment): a_bar [lambda]_+ + a_low [lambda]_-.
+__device__ __forceinline__ float crown_rho(const Problem& P, int b, int j, float lam) {
+  float l, u;
+  clamped_bounds(P, b, j, l, u);
+  float a_up, a_lo;
+  if (u <= 0.f) {            // blocking
+    a_up = 0.f; a_lo = 0.f;
+  } else if (l >= 0.f) {     // passing
+    a_up = 1.f; a_lo = 1.f;
+  } else {                   // ambiguous: u/(u-l); CROWN lower slope 1[u >= -l]
+    a_up = u / (u - l);
+    a_lo = (u >= -l) ? 1.f : 0.f;
+  }
+  return a_up * fmaxf(lam, 0.f) + a_lo * fminf(lam, 0.f);
+}
+
 struct EpiCrown {
   Problem P;
   int r_off;
   float* rho;          // [B, N]
   __device__ __forceinline__ void operator()(int b, int i, float lam) const {
     const int j = r_off + i;
-    float l, u;
-    clamped_bounds(P, b, j, l, u);
-    float a_up, a_lo;
-    if (u <= 0.f) {            // blocking
-      a_up = 0.f; a_lo = 0.f;
-    } else if (l >= 0.f) {     // passing
-      a_up = 1.f; a_lo = 1.f;
-    } else {                   // ambiguous: u/(u-l); CROWN lower slope 1[u >= -l]
-      a_up = u / (u - l);
-      a_lo = (u >= -l) ? 1.f : 0.f;
-    }
-    rho[(size_t)b * P.N + j] = a_up * fmaxf(lam, 0.f) + a_lo * fminf(lam, 0.f);
+    rho[(size_t)b * P.N + j] = crown_rho(P, b, j, lam);
   }
 };
 
@@ -281,6 +287,67 @@ FusedNet make_fused_net(const std::vector<LayerDev>& Ls);
 size_t fused_smem_bytes(const FusedNet& f, int S);
 cudaError_t launch_fused(const FusedNet& f, int S, const Problem& P, float* rho, float* m, float* v,
                          const FusedIter& it, cudaStream_t s);
+
+// ---------------------------------------------------------------- BF16 tensor-core engine
+// Plan of layer k for the tcgen05 passes (ld_tc.cu).  The BF16 operand copies
+// ("shadows") of x_{k-1} and rho_k live in per-subdomain rows [B, XH] and
+// [B, RH] in the layout the consuming GEMM gathers from:
+//   conv input x_{k-1}:  [h][w][cp_in] (channels innermost, zero-padded)
+//   FC input x_{k-1}:    [n_in rounded up to 8] (flat, neuron order)
+//   conv output rho_k:   [ho][wo][cp_out]
+//   FC output rho_k:     [n_out rounded up to 16]
+struct TcLayer {
+  int kind;
+  int xh_off, xh_len;          // shadow of x_{k-1} (layers k <= n-1)
+  int cp_in;                   // conv: channels per pixel of that shadow (4 or a multiple of 8)
+  int rh_off, rh_len;          // shadow of rho_k (layers k <= n-1)
+  int cp_out;                  // conv: channels per pixel of that shadow (multiple of 8)
+  // forward GEMM operand (bf16 bits, canonical K-major tiles)
+  int nf, kf;                  // conv: N = cout rounded to 16, K = taps x cp_in rounded to 16
+  int fc_kc, fc_nkc, fc_nmt;   // FC: K chunk, chunks, 128-row tiles over n_out
+  const uint16_t* Wf;
+  // transposed GEMM operand
+  int nt, kt;                  // conv: N = cin rounded to 16, K per stride phase; FC: K = rh_len
+  int n_phase, na, nb;         // conv: stride phases, taps per phase along y / x
+  int fc_nmt_t;                // FC: 128-row tiles over n_in
+  const uint16_t* Wt;
+};
+struct TcNet {
+  int n = 0;
+  int XH = 0, RH = 0;          // bf16 elements per subdomain of the two shadow rows
+  int n1 = 0;                  // neurons of layer 1 (width of the centred-input constant)
+  TcLayer T[kMaxLayers];       // T[k-1] = layer k
+  uint16_t* d_w = nullptr;     // all re-laid weights (owned)
+};
+// Shadows and per-call buffers of the BF16 iterations.
+struct TcState {
+  uint16_t* xh;                // [B, XH]
+  uint16_t* rh;                // [B, RH]
+  float* c1;                   // [n_props, n1]: W_1 c_0 + b_1 at the box centre c_0
+  float* rho;
+  float* m;
+  float* v;
+  float* xB;
+  int* status;
+  float beta1, beta2, eps;
+};
+// Builds the plan and uploads the re-laid BF16 weights; LD_ERR_UNSUPPORTED if
+// a layer's shape has no tensor-core path.
+ld_status build_tc_net(const std::vector<LayerDev>& Ls, TcNet* out);
+void free_tc_net(TcNet* t);
+// rho (FP32) -> shadows of rho_k for k_lo <= k <= k_hi.
+void launch_tc_shadow_rho(const TcNet& t, const std::vector<LayerDev>& Ls, const Problem& P, const TcState& S,
+                          int k_lo, int k_hi, cudaStream_t s);
+// c1 = W_1 c_0 + b_1 per property, c_0 = l_0 + (u_0 - l_0) / 2.
+void launch_tc_centre(const TcNet& t, const LayerDev& L1, const Problem& P, const TcState& S, cudaStream_t s);
+// Transposed pass of layer k (1 <= k <= n-1) -> inner minimisation of layer
+// k-1; crown = 1 (k >= 2): the CROWN dual of layer k-1 instead (rho and its
+// shadow), so that the start and the iterations share the same products.
+void launch_tc_transposed(const TcNet& t, const std::vector<LayerDev>& Ls, int k, const Problem& P,
+                          const TcState& S, int n_sm, cudaStream_t s, int crown = 0);
+// Forward pass of layer k (1 <= k <= n-1) -> supergradient and Adam on rho_k.
+void launch_tc_forward(const TcNet& t, const std::vector<LayerDev>& Ls, int k, const Problem& P, const TcState& S,
+                       AdamStep st, int n_sm, cudaStream_t s);
 
 // ---------------------------------------------------------------- launchers
 // FP32 passes (ld_passes.cu).

@@ -1,0 +1,1215 @@
+// BF16 tensor-core passes of the LD iteration (Blackwell tcgen05).
+//
+// With precision LD_PREC_BF16 the two linear passes of every Adam iteration,
+//     transposed  g_{k-1} = W_k^T rho_k      (Sec. 5.2, "analogous to backpropagation")
+//     forward     x_hat_A,k = W_k x_{k-1}^*  (Sec. 5.2, "exactly forward passes")
+// run as BF16 GEMMs with FP32 accumulation in tensor memory (TMEM):
+//   conv layers  implicit GEMM, M = 128 (subdomain, position) rows, N = the
+//                channels, K = taps x channels; the weight matrix (all stride
+//                phases for the transposed pass) is bulk-copied into shared
+//                memory once per CTA and the activation rows are gathered
+//                with cp.async into the canonical K-major tile layout;
+//   FC layers    M = 128 neurons, N = a tile of subdomains (the subdomain
+//                batch is the GEMM N dimension), K = the layer inputs; the
+//                weight blocks stream by bulk copy, the subdomain rows by
+//                cp.async.
+// One elected thread issues tcgen05.mma and commits to an mbarrier; all
+// eight warps then read the accumulator tile with tcgen05.ld (two warps per
+// TMEM lane quadrant, each half of the columns) and run the fused epilogue:
+// the inner minimisation of Sec. 3.2.2 (transposed pass) or the supergradient
+// x_hat_B - x_hat_A and Adam step of Algorithm 1 (forward pass).  The
+// epilogues keep rho, the Adam moments and x_hat_B in FP32 and write the BF16
+// copies ("shadows") of x_k and rho_k that the next GEMMs read; the final
+// bound is evaluated in FP64 from the FP32 duals (ld_final.cu).
+//
+// The input box enters as x_0 = c_0 + delta_0 with c_0 the box centre: the
+// forward GEMM of layer 1 multiplies the BF16 delta_0 = +-(u_0 - l_0)/2 and
+// the epilogue adds W_1 c_0 + b_1 computed once per call in FP32, so the
+// box width (a few BF16 ulps of the pixel value) is not lost to rounding.
+//
+// Every wait on an mbarrier is bounded (2 s); on expiry the kernel records
+// LD_ERR_TIMEOUT in the status word and all threads leave the tile loop.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "ld_common.cuh"
+
+namespace ld {
+namespace {
+
+constexpr int kThreads = 256;                 // 8 warps, 2 per TMEM lane quadrant
+constexpr int kRows = 128;                    // M of every MMA = TMEM lanes
+constexpr int kFcKC = 128;                    // K chunk of the FC forward GEMM
+constexpr int kConvKC = 64;                   // K per pipeline stage of the conv GEMMs
+constexpr int kTabMax = 256;                  // gather table entries (K pieces)
+constexpr unsigned long long kWaitNs = 2000000000ull;
+constexpr size_t kSmemBudget = 216 * 1024;    // dynamic shared memory a launch may ask for
+
+// ------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for the phase with the given parity to complete; false after kWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > kWaitNs) return false;
+  return true;
+}
+// Bulk (TMA) copy global -> shared, completion counted on an mbarrier.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+// cp.async of 16 / 8 bytes; a copy with valid == false writes zeros.
+__device__ __forceinline__ void cp16(uint32_t dst, const void* src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp8(uint32_t dst, const void* src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(valid ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// Generic-proxy writes to shared memory -> visible to the tensor core (async proxy).
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// D[tmem] (+)= A * B^T, A and B K-major BF16 tiles in shared memory, D FP32.
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// Arrive on the mbarrier once all MMAs issued so far by this thread are done.
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+// 8 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Canonical no-swizzle K-major operand tile of R rows: 16-byte chunks
+// (8 BF16 along K) ordered k-group-major, row-minor, so that the 8x16-byte
+// core matrices are contiguous; rows of a core matrix 16 B apart, 8-row
+// groups 128 B apart (SBO), K-adjacent core matrices R*16 B apart (LBO).
+__device__ __forceinline__ uint32_t chunk_off(int r, int k8, int R) { return (uint32_t)((k8 * R + r) * 16); }
+__device__ __forceinline__ uint64_t op_desc(uint32_t tile, int s, int R) {
+  const uint32_t start = tile + (uint32_t)(2 * s * R * 16);  // K step s = k-groups 2s, 2s+1
+  const uint64_t lbo = (uint64_t)(R * 16) >> 4, sbo = 128u >> 4;
+  return (uint64_t)((start & 0x3FFFFu) >> 4) | (lbo << 16) | (sbo << 32) | (1ull << 46);
+}
+// Instruction descriptor: kind::f16, A = B = BF16, D = FP32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ uint16_t bf16_bits(float f) {
+  return __bfloat16_as_ushort(__float2bfloat16_rn(f));
+}
+__device__ __forceinline__ uint4 pack8(const float (&v)[8]) {
+  uint4 u;
+  u.x = (uint32_t)bf16_bits(v[0]) | ((uint32_t)bf16_bits(v[1]) << 16);
+  u.y = (uint32_t)bf16_bits(v[2]) | ((uint32_t)bf16_bits(v[3]) << 16);
+  u.z = (uint32_t)bf16_bits(v[4]) | ((uint32_t)bf16_bits(v[5]) << 16);
+  u.w = (uint32_t)bf16_bits(v[6]) | ((uint32_t)bf16_bits(v[7]) << 16);
+  return u;
+}
+
+// Adam ascent step on one dual (same arithmetic as EpiAdam); returns new rho.
+struct AdamArgs {
+  const float* xB;
+  float* rho;
+  float* m;
+  float* v;
+  float beta1, beta2, eps;
+  AdamStep st;
+};
+__device__ __forceinline__ float adam_update(const AdamArgs& a, size_t j, float xa) {
+  const float s = a.xB[j] - xa;
+  const float mm = a.beta1 * a.m[j] + (1.f - a.beta1) * s;
+  const float vv = a.beta2 * a.v[j] + (1.f - a.beta2) * s * s;
+  a.m[j] = mm;
+  a.v[j] = vv;
+  const float mhat = mm * a.st.inv_bc1;
+  const float vhat = vv * a.st.inv_bc2;
+  const float r = a.rho[j] + a.st.alpha * mhat / (sqrtf(vhat) + a.eps);
+  a.rho[j] = r;
+  return r;
+}
+
+// Adam on up to 8 duals: every load first (so that the 32 loads overlap
+// instead of forming 8 dependent round trips), then the updates and stores.
+// Same arithmetic as adam_update.
+__device__ __forceinline__ void adam8(const AdamArgs& a, const size_t (&j)[8], const bool (&on)[8],
+                                      const float (&xa)[8], float (&rn)[8]) {
+  float xb[8], m0[8], v0[8], r0[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e)
+    if (on[e]) {
+      xb[e] = a.xB[j[e]];
+      m0[e] = a.m[j[e]];
+      v0[e] = a.v[j[e]];
+      r0[e] = a.rho[j[e]];
+    }
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    rn[e] = 0.f;
+    if (!on[e]) continue;
+    const float s = xb[e] - xa[e];
+    const float mm = a.beta1 * m0[e] + (1.f - a.beta1) * s;
+    const float vv = a.beta2 * v0[e] + (1.f - a.beta2) * s * s;
+    a.m[j[e]] = mm;
+    a.v[j[e]] = vv;
+    const float mhat = mm * a.st.inv_bc1;
+    const float vhat = vv * a.st.inv_bc2;
+    const float r = r0[e] + a.st.alpha * mhat / (sqrtf(vhat) + a.eps);
+    a.rho[j[e]] = r;
+    rn[e] = r;
+  }
+}
+
+// Inner minimisation of up to 8 neurons of a layer k >= 1 (flat indices jf
+// of subdomains bb): loads first, then relu_argmin; writes x_hat_B, returns x.
+__device__ __forceinline__ void argmin8(const Problem& P, const float* rho, float* xB, const int (&bb)[8],
+                                        const int (&jf)[8], const bool (&on)[8], const float (&g)[8],
+                                        float (&xv)[8]) {
+  float r[8], l[8], u[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e)
+    if (on[e]) {
+      r[e] = rho[(size_t)bb[e] * P.N + jf[e]];
+      clamped_bounds(P, bb[e], jf[e], l[e], u[e]);
+    }
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    xv[e] = 0.f;
+    if (!on[e]) continue;
+    float xb, xk;
+    int code;
+    relu_argmin<float>(r[e], g[e], l[e], u[e], xb, xk, code);
+    xB[(size_t)bb[e] * P.N + jf[e]] = xb;
+    xv[e] = xk;
+  }
+}
+
+// ------------------------------------------------------------------ ops
+// Common fields of one tensor-core launch.
+struct TcCommon {
+  int n_tiles, n_chunks;
+  uint32_t res_bytes;      // resident operand (conv weights), 0 if none
+  uint32_t stage_bytes;    // one pipeline stage (both operands of a K chunk)
+  uint32_t tmem_cols;
+  int* status;
+};
+
+// Forward conv of layer k: D[(b, p), o] = sum_{tap, c} x_{k-1}[b, tap(p), c] W[o, c, tap];
+// epilogue: Adam on rho_k.
+struct ConvFwdOp {
+  static constexpr bool kStageBulk = false;
+  TcCommon c;
+  int nf, kf, KC;              // N, K, K per stage (the last stage may be shorter)
+  const uint16_t* W;
+  int B, h, w, cout, ho, wo, kw, kh, S, pad, cp_in, cp_out;
+  int XH, xh_off, RH, rh_off;
+  const uint16_t* xh;
+  uint16_t* rh;
+  Problem P;
+  int first, r_off;
+  const float* bias;
+  const float* c1;
+  AdamArgs ad;
+
+  // gather table: per K piece (16 B for cp_in >= 8, 8 B for cp_in == 4):
+  // (tap row offset, tap column offset, first channel, tap exists)
+  __device__ void prepare(int4* tab) const {
+    const int step = cp_in >= 8 ? 8 : 4;
+    for (int e = threadIdx.x; e < kf / step; e += kThreads) {
+      const int kel = e * step, tap = kel / cp_in, c0 = kel % cp_in;
+      tab[e] = make_int4(tap / kw - pad, tap % kw - pad, c0, tap < kh * kw ? 1 : 0);
+    }
+  }
+  __device__ void load_resident(uint32_t sres, uint32_t bar) const {
+    mbar_expect_tx(bar, c.res_bytes);
+    bulk_g2s(sres, W, c.res_bytes, bar);
+  }
+  __device__ void load_stage(int tile, int chunk, uint32_t sst, uint32_t, const int4* tab) const {
+    const int r = threadIdx.x & (kRows - 1);
+    const int R = tile * kRows + r, hw = ho * wo;
+    const int b = R / hw, p = R - b * hw;
+    const int yo = p / wo, xo = p - yo * wo;
+    const bool row_ok = b < B;
+    const uint16_t* src_b = xh + (size_t)(row_ok ? b : 0) * XH + xh_off;
+    const int k8_lo = chunk * KC / 8, k8_hi = min(kf, (chunk + 1) * KC) / 8;
+    for (int k8 = k8_lo + (threadIdx.x >> 7); k8 < k8_hi; k8 += kThreads / kRows) {
+      const uint32_t dst = sst + chunk_off(r, k8 - k8_lo, kRows);
+      if (cp_in >= 8) {
+        const int4 t = tab[k8];
+        const int yy = yo * S + t.x, xx = xo * S + t.y;
+        const bool ok = row_ok && t.w && yy >= 0 && yy < h && xx >= 0 && xx < w;
+        cp16(dst, ok ? src_b + ((size_t)(yy * w + xx) * cp_in + t.z) : xh, ok);
+      } else {
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+          const int4 t = tab[2 * k8 + hf];
+          const int yy = yo * S + t.x, xx = xo * S + t.y;
+          const bool ok = row_ok && t.w && yy >= 0 && yy < h && xx >= 0 && xx < w;
+          cp8(dst + 8 * hf, ok ? src_b + ((size_t)(yy * w + xx) * cp_in + t.z) : xh, ok);
+        }
+      }
+    }
+  }
+  __device__ void issue_mma(int, int chunk, uint32_t sres, uint32_t sst, uint32_t tmem) const {
+    const uint32_t id = idesc_bf16(kRows, nf);
+    const int s0 = chunk * KC / 16, ns = (min(kf, (chunk + 1) * KC) - chunk * KC) / 16;
+    for (int s = 0; s < ns; ++s)
+      mma_bf16(tmem, op_desc(sst, s, kRows), op_desc(sres, s0 + s, nf), id, (chunk > 0 || s > 0) ? 1u : 0u);
+  }
+  __device__ void epilogue(int tile, uint32_t tmem) const {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = warp & 3, half = warp >> 2;
+    const int r = q * 32 + lane, R = tile * kRows + r, hw = ho * wo;
+    const int b = R / hw, p = R - b * hw;
+    const bool row_ok = b < B && !P.empty[b];
+    const int prop = row_ok ? prop_of(P, b) : 0;
+    const int cols = nf / 2, lo = half * cols;
+    for (int c0 = lo; c0 < lo + cols; c0 += 8) {
+      float acc[8];
+      tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, acc);
+      if (!row_ok || c0 >= cout) continue;
+      size_t j[8];
+      bool on[8];
+      float xa[8], rn[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int o = c0 + e, jj = o * hw + p;
+        on[e] = o < cout;
+        j[e] = (size_t)b * P.N + r_off + jj;
+        xa[e] = on[e] ? acc[e] + (first ? c1[(size_t)prop * cout * hw + jj] : bias[o]) : 0.f;
+      }
+      adam8(ad, j, on, xa, rn);
+      *reinterpret_cast<uint4*>(rh + (size_t)b * RH + rh_off + (size_t)p * cp_out + c0) = pack8(rn);
+    }
+  }
+};
+
+// Transposed conv of layer k by stride phase (ry, rx): rows = (b, qy, qx) of the
+// phase, g_{k-1}[b, c, S qy + ry, S qx + rx] = sum_{a, bb, o} W[o, c, i0 + S a, j0 + S bb]
+// rho_k[b, o, qy + dy0 - a, qx + dx0 - bb]; epilogue: inner minimisation of layer k-1.
+struct ConvTOp {
+  static constexpr bool kStageBulk = false;
+  TcCommon c;
+  int nt, kt, KC, n_phase, tpp, na, nb;
+  const uint16_t* W;
+  int B, cin, h, w, ho, wo, S, pad, cp_in, cp_out;
+  int XH, xh_off, RH, rh_off;
+  uint16_t* rh;                // read: shadow of rho_k; CROWN epilogue writes: shadow of rho_kb
+  uint16_t* xh;
+  Problem P;
+  int kb, r_off_kb;
+  float* xB;
+  float* rho;
+  int crown;                   // 1: CROWN dual of layer kb (rho and its shadow) instead of the argmin
+  int rhb_off, rhb_conv, rhb_hw, rhb_cp;  // layout of the shadow of rho_kb
+
+  __device__ void prepare(int4* tab) const {
+    for (int e = threadIdx.x; e < kt / 8; e += kThreads) {
+      const int tap = (8 * e) / cp_out, o0 = (8 * e) % cp_out;
+      tab[e] = make_int4(tap / nb, tap % nb, o0, tap < na * nb ? 1 : 0);
+    }
+  }
+  __device__ void load_resident(uint32_t sres, uint32_t bar) const {
+    mbar_expect_tx(bar, c.res_bytes);
+    bulk_g2s(sres, W, c.res_bytes, bar);
+  }
+  __device__ void phase_geo(int ph, int& ry, int& rx, int& dy0, int& dx0) const {
+    ry = ph / S;
+    rx = ph - ry * S;
+    const int i0 = (ry + pad) % S, j0 = (rx + pad) % S;
+    dy0 = (ry + pad - i0) / S;
+    dx0 = (rx + pad - j0) / S;
+  }
+  __device__ void load_stage(int tile, int chunk, uint32_t sst, uint32_t, const int4* tab) const {
+    const int ph = tile / tpp, R = (tile - ph * tpp) * kRows + (threadIdx.x & (kRows - 1));
+    int ry, rx, dy0, dx0;
+    phase_geo(ph, ry, rx, dy0, dx0);
+    const int PW = w / S, PP = (h / S) * PW;
+    const int b = R / PP, qq = R - b * PP, qy = qq / PW, qx = qq - qy * PW;
+    const bool row_ok = b < B;
+    const uint16_t* src_b = rh + (size_t)(row_ok ? b : 0) * RH + rh_off;
+    const int r = threadIdx.x & (kRows - 1);
+    const int k8_lo = chunk * KC / 8, k8_hi = min(kt, (chunk + 1) * KC) / 8;
+    for (int k8 = k8_lo + (threadIdx.x >> 7); k8 < k8_hi; k8 += kThreads / kRows) {
+      const int4 t = tab[k8];
+      const int y = qy + dy0 - t.x, x = qx + dx0 - t.y;
+      const bool ok = row_ok && t.w && y >= 0 && y < ho && x >= 0 && x < wo;
+      cp16(sst + chunk_off(r, k8 - k8_lo, kRows), ok ? src_b + ((size_t)(y * wo + x) * cp_out + t.z) : rh, ok);
+    }
+  }
+  __device__ void issue_mma(int tile, int chunk, uint32_t sres, uint32_t sst, uint32_t tmem) const {
+    const int ph = tile / tpp;
+    const uint32_t wb = sres + (uint32_t)(ph * nt * kt * 2);
+    const uint32_t id = idesc_bf16(kRows, nt);
+    const int s0 = chunk * KC / 16, ns = (min(kt, (chunk + 1) * KC) - chunk * KC) / 16;
+    for (int s = 0; s < ns; ++s)
+      mma_bf16(tmem, op_desc(sst, s, kRows), op_desc(wb, s0 + s, nt), id, (chunk > 0 || s > 0) ? 1u : 0u);
+  }
+  __device__ void epilogue(int tile, uint32_t tmem) const {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = warp & 3, half = warp >> 2;
+    const int ph = tile / tpp, R = (tile - ph * tpp) * kRows + q * 32 + lane;
+    int ry, rx, dy0, dx0;
+    phase_geo(ph, ry, rx, dy0, dx0);
+    const int PW = w / S, PP = (h / S) * PW;
+    const int b = R / PP, qq = R - b * PP, qy = qq / PW, qx = qq - qy * PW;
+    const int yy = S * qy + ry, xx = S * qx + rx, pix = yy * w + xx;
+    const bool row_ok = b < B;
+    const int prop = row_ok ? prop_of(P, b) : 0;
+    const int cols = nt / 2, lo = half * cols;
+    for (int c0 = lo; c0 < lo + cols; c0 += 8) {
+      float acc[8];
+      tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, acc);
+      if (!row_ok || c0 >= cin || c0 >= cp_in) continue;
+      float xv[8];
+      if (crown) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int ch = c0 + e;
+          if (ch >= cin) continue;
+          const int jn = ch * h * w + pix, jf = r_off_kb + jn;
+          const float r = crown_rho(P, b, jf, acc[e]);
+          rho[(size_t)b * P.N + jf] = r;
+          const int pos = rhb_conv ? (jn % rhb_hw) * rhb_cp + jn / rhb_hw : jn;
+          rh[(size_t)b * RH + rhb_off + pos] = bf16_bits(r);
+        }
+        continue;
+      }
+      if (kb == 0) {
+        // P0 (Eq. box_bounds_sol): x0 = u0 where g_0 >= 0, else l0; stored centred
+        float l0[8], u0[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+          if (c0 + e < cin) {
+            const int jn = (c0 + e) * h * w + pix;
+            l0[e] = P.l0[(size_t)prop * P.n0 + jn];
+            u0[e] = P.u0[(size_t)prop * P.n0 + jn];
+          }
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          xv[e] = 0.f;
+          if (c0 + e < cin) {
+            const float hw0 = 0.5f * (u0[e] - l0[e]);
+            xv[e] = acc[e] >= 0.f ? hw0 : -hw0;
+          }
+        }
+      } else {
+        int bb[8], jf[8];
+        bool on[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          on[e] = c0 + e < cin;
+          bb[e] = b;
+          jf[e] = r_off_kb + (c0 + e) * h * w + pix;
+        }
+        argmin8(P, rho, xB, bb, jf, on, acc, xv);
+      }
+      uint16_t* dst = xh + (size_t)b * XH + xh_off + (size_t)pix * cp_in + c0;
+      const uint4 pk = pack8(xv);
+      if (cp_in >= 8)
+        *reinterpret_cast<uint4*>(dst) = pk;
+      else
+        *reinterpret_cast<uint2*>(dst) = make_uint2(pk.x, pk.y);
+    }
+  }
+};
+
+// Forward FC of layer k: D[o, b] = sum_i W[o, i] x_{k-1}[b, i] (M = neurons,
+// N = subdomains); epilogue: Adam on rho_k.
+struct FcFwdOp {
+  static constexpr bool kStageBulk = true;
+  TcCommon c;
+  int n_mt, BN, KC;
+  uint32_t a_bytes;
+  const uint16_t* W;       // [n_mt][n_chunks][128 x KC]
+  int B, n_out, XH, xh_off, xh_len, RH, rh_off;
+  const uint16_t* xh;
+  uint16_t* rh;
+  Problem P;
+  int first, r_off;
+  const float* bias;
+  const float* c1;
+  AdamArgs ad;
+
+  __device__ void prepare(int4*) const {}
+  __device__ void load_resident(uint32_t, uint32_t) const {}
+  __device__ void load_stage(int tile, int chunk, uint32_t sst, uint32_t bar, const int4*) const {
+    const int mt = tile % n_mt, ntile = tile / n_mt;
+    if (threadIdx.x == 0) {
+      mbar_expect_tx(bar, a_bytes);
+      bulk_g2s(sst, W + ((size_t)mt * c.n_chunks + chunk) * kRows * KC, a_bytes, bar);
+    }
+    const int nk8 = KC / 8;
+    for (int idx = threadIdx.x; idx < BN * nk8; idx += kThreads) {
+      const int r = idx % BN, k8 = idx / BN;
+      const int b = ntile * BN + r, kk = chunk * KC + 8 * k8;
+      const bool ok = b < B && kk < xh_len;
+      cp16(sst + a_bytes + chunk_off(r, k8, BN), ok ? xh + (size_t)b * XH + xh_off + kk : xh, ok);
+    }
+  }
+  __device__ void issue_mma(int, int chunk, uint32_t, uint32_t sst, uint32_t tmem) const {
+    const uint32_t id = idesc_bf16(kRows, BN);
+    for (int s = 0; s < KC / 16; ++s)
+      mma_bf16(tmem, op_desc(sst, s, kRows), op_desc(sst + a_bytes, s, BN), id, (chunk > 0 || s > 0) ? 1u : 0u);
+  }
+  __device__ void epilogue(int tile, uint32_t tmem) const {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = warp & 3, half = warp >> 2;
+    const int mt = tile % n_mt, ntile = tile / n_mt;
+    const int o = mt * kRows + q * 32 + lane;
+    const int cols = BN / 2, lo = half * cols;
+    for (int c0 = lo; c0 < lo + cols; c0 += 8) {
+      float acc[8];
+      tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, acc);
+      if (o >= n_out) continue;
+      size_t j[8];
+      bool on[8];
+      float xa[8], rn[8];
+      const float bo = bias[o];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int b = ntile * BN + c0 + e;
+        on[e] = b < B && !P.empty[b];
+        j[e] = (size_t)b * P.N + r_off + o;
+        xa[e] = on[e] ? acc[e] + (first ? c1[(size_t)prop_of(P, b) * n_out + o] : bo) : 0.f;
+      }
+      adam8(ad, j, on, xa, rn);
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        if (on[e]) rh[(size_t)(ntile * BN + c0 + e) * RH + rh_off + o] = bf16_bits(rn[e]);
+    }
+  }
+};
+
+// Transposed FC of layer k: D[i, b] = sum_o W[o, i] rho_k[b, o] (M = inputs,
+// N = subdomains); epilogue: inner minimisation of layer k-1.
+struct FcTOp {
+  static constexpr bool kStageBulk = true;
+  TcCommon c;
+  int n_mt, BN, kt;
+  uint32_t a_bytes;
+  const uint16_t* W;       // [n_mt][128 x kt]
+  int B, n_in, XH, xh_off, RH, rh_off;
+  uint16_t* rh;                // read: shadow of rho_k; CROWN epilogue writes: shadow of rho_kb
+  uint16_t* xh;
+  Problem P;
+  int kb, r_off_kb;
+  float* xB;
+  float* rho;
+  int crown;
+  int rhb_off, rhb_conv, rhb_hw, rhb_cp;
+
+  __device__ void prepare(int4*) const {}
+  __device__ void load_resident(uint32_t, uint32_t) const {}
+  __device__ void load_stage(int tile, int, uint32_t sst, uint32_t bar, const int4*) const {
+    const int mt = tile % n_mt, ntile = tile / n_mt;
+    if (threadIdx.x == 0) {
+      mbar_expect_tx(bar, a_bytes);
+      bulk_g2s(sst, W + (size_t)mt * kRows * kt, a_bytes, bar);
+    }
+    const int nk8 = kt / 8;
+    for (int idx = threadIdx.x; idx < BN * nk8; idx += kThreads) {
+      const int r = idx % BN, k8 = idx / BN;
+      const int b = ntile * BN + r;
+      const bool ok = b < B;
+      cp16(sst + a_bytes + chunk_off(r, k8, BN), ok ? rh + (size_t)b * RH + rh_off + 8 * k8 : rh, ok);
+    }
+  }
+  __device__ void issue_mma(int, int, uint32_t, uint32_t sst, uint32_t tmem) const {
+    const uint32_t id = idesc_bf16(kRows, BN);
+    for (int s = 0; s < kt / 16; ++s)
+      mma_bf16(tmem, op_desc(sst, s, kRows), op_desc(sst + a_bytes, s, BN), id, s > 0 ? 1u : 0u);
+  }
+  __device__ void epilogue(int tile, uint32_t tmem) const {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = warp & 3, half = warp >> 2;
+    const int mt = tile % n_mt, ntile = tile / n_mt;
+    const int i = mt * kRows + q * 32 + lane;
+    const int cols = BN / 2, lo = half * cols;
+    for (int c0 = lo; c0 < lo + cols; c0 += 8) {
+      float acc[8];
+      tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, acc);
+      if (i >= n_in) continue;
+      int bb[8], jf[8];
+      bool on[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        bb[e] = ntile * BN + c0 + e;
+        on[e] = bb[e] < B;
+        jf[e] = r_off_kb + i;
+      }
+      if (crown) {
+        const int pos = rhb_conv ? (i % rhb_hw) * rhb_cp + i / rhb_hw : i;
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+          if (on[e]) {
+            const float r = crown_rho(P, bb[e], jf[e], acc[e]);
+            rho[(size_t)bb[e] * P.N + jf[e]] = r;
+            rh[(size_t)bb[e] * RH + rhb_off + pos] = bf16_bits(r);
+          }
+        continue;
+      }
+      float xv[8];
+      if (kb == 0) {
+        float l0[8], u0[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+          if (on[e]) {
+            const int prop = prop_of(P, bb[e]);
+            l0[e] = P.l0[(size_t)prop * P.n0 + i];
+            u0[e] = P.u0[(size_t)prop * P.n0 + i];
+          }
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          xv[e] = 0.f;
+          if (on[e]) {
+            const float hw0 = 0.5f * (u0[e] - l0[e]);
+            xv[e] = acc[e] >= 0.f ? hw0 : -hw0;
+          }
+        }
+      } else {
+        argmin8(P, rho, xB, bb, jf, on, acc, xv);
+      }
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        if (on[e]) xh[(size_t)bb[e] * XH + xh_off + i] = bf16_bits(xv[e]);
+    }
+  }
+};
+
+// ------------------------------------------------------------------ pipeline
+template <int N>
+__device__ __forceinline__ void cp_wait_pending() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Persistent tile loop of one CTA over stages s = (tile, K chunk) of its
+// tiles, NS-deep ring of shared-memory stage buffers: the gathers of stages
+// s+1 .. s+NS-1 are in flight while the MMAs and the epilogue of stage s run.
+// Every thread commits one cp.async group per stage (empty past the end), so
+// "all but the newest NS-2 groups done" means "stage s landed".
+template <class Op, int NS>
+__global__ void __launch_bounds__(kThreads, 3) tc_kernel(const Op op) {
+  extern __shared__ __align__(1024) uint8_t dyn_smem[];
+  __shared__ __align__(8) uint64_t bar_res;
+  __shared__ __align__(8) uint64_t bar_ld[NS];
+  __shared__ __align__(8) uint64_t bar_mma;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int4 tab[kTabMax];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t base = (smem_u32(dyn_smem) + 1023u) & ~1023u;
+  const uint32_t sres = base, sst0 = base + op.c.res_bytes;
+  const uint32_t b_res = smem_u32(&bar_res), b_mma = smem_u32(&bar_mma), b_ld0 = smem_u32(&bar_ld[0]);
+  if (tid == 0) {
+    mbar_init(b_res, 1);
+    for (int i = 0; i < NS; ++i) mbar_init(b_ld0 + 8 * i, 1);
+    mbar_init(b_mma, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(smem_u32(&tmem_slot), op.c.tmem_cols);
+    tmem_relinquish();
+  }
+  op.prepare(tab);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  const int my_tiles = (int)blockIdx.x < op.c.n_tiles ? (op.c.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int n_stages = my_tiles * op.c.n_chunks;
+  auto tile_of = [&](int st) { return (int)blockIdx.x + (st / op.c.n_chunks) * (int)gridDim.x; };
+  int issued = 0;        // stages whose loads were issued
+  auto issue = [&](int st) {  // loads of stage st (if it exists) + one commit group
+    if (st < n_stages) {
+      const int bi = st % NS;
+      op.load_stage(tile_of(st), st % op.c.n_chunks, sst0 + (uint32_t)bi * op.c.stage_bytes, b_ld0 + 8 * bi, tab);
+      issued = st + 1;
+    }
+    cp_commit();
+  };
+  if (tid == 0 && op.c.res_bytes && n_stages > 0) op.load_resident(sres, b_res);
+  for (int p = 0; p < NS - 1; ++p) issue(p);
+  int bulk_waited = 0;  // thread 0: bulk-loaded stages already waited on
+  int bad = 0;
+  for (int s = 0; s < n_stages; ++s) {
+    const int bi = s % NS;
+    const int tile = tile_of(s), chunk = s % op.c.n_chunks;
+    const uint32_t sst = sst0 + (uint32_t)bi * op.c.stage_bytes;
+    cp_wait_pending<NS - 2>();
+    fence_proxy_async();
+    if (__syncthreads_or(bad)) break;
+    if (tid == 0) {
+      bool ready = true;
+      if (s == 0 && op.c.res_bytes) ready = mbar_wait(b_res, 0);
+      if (Op::kStageBulk && ready) {
+        ready = mbar_wait(b_ld0 + 8 * bi, (uint32_t)((s / NS) & 1));
+        if (ready) bulk_waited = s + 1;
+      }
+      if (ready) {
+        tc_fence_after();
+        op.issue_mma(tile, chunk, sres, sst, tmem);
+      } else {
+        bad = 1;
+        atomicCAS(op.c.status, 0, (int)LD_ERR_TIMEOUT);
+      }
+      mma_commit(b_mma);  // with no MMA issued this arrives at once
+    }
+    // the buffer of stage s+NS-1 was last read by the MMAs of stage s-1 (waited below, one iteration ago)
+    issue(s + NS - 1);
+    if (!mbar_wait(b_mma, (uint32_t)(s & 1))) {
+      bad = 1;
+      atomicCAS(op.c.status, 0, (int)LD_ERR_TIMEOUT);
+    }
+    tc_fence_after();
+    if (!bad && chunk == op.c.n_chunks - 1) op.epilogue(tile, tmem);
+    tc_fence_before();
+  }
+  cp_wait_pending<0>();
+  // bulk copies issued for stages that never ran must land before the CTA exits
+  if (Op::kStageBulk && tid == 0)
+    for (int st = bulk_waited; st < issued; ++st)
+      if (!mbar_wait(b_ld0 + 8 * (st % NS), (uint32_t)((st / NS) & 1))) {
+        atomicCAS(op.c.status, 0, (int)LD_ERR_TIMEOUT);
+        break;
+      }
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, op.c.tmem_cols);
+  }
+}
+
+// rho (FP32, [B, N]) -> BF16 shadows of rho_1..rho_{n-1}.
+struct ShadowLayer {
+  int conv, r_off, n, hw, cp_out, rh_off;
+};
+struct ShadowPlan {
+  int n_layers;
+  ShadowLayer S[kMaxLayers];
+};
+__global__ void shadow_rho_kernel(ShadowPlan sp, int B, int N, int RH, const float* __restrict__ rho, uint16_t* rh) {
+  const size_t total = (size_t)B * N;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(e / N), j = (int)(e % N);
+    for (int k = 0; k < sp.n_layers; ++k) {
+      const ShadowLayer& L = sp.S[k];
+      if (j < L.r_off || j >= L.r_off + L.n) continue;
+      const int jj = j - L.r_off;
+      const int pos = L.conv ? (jj % L.hw) * L.cp_out + jj / L.hw : jj;
+      rh[(size_t)b * RH + L.rh_off + pos] = bf16_bits(rho[e]);
+    }
+  }
+}
+
+// c1[p, j] = b_1[o(j)] + (W_1 c_0)[j], c_0 = l_0 + (u_0 - l_0) / 2 (FP32).
+__global__ void centre_kernel(LayerDev L, int n_props, int n0, const float* __restrict__ l0,
+                              const float* __restrict__ u0, float* c1) {
+  const int n_out = L.n_out;
+  const size_t total = (size_t)n_props * n_out;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int p = (int)(e / n_out), j = (int)(e % n_out);
+    const float* lp = l0 + (size_t)p * n0;
+    const float* up = u0 + (size_t)p * n0;
+    float acc = 0.f;
+    if (L.kind == LD_LAYER_FC) {
+      for (int i = 0; i < L.n_in; ++i) acc = fmaf(L.W[(size_t)j * L.n_in + i], lp[i] + 0.5f * (up[i] - lp[i]), acc);
+      acc += L.b[j];
+    } else {
+      const int hw = L.ho * L.wo, o = j / hw, pos = j % hw, yo = pos / L.wo, xo = pos % L.wo;
+      for (int c = 0; c < L.cin; ++c)
+        for (int i = 0; i < L.kh; ++i) {
+          const int yy = yo * L.stride - L.pad + i;
+          if (yy < 0 || yy >= L.h) continue;
+          for (int jx = 0; jx < L.kw; ++jx) {
+            const int xx = xo * L.stride - L.pad + jx;
+            if (xx < 0 || xx >= L.w) continue;
+            const int ii = (c * L.h + yy) * L.w + xx;
+            acc = fmaf(L.W[((size_t)(o * L.cin + c) * L.kh + i) * L.kw + jx], lp[ii] + 0.5f * (up[ii] - lp[ii]), acc);
+          }
+        }
+      acc += L.b[o];
+    }
+    c1[e] = acc;
+  }
+}
+
+// ------------------------------------------------------------------ host side
+inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// FP32 -> BF16 bits, round to nearest even.
+uint16_t host_bf16(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)((u >> 16) | ((u & 0xffffu) ? 0x40u : 0u));
+  u += 0x7fffu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+// Element (r, k) of an R-row canonical tile (see chunk_off).
+inline size_t canon(int r, int k, int R) { return ((size_t)(k / 8) * R + r) * 8 + (k % 8); }
+
+uint32_t tmem_cols_for(int n) {
+  uint32_t c = 32;
+  while ((int)c < n) c <<= 1;
+  return c;
+}
+
+// Dynamic shared memory for a launch: operands + 1 KB alignment slack, and
+// at least enough that no more CTAs fit on an SM than TMEM columns allow.
+size_t launch_smem(size_t need, uint32_t tmem_cols) {
+  size_t s = need + 1024;
+  const int max_ctas = 512 / (int)tmem_cols;
+  if (max_ctas < 8) {
+    const size_t floor_bytes = (size_t)228 * 1024 / (size_t)(max_ctas + 1) + 1024;
+    if (s < floor_bytes) s = floor_bytes;
+  }
+  return s;
+}
+
+// Resident CTAs per SM from the kernel's registers and shared memory, the
+// thread limit and the TMEM columns (512 per SM).
+int ctas_per_sm(const void* func, size_t dyn_smem, uint32_t tmem_cols) {
+  static int regs_sm = 0, smem_sm = 0, smem_rsv = 0, thr_sm = 0;
+  if (!regs_sm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+  }
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, func) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  const int per_warp = (fa.numRegs * 32 + 255) / 256 * 256;
+  int n = regs_sm / (per_warp * (kThreads / 32));
+  const int by_smem = (int)((size_t)smem_sm / (dyn_smem + fa.sharedSizeBytes + (size_t)smem_rsv));
+  if (by_smem < n) n = by_smem;
+  if (thr_sm / kThreads < n) n = thr_sm / kThreads;
+  if ((int)(512 / tmem_cols) < n) n = (int)(512 / tmem_cols);
+  return n < 1 ? 1 : n;
+}
+
+template <class Op, int NS>
+cudaError_t launch_ns(const Op& op, size_t smem, int n_sm, cudaStream_t s) {
+  static size_t attr_bytes = 0;  // dynamic shared memory opted in for this instantiation
+  if (smem > attr_bytes) {
+    if (cudaFuncSetAttribute(tc_kernel<Op, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return cudaGetLastError();
+    attr_bytes = smem;
+  }
+  const int per_sm = ctas_per_sm(reinterpret_cast<const void*>(tc_kernel<Op, NS>), smem, op.c.tmem_cols);
+  int grid = n_sm * per_sm;
+  if (grid > op.c.n_tiles) grid = op.c.n_tiles;
+  count_launch();
+  tc_kernel<Op, NS><<<grid, kThreads, smem, s>>>(op);
+  return cudaGetLastError();
+}
+
+// Three stage buffers unless two keep more CTAs resident on an SM.
+template <class Op>
+cudaError_t launch_op(const Op& op, int n_sm, cudaStream_t s) {
+  if (op.c.n_tiles <= 0) return cudaSuccess;
+  const size_t m3 = launch_smem((size_t)op.c.res_bytes + 3 * (size_t)op.c.stage_bytes, op.c.tmem_cols);
+  const size_t m2 = launch_smem((size_t)op.c.res_bytes + 2 * (size_t)op.c.stage_bytes, op.c.tmem_cols);
+  const int o3 = m3 <= kSmemBudget
+                     ? ctas_per_sm(reinterpret_cast<const void*>(tc_kernel<Op, 3>), m3, op.c.tmem_cols) : 0;
+  const int o2 = ctas_per_sm(reinterpret_cast<const void*>(tc_kernel<Op, 2>), m2, op.c.tmem_cols);
+  if (o3 >= o2) return launch_ns<Op, 3>(op, m3, n_sm, s);
+  return launch_ns<Op, 2>(op, m2, n_sm, s);
+}
+
+AdamArgs adam_args(const TcState& S, AdamStep st) {
+  return AdamArgs{S.xB, S.rho, S.m, S.v, S.beta1, S.beta2, S.eps, st};
+}
+
+// Subdomains per FC tile: the largest of 128, 64, 32, 16 that still gives
+// about one tile per SM.
+int fc_bn(int n_mt, int B, int n_sm) {
+  int bn = 128;
+  while (bn > 16 && n_mt * ((B + bn - 1) / bn) < n_sm) bn /= 2;
+  return bn;
+}
+
+}  // namespace
+
+ld_status build_tc_net(const std::vector<LayerDev>& Ls, TcNet* out) {
+  TcNet t;
+  t.n = (int)Ls.size();
+  const int n = t.n;
+  if (n < 2 || n > kMaxLayers) return LD_ERR_UNSUPPORTED;
+  std::vector<std::vector<float>> W(n);
+  for (int k = 0; k < n; ++k) {
+    const LayerDev& L = Ls[k];
+    const size_t nw = L.kind == LD_LAYER_FC ? (size_t)L.n_out * L.n_in : (size_t)L.cout * L.cin * L.kh * L.kw;
+    W[k].resize(nw);
+    if (cudaMemcpy(W[k].data(), L.W, 4 * nw, cudaMemcpyDeviceToHost) != cudaSuccess) return LD_ERR_CUDA;
+  }
+  std::vector<std::vector<uint16_t>> wf(n), wt(n);
+  int xh = 0, rh = 0;
+  for (int k = 1; k <= n - 1; ++k) {
+    const LayerDev& L = Ls[k - 1];
+    TcLayer& T = t.T[k - 1];
+    std::memset(&T, 0, sizeof(T));
+    T.kind = L.kind;
+    const std::vector<float>& w = W[k - 1];
+    if (L.kind == LD_LAYER_CONV) {
+      const int S = L.stride;
+      if (!(S == 1 || S == 2) || L.h % S || L.w % S || L.cout > 256 || L.cin > 256) return LD_ERR_UNSUPPORTED;
+      T.cp_in = L.cin <= 4 ? 4 : round_up(L.cin, 8);
+      T.cp_out = round_up(L.cout, 8);
+      T.xh_len = round_up(L.h * L.w * T.cp_in, 8);
+      T.rh_len = L.ho * L.wo * T.cp_out;
+      // forward: B operand [nf x kf], K = tap * cp_in + c
+      T.nf = round_up(L.cout, 16);
+      T.kf = round_up(L.kh * L.kw * T.cp_in, 16);
+      const int pieces = T.cp_in >= 8 ? T.kf / 8 : T.kf / 4;
+      if (pieces > kTabMax) return LD_ERR_UNSUPPORTED;
+      wf[k - 1].assign((size_t)T.nf * T.kf, 0);
+      for (int o = 0; o < L.cout; ++o)
+        for (int c = 0; c < L.cin; ++c)
+          for (int i = 0; i < L.kh; ++i)
+            for (int j = 0; j < L.kw; ++j)
+              wf[k - 1][canon(o, (i * L.kw + j) * T.cp_in + c, T.nf)] =
+                  host_bf16(w[((size_t)(o * L.cin + c) * L.kh + i) * L.kw + j]);
+      // transposed: per stride phase, B operand [nt x kt], K = (a * nb + bb) * cp_out + o
+      T.nt = round_up(L.cin, 16);
+      T.n_phase = S * S;
+      T.na = (L.kh + S - 1) / S;
+      T.nb = (L.kw + S - 1) / S;
+      T.kt = round_up(T.na * T.nb * T.cp_out, 16);
+      if (T.kt / 8 > kTabMax) return LD_ERR_UNSUPPORTED;
+      const size_t per = (size_t)T.nt * T.kt;
+      wt[k - 1].assign(per * T.n_phase, 0);
+      for (int ph = 0; ph < T.n_phase; ++ph) {
+        const int ry = ph / S, rx = ph % S;
+        const int i0 = (ry + L.pad) % S, j0 = (rx + L.pad) % S;
+        for (int a = 0; a < T.na; ++a)
+          for (int bb = 0; bb < T.nb; ++bb) {
+            const int i = i0 + S * a, j = j0 + S * bb;
+            if (i >= L.kh || j >= L.kw) continue;
+            for (int o = 0; o < L.cout; ++o)
+              for (int c = 0; c < L.cin; ++c)
+                wt[k - 1][per * ph + canon(c, (a * T.nb + bb) * T.cp_out + o, T.nt)] =
+                    host_bf16(w[((size_t)(o * L.cin + c) * L.kh + i) * L.kw + j]);
+          }
+      }
+      // shared memory: forward = weights + 2 stages of 128 x kf; transposed = all phases + 2 x 128 x kt
+      if ((size_t)2 * T.nf * T.kf + (size_t)4 * kRows * T.kf + 2048 > (size_t)200 * 1024) return LD_ERR_UNSUPPORTED;
+      if ((size_t)2 * per * T.n_phase + (size_t)4 * kRows * T.kt + 2048 > (size_t)200 * 1024) return LD_ERR_UNSUPPORTED;
+    } else {
+      T.xh_len = round_up(L.n_in, 8);
+      T.rh_len = round_up(L.n_out, 16);
+      T.fc_kc = kFcKC;
+      T.fc_nkc = (L.n_in + kFcKC - 1) / kFcKC;
+      T.fc_nmt = (L.n_out + kRows - 1) / kRows;
+      wf[k - 1].assign((size_t)T.fc_nmt * T.fc_nkc * kRows * kFcKC, 0);
+      for (int o = 0; o < L.n_out; ++o)
+        for (int i = 0; i < L.n_in; ++i) {
+          const int mt = o / kRows, kc = i / kFcKC;
+          wf[k - 1][((size_t)mt * T.fc_nkc + kc) * kRows * kFcKC + canon(o % kRows, i % kFcKC, kRows)] =
+              host_bf16(w[(size_t)o * L.n_in + i]);
+        }
+      T.kt = T.rh_len;
+      T.fc_nmt_t = (L.n_in + kRows - 1) / kRows;
+      wt[k - 1].assign((size_t)T.fc_nmt_t * kRows * T.kt, 0);
+      for (int o = 0; o < L.n_out; ++o)
+        for (int i = 0; i < L.n_in; ++i)
+          wt[k - 1][(size_t)(i / kRows) * kRows * T.kt + canon(i % kRows, o, kRows)] =
+              host_bf16(w[(size_t)o * L.n_in + i]);
+    }
+    T.xh_off = xh;
+    T.rh_off = rh;
+    xh += round_up(T.xh_len, 8);
+    rh += round_up(T.rh_len, 8);
+  }
+  t.XH = xh;
+  t.RH = rh;
+  t.n1 = Ls[0].n_out;
+  // one allocation, each block 1 KB aligned (bulk copies need 16 B)
+  std::vector<size_t> off_f(n, 0), off_t(n, 0);
+  size_t total = 0;
+  for (int k = 0; k < n - 1; ++k) {
+    off_f[k] = total;
+    total += (wf[k].size() * 2 + 1023) / 1024 * 1024;
+    off_t[k] = total;
+    total += (wt[k].size() * 2 + 1023) / 1024 * 1024;
+  }
+  if (total == 0) return LD_ERR_UNSUPPORTED;
+  void* d = nullptr;
+  if (cudaMalloc(&d, total) != cudaSuccess) {
+    cudaGetLastError();
+    return LD_ERR_NOMEM;
+  }
+  char* base = static_cast<char*>(d);
+  for (int k = 0; k < n - 1; ++k) {
+    if (cudaMemcpy(base + off_f[k], wf[k].data(), wf[k].size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(base + off_t[k], wt[k].data(), wt[k].size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaFree(d);
+      return LD_ERR_CUDA;
+    }
+    t.T[k].Wf = reinterpret_cast<const uint16_t*>(base + off_f[k]);
+    t.T[k].Wt = reinterpret_cast<const uint16_t*>(base + off_t[k]);
+  }
+  t.d_w = static_cast<uint16_t*>(d);
+  *out = t;
+  return LD_OK;
+}
+
+void free_tc_net(TcNet* t) {
+  if (t->d_w) cudaFree(t->d_w);
+  t->d_w = nullptr;
+  t->n = 0;
+}
+
+void launch_tc_shadow_rho(const TcNet& t, const std::vector<LayerDev>& Ls, const Problem& P, const TcState& S,
+                          int k_lo, int k_hi, cudaStream_t s) {
+  ShadowPlan sp{};
+  sp.n_layers = 0;
+  for (int k = k_lo; k <= k_hi && k <= t.n - 1; ++k) {
+    const LayerDev& L = Ls[k - 1];
+    const TcLayer& T = t.T[k - 1];
+    sp.S[sp.n_layers++] = ShadowLayer{L.kind == LD_LAYER_CONV ? 1 : 0, L.r_out_off, L.n_out,
+                                      L.kind == LD_LAYER_CONV ? L.ho * L.wo : 1, T.cp_out, T.rh_off};
+  }
+  if (sp.n_layers == 0) return;
+  const size_t total = (size_t)P.B * P.N;
+  int grid = (int)((total + 255) / 256);
+  if (grid > 65535 * 8) grid = 65535 * 8;
+  if (grid < 1) grid = 1;
+  count_launch();
+  shadow_rho_kernel<<<grid, 256, 0, s>>>(sp, P.B, P.N, t.RH, S.rho, S.rh);
+}
+
+void launch_tc_centre(const TcNet& t, const LayerDev& L1, const Problem& P, const TcState& S, cudaStream_t s) {
+  const size_t total = (size_t)P.n_props * t.n1;
+  count_launch();
+  centre_kernel<<<(int)((total + 255) / 256), 256, 0, s>>>(L1, P.n_props, P.n0, P.l0, P.u0, S.c1);
+}
+
+void launch_tc_transposed(const TcNet& t, const std::vector<LayerDev>& Ls, int k, const Problem& P,
+                          const TcState& S, int n_sm, cudaStream_t s, int crown) {
+  const LayerDev& L = Ls[k - 1];
+  const TcLayer& T = t.T[k - 1];
+  const int kb = k - 1;
+  const int r_off_kb = kb >= 1 ? Ls[kb - 1].r_out_off : 0;
+  if (crown && kb < 1) return;
+  // where the CROWN epilogue puts the shadow of rho_kb (layout read by layer kb's transposed pass)
+  int rhb_off = 0, rhb_conv = 0, rhb_hw = 1, rhb_cp = 0;
+  if (kb >= 1) {
+    const LayerDev& Lb = Ls[kb - 1];
+    rhb_off = t.T[kb - 1].rh_off;
+    rhb_conv = Lb.kind == LD_LAYER_CONV ? 1 : 0;
+    rhb_hw = rhb_conv ? Lb.ho * Lb.wo : 1;
+    rhb_cp = t.T[kb - 1].cp_out;
+  }
+  if (L.kind == LD_LAYER_CONV) {
+    ConvTOp op{};
+    const int PP = (L.h / L.stride) * (L.w / L.stride);
+    op.tpp = (int)(((size_t)P.B * PP + kRows - 1) / kRows);
+    op.c.n_tiles = op.tpp * T.n_phase;
+    op.KC = T.kt < kConvKC ? T.kt : kConvKC;
+    op.c.n_chunks = (T.kt + op.KC - 1) / op.KC;
+    op.c.res_bytes = (uint32_t)(2 * T.nt * T.kt * T.n_phase);
+    op.c.stage_bytes = (uint32_t)(2 * kRows * op.KC);
+    op.c.tmem_cols = tmem_cols_for(T.nt);
+    op.c.status = S.status;
+    op.nt = T.nt;
+    op.kt = T.kt;
+    op.n_phase = T.n_phase;
+    op.na = T.na;
+    op.nb = T.nb;
+    op.W = T.Wt;
+    op.B = P.B;
+    op.cin = L.cin;
+    op.h = L.h;
+    op.w = L.w;
+    op.ho = L.ho;
+    op.wo = L.wo;
+    op.S = L.stride;
+    op.pad = L.pad;
+    op.cp_in = T.cp_in;
+    op.cp_out = T.cp_out;
+    op.XH = t.XH;
+    op.xh_off = T.xh_off;
+    op.RH = t.RH;
+    op.rh_off = T.rh_off;
+    op.rh = S.rh;
+    op.xh = S.xh;
+    op.P = P;
+    op.kb = kb;
+    op.r_off_kb = r_off_kb;
+    op.xB = S.xB;
+    op.rho = S.rho;
+    op.crown = crown;
+    op.rhb_off = rhb_off;
+    op.rhb_conv = rhb_conv;
+    op.rhb_hw = rhb_hw;
+    op.rhb_cp = rhb_cp;
+    launch_op(op, n_sm, s);
+    return;
+  }
+  FcTOp op{};
+  op.n_mt = T.fc_nmt_t;
+  op.BN = fc_bn(op.n_mt, P.B, n_sm);
+  op.kt = T.kt;
+  op.a_bytes = (uint32_t)(2 * kRows * T.kt);
+  op.c.n_tiles = op.n_mt * ((P.B + op.BN - 1) / op.BN);
+  op.c.n_chunks = 1;
+  op.c.res_bytes = 0;
+  op.c.stage_bytes = op.a_bytes + (uint32_t)(2 * op.BN * T.kt);
+  op.c.tmem_cols = tmem_cols_for(op.BN);
+  op.c.status = S.status;
+  op.W = T.Wt;
+  op.B = P.B;
+  op.n_in = L.n_in;
+  op.XH = t.XH;
+  op.xh_off = T.xh_off;
+  op.RH = t.RH;
+  op.rh_off = T.rh_off;
+  op.rh = S.rh;
+  op.xh = S.xh;
+  op.P = P;
+  op.kb = kb;
+  op.r_off_kb = r_off_kb;
+  op.xB = S.xB;
+  op.rho = S.rho;
+  op.crown = crown;
+  op.rhb_off = rhb_off;
+  op.rhb_conv = rhb_conv;
+  op.rhb_hw = rhb_hw;
+  op.rhb_cp = rhb_cp;
+  launch_op(op, n_sm, s);
+}
+
+void launch_tc_forward(const TcNet& t, const std::vector<LayerDev>& Ls, int k, const Problem& P, const TcState& S,
+                       AdamStep st, int n_sm, cudaStream_t s) {
+  const LayerDev& L = Ls[k - 1];
+  const TcLayer& T = t.T[k - 1];
+  if (L.kind == LD_LAYER_CONV) {
+    ConvFwdOp op{};
+    op.c.n_tiles = (int)(((size_t)P.B * L.ho * L.wo + kRows - 1) / kRows);
+    op.KC = T.kf < kConvKC ? T.kf : kConvKC;
+    op.c.n_chunks = (T.kf + op.KC - 1) / op.KC;
+    op.c.res_bytes = (uint32_t)(2 * T.nf * T.kf);
+    op.c.stage_bytes = (uint32_t)(2 * kRows * op.KC);
+    op.c.tmem_cols = tmem_cols_for(T.nf);
+    op.c.status = S.status;
+    op.nf = T.nf;
+    op.kf = T.kf;
+    op.W = T.Wf;
+    op.B = P.B;
+    op.h = L.h;
+    op.w = L.w;
+    op.cout = L.cout;
+    op.ho = L.ho;
+    op.wo = L.wo;
+    op.kw = L.kw;
+    op.kh = L.kh;
+    op.S = L.stride;
+    op.pad = L.pad;
+    op.cp_in = T.cp_in;
+    op.cp_out = T.cp_out;
+    op.XH = t.XH;
+    op.xh_off = T.xh_off;
+    op.RH = t.RH;
+    op.rh_off = T.rh_off;
+    op.xh = S.xh;
+    op.rh = S.rh;
+    op.P = P;
+    op.first = k == 1 ? 1 : 0;
+    op.r_off = L.r_out_off;
+    op.bias = L.b;
+    op.c1 = S.c1;
+    op.ad = adam_args(S, st);
+    launch_op(op, n_sm, s);
+    return;
+  }
+  FcFwdOp op{};
+  op.n_mt = T.fc_nmt;
+  op.BN = fc_bn(op.n_mt, P.B, n_sm);
+  op.KC = T.fc_kc;
+  op.a_bytes = (uint32_t)(2 * kRows * T.fc_kc);
+  op.c.n_tiles = op.n_mt * ((P.B + op.BN - 1) / op.BN);
+  op.c.n_chunks = T.fc_nkc;
+  op.c.res_bytes = 0;
+  op.c.stage_bytes = op.a_bytes + (uint32_t)(2 * op.BN * T.fc_kc);
+  op.c.tmem_cols = tmem_cols_for(op.BN);
+  op.c.status = S.status;
+  op.W = T.Wf;
+  op.B = P.B;
+  op.n_out = L.n_out;
+  op.XH = t.XH;
+  op.xh_off = T.xh_off;
+  op.xh_len = T.xh_len;
+  op.RH = t.RH;
+  op.rh_off = T.rh_off;
+  op.xh = S.xh;
+  op.rh = S.rh;
+  op.P = P;
+  op.first = k == 1 ? 1 : 0;
+  op.r_off = L.r_out_off;
+  op.bias = L.b;
+  op.c1 = S.c1;
+  op.ad = adam_args(S, st);
+  launch_op(op, n_sm, s);
+}
+
+}  // namespace ld

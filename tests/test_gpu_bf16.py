@@ -1,0 +1,151 @@
+"""GPU: the BF16 tensor-core iterations (precision "bf16").
+
+The transposed and forward passes of the Adam iterations run as BF16 GEMMs
+with FP32 accumulation; rho, the Adam moments and x_hat_B stay FP32 and the
+returned bound is the FP64 evaluation at the final rho (sound for any rho).
+
+Checks:
+  * short runs against the oracle with the same operand rounding
+    (oracle.BF16Passes: BF16 weights and operands, exact sums)   1e-5
+  * long runs against that oracle                                 FP32 chaos floor
+  * the BF16-vs-FP32 bound gap on the Base / Deep / Wide nets     <= 1e-3 relative
+  * soundness on tiny nets: never above the Planet LP optimum nor the exact minimum
+  * empty subdomains, bitwise resume, the full-size Wide call (2048 subdomains)
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import lp
+from paper_2104_06718_gb300 import binding as ldb
+from paper_2104_06718_gb300 import synth
+from helpers import conv_problem, oracle_lists, outward_f32, tiny_problem
+
+pytestmark = pytest.mark.gpu
+
+BF16 = ldb.Options(precision="bf16")
+FULL_RUN_MAX = 1e-3
+FULL_RUN_MEDIAN = 3e-4
+GAP_MAX = 1e-3        # BF16 vs FP32 iterations, same problem, same T
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2104_06718_gb300 import build
+    build.build()
+    ldb.load_library()
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return np.abs(a - b) / np.maximum(np.abs(b), 1.0)
+
+
+def run_gpu(pb, T, opts):
+    net = ldb.Net(pb["specs"])
+    return ldb.ld_bound(net, pb["l0"], pb["u0"], pb["lbk"], pb["ubk"], pb["prop"], pb["masks"], n_iters=T,
+                        opts=opts).cpu().numpy()
+
+
+def run_oracle(pb, T, operands="bf16", rows=None):
+    prop = pb["prop"] if rows is None else pb["prop"][rows]
+    masks = pb["masks"] if rows is None else pb["masks"][rows]
+    ref, _, _ = oracle.ld_bound(pb["net"], pb["l0"].astype(np.float64), pb["u0"].astype(np.float64),
+                                pb["lbk"].astype(np.float64), pb["ubk"].astype(np.float64), prop, masks, T,
+                                operands=operands)
+    return ref
+
+
+@pytest.mark.parametrize("name", ["base", "wide", "deep"])
+@pytest.mark.parametrize("T", [1, 3])
+def test_bf16_short_runs_match_bf16_oracle(name, T):
+    pb = conv_problem(name, 16, depth=(0, 8), block=8)
+    out = run_gpu(pb, T, BF16)
+    ref = run_oracle(pb, T)
+    fin = np.isfinite(ref)
+    assert np.array_equal(np.isfinite(out), fin)
+    assert np.max(rel(out[fin], ref[fin])) < 1e-5
+
+
+@pytest.mark.parametrize("name,B,T", [("base", 24, 100), ("deep", 12, 100), ("wide", 8, 60)])
+def test_bf16_full_runs_match_bf16_oracle_and_fp32(name, B, T):
+    pb = conv_problem(name, B, depth=(0, 8), block=5)
+    out = run_gpu(pb, T, BF16)
+    ref = run_oracle(pb, T)
+    fin = np.isfinite(ref)
+    assert np.array_equal(np.isfinite(out), fin)
+    r = rel(out[fin], ref[fin])
+    assert np.max(r) < FULL_RUN_MAX and np.median(r) < FULL_RUN_MEDIAN
+    f32 = run_gpu(pb, T, ldb.Options(engine="layerwise"))
+    assert np.max(rel(out[fin], f32[fin])) < GAP_MAX
+
+
+def test_bf16_tiny_nets_are_sound_and_match():
+    """FC-only nets (the FC tensor-core kernels): against the BF16 oracle,
+    and never above the LP optimum nor the exact minimum (enumeration)."""
+    for i in range(6):
+        specs, on, l0, u0, lb, ub = tiny_problem(i)
+        flat_l = np.concatenate([lb[k] for k in range(1, on.n)], axis=1)
+        flat_u = np.concatenate([ub[k] for k in range(1, on.n)], axis=1)
+        lbk, ubk = outward_f32(flat_l, flat_u)
+        pb = dict(specs=specs, net=on, l0=l0.astype(np.float32), u0=u0.astype(np.float32), lbk=lbk, ubk=ubk,
+                  prop=np.zeros(1, np.int32), masks=np.zeros((1, lbk.shape[1]), np.int8), B=1)
+        out = run_gpu(pb, 200, BF16)
+        ref = run_oracle(pb, 200)
+        assert rel(out[0], ref[0]) < FULL_RUN_MAX
+        L0, U0, lbs, ubs, _ = oracle_lists(on, pb)
+        lbs1 = [None] + [x[0] for x in lbs[1:]]
+        ubs1 = [None] + [x[0] for x in ubs[1:]]
+        p = lp.planet_lp(on, L0[0], U0[0], lbs1, ubs1)
+        assert out[0] <= p.p_star + 1e-9 * max(1.0, abs(p.p_star))
+        ex = lp.exact_min_milp(on, L0[0], U0[0], lbs1, ubs1)
+        assert out[0] <= ex + 1e-9 * max(1.0, abs(ex))
+
+
+def test_bf16_empty_subdomains_and_resume():
+    pb = conv_problem("base", 16, depth=(0, 8), block=1)
+    masks = pb["masks"].copy()
+    # subdomain 3: a ReLU forced both passing (+1) and, through its bounds, blocking -> empty
+    amb = np.nonzero((pb["lbk"][0] < 0) & (pb["ubk"][0] > 0))[0]
+    blk = np.nonzero(pb["ubk"][0] < 0)[0]
+    masks[3, blk[0]] = 1
+    pb = dict(pb, masks=masks)
+    net = ldb.Net(pb["specs"])
+    args = (pb["l0"], pb["u0"], pb["lbk"], pb["ubk"], pb["prop"], pb["masks"])
+    out_a, rho_a = ldb.ld_bound(net, *args, n_iters=20, return_rho=True, opts=BF16)
+    assert np.isinf(out_a[3].item()) and np.isfinite(np.delete(out_a.cpu().numpy(), 3)).all()
+    assert amb.size > 0
+    B, N = pb["B"], pb["lbk"].shape[1]
+    mv = torch.zeros((2, B, N), dtype=torch.float32, device="cuda")
+    o1 = ldb.Options(precision="bf16", t_offset=0, t_total=20)
+    _, rho_1 = ldb.ld_bound(net, *args, n_iters=12, opts=o1, return_rho=True, adam_mv=mv)
+    o2 = ldb.Options(precision="bf16", t_offset=12, t_total=20, init="given")
+    out_b, rho_b = ldb.ld_bound(net, *args, n_iters=8, opts=o2, rho_in=rho_1, return_rho=True, adam_mv=mv)
+    assert torch.equal(rho_a, rho_b)
+    assert torch.equal(out_a, out_b)
+
+
+def test_bf16_wide_2048_sampled_against_oracle():
+    """The full-size Wide call of the benchmark (2048 subdomains, split depth
+    0-20, 100 iterations) in BF16; sampled subdomains against the BF16 oracle
+    and the FP32 run; the root bound below network evaluations."""
+    pb = conv_problem("wide", 2048, depth=(0, 20), block=7)
+    out = run_gpu(pb, 100, BF16)
+    rows = np.array([0, 1, 777, 2047])
+    ref = run_oracle(pb, 100, rows=rows)
+    fin = np.isfinite(ref)
+    assert np.array_equal(np.isfinite(out[rows]), fin)
+    assert np.max(rel(out[rows][fin], ref[fin])) < FULL_RUN_MAX
+    f32 = run_gpu(pb, 100, ldb.Options(engine="layerwise"))
+    both = np.isfinite(out) & np.isfinite(f32)
+    assert np.array_equal(np.isfinite(out), np.isfinite(f32))
+    # over 2048 trajectories the gap is a distribution (FP32 itself spreads
+    # around the FP64 oracle the same way): median, 99th percentile, max
+    gap = rel(out[both], f32[both])
+    assert np.median(gap) < FULL_RUN_MEDIAN and np.percentile(gap, 99) < GAP_MAX and gap.max() < 2 * GAP_MAX
+    xs = synth.random_box_points(pb["l0"][0], pb["u0"][0], 256, seed=9)
+    assert out[0] <= pb["net"].evaluate(xs).min()

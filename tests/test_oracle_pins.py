@@ -509,3 +509,68 @@ def test_dual_value_is_the_exact_minimum(i):
     rr = [None] + [r.astype(np.float64) for r in synth.random_duals([L[1].shape[1], L[2].shape[1]], 1, seed=3)]
     s2 = oracle.inner_minimisation(net, l0, u0, L, U, rr)
     assert abs(s2.q_point[0] - s2.q[0]) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# BF16 operand emulation (the precision of the tensor-core passes)
+# --------------------------------------------------------------------------
+
+def test_round_bf16_matches_torch_bfloat16():
+    """round_bf16 is round-to-nearest-even to bfloat16 (the library conversion)."""
+    rng = np.random.default_rng(11)
+    a = np.concatenate([rng.standard_normal(20000) * 10.0 ** rng.integers(-6, 6, 20000),
+                        [0.0, -0.0, 1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, 65504.0, 1e-30]])
+    a = a.astype(np.float32).astype(np.float64)
+    ref = torch.tensor(a, dtype=torch.float32).to(torch.bfloat16).double().numpy()
+    assert np.array_equal(oracle.round_bf16(a), ref)
+
+
+def _bf16_exact_net():
+    """A small conv + FC net whose weights are exactly representable in bf16."""
+    rng = np.random.default_rng(5)
+    Wc = rng.integers(-4, 5, size=(4, 2, 3, 3)) / 8.0
+    bc = rng.integers(-4, 5, size=4) / 16.0
+    conv = oracle.Layer("conv", Wc, bc, (2, 6, 6), 2, 1)
+    Wf = rng.integers(-4, 5, size=(5, conv.n_out)) / 4.0
+    fc = oracle.Layer("fc", Wf, rng.integers(-3, 4, size=5) / 8.0)
+    top = oracle.Layer("fc", rng.integers(-3, 4, size=(1, 5)) / 2.0, np.array([0.25]))
+    return oracle.Net([conv, fc, top])
+
+
+def test_bf16_passes_equal_exact_passes_on_representable_values():
+    """With bf16-representable weights, duals, activations and box offsets the
+    BF16 passes are the exact passes (rounding is the only difference)."""
+    net = _bf16_exact_net()
+    rng = np.random.default_rng(6)
+    B = 3
+    l0 = rng.integers(0, 8, size=(B, net.widths[0])) / 8.0
+    u0 = l0 + rng.integers(1, 4, size=l0.shape) / 16.0
+    ps, ex = oracle.BF16Passes(net, l0, u0), oracle.ExactPasses(net)
+    for k in (1, 2):
+        r = rng.integers(-8, 9, size=(B, net.widths[k])) / 16.0
+        assert np.allclose(ps.transposed(k, r), ex.transposed(k, r), rtol=0, atol=1e-12)
+    x0 = np.where(rng.random(l0.shape) < 0.5, l0, u0)
+    assert np.allclose(ps.forward(1, x0), ex.forward(1, x0), rtol=0, atol=1e-12)
+    x1 = rng.integers(0, 8, size=(B, net.widths[1])) / 4.0
+    assert np.allclose(ps.forward(2, x1), ex.forward(2, x1), rtol=0, atol=1e-12)
+
+
+def test_bf16_passes_round_what_they_should():
+    """Off the bf16 grid, the forward pass of layer 1 keeps the box centre
+    exact (only x0 - c0 is rounded) and hidden layers round weights and
+    inputs; the top layer is untouched."""
+    net = _bf16_exact_net()
+    rng = np.random.default_rng(7)
+    l0 = rng.random((2, net.widths[0])) + 100.0       # pixel values far above the box width
+    u0 = l0 + 1e-3
+    ps, ex = oracle.BF16Passes(net, l0, u0), oracle.ExactPasses(net)
+    x0 = np.where(rng.random(l0.shape) < 0.5, l0, u0)
+    # exact weights and a box offset +-5e-4 (rounded by ~2^-9 relative): the
+    # error is that of the offset, not of the pixel values near 100
+    err = np.abs(ps.forward(1, x0) - ex.forward(1, x0))
+    scale = np.abs(net.L(1).W).sum() * 5e-4
+    assert err.max() < 2 ** -8 * scale
+    r = rng.standard_normal((2, 1))
+    assert np.array_equal(ps.transposed(3, r), ex.transposed(3, r))
+    x1 = rng.standard_normal((2, net.widths[1])) * 3
+    assert np.allclose(ps.forward(2, x1), ex.forward(2, oracle.round_bf16(x1)), rtol=0, atol=1e-12)

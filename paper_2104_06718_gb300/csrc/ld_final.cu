@@ -223,6 +223,106 @@ __global__ void __launch_bounds__(NT) final_conv_kernel(LayerDev L, const float*
   block_reduce_add(acc_out, acc_out.slot + blockIdx.x, b, st, se, sa);
 }
 
+// FP64 transposed conv by stride phase (k4 s2 / k3 s1), G input channels per
+// thread: g[b, c, yy, xx] = sum over the phase's taps (i, j) and o of
+// W[o, c, i, j] rho[b, o, y, x].  Weights sit in shared memory as doubles and
+// their magnitudes as floats, [o][i][j][c], so one rho load (one conversion)
+// feeds G FP64 FMAs.  Same terms and error bounds as final_conv_kernel; the
+// slots are this grid's blocks.
+template <int KH, int KW, int ST, int G>
+__global__ void __launch_bounds__(NT) final_conv_fast_kernel(LayerDev L, const float* __restrict__ r, int rs,
+                                                             FinalEpi epi, FinalAcc acc_out) {
+  extern __shared__ double sWd[];
+  const int nw = L.cout * L.cin * KH * KW;
+  float* sWa = reinterpret_cast<float*>(sWd + nw);
+  for (int e = threadIdx.x; e < nw; e += NT) {
+    const float w = L.Wt[e];
+    sWd[e] = (double)w;
+    sWa[e] = fabsf(w);
+  }
+  __syncthreads();
+  const int b = blockIdx.y;
+  const float* rb = r + (size_t)b * rs;
+  const int qh = L.h / ST, qw = L.w / ST, ncg = L.cin / G, hw_o = L.ho * L.wo;
+  const int items = ST * ST * ncg * qh * qw;
+  double st = 0.0, se = 0.0, sa = 0.0;
+  for (int e = blockIdx.x * NT + threadIdx.x; e < items; e += gridDim.x * NT) {
+    int q = e;
+    const int qx = q % qw;
+    q /= qw;
+    const int qy = q % qh;
+    q /= qh;
+    const int cg = q % ncg;
+    q /= ncg;
+    const int rx = q % ST;
+    const int ry = q / ST;
+    const int i0 = (ry + L.pad) % ST, j0 = (rx + L.pad) % ST;
+    const int dy0 = (ry + L.pad - i0) / ST, dx0 = (rx + L.pad - j0) / ST;
+    double acc[G];
+    float aab[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      acc[g] = 0.0;
+      aab[g] = 0.f;
+    }
+#pragma unroll
+    for (int a = 0; a < KH / ST; ++a) {
+      const int y = qy + dy0 - a;
+      if (y < 0 || y >= L.ho) continue;
+#pragma unroll
+      for (int bb = 0; bb < KW / ST; ++bb) {
+        const int x = qx + dx0 - bb;
+        if (x < 0 || x >= L.wo) continue;
+        const float* rp = rb + y * L.wo + x;
+        const int wo0 = ((i0 + ST * a) * KW + j0 + ST * bb) * L.cin + cg * G;
+        for (int o = 0; o < L.cout; ++o) {
+          const float rv = __ldg(rp + (size_t)o * hw_o);
+          const double rd = (double)rv;
+          const float ra = fabsf(rv);
+          const double* wd = sWd + wo0 + o * KH * KW * L.cin;
+          const float* wa = sWa + wo0 + o * KH * KW * L.cin;
+#pragma unroll
+          for (int g = 0; g < G; ++g) {
+            acc[g] = fma(wd[g], rd, acc[g]);
+            aab[g] = __fmaf_ru(wa[g], ra, aab[g]);
+          }
+        }
+      }
+    }
+    const int yy = ry + ST * qy, xx = rx + ST * qx;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      double tv, ev;
+      epi.term(b, ((cg * G + g) * L.h + yy) * L.w + xx, acc[g], aab[g], tv, ev);
+      st += tv;
+      se = __dadd_ru(se, ev);
+      sa = __dadd_ru(sa, fabs(tv));
+    }
+  }
+  block_reduce_add(acc_out, acc_out.slot + blockIdx.x, b, st, se, sa);
+}
+
+// Geometry and channel blocking of the phase-split FP64 transposed conv, or 0.
+int final_fast_geo(const LayerDev& L, int& G) {
+  G = 0;
+  if (!L.Wt || L.h % L.stride || L.w % L.stride) return 0;
+  int geo = 0;
+  if (L.kh == 4 && L.kw == 4 && L.stride == 2) geo = 1;
+  if (L.kh == 3 && L.kw == 3 && L.stride == 1) geo = 2;
+  if (!geo) return 0;
+  if (L.cin % 4 == 0) G = 4;
+  else if (L.cin == 3) G = 3;
+  else return 0;
+  const size_t smem = (size_t)L.cout * L.cin * L.kh * L.kw * 12;  // double + float per weight
+  if (smem > 96 * 1024) return 0;
+  return geo;
+}
+
+int final_fast_blocks(const LayerDev& L, int G) {
+  const int items = L.stride * L.stride * (L.cin / G) * (L.h / L.stride) * (L.w / L.stride);
+  return (items + NT - 1) / NT;
+}
+
 // Top subproblem P_{n-1}: g_{n-1} = -W_n exactly (no rounding, delta = 0).
 __global__ void __launch_bounds__(NT) final_top_kernel(int n, const float* __restrict__ Wn, FinalEpi epi,
                                                        FinalAcc acc_out) {
@@ -291,6 +391,18 @@ static double gamma_of(double K) {
   return (K * u) / (1.0 - K * u) * (1.0 + 1e-12);
 }
 
+template <int KH, int KW, int ST, int G>
+void launch_fast(dim3 grid, size_t smem, const LayerDev& L, const float* r, int rs, FinalEpi epi, FinalAcc acc,
+                 cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(final_conv_fast_kernel<KH, KW, ST, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         96 * 1024);
+    attr = true;
+  }
+  final_conv_fast_kernel<KH, KW, ST, G><<<grid, NT, smem, s>>>(L, r, rs, epi, acc);
+}
+
 void launch_final_layer(const LayerDev& Lnext, int layer, int r_off, int x_off, const Problem& P,
                         const float* rho, int top, FinalAcc acc, cudaStream_t s) {
   (void)x_off;
@@ -306,6 +418,20 @@ void launch_final_layer(const LayerDev& Lnext, int layer, int r_off, int x_off, 
     dim3 grid((Lnext.n_in + BN - 1) / BN, (P.B + BM - 1) / BM);
     final_fc_kernel<<<grid, NT, 0, s>>>(P.B, Lnext.n_in, Lnext.n_out, r, P.N, Lnext.W, Lnext.n_in, epi, acc);
   } else {
+    int G = 0;
+    const int geo = final_fast_geo(Lnext, G);
+    if (geo) {
+      dim3 grid(final_fast_blocks(Lnext, G), P.B);
+      const size_t smem = (size_t)Lnext.cout * Lnext.cin * Lnext.kh * Lnext.kw * 12;
+      if (geo == 1) {
+        if (G == 4) launch_fast<4, 4, 2, 4>(grid, smem, Lnext, r, P.N, epi, acc, s);
+        else launch_fast<4, 4, 2, 3>(grid, smem, Lnext, r, P.N, epi, acc, s);
+      } else {
+        if (G == 4) launch_fast<3, 3, 1, 4>(grid, smem, Lnext, r, P.N, epi, acc, s);
+        else launch_fast<3, 3, 1, 3>(grid, smem, Lnext, r, P.N, epi, acc, s);
+      }
+      return;
+    }
     const int plane = Lnext.cin * Lnext.h * Lnext.w;
     dim3 grid((plane + NT - 1) / NT, P.B);
     const size_t smem = sizeof(float) * Lnext.cout * Lnext.cin * Lnext.kh * Lnext.kw;
@@ -349,6 +475,8 @@ void launch_record_finish(const Problem& P, const double* q, double* out, cudaSt
 int final_slots(const LayerDev& Lnext, int top) {
   if (top) return 1;
   if (Lnext.kind == LD_LAYER_FC) return (Lnext.n_in + BN - 1) / BN;
+  int G = 0;
+  if (final_fast_geo(Lnext, G)) return final_fast_blocks(Lnext, G);
   return (Lnext.cin * Lnext.h * Lnext.w + NT - 1) / NT;
 }
 

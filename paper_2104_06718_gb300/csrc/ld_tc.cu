@@ -40,10 +40,12 @@
 namespace ld {
 namespace {
 
-constexpr int kThreads = 256;                 // 8 warps, 2 per TMEM lane quadrant
+constexpr int kThreads = 256;                 // worker warps: 8, 2 per TMEM lane quadrant
+constexpr int kCtaThreads = kThreads + 32;    // + one warp that issues the MMAs
 constexpr int kRows = 128;                    // M of every MMA = TMEM lanes
 constexpr int kFcKC = 128;                    // K chunk of the FC forward GEMM
-constexpr int kConvKC = 64;                   // K per pipeline stage of the conv GEMMs
+constexpr int kConvKC = 64;                   // K per pipeline stage of the forward conv GEMM
+constexpr int kConvTKC = 32;                  // K per stage and phase of the transposed conv GEMM
 constexpr int kTabMax = 256;                  // gather table entries (K pieces)
 constexpr unsigned long long kWaitNs = 2000000000ull;
 constexpr size_t kSmemBudget = 216 * 1024;    // dynamic shared memory a launch may ask for
@@ -85,15 +87,38 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     if (global_ns() - t0 > kWaitNs) return false;
   return true;
 }
+// As mbar_wait, and also gives up once *abort is set (by a wait that timed
+// out elsewhere in the CTA); sets *abort itself on time-out.
+__device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, uint32_t parity, volatile int* abort) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort) return false;
+    if (global_ns() - t0 > kWaitNs) {
+      *abort = 1;
+      return false;
+    }
+  }
+  return true;
+}
+// Arrive on the mbarrier once all cp.async copies issued so far by this thread have landed.
+__device__ __forceinline__ void cp_arrive_noinc(uint32_t bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
 // Bulk (TMA) copy global -> shared, completion counted on an mbarrier.
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                "l"(src), "r"(bytes), "r"(bar)
                : "memory");
 }
-// cp.async of 16 / 8 bytes; a copy with valid == false writes zeros.
+// cp.async of 16 / 8 bytes; a copy with valid == false writes zeros.  The
+// 16-byte form bypasses L1 (.cg): these kernels give most of the SM's
+// on-chip memory to shared memory, and the operands live in L2.
 __device__ __forceinline__ void cp16(uint32_t dst, const void* src, bool valid) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0) : "memory");
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0) : "memory");
 }
 __device__ __forceinline__ void cp8(uint32_t dst, const void* src, bool valid) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(valid ? 8 : 0) : "memory");
@@ -218,8 +243,23 @@ __device__ __forceinline__ void adam8(const AdamArgs& a, const size_t (&j)[8], c
   }
 }
 
+// relu_argmin (ld_common.cuh) without branches: the same comparisons in the
+// same arithmetic, so the same vertex for every input; the three cases are
+// selected per lane instead of executed as divergent paths.
+__device__ __forceinline__ void argmin_sel(float r, float g, float l, float u, float& xb, float& x) {
+  const float d = r - g;
+  const float mag = kTieRel * (fabsf(r) + fabsf(g));
+  const bool blk = u <= 0.f, pas = !blk && l >= 0.f;
+  const float vl0 = r * l;
+  const float best = fminf(vl0, 0.f);
+  const bool uu = d * u < best - mag * fmaxf(-l, u);       // ambiguous: (u,u) wins by the margin
+  const bool up = blk ? (r <= 0.f) : (pas ? (d <= mag) : uu);
+  xb = up ? u : ((blk || pas || vl0 <= 0.f) ? l : 0.f);
+  x = blk ? 0.f : (pas ? xb : (uu ? u : 0.f));
+}
+
 // Inner minimisation of up to 8 neurons of a layer k >= 1 (flat indices jf
-// of subdomains bb): loads first, then relu_argmin; writes x_hat_B, returns x.
+// of subdomains bb): loads first, then the vertex choice; writes x_hat_B, returns x.
 __device__ __forceinline__ void argmin8(const Problem& P, const float* rho, float* xB, const int (&bb)[8],
                                         const int (&jf)[8], const bool (&on)[8], const float (&g)[8],
                                         float (&xv)[8]) {
@@ -235,8 +275,7 @@ __device__ __forceinline__ void argmin8(const Problem& P, const float* rho, floa
     xv[e] = 0.f;
     if (!on[e]) continue;
     float xb, xk;
-    int code;
-    relu_argmin<float>(r[e], g[e], l[e], u[e], xb, xk, code);
+    argmin_sel(r[e], g[e], l[e], u[e], xb, xk);
     xB[(size_t)bb[e] * P.N + jf[e]] = xb;
     xv[e] = xk;
   }
@@ -246,6 +285,7 @@ __device__ __forceinline__ void argmin8(const Problem& P, const float* rho, floa
 // Common fields of one tensor-core launch.
 struct TcCommon {
   int n_tiles, n_chunks;
+  int grid_multiple;       // the grid is rounded down to a multiple of this (>= 1)
   uint32_t res_bytes;      // resident operand (conv weights), 0 if none
   uint32_t stage_bytes;    // one pipeline stage (both operands of a K chunk)
   uint32_t tmem_cols;
@@ -283,13 +323,33 @@ struct ConvFwdOp {
     bulk_g2s(sres, W, c.res_bytes, bar);
   }
   __device__ void load_stage(int tile, int chunk, uint32_t sst, uint32_t, const int4* tab) const {
+    const int k8_lo = chunk * KC / 8, k8_hi = min(kf, (chunk + 1) * KC) / 8;
+    const int hw = ho * wo;
+    if (cp_in >= 16 && cp_in <= 64) {
+      // KQ = cp_in / 8 consecutive lanes load the KQ channel chunks of one tap
+      // of one pixel, so a warp reads whole pixels (contiguous along x)
+      const int KQ = cp_in / 8, kq = threadIdx.x % KQ, rpp = kThreads / KQ;
+      for (int rr = threadIdx.x / KQ; rr < kRows; rr += rpp) {
+        const int R = tile * kRows + rr;
+        const int b = R / hw, p = R - b * hw;
+        const int yo = p / wo, xo = p - yo * wo;
+        const bool row_ok = b < B;
+        const uint16_t* src_b = xh + (size_t)(row_ok ? b : 0) * XH + xh_off + kq * 8;
+        for (int k8 = k8_lo + kq; k8 < k8_hi; k8 += KQ) {
+          const int4 t = tab[k8];
+          const int yy = yo * S + t.x, xx = xo * S + t.y;
+          const bool ok = row_ok && t.w && yy >= 0 && yy < h && xx >= 0 && xx < w;
+          cp16(sst + chunk_off(rr, k8 - k8_lo, kRows), ok ? src_b + (size_t)(yy * w + xx) * cp_in : xh, ok);
+        }
+      }
+      return;
+    }
     const int r = threadIdx.x & (kRows - 1);
-    const int R = tile * kRows + r, hw = ho * wo;
+    const int R = tile * kRows + r;
     const int b = R / hw, p = R - b * hw;
     const int yo = p / wo, xo = p - yo * wo;
     const bool row_ok = b < B;
     const uint16_t* src_b = xh + (size_t)(row_ok ? b : 0) * XH + xh_off;
-    const int k8_lo = chunk * KC / 8, k8_hi = min(kf, (chunk + 1) * KC) / 8;
     for (int k8 = k8_lo + (threadIdx.x >> 7); k8 < k8_hi; k8 += kThreads / kRows) {
       const uint32_t dst = sst + chunk_off(r, k8 - k8_lo, kRows);
       if (cp_in >= 8) {
@@ -341,15 +401,24 @@ struct ConvFwdOp {
   }
 };
 
-// Transposed conv of layer k by stride phase (ry, rx): rows = (b, qy, qx) of the
-// phase, g_{k-1}[b, c, S qy + ry, S qx + rx] = sum_{a, bb, o} W[o, c, i0 + S a, j0 + S bb]
-// rho_k[b, o, qy + dy0 - a, qx + dx0 - bb]; epilogue: inner minimisation of layer k-1.
+// Transposed conv of layer k, all S*S stride phases of a tile together:
+// rows = (b, qy, qx) of the phase plane; phase (ry, rx) has its own A tile
+// and weight matrix and accumulates into its own column block of D:
+//   g_{k-1}[b, c, S qy + ry, S qx + rx] = sum_{a, bb, o} W[o, c, i0 + S a, j0 + S bb]
+//                                          rho_k[b, o, qy + dy0 - a, qx + dx0 - bb]
+// so a thread's epilogue owns the S x S output block of its row: for S = 2
+// the two x-phases of a row are adjacent pixels and every epilogue access is
+// a coalesced pair.  Epilogue: inner minimisation of layer k-1 (or its CROWN
+// dual, or the P0 box argmin).
+template <int SS>  // stride (1 or 2)
 struct ConvTOp {
   static constexpr bool kStageBulk = false;
+  static constexpr int S = SS;
   TcCommon c;
-  int nt, kt, KC, n_phase, tpp, na, nb;
+  int nt, kt, KC, n_phase, na, nb;
+  uint32_t sub_bytes;          // one phase's A tile in a stage: 128 x KC bf16
   const uint16_t* W;
-  int B, cin, h, w, ho, wo, S, pad, cp_in, cp_out;
+  int B, cin, h, w, ho, wo, pad, cp_in, cp_out;
   int XH, xh_off, RH, rh_off;
   uint16_t* rh;                // read: shadow of rho_k; CROWN epilogue writes: shadow of rho_kb
   uint16_t* xh;
@@ -359,6 +428,7 @@ struct ConvTOp {
   float* rho;
   int crown;                   // 1: CROWN dual of layer kb (rho and its shadow) instead of the argmin
   int rhb_off, rhb_conv, rhb_hw, rhb_cp;  // layout of the shadow of rho_kb
+  int pairs;                   // S == 2 and every flat index of an x-pair even (float2 accesses)
 
   __device__ void prepare(int4* tab) const {
     for (int e = threadIdx.x; e < kt / 8; e += kThreads) {
@@ -377,95 +447,197 @@ struct ConvTOp {
     dy0 = (ry + pad - i0) / S;
     dx0 = (rx + pad - j0) / S;
   }
-  __device__ void load_stage(int tile, int chunk, uint32_t sst, uint32_t, const int4* tab) const {
-    const int ph = tile / tpp, R = (tile - ph * tpp) * kRows + (threadIdx.x & (kRows - 1));
-    int ry, rx, dy0, dx0;
-    phase_geo(ph, ry, rx, dy0, dx0);
+  // chunks (rr, k8) of every phase for one row
+  __device__ void gather_row(int tile, int rr, int kq, int kstep, int k8_lo, int k8_hi, uint32_t sst,
+                             const int4* tab) const {
     const int PW = w / S, PP = (h / S) * PW;
+    const int R = tile * kRows + rr;
     const int b = R / PP, qq = R - b * PP, qy = qq / PW, qx = qq - qy * PW;
     const bool row_ok = b < B;
     const uint16_t* src_b = rh + (size_t)(row_ok ? b : 0) * RH + rh_off;
-    const int r = threadIdx.x & (kRows - 1);
-    const int k8_lo = chunk * KC / 8, k8_hi = min(kt, (chunk + 1) * KC) / 8;
-    for (int k8 = k8_lo + (threadIdx.x >> 7); k8 < k8_hi; k8 += kThreads / kRows) {
-      const int4 t = tab[k8];
-      const int y = qy + dy0 - t.x, x = qx + dx0 - t.y;
-      const bool ok = row_ok && t.w && y >= 0 && y < ho && x >= 0 && x < wo;
-      cp16(sst + chunk_off(r, k8 - k8_lo, kRows), ok ? src_b + ((size_t)(y * wo + x) * cp_out + t.z) : rh, ok);
+    for (int ph = 0; ph < n_phase; ++ph) {
+      int ry, rx, dy0, dx0;
+      phase_geo(ph, ry, rx, dy0, dx0);
+      const uint32_t sub = sst + (uint32_t)ph * sub_bytes;
+      for (int k8 = k8_lo + kq; k8 < k8_hi; k8 += kstep) {
+        const int4 t = tab[k8];
+        const int y = qy + dy0 - t.x, x = qx + dx0 - t.y;
+        const bool ok = row_ok && t.w && y >= 0 && y < ho && x >= 0 && x < wo;
+        cp16(sub + chunk_off(rr, k8 - k8_lo, kRows), ok ? src_b + ((size_t)(y * wo + x) * cp_out + t.z) : rh, ok);
+      }
     }
   }
-  __device__ void issue_mma(int tile, int chunk, uint32_t sres, uint32_t sst, uint32_t tmem) const {
-    const int ph = tile / tpp;
-    const uint32_t wb = sres + (uint32_t)(ph * nt * kt * 2);
+  __device__ void load_stage(int tile, int chunk, uint32_t sst, uint32_t, const int4* tab) const {
+    const int k8_lo = chunk * KC / 8, k8_hi = min(kt, (chunk + 1) * KC) / 8;
+    if (cp_out >= 16 && cp_out <= 64) {
+      // KQ consecutive lanes load the KQ channel chunks of one tap of one pixel
+      const int KQ = cp_out / 8;
+      for (int rr = threadIdx.x / KQ; rr < kRows; rr += kThreads / KQ)
+        gather_row(tile, rr, threadIdx.x % KQ, KQ, k8_lo, k8_hi, sst, tab);
+      return;
+    }
+    gather_row(tile, threadIdx.x & (kRows - 1), threadIdx.x >> 7, kThreads / kRows, k8_lo, k8_hi, sst, tab);
+  }
+  __device__ void issue_mma(int, int chunk, uint32_t sres, uint32_t sst, uint32_t tmem) const {
     const uint32_t id = idesc_bf16(kRows, nt);
     const int s0 = chunk * KC / 16, ns = (min(kt, (chunk + 1) * KC) - chunk * KC) / 16;
-    for (int s = 0; s < ns; ++s)
-      mma_bf16(tmem, op_desc(sst, s, kRows), op_desc(wb, s0 + s, nt), id, (chunk > 0 || s > 0) ? 1u : 0u);
+    for (int ph = 0; ph < n_phase; ++ph) {
+      const uint32_t wb = sres + (uint32_t)(ph * nt * kt * 2), a = sst + (uint32_t)ph * sub_bytes;
+      for (int s = 0; s < ns; ++s)
+        mma_bf16(tmem + (uint32_t)(ph * nt), op_desc(a, s, kRows), op_desc(wb, s0 + s, nt), id,
+                 (chunk > 0 || s > 0) ? 1u : 0u);
+    }
+  }
+  // CROWN dual of neuron jn (layer kb) of subdomain b: rho and its shadow
+  __device__ void crown_one(int b, int jn, float g) const {
+    const int jf = r_off_kb + jn;
+    const float r = crown_rho(P, b, jf, g);
+    rho[(size_t)b * P.N + jf] = r;
+    const int pos = rhb_conv ? (jn % rhb_hw) * rhb_cp + jn / rhb_hw : jn;
+    rh[(size_t)b * RH + rhb_off + pos] = bf16_bits(r);
   }
   __device__ void epilogue(int tile, uint32_t tmem) const {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = warp & 3, half = warp >> 2;
-    const int ph = tile / tpp, R = (tile - ph * tpp) * kRows + q * 32 + lane;
-    int ry, rx, dy0, dx0;
-    phase_geo(ph, ry, rx, dy0, dx0);
-    const int PW = w / S, PP = (h / S) * PW;
+    const int PW = w / SS, PP = (h / SS) * PW, hw = h * w;
+    const int R = tile * kRows + q * 32 + lane;
     const int b = R / PP, qq = R - b * PP, qy = qq / PW, qx = qq - qy * PW;
-    const int yy = S * qy + ry, xx = S * qx + rx, pix = yy * w + xx;
     const bool row_ok = b < B;
     const int prop = row_ok ? prop_of(P, b) : 0;
-    const int cols = nt / 2, lo = half * cols;
-    for (int c0 = lo; c0 < lo + cols; c0 += 8) {
-      float acc[8];
-      tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, acc);
-      if (!row_ok || c0 >= cin || c0 >= cp_in) continue;
-      float xv[8];
-      if (crown) {
+    const uint32_t lanes = (uint32_t)(q * 32) << 16;
+    const int ngroups = (nt + 7) / 8;  // channel groups of 8, split between the two warp halves
+    const int c_hi = crown ? cin : min(cin, cp_in);
+    for (int cg = half; cg < ngroups; cg += 2) {
+      const int c0 = cg * 8;
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int ch = c0 + e;
-          if (ch >= cin) continue;
-          const int jn = ch * h * w + pix, jf = r_off_kb + jn;
-          const float r = crown_rho(P, b, jf, acc[e]);
-          rho[(size_t)b * P.N + jf] = r;
-          const int pos = rhb_conv ? (jn % rhb_hw) * rhb_cp + jn / rhb_hw : jn;
-          rh[(size_t)b * RH + rhb_off + pos] = bf16_bits(r);
+      for (int ry = 0; ry < SS; ++ry) {
+        // accumulators of the phases (ry, 0 .. SS-1): warp-collective loads first
+        float g0[8], g1[8];
+        tmem_ld8(tmem + lanes + (uint32_t)((ry * SS) * nt + c0), g0);
+        if (SS == 2) tmem_ld8(tmem + lanes + (uint32_t)((ry * SS + 1) * nt + c0), g1);
+        if (!row_ok || c0 >= c_hi) continue;
+        const int yy = SS * qy + ry, x0 = SS * qx;
+        if (crown) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e)
+            if (c0 + e < cin) {
+              const int jn = (c0 + e) * hw + yy * w + x0;
+              crown_one(b, jn, g0[e]);
+              if (SS == 2) crown_one(b, jn + 1, g1[e]);
+            }
+          continue;
         }
-        continue;
-      }
-      if (kb == 0) {
-        // P0 (Eq. box_bounds_sol): x0 = u0 where g_0 >= 0, else l0; stored centred
-        float l0[8], u0[8];
+        if (SS == 2 && pairs) {
+          // pixels (yy, x0) and (yy, x0 + 1): every access a coalesced pair
+          float xv0[8], xv1[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e)
-          if (c0 + e < cin) {
-            const int jn = (c0 + e) * h * w + pix;
-            l0[e] = P.l0[(size_t)prop * P.n0 + jn];
-            u0[e] = P.u0[(size_t)prop * P.n0 + jn];
+          for (int e4 = 0; e4 < 8; e4 += 4) {
+            if (kb == 0) {
+              float2 lo[4], up[4];
+#pragma unroll
+              for (int e = 0; e < 4; ++e)
+                if (c0 + e4 + e < cin) {
+                  const size_t j = (size_t)prop * P.n0 + (c0 + e4 + e) * hw + yy * w + x0;
+                  lo[e] = *reinterpret_cast<const float2*>(P.l0 + j);
+                  up[e] = *reinterpret_cast<const float2*>(P.u0 + j);
+                }
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                xv0[e4 + e] = xv1[e4 + e] = 0.f;
+                if (c0 + e4 + e < cin) {
+                  // P0 (Eq. box_bounds_sol): x0 = u0 where g_0 >= 0, else l0; stored centred
+                  const float h0 = 0.5f * (up[e].x - lo[e].x), h1 = 0.5f * (up[e].y - lo[e].y);
+                  xv0[e4 + e] = g0[e4 + e] >= 0.f ? h0 : -h0;
+                  xv1[e4 + e] = g1[e4 + e] >= 0.f ? h1 : -h1;
+                }
+              }
+            } else {
+              float2 rr[4], lo[4], up[4];
+              char2 mk[4];
+#pragma unroll
+              for (int e = 0; e < 4; ++e)
+                if (c0 + e4 + e < cin) {
+                  const int jf = r_off_kb + (c0 + e4 + e) * hw + yy * w + x0;
+                  rr[e] = *reinterpret_cast<const float2*>(rho + (size_t)b * P.N + jf);
+                  lo[e] = *reinterpret_cast<const float2*>(P.lbk + (size_t)prop * P.N + jf);
+                  up[e] = *reinterpret_cast<const float2*>(P.ubk + (size_t)prop * P.N + jf);
+                  mk[e] = P.mask ? *reinterpret_cast<const char2*>(P.mask + (size_t)b * P.N + jf) : make_char2(0, 0);
+                }
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                xv0[e4 + e] = xv1[e4 + e] = 0.f;
+                if (c0 + e4 + e < cin) {
+                  // split-mask clamp (Sec. 2.3.2), as clamped_bounds
+                  float l0v = lo[e].x, u0v = up[e].x, l1v = lo[e].y, u1v = up[e].y;
+                  if (mk[e].x > 0) l0v = fmaxf(l0v, 0.f);
+                  if (mk[e].x < 0) u0v = fminf(u0v, 0.f);
+                  if (mk[e].y > 0) l1v = fmaxf(l1v, 0.f);
+                  if (mk[e].y < 0) u1v = fminf(u1v, 0.f);
+                  float2 xb;
+                  argmin_sel(rr[e].x, g0[e4 + e], l0v, u0v, xb.x, xv0[e4 + e]);
+                  argmin_sel(rr[e].y, g1[e4 + e], l1v, u1v, xb.y, xv1[e4 + e]);
+                  const int jf = r_off_kb + (c0 + e4 + e) * hw + yy * w + x0;
+                  *reinterpret_cast<float2*>(xB + (size_t)b * P.N + jf) = xb;
+                }
+              }
+            }
           }
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          xv[e] = 0.f;
-          if (c0 + e < cin) {
-            const float hw0 = 0.5f * (u0[e] - l0[e]);
-            xv[e] = acc[e] >= 0.f ? hw0 : -hw0;
+          uint16_t* dst = xh + (size_t)b * XH + xh_off + (size_t)(yy * w + x0) * cp_in + c0;
+          if (cp_in >= 8) {
+            *reinterpret_cast<uint4*>(dst) = pack8(xv0);
+            *reinterpret_cast<uint4*>(dst + cp_in) = pack8(xv1);
+          } else {  // cp_in == 4: the two pixels' 4 channels are one 16-byte block
+            float v[8] = {xv0[0], xv0[1], xv0[2], xv0[3], xv1[0], xv1[1], xv1[2], xv1[3]};
+            *reinterpret_cast<uint4*>(dst) = pack8(v);
           }
+          continue;
         }
-      } else {
-        int bb[8], jf[8];
-        bool on[8];
+        // one pixel per phase (S == 1, or no pair alignment)
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          on[e] = c0 + e < cin;
-          bb[e] = b;
-          jf[e] = r_off_kb + (c0 + e) * h * w + pix;
+        for (int rx = 0; rx < SS; ++rx) {
+          const int pix = yy * w + x0 + rx;
+          float xv[8];
+          float gx[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) gx[e] = rx == 0 ? g0[e] : g1[e];
+          if (kb == 0) {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              xv[e] = 0.f;
+              if (c0 + e < cin) {
+                const int jn = (c0 + e) * hw + pix;
+                const float hw0 = 0.5f * (P.u0[(size_t)prop * P.n0 + jn] - P.l0[(size_t)prop * P.n0 + jn]);
+                xv[e] = gx[e] >= 0.f ? hw0 : -hw0;
+              }
+            }
+          } else if (SS == 1) {
+            int bb[8], jf[8];
+            bool on[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              on[e] = c0 + e < cin;
+              bb[e] = b;
+              jf[e] = r_off_kb + (c0 + e) * hw + pix;
+            }
+            argmin8(P, rho, xB, bb, jf, on, gx, xv);
+          } else {  // stride 2 without pair alignment: one neuron at a time (small code, rare)
+            for (int e = 0; e < 8; ++e) {
+              xv[e] = 0.f;
+              if (c0 + e >= cin) continue;
+              const int jf = r_off_kb + (c0 + e) * hw + pix;
+              float l, u, xb;
+              clamped_bounds(P, b, jf, l, u);
+              argmin_sel(rho[(size_t)b * P.N + jf], gx[e], l, u, xb, xv[e]);
+              xB[(size_t)b * P.N + jf] = xb;
+            }
+          }
+          uint16_t* dst = xh + (size_t)b * XH + xh_off + (size_t)pix * cp_in + c0;
+          const uint4 pk = pack8(xv);
+          if (cp_in >= 8)
+            *reinterpret_cast<uint4*>(dst) = pk;
+          else
+            *reinterpret_cast<uint2*>(dst) = make_uint2(pk.x, pk.y);
         }
-        argmin8(P, rho, xB, bb, jf, on, acc, xv);
       }
-      uint16_t* dst = xh + (size_t)b * XH + xh_off + (size_t)pix * cp_in + c0;
-      const uint4 pk = pack8(xv);
-      if (cp_in >= 8)
-        *reinterpret_cast<uint4*>(dst) = pk;
-      else
-        *reinterpret_cast<uint2*>(dst) = make_uint2(pk.x, pk.y);
     }
   }
 };
@@ -539,7 +711,7 @@ struct FcFwdOp {
 // Transposed FC of layer k: D[i, b] = sum_o W[o, i] rho_k[b, o] (M = inputs,
 // N = subdomains); epilogue: inner minimisation of layer k-1.
 struct FcTOp {
-  static constexpr bool kStageBulk = true;
+  static constexpr bool kStageBulk = false;
   TcCommon c;
   int n_mt, BN, kt;
   uint32_t a_bytes;
@@ -554,26 +726,27 @@ struct FcTOp {
   int crown;
   int rhb_off, rhb_conv, rhb_hw, rhb_cp;
 
+  // the grid is a multiple of n_mt, so every tile of a CTA has the same 128-row
+  // block of W^T (mt = blockIdx.x % n_mt): it stays resident
   __device__ void prepare(int4*) const {}
-  __device__ void load_resident(uint32_t, uint32_t) const {}
-  __device__ void load_stage(int tile, int, uint32_t sst, uint32_t bar, const int4*) const {
-    const int mt = tile % n_mt, ntile = tile / n_mt;
-    if (threadIdx.x == 0) {
-      mbar_expect_tx(bar, a_bytes);
-      bulk_g2s(sst, W + (size_t)mt * kRows * kt, a_bytes, bar);
-    }
+  __device__ void load_resident(uint32_t sres, uint32_t bar) const {
+    mbar_expect_tx(bar, a_bytes);
+    bulk_g2s(sres, W + (size_t)(blockIdx.x % n_mt) * kRows * kt, a_bytes, bar);
+  }
+  __device__ void load_stage(int tile, int, uint32_t sst, uint32_t, const int4*) const {
+    const int ntile = tile / n_mt;
     const int nk8 = kt / 8;
     for (int idx = threadIdx.x; idx < BN * nk8; idx += kThreads) {
       const int r = idx % BN, k8 = idx / BN;
       const int b = ntile * BN + r;
       const bool ok = b < B;
-      cp16(sst + a_bytes + chunk_off(r, k8, BN), ok ? rh + (size_t)b * RH + rh_off + 8 * k8 : rh, ok);
+      cp16(sst + chunk_off(r, k8, BN), ok ? rh + (size_t)b * RH + rh_off + 8 * k8 : rh, ok);
     }
   }
-  __device__ void issue_mma(int, int, uint32_t, uint32_t sst, uint32_t tmem) const {
+  __device__ void issue_mma(int, int, uint32_t sres, uint32_t sst, uint32_t tmem) const {
     const uint32_t id = idesc_bf16(kRows, BN);
     for (int s = 0; s < kt / 16; ++s)
-      mma_bf16(tmem, op_desc(sst, s, kRows), op_desc(sst + a_bytes, s, BN), id, s > 0 ? 1u : 0u);
+      mma_bf16(tmem, op_desc(sres, s, kRows), op_desc(sst, s, BN), id, s > 0 ? 1u : 0u);
   }
   __device__ void epilogue(int tile, uint32_t tmem) const {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = warp & 3, half = warp >> 2;
@@ -604,7 +777,28 @@ struct FcTOp {
         continue;
       }
       float xv[8];
-      if (kb == 0) {
+      if (kb != 0 && !P.prop) {
+        // one property: the bounds of neuron i are the same for every column
+        const int jf = r_off_kb + i;
+        const float lb = P.lbk[jf], ub = P.ubk[jf];
+        float r[8];
+        int8_t mk[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+          if (on[e]) {
+            r[e] = rho[(size_t)bb[e] * P.N + jf];
+            mk[e] = P.mask ? P.mask[(size_t)bb[e] * P.N + jf] : (int8_t)0;
+          }
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          xv[e] = 0.f;
+          if (!on[e]) continue;
+          const float l = mk[e] > 0 ? fmaxf(lb, 0.f) : lb, u = mk[e] < 0 ? fminf(ub, 0.f) : ub;
+          float xb;
+          argmin_sel(r[e], acc[e], l, u, xb, xv[e]);
+          xB[(size_t)bb[e] * P.N + jf] = xb;
+        }
+      } else if (kb == 0) {
         float l0[8], u0[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e)
@@ -637,98 +831,117 @@ __device__ __forceinline__ void cp_wait_pending() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Persistent tile loop of one CTA over stages s = (tile, K chunk) of its
-// tiles, NS-deep ring of shared-memory stage buffers: the gathers of stages
-// s+1 .. s+NS-1 are in flight while the MMAs and the epilogue of stage s run.
-// Every thread commits one cp.async group per stage (empty past the end), so
-// "all but the newest NS-2 groups done" means "stage s landed".
+// Persistent, warp-specialised tile loop of one CTA.  Stage s = (tile, K
+// chunk) of this CTA's tiles; NS shared-memory stage buffers; two
+// accumulator buffers in TMEM (columns [0, dcols) and [dcols, 2 dcols)).
+//   worker warps 0-7   iteration i: gather stage i into its buffer once the
+//                      MMAs of stage i-NS released it (cp.async; each thread
+//                      arrives on full[i % NS] when its copies land), then run
+//                      the epilogue of the tile whose last stage is i-LAG once
+//                      its accumulators are final, and release that buffer
+//   warp 8, lane 0     stage s: wait full[s % NS], wait the accumulator buffer
+//                      (first chunk of a tile), issue the MMAs, commit to
+//                      free[s % NS] and, after a tile's last chunk, to acc_full
+// There is no CTA-wide barrier inside the loop; every wait is bounded and a
+// time-out anywhere makes every other wait give up (abort flag).
 template <class Op, int NS>
-__global__ void __launch_bounds__(kThreads, 3) tc_kernel(const Op op) {
+__global__ void __launch_bounds__(kCtaThreads, 2) tc_kernel(const Op op) {
+  constexpr int LAG = NS - 1;
   extern __shared__ __align__(1024) uint8_t dyn_smem[];
   __shared__ __align__(8) uint64_t bar_res;
-  __shared__ __align__(8) uint64_t bar_ld[NS];
-  __shared__ __align__(8) uint64_t bar_mma;
+  __shared__ __align__(8) uint64_t bar_full[NS];
+  __shared__ __align__(8) uint64_t bar_free[NS];
+  __shared__ __align__(8) uint64_t bar_acc_full[2];
+  __shared__ __align__(8) uint64_t bar_acc_empty[2];
   __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
   __shared__ int4 tab[kTabMax];
   const int tid = threadIdx.x, warp = tid >> 5;
   const uint32_t base = (smem_u32(dyn_smem) + 1023u) & ~1023u;
   const uint32_t sres = base, sst0 = base + op.c.res_bytes;
-  const uint32_t b_res = smem_u32(&bar_res), b_mma = smem_u32(&bar_mma), b_ld0 = smem_u32(&bar_ld[0]);
+  const uint32_t b_res = smem_u32(&bar_res), b_full = smem_u32(&bar_full[0]), b_free = smem_u32(&bar_free[0]);
+  const uint32_t b_af = smem_u32(&bar_acc_full[0]), b_ae = smem_u32(&bar_acc_empty[0]);
+  volatile int* abort = &abort_flag;
   if (tid == 0) {
     mbar_init(b_res, 1);
-    for (int i = 0; i < NS; ++i) mbar_init(b_ld0 + 8 * i, 1);
-    mbar_init(b_mma, 1);
+    for (int i = 0; i < NS; ++i) {
+      mbar_init(b_full + 8 * i, kThreads + (Op::kStageBulk ? 1 : 0));
+      mbar_init(b_free + 8 * i, 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(b_af + 8 * i, 1);
+      mbar_init(b_ae + 8 * i, kThreads);
+    }
+    abort_flag = 0;
     fence_mbar_init();
   }
-  if (warp == 0) {
+  if (warp == kThreads / 32) {
     tmem_alloc(smem_u32(&tmem_slot), op.c.tmem_cols);
     tmem_relinquish();
   }
-  op.prepare(tab);
+  if (tid < kThreads) op.prepare(tab);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
-
+  const uint32_t dcols = op.c.tmem_cols / 2;
+  const int nch = op.c.n_chunks;
   const int my_tiles = (int)blockIdx.x < op.c.n_tiles ? (op.c.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-  const int n_stages = my_tiles * op.c.n_chunks;
-  auto tile_of = [&](int st) { return (int)blockIdx.x + (st / op.c.n_chunks) * (int)gridDim.x; };
-  int issued = 0;        // stages whose loads were issued
-  auto issue = [&](int st) {  // loads of stage st (if it exists) + one commit group
-    if (st < n_stages) {
-      const int bi = st % NS;
-      op.load_stage(tile_of(st), st % op.c.n_chunks, sst0 + (uint32_t)bi * op.c.stage_bytes, b_ld0 + 8 * bi, tab);
-      issued = st + 1;
-    }
-    cp_commit();
-  };
-  if (tid == 0 && op.c.res_bytes && n_stages > 0) op.load_resident(sres, b_res);
-  for (int p = 0; p < NS - 1; ++p) issue(p);
-  int bulk_waited = 0;  // thread 0: bulk-loaded stages already waited on
-  int bad = 0;
-  for (int s = 0; s < n_stages; ++s) {
-    const int bi = s % NS;
-    const int tile = tile_of(s), chunk = s % op.c.n_chunks;
-    const uint32_t sst = sst0 + (uint32_t)bi * op.c.stage_bytes;
-    cp_wait_pending<NS - 2>();
-    fence_proxy_async();
-    if (__syncthreads_or(bad)) break;
-    if (tid == 0) {
-      bool ready = true;
-      if (s == 0 && op.c.res_bytes) ready = mbar_wait(b_res, 0);
-      if (Op::kStageBulk && ready) {
-        ready = mbar_wait(b_ld0 + 8 * bi, (uint32_t)((s / NS) & 1));
-        if (ready) bulk_waited = s + 1;
+  const int n_stages = my_tiles * nch;
+  auto tile_of = [&](int st) { return (int)blockIdx.x + (st / nch) * (int)gridDim.x; };
+
+  if (tid < kThreads) {
+    // ---------------------------------------------------------- worker warps
+    int issued = 0;  // stages whose loads this thread issued (thread 0: incl. bulk copies)
+    for (int i = 0; i < n_stages + LAG; ++i) {
+      if (i < n_stages) {
+        const int bi = i % NS;
+        const bool fr = i < NS || mbar_wait_ab(b_free + 8 * bi, (uint32_t)(((i / NS) - 1) & 1), abort);
+        if (__any_sync(0xffffffffu, !fr)) break;
+        op.load_stage(tile_of(i), i % nch, sst0 + (uint32_t)bi * op.c.stage_bytes, b_full + 8 * bi, tab);
+        cp_arrive_noinc(b_full + 8 * bi);
+        issued = i + 1;
       }
-      if (ready) {
+      const int e = i - LAG;
+      if (e >= 0 && e % nch == nch - 1) {
+        const int tl = e / nch;  // tile index within this CTA
+        const bool ok = mbar_wait_ab(b_af + 8 * (tl & 1), (uint32_t)((tl >> 1) & 1), abort);
+        if (__any_sync(0xffffffffu, !ok)) break;  // warp-uniform: the TMEM loads are warp-collective
         tc_fence_after();
-        op.issue_mma(tile, chunk, sres, sst, tmem);
-      } else {
-        bad = 1;
-        atomicCAS(op.c.status, 0, (int)LD_ERR_TIMEOUT);
+        op.epilogue(tile_of(e), tmem + (uint32_t)(tl & 1) * dcols);
+        tc_fence_before();
+        mbar_arrive(b_ae + 8 * (tl & 1));
       }
-      mma_commit(b_mma);  // with no MMA issued this arrives at once
     }
-    // the buffer of stage s+NS-1 was last read by the MMAs of stage s-1 (waited below, one iteration ago)
-    issue(s + NS - 1);
-    if (!mbar_wait(b_mma, (uint32_t)(s & 1))) {
-      bad = 1;
-      atomicCAS(op.c.status, 0, (int)LD_ERR_TIMEOUT);
-    }
-    tc_fence_after();
-    if (!bad && chunk == op.c.n_chunks - 1) op.epilogue(tile, tmem);
-    tc_fence_before();
-  }
-  cp_wait_pending<0>();
-  // bulk copies issued for stages that never ran must land before the CTA exits
-  if (Op::kStageBulk && tid == 0)
-    for (int st = bulk_waited; st < issued; ++st)
-      if (!mbar_wait(b_ld0 + 8 * (st % NS), (uint32_t)((st / NS) & 1))) {
-        atomicCAS(op.c.status, 0, (int)LD_ERR_TIMEOUT);
+    // copies issued for stages that were never consumed must land before exit
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    if (Op::kStageBulk && tid == 0 && *abort)
+      for (int st = (issued > NS ? issued - NS : 0); st < issued; ++st)
+        if (!mbar_wait(b_full + 8 * (st % NS), (uint32_t)((st / NS) & 1))) break;
+  } else if (tid == kThreads) {
+    // ---------------------------------------------------------- MMA issuer
+    if (op.c.res_bytes && n_stages > 0) op.load_resident(sres, b_res);
+    bool ok = !(op.c.res_bytes && n_stages > 0) || mbar_wait_ab(b_res, 0, abort);
+    int last = -1;  // last stage whose MMAs were committed
+    for (int s = 0; ok && s < n_stages; ++s) {
+      const int bi = s % NS, tl = s / nch, chunk = s % nch;
+      if (!mbar_wait_ab(b_full + 8 * bi, (uint32_t)((s / NS) & 1), abort)) break;
+      fence_proxy_async();  // the workers' cp.async writes (generic proxy) -> tensor core reads
+      if (chunk == 0 && tl >= 2 && !mbar_wait_ab(b_ae + 8 * (tl & 1), (uint32_t)(((tl >> 1) - 1) & 1), abort))
         break;
-      }
+      tc_fence_after();
+      op.issue_mma(tile_of(s), chunk, sres, sst0 + (uint32_t)bi * op.c.stage_bytes, tmem + (uint32_t)(tl & 1) * dcols);
+      mma_commit(b_free + 8 * bi);
+      if (chunk == nch - 1) mma_commit(b_af + 8 * (tl & 1));
+      last = s;
+    }
+    if (*abort) atomicCAS(op.c.status, 0, (int)LD_ERR_TIMEOUT);
+    // let the last MMAs finish before the accumulators are freed
+    if (last >= 0) mbar_wait(b_free + 8 * (last % NS), (uint32_t)((last / NS) & 1));
+  }
+  tc_fence_before();
   __syncthreads();
-  if (warp == 0) {
+  if (warp == kThreads / 32) {
     tc_fence_after();
     tmem_dealloc(tmem, op.c.tmem_cols);
   }
@@ -838,10 +1051,10 @@ int ctas_per_sm(const void* func, size_t dyn_smem, uint32_t tmem_cols) {
     return 1;
   }
   const int per_warp = (fa.numRegs * 32 + 255) / 256 * 256;
-  int n = regs_sm / (per_warp * (kThreads / 32));
+  int n = regs_sm / (per_warp * (kCtaThreads / 32));
   const int by_smem = (int)((size_t)smem_sm / (dyn_smem + fa.sharedSizeBytes + (size_t)smem_rsv));
   if (by_smem < n) n = by_smem;
-  if (thr_sm / kThreads < n) n = thr_sm / kThreads;
+  if (thr_sm / kCtaThreads < n) n = thr_sm / kCtaThreads;
   if ((int)(512 / tmem_cols) < n) n = (int)(512 / tmem_cols);
   return n < 1 ? 1 : n;
 }
@@ -858,8 +1071,11 @@ cudaError_t launch_ns(const Op& op, size_t smem, int n_sm, cudaStream_t s) {
   const int per_sm = ctas_per_sm(reinterpret_cast<const void*>(tc_kernel<Op, NS>), smem, op.c.tmem_cols);
   int grid = n_sm * per_sm;
   if (grid > op.c.n_tiles) grid = op.c.n_tiles;
+  const int gm = op.c.grid_multiple > 1 ? op.c.grid_multiple : 1;
+  grid = grid / gm * gm;
+  if (grid < gm) grid = gm;
   count_launch();
-  tc_kernel<Op, NS><<<grid, kThreads, smem, s>>>(op);
+  tc_kernel<Op, NS><<<grid, kCtaThreads, smem, s>>>(op);
   return cudaGetLastError();
 }
 
@@ -1044,36 +1260,24 @@ void launch_tc_centre(const TcNet& t, const LayerDev& L1, const Problem& P, cons
   centre_kernel<<<(int)((total + 255) / 256), 256, 0, s>>>(L1, P.n_props, P.n0, P.l0, P.u0, S.c1);
 }
 
-void launch_tc_transposed(const TcNet& t, const std::vector<LayerDev>& Ls, int k, const Problem& P,
-                          const TcState& S, int n_sm, cudaStream_t s, int crown) {
-  const LayerDev& L = Ls[k - 1];
-  const TcLayer& T = t.T[k - 1];
-  const int kb = k - 1;
-  const int r_off_kb = kb >= 1 ? Ls[kb - 1].r_out_off : 0;
-  if (crown && kb < 1) return;
-  // where the CROWN epilogue puts the shadow of rho_kb (layout read by layer kb's transposed pass)
-  int rhb_off = 0, rhb_conv = 0, rhb_hw = 1, rhb_cp = 0;
-  if (kb >= 1) {
-    const LayerDev& Lb = Ls[kb - 1];
-    rhb_off = t.T[kb - 1].rh_off;
-    rhb_conv = Lb.kind == LD_LAYER_CONV ? 1 : 0;
-    rhb_hw = rhb_conv ? Lb.ho * Lb.wo : 1;
-    rhb_cp = t.T[kb - 1].cp_out;
-  }
-  if (L.kind == LD_LAYER_CONV) {
-    ConvTOp op{};
+template <int SS>
+void launch_conv_t(const TcNet& t, const TcLayer& T, const LayerDev& L, const Problem& P, const TcState& S, int kb,
+                   int r_off_kb, int crown, int rhb_off, int rhb_conv, int rhb_hw, int rhb_cp, int n_sm,
+                   cudaStream_t s) {
+    ConvTOp<SS> op{};
     const int PP = (L.h / L.stride) * (L.w / L.stride);
-    op.tpp = (int)(((size_t)P.B * PP + kRows - 1) / kRows);
-    op.c.n_tiles = op.tpp * T.n_phase;
-    op.KC = T.kt < kConvKC ? T.kt : kConvKC;
+    op.n_phase = T.n_phase;
+    op.c.n_tiles = (int)(((size_t)P.B * PP + kRows - 1) / kRows);
+    op.KC = T.kt < kConvTKC ? T.kt : kConvTKC;
     op.c.n_chunks = (T.kt + op.KC - 1) / op.KC;
+    op.sub_bytes = (uint32_t)(2 * kRows * op.KC);
     op.c.res_bytes = (uint32_t)(2 * T.nt * T.kt * T.n_phase);
-    op.c.stage_bytes = (uint32_t)(2 * kRows * op.KC);
-    op.c.tmem_cols = tmem_cols_for(T.nt);
+    op.c.stage_bytes = op.sub_bytes * (uint32_t)T.n_phase;
+    op.c.tmem_cols = tmem_cols_for(2 * T.n_phase * T.nt);
+    op.c.grid_multiple = 1;
     op.c.status = S.status;
     op.nt = T.nt;
     op.kt = T.kt;
-    op.n_phase = T.n_phase;
     op.na = T.na;
     op.nb = T.nb;
     op.W = T.Wt;
@@ -1083,7 +1287,6 @@ void launch_tc_transposed(const TcNet& t, const std::vector<LayerDev>& Ls, int k
     op.w = L.w;
     op.ho = L.ho;
     op.wo = L.wo;
-    op.S = L.stride;
     op.pad = L.pad;
     op.cp_in = T.cp_in;
     op.cp_out = T.cp_out;
@@ -1103,19 +1306,46 @@ void launch_tc_transposed(const TcNet& t, const std::vector<LayerDev>& Ls, int k
     op.rhb_conv = rhb_conv;
     op.rhb_hw = rhb_hw;
     op.rhb_cp = rhb_cp;
+    // float2 pairs need even flat indices: N, n0, the layer offset and the plane width even
+    op.pairs = (L.stride == 2 && P.N % 2 == 0 && P.n0 % 2 == 0 && r_off_kb % 2 == 0 && L.w % 2 == 0) ? 1 : 0;
     launch_op(op, n_sm, s);
+}
+
+void launch_tc_transposed(const TcNet& t, const std::vector<LayerDev>& Ls, int k, const Problem& P,
+                          const TcState& S, int n_sm, cudaStream_t s, int crown) {
+  const LayerDev& L = Ls[k - 1];
+  const TcLayer& T = t.T[k - 1];
+  const int kb = k - 1;
+  const int r_off_kb = kb >= 1 ? Ls[kb - 1].r_out_off : 0;
+  if (crown && kb < 1) return;
+  // where the CROWN epilogue puts the shadow of rho_kb (layout read by layer kb's transposed pass)
+  int rhb_off = 0, rhb_conv = 0, rhb_hw = 1, rhb_cp = 0;
+  if (kb >= 1) {
+    const LayerDev& Lb = Ls[kb - 1];
+    rhb_off = t.T[kb - 1].rh_off;
+    rhb_conv = Lb.kind == LD_LAYER_CONV ? 1 : 0;
+    rhb_hw = rhb_conv ? Lb.ho * Lb.wo : 1;
+    rhb_cp = t.T[kb - 1].cp_out;
+  }
+  if (L.kind == LD_LAYER_CONV) {
+    if (L.stride == 2)
+      launch_conv_t<2>(t, T, L, P, S, kb, r_off_kb, crown, rhb_off, rhb_conv, rhb_hw, rhb_cp, n_sm, s);
+    else
+      launch_conv_t<1>(t, T, L, P, S, kb, r_off_kb, crown, rhb_off, rhb_conv, rhb_hw, rhb_cp, n_sm, s);
     return;
   }
   FcTOp op{};
   op.n_mt = T.fc_nmt_t;
   op.BN = fc_bn(op.n_mt, P.B, n_sm);
+  if (op.BN > 64) op.BN = 64;
   op.kt = T.kt;
   op.a_bytes = (uint32_t)(2 * kRows * T.kt);
   op.c.n_tiles = op.n_mt * ((P.B + op.BN - 1) / op.BN);
   op.c.n_chunks = 1;
-  op.c.res_bytes = 0;
-  op.c.stage_bytes = op.a_bytes + (uint32_t)(2 * op.BN * T.kt);
-  op.c.tmem_cols = tmem_cols_for(op.BN);
+  op.c.res_bytes = op.a_bytes;
+  op.c.stage_bytes = (uint32_t)(2 * op.BN * T.kt);
+  op.c.grid_multiple = op.n_mt;
+  op.c.tmem_cols = tmem_cols_for(2 * op.BN);
   op.c.status = S.status;
   op.W = T.Wt;
   op.B = P.B;
@@ -1150,7 +1380,7 @@ void launch_tc_forward(const TcNet& t, const std::vector<LayerDev>& Ls, int k, c
     op.c.n_chunks = (T.kf + op.KC - 1) / op.KC;
     op.c.res_bytes = (uint32_t)(2 * T.nf * T.kf);
     op.c.stage_bytes = (uint32_t)(2 * kRows * op.KC);
-    op.c.tmem_cols = tmem_cols_for(T.nf);
+    op.c.tmem_cols = tmem_cols_for(2 * T.nf);
     op.c.status = S.status;
     op.nf = T.nf;
     op.kf = T.kf;
@@ -1191,7 +1421,7 @@ void launch_tc_forward(const TcNet& t, const std::vector<LayerDev>& Ls, int k, c
   op.c.n_chunks = T.fc_nkc;
   op.c.res_bytes = 0;
   op.c.stage_bytes = op.a_bytes + (uint32_t)(2 * op.BN * T.fc_kc);
-  op.c.tmem_cols = tmem_cols_for(op.BN);
+  op.c.tmem_cols = tmem_cols_for(2 * op.BN);
   op.c.status = S.status;
   op.W = T.Wf;
   op.B = P.B;

@@ -7,6 +7,7 @@
 //   per-property data [P, n_0] boxes, [P, N] intermediate bounds
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (tensor-map descriptors; header only)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -312,12 +313,20 @@ struct TcLayer {
   int fc_nmt_t;                // FC: 128-row tiles over n_in
   const uint16_t* Wt;
 };
+// Tensor maps of one conv layer's shadow operands, valid for one workspace
+// (base pointer) and batch size.
+struct TcMaps {
+  const void* base = nullptr;
+  int B = -1;
+  CUtensorMap m[4];            // forward: x_{k-1} by input stride phase; transposed: rho_k in m[0]
+};
 struct TcNet {
   int n = 0;
   int XH = 0, RH = 0;          // bf16 elements per subdomain of the two shadow rows
   int n1 = 0;                  // neurons of layer 1 (width of the centred-input constant)
   TcLayer T[kMaxLayers];       // T[k-1] = layer k
   uint16_t* d_w = nullptr;     // all re-laid weights (owned)
+  TcMaps fwd[kMaxLayers], tr[kMaxLayers];  // cached tensor maps per layer
 };
 // Shadows and per-call buffers of the BF16 iterations.
 struct TcState {
@@ -343,10 +352,10 @@ void launch_tc_centre(const TcNet& t, const LayerDev& L1, const Problem& P, cons
 // Transposed pass of layer k (1 <= k <= n-1) -> inner minimisation of layer
 // k-1; crown = 1 (k >= 2): the CROWN dual of layer k-1 instead (rho and its
 // shadow), so that the start and the iterations share the same products.
-void launch_tc_transposed(const TcNet& t, const std::vector<LayerDev>& Ls, int k, const Problem& P,
+void launch_tc_transposed(TcNet& t, const std::vector<LayerDev>& Ls, int k, const Problem& P,
                           const TcState& S, int n_sm, cudaStream_t s, int crown = 0);
 // Forward pass of layer k (1 <= k <= n-1) -> supergradient and Adam on rho_k.
-void launch_tc_forward(const TcNet& t, const std::vector<LayerDev>& Ls, int k, const Problem& P, const TcState& S,
+void launch_tc_forward(TcNet& t, const std::vector<LayerDev>& Ls, int k, const Problem& P, const TcState& S,
                        AdamStep st, int n_sm, cudaStream_t s);
 
 // ---------------------------------------------------------------- launchers

@@ -41,7 +41,7 @@ namespace ld {
 namespace {
 
 constexpr int kThreads = 256;                 // worker warps: 8, 2 per TMEM lane quadrant
-constexpr int kCtaThreads = kThreads + 32;    // + one warp that issues the MMAs
+constexpr int kCtaThreads = kThreads + 64;    // + a warp that issues the MMAs + a warp that issues TMA loads
 constexpr int kRows = 128;                    // M of every MMA = TMEM lanes
 constexpr int kFcKC = 128;                    // K chunk of the FC forward GEMM
 constexpr int kConvKC = 64;                   // K per pipeline stage of the forward conv GEMM
@@ -101,6 +101,18 @@ __device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, uint32_t parity, vola
   }
   return true;
 }
+// TMA tile load of a 4-D box (coordinates innermost first) into shared memory,
+// completion (bytes) counted on an mbarrier.
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
+constexpr int kFar = -(1 << 20);  // a box start this far out of range is all zero fill
+
 // Arrive on the mbarrier once all cp.async copies issued so far by this thread have landed.
 __device__ __forceinline__ void cp_arrive_noinc(uint32_t bar) {
   asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
@@ -114,17 +126,12 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                "l"(src), "r"(bytes), "r"(bar)
                : "memory");
 }
-// cp.async of 16 / 8 bytes; a copy with valid == false writes zeros.  The
+// cp.async of 16 bytes; a copy with valid == false writes zeros.  The
 // 16-byte form bypasses L1 (.cg): these kernels give most of the SM's
 // on-chip memory to shared memory, and the operands live in L2.
 __device__ __forceinline__ void cp16(uint32_t dst, const void* src, bool valid) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0) : "memory");
 }
-__device__ __forceinline__ void cp8(uint32_t dst, const void* src, bool valid) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(valid ? 8 : 0) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 // Generic-proxy writes to shared memory -> visible to the tensor core (async proxy).
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
@@ -178,6 +185,8 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+__host__ __device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
 __device__ __forceinline__ uint16_t bf16_bits(float f) {
   return __bfloat16_as_ushort(__float2bfloat16_rn(f));
 }
@@ -190,7 +199,7 @@ __device__ __forceinline__ uint4 pack8(const float (&v)[8]) {
   return u;
 }
 
-// Adam ascent step on one dual (same arithmetic as EpiAdam); returns new rho.
+// Adam arguments of the forward-pass epilogues.
 struct AdamArgs {
   const float* xB;
   float* rho;
@@ -199,22 +208,10 @@ struct AdamArgs {
   float beta1, beta2, eps;
   AdamStep st;
 };
-__device__ __forceinline__ float adam_update(const AdamArgs& a, size_t j, float xa) {
-  const float s = a.xB[j] - xa;
-  const float mm = a.beta1 * a.m[j] + (1.f - a.beta1) * s;
-  const float vv = a.beta2 * a.v[j] + (1.f - a.beta2) * s * s;
-  a.m[j] = mm;
-  a.v[j] = vv;
-  const float mhat = mm * a.st.inv_bc1;
-  const float vhat = vv * a.st.inv_bc2;
-  const float r = a.rho[j] + a.st.alpha * mhat / (sqrtf(vhat) + a.eps);
-  a.rho[j] = r;
-  return r;
-}
 
 // Adam on up to 8 duals: every load first (so that the 32 loads overlap
 // instead of forming 8 dependent round trips), then the updates and stores.
-// Same arithmetic as adam_update.
+// Same arithmetic as EpiAdam.
 __device__ __forceinline__ void adam8(const AdamArgs& a, const size_t (&j)[8], const bool (&on)[8],
                                       const float (&xa)[8], float (&rn)[8]) {
   float xb[8], m0[8], v0[8], r0[8];
@@ -294,10 +291,13 @@ struct TcCommon {
 
 // Forward conv of layer k: D[(b, p), o] = sum_{tap, c} x_{k-1}[b, tap(p), c] W[o, c, tap];
 // epilogue: Adam on rho_k.
-struct ConvFwdOp {
+struct alignas(128) ConvFwdOp {
   static constexpr bool kStageBulk = false;
+  static constexpr bool kTma = true;
+  CUtensorMap mx[4];           // x_{k-1} shadow by input stride phase (py, px): (c, x', y', b)
   TcCommon c;
-  int nf, kf, KC;              // N, K, K per stage (the last stage may be shorter)
+  int nf, kf, KC, kq;          // N, K, K per stage (the last stage may be shorter), channel groups per tap
+  int nsub, rows_y, tiles_b;   // tile = nsub subdomains x rows_y output rows (x all columns), or 1/tiles_b of one
   const uint16_t* W;
   int B, h, w, cout, ho, wo, kw, kh, S, pad, cp_in, cp_out;
   int XH, xh_off, RH, rh_off;
@@ -309,63 +309,33 @@ struct ConvFwdOp {
   const float* c1;
   AdamArgs ad;
 
-  // gather table: per K piece (16 B for cp_in >= 8, 8 B for cp_in == 4):
-  // (tap row offset, tap column offset, first channel, tap exists)
-  __device__ void prepare(int4* tab) const {
-    const int step = cp_in >= 8 ? 8 : 4;
-    for (int e = threadIdx.x; e < kf / step; e += kThreads) {
-      const int kel = e * step, tap = kel / cp_in, c0 = kel % cp_in;
-      tab[e] = make_int4(tap / kw - pad, tap % kw - pad, c0, tap < kh * kw ? 1 : 0);
-    }
-  }
+  __device__ void prepare(int4*) const {}
   __device__ void load_resident(uint32_t sres, uint32_t bar) const {
     mbar_expect_tx(bar, c.res_bytes);
     bulk_g2s(sres, W, c.res_bytes, bar);
   }
-  __device__ void load_stage(int tile, int chunk, uint32_t sst, uint32_t, const int4* tab) const {
+  __device__ void load_stage(int, int, uint32_t, uint32_t, const int4*) const {}
+  // TMA loads of one stage: one box of 8 channels x 128 output positions per
+  // k-group (tap, channel group), into the k-group's 128 x 16-byte sub-tile;
+  // lanes of the producer warp share the boxes.  Output (yo, xo) of tap (i, j)
+  // reads input (S yo + i - pad, S xo + j - pad) = phase (py, px) position
+  // (yo + dy, xo + dx): a contiguous box of that phase's map.
+  __device__ uint32_t stage_bytes_of(int chunk) const { return (uint32_t)((min(kf, (chunk + 1) * KC) - chunk * KC) / 8) * 2048u; }
+  __device__ void produce(int tile, int chunk, uint32_t sst, uint32_t bar, int lane) const {
     const int k8_lo = chunk * KC / 8, k8_hi = min(kf, (chunk + 1) * KC) / 8;
-    const int hw = ho * wo;
-    if (cp_in >= 16 && cp_in <= 64) {
-      // KQ = cp_in / 8 consecutive lanes load the KQ channel chunks of one tap
-      // of one pixel, so a warp reads whole pixels (contiguous along x)
-      const int KQ = cp_in / 8, kq = threadIdx.x % KQ, rpp = kThreads / KQ;
-      for (int rr = threadIdx.x / KQ; rr < kRows; rr += rpp) {
-        const int R = tile * kRows + rr;
-        const int b = R / hw, p = R - b * hw;
-        const int yo = p / wo, xo = p - yo * wo;
-        const bool row_ok = b < B;
-        const uint16_t* src_b = xh + (size_t)(row_ok ? b : 0) * XH + xh_off + kq * 8;
-        for (int k8 = k8_lo + kq; k8 < k8_hi; k8 += KQ) {
-          const int4 t = tab[k8];
-          const int yy = yo * S + t.x, xx = xo * S + t.y;
-          const bool ok = row_ok && t.w && yy >= 0 && yy < h && xx >= 0 && xx < w;
-          cp16(sst + chunk_off(rr, k8 - k8_lo, kRows), ok ? src_b + (size_t)(yy * w + xx) * cp_in : xh, ok);
-        }
+    const int b0 = tiles_b > 1 ? tile / tiles_b : tile * nsub;
+    const int yo0 = tiles_b > 1 ? (tile % tiles_b) * rows_y : 0;
+    for (int k8 = k8_lo + lane; k8 < k8_hi; k8 += 32) {
+      const int tap = k8 / kq, g = k8 - tap * kq;
+      const uint32_t dst = sst + (uint32_t)(k8 - k8_lo) * 2048u;
+      if (tap >= kh * kw) {  // K padding: a box entirely out of range (zeros)
+        tma_load_4d(dst, &mx[0], 0, kFar, kFar, b0, bar);
+        continue;
       }
-      return;
-    }
-    const int r = threadIdx.x & (kRows - 1);
-    const int R = tile * kRows + r;
-    const int b = R / hw, p = R - b * hw;
-    const int yo = p / wo, xo = p - yo * wo;
-    const bool row_ok = b < B;
-    const uint16_t* src_b = xh + (size_t)(row_ok ? b : 0) * XH + xh_off;
-    for (int k8 = k8_lo + (threadIdx.x >> 7); k8 < k8_hi; k8 += kThreads / kRows) {
-      const uint32_t dst = sst + chunk_off(r, k8 - k8_lo, kRows);
-      if (cp_in >= 8) {
-        const int4 t = tab[k8];
-        const int yy = yo * S + t.x, xx = xo * S + t.y;
-        const bool ok = row_ok && t.w && yy >= 0 && yy < h && xx >= 0 && xx < w;
-        cp16(dst, ok ? src_b + ((size_t)(yy * w + xx) * cp_in + t.z) : xh, ok);
-      } else {
-#pragma unroll
-        for (int hf = 0; hf < 2; ++hf) {
-          const int4 t = tab[2 * k8 + hf];
-          const int yy = yo * S + t.x, xx = xo * S + t.y;
-          const bool ok = row_ok && t.w && yy >= 0 && yy < h && xx >= 0 && xx < w;
-          cp8(dst + 8 * hf, ok ? src_b + ((size_t)(yy * w + xx) * cp_in + t.z) : xh, ok);
-        }
-      }
+      const int ii = tap / kw - pad, jj = tap % kw - pad;
+      const int dy = floor_div(ii, S), dx = floor_div(jj, S);
+      const int py = ii - dy * S, px = jj - dx * S;
+      tma_load_4d(dst, &mx[py * S + px], 8 * g, dx, yo0 + dy, b0, bar);
     }
   }
   __device__ void issue_mma(int, int chunk, uint32_t sres, uint32_t sst, uint32_t tmem) const {
@@ -411,11 +381,14 @@ struct ConvFwdOp {
 // a coalesced pair.  Epilogue: inner minimisation of layer k-1 (or its CROWN
 // dual, or the P0 box argmin).
 template <int SS>  // stride (1 or 2)
-struct ConvTOp {
+struct alignas(128) ConvTOp {
   static constexpr bool kStageBulk = false;
+  static constexpr bool kTma = true;
   static constexpr int S = SS;
+  CUtensorMap mr;              // rho_k shadow: (c, x, y, b)
   TcCommon c;
-  int nt, kt, KC, n_phase, na, nb;
+  int nt, kt, KC, n_phase, na, nb, kq;
+  int nsub, rows_y, tiles_b;   // tile = nsub subdomains x rows_y phase rows, or 1/tiles_b of one
   uint32_t sub_bytes;          // one phase's A tile in a stage: 128 x KC bf16
   const uint16_t* W;
   int B, cin, h, w, ho, wo, pad, cp_in, cp_out;
@@ -430,12 +403,7 @@ struct ConvTOp {
   int rhb_off, rhb_conv, rhb_hw, rhb_cp;  // layout of the shadow of rho_kb
   int pairs;                   // S == 2 and every flat index of an x-pair even (float2 accesses)
 
-  __device__ void prepare(int4* tab) const {
-    for (int e = threadIdx.x; e < kt / 8; e += kThreads) {
-      const int tap = (8 * e) / cp_out, o0 = (8 * e) % cp_out;
-      tab[e] = make_int4(tap / nb, tap % nb, o0, tap < na * nb ? 1 : 0);
-    }
-  }
+  __device__ void prepare(int4*) const {}
   __device__ void load_resident(uint32_t sres, uint32_t bar) const {
     mbar_expect_tx(bar, c.res_bytes);
     bulk_g2s(sres, W, c.res_bytes, bar);
@@ -447,36 +415,29 @@ struct ConvTOp {
     dy0 = (ry + pad - i0) / S;
     dx0 = (rx + pad - j0) / S;
   }
-  // chunks (rr, k8) of every phase for one row
-  __device__ void gather_row(int tile, int rr, int kq, int kstep, int k8_lo, int k8_hi, uint32_t sst,
-                             const int4* tab) const {
-    const int PW = w / S, PP = (h / S) * PW;
-    const int R = tile * kRows + rr;
-    const int b = R / PP, qq = R - b * PP, qy = qq / PW, qx = qq - qy * PW;
-    const bool row_ok = b < B;
-    const uint16_t* src_b = rh + (size_t)(row_ok ? b : 0) * RH + rh_off;
-    for (int ph = 0; ph < n_phase; ++ph) {
+  __device__ void load_stage(int, int, uint32_t, uint32_t, const int4*) const {}
+  __device__ uint32_t stage_bytes_of(int chunk) const {
+    return (uint32_t)(n_phase * (min(kt, (chunk + 1) * KC) - chunk * KC) / 8) * 2048u;
+  }
+  // TMA loads of one stage: per phase and k-group (tap (a, bb), channel
+  // group), one box of 8 channels x the tile's 128 phase positions (qy, qx)
+  // of rho_k at (qy + dy0 - a, qx + dx0 - bb); out-of-range pixels read zero.
+  __device__ void produce(int tile, int chunk, uint32_t sst, uint32_t bar, int lane) const {
+    const int k8_lo = chunk * KC / 8, nk = (min(kt, (chunk + 1) * KC) - chunk * KC) / 8;
+    const int b0 = tiles_b > 1 ? tile / tiles_b : tile * nsub;
+    const int qy0 = tiles_b > 1 ? (tile % tiles_b) * rows_y : 0;
+    for (int idx = lane; idx < n_phase * nk; idx += 32) {
+      const int ph = idx / nk, k8 = k8_lo + (idx - ph * nk);
+      const int tap = k8 / kq, g = k8 - tap * kq;
+      const uint32_t dst = sst + (uint32_t)ph * sub_bytes + (uint32_t)(k8 - k8_lo) * 2048u;
+      if (tap >= na * nb) {
+        tma_load_4d(dst, &mr, 0, kFar, kFar, b0, bar);
+        continue;
+      }
       int ry, rx, dy0, dx0;
       phase_geo(ph, ry, rx, dy0, dx0);
-      const uint32_t sub = sst + (uint32_t)ph * sub_bytes;
-      for (int k8 = k8_lo + kq; k8 < k8_hi; k8 += kstep) {
-        const int4 t = tab[k8];
-        const int y = qy + dy0 - t.x, x = qx + dx0 - t.y;
-        const bool ok = row_ok && t.w && y >= 0 && y < ho && x >= 0 && x < wo;
-        cp16(sub + chunk_off(rr, k8 - k8_lo, kRows), ok ? src_b + ((size_t)(y * wo + x) * cp_out + t.z) : rh, ok);
-      }
+      tma_load_4d(dst, &mr, 8 * g, dx0 - tap % nb, qy0 + dy0 - tap / nb, b0, bar);
     }
-  }
-  __device__ void load_stage(int tile, int chunk, uint32_t sst, uint32_t, const int4* tab) const {
-    const int k8_lo = chunk * KC / 8, k8_hi = min(kt, (chunk + 1) * KC) / 8;
-    if (cp_out >= 16 && cp_out <= 64) {
-      // KQ consecutive lanes load the KQ channel chunks of one tap of one pixel
-      const int KQ = cp_out / 8;
-      for (int rr = threadIdx.x / KQ; rr < kRows; rr += kThreads / KQ)
-        gather_row(tile, rr, threadIdx.x % KQ, KQ, k8_lo, k8_hi, sst, tab);
-      return;
-    }
-    gather_row(tile, threadIdx.x & (kRows - 1), threadIdx.x >> 7, kThreads / kRows, k8_lo, k8_hi, sst, tab);
   }
   __device__ void issue_mma(int, int chunk, uint32_t sres, uint32_t sst, uint32_t tmem) const {
     const uint32_t id = idesc_bf16(kRows, nt);
@@ -645,6 +606,7 @@ struct ConvTOp {
 // Forward FC of layer k: D[o, b] = sum_i W[o, i] x_{k-1}[b, i] (M = neurons,
 // N = subdomains); epilogue: Adam on rho_k.
 struct FcFwdOp {
+  static constexpr bool kTma = false;
   static constexpr bool kStageBulk = true;
   TcCommon c;
   int n_mt, BN, KC;
@@ -661,6 +623,8 @@ struct FcFwdOp {
 
   __device__ void prepare(int4*) const {}
   __device__ void load_resident(uint32_t, uint32_t) const {}
+  __device__ uint32_t stage_bytes_of(int) const { return 0; }
+  __device__ void produce(int, int, uint32_t, uint32_t, int) const {}
   __device__ void load_stage(int tile, int chunk, uint32_t sst, uint32_t bar, const int4*) const {
     const int mt = tile % n_mt, ntile = tile / n_mt;
     if (threadIdx.x == 0) {
@@ -711,6 +675,7 @@ struct FcFwdOp {
 // Transposed FC of layer k: D[i, b] = sum_o W[o, i] rho_k[b, o] (M = inputs,
 // N = subdomains); epilogue: inner minimisation of layer k-1.
 struct FcTOp {
+  static constexpr bool kTma = false;
   static constexpr bool kStageBulk = false;
   TcCommon c;
   int n_mt, BN, kt;
@@ -733,6 +698,8 @@ struct FcTOp {
     mbar_expect_tx(bar, a_bytes);
     bulk_g2s(sres, W + (size_t)(blockIdx.x % n_mt) * kRows * kt, a_bytes, bar);
   }
+  __device__ uint32_t stage_bytes_of(int) const { return 0; }
+  __device__ void produce(int, int, uint32_t, uint32_t, int) const {}
   __device__ void load_stage(int tile, int, uint32_t sst, uint32_t, const int4*) const {
     const int ntile = tile / n_mt;
     const int nk8 = kt / 8;
@@ -845,7 +812,7 @@ __device__ __forceinline__ void cp_wait_pending() {
 // There is no CTA-wide barrier inside the loop; every wait is bounded and a
 // time-out anywhere makes every other wait give up (abort flag).
 template <class Op, int NS>
-__global__ void __launch_bounds__(kCtaThreads, 2) tc_kernel(const Op op) {
+__global__ void __launch_bounds__(kCtaThreads, 2) tc_kernel(const __grid_constant__ Op op) {
   constexpr int LAG = NS - 1;
   extern __shared__ __align__(1024) uint8_t dyn_smem[];
   __shared__ __align__(8) uint64_t bar_res;
@@ -865,7 +832,7 @@ __global__ void __launch_bounds__(kCtaThreads, 2) tc_kernel(const Op op) {
   if (tid == 0) {
     mbar_init(b_res, 1);
     for (int i = 0; i < NS; ++i) {
-      mbar_init(b_full + 8 * i, kThreads + (Op::kStageBulk ? 1 : 0));
+      mbar_init(b_full + 8 * i, Op::kTma ? 1 : kThreads + (Op::kStageBulk ? 1 : 0));
       mbar_init(b_free + 8 * i, 1);
     }
     for (int i = 0; i < 2; ++i) {
@@ -890,7 +857,34 @@ __global__ void __launch_bounds__(kCtaThreads, 2) tc_kernel(const Op op) {
   const int n_stages = my_tiles * nch;
   auto tile_of = [&](int st) { return (int)blockIdx.x + (st / nch) * (int)gridDim.x; };
 
-  if (tid < kThreads) {
+  if (Op::kTma && tid < kThreads) {
+    // ---------------------------------------------------------- worker warps (TMA-fed): epilogues only
+    for (int tl = 0; tl < my_tiles; ++tl) {
+      const bool ok = mbar_wait_ab(b_af + 8 * (tl & 1), (uint32_t)((tl >> 1) & 1), abort);
+      if (__any_sync(0xffffffffu, !ok)) break;  // warp-uniform: the TMEM loads are warp-collective
+      tc_fence_after();
+      op.epilogue(tile_of(tl * nch), tmem + (uint32_t)(tl & 1) * dcols);
+      tc_fence_before();
+      mbar_arrive(b_ae + 8 * (tl & 1));
+    }
+  } else if (Op::kTma && warp == kThreads / 32 + 1) {
+    // ---------------------------------------------------------- TMA producer warp
+    const int lane = tid & 31;
+    int issued = 0;
+    for (int st = 0; st < n_stages; ++st) {
+      const int bi = st % NS;
+      const bool fr = st < NS || mbar_wait_ab(b_free + 8 * bi, (uint32_t)(((st / NS) - 1) & 1), abort);
+      if (__any_sync(0xffffffffu, !fr)) break;
+      if (lane == 0) mbar_expect_tx(b_full + 8 * bi, op.stage_bytes_of(st % nch));
+      __syncwarp();
+      op.produce(tile_of(st), st % nch, sst0 + (uint32_t)bi * op.c.stage_bytes, b_full + 8 * bi, lane);
+      issued = st + 1;
+    }
+    // loads issued for stages never consumed must land before the CTA exits
+    if (lane == 0 && *abort)
+      for (int st = (issued > NS ? issued - NS : 0); st < issued; ++st)
+        if (!mbar_wait(b_full + 8 * (st % NS), (uint32_t)((st / NS) & 1))) break;
+  } else if (tid < kThreads) {
     // ---------------------------------------------------------- worker warps
     int issued = 0;  // stages whose loads this thread issued (thread 0: incl. bulk copies)
     for (int i = 0; i < n_stages + LAG; ++i) {
@@ -1015,6 +1009,17 @@ uint16_t host_bf16(float f) {
 // Element (r, k) of an R-row canonical tile (see chunk_off).
 inline size_t canon(int r, int k, int R) { return ((size_t)(k / 8) * R + r) * 8 + (k % 8); }
 
+// A launch that cannot be encoded sets LD_ERR_UNSUPPORTED in the status word
+// (stream-ordered is not needed: nothing of the launch ran).
+void atomic_status_host(int* status) {
+  int cur = 0;
+  if (cudaMemcpy(&cur, status, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && cur == 0) {
+    const int v = (int)LD_ERR_UNSUPPORTED;
+    cudaMemcpy(status, &v, sizeof(int), cudaMemcpyHostToDevice);
+  }
+  cudaGetLastError();
+}
+
 uint32_t tmem_cols_for(int n) {
   uint32_t c = 32;
   while ((int)c < n) c <<= 1;
@@ -1104,6 +1109,62 @@ int fc_bn(int n_mt, int B, int n_sm) {
   return bn;
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// dependency on the driver library).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// 4-D BF16 tensor map: dims innermost first, byte strides of dims 1..3, box
+// (8 channels, b1, b2, b3), no swizzle, out-of-range elements read as zero.
+bool encode_map(CUtensorMap* m, const void* base, uint64_t d0, uint64_t d1, uint64_t d2, uint64_t d3, uint64_t s1,
+                uint64_t s2, uint64_t s3, uint32_t b1, uint32_t b2, uint32_t b3) {
+  const EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  const cuuint64_t gd[4] = {d0, d1, d2, d3};
+  const cuuint64_t gs[3] = {s1, s2, s3};
+  const cuuint32_t bd[4] = {8, b1, b2, b3};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), gd, gs, bd, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Rows of a 128-row tile over a plane of PH x PW positions per subdomain:
+// nsub whole planes (PH*PW divides 128), or rows_y rows of one plane
+// (128 / PW rows; the plane has tiles_b such tiles).  false: neither fits.
+bool plane_tiling(int PH, int PW, int& nsub, int& rows_y, int& tiles_b) {
+  const int PP = PH * PW;
+  if (PP <= kRows && kRows % PP == 0) {
+    nsub = kRows / PP;
+    rows_y = PH;
+    tiles_b = 1;
+    return PW <= 256 && PH <= 256 && nsub <= 256;
+  }
+  if (PP % kRows == 0 && kRows % PW == 0) {
+    nsub = 1;
+    rows_y = kRows / PW;
+    tiles_b = PP / kRows;
+    return PW <= 256;
+  }
+  return false;
+}
+
 }  // namespace
 
 ld_status build_tc_net(const std::vector<LayerDev>& Ls, TcNet* out) {
@@ -1129,8 +1190,13 @@ ld_status build_tc_net(const std::vector<LayerDev>& Ls, TcNet* out) {
     if (L.kind == LD_LAYER_CONV) {
       const int S = L.stride;
       if (!(S == 1 || S == 2) || L.h % S || L.w % S || L.cout > 256 || L.cin > 256) return LD_ERR_UNSUPPORTED;
-      T.cp_in = L.cin <= 4 ? 4 : round_up(L.cin, 8);
+      T.cp_in = round_up(L.cin < 8 ? 8 : L.cin, 8);  // >= 16-byte rows for the TMA boxes
       T.cp_out = round_up(L.cout, 8);
+      {
+        int ns, ry, tb;
+        if (!plane_tiling(L.ho, L.wo, ns, ry, tb) || !plane_tiling(L.h / S, L.w / S, ns, ry, tb))
+          return LD_ERR_UNSUPPORTED;
+      }
       T.xh_len = round_up(L.h * L.w * T.cp_in, 8);
       T.rh_len = L.ho * L.wo * T.cp_out;
       // forward: B operand [nf x kf], K = tap * cp_in + c
@@ -1261,13 +1327,27 @@ void launch_tc_centre(const TcNet& t, const LayerDev& L1, const Problem& P, cons
 }
 
 template <int SS>
-void launch_conv_t(const TcNet& t, const TcLayer& T, const LayerDev& L, const Problem& P, const TcState& S, int kb,
+void launch_conv_t(TcNet& t, int k, const TcLayer& T, const LayerDev& L, const Problem& P, const TcState& S, int kb,
                    int r_off_kb, int crown, int rhb_off, int rhb_conv, int rhb_hw, int rhb_cp, int n_sm,
                    cudaStream_t s) {
     ConvTOp<SS> op{};
-    const int PP = (L.h / L.stride) * (L.w / L.stride);
+    const int PH = L.h / L.stride, PW = L.w / L.stride;
+    if (!plane_tiling(PH, PW, op.nsub, op.rows_y, op.tiles_b)) return;
+    TcMaps& mc = t.tr[k - 1];
+    if (mc.base != S.rh || mc.B != P.B) {
+      // rho_k shadow of this layer: (cp_out, wo, ho, B), subdomain rows RH apart
+      if (!encode_map(&mc.m[0], S.rh + T.rh_off, T.cp_out, L.wo, L.ho, P.B, (uint64_t)T.cp_out * 2,
+                      (uint64_t)L.wo * T.cp_out * 2, (uint64_t)t.RH * 2, PW, op.rows_y, op.nsub)) {
+        atomic_status_host(S.status);
+        return;
+      }
+      mc.base = S.rh;
+      mc.B = P.B;
+    }
+    op.mr = mc.m[0];
+    op.kq = T.cp_out / 8;
     op.n_phase = T.n_phase;
-    op.c.n_tiles = (int)(((size_t)P.B * PP + kRows - 1) / kRows);
+    op.c.n_tiles = op.tiles_b > 1 ? P.B * op.tiles_b : (P.B + op.nsub - 1) / op.nsub;
     op.KC = T.kt < kConvTKC ? T.kt : kConvTKC;
     op.c.n_chunks = (T.kt + op.KC - 1) / op.KC;
     op.sub_bytes = (uint32_t)(2 * kRows * op.KC);
@@ -1311,7 +1391,7 @@ void launch_conv_t(const TcNet& t, const TcLayer& T, const LayerDev& L, const Pr
     launch_op(op, n_sm, s);
 }
 
-void launch_tc_transposed(const TcNet& t, const std::vector<LayerDev>& Ls, int k, const Problem& P,
+void launch_tc_transposed(TcNet& t, const std::vector<LayerDev>& Ls, int k, const Problem& P,
                           const TcState& S, int n_sm, cudaStream_t s, int crown) {
   const LayerDev& L = Ls[k - 1];
   const TcLayer& T = t.T[k - 1];
@@ -1329,9 +1409,9 @@ void launch_tc_transposed(const TcNet& t, const std::vector<LayerDev>& Ls, int k
   }
   if (L.kind == LD_LAYER_CONV) {
     if (L.stride == 2)
-      launch_conv_t<2>(t, T, L, P, S, kb, r_off_kb, crown, rhb_off, rhb_conv, rhb_hw, rhb_cp, n_sm, s);
+      launch_conv_t<2>(t, k, T, L, P, S, kb, r_off_kb, crown, rhb_off, rhb_conv, rhb_hw, rhb_cp, n_sm, s);
     else
-      launch_conv_t<1>(t, T, L, P, S, kb, r_off_kb, crown, rhb_off, rhb_conv, rhb_hw, rhb_cp, n_sm, s);
+      launch_conv_t<1>(t, k, T, L, P, S, kb, r_off_kb, crown, rhb_off, rhb_conv, rhb_hw, rhb_cp, n_sm, s);
     return;
   }
   FcTOp op{};
@@ -1369,13 +1449,31 @@ void launch_tc_transposed(const TcNet& t, const std::vector<LayerDev>& Ls, int k
   launch_op(op, n_sm, s);
 }
 
-void launch_tc_forward(const TcNet& t, const std::vector<LayerDev>& Ls, int k, const Problem& P, const TcState& S,
+void launch_tc_forward(TcNet& t, const std::vector<LayerDev>& Ls, int k, const Problem& P, const TcState& S,
                        AdamStep st, int n_sm, cudaStream_t s) {
   const LayerDev& L = Ls[k - 1];
   const TcLayer& T = t.T[k - 1];
   if (L.kind == LD_LAYER_CONV) {
     ConvFwdOp op{};
-    op.c.n_tiles = (int)(((size_t)P.B * L.ho * L.wo + kRows - 1) / kRows);
+    if (!plane_tiling(L.ho, L.wo, op.nsub, op.rows_y, op.tiles_b)) return;
+    const int SS = L.stride;
+    TcMaps& mc = t.fwd[k - 1];
+    if (mc.base != S.xh || mc.B != P.B) {
+      // x_{k-1} shadow by input stride phase (py, px): positions (S y' + py, S x' + px)
+      for (int py = 0; py < SS; ++py)
+        for (int px = 0; px < SS; ++px)
+          if (!encode_map(&mc.m[py * SS + px], S.xh + T.xh_off + (size_t)(py * L.w + px) * T.cp_in, T.cp_in,
+                          (L.w - px + SS - 1) / SS, (L.h - py + SS - 1) / SS, P.B, (uint64_t)SS * T.cp_in * 2,
+                          (uint64_t)SS * L.w * T.cp_in * 2, (uint64_t)t.XH * 2, L.wo, op.rows_y, op.nsub)) {
+            atomic_status_host(S.status);
+            return;
+          }
+      mc.base = S.xh;
+      mc.B = P.B;
+    }
+    for (int i = 0; i < SS * SS; ++i) op.mx[i] = mc.m[i];
+    op.kq = T.cp_in / 8;
+    op.c.n_tiles = op.tiles_b > 1 ? P.B * op.tiles_b : (P.B + op.nsub - 1) / op.nsub;
     op.KC = T.kf < kConvKC ? T.kf : kConvKC;
     op.c.n_chunks = (T.kf + op.KC - 1) / op.KC;
     op.c.res_bytes = (uint32_t)(2 * T.nf * T.kf);

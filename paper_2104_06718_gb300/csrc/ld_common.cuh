@@ -308,8 +308,10 @@ struct TcLayer {
   int fc_kc, fc_nkc, fc_nmt;   // FC: K chunk, chunks, 128-row tiles over n_out
   const uint16_t* Wf;
   // transposed GEMM operand
-  int nt, kt;                  // conv: N = cin rounded to 16, K per stride phase; FC: K = rh_len
-  int n_phase, na, nb;         // conv: stride phases, taps per phase along y / x
+  int nt, kt;                  // conv: N = phases x cg rounded to 16, K = taps x cp_out; FC: K = rh_len
+  int n_phase, na, nb;         // conv: stride phases, neighbourhood rows / columns of rho_k read per position
+  int cg;                      // conv: output columns per phase (cin rounded to 4 or 8)
+  int dmy, dmx;                // conv: offset of the neighbourhood's first row / column
   int fc_nmt_t;                // FC: 128-row tiles over n_in
   const uint16_t* Wt;
 };

@@ -31,6 +31,7 @@
 // LD_ERR_TIMEOUT in the status word and all threads leave the tile loop.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -45,7 +46,7 @@ constexpr int kCtaThreads = kThreads + 64;    // + a warp that issues the MMAs +
 constexpr int kRows = 128;                    // M of every MMA = TMEM lanes
 constexpr int kFcKC = 128;                    // K chunk of the FC forward GEMM
 constexpr int kConvKC = 64;                   // K per pipeline stage of the forward conv GEMM
-constexpr int kConvTKC = 32;                  // K per stage and phase of the transposed conv GEMM
+constexpr int kConvTKC = 96;                  // K per stage of the transposed conv GEMM
 constexpr int kTabMax = 256;                  // gather table entries (K pieces)
 constexpr unsigned long long kWaitNs = 2000000000ull;
 constexpr size_t kSmemBudget = 216 * 1024;    // dynamic shared memory a launch may ask for
@@ -341,8 +342,12 @@ struct alignas(128) ConvFwdOp {
   __device__ void issue_mma(int, int chunk, uint32_t sres, uint32_t sst, uint32_t tmem) const {
     const uint32_t id = idesc_bf16(kRows, nf);
     const int s0 = chunk * KC / 16, ns = (min(kf, (chunk + 1) * KC) - chunk * KC) / 16;
-    for (int s = 0; s < ns; ++s)
-      mma_bf16(tmem, op_desc(sst, s, kRows), op_desc(sres, s0 + s, nf), id, (chunk > 0 || s > 0) ? 1u : 0u);
+    uint64_t da = op_desc(sst, 0, kRows), db = op_desc(sres, s0, nf);
+    for (int s = 0; s < ns; ++s) {
+      mma_bf16(tmem, da, db, id, (chunk > 0 || s > 0) ? 1u : 0u);
+      da += (uint64_t)(2 * kRows * 16 >> 4);
+      db += (uint64_t)(2 * nf * 16 >> 4);
+    }
   }
   __device__ void epilogue(int tile, uint32_t tmem) const {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = warp & 3, half = warp >> 2;
@@ -371,25 +376,24 @@ struct alignas(128) ConvFwdOp {
   }
 };
 
-// Transposed conv of layer k, all S*S stride phases of a tile together:
-// rows = (b, qy, qx) of the phase plane; phase (ry, rx) has its own A tile
-// and weight matrix and accumulates into its own column block of D:
-//   g_{k-1}[b, c, S qy + ry, S qx + rx] = sum_{a, bb, o} W[o, c, i0 + S a, j0 + S bb]
-//                                          rho_k[b, o, qy + dy0 - a, qx + dx0 - bb]
-// so a thread's epilogue owns the S x S output block of its row: for S = 2
-// the two x-phases of a row are adjacent pixels and every epilogue access is
-// a coalesced pair.  Epilogue: inner minimisation of layer k-1 (or its CROWN
-// dual, or the P0 box argmin).
+// Transposed conv of layer k as one stride-1 convolution over rho_k: rows =
+// (b, qy, qx) positions of the stride-phase plane; K = the na x nb pixels of
+// rho_k around (qy, qx) (offset (dmy, dmx)) x channels; output column
+// ph * cg + c = g_{k-1}[b, c, S qy + ry, S qx + rx], ph = ry * S + rx
+//   (Sec. 5.2's transposed pass, W_k^T rho_k, with the S x S output block of a
+//    position computed together; weights of taps a phase does not use are 0).
+// For S = 2 each warp half takes one output row parity ry and holds both
+// x-phases, i.e. two adjacent pixels: every epilogue access is a coalesced
+// pair.  Epilogue: inner minimisation of layer k-1 (or its CROWN dual, or
+// the P0 box argmin).
 template <int SS>  // stride (1 or 2)
 struct alignas(128) ConvTOp {
   static constexpr bool kStageBulk = false;
   static constexpr bool kTma = true;
-  static constexpr int S = SS;
   CUtensorMap mr;              // rho_k shadow: (c, x, y, b)
   TcCommon c;
-  int nt, kt, KC, n_phase, na, nb, kq;
+  int nt, kt, KC, cg, na, nb, dmy, dmx, kq;
   int nsub, rows_y, tiles_b;   // tile = nsub subdomains x rows_y phase rows, or 1/tiles_b of one
-  uint32_t sub_bytes;          // one phase's A tile in a stage: 128 x KC bf16
   const uint16_t* W;
   int B, cin, h, w, ho, wo, pad, cp_in, cp_out;
   int XH, xh_off, RH, rh_off;
@@ -408,45 +412,34 @@ struct alignas(128) ConvTOp {
     mbar_expect_tx(bar, c.res_bytes);
     bulk_g2s(sres, W, c.res_bytes, bar);
   }
-  __device__ void phase_geo(int ph, int& ry, int& rx, int& dy0, int& dx0) const {
-    ry = ph / S;
-    rx = ph - ry * S;
-    const int i0 = (ry + pad) % S, j0 = (rx + pad) % S;
-    dy0 = (ry + pad - i0) / S;
-    dx0 = (rx + pad - j0) / S;
-  }
   __device__ void load_stage(int, int, uint32_t, uint32_t, const int4*) const {}
   __device__ uint32_t stage_bytes_of(int chunk) const {
-    return (uint32_t)(n_phase * (min(kt, (chunk + 1) * KC) - chunk * KC) / 8) * 2048u;
+    return (uint32_t)((min(kt, (chunk + 1) * KC) - chunk * KC) / 8) * 2048u;
   }
-  // TMA loads of one stage: per phase and k-group (tap (a, bb), channel
-  // group), one box of 8 channels x the tile's 128 phase positions (qy, qx)
-  // of rho_k at (qy + dy0 - a, qx + dx0 - bb); out-of-range pixels read zero.
+  // TMA loads of one stage: per k-group (neighbourhood pixel, channel group)
+  // one box of 8 channels x the tile's 128 positions of rho_k at
+  // (qy + dmy + ty, qx + dmx + tx); out-of-range pixels read zero.
   __device__ void produce(int tile, int chunk, uint32_t sst, uint32_t bar, int lane) const {
-    const int k8_lo = chunk * KC / 8, nk = (min(kt, (chunk + 1) * KC) - chunk * KC) / 8;
+    const int k8_lo = chunk * KC / 8, k8_hi = min(kt, (chunk + 1) * KC) / 8;
     const int b0 = tiles_b > 1 ? tile / tiles_b : tile * nsub;
     const int qy0 = tiles_b > 1 ? (tile % tiles_b) * rows_y : 0;
-    for (int idx = lane; idx < n_phase * nk; idx += 32) {
-      const int ph = idx / nk, k8 = k8_lo + (idx - ph * nk);
+    for (int k8 = k8_lo + lane; k8 < k8_hi; k8 += 32) {
       const int tap = k8 / kq, g = k8 - tap * kq;
-      const uint32_t dst = sst + (uint32_t)ph * sub_bytes + (uint32_t)(k8 - k8_lo) * 2048u;
-      if (tap >= na * nb) {
+      const uint32_t dst = sst + (uint32_t)(k8 - k8_lo) * 2048u;
+      if (tap >= na * nb)
         tma_load_4d(dst, &mr, 0, kFar, kFar, b0, bar);
-        continue;
-      }
-      int ry, rx, dy0, dx0;
-      phase_geo(ph, ry, rx, dy0, dx0);
-      tma_load_4d(dst, &mr, 8 * g, dx0 - tap % nb, qy0 + dy0 - tap / nb, b0, bar);
+      else
+        tma_load_4d(dst, &mr, 8 * g, dmx + tap % nb, qy0 + dmy + tap / nb, b0, bar);
     }
   }
   __device__ void issue_mma(int, int chunk, uint32_t sres, uint32_t sst, uint32_t tmem) const {
     const uint32_t id = idesc_bf16(kRows, nt);
     const int s0 = chunk * KC / 16, ns = (min(kt, (chunk + 1) * KC) - chunk * KC) / 16;
-    for (int ph = 0; ph < n_phase; ++ph) {
-      const uint32_t wb = sres + (uint32_t)(ph * nt * kt * 2), a = sst + (uint32_t)ph * sub_bytes;
-      for (int s = 0; s < ns; ++s)
-        mma_bf16(tmem + (uint32_t)(ph * nt), op_desc(a, s, kRows), op_desc(wb, s0 + s, nt), id,
-                 (chunk > 0 || s > 0) ? 1u : 0u);
+    uint64_t da = op_desc(sst, 0, kRows), db = op_desc(sres, s0, nt);
+    for (int s = 0; s < ns; ++s) {
+      mma_bf16(tmem, da, db, id, (chunk > 0 || s > 0) ? 1u : 0u);
+      da += (uint64_t)(2 * kRows * 16 >> 4);
+      db += (uint64_t)(2 * nt * 16 >> 4);
     }
   }
   // CROWN dual of neuron jn (layer kb) of subdomain b: rho and its shadow
@@ -457,147 +450,163 @@ struct alignas(128) ConvTOp {
     const int pos = rhb_conv ? (jn % rhb_hw) * rhb_cp + jn / rhb_hw : jn;
     rh[(size_t)b * RH + rhb_off + pos] = bf16_bits(r);
   }
+  // pixels (yy, x0) and (yy, x0 + 1) (g0, g1 = their g for channels c0 + e, e < ne)
+  __device__ void pair_out(int b, int prop, int yy, int x0, int c0, int ne, const float (&g0)[8],
+                           const float (&g1)[8]) const {
+    const int hw = h * w;
+    if (crown) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        if (e < ne) {
+          const int jn = (c0 + e) * hw + yy * w + x0;
+          crown_one(b, jn, g0[e]);
+          crown_one(b, jn + 1, g1[e]);
+        }
+      return;
+    }
+    float xv0[8], xv1[8];
+#pragma unroll
+    for (int e4 = 0; e4 < 8; e4 += 4) {
+      if (kb == 0) {
+        float2 lo[4], up[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (e4 + e < ne) {
+            const size_t j = (size_t)prop * P.n0 + (c0 + e4 + e) * hw + yy * w + x0;
+            lo[e] = *reinterpret_cast<const float2*>(P.l0 + j);
+            up[e] = *reinterpret_cast<const float2*>(P.u0 + j);
+          }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          xv0[e4 + e] = xv1[e4 + e] = 0.f;
+          if (e4 + e < ne) {
+            // P0 (Eq. box_bounds_sol): x0 = u0 where g_0 >= 0, else l0; stored centred
+            const float h0 = 0.5f * (up[e].x - lo[e].x), h1 = 0.5f * (up[e].y - lo[e].y);
+            xv0[e4 + e] = g0[e4 + e] >= 0.f ? h0 : -h0;
+            xv1[e4 + e] = g1[e4 + e] >= 0.f ? h1 : -h1;
+          }
+        }
+      } else {
+        float2 rr[4], lo[4], up[4];
+        char2 mk[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (e4 + e < ne) {
+            const int jf = r_off_kb + (c0 + e4 + e) * hw + yy * w + x0;
+            rr[e] = *reinterpret_cast<const float2*>(rho + (size_t)b * P.N + jf);
+            lo[e] = *reinterpret_cast<const float2*>(P.lbk + (size_t)prop * P.N + jf);
+            up[e] = *reinterpret_cast<const float2*>(P.ubk + (size_t)prop * P.N + jf);
+            mk[e] = P.mask ? *reinterpret_cast<const char2*>(P.mask + (size_t)b * P.N + jf) : make_char2(0, 0);
+          }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          xv0[e4 + e] = xv1[e4 + e] = 0.f;
+          if (e4 + e < ne) {
+            // split-mask clamp (Sec. 2.3.2), as clamped_bounds
+            float l0v = lo[e].x, u0v = up[e].x, l1v = lo[e].y, u1v = up[e].y;
+            if (mk[e].x > 0) l0v = fmaxf(l0v, 0.f);
+            if (mk[e].x < 0) u0v = fminf(u0v, 0.f);
+            if (mk[e].y > 0) l1v = fmaxf(l1v, 0.f);
+            if (mk[e].y < 0) u1v = fminf(u1v, 0.f);
+            float2 xb;
+            argmin_sel(rr[e].x, g0[e4 + e], l0v, u0v, xb.x, xv0[e4 + e]);
+            argmin_sel(rr[e].y, g1[e4 + e], l1v, u1v, xb.y, xv1[e4 + e]);
+            const int jf = r_off_kb + (c0 + e4 + e) * hw + yy * w + x0;
+            *reinterpret_cast<float2*>(xB + (size_t)b * P.N + jf) = xb;
+          }
+        }
+      }
+    }
+    uint16_t* dst = xh + (size_t)b * XH + xh_off + (size_t)(yy * w + x0) * cp_in + c0;
+    *reinterpret_cast<uint4*>(dst) = pack8(xv0);
+    *reinterpret_cast<uint4*>(dst + cp_in) = pack8(xv1);
+  }
+  // one pixel (yy, xx), channels c0 + e, e < ne
+  __device__ void single_out(int b, int prop, int pix, int c0, int ne, const float (&g)[8]) const {
+    const int hw = h * w;
+    if (crown) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        if (e < ne) crown_one(b, (c0 + e) * hw + pix, g[e]);
+      return;
+    }
+    float xv[8];
+    if (kb == 0) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        xv[e] = 0.f;
+        if (e < ne) {
+          const int jn = (c0 + e) * hw + pix;
+          const float hw0 = 0.5f * (P.u0[(size_t)prop * P.n0 + jn] - P.l0[(size_t)prop * P.n0 + jn]);
+          xv[e] = g[e] >= 0.f ? hw0 : -hw0;
+        }
+      }
+    } else if (SS == 1) {
+      int bb[8], jf[8];
+      bool on[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        on[e] = e < ne;
+        bb[e] = b;
+        jf[e] = r_off_kb + (c0 + e) * hw + pix;
+      }
+      argmin8(P, rho, xB, bb, jf, on, g, xv);
+    } else {  // stride 2 without pair alignment: one neuron at a time (small code, rare)
+      for (int e = 0; e < 8; ++e) {
+        xv[e] = 0.f;
+        if (e >= ne) continue;
+        const int jf = r_off_kb + (c0 + e) * hw + pix;
+        float l, u, xb;
+        clamped_bounds(P, b, jf, l, u);
+        argmin_sel(rho[(size_t)b * P.N + jf], g[e], l, u, xb, xv[e]);
+        xB[(size_t)b * P.N + jf] = xb;
+      }
+    }
+    *reinterpret_cast<uint4*>(xh + (size_t)b * XH + xh_off + (size_t)pix * cp_in + c0) = pack8(xv);
+  }
   __device__ void epilogue(int tile, uint32_t tmem) const {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = warp & 3, half = warp >> 2;
-    const int PW = w / SS, PP = (h / SS) * PW, hw = h * w;
+    const int PW = w / SS, PP = (h / SS) * PW;
     const int R = tile * kRows + q * 32 + lane;
     const int b = R / PP, qq = R - b * PP, qy = qq / PW, qx = qq - qy * PW;
     const bool row_ok = b < B;
     const int prop = row_ok ? prop_of(P, b) : 0;
     const uint32_t lanes = (uint32_t)(q * 32) << 16;
-    const int ngroups = (nt + 7) / 8;  // channel groups of 8, split between the two warp halves
-    const int c_hi = crown ? cin : min(cin, cp_in);
-    for (int cg = half; cg < ngroups; cg += 2) {
-      const int c0 = cg * 8;
-#pragma unroll
-      for (int ry = 0; ry < SS; ++ry) {
-        // accumulators of the phases (ry, 0 .. SS-1): warp-collective loads first
+    if (SS == 2) {
+      // this half: output row parity ry = half, both x-phases
+      const int ry = half, yy = 2 * qy + ry, x0 = 2 * qx;
+      const int step = cg == 4 ? 4 : 8;
+      for (int c0 = 0; c0 < cin; c0 += step) {
         float g0[8], g1[8];
-        tmem_ld8(tmem + lanes + (uint32_t)((ry * SS) * nt + c0), g0);
-        if (SS == 2) tmem_ld8(tmem + lanes + (uint32_t)((ry * SS + 1) * nt + c0), g1);
-        if (!row_ok || c0 >= c_hi) continue;
-        const int yy = SS * qy + ry, x0 = SS * qx;
-        if (crown) {
+        if (cg == 4) {  // one load: [phase (ry,0) c0..3 | phase (ry,1) c0..3]
+          float v[8];
+          tmem_ld8(tmem + lanes + (uint32_t)(2 * ry * 4), v);
 #pragma unroll
-          for (int e = 0; e < 8; ++e)
-            if (c0 + e < cin) {
-              const int jn = (c0 + e) * hw + yy * w + x0;
-              crown_one(b, jn, g0[e]);
-              if (SS == 2) crown_one(b, jn + 1, g1[e]);
-            }
-          continue;
-        }
-        if (SS == 2 && pairs) {
-          // pixels (yy, x0) and (yy, x0 + 1): every access a coalesced pair
-          float xv0[8], xv1[8];
-#pragma unroll
-          for (int e4 = 0; e4 < 8; e4 += 4) {
-            if (kb == 0) {
-              float2 lo[4], up[4];
-#pragma unroll
-              for (int e = 0; e < 4; ++e)
-                if (c0 + e4 + e < cin) {
-                  const size_t j = (size_t)prop * P.n0 + (c0 + e4 + e) * hw + yy * w + x0;
-                  lo[e] = *reinterpret_cast<const float2*>(P.l0 + j);
-                  up[e] = *reinterpret_cast<const float2*>(P.u0 + j);
-                }
-#pragma unroll
-              for (int e = 0; e < 4; ++e) {
-                xv0[e4 + e] = xv1[e4 + e] = 0.f;
-                if (c0 + e4 + e < cin) {
-                  // P0 (Eq. box_bounds_sol): x0 = u0 where g_0 >= 0, else l0; stored centred
-                  const float h0 = 0.5f * (up[e].x - lo[e].x), h1 = 0.5f * (up[e].y - lo[e].y);
-                  xv0[e4 + e] = g0[e4 + e] >= 0.f ? h0 : -h0;
-                  xv1[e4 + e] = g1[e4 + e] >= 0.f ? h1 : -h1;
-                }
-              }
-            } else {
-              float2 rr[4], lo[4], up[4];
-              char2 mk[4];
-#pragma unroll
-              for (int e = 0; e < 4; ++e)
-                if (c0 + e4 + e < cin) {
-                  const int jf = r_off_kb + (c0 + e4 + e) * hw + yy * w + x0;
-                  rr[e] = *reinterpret_cast<const float2*>(rho + (size_t)b * P.N + jf);
-                  lo[e] = *reinterpret_cast<const float2*>(P.lbk + (size_t)prop * P.N + jf);
-                  up[e] = *reinterpret_cast<const float2*>(P.ubk + (size_t)prop * P.N + jf);
-                  mk[e] = P.mask ? *reinterpret_cast<const char2*>(P.mask + (size_t)b * P.N + jf) : make_char2(0, 0);
-                }
-#pragma unroll
-              for (int e = 0; e < 4; ++e) {
-                xv0[e4 + e] = xv1[e4 + e] = 0.f;
-                if (c0 + e4 + e < cin) {
-                  // split-mask clamp (Sec. 2.3.2), as clamped_bounds
-                  float l0v = lo[e].x, u0v = up[e].x, l1v = lo[e].y, u1v = up[e].y;
-                  if (mk[e].x > 0) l0v = fmaxf(l0v, 0.f);
-                  if (mk[e].x < 0) u0v = fminf(u0v, 0.f);
-                  if (mk[e].y > 0) l1v = fmaxf(l1v, 0.f);
-                  if (mk[e].y < 0) u1v = fminf(u1v, 0.f);
-                  float2 xb;
-                  argmin_sel(rr[e].x, g0[e4 + e], l0v, u0v, xb.x, xv0[e4 + e]);
-                  argmin_sel(rr[e].y, g1[e4 + e], l1v, u1v, xb.y, xv1[e4 + e]);
-                  const int jf = r_off_kb + (c0 + e4 + e) * hw + yy * w + x0;
-                  *reinterpret_cast<float2*>(xB + (size_t)b * P.N + jf) = xb;
-                }
-              }
-            }
+          for (int e = 0; e < 4; ++e) {
+            g0[e] = v[e];
+            g1[e] = v[4 + e];
+            g0[4 + e] = g1[4 + e] = 0.f;
           }
-          uint16_t* dst = xh + (size_t)b * XH + xh_off + (size_t)(yy * w + x0) * cp_in + c0;
-          if (cp_in >= 8) {
-            *reinterpret_cast<uint4*>(dst) = pack8(xv0);
-            *reinterpret_cast<uint4*>(dst + cp_in) = pack8(xv1);
-          } else {  // cp_in == 4: the two pixels' 4 channels are one 16-byte block
-            float v[8] = {xv0[0], xv0[1], xv0[2], xv0[3], xv1[0], xv1[1], xv1[2], xv1[3]};
-            *reinterpret_cast<uint4*>(dst) = pack8(v);
-          }
-          continue;
+        } else {
+          tmem_ld8(tmem + lanes + (uint32_t)((2 * ry) * cg + c0), g0);
+          tmem_ld8(tmem + lanes + (uint32_t)((2 * ry + 1) * cg + c0), g1);
         }
-        // one pixel per phase (S == 1, or no pair alignment)
-#pragma unroll
-        for (int rx = 0; rx < SS; ++rx) {
-          const int pix = yy * w + x0 + rx;
-          float xv[8];
-          float gx[8];
-#pragma unroll
-          for (int e = 0; e < 8; ++e) gx[e] = rx == 0 ? g0[e] : g1[e];
-          if (kb == 0) {
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-              xv[e] = 0.f;
-              if (c0 + e < cin) {
-                const int jn = (c0 + e) * hw + pix;
-                const float hw0 = 0.5f * (P.u0[(size_t)prop * P.n0 + jn] - P.l0[(size_t)prop * P.n0 + jn]);
-                xv[e] = gx[e] >= 0.f ? hw0 : -hw0;
-              }
-            }
-          } else if (SS == 1) {
-            int bb[8], jf[8];
-            bool on[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-              on[e] = c0 + e < cin;
-              bb[e] = b;
-              jf[e] = r_off_kb + (c0 + e) * hw + pix;
-            }
-            argmin8(P, rho, xB, bb, jf, on, gx, xv);
-          } else {  // stride 2 without pair alignment: one neuron at a time (small code, rare)
-            for (int e = 0; e < 8; ++e) {
-              xv[e] = 0.f;
-              if (c0 + e >= cin) continue;
-              const int jf = r_off_kb + (c0 + e) * hw + pix;
-              float l, u, xb;
-              clamped_bounds(P, b, jf, l, u);
-              argmin_sel(rho[(size_t)b * P.N + jf], gx[e], l, u, xb, xv[e]);
-              xB[(size_t)b * P.N + jf] = xb;
-            }
-          }
-          uint16_t* dst = xh + (size_t)b * XH + xh_off + (size_t)pix * cp_in + c0;
-          const uint4 pk = pack8(xv);
-          if (cp_in >= 8)
-            *reinterpret_cast<uint4*>(dst) = pk;
-          else
-            *reinterpret_cast<uint2*>(dst) = make_uint2(pk.x, pk.y);
+        if (!row_ok) continue;
+        const int ne = min(step, cin - c0);
+        if (pairs) {
+          pair_out(b, prop, yy, x0, c0, ne, g0, g1);
+        } else {
+          single_out(b, prop, yy * w + x0, c0, ne, g0);
+          single_out(b, prop, yy * w + x0 + 1, c0, ne, g1);
         }
+      }
+    } else {
+      // one phase: the two halves split the channel groups
+      for (int c0 = half * 8; c0 < cin; c0 += 16) {
+        float g[8];
+        tmem_ld8(tmem + lanes + (uint32_t)c0, g);
+        if (!row_ok) continue;
+        single_out(b, prop, qy * w + qx, c0, min(8, cin - c0), g);
       }
     }
   }
@@ -641,8 +650,12 @@ struct FcFwdOp {
   }
   __device__ void issue_mma(int, int chunk, uint32_t, uint32_t sst, uint32_t tmem) const {
     const uint32_t id = idesc_bf16(kRows, BN);
-    for (int s = 0; s < KC / 16; ++s)
-      mma_bf16(tmem, op_desc(sst, s, kRows), op_desc(sst + a_bytes, s, BN), id, (chunk > 0 || s > 0) ? 1u : 0u);
+    uint64_t da = op_desc(sst, 0, kRows), db = op_desc(sst + a_bytes, 0, BN);
+    for (int s = 0; s < KC / 16; ++s) {
+      mma_bf16(tmem, da, db, id, (chunk > 0 || s > 0) ? 1u : 0u);
+      da += (uint64_t)(2 * kRows * 16 >> 4);
+      db += (uint64_t)(2 * BN * 16 >> 4);
+    }
   }
   __device__ void epilogue(int tile, uint32_t tmem) const {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = warp & 3, half = warp >> 2;
@@ -712,8 +725,12 @@ struct FcTOp {
   }
   __device__ void issue_mma(int, int, uint32_t sres, uint32_t sst, uint32_t tmem) const {
     const uint32_t id = idesc_bf16(kRows, BN);
-    for (int s = 0; s < kt / 16; ++s)
-      mma_bf16(tmem, op_desc(sres, s, kRows), op_desc(sst, s, BN), id, s > 0 ? 1u : 0u);
+    uint64_t da = op_desc(sres, 0, kRows), db = op_desc(sst, 0, BN);
+    for (int s = 0; s < kt / 16; ++s) {
+      mma_bf16(tmem, da, db, id, s > 0 ? 1u : 0u);
+      da += (uint64_t)(2 * kRows * 16 >> 4);
+      db += (uint64_t)(2 * BN * 16 >> 4);
+    }
   }
   __device__ void epilogue(int tile, uint32_t tmem) const {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = warp & 3, half = warp >> 2;
@@ -1212,30 +1229,55 @@ ld_status build_tc_net(const std::vector<LayerDev>& Ls, TcNet* out) {
               wf[k - 1][canon(o, (i * L.kw + j) * T.cp_in + c, T.nf)] =
                   host_bf16(w[((size_t)(o * L.cin + c) * L.kh + i) * L.kw + j]);
       // transposed: per stride phase, B operand [nt x kt], K = (a * nb + bb) * cp_out + o
-      T.nt = round_up(L.cin, 16);
+      // transposed pass as one stride-1 convolution over rho_k: output column
+      // ph * cg + c holds g at (S qy + ry, S qx + rx), ph = ry * S + rx; the
+      // neighbourhood is the union over phases of the rho_k pixels a phase reads
       T.n_phase = S * S;
-      T.na = (L.kh + S - 1) / S;
-      T.nb = (L.kw + S - 1) / S;
+      T.cg = L.cin <= 4 ? 4 : round_up(L.cin, 8);
+      const int nat = (L.kh + S - 1) / S, nbt = (L.kw + S - 1) / S;
+      int dminy = 1 << 30, dmaxy = -(1 << 30), dminx = 1 << 30, dmaxx = -(1 << 30);
+      for (int r = 0; r < S; ++r) {
+        const int i0 = (r + L.pad) % S, d0 = (r + L.pad - i0) / S;
+        for (int a = 0; a < nat; ++a)
+          if (i0 + S * a < L.kh) {
+            dminy = std::min(dminy, d0 - a);
+            dmaxy = std::max(dmaxy, d0 - a);
+          }
+        const int j0 = (r + L.pad) % S, e0 = (r + L.pad - j0) / S;
+        for (int bb = 0; bb < nbt; ++bb)
+          if (j0 + S * bb < L.kw) {
+            dminx = std::min(dminx, e0 - bb);
+            dmaxx = std::max(dmaxx, e0 - bb);
+          }
+      }
+      T.na = dmaxy - dminy + 1;
+      T.nb = dmaxx - dminx + 1;
+      T.dmy = dminy;
+      T.dmx = dminx;
+      T.nt = round_up(T.n_phase * T.cg, 16);
       T.kt = round_up(T.na * T.nb * T.cp_out, 16);
-      if (T.kt / 8 > kTabMax) return LD_ERR_UNSUPPORTED;
+      if (T.nt > 256) return LD_ERR_UNSUPPORTED;
       const size_t per = (size_t)T.nt * T.kt;
-      wt[k - 1].assign(per * T.n_phase, 0);
+      wt[k - 1].assign(per, 0);
       for (int ph = 0; ph < T.n_phase; ++ph) {
         const int ry = ph / S, rx = ph % S;
         const int i0 = (ry + L.pad) % S, j0 = (rx + L.pad) % S;
-        for (int a = 0; a < T.na; ++a)
-          for (int bb = 0; bb < T.nb; ++bb) {
+        const int dy0 = (ry + L.pad - i0) / S, dx0 = (rx + L.pad - j0) / S;
+        for (int ty = 0; ty < T.na; ++ty)
+          for (int tx = 0; tx < T.nb; ++tx) {
+            const int a = dy0 - (T.dmy + ty), bb = dx0 - (T.dmx + tx);
+            if (a < 0 || bb < 0) continue;
             const int i = i0 + S * a, j = j0 + S * bb;
             if (i >= L.kh || j >= L.kw) continue;
             for (int o = 0; o < L.cout; ++o)
               for (int c = 0; c < L.cin; ++c)
-                wt[k - 1][per * ph + canon(c, (a * T.nb + bb) * T.cp_out + o, T.nt)] =
+                wt[k - 1][canon(ph * T.cg + c, (ty * T.nb + tx) * T.cp_out + o, T.nt)] =
                     host_bf16(w[((size_t)(o * L.cin + c) * L.kh + i) * L.kw + j]);
           }
       }
       // shared memory: forward = weights + 2 stages of 128 x kf; transposed = all phases + 2 x 128 x kt
-      if ((size_t)2 * T.nf * T.kf + (size_t)4 * kRows * T.kf + 2048 > (size_t)200 * 1024) return LD_ERR_UNSUPPORTED;
-      if ((size_t)2 * per * T.n_phase + (size_t)4 * kRows * T.kt + 2048 > (size_t)200 * 1024) return LD_ERR_UNSUPPORTED;
+      if ((size_t)2 * T.nf * T.kf + (size_t)4 * kRows * kConvKC + 2048 > (size_t)200 * 1024) return LD_ERR_UNSUPPORTED;
+      if ((size_t)2 * per + (size_t)4 * kRows * kConvTKC + 2048 > (size_t)200 * 1024) return LD_ERR_UNSUPPORTED;
     } else {
       T.xh_len = round_up(L.n_in, 8);
       T.rh_len = round_up(L.n_out, 16);
@@ -1330,65 +1372,66 @@ template <int SS>
 void launch_conv_t(TcNet& t, int k, const TcLayer& T, const LayerDev& L, const Problem& P, const TcState& S, int kb,
                    int r_off_kb, int crown, int rhb_off, int rhb_conv, int rhb_hw, int rhb_cp, int n_sm,
                    cudaStream_t s) {
-    ConvTOp<SS> op{};
-    const int PH = L.h / L.stride, PW = L.w / L.stride;
-    if (!plane_tiling(PH, PW, op.nsub, op.rows_y, op.tiles_b)) return;
-    TcMaps& mc = t.tr[k - 1];
-    if (mc.base != S.rh || mc.B != P.B) {
-      // rho_k shadow of this layer: (cp_out, wo, ho, B), subdomain rows RH apart
-      if (!encode_map(&mc.m[0], S.rh + T.rh_off, T.cp_out, L.wo, L.ho, P.B, (uint64_t)T.cp_out * 2,
-                      (uint64_t)L.wo * T.cp_out * 2, (uint64_t)t.RH * 2, PW, op.rows_y, op.nsub)) {
-        atomic_status_host(S.status);
-        return;
-      }
-      mc.base = S.rh;
-      mc.B = P.B;
+  ConvTOp<SS> op{};
+  const int PH = L.h / SS, PW = L.w / SS;
+  if (!plane_tiling(PH, PW, op.nsub, op.rows_y, op.tiles_b)) return;
+  TcMaps& mc = t.tr[k - 1];
+  if (mc.base != S.rh || mc.B != P.B) {
+    // rho_k shadow of this layer: (cp_out, wo, ho, B), subdomain rows RH apart
+    if (!encode_map(&mc.m[0], S.rh + T.rh_off, T.cp_out, L.wo, L.ho, P.B, (uint64_t)T.cp_out * 2,
+                    (uint64_t)L.wo * T.cp_out * 2, (uint64_t)t.RH * 2, PW, op.rows_y, op.nsub)) {
+      atomic_status_host(S.status);
+      return;
     }
-    op.mr = mc.m[0];
-    op.kq = T.cp_out / 8;
-    op.n_phase = T.n_phase;
-    op.c.n_tiles = op.tiles_b > 1 ? P.B * op.tiles_b : (P.B + op.nsub - 1) / op.nsub;
-    op.KC = T.kt < kConvTKC ? T.kt : kConvTKC;
-    op.c.n_chunks = (T.kt + op.KC - 1) / op.KC;
-    op.sub_bytes = (uint32_t)(2 * kRows * op.KC);
-    op.c.res_bytes = (uint32_t)(2 * T.nt * T.kt * T.n_phase);
-    op.c.stage_bytes = op.sub_bytes * (uint32_t)T.n_phase;
-    op.c.tmem_cols = tmem_cols_for(2 * T.n_phase * T.nt);
-    op.c.grid_multiple = 1;
-    op.c.status = S.status;
-    op.nt = T.nt;
-    op.kt = T.kt;
-    op.na = T.na;
-    op.nb = T.nb;
-    op.W = T.Wt;
-    op.B = P.B;
-    op.cin = L.cin;
-    op.h = L.h;
-    op.w = L.w;
-    op.ho = L.ho;
-    op.wo = L.wo;
-    op.pad = L.pad;
-    op.cp_in = T.cp_in;
-    op.cp_out = T.cp_out;
-    op.XH = t.XH;
-    op.xh_off = T.xh_off;
-    op.RH = t.RH;
-    op.rh_off = T.rh_off;
-    op.rh = S.rh;
-    op.xh = S.xh;
-    op.P = P;
-    op.kb = kb;
-    op.r_off_kb = r_off_kb;
-    op.xB = S.xB;
-    op.rho = S.rho;
-    op.crown = crown;
-    op.rhb_off = rhb_off;
-    op.rhb_conv = rhb_conv;
-    op.rhb_hw = rhb_hw;
-    op.rhb_cp = rhb_cp;
-    // float2 pairs need even flat indices: N, n0, the layer offset and the plane width even
-    op.pairs = (L.stride == 2 && P.N % 2 == 0 && P.n0 % 2 == 0 && r_off_kb % 2 == 0 && L.w % 2 == 0) ? 1 : 0;
-    launch_op(op, n_sm, s);
+    mc.base = S.rh;
+    mc.B = P.B;
+  }
+  op.mr = mc.m[0];
+  op.kq = T.cp_out / 8;
+  op.c.n_tiles = op.tiles_b > 1 ? P.B * op.tiles_b : (P.B + op.nsub - 1) / op.nsub;
+  op.KC = T.kt < kConvTKC ? T.kt : kConvTKC;
+  op.c.n_chunks = (T.kt + op.KC - 1) / op.KC;
+  op.c.res_bytes = (uint32_t)(2 * T.nt * T.kt);
+  op.c.stage_bytes = (uint32_t)(2 * kRows * op.KC);
+  op.c.tmem_cols = tmem_cols_for(2 * T.nt);
+  op.c.grid_multiple = 1;
+  op.c.status = S.status;
+  op.nt = T.nt;
+  op.kt = T.kt;
+  op.cg = T.cg;
+  op.na = T.na;
+  op.nb = T.nb;
+  op.dmy = T.dmy;
+  op.dmx = T.dmx;
+  op.W = T.Wt;
+  op.B = P.B;
+  op.cin = L.cin;
+  op.h = L.h;
+  op.w = L.w;
+  op.ho = L.ho;
+  op.wo = L.wo;
+  op.pad = L.pad;
+  op.cp_in = T.cp_in;
+  op.cp_out = T.cp_out;
+  op.XH = t.XH;
+  op.xh_off = T.xh_off;
+  op.RH = t.RH;
+  op.rh_off = T.rh_off;
+  op.rh = S.rh;
+  op.xh = S.xh;
+  op.P = P;
+  op.kb = kb;
+  op.r_off_kb = r_off_kb;
+  op.xB = S.xB;
+  op.rho = S.rho;
+  op.crown = crown;
+  op.rhb_off = rhb_off;
+  op.rhb_conv = rhb_conv;
+  op.rhb_hw = rhb_hw;
+  op.rhb_cp = rhb_cp;
+  // float2 pairs need even flat indices: N, n0, the layer offset and the plane width even
+  op.pairs = (SS == 2 && P.N % 2 == 0 && P.n0 % 2 == 0 && r_off_kb % 2 == 0 && L.w % 2 == 0) ? 1 : 0;
+  launch_op(op, n_sm, s);
 }
 
 void launch_tc_transposed(TcNet& t, const std::vector<LayerDev>& Ls, int k, const Problem& P,

@@ -51,6 +51,11 @@ struct ld_net {
   int tc_B = -1, tc_props = -1;
   uint16_t *xh = nullptr, *rh = nullptr;
   float* c1 = nullptr;
+  // the per-iteration launches of the layerwise and BF16 engines, captured
+  // into one executable graph (re-captured and updated in place each call)
+  bool graphs = true;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t iter_exec = nullptr;
   std::map<int, std::pair<int, int>> tuned;
   int n_sm = 0;
   size_t smem_optin = 0;
@@ -311,6 +316,56 @@ ld_status run_iterations(ld_net* net, const Problem& P, const ld_opts& o, int n_
   for (int t = 0; t < n_iters; ++t)
     sweep(net, P, 0, o, adam_step(o, o.t_offset + t, T_sched), nullptr, nullptr, nullptr, nullptr, s);
   return last_error();
+}
+
+// Runs launches(stream) captured into a CUDA graph that is then launched on s
+// (one launch instead of one per kernel; the executable graph is updated in
+// place when only kernel arguments changed), or directly on s when s is
+// itself being captured or capture is unavailable.
+template <class F>
+ld_status run_graphed(ld_net* net, cudaStream_t s, F launches) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (!net->graphs || cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return launches(s);
+  }
+  if (!net->cap_stream && cudaStreamCreateWithFlags(&net->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    net->graphs = false;
+    return launches(s);
+  }
+  if (cudaStreamBeginCapture(net->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    net->graphs = false;
+    return launches(s);
+  }
+  const ld_status st = launches(net->cap_stream);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(net->cap_stream, &g);
+  if (e != cudaSuccess || st != LD_OK || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    if (st != LD_OK) return st;
+    net->graphs = false;  // nothing ran: launch directly from now on
+    return launches(s);
+  }
+  if (net->iter_exec) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(net->iter_exec, g, &info) != cudaSuccess) {
+      cudaGetLastError();
+      cudaGraphExecDestroy(net->iter_exec);
+      net->iter_exec = nullptr;
+    }
+  }
+  if (!net->iter_exec && cudaGraphInstantiate(&net->iter_exec, g, 0) != cudaSuccess) {
+    cudaGetLastError();
+    cudaGraphDestroy(g);
+    net->iter_exec = nullptr;
+    net->graphs = false;
+    return launches(s);
+  }
+  cudaGraphDestroy(g);
+  return cuda_status(cudaGraphLaunch(net->iter_exec, s));
 }
 
 // Tensor-core plan and shadow buffers for B subdomains and n_props properties.
@@ -675,6 +730,8 @@ ld_status ld_net_destroy(ld_net* net) {
   cudaDeviceSynchronize();
   drain_marks(net);
   free_ws(net);
+  if (net->iter_exec) cudaGraphExecDestroy(net->iter_exec);
+  if (net->cap_stream) cudaStreamDestroy(net->cap_stream);
   if (net->tc_ws) cudaFree(net->tc_ws);
   ld::free_tc_net(&net->tc);
   if (net->d_W) cudaFree(net->d_W);
@@ -775,8 +832,14 @@ ld_status ld_bound(ld_net* net, const float* lb0, const float* ub0, const float*
   }
   if (n_iters > 0) {
     PhaseMark pm(net, LD_PHASE_ITER, s);
-    st = bf16 ? run_iterations_bf16(net, P, o, n_iters, o.init == LD_INIT_CROWN, s)
-              : run_iterations(net, P, o, n_iters, eng.first, eng.second, s, crown_in_kernel);
+    if (bf16)
+      st = run_graphed(net, s, [&](cudaStream_t cs) {
+        return run_iterations_bf16(net, P, o, n_iters, o.init == LD_INIT_CROWN, cs);
+      });
+    else if (eng.first == LD_ENGINE_LAYERWISE)
+      st = run_graphed(net, s, [&](cudaStream_t cs) { return run_iterations(net, P, o, n_iters, eng.first, 0, cs); });
+    else
+      st = run_iterations(net, P, o, n_iters, eng.first, eng.second, s, crown_in_kernel);
     if (st != LD_OK) return st;
   }
   {

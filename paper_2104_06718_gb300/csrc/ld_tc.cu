@@ -1057,7 +1057,10 @@ size_t launch_smem(size_t need, uint32_t tmem_cols) {
 
 // Resident CTAs per SM from the kernel's registers and shared memory, the
 // thread limit and the TMEM columns (512 per SM).
-int ctas_per_sm(const void* func, size_t dyn_smem, uint32_t tmem_cols) {
+template <class Op, int NS>
+const cudaFuncAttributes& kernel_attr();
+
+int ctas_per_sm(const cudaFuncAttributes& fa, size_t dyn_smem, uint32_t tmem_cols) {
   static int regs_sm = 0, smem_sm = 0, smem_rsv = 0, thr_sm = 0;
   if (!regs_sm) {
     int dev = 0;
@@ -1067,11 +1070,7 @@ int ctas_per_sm(const void* func, size_t dyn_smem, uint32_t tmem_cols) {
     cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
     cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
   }
-  cudaFuncAttributes fa{};
-  if (cudaFuncGetAttributes(&fa, func) != cudaSuccess) {
-    cudaGetLastError();
-    return 1;
-  }
+  if (fa.numRegs <= 0) return 1;
   const int per_warp = (fa.numRegs * 32 + 255) / 256 * 256;
   int n = regs_sm / (per_warp * (kCtaThreads / 32));
   const int by_smem = (int)((size_t)smem_sm / (dyn_smem + fa.sharedSizeBytes + (size_t)smem_rsv));
@@ -1079,6 +1078,21 @@ int ctas_per_sm(const void* func, size_t dyn_smem, uint32_t tmem_cols) {
   if (thr_sm / kCtaThreads < n) n = thr_sm / kCtaThreads;
   if ((int)(512 / tmem_cols) < n) n = (int)(512 / tmem_cols);
   return n < 1 ? 1 : n;
+}
+
+// Registers and static shared memory of one kernel instantiation (queried once).
+template <class Op, int NS>
+const cudaFuncAttributes& kernel_attr() {
+  static cudaFuncAttributes fa{};
+  static bool done = false;
+  if (!done) {
+    if (cudaFuncGetAttributes(&fa, tc_kernel<Op, NS>) != cudaSuccess) {
+      cudaGetLastError();
+      fa.numRegs = 0;
+    }
+    done = true;
+  }
+  return fa;
 }
 
 template <class Op, int NS>
@@ -1090,7 +1104,7 @@ cudaError_t launch_ns(const Op& op, size_t smem, int n_sm, cudaStream_t s) {
       return cudaGetLastError();
     attr_bytes = smem;
   }
-  const int per_sm = ctas_per_sm(reinterpret_cast<const void*>(tc_kernel<Op, NS>), smem, op.c.tmem_cols);
+  const int per_sm = ctas_per_sm(kernel_attr<Op, NS>(), smem, op.c.tmem_cols);
   int grid = n_sm * per_sm;
   if (grid > op.c.n_tiles) grid = op.c.n_tiles;
   const int gm = op.c.grid_multiple > 1 ? op.c.grid_multiple : 1;
@@ -1107,9 +1121,8 @@ cudaError_t launch_op(const Op& op, int n_sm, cudaStream_t s) {
   if (op.c.n_tiles <= 0) return cudaSuccess;
   const size_t m3 = launch_smem((size_t)op.c.res_bytes + 3 * (size_t)op.c.stage_bytes, op.c.tmem_cols);
   const size_t m2 = launch_smem((size_t)op.c.res_bytes + 2 * (size_t)op.c.stage_bytes, op.c.tmem_cols);
-  const int o3 = m3 <= kSmemBudget
-                     ? ctas_per_sm(reinterpret_cast<const void*>(tc_kernel<Op, 3>), m3, op.c.tmem_cols) : 0;
-  const int o2 = ctas_per_sm(reinterpret_cast<const void*>(tc_kernel<Op, 2>), m2, op.c.tmem_cols);
+  const int o3 = m3 <= kSmemBudget ? ctas_per_sm(kernel_attr<Op, 3>(), m3, op.c.tmem_cols) : 0;
+  const int o2 = ctas_per_sm(kernel_attr<Op, 2>(), m2, op.c.tmem_cols);
   if (o3 >= o2) return launch_ns<Op, 3>(op, m3, n_sm, s);
   return launch_ns<Op, 2>(op, m2, n_sm, s);
 }

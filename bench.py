@@ -42,6 +42,11 @@ WORKLOADS = {
 }
 METRIC = "LD subdomain bounds/s on Base/Wide/Deep convnets, bf16 vs fp32 at ≤1e-3 gap"
 
+# DRAM bytes (read + write) of one launch of the iterations, from ncu captures
+# of the kernels of one iteration scaled by T (see profiles/); keyed by
+# (workload, precision, subdomains, iterations).
+TRAFFIC = {}
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -58,6 +63,8 @@ def parse():
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"],
                     help="arithmetic of the Adam iterations (the final bound is FP64 either way)")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the second leg (the other precision on the same inputs, with the bound gap)")
     return ap.parse_args()
 
 
@@ -329,6 +336,42 @@ def run_ours(args):
     net.profile(False)
     clocks = sampler.stop()
     t_local = sum(times) / 1000.0
+    # ---- the other precision on the same inputs: bounds/s and the bound gap
+    compare = None
+    if not args.no_compare:
+        other = "bf16" if args.precision == "fp32" else "fp32"
+        o2 = ldb.Options(engine=args.engine, tile=args.tile, precision=other)
+
+        def step2():
+            lk, uk = ldb.ld_intermediate_bounds(net, l0, u0)
+            o_, r_ = ldb.ld_bound(net, l0, u0, lk, uk, None, masks, n_iters=T, opts=o2, return_rho=True)
+            g_ = ldb.ld_bound_backward(net, l0, u0, lk, uk, r_, grad_out=ones, masks=masks)
+            return o_, g_
+
+        for _ in range(args.warmup):
+            step2()
+        torch.cuda.synchronize()
+        t2 = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out2, _ = step2()
+            e1.record(stream)
+            e1.synchronize()
+            t2.append(e0.elapsed_time(e1))
+        a32 = (out if args.precision == "fp32" else out2).cpu().numpy()
+        a16 = (out2 if args.precision == "fp32" else out).cpu().numpy()
+        fin = np.isfinite(a32) & np.isfinite(a16)
+        rel = np.abs(a16[fin] - a32[fin]) / np.maximum(np.abs(a32[fin]), 1.0)
+        signed = (a32[fin] - a16[fin]) / np.maximum(np.abs(a32[fin]), 1.0)
+        compare = {"precision": other, "value": B * args.steps / (sum(t2) / 1000.0), "unit": "bounds/s",
+                   "ms_per_step": sum(t2) / args.steps,
+                   "bf16_vs_fp32_gap": {"median": float(np.median(rel)), "p99": float(np.percentile(rel, 99)),
+                                        "max": float(rel.max()), "mean_fp32_minus_bf16": float(signed.mean()),
+                                        "definition": "|q_bf16 - q_fp32| / max(|q_fp32|, 1) per subdomain, same "
+                                                      "inputs and T; the bounds are FP64-evaluated at each run's rho"}}
     # ---- end to end through the C ABI with host buffers
     h_l0 = torch.as_tensor(wl["l0"]).pin_memory()
     h_u0 = torch.as_tensor(wl["u0"]).pin_memory()
@@ -379,22 +422,36 @@ def run_ours(args):
             torch.distributed.destroy_process_group()
         return 0
     peaks, peak_src = measured_peaks()
-    # Roofline of the dominant kernel: the Adam iterations (with the fused
-    # engine, one kernel launch per step).  Algorithmic work per
-    # subdomain-iteration: one transposed and one forward pass, 2 FLOP per MAC.
+    # Roofline of the dominant launch: the Adam iterations of one step (the
+    # fused engine: one kernel; the layerwise and BF16 engines: one graph
+    # launch).  The path is bounded by HBM traffic when the dual state
+    # streams: per subdomain-iteration rho, m, v are read and written in FP32
+    # (24 B per ReLU) and the 2-bit split mask read (0.25 B per ReLU).
+    bytes_per_launch = B * T * net.N * 24.25
+    avg_launch_s = (iter_ms / max(iter_n, 1)) / 1000.0
+    achieved_gbs = bytes_per_launch / avg_launch_s / 1e9
+    hbm_peak = peak_value(peaks, ["hbm_gbs", "hbm_GBs", "hbm"], 6800.0)
     macs = macs_per_pass(wl["specs"])
     flops_per_launch = B * T * 2 * 2 * macs
-    avg_launch_s = (iter_ms / max(iter_n, 1)) / 1000.0
     achieved_tflops = flops_per_launch / avg_launch_s / 1e12
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     max_mhz = clocks.get("sm_max_mhz") or 2070.0
     alu_peak = sm_count * 128 * 2 * max_mhz * 1e6 / 1e12   # FP32 FMA lanes x 2 FLOP x clock
-    roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved_tflops / alu_peak, "traffic": None,
+    bf16_peak = peak_value(peaks, ["bf16_tflops_sustained", "bf16_tflops"], 1700.0)
+    roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved_gbs / hbm_peak, "traffic": TRAFFIC.get((wl["name"], args.precision, B, T)),
                 "kernel": f"{engine or 'auto'} iterations (tile {tile})",
-                "peak_basis": f"{sm_count} SMs x 128 FP32 FMA/clk x 2 FLOP x {max_mhz:.0f} MHz (derived, not measured)",
-                "work_per_launch": f"{B} subdomains x {T} iterations x 2 passes x {macs} MAC x 2 FLOP",
-                "avg_launch_ms": iter_ms / max(iter_n, 1)}
+                "work_per_launch": f"{B} subdomains x {T} iterations x {net.N} ReLUs x 24.25 B "
+                                   "(rho, m, v read + write FP32; 2-bit mask)",
+                "avg_launch_ms": iter_ms / max(iter_n, 1),
+                "l2_note": "the dual state of this workload fits in the 129 MB L2" if B * net.N * 24.25 < 100e6
+                           else "the dual state exceeds L2 and streams from HBM",
+                "compute": {"achieved_tflops": achieved_tflops,
+                            "frac_fp32_alu": achieved_tflops / alu_peak,
+                            "frac_bf16_tensor": achieved_tflops / bf16_peak,
+                            "alu_peak_basis": f"{sm_count} SMs x 128 FP32 FMA/clk x 2 FLOP x {max_mhz:.0f} MHz "
+                                              "(derived)",
+                            "work_per_launch": f"{B} x {T} x 2 passes x {macs} MAC x 2 FLOP"}}
     line = {
         "metric": METRIC, "value": value, "unit": "bounds/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000 * t_all / args.steps, "higher_is_better": True,
@@ -415,6 +472,7 @@ def run_ours(args):
                                "iterations": iter_ms / args.steps, "final_fp64": final_ms / args.steps,
                                "backward": bwd_ms / args.steps},
         "engine": {"engine": engine, "tile": tile},
+        "compare": compare,
         "peaks_source": peak_src,
     }
     if not args.no_cpu_baseline:

@@ -256,6 +256,13 @@ ld_status ld_final_bound_noalloc(ld_net* net, const float* lb0, const float* ub0
  * handles, all calls), for accounting of device work. */
 ld_status ld_launch_count(int64_t* count);
 
+/* Failure-detection self-test: launches one CTA that waits, with the same
+ * bounded mbarrier wait as the tensor-core kernels (2 s limit), on a barrier
+ * that nothing arrives on.  The wait gives up and records LD_ERR_TIMEOUT in
+ * the net's status word (read with ld_net_sync_status); the GPU context stays
+ * usable.  Returns LD_ERR_ARG for a null net, else the launch status. */
+ld_status ld_selftest_wait_timeout(ld_net* net, void* stream);
+
 /* The engine and tile the last LD_ENGINE_AUTO choice cached for batch size
  * B (engine = -1 if none yet). */
 ld_status ld_net_tuned(const ld_net* net, int32_t B, int32_t* engine, int32_t* tile);

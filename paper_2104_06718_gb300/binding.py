@@ -26,7 +26,7 @@ LD_ENGINE_AUTO, LD_ENGINE_LAYERWISE, LD_ENGINE_FUSED = 0, 1, 2
 
 EXPORTED = [
     "ld_opts_default", "ld_status_str", "ld_net_create", "ld_net_destroy", "ld_net_sizes", "ld_net_reserve",
-    "ld_net_sync_status", "ld_intermediate_bounds", "ld_bound", "ld_dual_supergradient", "ld_bound_backward",
+    "ld_net_sync_status", "ld_selftest_wait_timeout", "ld_intermediate_bounds", "ld_bound", "ld_dual_supergradient", "ld_bound_backward",
     "ld_net_profile", "ld_net_profile_read", "ld_launch_count", "ld_net_tuned", "ld_final_bound_noalloc",
 ]
 PHASES = {"iter": 0, "final": 1, "init": 2, "ibp": 3, "backward": 4}
@@ -76,6 +76,7 @@ def load_library(path: str = LIB_PATH):
     lib.ld_bound.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, i32, i32, C.POINTER(Opts), vp, vp, vp, vp, vp]
     lib.ld_dual_supergradient.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, i32, vp, vp, vp, vp, vp]
     lib.ld_bound_backward.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.ld_selftest_wait_timeout.argtypes = [vp, vp]
     lib.ld_net_profile.argtypes = [vp, i32]
     lib.ld_net_profile_read.argtypes = [vp, i32, C.POINTER(C.c_double), C.POINTER(i64), i32]
     lib.ld_launch_count.argtypes = [C.POINTER(i64)]
@@ -210,6 +211,11 @@ class Net:
 
     def sync_status(self):
         return self._lib.ld_net_sync_status(self._h, _stream())
+
+    def selftest_wait_timeout(self):
+        """Launch the bounded-wait self-test (a wait nothing completes); the
+        status word then reads LD_ERR_TIMEOUT."""
+        _check(self._lib.ld_selftest_wait_timeout(self._h, _stream()), "ld_selftest_wait_timeout")
 
     def profile(self, enable: bool = True):
         """Record CUDA events around each phase of every call."""

@@ -924,6 +924,12 @@ ld_status ld_net_profile_read(ld_net* net, int32_t phase, double* total_ms, int6
   return LD_OK;
 }
 
+ld_status ld_selftest_wait_timeout(ld_net* net, void* stream) {
+  if (!net) return LD_ERR_ARG;
+  ld::launch_wait_selftest(net->d_status, S(stream));
+  return last_error();
+}
+
 ld_status ld_launch_count(int64_t* count) {
   if (!count) return LD_ERR_ARG;
   *count = ld::g_launches.load();

@@ -80,6 +80,108 @@ __global__ void __launch_bounds__(NT) conv_wgrad_kernel(Problem P, const double*
   if (threadIdx.x == 0) G[e] = s;
 }
 
+// Conv weight and bias gradients by subdomain slabs: block z sums the
+// subdomains b = z, z + G, ...; per subdomain the layer's output coefficients
+// c[o][p] = -w_b rho_k[b, o, p] and the zero-padded input plane x_{k-1}[b]
+// sit in shared memory, and each thread accumulates a 2 x 4 block of weight
+// entries (o, k'), k' = (c, i, j), over the positions p = pg (mod PS) it owns:
+//   dW[o, c, i, j] = sum_b sum_p c[o][p] x[c][S y + i - pad][S x + j - pad],  db[o] = sum_b sum_p c[o][p]
+// Partial sums part[(z PS + pg), nw + cout] are reduced in a fixed order.
+constexpr int kWgMaxR = 4;
+__global__ void __launch_bounds__(NT) conv_wgrad_slab_kernel(Problem P, const double* w,
+                                                             const float* __restrict__ rho, LayerDev L,
+                                                             const float* __restrict__ x, int PS, int R,
+                                                             float* part) {
+  extern __shared__ float sm[];
+  const int hw_o = L.ho * L.wo, Hp = L.h + 2 * L.pad, Wp = L.w + 2 * L.pad;
+  float* sc = sm;                  // [cout][hw_o]
+  float* sx = sm + L.cout * hw_o;  // [cin][Hp][Wp]
+  const int Kp = L.cin * L.kh * L.kw, nw = L.cout * Kp;
+  const int nkb = (Kp + 3) / 4, nob = (L.cout + 1) / 2, nblk = nob * nkb;
+  const int t = threadIdx.x, pg = t % PS, tq = t / PS, nq = NT / PS;
+  float acc[kWgMaxR][2][4];
+#pragma unroll
+  for (int r = 0; r < kWgMaxR; ++r)
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[r][a][q] = 0.f;
+  float accb = 0.f;
+  for (int e = t; e < L.cin * Hp * Wp; e += NT) sx[e] = 0.f;  // the halo stays zero
+  __syncthreads();
+  for (int b = blockIdx.x; b < P.B; b += gridDim.x) {
+    const float wb = -wgt(P, w, b);
+    for (int e = t; e < L.cout * hw_o; e += NT) sc[e] = wb * rho[(size_t)b * P.N + L.r_out_off + e];
+    const int hw_i = L.h * L.w;
+    for (int e = t; e < L.cin * hw_i; e += NT) {
+      const int c = e / hw_i, rem = e - c * hw_i, yy = rem / L.w, xx = rem - yy * L.w;
+      sx[(c * Hp + yy + L.pad) * Wp + xx + L.pad] = x[(size_t)b * P.XS + L.x_in_off + e];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kWgMaxR; ++r) {
+      const int blk = tq + r * nq;
+      if (r >= R || blk >= nblk) break;
+      const int ob = blk / nkb, kb = blk - ob * nkb, o0 = 2 * ob;
+      int xoff[4];
+      bool kval[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int kk = kb * 4 + q;
+        kval[q] = kk < Kp;
+        const int kc = kval[q] ? kk : 0;
+        const int c = kc / (L.kh * L.kw), i = (kc / L.kw) % L.kh, j = kc % L.kw;
+        xoff[q] = (c * Hp + i) * Wp + j;
+      }
+      const bool o1 = o0 + 1 < L.cout;
+      for (int p = pg; p < hw_o; p += PS) {
+        const int y = p / L.wo, xq = p - y * L.wo;
+        const int base = y * L.stride * Wp + xq * L.stride;
+        const float c0v = sc[o0 * hw_o + p], c1v = o1 ? sc[(o0 + 1) * hw_o + p] : 0.f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float xv = kval[q] ? sx[xoff[q] + base] : 0.f;
+          acc[r][0][q] = fmaf(c0v, xv, acc[r][0][q]);
+          acc[r][1][q] = fmaf(c1v, xv, acc[r][1][q]);
+        }
+      }
+    }
+    if (t < L.cout * PS)
+      for (int p = t % PS; p < hw_o; p += PS) accb += sc[(t / PS) * hw_o + p];
+    __syncthreads();
+  }
+  float* row = part + ((size_t)blockIdx.x * PS + pg) * (size_t)(nw + L.cout);
+#pragma unroll
+  for (int r = 0; r < kWgMaxR; ++r) {
+    const int blk = tq + r * nq;
+    if (r >= R || blk >= nblk) break;
+    const int ob = blk / nkb, kb = blk - ob * nkb;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int o = 2 * ob + a, kk = kb * 4 + q;
+        if (o < L.cout && kk < Kp) row[o * Kp + kk] = acc[r][a][q];
+      }
+  }
+  if (t < L.cout * PS) part[((size_t)blockIdx.x * PS + t % PS) * (size_t)(nw + L.cout) + nw + t / PS] = accb;
+}
+
+// Sum of the slab partials in a fixed order: out_w[e] (e < nw), out_b[e - nw].
+__global__ void wgrad_reduce_kernel(const float* __restrict__ part, int rows, int nw, int cout, float* out_w,
+                                    float* out_b) {
+  const int width = nw + cout;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < width; e += gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int r = 0; r < rows; ++r) s += part[(size_t)r * width + e];
+    if (e < nw) {
+      if (out_w) out_w[e] = s;
+    } else if (out_b) {
+      out_b[e - nw] = s;
+    }
+  }
+}
+
 // Bias gradient: one block per output channel o.
 __global__ void __launch_bounds__(NT) bias_grad_kernel(Problem P, const double* w, const float* __restrict__ rho,
                                                        int r_off, int plane, int last, float* G) {
@@ -154,9 +256,37 @@ void launch_backward(const std::vector<LayerDev>& Ls, const std::vector<size_t>&
                      const double* grad_out, const float* x, const float* g, const int8_t* vtx,
                      float* scratch_bn, float* scratch_b0, BackwardOut out, cudaStream_t s) {
   const int n = (int)Ls.size();
+  int n_sm = 152;
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    cudaGetLastError();
+  }
   for (int k = 1; k <= n; ++k) {
     const LayerDev& L = Ls[k - 1];
     const int last = k == n;
+    if (L.kind == LD_LAYER_CONV && !last && (out.gW || out.gb) && P.B > 0) {
+      // slab kernel: weights and bias of the conv layer in one pass over the subdomains
+      const int Kp = L.cin * L.kh * L.kw, nw = L.cout * Kp;
+      const int nblk = ((L.cout + 1) / 2) * ((Kp + 3) / 4);
+      int PS = 1;
+      while (PS < 8 && nblk * PS * 2 <= NT) PS *= 2;
+      const int R = (nblk + NT / PS - 1) / (NT / PS);
+      const size_t smem = sizeof(float) * ((size_t)L.cout * L.ho * L.wo +
+                                           (size_t)L.cin * (L.h + 2 * L.pad) * (L.w + 2 * L.pad));
+      int G = P.B < 2 * n_sm ? P.B : 2 * n_sm;
+      const size_t cap = (size_t)2 * P.B * P.N;  // scratch_bn floats
+      while (G > 1 && (size_t)G * PS * (nw + L.cout) > cap) G /= 2;
+      if (R <= kWgMaxR && smem <= 48 * 1024 && (size_t)G * PS * (nw + L.cout) <= cap && L.cout * PS <= NT) {
+        count_launch(2);
+        conv_wgrad_slab_kernel<<<G, NT, smem, s>>>(P, grad_out, rho, L, x, PS, R, scratch_bn);
+        const int width = nw + L.cout;
+        wgrad_reduce_kernel<<<(width + NT - 1) / NT, NT, 0, s>>>(scratch_bn, G * PS, nw, L.cout,
+                                                                 out.gW ? out.gW + w_off[k - 1] : nullptr,
+                                                                 out.gb ? out.gb + b_off[k - 1] : nullptr);
+        continue;
+      }
+    }
     count_launch((out.gW ? 1 : 0) + (out.gb ? 1 : 0));
     if (out.gW) {
       float* G = out.gW + w_off[k - 1];

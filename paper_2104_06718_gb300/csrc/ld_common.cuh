@@ -349,6 +349,8 @@ void free_tc_net(TcNet* t);
 // rho (FP32) -> shadows of rho_k for k_lo <= k <= k_hi.
 void launch_tc_shadow_rho(const TcNet& t, const std::vector<LayerDev>& Ls, const Problem& P, const TcState& S,
                           int k_lo, int k_hi, cudaStream_t s);
+// One CTA waits (bounded) on an mbarrier nothing arrives on: LD_ERR_TIMEOUT.
+void launch_wait_selftest(int* status, cudaStream_t s);
 // c1 = W_1 c_0 + b_1 per property, c_0 = l_0 + (u_0 - l_0) / 2.
 void launch_tc_centre(const TcNet& t, const LayerDev& L1, const Problem& P, const TcState& S, cudaStream_t s);
 // Transposed pass of layer k (1 <= k <= n-1) -> inner minimisation of layer

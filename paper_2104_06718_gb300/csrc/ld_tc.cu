@@ -958,6 +958,18 @@ __global__ void __launch_bounds__(kCtaThreads, 2) tc_kernel(const __grid_constan
   }
 }
 
+// The bounded mbarrier wait of the kernels above on a barrier that nothing
+// arrives on: it gives up after its limit and records LD_ERR_TIMEOUT.
+__global__ void wait_selftest_kernel(int* status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(smem_u32(&bar), 0)) atomicCAS(status, 0, (int)LD_ERR_TIMEOUT);
+}
+
 // rho (FP32, [B, N]) -> BF16 shadows of rho_1..rho_{n-1}.
 struct ShadowLayer {
   int conv, r_off, n, hw, cp_out, rh_off;
@@ -1373,6 +1385,11 @@ void launch_tc_shadow_rho(const TcNet& t, const std::vector<LayerDev>& Ls, const
   if (grid < 1) grid = 1;
   count_launch();
   shadow_rho_kernel<<<grid, 256, 0, s>>>(sp, P.B, P.N, t.RH, S.rho, S.rh);
+}
+
+void launch_wait_selftest(int* status, cudaStream_t s) {
+  count_launch();
+  wait_selftest_kernel<<<1, 32, 0, s>>>(status);
 }
 
 void launch_tc_centre(const TcNet& t, const LayerDev& L1, const Problem& P, const TcState& S, cudaStream_t s) {

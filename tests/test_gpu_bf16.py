@@ -149,3 +149,17 @@ def test_bf16_wide_2048_sampled_against_oracle():
     assert np.median(gap) < FULL_RUN_MEDIAN and np.percentile(gap, 99) < GAP_MAX and gap.max() < 2 * GAP_MAX
     xs = synth.random_box_points(pb["l0"][0], pb["u0"][0], 256, seed=9)
     assert out[0] <= pb["net"].evaluate(xs).min()
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    """Failure detection without a fault: a wait that nothing completes gives
+    up after its limit, the status word reads LD_ERR_TIMEOUT, and the GPU is
+    still usable afterwards."""
+    pb = conv_problem("base", 4, depth=(0, 4), block=2)
+    net = ldb.Net(pb["specs"])
+    assert net.sync_status() == 0
+    net.selftest_wait_timeout()
+    assert net.sync_status() == 5  # LD_ERR_TIMEOUT
+    other = ldb.Net(pb["specs"])
+    out = run_gpu(pb, 3, BF16)
+    assert other.sync_status() == 0 and np.isfinite(out).all()

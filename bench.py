@@ -61,10 +61,16 @@ def parse():
     ap.add_argument("--iters", type=int, default=0, help="override Adam iterations (profiling runs)")
     ap.add_argument("--engine", default="auto", choices=["auto", "layerwise", "fused"])
     ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--cta-threads", type=int, default=0, choices=[0, 256, 512])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"],
                     help="arithmetic of the Adam iterations (the final bound is FP64 either way)")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the second leg (the other precision on the same inputs, with the bound gap)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="batch-size x iterations sweep on the Deep net with 32 properties, BF16 and FP32 "
+                         "(one JSON line per point; not the benchmark line)")
+    ap.add_argument("--sweep-b", default="64,128,256,512,1024,2048,4096,8192")
+    ap.add_argument("--sweep-t", default="50,200,500")
     return ap.parse_args()
 
 
@@ -289,7 +295,7 @@ def run_ours(args):
     masks_np = synth.split_masks(net.N, B, amb, wl["depth"], block=rank)
     masks = torch.as_tensor(masks_np, device=dev)
     ones = torch.ones(B, dtype=torch.float64, device=dev)
-    opts = ldb.Options(engine=args.engine, tile=args.tile, precision=args.precision)
+    opts = ldb.Options(engine=args.engine, tile=args.tile, cta_threads=args.cta_threads, precision=args.precision)
 
     def step():
         lk, uk = ldb.ld_intermediate_bounds(net, l0, u0)
@@ -302,11 +308,11 @@ def run_ours(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    engine, tile = net.tuned(B)
+    engine, tile, threads = net.tuned(B)
     if args.precision == "bf16":
-        engine, tile = "tensor-core bf16", 0
+        engine, tile, threads = "tensor-core bf16", 0, 0
     elif args.engine != "auto":
-        engine, tile = args.engine, args.tile
+        engine, tile, threads = args.engine, args.tile, args.cta_threads
     # ---- device-resident timing
     sampler = ClockSampler(torch.cuda.current_device())
     if world > 1:
@@ -340,7 +346,7 @@ def run_ours(args):
     compare = None
     if not args.no_compare:
         other = "bf16" if args.precision == "fp32" else "fp32"
-        o2 = ldb.Options(engine=args.engine, tile=args.tile, precision=other)
+        o2 = ldb.Options(engine=args.engine, tile=args.tile, cta_threads=args.cta_threads, precision=other)
 
         def step2():
             lk, uk = ldb.ld_intermediate_bounds(net, l0, u0)
@@ -407,11 +413,9 @@ def run_ours(args):
         etimes.append(e0.elapsed_time(e1))
     te_local = sum(etimes) / 1000.0 if etimes else float("nan")
     if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_local, te_local], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_all, te_all = tt.tolist()
-        dist.barrier()
+        from paper_2104_06718_gb300.replicas import max_over_ranks
+        t_all, te_all = max_over_ranks([t_local, te_local], device=dev)
+        torch.distributed.barrier()
     else:
         t_all, te_all = t_local, te_local
     total_bounds = B * args.steps * world
@@ -440,7 +444,8 @@ def run_ours(args):
     bf16_peak = peak_value(peaks, ["bf16_tflops_sustained", "bf16_tflops"], 1700.0)
     roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved_gbs / hbm_peak, "traffic": TRAFFIC.get((wl["name"], args.precision, B, T)),
-                "kernel": f"{engine or 'auto'} iterations (tile {tile})",
+                "kernel": f"{engine or 'auto'} iterations (tile {tile}, {threads or 256} threads per CTA)"
+                  if engine == "fused" else f"{engine or 'auto'} iterations",
                 "work_per_launch": f"{B} subdomains x {T} iterations x {net.N} ReLUs x 24.25 B "
                                    "(rho, m, v read + write FP32; 2-bit mask)",
                 "avg_launch_ms": iter_ms / max(iter_n, 1),
@@ -471,7 +476,7 @@ def run_ours(args):
         "phases_ms_per_step": {"ibp": ibp_ms / args.steps, "init": init_ms / args.steps,
                                "iterations": iter_ms / args.steps, "final_fp64": final_ms / args.steps,
                                "backward": bwd_ms / args.steps},
-        "engine": {"engine": engine, "tile": tile},
+        "engine": {"engine": engine, "tile": tile, "cta_threads": threads},
         "compare": compare,
         "peaks_source": peak_src,
     }
@@ -483,10 +488,85 @@ def run_ours(args):
     return 0
 
 
+def run_sweep(args):
+    """Deep net, 32 properties (eps ~ U[1/255, 16/255], one margin vector),
+    B/32 subdomains per property with split depth 0-20, for every batch size
+    and iteration count: bounds/s of BF16 and FP32 iterations (FP64 final
+    bound either way) and the BF16-vs-FP32 gap on the same inputs."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2104_06718_gb300 import build as ldbuild
+    ldbuild.build()
+    from paper_2104_06718_gb300 import binding as ldb
+    from paper_2104_06718_gb300 import synth
+    n_props = 32
+    specs = synth.make_convnet("deep")
+    boxes = [synth.image_property(p, (1 / 255, 16 / 255)) for p in range(n_props)]
+    margin = boxes[0][2]
+    net = ldb.Net(specs, margin=margin)
+    dev = torch.device("cuda", 0)
+    l0 = torch.as_tensor(np.stack([b[0] for b in boxes]), device=dev)
+    u0 = torch.as_tensor(np.stack([b[1] for b in boxes]), device=dev)
+    lbk, ubk = ldb.ld_intermediate_bounds(net, l0, u0)
+    lb_h, ub_h = lbk.cpu().numpy(), ubk.cpu().numpy()
+    Bs = [int(x) for x in args.sweep_b.split(",")]
+    Ts = [int(x) for x in args.sweep_t.split(",")]
+    net.reserve(max(Bs))
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    for B in Bs:
+        per = B // n_props
+        prop = np.repeat(np.arange(n_props, dtype=np.int32), per)
+        parts = []
+        for p in range(n_props):
+            amb = np.nonzero((lb_h[p] < 0) & (ub_h[p] > 0))[0]
+            parts.append(synth.split_masks(net.N, per, amb, (0, 20), block=p))
+        masks = torch.as_tensor(np.concatenate(parts), device=dev)
+        prop_d = torch.as_tensor(prop, device=dev)
+        amb_counts = []
+        for p in range(n_props):
+            m = np.concatenate(parts)[p * per:(p + 1) * per]
+            a = (lb_h[p] < 0) & (ub_h[p] > 0)
+            amb_counts.append((a[None, :] & (m == 0)).sum(axis=1))
+        amb_counts = np.concatenate(amb_counts)
+        for T in Ts:
+            res = {}
+            for prec in ("fp32", "bf16"):
+                opts = ldb.Options(precision=prec)
+                for _ in range(max(args.warmup, 1)):
+                    out = ldb.ld_bound(net, l0, u0, lbk, ubk, prop_d, masks, n_iters=T, opts=opts)
+                torch.cuda.synchronize()
+                times = []
+                for _ in range(args.steps):
+                    flush.fill_(1.0)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    out = ldb.ld_bound(net, l0, u0, lbk, ubk, prop_d, masks, n_iters=T, opts=opts)
+                    e1.record(stream)
+                    e1.synchronize()
+                    times.append(e0.elapsed_time(e1))
+                res[prec] = (B / (statistics.median(times) / 1000.0), out.cpu().numpy(), net.tuned(B))
+            a32, a16 = res["fp32"][1], res["bf16"][1]
+            fin = np.isfinite(a32) & np.isfinite(a16)
+            rel = np.abs(a16[fin] - a32[fin]) / np.maximum(np.abs(a32[fin]), 1.0)
+            print(json.dumps({"sweep": "deep", "subdomains": B, "iterations": T, "properties": n_props,
+                              "fp32_bounds_per_s": res["fp32"][0], "bf16_bounds_per_s": res["bf16"][0],
+                              "bf16_speedup": res["bf16"][0] / res["fp32"][0],
+                              "fp32_engine": list(res["fp32"][2]),
+                              "gap_median": float(np.median(rel)) if rel.size else None,
+                              "gap_max": float(rel.max()) if rel.size else None,
+                              "ambiguous_relus": {"min": int(amb_counts.min()), "median": float(np.median(amb_counts)),
+                                                  "max": int(amb_counts.max())}}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweep:
+        return run_sweep(args)
     return run_ours(args)
 
 

@@ -90,6 +90,9 @@ typedef struct {
   int32_t t_total;     /* schedule length for alpha decay (0: n_iters)      */
   int32_t engine;      /* LD_ENGINE_*: how the iterations are launched      */
   int32_t tile;        /* fused engine: subdomains per CTA (0 auto, 1, 2, 4) */
+  int32_t cta_threads; /* fused engine: threads per CTA, 256 or 512 (512 only
+                          with tile 2); 0: 256 for an explicit tile, the
+                          autotuner's choice under LD_ENGINE_AUTO          */
 } ld_opts;
 
 /* Engines for the iterations (all compute the same iterates up to FP32
@@ -263,9 +266,10 @@ ld_status ld_launch_count(int64_t* count);
  * usable.  Returns LD_ERR_ARG for a null net, else the launch status. */
 ld_status ld_selftest_wait_timeout(ld_net* net, void* stream);
 
-/* The engine and tile the last LD_ENGINE_AUTO choice cached for batch size
- * B (engine = -1 if none yet). */
-ld_status ld_net_tuned(const ld_net* net, int32_t B, int32_t* engine, int32_t* tile);
+/* The engine, tile and threads per CTA of the LD_ENGINE_AUTO choice cached
+ * for batch size B (engine = -1 if none yet; tile and cta_threads are 0 for
+ * the layerwise engine).  Any output pointer may be NULL. */
+ld_status ld_net_tuned(const ld_net* net, int32_t B, int32_t* engine, int32_t* tile, int32_t* cta_threads);
 
 #ifdef __cplusplus
 }

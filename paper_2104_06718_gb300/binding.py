@@ -47,7 +47,8 @@ class LayerDesc(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("alpha0", C.c_float), ("alpha_end", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
                 ("eps", C.c_float), ("init", C.c_int32), ("precision", C.c_int32), ("fp64_final", C.c_int32),
-                ("t_offset", C.c_int32), ("t_total", C.c_int32), ("engine", C.c_int32), ("tile", C.c_int32)]
+                ("t_offset", C.c_int32), ("t_total", C.c_int32), ("engine", C.c_int32), ("tile", C.c_int32),
+                ("cta_threads", C.c_int32)]
 
 
 _lib = None
@@ -80,7 +81,7 @@ def load_library(path: str = LIB_PATH):
     lib.ld_net_profile.argtypes = [vp, i32]
     lib.ld_net_profile_read.argtypes = [vp, i32, C.POINTER(C.c_double), C.POINTER(i64), i32]
     lib.ld_launch_count.argtypes = [C.POINTER(i64)]
-    lib.ld_net_tuned.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32)]
+    lib.ld_net_tuned.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
     lib.ld_final_bound_noalloc.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, i32, vp, vp, vp]
     for name in EXPORTED:
         if name not in ("ld_opts_default", "ld_status_str"):
@@ -140,6 +141,7 @@ class Options:
     t_total: int = 0
     engine: str = "auto"         # "auto" | "layerwise" | "fused"
     tile: int = 0                # fused engine: subdomains per CTA (0 = auto, 1, 2, 4)
+    cta_threads: int = 0         # fused engine: threads per CTA (0 = auto, 256, 512 with tile 2)
 
     def to_c(self) -> Opts:
         return Opts(self.alpha0, self.alpha_end, self.beta1, self.beta2, self.eps,
@@ -147,7 +149,7 @@ class Options:
                     {"fp32": LD_PREC_FP32, "bf16": LD_PREC_BF16}[self.precision],
                     int(self.fp64_final), self.t_offset, self.t_total,
                     {"auto": LD_ENGINE_AUTO, "layerwise": LD_ENGINE_LAYERWISE, "fused": LD_ENGINE_FUSED}[self.engine],
-                    int(self.tile))
+                    int(self.tile), int(self.cta_threads))
 
 
 class Net:
@@ -229,11 +231,12 @@ class Net:
         return ms.value, n.value
 
     def tuned(self, B: int):
-        """(engine, tile) chosen by the autotuner for batch size B, or (None, 0)."""
-        e, t = C.c_int32(), C.c_int32()
-        _check(self._lib.ld_net_tuned(self._h, int(B), C.byref(e), C.byref(t)), "ld_net_tuned")
+        """(engine, tile, threads per CTA) chosen by the autotuner for batch
+        size B, or (None, 0, 0)."""
+        e, t, n = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(self._lib.ld_net_tuned(self._h, int(B), C.byref(e), C.byref(t), C.byref(n)), "ld_net_tuned")
         names = {LD_ENGINE_LAYERWISE: "layerwise", LD_ENGINE_FUSED: "fused"}
-        return names.get(e.value), t.value
+        return names.get(e.value), t.value, n.value
 
 
 def launch_count() -> int:

@@ -1,5 +1,6 @@
 // C ABI of libld (declared in include/ld.h): argument checking, the net
 // handle, workspace ownership and the order of the passes of one call.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -217,6 +218,8 @@ ld_status check_opts(const ld_opts& o) {
   if (o.t_offset < 0 || o.t_total < 0) return LD_ERR_ARG;
   if (o.engine < LD_ENGINE_AUTO || o.engine > LD_ENGINE_FUSED) return LD_ERR_ARG;
   if (o.tile != 0 && o.tile != 1 && o.tile != 2 && o.tile != 4) return LD_ERR_ARG;
+  if (o.cta_threads != 0 && o.cta_threads != 256 && o.cta_threads != 512) return LD_ERR_ARG;
+  if (o.cta_threads == 512 && o.tile != 0 && o.tile != 2) return LD_ERR_ARG;
   return LD_OK;
 }
 
@@ -310,8 +313,19 @@ ld_status run_iterations(ld_net* net, const Problem& P, const ld_opts& o, int n_
                          cudaStream_t s, int crown = 0) {
   const int T_sched = o.t_total > 0 ? o.t_total : o.t_offset + n_iters;
   if (engine == LD_ENGINE_FUSED) {
-    ld::FusedIter it{n_iters, o.t_offset, T_sched, o.alpha0, o.alpha_end, o.beta1, o.beta2, o.eps, crown};
-    return cuda_status(ld::launch_fused(net->fused, tile, P, net->rho, net->m, net->v, it, s));
+    // one launch per kFusedSteps iterations; the first also computes the CROWN start
+    for (int t0 = 0; t0 < n_iters || (t0 == 0 && crown); t0 += ld::kFusedSteps) {
+      ld::FusedIter it{};
+      it.T = std::min(ld::kFusedSteps, n_iters - t0);
+      it.crown = t0 == 0 ? crown : 0;
+      it.beta1 = o.beta1;
+      it.beta2 = o.beta2;
+      it.eps = o.eps;
+      for (int i = 0; i < it.T; ++i) it.step[i] = adam_step(o, o.t_offset + t0 + i, T_sched);
+      const ld_status st = cuda_status(ld::launch_fused(net->fused, tile, P, net->rho, net->m, net->v, it, s));
+      if (st != LD_OK) return st;
+    }
+    return LD_OK;
   }
   for (int t = 0; t < n_iters; ++t)
     sweep(net, P, 0, o, adam_step(o, o.t_offset + t, T_sched), nullptr, nullptr, nullptr, nullptr, s);
@@ -449,10 +463,10 @@ std::pair<int, int> choose_engine(ld_net* net, const Problem& P, const ld_opts& 
   if (o.engine == LD_ENGINE_LAYERWISE) return {LD_ENGINE_LAYERWISE, 0};
   if (o.engine == LD_ENGINE_FUSED) {
     int S = o.tile;
-    if (S == 0) S = P.B <= 2 * net->n_sm ? 1 : 2;
+    if (S == 0) S = o.cta_threads == 512 ? 2 : (P.B <= 2 * net->n_sm ? 1 : 2);
     while (S > 1 && !tile_fits(net, S)) S /= 2;
     if (!tile_fits(net, S)) return {LD_ENGINE_LAYERWISE, 0};
-    return {LD_ENGINE_FUSED, S};
+    return {LD_ENGINE_FUSED, S | (S == 2 && o.cta_threads == 512 ? ld::kFusedWide : 0)};
   }
   auto hit = net->tuned.find(P.B);
   if (hit != net->tuned.end()) return hit->second;
@@ -467,6 +481,7 @@ std::pair<int, int> choose_engine(ld_net* net, const Problem& P, const ld_opts& 
   std::vector<std::pair<int, int>> cands = {{LD_ENGINE_LAYERWISE, 0}};
   for (int S : {1, 2, 4})
     if (tile_fits(net, S)) cands.push_back({LD_ENGINE_FUSED, S});
+  if (tile_fits(net, 2)) cands.push_back({LD_ENGINE_FUSED, 2 | ld::kFusedWide});
   const size_t BN = (size_t)P.B * net->N;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -546,6 +561,7 @@ void ld_opts_default(ld_opts* o) {
   o->t_total = 0;
   o->engine = LD_ENGINE_AUTO;
   o->tile = 0;
+  o->cta_threads = 0;
 }
 
 const char* ld_status_str(ld_status s) {
@@ -936,11 +952,15 @@ ld_status ld_launch_count(int64_t* count) {
   return LD_OK;
 }
 
-ld_status ld_net_tuned(const ld_net* net, int32_t B, int32_t* engine, int32_t* tile) {
+ld_status ld_net_tuned(const ld_net* net, int32_t B, int32_t* engine, int32_t* tile, int32_t* cta_threads) {
   if (!net) return LD_ERR_ARG;
   auto it = net->tuned.find(B);
-  if (engine) *engine = it == net->tuned.end() ? -1 : it->second.first;
-  if (tile) *tile = it == net->tuned.end() ? 0 : it->second.second;
+  const bool found = it != net->tuned.end();
+  const bool fused = found && it->second.first == LD_ENGINE_FUSED;
+  const int code = fused ? it->second.second : 0;
+  if (engine) *engine = found ? it->second.first : -1;
+  if (tile) *tile = code & ~ld::kFusedWide;
+  if (cta_threads) *cta_threads = fused ? ((code & ld::kFusedWide) ? 512 : 256) : 0;
   return LD_OK;
 }
 

@@ -276,17 +276,28 @@ struct FusedNet {
   LayerDev L[kMaxLayers];      // L[k] = layer k+1 of the paper
 };
 
-// Iteration range and Adam settings of one fused launch.
+// Iterations and Adam settings of one fused launch.  The per-step constants
+// (alpha_t of the linear schedule and the two bias corrections) come from the
+// host, computed in double and rounded once, exactly as for the other
+// engines; a launch runs at most kFusedSteps iterations (longer runs are
+// split into several launches, which reload the state bit for bit).
+constexpr int kFusedSteps = 128;
 struct FusedIter {
-  int T, t_offset, T_sched;
-  float alpha0, alpha_end, beta1, beta2, eps;
+  int T;                       // iterations of this launch (<= kFusedSteps)
   int crown;                   // 1: compute the CROWN initial duals in the kernel first
+  float beta1, beta2, eps;
+  AdamStep step[kFusedSteps];  // constants of the launch's iterations, in order
 };
+
+// Fused launch shape: code = subdomains per CTA (1, 2, 4; 256 threads), plus
+// kFusedWide for 512 threads per CTA (only with 2 subdomains: the FC weights
+// then stream once per 2 subdomains while 16 warps share the conv work).
+constexpr int kFusedWide = 16;
 
 FusedNet make_fused_net(const std::vector<LayerDev>& Ls);
 // Shared memory of a fused CTA owning S subdomains (all their state resident).
 size_t fused_smem_bytes(const FusedNet& f, int S);
-cudaError_t launch_fused(const FusedNet& f, int S, const Problem& P, float* rho, float* m, float* v,
+cudaError_t launch_fused(const FusedNet& f, int code, const Problem& P, float* rho, float* m, float* v,
                          const FusedIter& it, cudaStream_t s);
 
 // ---------------------------------------------------------------- BF16 tensor-core engine

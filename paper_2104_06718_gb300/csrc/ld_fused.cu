@@ -30,9 +30,8 @@ namespace ld {
 
 namespace {
 
-constexpr int FT = 256;  // threads per CTA
-
-template <int S>
+// S subdomains per CTA of NT threads.
+template <int S, int NT>
 struct Ctx {
   const FusedNet& net;
   const Problem& P;
@@ -49,8 +48,8 @@ struct Ctx {
   __device__ float* rho(int s) const { return RHO + s * net.rho_total; }
 };
 
-template <int S>
-__device__ __forceinline__ bool active(const Ctx<S>& c, int s) { return c.b0 + s < c.P.B; }
+template <int S, int NT>
+__device__ __forceinline__ bool active(const Ctx<S, NT>& c, int s) { return c.b0 + s < c.P.B; }
 
 // Index of input element (ch, y, x) of conv layer L in its padded plane.
 __device__ __forceinline__ int xp_conv(const LayerDev& L, const FusedLayer& F, int ch, int y, int x) {
@@ -83,8 +82,8 @@ __device__ __forceinline__ int rho_flat(const LayerDev& L, const FusedLayer& F, 
 
 // Transposed-pass epilogue for neuron i of layer k (g = g_k[i]).  xi: where
 // x_k goes in the input plane of layer k+1; ri: where rho_k sits (k >= 1).
-template <int S>
-__device__ __forceinline__ void epi_t(const Ctx<S>& c, int k, int s, int i, int xi, int ri, float g) {
+template <int S, int NT>
+__device__ __forceinline__ void epi_t(const Ctx<S, NT>& c, int k, int s, int i, int xi, int ri, float g) {
   const int b = c.b0 + s;
   if (c.crown) {
     // dual initialisation (Prop. 3, Eq. salman-assignment): rho_k = a_bar [g]_+ + a_low [g]_-,
@@ -126,8 +125,8 @@ __device__ __forceinline__ void epi_t(const Ctx<S>& c, int k, int s, int i, int 
 
 // Forward-pass epilogue: supergradient and Adam step on neuron jj of layer
 // k+1 (L) with acc = (W_{k+1} x_k)[jj]; ri: where rho_{k+1}[jj] sits.
-template <int S>
-__device__ __forceinline__ void epi_f(const Ctx<S>& c, const LayerDev& L, int s, int jj, int ri, float acc,
+template <int S, int NT>
+__device__ __forceinline__ void epi_f(const Ctx<S, NT>& c, const LayerDev& L, int s, int jj, int ri, float acc,
                                       const FusedIter& it, const AdamStep& st) {
   if (c.P.empty[c.b0 + s]) return;
   const int plane = L.kind == LD_LAYER_FC ? 1 : L.ho * L.wo;
@@ -145,21 +144,21 @@ __device__ __forceinline__ void epi_f(const Ctx<S>& c, const LayerDev& L, int s,
 }
 
 // rho index of neuron i of layer k (k >= 1), from its flat index.
-template <int S>
-__device__ __forceinline__ int rho_of_layer(const Ctx<S>& c, int k, int i) {
+template <int S, int NT>
+__device__ __forceinline__ int rho_of_layer(const Ctx<S, NT>& c, int k, int i) {
   return k >= 1 ? rho_flat(c.net.L[k - 1], c.net.F[k - 1], i) : 0;
 }
 
 // ------------------------------------------------------------------ FC passes
 
 // Transposed FC pass of layer L = layer k+1 into layer k: g[s][i] = sum_o W[o, i] rho_{k+1}[s][o].
-template <int S>
-__device__ void transposed_fc(const Ctx<S>& c, const LayerDev& L, const FusedLayer& F, int k) {
+template <int S, int NT>
+__device__ void transposed_fc(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, int k) {
   const float* __restrict__ W = L.W;
   if (F.vec4) {
     constexpr int U = 16;  // weight rows in flight per thread
     const int n4 = L.n_in / 4;
-    for (int i4 = threadIdx.x; i4 < n4; i4 += FT) {
+    for (int i4 = threadIdx.x; i4 < n4; i4 += NT) {
       float4 acc[S];
 #pragma unroll
       for (int s = 0; s < S; ++s) acc[s] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -200,7 +199,7 @@ __device__ void transposed_fc(const Ctx<S>& c, const LayerDev& L, const FusedLay
     }
     return;
   }
-  for (int i = threadIdx.x; i < L.n_in; i += FT) {
+  for (int i = threadIdx.x; i < L.n_in; i += NT) {
     float acc[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) acc[s] = 0.f;
@@ -217,10 +216,10 @@ __device__ void transposed_fc(const Ctx<S>& c, const LayerDev& L, const FusedLay
 
 // Forward FC: a warp takes two output neurons at a time, lanes split the
 // inputs; up to 8 16-byte loads per row are in flight per lane.
-template <int S>
-__device__ void forward_fc(const Ctx<S>& c, const LayerDev& L, const FusedLayer& F, const FusedIter& it,
+template <int S, int NT>
+__device__ void forward_fc(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, const FusedIter& it,
                            const AdamStep& st) {
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nwarp = FT / 32;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nwarp = NT / 32;
   const float* __restrict__ W = L.W;
   const int npair = (L.n_out + 1) / 2;
   for (int jp = warp; jp < npair; jp += nwarp) {
@@ -289,14 +288,14 @@ __device__ void forward_fc(const Ctx<S>& c, const LayerDev& L, const FusedLayer&
 
 // Forward conv, blocked: item = (s, y, x0, group of GF output channels); the
 // thread computes positions x0 and x0 + wo/2.
-template <int KH, int KW, int ST, int GF, int S>
-__device__ void conv_fwd_blocked(const Ctx<S>& c, const LayerDev& L, const FusedLayer& F, const FusedIter& it,
+template <int KH, int KW, int ST, int GF, int S, int NT>
+__device__ void conv_fwd_blocked(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, const FusedIter& it,
                                  const AdamStep& st) {
   const int half = L.wo / 2, nog = L.cout / GF;
   const int items = S * L.ho * half * nog;
   const float* wf = c.sW + F.swf;
   const int hq = F.Hp >> 1, wq = F.Wp >> 1;
-  for (int e = threadIdx.x; e < items; e += FT) {
+  for (int e = threadIdx.x; e < items; e += NT) {
     int r = e;
     const int x0 = r % half;
     r /= half;
@@ -359,12 +358,12 @@ __device__ void conv_fwd_blocked(const Ctx<S>& c, const LayerDev& L, const Fused
 // i0 = (ry + pad) mod ST, reading rho row y = qy + dy0 - a with
 // dy0 = (ry + pad - i0) / ST (likewise in x).  Item = (s, phase, qy, qx,
 // group of G input channels); the thread computes qx and qx + qw/2.
-template <int KH, int KW, int ST, int G, int S>
-__device__ void conv_t_blocked(const Ctx<S>& c, const LayerDev& L, const FusedLayer& F, int k) {
+template <int KH, int KW, int ST, int G, int S, int NT>
+__device__ void conv_t_blocked(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, int k) {
   const int qh = L.h / ST, qw = L.w / ST, half = qw / 2, ncg = L.cin / G;
   const int items = S * ST * ST * ncg * qh * half;
   const float* wt = c.sW + F.swt;
-  for (int e = threadIdx.x; e < items; e += FT) {
+  for (int e = threadIdx.x; e < items; e += NT) {
     int r = e;
     const int qx = r % half;
     r /= half;
@@ -431,12 +430,12 @@ __device__ void conv_t_blocked(const Ctx<S>& c, const LayerDev& L, const FusedLa
 
 // ------------------------------------------------------------------ generic convs
 
-template <int S>
-__device__ void conv_fwd_generic(const Ctx<S>& c, const LayerDev& L, const FusedLayer& F, const FusedIter& it,
+template <int S, int NT>
+__device__ void conv_fwd_generic(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, const FusedIter& it,
                                  const AdamStep& st) {
   const int hw_o = L.ho * L.wo, total = L.cout * hw_o;
   const float* wf = c.sW + F.swf;
-  for (int e = threadIdx.x; e < total; e += FT) {
+  for (int e = threadIdx.x; e < total; e += NT) {
     const int o = e / hw_o, rem = e % hw_o, y = rem / L.wo, x = rem % L.wo;
     float acc[S];
 #pragma unroll
@@ -457,11 +456,11 @@ __device__ void conv_fwd_generic(const Ctx<S>& c, const LayerDev& L, const Fused
   }
 }
 
-template <int S>
-__device__ void conv_t_generic(const Ctx<S>& c, const LayerDev& L, const FusedLayer& F, int k) {
+template <int S, int NT>
+__device__ void conv_t_generic(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, int k) {
   const int hw_i = L.h * L.w, total = L.cin * hw_i;
   const float* wt = c.sW + F.swt;
-  for (int e = threadIdx.x; e < total; e += FT) {
+  for (int e = threadIdx.x; e < total; e += NT) {
     const int ch = e / hw_i, rem = e % hw_i, yy = rem / L.w, xx = rem % L.w;
     float acc[S];
 #pragma unroll
@@ -489,8 +488,8 @@ __device__ void conv_t_generic(const Ctx<S>& c, const LayerDev& L, const FusedLa
 }
 
 // Transposed pass of layer L = layer k+1 into layer k, with the epilogue.
-template <int S>
-__device__ void transposed_pass(const Ctx<S>& c, const LayerDev& L, const FusedLayer& F, int k) {
+template <int S, int NT>
+__device__ void transposed_pass(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, int k) {
   if (L.kind == LD_LAYER_FC) {
     transposed_fc(c, L, F, k);
   } else if (F.tmode == 1) {
@@ -509,12 +508,12 @@ __device__ void transposed_pass(const Ctx<S>& c, const LayerDev& L, const FusedL
 }
 
 // Top subproblem: g_{n-1} = -W_n (rho_n = -1); layer n is FC.
-template <int S>
-__device__ void top_pass(const Ctx<S>& c) {
+template <int S, int NT>
+__device__ void top_pass(const Ctx<S, NT>& c) {
   const int k = c.net.n - 1;
   const LayerDev& L = c.net.L[k];
   const FusedLayer& F = c.net.F[k];
-  for (int e = threadIdx.x; e < S * L.n_in; e += FT) {
+  for (int e = threadIdx.x; e < S * L.n_in; e += NT) {
     const int s = e / L.n_in, i = e % L.n_in;
     if (active(c, s)) epi_t(c, k, s, i, F.xoff + i, rho_of_layer(c, k, i), -__ldg(L.W + i));
   }
@@ -522,10 +521,10 @@ __device__ void top_pass(const Ctx<S>& c) {
 
 // ------------------------------------------------------------------ kernel
 
-template <int S>
-__global__ void __launch_bounds__(FT) fused_kernel(const __grid_constant__ FusedNet net,
+template <int S, int NT>
+__global__ void __launch_bounds__(NT) fused_kernel(const __grid_constant__ FusedNet net,
                                                    const __grid_constant__ Problem P, float* rho, float* m, float* v,
-                                                   FusedIter it) {
+                                                   const __grid_constant__ FusedIter it) {
   extern __shared__ __align__(16) float smem[];
   const int b0 = (int)blockIdx.x * S;
   float* sW = smem;
@@ -534,20 +533,20 @@ __global__ void __launch_bounds__(FT) fused_kernel(const __grid_constant__ Fused
   float* RHO = XB + S * net.nb;
   float* M = RHO + S * net.rho_total;
   float* V = M + S * net.nb;
-  Ctx<S> c{net, P, sW, XP, XB, RHO, M, V, b0, false};
+  Ctx<S, NT> c{net, P, sW, XP, XB, RHO, M, V, b0, false};
   // conv weights; zero planes (their halos stay zero for the whole run)
   for (int k = 0; k < net.n; ++k) {
     const LayerDev& L = net.L[k];
     if (L.kind == LD_LAYER_CONV) {
       const int nw = L.cout * L.cin * L.kh * L.kw;
-      for (int e = threadIdx.x; e < nw; e += FT) {
+      for (int e = threadIdx.x; e < nw; e += NT) {
         sW[net.F[k].swf + e] = L.Wf[e];
         sW[net.F[k].swt + e] = L.Wt[e];
       }
     }
   }
-  for (int e = threadIdx.x; e < S * net.xp_total; e += FT) XP[e] = 0.f;
-  for (int e = threadIdx.x; e < S * net.rho_total; e += FT) RHO[e] = 0.f;
+  for (int e = threadIdx.x; e < S * net.xp_total; e += NT) XP[e] = 0.f;
+  for (int e = threadIdx.x; e < S * net.rho_total; e += NT) RHO[e] = 0.f;
   __syncthreads();
   // load rho (into the padded planes), m and v
   for (int s = 0; s < S; ++s) {
@@ -557,9 +556,9 @@ __global__ void __launch_bounds__(FT) fused_kernel(const __grid_constant__ Fused
       const LayerDev& L = net.L[k - 1];
       const FusedLayer& F = net.F[k - 1];
       if (it.crown) continue;
-      for (int j = threadIdx.x; j < L.n_out; j += FT) c.rho(s)[rho_flat(L, F, j)] = rho[gb + L.r_out_off + j];
+      for (int j = threadIdx.x; j < L.n_out; j += NT) c.rho(s)[rho_flat(L, F, j)] = rho[gb + L.r_out_off + j];
     }
-    for (int j = threadIdx.x; j < P.N; j += FT) {
+    for (int j = threadIdx.x; j < P.N; j += NT) {
       M[s * net.nb + j] = m[gb + j];
       V[s * net.nb + j] = v[gb + j];
     }
@@ -576,12 +575,7 @@ __global__ void __launch_bounds__(FT) fused_kernel(const __grid_constant__ Fused
     c.crown = false;
   }
   for (int t = 0; t < it.T; ++t) {
-    const int tt = it.t_offset + t;
-    AdamStep st;
-    const double den = (double)(it.T_sched - 1 > 1 ? it.T_sched - 1 : 1);
-    st.alpha = (float)((double)it.alpha0 + ((double)it.alpha_end - (double)it.alpha0) * (double)tt / den);
-    st.inv_bc1 = (float)(1.0 / (1.0 - pow((double)it.beta1, (double)(tt + 1))));
-    st.inv_bc2 = (float)(1.0 / (1.0 - pow((double)it.beta2, (double)(tt + 1))));
+    const AdamStep st = it.step[t];
     top_pass(c);
     __syncthreads();
     for (int k = net.n - 2; k >= 0; --k) {
@@ -591,11 +585,11 @@ __global__ void __launch_bounds__(FT) fused_kernel(const __grid_constant__ Fused
       __syncthreads();
       if (L.kind == LD_LAYER_FC)
         forward_fc(c, L, F, it, st);
-      else if (F.fmode == 1 && S * L.ho * (L.wo / 2) * (L.cout / 4) >= FT)
+      else if (F.fmode == 1 && S * L.ho * (L.wo / 2) * (L.cout / 4) >= NT)
         conv_fwd_blocked<4, 4, 2, 4>(c, L, F, it, st);
       else if (F.fmode == 1)  // too few 4-channel items to fill the CTA
         conv_fwd_blocked<4, 4, 2, 2>(c, L, F, it, st);
-      else if (F.fmode == 2 && S * L.ho * (L.wo / 2) * (L.cout / 4) >= FT)
+      else if (F.fmode == 2 && S * L.ho * (L.wo / 2) * (L.cout / 4) >= NT)
         conv_fwd_blocked<3, 3, 1, 4>(c, L, F, it, st);
       else if (F.fmode == 2)
         conv_fwd_blocked<3, 3, 1, 2>(c, L, F, it, st);
@@ -611,9 +605,9 @@ __global__ void __launch_bounds__(FT) fused_kernel(const __grid_constant__ Fused
     for (int k = 1; k < net.n; ++k) {
       const LayerDev& L = net.L[k - 1];
       const FusedLayer& F = net.F[k - 1];
-      for (int j = threadIdx.x; j < L.n_out; j += FT) rho[gb + L.r_out_off + j] = c.rho(s)[rho_flat(L, F, j)];
+      for (int j = threadIdx.x; j < L.n_out; j += NT) rho[gb + L.r_out_off + j] = c.rho(s)[rho_flat(L, F, j)];
     }
-    for (int j = threadIdx.x; j < P.N; j += FT) {
+    for (int j = threadIdx.x; j < P.N; j += NT) {
       m[gb + j] = M[s * net.nb + j];
       v[gb + j] = V[s * net.nb + j];
     }
@@ -624,15 +618,15 @@ size_t smem_bytes(const FusedNet& f, int S) {
   return sizeof(float) * ((size_t)f.convW_total + (size_t)S * (f.xp_total + f.rho_total + 3 * (size_t)f.nb));
 }
 
-template <int S>
+template <int S, int NT>
 cudaError_t launch_s(const FusedNet& f, const Problem& P, float* rho, float* m, float* v, const FusedIter& it,
                      cudaStream_t s) {
   const size_t sm = smem_bytes(f, S);
-  cudaError_t e = cudaFuncSetAttribute(fused_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = cudaFuncSetAttribute(fused_kernel<S, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   const int grid = (P.B + S - 1) / S;
   count_launch();
-  fused_kernel<S><<<grid, FT, sm, s>>>(f, P, rho, m, v, it);
+  fused_kernel<S, NT><<<grid, NT, sm, s>>>(f, P, rho, m, v, it);
   return cudaGetLastError();
 }
 
@@ -707,13 +701,14 @@ FusedNet make_fused_net(const std::vector<LayerDev>& Ls) {
 
 size_t fused_smem_bytes(const FusedNet& f, int S) { return smem_bytes(f, S); }
 
-cudaError_t launch_fused(const FusedNet& f, int S, const Problem& P, float* rho, float* m, float* v,
+cudaError_t launch_fused(const FusedNet& f, int code, const Problem& P, float* rho, float* m, float* v,
                          const FusedIter& it, cudaStream_t s) {
   if (P.B == 0 || (it.T == 0 && !it.crown)) return cudaSuccess;
-  switch (S) {
-    case 1: return launch_s<1>(f, P, rho, m, v, it, s);
-    case 2: return launch_s<2>(f, P, rho, m, v, it, s);
-    case 4: return launch_s<4>(f, P, rho, m, v, it, s);
+  switch (code) {
+    case 1: return launch_s<1, 256>(f, P, rho, m, v, it, s);
+    case 2: return launch_s<2, 256>(f, P, rho, m, v, it, s);
+    case 4: return launch_s<4, 256>(f, P, rho, m, v, it, s);
+    case 2 | kFusedWide: return launch_s<2, 512>(f, P, rho, m, v, it, s);
   }
   return cudaErrorInvalidValue;
 }

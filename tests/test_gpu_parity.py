@@ -251,7 +251,7 @@ FULL_RUN_MEDIAN = 3e-4
 
 ENGINES = {"layerwise": ldb.Options(engine="layerwise"), "fused1": ldb.Options(engine="fused", tile=1),
            "fused2": ldb.Options(engine="fused", tile=2), "fused4": ldb.Options(engine="fused", tile=4),
-           "auto": ldb.Options()}
+           "fused2w": ldb.Options(engine="fused", tile=2, cta_threads=512), "auto": ldb.Options()}
 _oracle_cache = {}
 
 
@@ -272,7 +272,7 @@ def run_both(pb, T, engine="auto", key=None):
     return out[fin], ref[fin]
 
 
-@pytest.mark.parametrize("engine", ["layerwise", "fused1", "fused2", "fused4"])
+@pytest.mark.parametrize("engine", ["layerwise", "fused1", "fused2", "fused4", "fused2w"])
 @pytest.mark.parametrize("name", ["base", "wide", "deep"])
 @pytest.mark.parametrize("T", [1, 3])
 def test_short_runs_match_oracle_strictly(name, T, engine):
@@ -295,7 +295,7 @@ def test_tiny_full_runs_match_oracle_and_stay_below_lp(tiny_set):
     assert max(errs) < FULL_RUN_MAX and np.median(errs) < FULL_RUN_MEDIAN
 
 
-@pytest.mark.parametrize("engine", ["layerwise", "fused1", "fused2", "fused4"])
+@pytest.mark.parametrize("engine", ["layerwise", "fused1", "fused2", "fused4", "fused2w"])
 @pytest.mark.parametrize("name,B,T", [("base", 24, 100), ("deep", 12, 100), ("wide", 8, 60)])
 def test_convnet_full_runs_match_oracle(name, B, T, engine):
     pb = conv_problem(name, B, depth=(0, 8), block=5)
@@ -318,6 +318,26 @@ def test_resume_is_bitwise(base16, engine):
     _, rho_1 = ldb.ld_bound(net, *args, n_iters=12, opts=o1, return_rho=True, adam_mv=mv)
     o2 = ldb.Options(t_offset=12, t_total=20, init="given", engine=engine, tile=2)
     out_b, rho_b = ldb.ld_bound(net, *args, n_iters=8, opts=o2, rho_in=rho_1, return_rho=True, adam_mv=mv)
+    assert torch.equal(rho_a, rho_b)
+    assert torch.equal(out_a, out_b)
+
+
+@pytest.mark.parametrize("tile,nt", [(1, 256), (2, 512)])
+def test_fused_long_runs_split_into_launches_bitwise(base16, tile, nt):
+    """A fused run longer than one launch's step table (128 iterations) is
+    split into launches that reload the state; the result equals the same
+    iterations resumed at another split point."""
+    pb = base16
+    net = gpu_net(pb)
+    args = (pb["l0"], pb["u0"], pb["lbk"], pb["ubk"], pb["prop"], pb["masks"])
+    kw = dict(engine="fused", tile=tile, cta_threads=nt)
+    out_a, rho_a = ldb.ld_bound(net, *args, n_iters=150, return_rho=True, opts=ldb.Options(**kw))
+    B, N = pb["B"], pb["lbk"].shape[1]
+    mv = torch.zeros((2, B, N), dtype=torch.float32, device="cuda")
+    _, rho_1 = ldb.ld_bound(net, *args, n_iters=100, opts=ldb.Options(t_offset=0, t_total=150, **kw),
+                            return_rho=True, adam_mv=mv)
+    out_b, rho_b = ldb.ld_bound(net, *args, n_iters=50, rho_in=rho_1, return_rho=True, adam_mv=mv,
+                                opts=ldb.Options(t_offset=100, t_total=150, init="given", **kw))
     assert torch.equal(rho_a, rho_b)
     assert torch.equal(out_a, out_b)
 
@@ -403,8 +423,9 @@ def test_engines_agree_after_one_iteration(base16):
     net = gpu_net(pb)
     args = (pb["l0"], pb["u0"], pb["lbk"], pb["ubk"], pb["prop"], pb["masks"])
     outs, rhos = [], []
-    for eng, tile in (("layerwise", 0), ("fused", 1), ("fused", 2), ("fused", 4)):
-        o, r = ldb.ld_bound(net, *args, n_iters=1, return_rho=True, opts=ldb.Options(engine=eng, tile=tile))
+    for eng, tile, nt in (("layerwise", 0, 0), ("fused", 1, 0), ("fused", 2, 0), ("fused", 4, 0), ("fused", 2, 512)):
+        o, r = ldb.ld_bound(net, *args, n_iters=1, return_rho=True,
+                            opts=ldb.Options(engine=eng, tile=tile, cta_threads=nt))
         outs.append(o.cpu().numpy())
         rhos.append(r.cpu().numpy())
     for o, r in zip(outs[1:], rhos[1:]):

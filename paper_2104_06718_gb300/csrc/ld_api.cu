@@ -304,7 +304,8 @@ ld::AdamStep adam_step(const ld_opts& o, int tt, int T_sched) {
   return a;
 }
 
-bool tile_fits(const ld_net* net, int S) { return ld::fused_smem_bytes(net->fused, S) <= net->smem_optin; }
+// code: subdomains per CTA, plus ld::kFusedWide for 512-thread CTAs.
+bool tile_fits(const ld_net* net, int code) { return ld::fused_smem_bytes(net->fused, code) <= net->smem_optin; }
 
 // T Adam iterations with the given engine (tile = subdomains per CTA).
 // crown: the fused engine computes the CROWN start itself (with the same
@@ -464,9 +465,11 @@ std::pair<int, int> choose_engine(ld_net* net, const Problem& P, const ld_opts& 
   if (o.engine == LD_ENGINE_FUSED) {
     int S = o.tile;
     if (S == 0) S = o.cta_threads == 512 ? 2 : (P.B <= 2 * net->n_sm ? 1 : 2);
-    while (S > 1 && !tile_fits(net, S)) S /= 2;
-    if (!tile_fits(net, S)) return {LD_ENGINE_LAYERWISE, 0};
-    return {LD_ENGINE_FUSED, S | (S == 2 && o.cta_threads == 512 ? ld::kFusedWide : 0)};
+    const int wide = o.cta_threads == 512 ? ld::kFusedWide : 0;
+    while (S > 1 && !tile_fits(net, S | (S == 2 ? wide : 0))) S /= 2;
+    const int code = S | (S == 2 ? wide : 0);
+    if (!tile_fits(net, code)) return {LD_ENGINE_LAYERWISE, 0};
+    return {LD_ENGINE_FUSED, code};
   }
   auto hit = net->tuned.find(P.B);
   if (hit != net->tuned.end()) return hit->second;
@@ -481,7 +484,7 @@ std::pair<int, int> choose_engine(ld_net* net, const Problem& P, const ld_opts& 
   std::vector<std::pair<int, int>> cands = {{LD_ENGINE_LAYERWISE, 0}};
   for (int S : {1, 2, 4})
     if (tile_fits(net, S)) cands.push_back({LD_ENGINE_FUSED, S});
-  if (tile_fits(net, 2)) cands.push_back({LD_ENGINE_FUSED, 2 | ld::kFusedWide});
+  if (tile_fits(net, 2 | ld::kFusedWide)) cands.push_back({LD_ENGINE_FUSED, 2 | ld::kFusedWide});
   const size_t BN = (size_t)P.B * net->N;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);

@@ -295,8 +295,8 @@ struct FusedIter {
 constexpr int kFusedWide = 16;
 
 FusedNet make_fused_net(const std::vector<LayerDev>& Ls);
-// Shared memory of a fused CTA owning S subdomains (all their state resident).
-size_t fused_smem_bytes(const FusedNet& f, int S);
+// Shared memory of a fused launch of the given shape code (all state resident).
+size_t fused_smem_bytes(const FusedNet& f, int code);
 cudaError_t launch_fused(const FusedNet& f, int code, const Problem& P, float* rho, float* m, float* v,
                          const FusedIter& it, cudaStream_t s);
 

@@ -22,6 +22,7 @@
 // paths: a thread computes 2 positions (x and x + half) x 4 channels with
 // compile-time taps, and the transposed conv is split by stride phase so that
 // every tap it visits is valid.  Other geometries take generic loops.
+#include <algorithm>
 #include <cmath>
 
 #include "ld_common.cuh"
@@ -41,8 +42,10 @@ struct Ctx {
   float* RHO;      // [S][rho_total] padded rho planes
   float* M;        // [S][nb]
   float* V;        // [S][nb]
+  float* RED;      // scratch of the FC passes (partial sums, deferred epilogue inputs)
   int b0;          // first subdomain of this CTA
   bool crown;      // transposed-pass epilogue computes the CROWN duals instead of the argmin
+  unsigned empty;  // bit s: subdomain b0 + s has crossing bounds (no update)
   __device__ float* xp(int s) const { return XP + s * net.xp_total; }
   __device__ float* xb(int s) const { return XB + s * net.nb; }
   __device__ float* rho(int s) const { return RHO + s * net.rho_total; }
@@ -59,13 +62,6 @@ __device__ __forceinline__ int xp_conv(const LayerDev& L, const FusedLayer& F, i
     return F.xoff + (((ch * 2 + (Y & 1)) * 2 + (X & 1)) * hq + (Y >> 1)) * wq + (X >> 1);
   }
   return F.xoff + (ch * F.Hp + Y) * F.Wp + X;
-}
-
-// Index of input element i (flat c,h,w) of layer L in its padded plane.
-__device__ __forceinline__ int xp_flat(const LayerDev& L, const FusedLayer& F, int i) {
-  if (L.kind == LD_LAYER_FC) return F.xoff + i;
-  const int hw = L.h * L.w, ch = i / hw, r = i % hw;
-  return xp_conv(L, F, ch, r / L.w, r % L.w);
 }
 
 // Index of output element (o, y, x) of conv layer L in its padded rho plane.
@@ -123,14 +119,43 @@ __device__ __forceinline__ void epi_t(const Ctx<S, NT>& c, int k, int s, int i, 
   c.xb(s)[j] = xb;
 }
 
-// Forward-pass epilogue: supergradient and Adam step on neuron jj of layer
-// k+1 (L) with acc = (W_{k+1} x_k)[jj]; ri: where rho_{k+1}[jj] sits.
+// epi_t for a layer k >= 1 whose clamped bounds (l, u) of neuron i were
+// loaded beforehand.
 template <int S, int NT>
-__device__ __forceinline__ void epi_f(const Ctx<S, NT>& c, const LayerDev& L, int s, int jj, int ri, float acc,
-                                      const FusedIter& it, const AdamStep& st) {
-  if (c.P.empty[c.b0 + s]) return;
-  const int plane = L.kind == LD_LAYER_FC ? 1 : L.ho * L.wo;
-  const float xa = acc + __ldg(L.b + jj / plane);
+__device__ __forceinline__ void epi_t_lu(const Ctx<S, NT>& c, int k, int s, int i, int xi, int ri, float g, float l,
+                                         float u) {
+  if (c.crown) {
+    float a_up, a_lo;
+    if (u <= 0.f) {
+      a_up = 0.f;
+      a_lo = 0.f;
+    } else if (l >= 0.f) {
+      a_up = 1.f;
+      a_lo = 1.f;
+    } else {
+      a_up = u / (u - l);
+      a_lo = (u >= -l) ? 1.f : 0.f;
+    }
+    c.rho(s)[ri] = a_up * fmaxf(g, 0.f) + a_lo * fminf(g, 0.f);
+    return;
+  }
+  const int j = c.net.L[k - 1].r_out_off + i;
+  const float r = c.rho(s)[ri];
+  float xb, xv;
+  int code;
+  relu_argmin<float>(r, g, l, u, xb, xv, code);
+  c.xp(s)[xi] = xv;
+  c.xb(s)[j] = xb;
+}
+
+// Forward-pass epilogue: supergradient and Adam step on neuron jj (output
+// channel ch) of layer k+1 (L) with acc = (W_{k+1} x_k)[jj]; ri: where
+// rho_{k+1}[jj] sits.
+template <int S, int NT>
+__device__ __forceinline__ void epi_f(const Ctx<S, NT>& c, const LayerDev& L, int s, int jj, int ch, int ri,
+                                      float acc, const FusedIter& it, const AdamStep& st) {
+  if ((c.empty >> s) & 1u) return;
+  const float xa = acc + __ldg(L.b + ch);
   const int j = L.r_out_off + jj;
   const float sg = c.xb(s)[j] - xa;
   float* m = c.M + s * c.net.nb;
@@ -152,50 +177,120 @@ __device__ __forceinline__ int rho_of_layer(const Ctx<S, NT>& c, int k, int i) {
 // ------------------------------------------------------------------ FC passes
 
 // Transposed FC pass of layer L = layer k+1 into layer k: g[s][i] = sum_o W[o, i] rho_{k+1}[s][o].
+// A thread owns 4 consecutive columns i and streams the weight rows in
+// batches of U 16-byte loads; the clamped bounds its epilogue needs are
+// loaded before the weight loop.  When the CTA has at least twice as many
+// threads as 4-column groups, its two halves take one half of the rows each
+// and add their partial sums through shared memory (half p finalises the
+// subdomains s with s % 2 == p).
+template <int S, int NT>
+__device__ __forceinline__ void tfc_rows(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, int i4,
+                                         int b_lo, int b_hi, float4 (&acc)[S]) {
+  constexpr int U = 16;  // weight rows in flight per thread
+  const float* __restrict__ W = L.W;
+#pragma unroll
+  for (int s = 0; s < S; ++s) acc[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int nb = b_hi - b_lo;
+  for (int bi = 0; bi < nb; ++bi) {
+    // every CTA streams the same weight rows: start at a CTA-dependent batch
+    // so that concurrent CTAs spread over the L2 slices
+    const int o0 = U * (b_lo + (bi + (int)blockIdx.x) % nb);
+    float4 wv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      wv[u] = (o0 + u < L.n_out) ? __ldg(reinterpret_cast<const float4*>(W + (size_t)(o0 + u) * L.n_in) + i4)
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (o0 + u < L.n_out) {
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          const float r = c.rho(s)[F.roff + o0 + u];
+          acc[s].x = fmaf(wv[u].x, r, acc[s].x);
+          acc[s].y = fmaf(wv[u].y, r, acc[s].y);
+          acc[s].z = fmaf(wv[u].z, r, acc[s].z);
+          acc[s].w = fmaf(wv[u].w, r, acc[s].w);
+        }
+      }
+    }
+  }
+}
+
+// Epilogue of the 4 columns of group i4 for subdomain s (bounds preloaded for k >= 1).
+template <int S, int NT>
+__device__ __forceinline__ void tfc_epi(const Ctx<S, NT>& c, const FusedLayer& F, int k, int s, int i4,
+                                        const float4& a4, const float (&l)[4], const float (&u)[4]) {
+  const float a[4] = {a4.x, a4.y, a4.z, a4.w};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = 4 * i4 + q;
+    if (k >= 1)
+      epi_t_lu(c, k, s, i, F.xoff + i, rho_of_layer(c, k, i), a[q], l[q], u[q]);
+    else
+      epi_t(c, k, s, i, F.xoff + i, 0, a[q]);
+  }
+}
+
+template <int S, int NT>
+__device__ __forceinline__ void tfc_bounds(const Ctx<S, NT>& c, int k, int s, int i4, float (&l)[4], float (&u)[4]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    l[q] = 0.f;
+    u[q] = 0.f;
+    if (k >= 1) clamped_bounds(c.P, c.b0 + s, c.net.L[k - 1].r_out_off + 4 * i4 + q, l[q], u[q]);
+  }
+}
+
 template <int S, int NT>
 __device__ void transposed_fc(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, int k) {
   const float* __restrict__ W = L.W;
-  if (F.vec4) {
-    constexpr int U = 16;  // weight rows in flight per thread
-    const int n4 = L.n_in / 4;
-    for (int i4 = threadIdx.x; i4 < n4; i4 += NT) {
-      float4 acc[S];
+  constexpr int U = 16;
+  if (F.vec4 && 2 * (L.n_in / 4) <= NT) {
+    // row split between the two halves of the CTA (uniform control flow: one
+    // barrier in the middle)
+    const int n4 = L.n_in / 4, half = NT / 2;
+    const int part = (int)threadIdx.x >= half ? 1 : 0;
+    const int i4 = (int)threadIdx.x - part * half;
+    const bool valid = i4 < n4;
+    const int nbat = (L.n_out + U - 1) / U, mid = (nbat + 1) / 2;
+    float4 acc[S];
+    float l[S][4], u[S][4];
+    if (valid) {
 #pragma unroll
-      for (int s = 0; s < S; ++s) acc[s] = make_float4(0.f, 0.f, 0.f, 0.f);
-      // every CTA streams the same weight rows: start at a CTA-dependent batch
-      // so that concurrent CTAs spread over the L2 slices
-      const int nbat = (L.n_out + U - 1) / U;
-      for (int bi = 0; bi < nbat; ++bi) {
-        const int o0 = U * ((bi + (int)blockIdx.x) % nbat);
-        float4 wv[U];
+      for (int s = 0; s < S; ++s)
+        if ((S == 1 ? 0 : (s & 1)) == part) tfc_bounds(c, k, s, i4, l[s], u[s]);
+      tfc_rows(c, L, F, i4, part ? mid : 0, part ? nbat : mid, acc);
+    }
+    float4* X = reinterpret_cast<float4*>(c.RED);  // [S][n4] partial sums
+    if (valid) {
 #pragma unroll
-        for (int u = 0; u < U; ++u)
-          wv[u] = (o0 + u < L.n_out) ? __ldg(reinterpret_cast<const float4*>(W + (size_t)(o0 + u) * L.n_in) + i4)
-                                     : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          if (o0 + u < L.n_out) {
-#pragma unroll
-            for (int s = 0; s < S; ++s) {
-              const float r = c.rho(s)[F.roff + o0 + u];
-              acc[s].x = fmaf(wv[u].x, r, acc[s].x);
-              acc[s].y = fmaf(wv[u].y, r, acc[s].y);
-              acc[s].z = fmaf(wv[u].z, r, acc[s].z);
-              acc[s].w = fmaf(wv[u].w, r, acc[s].w);
-            }
-          }
-        }
-      }
+      for (int s = 0; s < S; ++s)
+        if ((S == 1 ? 0 : (s & 1)) != part) X[s * n4 + i4] = acc[s];
+    }
+    __syncthreads();
+    if (valid) {
 #pragma unroll
       for (int s = 0; s < S; ++s) {
-        if (!active(c, s)) continue;
-        const float a[4] = {acc[s].x, acc[s].y, acc[s].z, acc[s].w};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int i = 4 * i4 + q;
-          epi_t(c, k, s, i, F.xoff + i, rho_of_layer(c, k, i), a[q]);
-        }
+        if ((S == 1 ? 0 : (s & 1)) != part || !active(c, s)) continue;
+        const float4 o = X[s * n4 + i4];  // the other half's rows (one rounding, commutative)
+        const float4 a = make_float4(acc[s].x + o.x, acc[s].y + o.y, acc[s].z + o.z, acc[s].w + o.w);
+        tfc_epi(c, F, k, s, i4, a, l[s], u[s]);
       }
+    }
+    return;
+  }
+  if (F.vec4) {
+    const int n4 = L.n_in / 4;
+    const int nbat = (L.n_out + U - 1) / U;
+    for (int i4 = threadIdx.x; i4 < n4; i4 += NT) {
+      float l[S][4], u[S][4];
+#pragma unroll
+      for (int s = 0; s < S; ++s) tfc_bounds(c, k, s, i4, l[s], u[s]);
+      float4 acc[S];
+      tfc_rows(c, L, F, i4, 0, nbat, acc);
+#pragma unroll
+      for (int s = 0; s < S; ++s)
+        if (active(c, s)) tfc_epi(c, F, k, s, i4, acc[s], l[s], u[s]);
     }
     return;
   }
@@ -215,7 +310,8 @@ __device__ void transposed_fc(const Ctx<S, NT>& c, const LayerDev& L, const Fuse
 }
 
 // Forward FC: a warp takes two output neurons at a time, lanes split the
-// inputs; up to 8 16-byte loads per row are in flight per lane.
+// inputs; up to 8 16-byte loads per row are in flight per lane.  The sums go
+// to shared memory and the epilogue runs once all rows are done.
 template <int S, int NT>
 __device__ void forward_fc(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, const FusedIter& it,
                            const AdamStep& st) {
@@ -278,9 +374,16 @@ __device__ void forward_fc(const Ctx<S, NT>& c, const LayerDev& L, const FusedLa
         for (int off = 16; off > 0; off >>= 1) acc[q][s] += __shfl_xor_sync(0xffffffffu, acc[q][s], off);
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      if (lane == s && active(c, s)) epi_f(c, L, s, j0, F.roff + j0, acc[0][s], it, st);
-      if (two && lane == 16 + s && active(c, s)) epi_f(c, L, s, j0 + 1, F.roff + j0 + 1, acc[1][s], it, st);
+      if (lane == s) c.RED[s * L.n_out + j0] = acc[0][s];
+      if (two && lane == 16 + s) c.RED[s * L.n_out + j0 + 1] = acc[1][s];
     }
+  }
+  // the Adam epilogue of all outputs in one parallel pass (its loads do not
+  // wait behind the weight rounds)
+  __syncthreads();
+  for (int e = threadIdx.x; e < S * L.n_out; e += NT) {
+    const int s = e / L.n_out, j = e - s * L.n_out;
+    if (active(c, s)) epi_f(c, L, s, j, j, F.roff + j, c.RED[e], it, st);
   }
 }
 
@@ -348,7 +451,7 @@ __device__ void conv_fwd_blocked(const Ctx<S, NT>& c, const LayerDev& L, const F
 #pragma unroll
       for (int p = 0; p < 2; ++p) {
         const int o = og * GF + g, x = x0 + p * half;
-        epi_f(c, L, s, (o * L.ho + y) * L.wo + x, rho_conv(F, o, y, x), acc[p][g], it, st);
+        epi_f(c, L, s, (o * L.ho + y) * L.wo + x, o, rho_conv(F, o, y, x), acc[p][g], it, st);
       }
   }
 }
@@ -452,7 +555,7 @@ __device__ void conv_fwd_generic(const Ctx<S, NT>& c, const LayerDev& L, const F
         }
 #pragma unroll
     for (int s = 0; s < S; ++s)
-      if (active(c, s)) epi_f(c, L, s, e, rho_conv(F, o, y, x), acc[s], it, st);
+      if (active(c, s)) epi_f(c, L, s, e, o, rho_conv(F, o, y, x), acc[s], it, st);
   }
 }
 
@@ -533,7 +636,11 @@ __global__ void __launch_bounds__(NT) fused_kernel(const __grid_constant__ Fused
   float* RHO = XB + S * net.nb;
   float* M = RHO + S * net.rho_total;
   float* V = M + S * net.nb;
-  Ctx<S, NT> c{net, P, sW, XP, XB, RHO, M, V, b0, false};
+  float* RED = V + S * net.nb;
+  unsigned empty = 0;
+  for (int s = 0; s < S; ++s)
+    if (b0 + s < P.B && P.empty[b0 + s]) empty |= 1u << s;
+  Ctx<S, NT> c{net, P, sW, XP, XB, RHO, M, V, RED, b0, false, empty};
   // conv weights; zero planes (their halos stay zero for the whole run)
   for (int k = 0; k < net.n; ++k) {
     const LayerDev& L = net.L[k];
@@ -614,14 +721,29 @@ __global__ void __launch_bounds__(NT) fused_kernel(const __grid_constant__ Fused
   }
 }
 
-size_t smem_bytes(const FusedNet& f, int S) {
-  return sizeof(float) * ((size_t)f.convW_total + (size_t)S * (f.xp_total + f.rho_total + 3 * (size_t)f.nb));
+// Per-subdomain floats of the FC scratch: the forward pass's sums (n_out of
+// every hidden FC layer) and, for CTAs of NT threads, the partial sums of a
+// row-split transposed pass (n_in of the FC layers that split).
+size_t red_floats(const FusedNet& f, int NT) {
+  size_t r = 0;
+  for (int k = 0; k + 1 < f.n; ++k) {
+    const LayerDev& L = f.L[k];
+    if (L.kind != LD_LAYER_FC) continue;
+    r = std::max(r, (size_t)L.n_out);
+    if (f.F[k].vec4 && 2 * (L.n_in / 4) <= NT) r = std::max(r, (size_t)L.n_in);
+  }
+  return (r + 3) & ~size_t(3);
+}
+
+size_t smem_bytes(const FusedNet& f, int S, int NT) {
+  return sizeof(float) * ((size_t)f.convW_total +
+                          (size_t)S * (f.xp_total + f.rho_total + 3 * (size_t)f.nb + red_floats(f, NT)));
 }
 
 template <int S, int NT>
 cudaError_t launch_s(const FusedNet& f, const Problem& P, float* rho, float* m, float* v, const FusedIter& it,
                      cudaStream_t s) {
-  const size_t sm = smem_bytes(f, S);
+  const size_t sm = smem_bytes(f, S, NT);
   cudaError_t e = cudaFuncSetAttribute(fused_kernel<S, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   const int grid = (P.B + S - 1) / S;
@@ -699,7 +821,9 @@ FusedNet make_fused_net(const std::vector<LayerDev>& Ls) {
   return f;
 }
 
-size_t fused_smem_bytes(const FusedNet& f, int S) { return smem_bytes(f, S); }
+size_t fused_smem_bytes(const FusedNet& f, int code) {
+  return smem_bytes(f, code & ~kFusedWide, (code & kFusedWide) ? 512 : 256);
+}
 
 cudaError_t launch_fused(const FusedNet& f, int code, const Problem& P, float* rho, float* m, float* v,
                          const FusedIter& it, cudaStream_t s) {

@@ -91,8 +91,8 @@ typedef struct {
   int32_t engine;      /* LD_ENGINE_*: how the iterations are launched      */
   int32_t tile;        /* fused engine: subdomains per CTA (0 auto, 1, 2, 4) */
   int32_t cta_threads; /* fused engine: threads per CTA, 256 or 512 (512 only
-                          with tile 2); 0: 256 for an explicit tile, the
-                          autotuner's choice under LD_ENGINE_AUTO          */
+                          with tile 1 or 2); 0: 256 for an explicit tile,
+                          the autotuner's choice under LD_ENGINE_AUTO      */
 } ld_opts;
 
 /* Engines for the iterations (all compute the same iterates up to FP32

@@ -141,7 +141,7 @@ class Options:
     t_total: int = 0
     engine: str = "auto"         # "auto" | "layerwise" | "fused"
     tile: int = 0                # fused engine: subdomains per CTA (0 = auto, 1, 2, 4)
-    cta_threads: int = 0         # fused engine: threads per CTA (0 = auto, 256, 512 with tile 2)
+    cta_threads: int = 0         # fused engine: threads per CTA (0 = auto, 256, 512 with tile 1 or 2)
 
     def to_c(self) -> Opts:
         return Opts(self.alpha0, self.alpha_end, self.beta1, self.beta2, self.eps,

@@ -219,7 +219,7 @@ ld_status check_opts(const ld_opts& o) {
   if (o.engine < LD_ENGINE_AUTO || o.engine > LD_ENGINE_FUSED) return LD_ERR_ARG;
   if (o.tile != 0 && o.tile != 1 && o.tile != 2 && o.tile != 4) return LD_ERR_ARG;
   if (o.cta_threads != 0 && o.cta_threads != 256 && o.cta_threads != 512) return LD_ERR_ARG;
-  if (o.cta_threads == 512 && o.tile != 0 && o.tile != 2) return LD_ERR_ARG;
+  if (o.cta_threads == 512 && o.tile == 4) return LD_ERR_ARG;
   return LD_OK;
 }
 
@@ -466,8 +466,8 @@ std::pair<int, int> choose_engine(ld_net* net, const Problem& P, const ld_opts& 
     int S = o.tile;
     if (S == 0) S = o.cta_threads == 512 ? 2 : (P.B <= 2 * net->n_sm ? 1 : 2);
     const int wide = o.cta_threads == 512 ? ld::kFusedWide : 0;
-    while (S > 1 && !tile_fits(net, S | (S == 2 ? wide : 0))) S /= 2;
-    const int code = S | (S == 2 ? wide : 0);
+    while (S > 1 && !tile_fits(net, S | (S <= 2 ? wide : 0))) S /= 2;
+    const int code = S | (S <= 2 ? wide : 0);
     if (!tile_fits(net, code)) return {LD_ENGINE_LAYERWISE, 0};
     return {LD_ENGINE_FUSED, code};
   }
@@ -484,7 +484,8 @@ std::pair<int, int> choose_engine(ld_net* net, const Problem& P, const ld_opts& 
   std::vector<std::pair<int, int>> cands = {{LD_ENGINE_LAYERWISE, 0}};
   for (int S : {1, 2, 4})
     if (tile_fits(net, S)) cands.push_back({LD_ENGINE_FUSED, S});
-  if (tile_fits(net, 2 | ld::kFusedWide)) cands.push_back({LD_ENGINE_FUSED, 2 | ld::kFusedWide});
+  for (int S : {1, 2})
+    if (tile_fits(net, S | ld::kFusedWide)) cands.push_back({LD_ENGINE_FUSED, S | ld::kFusedWide});
   const size_t BN = (size_t)P.B * net->N;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);

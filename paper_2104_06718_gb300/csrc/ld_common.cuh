@@ -290,8 +290,9 @@ struct FusedIter {
 };
 
 // Fused launch shape: code = subdomains per CTA (1, 2, 4; 256 threads), plus
-// kFusedWide for 512 threads per CTA (only with 2 subdomains: the FC weights
-// then stream once per 2 subdomains while 16 warps share the conv work).
+// kFusedWide for 512 threads per CTA (with 1 or 2 subdomains: 16 warps share
+// the conv work of a CTA whose state takes most of the SM's shared memory;
+// with 2 the FC weights also stream once per 2 subdomains).
 constexpr int kFusedWide = 16;
 
 FusedNet make_fused_net(const std::vector<LayerDev>& Ls);

@@ -832,6 +832,7 @@ cudaError_t launch_fused(const FusedNet& f, int code, const Problem& P, float* r
     case 1: return launch_s<1, 256>(f, P, rho, m, v, it, s);
     case 2: return launch_s<2, 256>(f, P, rho, m, v, it, s);
     case 4: return launch_s<4, 256>(f, P, rho, m, v, it, s);
+    case 1 | kFusedWide: return launch_s<1, 512>(f, P, rho, m, v, it, s);
     case 2 | kFusedWide: return launch_s<2, 512>(f, P, rho, m, v, it, s);
   }
   return cudaErrorInvalidValue;

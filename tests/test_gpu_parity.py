@@ -251,7 +251,8 @@ FULL_RUN_MEDIAN = 3e-4
 
 ENGINES = {"layerwise": ldb.Options(engine="layerwise"), "fused1": ldb.Options(engine="fused", tile=1),
            "fused2": ldb.Options(engine="fused", tile=2), "fused4": ldb.Options(engine="fused", tile=4),
-           "fused2w": ldb.Options(engine="fused", tile=2, cta_threads=512), "auto": ldb.Options()}
+           "fused2w": ldb.Options(engine="fused", tile=2, cta_threads=512),
+           "fused1w": ldb.Options(engine="fused", tile=1, cta_threads=512), "auto": ldb.Options()}
 _oracle_cache = {}
 
 
@@ -272,7 +273,7 @@ def run_both(pb, T, engine="auto", key=None):
     return out[fin], ref[fin]
 
 
-@pytest.mark.parametrize("engine", ["layerwise", "fused1", "fused2", "fused4", "fused2w"])
+@pytest.mark.parametrize("engine", ["layerwise", "fused1", "fused2", "fused4", "fused2w", "fused1w"])
 @pytest.mark.parametrize("name", ["base", "wide", "deep"])
 @pytest.mark.parametrize("T", [1, 3])
 def test_short_runs_match_oracle_strictly(name, T, engine):
@@ -295,7 +296,7 @@ def test_tiny_full_runs_match_oracle_and_stay_below_lp(tiny_set):
     assert max(errs) < FULL_RUN_MAX and np.median(errs) < FULL_RUN_MEDIAN
 
 
-@pytest.mark.parametrize("engine", ["layerwise", "fused1", "fused2", "fused4", "fused2w"])
+@pytest.mark.parametrize("engine", ["layerwise", "fused1", "fused2", "fused4", "fused2w", "fused1w"])
 @pytest.mark.parametrize("name,B,T", [("base", 24, 100), ("deep", 12, 100), ("wide", 8, 60)])
 def test_convnet_full_runs_match_oracle(name, B, T, engine):
     pb = conv_problem(name, B, depth=(0, 8), block=5)
@@ -423,7 +424,8 @@ def test_engines_agree_after_one_iteration(base16):
     net = gpu_net(pb)
     args = (pb["l0"], pb["u0"], pb["lbk"], pb["ubk"], pb["prop"], pb["masks"])
     outs, rhos = [], []
-    for eng, tile, nt in (("layerwise", 0, 0), ("fused", 1, 0), ("fused", 2, 0), ("fused", 4, 0), ("fused", 2, 512)):
+    for eng, tile, nt in (("layerwise", 0, 0), ("fused", 1, 0), ("fused", 2, 0), ("fused", 4, 0), ("fused", 2, 512),
+                          ("fused", 1, 512)):
         o, r = ldb.ld_bound(net, *args, n_iters=1, return_rho=True,
                             opts=ldb.Options(engine=eng, tile=tile, cta_threads=nt))
         outs.append(o.cpu().numpy())

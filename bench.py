@@ -52,7 +52,7 @@ TRAFFIC = {}
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="base", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -98,7 +98,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -108,7 +108,11 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self, which):
+        """Host time of the start or end of the timed region (samples outside are dropped)."""
+        setattr(self, which, time.time())
 
     def stop(self):
         if self.proc is None:
@@ -122,7 +126,10 @@ class ClockSampler:
             self.thread.join(timeout=2)
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        t0, t1 = getattr(self, "t_start", 0.0), getattr(self, "t_end", float("inf"))
+        for t, ln in self.lines:
+            if not (t0 <= t <= t1 + 0.06):
+                continue
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -320,6 +327,8 @@ def run_ours(args):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     sampler.start()
+    time.sleep(0.5)  # nvidia-smi takes a moment to report; only samples inside the timed region count
+    sampler.mark("t_start")
     net.profile(True)
     net.profile_read("iter", reset=True)
     launches0 = ldb.launch_count()
@@ -334,6 +343,7 @@ def run_ours(args):
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
     torch.cuda.synchronize()
+    sampler.mark("t_end")
     launches = ldb.launch_count() - launches0
     iter_ms, iter_n = net.profile_read("iter")
     final_ms, final_n = net.profile_read("final")

@@ -176,6 +176,29 @@ __device__ __forceinline__ int rho_of_layer(const Ctx<S, NT>& c, int k, int i) {
 
 // ------------------------------------------------------------------ FC passes
 
+// FC scratch: every hidden FC layer k has its own slice of RED, S x red_need
+// floats, so that the FC passes of different layers may be in flight at the
+// same time.  The forward pass keeps its S x n_out sums there; a transposed
+// pass split between the two CTA halves keeps two slots of S x n_in partial
+// sums.  red_off: per-subdomain floats before layer k's slice.
+__host__ __device__ inline bool tfc_split(const LayerDev& L, const FusedLayer& F, int NT) {
+  return F.vec4 && 2 * (L.n_in / 4) <= NT;
+}
+__host__ __device__ inline int red_need(const LayerDev& L, const FusedLayer& F, int NT) {
+  const int a = L.n_out, b = tfc_split(L, F, NT) ? 2 * L.n_in : 0;
+  return ((a > b ? a : b) + 3) & ~3;
+}
+__host__ __device__ inline int red_off(const FusedNet& net, int k, int NT) {
+  int off = 0;
+  for (int j = 0; j < k; ++j)
+    if (net.L[j].kind == LD_LAYER_FC) off += red_need(net.L[j], net.F[j], NT);
+  return off;
+}
+template <int S, int NT>
+__device__ __forceinline__ float* red_of(const Ctx<S, NT>& c, int k) {
+  return c.RED + S * red_off(c.net, k, NT);
+}
+
 // Transposed FC pass of layer L = layer k+1 into layer k: g[s][i] = sum_o W[o, i] rho_{k+1}[s][o].
 // A thread owns 4 consecutive columns i and streams the weight rows in
 // batches of U 16-byte loads; the clamped bounds its epilogue needs are
@@ -241,42 +264,24 @@ __device__ __forceinline__ void tfc_bounds(const Ctx<S, NT>& c, int k, int s, in
   }
 }
 
+// Main part of the transposed FC pass.  Unsplit: the whole pass.  Split:
+// each half streams its rows and publishes its partial sums (slot = half);
+// tfc_finish adds the two slots and runs the epilogue once both are written.
 template <int S, int NT>
-__device__ void transposed_fc(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, int k) {
+__device__ void tfc_main(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, int k) {
   const float* __restrict__ W = L.W;
   constexpr int U = 16;
-  if (F.vec4 && 2 * (L.n_in / 4) <= NT) {
-    // row split between the two halves of the CTA (uniform control flow: one
-    // barrier in the middle)
+  if (tfc_split(L, F, NT)) {
     const int n4 = L.n_in / 4, half = NT / 2;
     const int part = (int)threadIdx.x >= half ? 1 : 0;
     const int i4 = (int)threadIdx.x - part * half;
-    const bool valid = i4 < n4;
+    if (i4 >= n4) return;
     const int nbat = (L.n_out + U - 1) / U, mid = (nbat + 1) / 2;
     float4 acc[S];
-    float l[S][4], u[S][4];
-    if (valid) {
+    tfc_rows(c, L, F, i4, part ? mid : 0, part ? nbat : mid, acc);
+    float4* X = reinterpret_cast<float4*>(red_of(c, k)) + part * S * n4;  // slot [part][S][n4]
 #pragma unroll
-      for (int s = 0; s < S; ++s)
-        if ((S == 1 ? 0 : (s & 1)) == part) tfc_bounds(c, k, s, i4, l[s], u[s]);
-      tfc_rows(c, L, F, i4, part ? mid : 0, part ? nbat : mid, acc);
-    }
-    float4* X = reinterpret_cast<float4*>(c.RED);  // [S][n4] partial sums
-    if (valid) {
-#pragma unroll
-      for (int s = 0; s < S; ++s)
-        if ((S == 1 ? 0 : (s & 1)) != part) X[s * n4 + i4] = acc[s];
-    }
-    __syncthreads();
-    if (valid) {
-#pragma unroll
-      for (int s = 0; s < S; ++s) {
-        if ((S == 1 ? 0 : (s & 1)) != part || !active(c, s)) continue;
-        const float4 o = X[s * n4 + i4];  // the other half's rows (one rounding, commutative)
-        const float4 a = make_float4(acc[s].x + o.x, acc[s].y + o.y, acc[s].z + o.z, acc[s].w + o.w);
-        tfc_epi(c, F, k, s, i4, a, l[s], u[s]);
-      }
-    }
+    for (int s = 0; s < S; ++s) X[s * n4 + i4] = acc[s];
     return;
   }
   if (F.vec4) {
@@ -309,12 +314,43 @@ __device__ void transposed_fc(const Ctx<S, NT>& c, const LayerDev& L, const Fuse
   }
 }
 
+// Second part of a split transposed FC pass: half p finalises the
+// subdomains s with s % 2 == p (all of them for S = 1) from slot 0 + slot 1.
+template <int S, int NT>
+__device__ void tfc_finish(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, int k) {
+  if (!tfc_split(L, F, NT)) return;
+  const int n4 = L.n_in / 4, half = NT / 2;
+  const int part = (int)threadIdx.x >= half ? 1 : 0;
+  const int i4 = (int)threadIdx.x - part * half;
+  if (i4 >= n4) return;
+  const float4* X = reinterpret_cast<const float4*>(red_of(c, k));
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    if ((S == 1 ? 0 : (s & 1)) != part || !active(c, s)) continue;
+    float l[4], u[4];
+    tfc_bounds(c, k, s, i4, l, u);
+    const float4 a0 = X[s * n4 + i4], a1 = X[S * n4 + s * n4 + i4];
+    const float4 a = make_float4(a0.x + a1.x, a0.y + a1.y, a0.z + a1.z, a0.w + a1.w);
+    tfc_epi(c, F, k, s, i4, a, l, u);
+  }
+}
+
+// The whole transposed FC pass (its two parts separated by a barrier).
+template <int S, int NT>
+__device__ void transposed_fc(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, int k) {
+  tfc_main(c, L, F, k);
+  if (tfc_split(L, F, NT)) {
+    __syncthreads();
+    tfc_finish(c, L, F, k);
+  }
+}
+
 // Forward FC: a warp takes two output neurons at a time, lanes split the
 // inputs; up to 8 16-byte loads per row are in flight per lane.  The sums go
 // to shared memory and the epilogue runs once all rows are done.
 template <int S, int NT>
-__device__ void forward_fc(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, const FusedIter& it,
-                           const AdamStep& st) {
+__device__ void ffc_main(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, int k) {
+  float* red = red_of(c, k);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nwarp = NT / 32;
   const float* __restrict__ W = L.W;
   const int npair = (L.n_out + 1) / 2;
@@ -374,16 +410,22 @@ __device__ void forward_fc(const Ctx<S, NT>& c, const LayerDev& L, const FusedLa
         for (int off = 16; off > 0; off >>= 1) acc[q][s] += __shfl_xor_sync(0xffffffffu, acc[q][s], off);
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      if (lane == s) c.RED[s * L.n_out + j0] = acc[0][s];
-      if (two && lane == 16 + s) c.RED[s * L.n_out + j0 + 1] = acc[1][s];
+      if (lane == s) red[s * L.n_out + j0] = acc[0][s];
+      if (two && lane == 16 + s) red[s * L.n_out + j0 + 1] = acc[1][s];
     }
   }
-  // the Adam epilogue of all outputs in one parallel pass (its loads do not
-  // wait behind the weight rounds)
-  __syncthreads();
+}
+
+// The Adam epilogue of all outputs of a forward FC pass, in one parallel
+// pass once the sums of ffc_main are written (its loads do not wait behind
+// the weight rounds).
+template <int S, int NT>
+__device__ void ffc_finish(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, int k, const FusedIter& it,
+                           const AdamStep& st) {
+  const float* red = red_of(c, k);
   for (int e = threadIdx.x; e < S * L.n_out; e += NT) {
     const int s = e / L.n_out, j = e - s * L.n_out;
-    if (active(c, s)) epi_f(c, L, s, j, j, F.roff + j, c.RED[e], it, st);
+    if (active(c, s)) epi_f(c, L, s, j, j, F.roff + j, red[e], it, st);
   }
 }
 
@@ -590,6 +632,22 @@ __device__ void conv_t_generic(const Ctx<S, NT>& c, const LayerDev& L, const Fus
   }
 }
 
+// Forward conv pass of layer L = layer k+1, with the Adam epilogue.
+template <int S, int NT>
+__device__ void forward_conv(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, const FusedIter& it,
+                             const AdamStep& st) {
+  if (F.fmode == 1 && S * L.ho * (L.wo / 2) * (L.cout / 4) >= NT)
+    conv_fwd_blocked<4, 4, 2, 4>(c, L, F, it, st);
+  else if (F.fmode == 1)  // too few 4-channel items to fill the CTA
+    conv_fwd_blocked<4, 4, 2, 2>(c, L, F, it, st);
+  else if (F.fmode == 2 && S * L.ho * (L.wo / 2) * (L.cout / 4) >= NT)
+    conv_fwd_blocked<3, 3, 1, 4>(c, L, F, it, st);
+  else if (F.fmode == 2)
+    conv_fwd_blocked<3, 3, 1, 2>(c, L, F, it, st);
+  else
+    conv_fwd_generic(c, L, F, it, st);
+}
+
 // Transposed pass of layer L = layer k+1 into layer k, with the epilogue.
 template <int S, int NT>
 __device__ void transposed_pass(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, int k) {
@@ -681,29 +739,42 @@ __global__ void __launch_bounds__(NT) fused_kernel(const __grid_constant__ Fused
     }
     c.crown = false;
   }
+  // Which passes need a second part after a barrier (uniform over the CTA).
+  bool any_fc = false, any_split = false;
+  for (int k = 0; k + 1 < net.n; ++k)
+    if (net.L[k].kind == LD_LAYER_FC) {
+      any_fc = true;
+      any_split = any_split || tfc_split(net.L[k], net.F[k], NT);
+    }
+  // One iteration in two phases.  Every transposed pass (and the top
+  // subproblem) reads only rho of the previous iteration and writes its own
+  // layer's x and x_hat_B; every forward pass reads those and updates only its
+  // own layer's rho, m, v.  So the passes of a phase run back to back without
+  // barriers (a warp that is done with its share of one pass starts on the
+  // next), in the order FC passes first (L2-bound weight streams) then convs.
   for (int t = 0; t < it.T; ++t) {
     const AdamStep st = it.step[t];
     top_pass(c);
+    for (int k = net.n - 2; k >= 0; --k)
+      if (net.L[k].kind == LD_LAYER_FC) tfc_main(c, net.L[k], net.F[k], k);
+    for (int k = net.n - 2; k >= 0; --k)
+      if (net.L[k].kind != LD_LAYER_FC) transposed_pass(c, net.L[k], net.F[k], k);
     __syncthreads();
-    for (int k = net.n - 2; k >= 0; --k) {
-      const LayerDev& L = net.L[k];  // layer k+1
-      const FusedLayer& F = net.F[k];
-      transposed_pass(c, L, F, k);
-      __syncthreads();
-      if (L.kind == LD_LAYER_FC)
-        forward_fc(c, L, F, it, st);
-      else if (F.fmode == 1 && S * L.ho * (L.wo / 2) * (L.cout / 4) >= NT)
-        conv_fwd_blocked<4, 4, 2, 4>(c, L, F, it, st);
-      else if (F.fmode == 1)  // too few 4-channel items to fill the CTA
-        conv_fwd_blocked<4, 4, 2, 2>(c, L, F, it, st);
-      else if (F.fmode == 2 && S * L.ho * (L.wo / 2) * (L.cout / 4) >= NT)
-        conv_fwd_blocked<3, 3, 1, 4>(c, L, F, it, st);
-      else if (F.fmode == 2)
-        conv_fwd_blocked<3, 3, 1, 2>(c, L, F, it, st);
-      else
-        conv_fwd_generic(c, L, F, it, st);
+    if (any_split) {
+      for (int k = net.n - 2; k >= 0; --k)
+        if (net.L[k].kind == LD_LAYER_FC) tfc_finish(c, net.L[k], net.F[k], k);
       __syncthreads();
     }
+    for (int k = net.n - 2; k >= 0; --k)
+      if (net.L[k].kind == LD_LAYER_FC) ffc_main(c, net.L[k], net.F[k], k);
+    for (int k = net.n - 2; k >= 0; --k)
+      if (net.L[k].kind != LD_LAYER_FC) forward_conv(c, net.L[k], net.F[k], it, st);
+    if (any_fc) {
+      __syncthreads();
+      for (int k = net.n - 2; k >= 0; --k)
+        if (net.L[k].kind == LD_LAYER_FC) ffc_finish(c, net.L[k], net.F[k], k, it, st);
+    }
+    __syncthreads();
   }
   // write back rho, m, v
   for (int s = 0; s < S; ++s) {
@@ -721,19 +792,8 @@ __global__ void __launch_bounds__(NT) fused_kernel(const __grid_constant__ Fused
   }
 }
 
-// Per-subdomain floats of the FC scratch: the forward pass's sums (n_out of
-// every hidden FC layer) and, for CTAs of NT threads, the partial sums of a
-// row-split transposed pass (n_in of the FC layers that split).
-size_t red_floats(const FusedNet& f, int NT) {
-  size_t r = 0;
-  for (int k = 0; k + 1 < f.n; ++k) {
-    const LayerDev& L = f.L[k];
-    if (L.kind != LD_LAYER_FC) continue;
-    r = std::max(r, (size_t)L.n_out);
-    if (f.F[k].vec4 && 2 * (L.n_in / 4) <= NT) r = std::max(r, (size_t)L.n_in);
-  }
-  return (r + 3) & ~size_t(3);
-}
+// Per-subdomain floats of the FC scratch: the slices of all hidden FC layers.
+size_t red_floats(const FusedNet& f, int NT) { return (size_t)red_off(f, f.n - 1, NT); }
 
 size_t smem_bytes(const FusedNet& f, int S, int NT) {
   return sizeof(float) * ((size_t)f.convW_total +

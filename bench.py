@@ -44,9 +44,14 @@ METRIC = "LD subdomain bounds/s on Base/Wide/Deep convnets, bf16 vs fp32 at ≤1
 
 # DRAM bytes (read + write) of one launch of the iterations, from ncu captures
 # of the current kernels (profiles/); keyed by (workload, precision, engine,
-# subdomains, iterations).  Only entries whose kernels have not changed since
+# tile, threads per CTA, subdomains, iterations).  Only entries whose kernels have not changed since
 # the capture are listed.
-TRAFFIC = {}
+TRAFFIC = {
+    # fused_kernel<2, 512>, one launch (CROWN start + 100 iterations): profiles/fused_kernel_base256.md
+    ("base", "fp32", "fused", 2, 512, 256, 100): 8.03e6,
+    # the seven launches of one BF16 iteration x 100 (cold-cache capture): profiles/tc_kernels_wide2048_bf16.md
+    ("wide", "bf16", "tensor-core bf16", 0, 0, 2048, 100): 4.415e10,
+}
 
 
 def parse():
@@ -469,7 +474,7 @@ def run_ours(args):
     main = alu_obj if resident else hbm_obj
     roofline = {"bound": "alu" if resident else "hbm", "achieved": main["achieved"], "peak": main["peak"],
                 "unit": main["unit"], "frac": main["frac"],
-                "traffic": TRAFFIC.get((wl["name"], args.precision, engine, B, T)),
+                "traffic": TRAFFIC.get((wl["name"], args.precision, engine, tile, threads, B, T)),
                 "kernel": f"fused iterations (tile {tile}, {threads or 256} threads per CTA; rho, m, v resident "
                           "in shared memory)" if resident else f"{engine or 'auto'} iterations (one graph launch)",
                 "avg_launch_ms": iter_ms / max(iter_n, 1),

@@ -153,6 +153,26 @@ ld_status ld_net_sync_status(ld_net* net, void* stream);
 ld_status ld_intermediate_bounds(ld_net* net, const float* lb0, const float* ub0, int32_t n_props,
                                  float* lbk, float* ubk, double* out_lb, void* stream);
 
+/* Interval bounds recomputed per subdomain after its splits (the
+ * per-subdomain intermediate bounds used by BaBSR, Sec. 7.1, with the split
+ * semantics of Sec. 2.3.2): for subdomain b, layer 1 is bounded over box
+ * prop_of_subdomain[b]; each hidden layer's bounds are clamped by b's split
+ * mask (+1 => l <- max(l,0), -1 => u <- min(u,0)) before they bound the
+ * next layer through [relu(l), relu(u)].  Root bounds (ld_intermediate_bounds)
+ * clamped by the same masks can only be looser.
+ *   lb0, ub0 [device] [n_props, n_0] float boxes; prop_of_subdomain
+ *   [device] [B] int32 (NULL only when n_props == 1; out-of-range entries
+ *   are clamped); split_masks [device] [B, N] int8 (NULL = no clamp).
+ *   lbk, ubk [device] [B, N] float outputs, rounded outward, already clamped.
+ * To bound the subdomains with them, call ld_bound with n_props = B, a
+ * property map b -> b and the boxes gathered per subdomain ([B, n_0]).
+ * Errors: LD_ERR_ARG (nulls, n_props < 1, B < 0, prop NULL with
+ * n_props > 1); LD_ERR_UNSUPPORTED (B > 65535); LD_ERR_NONFINITE via the
+ * status word as ld_intermediate_bounds. */
+ld_status ld_intermediate_bounds_split(ld_net* net, const float* lb0, const float* ub0, int32_t n_props,
+                                       const int32_t* prop_of_subdomain, const int8_t* split_masks, int32_t B,
+                                       float* lbk, float* ubk, void* stream);
+
 /* LD lower bounds for B subdomains after n_iters Adam iterations
  * (Algorithm 1; Eq. box_bounds_sol and Eq. min-pk for the inner minimum).
  *   lb0, ub0 [device] [n_props, n_0] float boxes; lbk, ubk [device]

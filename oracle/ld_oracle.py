@@ -243,6 +243,41 @@ def apply_masks(net: Net, lb, ub, masks):
     return lb2, ub2, empty
 
 
+def ibp_bounds_split(net: Net, l0: np.ndarray, u0: np.ndarray, masks: np.ndarray, prop=None):
+    """Interval bounds recomputed per subdomain after its splits (the
+    per-subdomain intermediate bounds of BaBSR, Sec. 7.1 / Sec. 2.3.2).
+
+    For subdomain b, layer 1 is bounded over box prop[b]; the split clamp of
+    Sec. 2.3.2 is applied to layer k's bounds (+1 => l <- max(l,0),
+    -1 => u <- min(u,0)) before they bound layer k+1 through
+    [relu(l_k), relu(u_k)].  Returns clamped lists lb, ub indexed 1..n-1 of
+    [B, n_k] and a boolean [B] that is True where some l > u (empty domain).
+    """
+    masks = np.asarray(masks)
+    B = masks.shape[0]
+    prop = np.zeros(B, dtype=np.int64) if prop is None else np.asarray(prop, dtype=np.int64)
+    lo = np.asarray(l0, np.float64)[prop]
+    hi = np.asarray(u0, np.float64)[prop]
+    offs = split_offsets(net)
+    lb, ub = [None], [None]
+    empty = np.zeros(B, dtype=bool)
+    for k in range(1, net.n):
+        lay = net.L(k)
+        mid = (lo + hi) / 2.0
+        rad = (hi - lo) / 2.0
+        c = lay.forward(mid)
+        r = np.asarray((abs(lay.mat) @ rad.T).T)
+        m = masks[:, offs[k - 1]:offs[k]]
+        lk = np.where(m > 0, np.maximum(c - r, 0.0), c - r)
+        uk = np.where(m < 0, np.minimum(c + r, 0.0), c + r)
+        empty |= np.any(lk > uk, axis=1)
+        lb.append(lk)
+        ub.append(uk)
+        lo = np.maximum(lk, 0.0)
+        hi = np.maximum(uk, 0.0)
+    return lb, ub, empty
+
+
 def classify(l, u):
     """ReLU phases of Sec. 2.3.2: 0 blocking (u <= 0), 1 passing (l >= 0), 2 ambiguous."""
     cls = np.full(l.shape, 2, dtype=np.int8)

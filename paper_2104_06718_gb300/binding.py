@@ -26,7 +26,8 @@ LD_ENGINE_AUTO, LD_ENGINE_LAYERWISE, LD_ENGINE_FUSED = 0, 1, 2
 
 EXPORTED = [
     "ld_opts_default", "ld_status_str", "ld_net_create", "ld_net_destroy", "ld_net_sizes", "ld_net_reserve",
-    "ld_net_sync_status", "ld_selftest_wait_timeout", "ld_intermediate_bounds", "ld_bound", "ld_dual_supergradient", "ld_bound_backward",
+    "ld_net_sync_status", "ld_selftest_wait_timeout", "ld_intermediate_bounds", "ld_intermediate_bounds_split",
+    "ld_bound", "ld_dual_supergradient", "ld_bound_backward",
     "ld_net_profile", "ld_net_profile_read", "ld_launch_count", "ld_net_tuned", "ld_final_bound_noalloc",
 ]
 PHASES = {"iter": 0, "final": 1, "init": 2, "ibp": 3, "backward": 4}
@@ -74,6 +75,7 @@ def load_library(path: str = LIB_PATH):
     lib.ld_net_reserve.argtypes = [vp, i32]
     lib.ld_net_sync_status.argtypes = [vp, vp]
     lib.ld_intermediate_bounds.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp]
+    lib.ld_intermediate_bounds_split.argtypes = [vp, vp, vp, i32, vp, vp, i32, vp, vp, vp]
     lib.ld_bound.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, i32, i32, C.POINTER(Opts), vp, vp, vp, vp, vp]
     lib.ld_dual_supergradient.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, i32, vp, vp, vp, vp, vp]
     lib.ld_bound_backward.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
@@ -260,6 +262,26 @@ def ld_intermediate_bounds(net: Net, lb0, ub0, want_output_lb: bool = False):
     _check(net._lib.ld_intermediate_bounds(net.handle, _ptr(lb0), _ptr(ub0), P, _ptr(lbk), _ptr(ubk), _ptr(out_lb),
                                            _stream()), "ld_intermediate_bounds")
     return (lbk, ubk, out_lb) if want_output_lb else (lbk, ubk)
+
+
+def ld_intermediate_bounds_split(net: Net, lb0, ub0, masks, prop=None):
+    """Interval bounds recomputed per subdomain after its splits: ([B, N],
+    [B, N]) float32, outward rounded and already clamped by the masks.
+    To bound with them, pass n_props = B: ld_bound(net, lb0[prop], ub0[prop],
+    lbk, ubk, prop=arange(B), masks=masks, ...)."""
+    lb0 = _dev(lb0, torch.float32)
+    ub0 = _dev(ub0, torch.float32)
+    if lb0.dim() == 1:
+        lb0, ub0 = lb0[None], ub0[None]
+    masks = _dev(masks, torch.int8)
+    B = masks.shape[0]
+    prop = None if prop is None else _dev(prop, torch.int32)
+    lbk = torch.empty((B, net.N), dtype=torch.float32, device="cuda")
+    ubk = torch.empty_like(lbk)
+    _check(net._lib.ld_intermediate_bounds_split(net.handle, _ptr(lb0), _ptr(ub0), lb0.shape[0], _ptr(prop),
+                                                 _ptr(masks), B, _ptr(lbk), _ptr(ubk), _stream()),
+           "ld_intermediate_bounds_split")
+    return lbk, ubk
 
 
 def _problem(lb0, ub0, lbk, ubk, prop, masks, B):

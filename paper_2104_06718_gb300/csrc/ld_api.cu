@@ -807,6 +807,34 @@ ld_status ld_intermediate_bounds(ld_net* net, const float* lb0, const float* ub0
   return last_error();
 }
 
+ld_status ld_intermediate_bounds_split(ld_net* net, const float* lb0, const float* ub0, int32_t n_props,
+                                       const int32_t* prop, const int8_t* masks, int32_t B, float* lbk, float* ubk,
+                                       void* stream) {
+  if (!net || !lb0 || !ub0 || !lbk || !ubk || n_props < 1 || B < 0) return LD_ERR_ARG;
+  if (B > 65535) return LD_ERR_UNSUPPORTED;
+  if (B == 0) return LD_OK;
+  cudaStream_t s = S(stream);
+  PhaseMark pm(net, LD_PHASE_IBP, s);
+  ld::IbpRows rows;
+  rows.in_row = prop;
+  rows.n_in_rows = n_props;
+  rows.mask = masks;
+  rows.mask_stride = (int)net->N;
+  if (!prop && n_props != 1) {
+    // without a property map every subdomain reads box 0: only valid for one property
+    return LD_ERR_ARG;
+  }
+  for (int k = 1; k < net->n; ++k) {
+    const LayerDev& L = layer(net, k);
+    const float* lin = k == 1 ? lb0 : lbk + r_off(net, k - 1);
+    const float* uin = k == 1 ? ub0 : ubk + r_off(net, k - 1);
+    const int in_stride = k == 1 ? (int)net->n0 : (int)net->N;
+    ld::launch_ibp_layer(L, k == 1, 0, B, lin, uin, in_stride, lbk + L.r_out_off, ubk + L.r_out_off, (int)net->N,
+                         nullptr, net->d_status, s, rows);
+  }
+  return last_error();
+}
+
 ld_status ld_bound(ld_net* net, const float* lb0, const float* ub0, const float* lbk, const float* ubk,
                    int32_t n_props, const int32_t* prop, const int8_t* masks, int32_t B, int32_t n_iters,
                    const ld_opts* opts, const float* rho_in, float* rho_out, float* adam_mv, double* out,

@@ -389,10 +389,18 @@ void launch_forward_record(const LayerDev& L, const Problem& P, const float* x, 
 // Feasibility pre-pass and box checks (ld_passes.cu).
 void launch_empty_flags(const Problem& P, int8_t* empty, int* status, cudaStream_t s);
 
-// IBP (ld_ibp.cu).
-void launch_ibp_layer(const LayerDev& L, int first, int last, int n_props, const float* lin, const float* uin,
+// IBP (ld_ibp.cu).  Rows are properties (root bounds: IbpRows{} ) or
+// subdomains: in_row maps a row to the box row the first layer reads, and
+// mask (row stride mask_stride, flat ReLU index) clamps every hidden layer.
+struct IbpRows {
+  const int32_t* in_row = nullptr;  // [rows] box row of each row's first layer (nullptr: box 0)
+  int n_in_rows = 0;                // boxes; 0: rows are the boxes themselves (root bounds)
+  const int8_t* mask = nullptr;     // [rows, mask_stride] or nullptr (no clamp)
+  int mask_stride = 0;
+};
+void launch_ibp_layer(const LayerDev& L, int first, int last, int n_rows, const float* lin, const float* uin,
                       int in_stride, float* lout, float* uout, int out_stride, double* out_lb, int* status,
-                      cudaStream_t s);
+                      cudaStream_t s, const IbpRows& rows = IbpRows{});
 
 // FP64 final bound (ld_final.cu).
 struct FinalAcc {

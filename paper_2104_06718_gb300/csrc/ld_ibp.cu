@@ -3,20 +3,29 @@
 // with [lo_0, hi_0] = the input box and [lo_k, hi_k] = [relu(l_hat_k), relu(u_hat_k)].
 // Every multiply-add is rounded outward (round-down for l_hat, round-up for
 // u_hat), so the FP32 results contain the exact interval bounds.
-// One launch per layer; one thread per (property, output neuron).
+// One launch per layer; one thread per (row, output neuron), a row being a
+// property (root bounds) or a subdomain (bounds recomputed after its splits:
+// the first layer reads the box of the subdomain's property, and the split
+// clamp of Sec. 2.3.2 is applied to every hidden layer's bounds before they
+// feed the next layer through [relu(l), relu(u)]).
 #include "ld_common.cuh"
 
 namespace ld {
 namespace {
 
-__global__ void ibp_kernel(LayerDev L, int first, int last, int n_props, const float* __restrict__ lin,
+__global__ void ibp_kernel(LayerDev L, int first, int last, int n_rows, const float* __restrict__ lin,
                            const float* __restrict__ uin, int in_stride, float* lout, float* uout,
-                           int out_stride, double* out_lb, int* status) {
-  const size_t total = (size_t)n_props * L.n_out;
+                           int out_stride, double* out_lb, int* status, IbpRows rows) {
+  const size_t total = (size_t)n_rows * L.n_out;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const int p = (int)(e / L.n_out), o = (int)(e % L.n_out);
-    const float* lp = lin + (size_t)p * in_stride;
-    const float* up = uin + (size_t)p * in_stride;
+    int src = p;  // input row (the first layer of a subdomain reads its property's box)
+    if (first && rows.n_in_rows > 0) {
+      src = rows.in_row ? rows.in_row[p] : 0;
+      src = src < 0 ? 0 : (src >= rows.n_in_rows ? rows.n_in_rows - 1 : src);
+    }
+    const float* lp = lin + (size_t)src * in_stride;
+    const float* up = uin + (size_t)src * in_stride;
     float lo, hi;
     if (L.kind == LD_LAYER_FC) {
       lo = L.b[o];
@@ -63,6 +72,11 @@ __global__ void ibp_kernel(LayerDev L, int first, int last, int n_props, const f
     if (last) {
       if (out_lb) out_lb[p] = (double)lo;
     } else {
+      if (rows.mask) {  // split clamp: +1 => l <- max(l,0); -1 => u <- min(u,0)
+        const int m = rows.mask[(size_t)p * rows.mask_stride + L.r_out_off + o];
+        if (m > 0) lo = fmaxf(lo, 0.f);
+        if (m < 0) hi = fminf(hi, 0.f);
+      }
       lout[(size_t)p * out_stride + o] = lo;
       uout[(size_t)p * out_stride + o] = hi;
     }
@@ -71,15 +85,15 @@ __global__ void ibp_kernel(LayerDev L, int first, int last, int n_props, const f
 
 }  // namespace
 
-void launch_ibp_layer(const LayerDev& L, int first, int last, int n_props, const float* lin, const float* uin,
+void launch_ibp_layer(const LayerDev& L, int first, int last, int n_rows, const float* lin, const float* uin,
                       int in_stride, float* lout, float* uout, int out_stride, double* out_lb, int* status,
-                      cudaStream_t s) {
-  const size_t total = (size_t)n_props * L.n_out;
+                      cudaStream_t s, const IbpRows& rows) {
+  const size_t total = (size_t)n_rows * L.n_out;
   int grid = (int)((total + 255) / 256);
   if (grid < 1) grid = 1;
   count_launch();
-  ibp_kernel<<<grid, 256, 0, s>>>(L, first, last, n_props, lin, uin, in_stride, lout, uout, out_stride, out_lb,
-                                  status);
+  ibp_kernel<<<grid, 256, 0, s>>>(L, first, last, n_rows, lin, uin, in_stride, lout, uout, out_stride, out_lb,
+                                  status, rows);
 }
 
 }  // namespace ld

@@ -83,6 +83,44 @@ def test_ibp_contains_oracle_bounds(name):
     assert np.array_equal(((gl < 0) & (gu > 0))[sure], ((fl < 0) & (fu > 0))[sure])
 
 
+@pytest.mark.parametrize("name", ["base", "deep"])
+def test_split_ibp_contains_oracle_bounds(name):
+    """Per-subdomain bounds recomputed after the splits: outward against the
+    oracle's FP64 recomputation and within 1e-4 of it; two properties."""
+    pb = conv_problem(name, 24, depth=(0, 8), block=4, props=(0, 1))
+    net = gpu_net(pb)
+    lbk, ubk = ldb.ld_intermediate_bounds_split(net, pb["l0"], pb["u0"], pb["masks"], prop=pb["prop"])
+    on = pb["net"]
+    ls, us, empty = oracle.ibp_bounds_split(on, pb["l0"].astype(np.float64), pb["u0"].astype(np.float64),
+                                            pb["masks"], pb["prop"])
+    fl, fu = flat(on, ls), flat(on, us)
+    gl, gu = lbk.cpu().numpy().astype(np.float64), ubk.cpu().numpy().astype(np.float64)
+    scale = np.maximum(np.abs(fl), np.abs(fu)) + 1.0
+    assert np.all(gl <= fl + 1e-12 * scale), "split IBP lower bound not outward"
+    assert np.all(gu >= fu - 1e-12 * scale), "split IBP upper bound not outward"
+    assert np.max((fl - gl) / scale) < 1e-4 and np.max((gu - fu) / scale) < 1e-4
+    # without masks every subdomain gets its property's root bounds
+    lb0, ub0 = ldb.ld_intermediate_bounds(net, pb["l0"], pb["u0"])
+    l2, u2 = ldb.ld_intermediate_bounds_split(net, pb["l0"], pb["u0"], np.zeros_like(pb["masks"]), prop=pb["prop"])
+    idx = torch.as_tensor(pb["prop"].astype(np.int64), device="cuda")
+    assert torch.equal(l2, lb0[idx]) and torch.equal(u2, ub0[idx])
+
+
+def test_bound_with_per_subdomain_bounds_matches_oracle():
+    """ld_bound on per-subdomain bounds (n_props = B, boxes gathered per
+    subdomain) against the oracle on the same bounds, after 3 iterations."""
+    pb = conv_problem("base", 16, depth=(0, 8), block=6)
+    on = pb["net"]
+    ls, us, empty = oracle.ibp_bounds_split(on, pb["l0"].astype(np.float64), pb["u0"].astype(np.float64),
+                                            pb["masks"], pb["prop"])
+    lbk, ubk = outward_f32(flat(on, ls), flat(on, us))
+    B = pb["B"]
+    q = dict(pb, l0=pb["l0"][pb["prop"]], u0=pb["u0"][pb["prop"]], lbk=lbk, ubk=ubk,
+             prop=np.arange(B, dtype=np.int32))
+    out, ref = run_both(q, 3, "auto")
+    assert np.max(rel(out, ref)) < 1e-5
+
+
 def test_nonfinite_box_sets_status(base16):
     pb = base16
     net = gpu_net(pb)

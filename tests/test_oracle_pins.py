@@ -92,6 +92,88 @@ def test_ibp_is_sound_on_samples():
         x = np.maximum(xh, 0)
 
 
+# ---------------------------------------------------------------- per-subdomain IBP after splits
+
+def test_split_ibp_hand_worked_chain():
+    """x0 in [-1, 1], x_hat_1 = x0, x_hat_2 = 2 relu(x_hat_1) + 1 (worked by hand).
+    Root IBP: x_hat_2 in [1, 3].  Split -1 on neuron 1 fixes relu(x_hat_1) = 0,
+    so the recomputed bound of x_hat_2 is [1, 1]; split +1 keeps x_hat_1 in
+    [0, 1] and x_hat_2 in [1, 3]."""
+    net = oracle.Net([oracle.Layer("fc", np.array([[1.0]]), np.zeros(1)),
+                      oracle.Layer("fc", np.array([[2.0]]), np.array([1.0])),
+                      oracle.Layer("fc", np.array([[1.0]]), np.zeros(1))])
+    l0, u0 = np.array([[-1.0]]), np.array([[1.0]])
+    masks = np.array([[0, 0], [-1, 0], [1, 0]], dtype=np.int8)
+    lb, ub, empty = oracle.ibp_bounds_split(net, l0, u0, masks)
+    np.testing.assert_array_equal(lb[1][:, 0], [-1.0, -1.0, 0.0])
+    np.testing.assert_array_equal(ub[1][:, 0], [1.0, 0.0, 1.0])
+    np.testing.assert_array_equal(lb[2][:, 0], [1.0, 1.0, 1.0])
+    np.testing.assert_array_equal(ub[2][:, 0], [3.0, 1.0, 3.0])
+    assert not empty.any()
+
+
+def _split_problem(i, B=24, depth=(0, 4)):
+    specs, net, l0, u0, lb, ub = tiny_problem(i)
+    Lr = np.concatenate([lb[k] for k in range(1, net.n)], axis=1)
+    Ur = np.concatenate([ub[k] for k in range(1, net.n)], axis=1)
+    amb = np.nonzero((Lr[0] < 0) & (Ur[0] > 0))[0]
+    masks = synth.split_masks(Lr.shape[1], B, amb, depth, block=40 + i)
+    return net, l0, u0, lb, ub, masks
+
+
+@pytest.mark.parametrize("i", range(3))
+def test_split_ibp_without_splits_is_root_ibp(i):
+    net, l0, u0, lb, ub, masks = _split_problem(i)
+    masks[:] = 0
+    ls, us, empty = oracle.ibp_bounds_split(net, l0, u0, masks)
+    for k in range(1, net.n):
+        np.testing.assert_allclose(ls[k], np.broadcast_to(lb[k], ls[k].shape), rtol=0, atol=1e-12)
+        np.testing.assert_allclose(us[k], np.broadcast_to(ub[k], us[k].shape), rtol=0, atol=1e-12)
+    assert not empty.any()
+
+
+@pytest.mark.parametrize("i", range(3))
+def test_split_ibp_is_tighter_than_root_clamp(i):
+    """IBP is monotone in its input intervals, so recomputing after the clamp
+    can only tighten the root bounds clamped by the same masks."""
+    net, l0, u0, lb, ub, masks = _split_problem(i)
+    ls, us, _ = oracle.ibp_bounds_split(net, l0, u0, masks)
+    lc, uc, _ = oracle.apply_masks(net, [None] + [np.broadcast_to(lb[k], ls[k].shape) for k in range(1, net.n)],
+                                   [None] + [np.broadcast_to(ub[k], us[k].shape) for k in range(1, net.n)], masks)
+    strict = False
+    for k in range(1, net.n):
+        assert np.all(ls[k] >= lc[k] - 1e-12) and np.all(us[k] <= uc[k] + 1e-12)
+        strict |= bool(np.any(ls[k] > lc[k] + 1e-9) or np.any(us[k] < uc[k] - 1e-9))
+    assert strict  # splits on layer 1 do tighten layer 2 here
+
+
+@pytest.mark.parametrize("i", range(3))
+def test_split_ibp_is_sound_on_samples(i):
+    """Every sampled input whose pre-activations satisfy a subdomain's splits
+    has pre-activations inside that subdomain's recomputed bounds."""
+    net, l0, u0, lb, ub, masks = _split_problem(i, B=8, depth=(1, 3))
+    offs = oracle.split_offsets(net)
+    xs = synth.random_box_points(l0[0], u0[0], 20000, seed=11 + i)
+    pre = []
+    x = xs
+    for k in range(1, net.n):
+        xh = net.L(k).forward(x)
+        pre.append(xh)
+        x = np.maximum(xh, 0)
+    flat = np.concatenate(pre, axis=1)
+    ls, us, _ = oracle.ibp_bounds_split(net, l0, u0, masks)
+    checked = 0
+    for b in range(masks.shape[0]):
+        m = masks[b]
+        ok = np.all((m <= 0) | (flat >= 0), axis=1) & np.all((m >= 0) | (flat <= 0), axis=1)
+        pts = flat[ok]
+        checked += len(pts)
+        for k in range(1, net.n):
+            seg = pts[:, offs[k - 1]:offs[k]]
+            assert np.all(seg >= ls[k][b] - 1e-9) and np.all(seg <= us[k][b] + 1e-9)
+    assert checked > 1000
+
+
 # ---------------------------------------------------------------- identities of the paper
 
 @pytest.mark.parametrize("i", range(4))

@@ -19,7 +19,7 @@
 // (L2-resident, batched 16-byte loads) and the read-only bounds and masks.
 //
 // The 4x4/stride-2 and 3x3/stride-1 convs (all the CIFAR nets) take blocked
-// paths: a thread computes 2 positions (x and x + half) x 4 channels with
+// paths: a thread computes 2 positions (rows y and y + h/2) x 4 channels with
 // compile-time taps, and the transposed conv is split by stride phase so that
 // every tap it visits is valid.  Other geometries take generic loops.
 #include <algorithm>
@@ -431,21 +431,25 @@ __device__ void ffc_finish(const Ctx<S, NT>& c, const LayerDev& L, const FusedLa
 
 // ------------------------------------------------------------------ blocked convs
 
-// Forward conv, blocked: item = (s, y, x0, group of GF output channels); the
-// thread computes positions x0 and x0 + wo/2.
+// Forward conv, blocked: item = (s, y0, x, group of GF output channels); the
+// thread computes rows y0 and y0 + ho/2 of column x.  Consecutive lanes take
+// consecutive columns of full rows, so the plane and epilogue accesses of a
+// warp fall in distinct shared-memory banks.
 template <int KH, int KW, int ST, int GF, int S, int NT>
 __device__ void conv_fwd_blocked(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, const FusedIter& it,
                                  const AdamStep& st) {
-  const int half = L.wo / 2, nog = L.cout / GF;
-  const int items = S * L.ho * half * nog;
+  const int hh = L.ho / 2, nog = L.cout / GF;
+  const int items = S * hh * L.wo * nog;
   const float* wf = c.sW + F.swf;
   const int hq = F.Hp >> 1, wq = F.Wp >> 1;
+  // offset of the second row's inputs: hh output rows down
+  const int dsec = ST == 2 ? hh * wq : hh * ST * F.Wp;
   for (int e = threadIdx.x; e < items; e += NT) {
     int r = e;
-    const int x0 = r % half;
-    r /= half;
-    const int y = r % L.ho;
-    r /= L.ho;
+    const int x0 = r % L.wo;
+    r /= L.wo;
+    const int y = r % hh;
+    r /= hh;
     const int og = r % nog;
     const int s = r / nog;
     float acc[2][GF];
@@ -479,7 +483,7 @@ __device__ void conv_fwd_blocked(const Ctx<S, NT>& c, const LayerDev& L, const F
           } else {
             a0i = (ch * F.Hp + y * ST + i) * F.Wp + x0 * ST + j;
           }
-          const float a0 = xs[a0i], a1 = xs[a0i + (ST == 2 ? half : half * ST)];
+          const float a0 = xs[a0i], a1 = xs[a0i + dsec];
 #pragma unroll
           for (int g = 0; g < GF; ++g) {
             acc[0][g] = fmaf(w[g], a0, acc[0][g]);
@@ -492,8 +496,8 @@ __device__ void conv_fwd_blocked(const Ctx<S, NT>& c, const LayerDev& L, const F
     for (int g = 0; g < GF; ++g)
 #pragma unroll
       for (int p = 0; p < 2; ++p) {
-        const int o = og * GF + g, x = x0 + p * half;
-        epi_f(c, L, s, (o * L.ho + y) * L.wo + x, o, rho_conv(F, o, y, x), acc[p][g], it, st);
+        const int o = og * GF + g, yy = y + p * hh;
+        epi_f(c, L, s, (o * L.ho + yy) * L.wo + x0, o, rho_conv(F, o, yy, x0), acc[p][g], it, st);
       }
   }
 }
@@ -502,18 +506,20 @@ __device__ void conv_fwd_blocked(const Ctx<S, NT>& c, const LayerDev& L, const F
 // stride phase: for rows yy = ry + ST*qy the valid taps are i = i0 + ST*a with
 // i0 = (ry + pad) mod ST, reading rho row y = qy + dy0 - a with
 // dy0 = (ry + pad - i0) / ST (likewise in x).  Item = (s, phase, qy, qx,
-// group of G input channels); the thread computes qx and qx + qw/2.
+// group of G input channels); the thread computes rows qy and qy + qh/2 of
+// column qx (consecutive lanes: consecutive columns of full rows).
 template <int KH, int KW, int ST, int G, int S, int NT>
 __device__ void conv_t_blocked(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, int k) {
-  const int qh = L.h / ST, qw = L.w / ST, half = qw / 2, ncg = L.cin / G;
-  const int items = S * ST * ST * ncg * qh * half;
+  const int qh = L.h / ST, qw = L.w / ST, hh = qh / 2, ncg = L.cin / G;
+  const int items = S * ST * ST * ncg * hh * qw;
   const float* wt = c.sW + F.swt;
+  const int dsec = hh * F.Wr;  // the second row's rho, hh rows down
   for (int e = threadIdx.x; e < items; e += NT) {
     int r = e;
-    const int qx = r % half;
-    r /= half;
-    const int qy = r % qh;
-    r /= qh;
+    const int qx = r % qw;
+    r /= qw;
+    const int qy = r % hh;
+    r /= hh;
     const int cg = r % ncg;
     r /= ncg;
     const int rx = r % ST;
@@ -537,7 +543,7 @@ __device__ void conv_t_blocked(const Ctx<S, NT>& c, const LayerDev& L, const Fus
       for (int a = 0; a < KH / ST; ++a)
 #pragma unroll
         for (int bb = 0; bb < KW / ST; ++bb) {
-          const float r0 = Ro[-a * F.Wr - bb], r1 = Ro[-a * F.Wr - bb + half];
+          const float r0 = Ro[-a * F.Wr - bb], r1 = Ro[-a * F.Wr - bb + dsec];
           const float* w = wo + ((i0 + ST * a) * KW + j0 + ST * bb) * L.cin;
           float wv[G];
           if (G == 4) {
@@ -558,13 +564,13 @@ __device__ void conv_t_blocked(const Ctx<S, NT>& c, const LayerDev& L, const Fus
         }
     }
     if (!active(c, s)) continue;
-    const int yy = ry + ST * qy;
+    const int xx = rx + ST * qx;
     const bool prev_fc = k >= 1 && c.net.L[k - 1].kind == LD_LAYER_FC;
 #pragma unroll
     for (int g = 0; g < G; ++g)
 #pragma unroll
       for (int p = 0; p < 2; ++p) {
-        const int xx = rx + ST * (qx + p * half);
+        const int yy = ry + ST * (qy + p * hh);
         const int ch = cg * G + g;
         const int i = (ch * L.h + yy) * L.w + xx;
         const int ri = k == 0 ? 0 : (prev_fc ? c.net.F[k - 1].roff + i : rho_conv(c.net.F[k - 1], ch, yy, xx));
@@ -636,11 +642,11 @@ __device__ void conv_t_generic(const Ctx<S, NT>& c, const LayerDev& L, const Fus
 template <int S, int NT>
 __device__ void forward_conv(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, const FusedIter& it,
                              const AdamStep& st) {
-  if (F.fmode == 1 && S * L.ho * (L.wo / 2) * (L.cout / 4) >= NT)
+  if (F.fmode == 1 && S * (L.ho / 2) * L.wo * (L.cout / 4) >= NT)
     conv_fwd_blocked<4, 4, 2, 4>(c, L, F, it, st);
   else if (F.fmode == 1)  // too few 4-channel items to fill the CTA
     conv_fwd_blocked<4, 4, 2, 2>(c, L, F, it, st);
-  else if (F.fmode == 2 && S * L.ho * (L.wo / 2) * (L.cout / 4) >= NT)
+  else if (F.fmode == 2 && S * (L.ho / 2) * L.wo * (L.cout / 4) >= NT)
     conv_fwd_blocked<3, 3, 1, 4>(c, L, F, it, st);
   else if (F.fmode == 2)
     conv_fwd_blocked<3, 3, 1, 2>(c, L, F, it, st);
@@ -861,9 +867,9 @@ FusedNet make_fused_net(const std::vector<LayerDev>& Ls) {
       woff += 2 * nw;
       xoff += round4(L.cin * F.Hp * F.Wp);
       const int geo = (L.kh == 4 && L.kw == 4 && L.stride == 2) ? 1 : (L.kh == 3 && L.kw == 3 && L.stride == 1) ? 2 : 0;
-      if (geo && L.cout % 4 == 0 && L.wo % 2 == 0 && (geo != 1 || F.poly)) F.fmode = geo;
+      if (geo && L.cout % 4 == 0 && L.ho % 2 == 0 && (geo != 1 || F.poly)) F.fmode = geo;
       if (geo && (L.cin % 4 == 0 || L.cin == 3) && L.h % L.stride == 0 && L.w % L.stride == 0 &&
-          (L.w / L.stride) % 2 == 0)
+          (L.h / L.stride) % 2 == 0)
         F.tmode = geo;
     }
     if (k < f.n - 1) {

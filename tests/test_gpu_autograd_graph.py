@@ -109,3 +109,76 @@ def test_bound_captures_in_a_cuda_graph():
     graph.replay()
     torch.cuda.synchronize()
     assert torch.equal(out, ref)
+
+
+def test_deep_128_backward_matches_finite_differences():
+    """Deep convnet, 128 subdomains: the Danskin gradients of the summed FP64
+    bound at a fixed rho (the autograd backward, recomputing the argmins)
+    against central differences of the bound, for conv and FC weights,
+    biases and the input box."""
+    pb = conv_problem("deep", 128, depth=(0, 8), block=24)
+    specs = pb["specs"]
+    net = ldb.Net(specs)
+    args = (pb["l0"], pb["u0"], pb["lbk"], pb["ubk"], pb["prop"], pb["masks"])
+    _, rho = ldb.ld_bound(net, *args, n_iters=40, return_rho=True)
+    # autograd over the weights and the box, at the rho of this run
+    params = _params(specs)
+    lb0 = torch.tensor(pb["l0"], device="cuda", requires_grad=True)
+    ub0 = torch.tensor(pb["u0"], device="cuda", requires_grad=True)
+    q0 = ldb.ld_bound(net, *args, n_iters=0, rho_in=rho).cpu().numpy()
+    fin = np.isfinite(q0)
+    g = ldb.ld_bound_backward(net, pb["l0"], pb["u0"], pb["lbk"], pb["ubk"], rho, prop=pb["prop"], masks=pb["masks"])
+    woff = np.cumsum([0] + [s.W.size for s in specs])
+    boff = np.cumsum([0] + [s.b.size for s in specs])
+
+    def q_sum(specs2=None, l0=None, u0=None):
+        n2 = net if specs2 is None else ldb.Net(specs2)
+        a = (pb["l0"] if l0 is None else l0, pb["u0"] if u0 is None else u0) + args[2:]
+        q = ldb.ld_bound(n2, *a, n_iters=0, rho_in=rho).cpu().numpy()
+        assert np.array_equal(np.isfinite(q), fin)
+        return q[fin].sum()
+
+    def copy_specs():
+        return [synth.LayerSpec(s.kind, s.W.copy(), s.b.copy(), s.in_shape, s.stride, s.pad) for s in specs]
+
+    h = 1e-3
+    checks = 0
+    # weights: conv 3->8 (k4s2), conv 8->8 (k3s1), FC 512->100; biases of the conv layers
+    for k, idx in [(0, (2, 1, 3, 0)), (2, (5, 7, 1, 2)), (4, (17, 300)), (1, None), (3, None)]:
+        what = "W" if idx is not None else "b"
+        vals = []
+        for sgn in (1, -1):
+            sp = copy_specs()
+            if what == "W":
+                sp[k].W[idx] += sgn * h
+            else:
+                sp[k].b[3] += sgn * h
+            vals.append(q_sum(sp))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        if what == "W":
+            ad = g["gW"][woff[k] + np.ravel_multi_index(idx, specs[k].W.shape)].item()
+        else:
+            ad = g["gb"][boff[k] + 3].item()
+        assert abs(fd - ad) < 1e-3 * max(1.0, abs(fd)), (k, what, fd, ad)
+        checks += 1
+    # the input box: pixels whose box argmin sits at the lower or the upper end
+    for j in (5, 1000, 2500):
+        for which in ("l0", "u0"):
+            vals = []
+            for sgn in (1, -1):
+                l0, u0 = pb["l0"].copy(), pb["u0"].copy()
+                (l0 if which == "l0" else u0)[:, j] += sgn * h
+                vals.append(q_sum(l0=l0, u0=u0))
+            fd = (vals[0] - vals[1]) / (2 * h)
+            ad = g["glb0" if which == "l0" else "gub0"][:, j].sum().item()
+            assert abs(fd - ad) < 1e-3 * max(1.0, abs(fd)), (which, j, fd, ad)
+            checks += 1
+    assert checks == 11
+    del q0
+    # the autograd Function gives the same gradients for the box and the weights
+    out = lda.bound(net, lb0, ub0, torch.tensor(pb["lbk"], device="cuda"), torch.tensor(pb["ubk"], device="cuda"),
+                    params, masks=pb["masks"], prop=pb["prop"], n_iters=40)
+    out[torch.isfinite(out)].sum().backward()
+    assert torch.allclose(lb0.grad, g["glb0"], rtol=1e-5, atol=1e-6)
+    assert torch.allclose(ub0.grad, g["gub0"], rtol=1e-5, atol=1e-6)
+    assert torch.allclose(params[2].grad.flatten(), g["gW"][woff[1]:woff[2]], rtol=1e-5, atol=1e-6)

@@ -456,11 +456,13 @@ ld_status run_iterations_bf16(ld_net* net, const Problem& P, const ld_opts& o, i
   return last_error();
 }
 
-// Engine and tile for this call.  LD_ENGINE_AUTO times a 4-iteration probe
-// of every candidate on the first call with a given B (on the call's own
-// inputs, before rho is initialised) and caches the fastest; while the
-// stream is being captured it falls back to a fixed rule.
-std::pair<int, int> choose_engine(ld_net* net, const Problem& P, const ld_opts& o, cudaStream_t s) {
+// Engine and tile for this call.  LD_ENGINE_AUTO times every candidate on
+// the first call with a given B (on the call's own inputs, before rho is
+// initialised): a 2- and a 6-iteration probe give its fixed cost per call
+// (the fused engine's state load and store) and its cost per iteration, and
+// the candidate with the least predicted time for this call's n_iters is
+// cached.  While the stream is being captured it falls back to a fixed rule.
+std::pair<int, int> choose_engine(ld_net* net, const Problem& P, const ld_opts& o, int n_iters, cudaStream_t s) {
   if (o.engine == LD_ENGINE_LAYERWISE) return {LD_ENGINE_LAYERWISE, 0};
   if (o.engine == LD_ENGINE_FUSED) {
     int S = o.tile;
@@ -478,7 +480,7 @@ std::pair<int, int> choose_engine(ld_net* net, const Problem& P, const ld_opts& 
   if (cap != cudaStreamCaptureStatusNone) {
     ld_opts f = o;
     f.engine = LD_ENGINE_FUSED;
-    return choose_engine(net, P, f, s);
+    return choose_engine(net, P, f, n_iters, s);
   }
   ld::launch_empty_flags(P, net->empty, net->d_status, s);
   std::vector<std::pair<int, int>> cands = {{LD_ENGINE_LAYERWISE, 0}};
@@ -493,20 +495,30 @@ std::pair<int, int> choose_engine(ld_net* net, const Problem& P, const ld_opts& 
   ld_opts probe = o;
   probe.t_offset = 0;
   probe.t_total = 100;
-  float best = 1e30f;
+  double best = 1e300;
   std::pair<int, int> choice = cands.back();
+  const double T = n_iters > 0 ? (double)n_iters : 1.0;
   for (const auto& c : cands) {
     cudaMemsetAsync(net->rho, 0, sizeof(float) * BN, s);
     cudaMemsetAsync(net->m, 0, sizeof(float) * BN, s);
     cudaMemsetAsync(net->v, 0, sizeof(float) * BN, s);
     run_iterations(net, P, probe, 1, c.first, c.second, s);  // warm-up
-    cudaEventRecord(e0, s);
-    ld_status st = run_iterations(net, P, probe, 4, c.first, c.second, s);
-    cudaEventRecord(e1, s);
-    cudaEventSynchronize(e1);
-    float ms = 0.f;
-    if (st == LD_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best) {
-      best = ms;
+    float ms[2] = {0.f, 0.f};
+    bool ok = true;
+    const int its[2] = {2, 6};
+    for (int r = 0; r < 2; ++r) {
+      cudaEventRecord(e0, s);
+      const ld_status st = run_iterations(net, P, probe, its[r], c.first, c.second, s);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      ok = ok && st == LD_OK && cudaEventElapsedTime(&ms[r], e0, e1) == cudaSuccess;
+    }
+    if (!ok) continue;
+    const double per_iter = std::max(0.0, (double)(ms[1] - ms[0]) / 4.0);
+    const double fixed = std::max(0.0, (double)ms[0] - 2.0 * per_iter);
+    const double predicted = fixed + T * per_iter;
+    if (predicted < best) {
+      best = predicted;
       choice = c;
     }
   }
@@ -854,7 +866,7 @@ ld_status ld_bound(ld_net* net, const float* lb0, const float* ub0, const float*
   const bool bf16 = o.precision == LD_PREC_BF16 && n_iters > 0;
   if (bf16 && (st = ensure_tc(net, B, n_props)) != LD_OK) return st;
   const std::pair<int, int> eng =
-      (n_iters > 0 && !bf16) ? choose_engine(net, P, o, s) : std::make_pair((int)LD_ENGINE_LAYERWISE, 0);
+      (n_iters > 0 && !bf16) ? choose_engine(net, P, o, n_iters, s) : std::make_pair((int)LD_ENGINE_LAYERWISE, 0);
   // The CROWN start must come from the same transposed-pass arithmetic as the
   // iterations (its exact ties would otherwise be broken by rounding): the
   // fused engine computes it in-kernel, the layerwise engine with its kernels.

@@ -229,10 +229,10 @@ __device__ __forceinline__ void tfc_rows(const Ctx<S, NT>& c, const LayerDev& L,
 #pragma unroll
         for (int s = 0; s < S; ++s) {
           const float r = c.rho(s)[F.roff + o0 + u];
-          acc[s].x = fmaf(wv[u].x, r, acc[s].x);
-          acc[s].y = fmaf(wv[u].y, r, acc[s].y);
-          acc[s].z = fmaf(wv[u].z, r, acc[s].z);
-          acc[s].w = fmaf(wv[u].w, r, acc[s].w);
+          const float2 rp = make_float2(r, r);
+          const float2 lo = __ffma2_rn(make_float2(wv[u].x, wv[u].y), rp, make_float2(acc[s].x, acc[s].y));
+          const float2 hi = __ffma2_rn(make_float2(wv[u].z, wv[u].w), rp, make_float2(acc[s].z, acc[s].w));
+          acc[s] = make_float4(lo.x, lo.y, hi.x, hi.y);
         }
       }
     }
@@ -452,11 +452,13 @@ __device__ void conv_fwd_blocked(const Ctx<S, NT>& c, const LayerDev& L, const F
     r /= hh;
     const int og = r % nog;
     const int s = r / nog;
-    float acc[2][GF];
+    // accumulators of channel pairs (g, g+1) as float2: one packed FMA
+    // (__ffma2_rn, two round-to-nearest FMAs) updates both channels
+    float2 acc2[2][GF / 2];
 #pragma unroll
     for (int p = 0; p < 2; ++p)
 #pragma unroll
-      for (int g = 0; g < GF; ++g) acc[p][g] = 0.f;
+      for (int h = 0; h < GF / 2; ++h) acc2[p][h] = make_float2(0.f, 0.f);
     const float* xs = c.xp(s) + F.xoff;
     const float* wg = wf + og * GF;
     for (int ch = 0; ch < L.cin; ++ch) {
@@ -465,17 +467,13 @@ __device__ void conv_fwd_blocked(const Ctx<S, NT>& c, const LayerDev& L, const F
       for (int i = 0; i < KH; ++i)
 #pragma unroll
         for (int j = 0; j < KW; ++j) {
-          float w[GF];
+          float2 w[GF / 2];
           if (GF == 4) {
             const float4 w4 = *reinterpret_cast<const float4*>(wc + (i * KW + j) * L.cout);
-            w[0] = w4.x;
-            w[1 % GF] = w4.y;
-            w[2 % GF] = w4.z;
-            w[3 % GF] = w4.w;
+            w[0] = make_float2(w4.x, w4.y);
+            w[1 % (GF / 2)] = make_float2(w4.z, w4.w);
           } else {
-            const float2 w2 = *reinterpret_cast<const float2*>(wc + (i * KW + j) * L.cout);
-            w[0] = w2.x;
-            w[1 % GF] = w2.y;
+            w[0] = *reinterpret_cast<const float2*>(wc + (i * KW + j) * L.cout);
           }
           int a0i;
           if (ST == 2) {  // stride-phase layout: phase (i&1, j&1), sub-position (y + i/2, x + j/2)
@@ -484,10 +482,11 @@ __device__ void conv_fwd_blocked(const Ctx<S, NT>& c, const LayerDev& L, const F
             a0i = (ch * F.Hp + y * ST + i) * F.Wp + x0 * ST + j;
           }
           const float a0 = xs[a0i], a1 = xs[a0i + dsec];
+          const float2 a0p = make_float2(a0, a0), a1p = make_float2(a1, a1);
 #pragma unroll
-          for (int g = 0; g < GF; ++g) {
-            acc[0][g] = fmaf(w[g], a0, acc[0][g]);
-            acc[1][g] = fmaf(w[g], a1, acc[1][g]);
+          for (int h = 0; h < GF / 2; ++h) {
+            acc2[0][h] = __ffma2_rn(w[h], a0p, acc2[0][h]);
+            acc2[1][h] = __ffma2_rn(w[h], a1p, acc2[1][h]);
           }
         }
     }
@@ -497,7 +496,8 @@ __device__ void conv_fwd_blocked(const Ctx<S, NT>& c, const LayerDev& L, const F
 #pragma unroll
       for (int p = 0; p < 2; ++p) {
         const int o = og * GF + g, yy = y + p * hh;
-        epi_f(c, L, s, (o * L.ho + yy) * L.wo + x0, o, rho_conv(F, o, yy, x0), acc[p][g], it, st);
+        const float a = (g & 1) ? acc2[p][g >> 1].y : acc2[p][g >> 1].x;
+        epi_f(c, L, s, (o * L.ho + yy) * L.wo + x0, o, rho_conv(F, o, yy, x0), a, it, st);
       }
   }
 }
@@ -528,11 +528,17 @@ __device__ void conv_t_blocked(const Ctx<S, NT>& c, const LayerDev& L, const Fus
     const int s = r / ST;
     const int i0 = (ry + L.pad) % ST, j0 = (rx + L.pad) % ST;
     const int dy0 = (ry + L.pad - i0) / ST, dx0 = (rx + L.pad - j0) / ST;
+    // G == 4: channel pairs as float2 (packed FMA); G == 3: scalar
+    constexpr int G2 = G == 4 ? 2 : 1;
+    float2 acc2[2][G2];
     float acc[2][G];
 #pragma unroll
-    for (int p = 0; p < 2; ++p)
+    for (int p = 0; p < 2; ++p) {
+#pragma unroll
+      for (int h = 0; h < G2; ++h) acc2[p][h] = make_float2(0.f, 0.f);
 #pragma unroll
       for (int g = 0; g < G; ++g) acc[p][g] = 0.f;
+    }
     const float* Rs = c.rho(s) + F.roff + (qy + dy0 + F.rhl) * F.Wr + qx + dx0 + F.rwl;
     const float* wg = wt + cg * G;
 #pragma unroll 2
@@ -545,21 +551,20 @@ __device__ void conv_t_blocked(const Ctx<S, NT>& c, const LayerDev& L, const Fus
         for (int bb = 0; bb < KW / ST; ++bb) {
           const float r0 = Ro[-a * F.Wr - bb], r1 = Ro[-a * F.Wr - bb + dsec];
           const float* w = wo + ((i0 + ST * a) * KW + j0 + ST * bb) * L.cin;
-          float wv[G];
           if (G == 4) {
             const float4 w4 = *reinterpret_cast<const float4*>(w);
-            wv[0] = w4.x;
-            wv[1 % G] = w4.y;
-            wv[2 % G] = w4.z;
-            wv[3 % G] = w4.w;
+            const float2 wl = make_float2(w4.x, w4.y), wh = make_float2(w4.z, w4.w);
+            const float2 r0p = make_float2(r0, r0), r1p = make_float2(r1, r1);
+            acc2[0][0] = __ffma2_rn(wl, r0p, acc2[0][0]);
+            acc2[0][G2 - 1] = __ffma2_rn(wh, r0p, acc2[0][G2 - 1]);
+            acc2[1][0] = __ffma2_rn(wl, r1p, acc2[1][0]);
+            acc2[1][G2 - 1] = __ffma2_rn(wh, r1p, acc2[1][G2 - 1]);
           } else {
 #pragma unroll
-            for (int g = 0; g < G; ++g) wv[g] = w[g];
-          }
-#pragma unroll
-          for (int g = 0; g < G; ++g) {
-            acc[0][g] = fmaf(wv[g], r0, acc[0][g]);
-            acc[1][g] = fmaf(wv[g], r1, acc[1][g]);
+            for (int g = 0; g < G; ++g) {
+              acc[0][g] = fmaf(w[g], r0, acc[0][g]);
+              acc[1][g] = fmaf(w[g], r1, acc[1][g]);
+            }
           }
         }
     }
@@ -574,7 +579,8 @@ __device__ void conv_t_blocked(const Ctx<S, NT>& c, const LayerDev& L, const Fus
         const int ch = cg * G + g;
         const int i = (ch * L.h + yy) * L.w + xx;
         const int ri = k == 0 ? 0 : (prev_fc ? c.net.F[k - 1].roff + i : rho_conv(c.net.F[k - 1], ch, yy, xx));
-        epi_t(c, k, s, i, xp_conv(L, F, ch, yy, xx), ri, acc[p][g]);
+        const float a = G == 4 ? ((g & 1) ? acc2[p][(g >> 1) % G2].y : acc2[p][(g >> 1) % G2].x) : acc[p][g];
+        epi_t(c, k, s, i, xp_conv(L, F, ch, yy, xx), ri, a);
       }
   }
 }

@@ -185,6 +185,14 @@ def macs_per_pass(specs):
     return total
 
 
+def workload_config(wl, N, B, T, world):
+    """The `config` object of the bench line (both arms)."""
+    return {"workload": f"{wl['net']} convnet ({N} ReLUs), {B} subdomains/GPU, split depth "
+                        f"{wl['depth'][0]}-{wl['depth'][1]}, T={T} Adam iterations, CROWN init, FP64 final "
+                        f"bound, Danskin backward",
+            "subdomains_per_gpu": B, "iterations": T, "parallelism": f"replicas x{world}"}
+
+
 def make_workload(name, rank):
     from paper_2104_06718_gb300 import synth
     net_name, B, T, depth, eps = WORKLOADS[name]
@@ -266,8 +274,10 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "bounds/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / max(len(times), 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{wl['net']} convnet, {wl['B']} subdomains, T={wl['T']} (oracle sample of {S} per step)",
-                       "subdomains_per_step": S, "iterations": wl["T"]},
+            "config": {**workload_config(wl, lbk.shape[1], wl["B"], wl["T"], args.gpus),
+                       "precision": "fp64 oracle (iterations and final bound)",
+                       "oracle_sample": f"first {S} of {wl['B']} subdomains per step (the bound only: no IBP or "
+                                        "backward in the timed region)"},
             "cpu_baseline": {"value": value, "unit": "bounds/s", "cores": os.cpu_count(), "kind": "oracle",
                              "sample": f"first {S} of {wl['B']} subdomains per step, T={wl['T']}, FP64 NumPy/SciPy"},
             "e2e": {"value": value, "unit": "bounds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -487,13 +497,10 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": 1000 * t_all / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if args.precision == "bf16" else "f32",
         "data": "synthetic",
-        "config": {"workload": f"{wl['net']} convnet ({net.N} ReLUs), {B} subdomains/GPU, split depth "
-                               f"{wl['depth'][0]}-{wl['depth'][1]}, T={T} Adam iterations, CROWN init, FP64 final "
-                               f"bound, Danskin backward",
-                   "subdomains_per_gpu": B, "iterations": T,
+        "config": {**workload_config(wl, net.N, B, T, world),
                    "precision": ("bf16 GEMM operands, fp32 accumulation and dual state" if args.precision == "bf16"
                                  else "fp32") + " iterations, fp64 final",
-                   "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
+                   "l2": "flushed between steps (512 MB write)"},
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": "bounds/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),

@@ -192,9 +192,10 @@ ld_status ld_intermediate_bounds_split(ld_net* net, const float* lb0, const floa
  *   out [device] [B] double: q(rho_T) evaluated in FP64 and lowered by an
  *   a-priori rounding-error bound (opts->fp64_final = 1), a valid lower
  *   bound of min x_hat_n over the subdomain (weak duality, Sec. 3.1).
- *   n_iters = 0 evaluates q at the initial rho.
+ *   n_iters = 0 evaluates q at the initial rho.  B = 0 does nothing and
+ *   returns LD_OK (the per-subdomain arrays may then be NULL).
  * Errors: LD_ERR_ARG (nulls, B < 0, n_iters < 0, n_props < 1, options out of
- * range), LD_ERR_UNSUPPORTED (precision not built), LD_ERR_NOMEM. */
+ * range), LD_ERR_UNSUPPORTED (precision not built, B > 65535), LD_ERR_NOMEM. */
 ld_status ld_bound(ld_net* net, const float* lb0, const float* ub0, const float* lbk,
                    const float* ubk, int32_t n_props, const int32_t* prop_of_subdomain,
                    const int8_t* split_masks, int32_t B, int32_t n_iters, const ld_opts* opts,

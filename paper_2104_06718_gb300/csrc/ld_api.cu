@@ -822,7 +822,7 @@ ld_status ld_intermediate_bounds(ld_net* net, const float* lb0, const float* ub0
 ld_status ld_intermediate_bounds_split(ld_net* net, const float* lb0, const float* ub0, int32_t n_props,
                                        const int32_t* prop, const int8_t* masks, int32_t B, float* lbk, float* ubk,
                                        void* stream) {
-  if (!net || !lb0 || !ub0 || !lbk || !ubk || n_props < 1 || B < 0) return LD_ERR_ARG;
+  if (!net || !lb0 || !ub0 || n_props < 1 || B < 0 || (B > 0 && (!lbk || !ubk))) return LD_ERR_ARG;
   if (B > 65535) return LD_ERR_UNSUPPORTED;
   if (B == 0) return LD_OK;
   cudaStream_t s = S(stream);
@@ -853,11 +853,11 @@ ld_status ld_bound(ld_net* net, const float* lb0, const float* ub0, const float*
                    void* stream) {
   ld_status st = check_problem(net, lb0, ub0, lbk, ubk, n_props, B);
   if (st != LD_OK) return st;
-  if (n_iters < 0 || !out) return LD_ERR_ARG;
+  if (n_iters < 0 || (!out && B > 0)) return LD_ERR_ARG;
   ld_opts o;
   if (opts) o = *opts; else ld_opts_default(&o);
   if ((st = check_opts(o)) != LD_OK) return st;
-  if (o.init == LD_INIT_GIVEN && !rho_in) return LD_ERR_ARG;
+  if (o.init == LD_INIT_GIVEN && !rho_in && B > 0) return LD_ERR_ARG;
   if (B == 0) return LD_OK;
   if ((st = ensure_ws(net, B)) != LD_OK) return st;
   cudaStream_t s = S(stream);

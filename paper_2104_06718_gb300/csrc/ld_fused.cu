@@ -3,11 +3,13 @@
 // Subdomains are independent, so each CTA owns S of them for the entire run
 // and never waits on another CTA.
 //
-// Per iteration the CTA walks the layer pairs top-down (k = n-1 .. 0):
+// Per iteration, for every layer pair (k = n-1 .. 0):
 //   transposed pass  g_k = W_{k+1}^T rho_{k+1} -> inner minimisation of layer k
 //                    (Eq. min-pk; Eq. box_bounds_sol for k = 0) -> x_k, x_hat_B,k
 //   forward pass     x_hat_A,k+1 = W_{k+1} x_k + b_{k+1} -> supergradient
 //                    x_hat_B,k+1 - x_hat_A,k+1 and the Adam step on rho_{k+1}
+// in two phases: all transposed passes (they read only the previous
+// iteration's rho), then all forward passes (see the kernel's loop).
 // Everything a subdomain owns lives in shared memory for the whole run:
 //   x_k      one zero-padded plane per layer input (stride-2 conv inputs stored
 //            by stride phase so that the conv reads consecutive addresses)
@@ -76,18 +78,16 @@ __device__ __forceinline__ int rho_flat(const LayerDev& L, const FusedLayer& F, 
   return rho_conv(F, o, r / L.wo, r % L.wo);
 }
 
-// Transposed-pass epilogue for neuron i of layer k (g = g_k[i]).  xi: where
-// x_k goes in the input plane of layer k+1; ri: where rho_k sits (k >= 1).
+// Transposed-pass epilogue for neuron i of layer k >= 1 (g = g_k[i]) with
+// the clamped bounds (l, u) of the neuron.  xi: where x_k goes in the input
+// plane of layer k+1; ri: where rho_k sits.
 template <int S, int NT>
-__device__ __forceinline__ void epi_t(const Ctx<S, NT>& c, int k, int s, int i, int xi, int ri, float g) {
-  const int b = c.b0 + s;
+__device__ __forceinline__ void epi_t_lu(const Ctx<S, NT>& c, int k, int s, int i, int xi, int ri, float g, float l,
+                                         float u) {
   if (c.crown) {
     // dual initialisation (Prop. 3, Eq. salman-assignment): rho_k = a_bar [g]_+ + a_low [g]_-,
     // computed by the same transposed pass the iterations use, so that the
     // exact ties it creates (rho_k = g_k for passing ReLUs) survive rounding
-    const int j = c.net.L[k - 1].r_out_off + i;
-    float l, u;
-    clamped_bounds(c.P, b, j, l, u);
     float a_up, a_lo;
     if (u <= 0.f) {
       a_up = 0.f;
@@ -102,15 +102,7 @@ __device__ __forceinline__ void epi_t(const Ctx<S, NT>& c, int k, int s, int i, 
     c.rho(s)[ri] = a_up * fmaxf(g, 0.f) + a_lo * fminf(g, 0.f);
     return;
   }
-  if (k == 0) {
-    // P0 (Eq. box_bounds_sol): minimise -g_0^T x0, i.e. x0 = u0 where g_0 >= 0
-    const int p = prop_of(c.P, b);
-    c.xp(s)[xi] = (g >= 0.f) ? c.P.u0[(size_t)p * c.P.n0 + i] : c.P.l0[(size_t)p * c.P.n0 + i];
-    return;
-  }
   const int j = c.net.L[k - 1].r_out_off + i;
-  float l, u;
-  clamped_bounds(c.P, b, j, l, u);
   const float r = c.rho(s)[ri];
   float xb, xv;
   int code;
@@ -119,33 +111,20 @@ __device__ __forceinline__ void epi_t(const Ctx<S, NT>& c, int k, int s, int i, 
   c.xb(s)[j] = xb;
 }
 
-// epi_t for a layer k >= 1 whose clamped bounds (l, u) of neuron i were
-// loaded beforehand.
+// Transposed-pass epilogue for neuron i of layer k (bounds loaded here; for
+// k = 0 the box argmin of P0).
 template <int S, int NT>
-__device__ __forceinline__ void epi_t_lu(const Ctx<S, NT>& c, int k, int s, int i, int xi, int ri, float g, float l,
-                                         float u) {
-  if (c.crown) {
-    float a_up, a_lo;
-    if (u <= 0.f) {
-      a_up = 0.f;
-      a_lo = 0.f;
-    } else if (l >= 0.f) {
-      a_up = 1.f;
-      a_lo = 1.f;
-    } else {
-      a_up = u / (u - l);
-      a_lo = (u >= -l) ? 1.f : 0.f;
-    }
-    c.rho(s)[ri] = a_up * fmaxf(g, 0.f) + a_lo * fminf(g, 0.f);
+__device__ __forceinline__ void epi_t(const Ctx<S, NT>& c, int k, int s, int i, int xi, int ri, float g) {
+  const int b = c.b0 + s;
+  if (k == 0) {
+    // P0 (Eq. box_bounds_sol): minimise -g_0^T x0, i.e. x0 = u0 where g_0 >= 0
+    const int p = prop_of(c.P, b);
+    c.xp(s)[xi] = (g >= 0.f) ? c.P.u0[(size_t)p * c.P.n0 + i] : c.P.l0[(size_t)p * c.P.n0 + i];
     return;
   }
-  const int j = c.net.L[k - 1].r_out_off + i;
-  const float r = c.rho(s)[ri];
-  float xb, xv;
-  int code;
-  relu_argmin<float>(r, g, l, u, xb, xv, code);
-  c.xp(s)[xi] = xv;
-  c.xb(s)[j] = xb;
+  float l, u;
+  clamped_bounds(c.P, b, c.net.L[k - 1].r_out_off + i, l, u);
+  epi_t_lu(c, k, s, i, xi, ri, g, l, u);
 }
 
 // Forward-pass epilogue: supergradient and Adam step on neuron jj (output
@@ -355,7 +334,7 @@ __device__ void ffc_main(const Ctx<S, NT>& c, const LayerDev& L, const FusedLaye
   const float* __restrict__ W = L.W;
   const int npair = (L.n_out + 1) / 2;
   for (int jp = warp; jp < npair; jp += nwarp) {
-    // CTA-dependent rotation of the rows (as in transposed_fc)
+    // CTA-dependent rotation of the rows (as in tfc_rows)
     const int j0 = 2 * ((jp + (int)blockIdx.x) % npair);
     const bool two = j0 + 1 < L.n_out;
     float acc[2][S];

@@ -20,7 +20,7 @@
 namespace ld {
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+constexpr int BN = 64, BK = 16, NT = 256;
 constexpr double U52 = 2.220446049250313e-16;  // 2^-52
 
 // Value and error bound of one per-neuron minimum.  box: P0 term with
@@ -78,57 +78,75 @@ __device__ __forceinline__ void acc_add(FinalAcc a, int slot, int b, double t, d
 }
 
 // FP64 transposed FC pass (A = rho_{k+1} [B, n_out], W [n_out, n_in]).
+// Tile: BM = 16 TM subdomains x BN = 64 columns (TM = 4, or 1 when the
+// 64-row grid would leave SMs idle; the column blocks, and so the partial-sum
+// slots, are the same either way).  The operands are converted to double once
+// when a tile is staged (the FP64 pipe is GB300's scarce unit), and their
+// magnitudes kept as floats for the FP32 round-up sum of |W||rho|.
+template <int TM>
 __global__ void __launch_bounds__(NT) final_fc_kernel(int M, int Ncol, int K, const float* __restrict__ A, int lda,
                                                       const float* __restrict__ W, int ldw, FinalEpi epi,
                                                       FinalAcc acc_out) {
-  __shared__ float As[BK][BM + 4];
-  __shared__ float Bs[BK][BN + 4];
+  constexpr int BMt = 16 * TM;
+  __shared__ double As[BK][BMt + 1];
+  __shared__ double Bs[BK][BN + 1];
+  __shared__ float Aa[BK][BMt + 4];
+  __shared__ float Ba[BK][BN + 4];
   const int t = threadIdx.x, tx = t % 16, ty = t / 16;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  double acc[4][4];
-  float aab[4][4];
+  const int m0 = blockIdx.y * BMt, n0 = blockIdx.x * BN;
+  double acc[TM][4];
+  float aab[TM][4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       acc[i][j] = 0.0;
       aab[i][j] = 0.f;
     }
   for (int k0 = 0; k0 < K; k0 += BK) {
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int idx = t + e * NT;
+    for (int idx = t; idx < BMt * BK; idx += NT) {
       const int mm = idx / BK, kk = idx % BK;
       const int gm = m0 + mm, gk = k0 + kk;
-      As[kk][mm] = (gm < M && gk < K) ? A[(size_t)gm * lda + gk] : 0.f;
+      const float v = (gm < M && gk < K) ? A[(size_t)gm * lda + gk] : 0.f;
+      As[kk][mm] = (double)v;
+      Aa[kk][mm] = fabsf(v);
     }
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const int idx = t + e * NT;
       const int kk = idx / BN, nn = idx % BN;
       const int gk = k0 + kk, gn = n0 + nn;
-      Bs[kk][nn] = (gk < K && gn < Ncol) ? W[(size_t)gk * ldw + gn] : 0.f;
+      const float v = (gk < K && gn < Ncol) ? W[(size_t)gk * ldw + gn] : 0.f;
+      Bs[kk][nn] = (double)v;
+      Ba[kk][nn] = fabsf(v);
     }
     __syncthreads();
 #pragma unroll 4
     for (int kk = 0; kk < BK; ++kk) {
-      float a[4], bb[4];
+      double a[TM], bb[4];
+      float aa[TM], ba[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < TM; ++i) {
+        a[i] = As[kk][ty + 16 * i];
+        aa[i] = Aa[kk][ty + 16 * i];
+      }
 #pragma unroll
-      for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < 4; ++j) {
+        bb[j] = Bs[kk][tx + 16 * j];
+        ba[j] = Ba[kk][tx + 16 * j];
+      }
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          acc[i][j] = fma((double)a[i], (double)bb[j], acc[i][j]);
-          aab[i][j] = __fmaf_ru(fabsf(a[i]), fabsf(bb[j]), aab[i][j]);
+          acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+          aab[i][j] = __fmaf_ru(aa[i], ba[j], aab[i][j]);
         }
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < TM; ++i) {
     const int m = m0 + ty + 16 * i;
     double st = 0.0, se = 0.0, sa = 0.0;
     if (m < M) {
@@ -226,24 +244,33 @@ __global__ void __launch_bounds__(NT) final_conv_kernel(LayerDev L, const float*
 // FP64 transposed conv by stride phase (k4 s2 / k3 s1), G input channels per
 // thread: g[b, c, yy, xx] = sum over the phase's taps (i, j) and o of
 // W[o, c, i, j] rho[b, o, y, x].  Weights sit in shared memory as doubles and
-// their magnitudes as floats, [o][i][j][c], so one rho load (one conversion)
-// feeds G FP64 FMAs.  Same terms and error bounds as final_conv_kernel; the
+// their magnitudes as floats, [o][i][j][c], and so does the subdomain's
+// rho_{k+1} (converted once per block), so one rho load feeds G FP64 FMAs.  Same terms and error bounds as final_conv_kernel; the
 // slots are this grid's blocks.
 template <int KH, int KW, int ST, int G>
 __global__ void __launch_bounds__(NT) final_conv_fast_kernel(LayerDev L, const float* __restrict__ r, int rs,
                                                              FinalEpi epi, FinalAcc acc_out) {
   extern __shared__ double sWd[];
   const int nw = L.cout * L.cin * KH * KW;
-  float* sWa = reinterpret_cast<float*>(sWd + nw);
+  const int hw_o = L.ho * L.wo, slab = L.cout * hw_o;
+  // the subdomain's rho_{k+1} as doubles (converted once) and its magnitudes
+  double* sR = sWd + nw;
+  float* sWa = reinterpret_cast<float*>(sR + slab);
+  float* sRa = sWa + nw;
+  const int b = blockIdx.y;
+  const float* rb = r + (size_t)b * rs;
   for (int e = threadIdx.x; e < nw; e += NT) {
     const float w = L.Wt[e];
     sWd[e] = (double)w;
     sWa[e] = fabsf(w);
   }
+  for (int e = threadIdx.x; e < slab; e += NT) {
+    const float v = __ldg(rb + e);
+    sR[e] = (double)v;
+    sRa[e] = fabsf(v);
+  }
   __syncthreads();
-  const int b = blockIdx.y;
-  const float* rb = r + (size_t)b * rs;
-  const int qh = L.h / ST, qw = L.w / ST, ncg = L.cin / G, hw_o = L.ho * L.wo;
+  const int qh = L.h / ST, qw = L.w / ST, ncg = L.cin / G;
   const int items = ST * ST * ncg * qh * qw;
   double st = 0.0, se = 0.0, sa = 0.0;
   for (int e = blockIdx.x * NT + threadIdx.x; e < items; e += gridDim.x * NT) {
@@ -273,12 +300,11 @@ __global__ void __launch_bounds__(NT) final_conv_fast_kernel(LayerDev L, const f
       for (int bb = 0; bb < KW / ST; ++bb) {
         const int x = qx + dx0 - bb;
         if (x < 0 || x >= L.wo) continue;
-        const float* rp = rb + y * L.wo + x;
+        const int rp = y * L.wo + x;
         const int wo0 = ((i0 + ST * a) * KW + j0 + ST * bb) * L.cin + cg * G;
         for (int o = 0; o < L.cout; ++o) {
-          const float rv = __ldg(rp + (size_t)o * hw_o);
-          const double rd = (double)rv;
-          const float ra = fabsf(rv);
+          const double rd = sR[rp + o * hw_o];
+          const float ra = sRa[rp + o * hw_o];
           const double* wd = sWd + wo0 + o * KH * KW * L.cin;
           const float* wa = sWa + wo0 + o * KH * KW * L.cin;
 #pragma unroll
@@ -302,6 +328,12 @@ __global__ void __launch_bounds__(NT) final_conv_fast_kernel(LayerDev L, const f
   block_reduce_add(acc_out, acc_out.slot + blockIdx.x, b, st, se, sa);
 }
 
+// Shared memory of the phase-split FP64 transposed conv: weights and the
+// rho slab, each as double + float magnitude.
+size_t final_fast_smem(const LayerDev& L) {
+  return (size_t)L.cout * L.cin * L.kh * L.kw * 12 + (size_t)L.cout * L.ho * L.wo * 12;
+}
+
 // Geometry and channel blocking of the phase-split FP64 transposed conv, or 0.
 int final_fast_geo(const LayerDev& L, int& G) {
   G = 0;
@@ -313,8 +345,7 @@ int final_fast_geo(const LayerDev& L, int& G) {
   if (L.cin % 4 == 0) G = 4;
   else if (L.cin == 3) G = 3;
   else return 0;
-  const size_t smem = (size_t)L.cout * L.cin * L.kh * L.kw * 12;  // double + float per weight
-  if (smem > 96 * 1024) return 0;
+  if (final_fast_smem(L) > 200 * 1024) return 0;
   return geo;
 }
 
@@ -394,13 +425,24 @@ static double gamma_of(double K) {
 template <int KH, int KW, int ST, int G>
 void launch_fast(dim3 grid, size_t smem, const LayerDev& L, const float* r, int rs, FinalEpi epi, FinalAcc acc,
                  cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
+  static size_t attr = 0;  // dynamic shared memory opted in for this instantiation
+  if (smem > attr) {
     cudaFuncSetAttribute(final_conv_fast_kernel<KH, KW, ST, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         96 * 1024);
-    attr = true;
+                         (int)smem);
+    attr = smem;
   }
   final_conv_fast_kernel<KH, KW, ST, G><<<grid, NT, smem, s>>>(L, r, rs, epi, acc);
+}
+
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
 }
 
 void launch_final_layer(const LayerDev& Lnext, int layer, int r_off, int x_off, const Problem& P,
@@ -415,14 +457,20 @@ void launch_final_layer(const LayerDev& Lnext, int layer, int r_off, int x_off, 
   }
   const float* r = rho + Lnext.r_out_off;
   if (Lnext.kind == LD_LAYER_FC) {
-    dim3 grid((Lnext.n_in + BN - 1) / BN, (P.B + BM - 1) / BM);
-    final_fc_kernel<<<grid, NT, 0, s>>>(P.B, Lnext.n_in, Lnext.n_out, r, P.N, Lnext.W, Lnext.n_in, epi, acc);
+    const int nb = (Lnext.n_in + BN - 1) / BN;
+    if (nb * ((P.B + 63) / 64) >= 2 * sm_count()) {
+      dim3 grid(nb, (P.B + 63) / 64);
+      final_fc_kernel<4><<<grid, NT, 0, s>>>(P.B, Lnext.n_in, Lnext.n_out, r, P.N, Lnext.W, Lnext.n_in, epi, acc);
+    } else {
+      dim3 grid(nb, (P.B + 15) / 16);
+      final_fc_kernel<1><<<grid, NT, 0, s>>>(P.B, Lnext.n_in, Lnext.n_out, r, P.N, Lnext.W, Lnext.n_in, epi, acc);
+    }
   } else {
     int G = 0;
     const int geo = final_fast_geo(Lnext, G);
     if (geo) {
       dim3 grid(final_fast_blocks(Lnext, G), P.B);
-      const size_t smem = (size_t)Lnext.cout * Lnext.cin * Lnext.kh * Lnext.kw * 12;
+      const size_t smem = final_fast_smem(Lnext);
       if (geo == 1) {
         if (G == 4) launch_fast<4, 4, 2, 4>(grid, smem, Lnext, r, P.N, epi, acc, s);
         else launch_fast<4, 4, 2, 3>(grid, smem, Lnext, r, P.N, epi, acc, s);

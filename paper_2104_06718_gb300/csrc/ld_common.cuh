@@ -285,6 +285,8 @@ constexpr int kFusedSteps = 128;
 struct FusedIter {
   int T;                       // iterations of this launch (<= kFusedSteps)
   int crown;                   // 1: compute the CROWN initial duals in the kernel first
+  int fc_threads;              // threads of the CTA that run the FC passes beside the conv passes
+                               // (a multiple of 32 below the CTA size; 0: all passes on all threads)
   float beta1, beta2, eps;
   AdamStep step[kFusedSteps];  // constants of the launch's iterations, in order
 };

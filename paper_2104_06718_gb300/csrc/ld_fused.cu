@@ -56,6 +56,12 @@ struct Ctx {
 template <int S, int NT>
 __device__ __forceinline__ bool active(const Ctx<S, NT>& c, int s) { return c.b0 + s < c.P.B; }
 
+// The threads a pass is spread over: this thread's index in the group (-1:
+// not a member) and the group's size (a multiple of 32).
+struct Team {
+  int tid, n;
+};
+
 // Index of input element (ch, y, x) of conv layer L in its padded plane.
 __device__ __forceinline__ int xp_conv(const LayerDev& L, const FusedLayer& F, int ch, int y, int x) {
   const int Y = y + L.pad, X = x + L.pad;
@@ -239,7 +245,7 @@ __device__ __forceinline__ void tfc_bounds(const Ctx<S, NT>& c, int k, int s, in
   for (int q = 0; q < 4; ++q) {
     l[q] = 0.f;
     u[q] = 0.f;
-    if (k >= 1) clamped_bounds(c.P, c.b0 + s, c.net.L[k - 1].r_out_off + 4 * i4 + q, l[q], u[q]);
+    if (k >= 1 && active(c, s)) clamped_bounds(c.P, c.b0 + s, c.net.L[k - 1].r_out_off + 4 * i4 + q, l[q], u[q]);
   }
 }
 
@@ -247,13 +253,14 @@ __device__ __forceinline__ void tfc_bounds(const Ctx<S, NT>& c, int k, int s, in
 // each half streams its rows and publishes its partial sums (slot = half);
 // tfc_finish adds the two slots and runs the epilogue once both are written.
 template <int S, int NT>
-__device__ void tfc_main(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, int k) {
+__device__ void tfc_main(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, int k, const Team& tm) {
   const float* __restrict__ W = L.W;
   constexpr int U = 16;
-  if (tfc_split(L, F, NT)) {
-    const int n4 = L.n_in / 4, half = NT / 2;
-    const int part = (int)threadIdx.x >= half ? 1 : 0;
-    const int i4 = (int)threadIdx.x - part * half;
+  if (tm.tid < 0) return;
+  if (tfc_split(L, F, tm.n)) {
+    const int n4 = L.n_in / 4, half = tm.n / 2;
+    const int part = tm.tid >= half ? 1 : 0;
+    const int i4 = tm.tid - part * half;
     if (i4 >= n4) return;
     const int nbat = (L.n_out + U - 1) / U, mid = (nbat + 1) / 2;
     float4 acc[S];
@@ -266,7 +273,7 @@ __device__ void tfc_main(const Ctx<S, NT>& c, const LayerDev& L, const FusedLaye
   if (F.vec4) {
     const int n4 = L.n_in / 4;
     const int nbat = (L.n_out + U - 1) / U;
-    for (int i4 = threadIdx.x; i4 < n4; i4 += NT) {
+    for (int i4 = tm.tid; i4 < n4; i4 += tm.n) {
       float l[S][4], u[S][4];
 #pragma unroll
       for (int s = 0; s < S; ++s) tfc_bounds(c, k, s, i4, l[s], u[s]);
@@ -278,7 +285,7 @@ __device__ void tfc_main(const Ctx<S, NT>& c, const LayerDev& L, const FusedLaye
     }
     return;
   }
-  for (int i = threadIdx.x; i < L.n_in; i += NT) {
+  for (int i = tm.tid; i < L.n_in; i += tm.n) {
     float acc[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) acc[s] = 0.f;
@@ -296,11 +303,11 @@ __device__ void tfc_main(const Ctx<S, NT>& c, const LayerDev& L, const FusedLaye
 // Second part of a split transposed FC pass: half p finalises the
 // subdomains s with s % 2 == p (all of them for S = 1) from slot 0 + slot 1.
 template <int S, int NT>
-__device__ void tfc_finish(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, int k) {
-  if (!tfc_split(L, F, NT)) return;
-  const int n4 = L.n_in / 4, half = NT / 2;
-  const int part = (int)threadIdx.x >= half ? 1 : 0;
-  const int i4 = (int)threadIdx.x - part * half;
+__device__ void tfc_finish(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, int k, const Team& tm) {
+  if (tm.tid < 0 || !tfc_split(L, F, tm.n)) return;
+  const int n4 = L.n_in / 4, half = tm.n / 2;
+  const int part = tm.tid >= half ? 1 : 0;
+  const int i4 = tm.tid - part * half;
   if (i4 >= n4) return;
   const float4* X = reinterpret_cast<const float4*>(red_of(c, k));
 #pragma unroll
@@ -314,13 +321,14 @@ __device__ void tfc_finish(const Ctx<S, NT>& c, const LayerDev& L, const FusedLa
   }
 }
 
-// The whole transposed FC pass (its two parts separated by a barrier).
+// The whole transposed FC pass on group tm (its two parts separated by a
+// barrier that every thread of the CTA reaches: tm.n is uniform).
 template <int S, int NT>
-__device__ void transposed_fc(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, int k) {
-  tfc_main(c, L, F, k);
-  if (tfc_split(L, F, NT)) {
+__device__ void transposed_fc(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, int k, const Team& tm) {
+  tfc_main(c, L, F, k, tm);
+  if (tfc_split(L, F, tm.n)) {
     __syncthreads();
-    tfc_finish(c, L, F, k);
+    tfc_finish(c, L, F, k, tm);
   }
 }
 
@@ -328,9 +336,10 @@ __device__ void transposed_fc(const Ctx<S, NT>& c, const LayerDev& L, const Fuse
 // inputs; up to 8 16-byte loads per row are in flight per lane.  The sums go
 // to shared memory and the epilogue runs once all rows are done.
 template <int S, int NT>
-__device__ void ffc_main(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, int k) {
+__device__ void ffc_main(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, int k, const Team& tm) {
+  if (tm.tid < 0) return;
   float* red = red_of(c, k);
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nwarp = NT / 32;
+  const int warp = tm.tid / 32, lane = tm.tid % 32, nwarp = tm.n / 32;
   const float* __restrict__ W = L.W;
   const int npair = (L.n_out + 1) / 2;
   for (int jp = warp; jp < npair; jp += nwarp) {
@@ -416,14 +425,15 @@ __device__ void ffc_finish(const Ctx<S, NT>& c, const LayerDev& L, const FusedLa
 // warp fall in distinct shared-memory banks.
 template <int KH, int KW, int ST, int GF, int S, int NT>
 __device__ void conv_fwd_blocked(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, const FusedIter& it,
-                                 const AdamStep& st) {
+                                 const AdamStep& st, const Team& tm) {
+  if (tm.tid < 0) return;
   const int hh = L.ho / 2, nog = L.cout / GF;
   const int items = S * hh * L.wo * nog;
   const float* wf = c.sW + F.swf;
   const int hq = F.Hp >> 1, wq = F.Wp >> 1;
   // offset of the second row's inputs: hh output rows down
   const int dsec = ST == 2 ? hh * wq : hh * ST * F.Wp;
-  for (int e = threadIdx.x; e < items; e += NT) {
+  for (int e = tm.tid; e < items; e += tm.n) {
     int r = e;
     const int x0 = r % L.wo;
     r /= L.wo;
@@ -488,12 +498,13 @@ __device__ void conv_fwd_blocked(const Ctx<S, NT>& c, const LayerDev& L, const F
 // group of G input channels); the thread computes rows qy and qy + qh/2 of
 // column qx (consecutive lanes: consecutive columns of full rows).
 template <int KH, int KW, int ST, int G, int S, int NT>
-__device__ void conv_t_blocked(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, int k) {
+__device__ void conv_t_blocked(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, int k, const Team& tm) {
+  if (tm.tid < 0) return;
   const int qh = L.h / ST, qw = L.w / ST, hh = qh / 2, ncg = L.cin / G;
   const int items = S * ST * ST * ncg * hh * qw;
   const float* wt = c.sW + F.swt;
   const int dsec = hh * F.Wr;  // the second row's rho, hh rows down
-  for (int e = threadIdx.x; e < items; e += NT) {
+  for (int e = tm.tid; e < items; e += tm.n) {
     int r = e;
     const int qx = r % qw;
     r /= qw;
@@ -568,10 +579,11 @@ __device__ void conv_t_blocked(const Ctx<S, NT>& c, const LayerDev& L, const Fus
 
 template <int S, int NT>
 __device__ void conv_fwd_generic(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, const FusedIter& it,
-                                 const AdamStep& st) {
+                                 const AdamStep& st, const Team& tm) {
+  if (tm.tid < 0) return;
   const int hw_o = L.ho * L.wo, total = L.cout * hw_o;
   const float* wf = c.sW + F.swf;
-  for (int e = threadIdx.x; e < total; e += NT) {
+  for (int e = tm.tid; e < total; e += tm.n) {
     const int o = e / hw_o, rem = e % hw_o, y = rem / L.wo, x = rem % L.wo;
     float acc[S];
 #pragma unroll
@@ -593,10 +605,11 @@ __device__ void conv_fwd_generic(const Ctx<S, NT>& c, const LayerDev& L, const F
 }
 
 template <int S, int NT>
-__device__ void conv_t_generic(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, int k) {
+__device__ void conv_t_generic(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, int k, const Team& tm) {
+  if (tm.tid < 0) return;
   const int hw_i = L.h * L.w, total = L.cin * hw_i;
   const float* wt = c.sW + F.swt;
-  for (int e = threadIdx.x; e < total; e += NT) {
+  for (int e = tm.tid; e < total; e += tm.n) {
     const int ch = e / hw_i, rem = e % hw_i, yy = rem / L.w, xx = rem % L.w;
     float acc[S];
 #pragma unroll
@@ -626,36 +639,38 @@ __device__ void conv_t_generic(const Ctx<S, NT>& c, const LayerDev& L, const Fus
 // Forward conv pass of layer L = layer k+1, with the Adam epilogue.
 template <int S, int NT>
 __device__ void forward_conv(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, const FusedIter& it,
-                             const AdamStep& st) {
-  if (F.fmode == 1 && S * (L.ho / 2) * L.wo * (L.cout / 4) >= NT)
-    conv_fwd_blocked<4, 4, 2, 4>(c, L, F, it, st);
-  else if (F.fmode == 1)  // too few 4-channel items to fill the CTA
-    conv_fwd_blocked<4, 4, 2, 2>(c, L, F, it, st);
-  else if (F.fmode == 2 && S * (L.ho / 2) * L.wo * (L.cout / 4) >= NT)
-    conv_fwd_blocked<3, 3, 1, 4>(c, L, F, it, st);
+                             const AdamStep& st, const Team& tm) {
+  if (F.fmode == 1 && S * (L.ho / 2) * L.wo * (L.cout / 4) >= tm.n)
+    conv_fwd_blocked<4, 4, 2, 4>(c, L, F, it, st, tm);
+  else if (F.fmode == 1)  // too few 4-channel items to fill the group
+    conv_fwd_blocked<4, 4, 2, 2>(c, L, F, it, st, tm);
+  else if (F.fmode == 2 && S * (L.ho / 2) * L.wo * (L.cout / 4) >= tm.n)
+    conv_fwd_blocked<3, 3, 1, 4>(c, L, F, it, st, tm);
   else if (F.fmode == 2)
-    conv_fwd_blocked<3, 3, 1, 2>(c, L, F, it, st);
+    conv_fwd_blocked<3, 3, 1, 2>(c, L, F, it, st, tm);
   else
-    conv_fwd_generic(c, L, F, it, st);
+    conv_fwd_generic(c, L, F, it, st, tm);
 }
 
-// Transposed pass of layer L = layer k+1 into layer k, with the epilogue.
+// Transposed pass of layer L = layer k+1 into layer k, with the epilogue, on
+// the threads of group tm.
 template <int S, int NT>
-__device__ void transposed_pass(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, int k) {
+__device__ void transposed_pass(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, int k,
+                                const Team& tm) {
   if (L.kind == LD_LAYER_FC) {
-    transposed_fc(c, L, F, k);
+    transposed_fc(c, L, F, k, tm);
   } else if (F.tmode == 1) {
     if (L.cin == 3)
-      conv_t_blocked<4, 4, 2, 3>(c, L, F, k);
+      conv_t_blocked<4, 4, 2, 3>(c, L, F, k, tm);
     else
-      conv_t_blocked<4, 4, 2, 4>(c, L, F, k);
+      conv_t_blocked<4, 4, 2, 4>(c, L, F, k, tm);
   } else if (F.tmode == 2) {
     if (L.cin == 3)
-      conv_t_blocked<3, 3, 1, 3>(c, L, F, k);
+      conv_t_blocked<3, 3, 1, 3>(c, L, F, k, tm);
     else
-      conv_t_blocked<3, 3, 1, 4>(c, L, F, k);
+      conv_t_blocked<3, 3, 1, 4>(c, L, F, k, tm);
   } else {
-    conv_t_generic(c, L, F, k);
+    conv_t_generic(c, L, F, k, tm);
   }
 }
 
@@ -720,12 +735,21 @@ __global__ void __launch_bounds__(NT) fused_kernel(const __grid_constant__ Fused
     }
   }
   __syncthreads();
+  // The FC passes of the iterations run on the first fc_threads threads and
+  // the conv passes on the rest, side by side (0: every pass on all threads).
+  const int nf = it.fc_threads;
+  const Team all{(int)threadIdx.x, NT};
+  const Team tf = nf ? Team{(int)threadIdx.x < nf ? (int)threadIdx.x : -1, nf} : all;
+  const Team tc = nf ? Team{(int)threadIdx.x >= nf ? (int)threadIdx.x - nf : -1, NT - nf} : all;
   if (it.crown) {
+    // The CROWN start sets rho_k = g_k exactly for passing ReLUs; those ties
+    // survive only if the iterations compute g_k with the same sums, so each
+    // FC layer runs on the group (and with the split) of the iterations.
     c.crown = true;
     top_pass(c);
     __syncthreads();
     for (int k = net.n - 2; k >= 1; --k) {
-      transposed_pass(c, net.L[k], net.F[k], k);
+      transposed_pass(c, net.L[k], net.F[k], k, net.L[k].kind == LD_LAYER_FC ? tf : all);
       __syncthreads();
     }
     c.crown = false;
@@ -735,7 +759,7 @@ __global__ void __launch_bounds__(NT) fused_kernel(const __grid_constant__ Fused
   for (int k = 0; k + 1 < net.n; ++k)
     if (net.L[k].kind == LD_LAYER_FC) {
       any_fc = true;
-      any_split = any_split || tfc_split(net.L[k], net.F[k], NT);
+      any_split = any_split || tfc_split(net.L[k], net.F[k], tf.n);
     }
   // One iteration in two phases.  Every transposed pass (and the top
   // subproblem) reads only rho of the previous iteration and writes its own
@@ -747,19 +771,19 @@ __global__ void __launch_bounds__(NT) fused_kernel(const __grid_constant__ Fused
     const AdamStep st = it.step[t];
     top_pass(c);
     for (int k = net.n - 2; k >= 0; --k)
-      if (net.L[k].kind == LD_LAYER_FC) tfc_main(c, net.L[k], net.F[k], k);
+      if (net.L[k].kind == LD_LAYER_FC) tfc_main(c, net.L[k], net.F[k], k, tf);
     for (int k = net.n - 2; k >= 0; --k)
-      if (net.L[k].kind != LD_LAYER_FC) transposed_pass(c, net.L[k], net.F[k], k);
+      if (net.L[k].kind != LD_LAYER_FC) transposed_pass(c, net.L[k], net.F[k], k, tc);
     __syncthreads();
     if (any_split) {
       for (int k = net.n - 2; k >= 0; --k)
-        if (net.L[k].kind == LD_LAYER_FC) tfc_finish(c, net.L[k], net.F[k], k);
+        if (net.L[k].kind == LD_LAYER_FC) tfc_finish(c, net.L[k], net.F[k], k, tf);
       __syncthreads();
     }
     for (int k = net.n - 2; k >= 0; --k)
-      if (net.L[k].kind == LD_LAYER_FC) ffc_main(c, net.L[k], net.F[k], k);
+      if (net.L[k].kind == LD_LAYER_FC) ffc_main(c, net.L[k], net.F[k], k, tf);
     for (int k = net.n - 2; k >= 0; --k)
-      if (net.L[k].kind != LD_LAYER_FC) forward_conv(c, net.L[k], net.F[k], it, st);
+      if (net.L[k].kind != LD_LAYER_FC) forward_conv(c, net.L[k], net.F[k], it, st, tc);
     if (any_fc) {
       __syncthreads();
       for (int k = net.n - 2; k >= 0; --k)

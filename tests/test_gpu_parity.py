@@ -320,6 +320,27 @@ def test_short_runs_match_oracle_strictly(name, T, engine):
     assert np.max(rel(out, ref)) < 1e-5
 
 
+@pytest.mark.parametrize("engine", ["layerwise", "fused1", "fused2", "fused4", "fused2w", "fused1w", "auto"])
+@pytest.mark.parametrize("name", ["base", "wide", "deep"])
+def test_crown_ties_survive_the_first_step(name, engine):
+    """The CROWN start (Prop. 3) sets rho_k = g_k exactly for passing ReLUs,
+    so at split-active units the vertex choice of the first inner problem is
+    a tie that the oracle resolves exactly.  The engines resolve it the same
+    way only if their iterations reproduce g_k bit for bit (the same sums as
+    the CROWN pass); a tie broken by rounding turns the first step at that
+    unit around (a change of 2 alpha = 2e-2), against 1e-7 of plain rounding."""
+    pb = conv_problem(name, 16, depth=(0, 8), block=31)
+    net = gpu_net(pb)
+    _, rho = ldb.ld_bound(net, pb["l0"], pb["u0"], pb["lbk"], pb["ubk"], pb["prop"], pb["masks"], n_iters=1,
+                          opts=ENGINES[engine], return_rho=True)
+    _, res, keep = oracle.ld_bound(pb["net"], pb["l0"].astype(np.float64), pb["u0"].astype(np.float64),
+                                   pb["lbk"].astype(np.float64), pb["ubk"].astype(np.float64), pb["prop"],
+                                   pb["masks"], 1)
+    ref = oracle.flatten_layers(pb["net"], res.rho)
+    d = np.abs(rho.cpu().numpy()[keep].astype(np.float64) - ref)
+    assert d.max() < 1e-4, np.argwhere(d >= 1e-4)[:8].tolist()
+
+
 def test_tiny_full_runs_match_oracle_and_stay_below_lp(tiny_set):
     from oracle import lp
     errs = []

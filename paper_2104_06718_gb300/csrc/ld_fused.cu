@@ -62,6 +62,12 @@ struct Team {
   int tid, n;
 };
 
+// Barrier over the n threads (whole warps) that execute it with this id
+// (id 0 is __syncthreads).
+__device__ __forceinline__ void group_sync(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
 // Index of input element (ch, y, x) of conv layer L in its padded plane.
 __device__ __forceinline__ int xp_conv(const LayerDev& L, const FusedLayer& F, int ch, int y, int x) {
   const int Y = y + L.pad, X = x + L.pad;
@@ -409,9 +415,10 @@ __device__ void ffc_main(const Ctx<S, NT>& c, const LayerDev& L, const FusedLaye
 // the weight rounds).
 template <int S, int NT>
 __device__ void ffc_finish(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, int k, const FusedIter& it,
-                           const AdamStep& st) {
+                           const AdamStep& st, const Team& tm) {
+  if (tm.tid < 0) return;
   const float* red = red_of(c, k);
-  for (int e = threadIdx.x; e < S * L.n_out; e += NT) {
+  for (int e = tm.tid; e < S * L.n_out; e += tm.n) {
     const int s = e / L.n_out, j = e - s * L.n_out;
     if (active(c, s)) epi_f(c, L, s, j, j, F.roff + j, red[e], it, st);
   }
@@ -676,11 +683,12 @@ __device__ void transposed_pass(const Ctx<S, NT>& c, const LayerDev& L, const Fu
 
 // Top subproblem: g_{n-1} = -W_n (rho_n = -1); layer n is FC.
 template <int S, int NT>
-__device__ void top_pass(const Ctx<S, NT>& c) {
+__device__ void top_pass(const Ctx<S, NT>& c, const Team& tm) {
+  if (tm.tid < 0) return;
   const int k = c.net.n - 1;
   const LayerDev& L = c.net.L[k];
   const FusedLayer& F = c.net.F[k];
-  for (int e = threadIdx.x; e < S * L.n_in; e += NT) {
+  for (int e = tm.tid; e < S * L.n_in; e += tm.n) {
     const int s = e / L.n_in, i = e % L.n_in;
     if (active(c, s)) epi_t(c, k, s, i, F.xoff + i, rho_of_layer(c, k, i), -__ldg(L.W + i));
   }
@@ -746,7 +754,7 @@ __global__ void __launch_bounds__(NT) fused_kernel(const __grid_constant__ Fused
     // survive only if the iterations compute g_k with the same sums, so each
     // FC layer runs on the group (and with the split) of the iterations.
     c.crown = true;
-    top_pass(c);
+    top_pass(c, all);
     __syncthreads();
     for (int k = net.n - 2; k >= 1; --k) {
       transposed_pass(c, net.L[k], net.F[k], k, net.L[k].kind == LD_LAYER_FC ? tf : all);
@@ -767,13 +775,34 @@ __global__ void __launch_bounds__(NT) fused_kernel(const __grid_constant__ Fused
   // own layer's rho, m, v.  So the passes of a phase run back to back without
   // barriers (a warp that is done with its share of one pass starts on the
   // next), in the order FC passes first (L2-bound weight streams) then convs.
+  // With the FC group split off, the Adam epilogues of an iteration's forward
+  // FC passes (which need all of that pass's sums) run on the FC group at the
+  // start of the next iteration: only the FC group reads what they write (rho
+  // of the FC outputs, in the top and transposed FC passes), so the group's own
+  // barrier orders them and the conv group goes straight on to its passes.
   for (int t = 0; t < it.T; ++t) {
     const AdamStep st = it.step[t];
-    top_pass(c);
-    for (int k = net.n - 2; k >= 0; --k)
-      if (net.L[k].kind == LD_LAYER_FC) tfc_main(c, net.L[k], net.F[k], k, tf);
-    for (int k = net.n - 2; k >= 0; --k)
-      if (net.L[k].kind != LD_LAYER_FC) transposed_pass(c, net.L[k], net.F[k], k, tc);
+    if (nf) {
+      if (tf.tid >= 0) {
+        if (t > 0 && any_fc) {
+          for (int k = net.n - 2; k >= 0; --k)
+            if (net.L[k].kind == LD_LAYER_FC) ffc_finish(c, net.L[k], net.F[k], k, it, it.step[t - 1], tf);
+          group_sync(1, nf);
+        }
+        top_pass(c, tf);
+        for (int k = net.n - 2; k >= 0; --k)
+          if (net.L[k].kind == LD_LAYER_FC) tfc_main(c, net.L[k], net.F[k], k, tf);
+      } else {
+        for (int k = net.n - 2; k >= 0; --k)
+          if (net.L[k].kind != LD_LAYER_FC) transposed_pass(c, net.L[k], net.F[k], k, tc);
+      }
+    } else {
+      top_pass(c, all);
+      for (int k = net.n - 2; k >= 0; --k)
+        if (net.L[k].kind == LD_LAYER_FC) tfc_main(c, net.L[k], net.F[k], k, all);
+      for (int k = net.n - 2; k >= 0; --k)
+        if (net.L[k].kind != LD_LAYER_FC) transposed_pass(c, net.L[k], net.F[k], k, all);
+    }
     __syncthreads();
     if (any_split) {
       for (int k = net.n - 2; k >= 0; --k)
@@ -784,11 +813,17 @@ __global__ void __launch_bounds__(NT) fused_kernel(const __grid_constant__ Fused
       if (net.L[k].kind == LD_LAYER_FC) ffc_main(c, net.L[k], net.F[k], k, tf);
     for (int k = net.n - 2; k >= 0; --k)
       if (net.L[k].kind != LD_LAYER_FC) forward_conv(c, net.L[k], net.F[k], it, st, tc);
-    if (any_fc) {
+    if (!nf && any_fc) {
       __syncthreads();
       for (int k = net.n - 2; k >= 0; --k)
-        if (net.L[k].kind == LD_LAYER_FC) ffc_finish(c, net.L[k], net.F[k], k, it, st);
+        if (net.L[k].kind == LD_LAYER_FC) ffc_finish(c, net.L[k], net.F[k], k, it, st, all);
     }
+    __syncthreads();
+  }
+  // the FC Adam epilogues of the last iteration
+  if (nf && any_fc && it.T > 0) {
+    for (int k = net.n - 2; k >= 0; --k)
+      if (net.L[k].kind == LD_LAYER_FC) ffc_finish(c, net.L[k], net.F[k], k, it, it.step[it.T - 1], all);
     __syncthreads();
   }
   // write back rho, m, v

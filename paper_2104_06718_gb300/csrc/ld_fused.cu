@@ -48,6 +48,7 @@ struct Ctx {
   int b0;          // first subdomain of this CTA
   bool crown;      // transposed-pass epilogue computes the CROWN duals instead of the argmin
   unsigned empty;  // bit s: subdomain b0 + s has crossing bounds (no update)
+  int prop[S];     // property of subdomain b0 + s (0 for the padding of a ragged last CTA); see prop_at
   __device__ float* xp(int s) const { return XP + s * net.xp_total; }
   __device__ float* xb(int s) const { return XB + s * net.nb; }
   __device__ float* rho(int s) const { return RHO + s * net.rho_total; }
@@ -55,6 +56,40 @@ struct Ctx {
 
 template <int S, int NT>
 __device__ __forceinline__ bool active(const Ctx<S, NT>& c, int s) { return c.b0 + s < c.P.B; }
+
+// Property of subdomain b0 + s.  With one subdomain per CTA it is resolved
+// once per launch; with more it is loaded where it is used (measured: the
+// extra live registers cost more than the loads at 2 subdomains per CTA).
+template <int S, int NT>
+__device__ __forceinline__ int prop_at(const Ctx<S, NT>& c, int s) {
+  return S == 1 ? c.prop[0] : prop_of(c.P, c.b0 + s);
+}
+
+// Bounds of neuron j (flat ReLU index) of subdomain s after its split-mask
+// clamp (Sec. 2.3.2: +1 => l <- max(l,0); -1 => u <- min(u,0)).
+template <int S, int NT>
+__device__ __forceinline__ void bounds_of(const Ctx<S, NT>& c, int s, int j, float& l, float& u) {
+  if (S > 1) {
+    clamped_bounds(c.P, c.b0 + s, j, l, u);
+    return;
+  }
+  const Problem& P = c.P;
+  const size_t row = (size_t)c.prop[0] * P.N;
+  l = P.lbk[row + j];
+  u = P.ubk[row + j];
+  const int m = P.mask ? P.mask[(size_t)c.b0 * P.N + j] : 0;
+  if (m > 0) l = fmaxf(l, 0.f);
+  if (m < 0) u = fminf(u, 0.f);
+}
+
+// Division of a non-negative index by a divisor that is uniform over the
+// CTA: a shift when the divisor is a power of two (every dimension of the
+// usual convnets), else the integer division.
+struct IntDiv {
+  int d, sh;  // sh >= 0: d == 1 << sh
+};
+__device__ __forceinline__ IntDiv int_div(int d) { return IntDiv{d, (d & (d - 1)) == 0 ? __ffs(d) - 1 : -1}; }
+__device__ __forceinline__ int div_of(int n, const IntDiv& v) { return v.sh >= 0 ? n >> v.sh : n / v.d; }
 
 // The threads a pass is spread over: this thread's index in the group (-1:
 // not a member) and the group's size (a multiple of 32).
@@ -86,8 +121,9 @@ __device__ __forceinline__ int rho_conv(const FusedLayer& F, int o, int y, int x
 // Index of output element j (flat) of layer L in its padded rho plane.
 __device__ __forceinline__ int rho_flat(const LayerDev& L, const FusedLayer& F, int j) {
   if (L.kind == LD_LAYER_FC) return F.roff + j;
-  const int hw = L.ho * L.wo, o = j / hw, r = j % hw;
-  return rho_conv(F, o, r / L.wo, r % L.wo);
+  const int hw = L.ho * L.wo, o = div_of(j, int_div(hw)), r = j - o * hw;
+  const int y = div_of(r, int_div(L.wo));
+  return rho_conv(F, o, y, r - y * L.wo);
 }
 
 // Transposed-pass epilogue for neuron i of layer k >= 1 (g = g_k[i]) with
@@ -130,12 +166,12 @@ __device__ __forceinline__ void epi_t(const Ctx<S, NT>& c, int k, int s, int i, 
   const int b = c.b0 + s;
   if (k == 0) {
     // P0 (Eq. box_bounds_sol): minimise -g_0^T x0, i.e. x0 = u0 where g_0 >= 0
-    const int p = prop_of(c.P, b);
+    const int p = prop_at(c, s);
     c.xp(s)[xi] = (g >= 0.f) ? c.P.u0[(size_t)p * c.P.n0 + i] : c.P.l0[(size_t)p * c.P.n0 + i];
     return;
   }
   float l, u;
-  clamped_bounds(c.P, b, c.net.L[k - 1].r_out_off + i, l, u);
+  bounds_of(c, s, c.net.L[k - 1].r_out_off + i, l, u);
   epi_t_lu(c, k, s, i, xi, ri, g, l, u);
 }
 
@@ -251,7 +287,7 @@ __device__ __forceinline__ void tfc_bounds(const Ctx<S, NT>& c, int k, int s, in
   for (int q = 0; q < 4; ++q) {
     l[q] = 0.f;
     u[q] = 0.f;
-    if (k >= 1 && active(c, s)) clamped_bounds(c.P, c.b0 + s, c.net.L[k - 1].r_out_off + 4 * i4 + q, l[q], u[q]);
+    if (k >= 1 && active(c, s)) bounds_of(c, s, c.net.L[k - 1].r_out_off + 4 * i4 + q, l[q], u[q]);
   }
 }
 
@@ -440,14 +476,17 @@ __device__ void conv_fwd_blocked(const Ctx<S, NT>& c, const LayerDev& L, const F
   const int hq = F.Hp >> 1, wq = F.Wp >> 1;
   // offset of the second row's inputs: hh output rows down
   const int dsec = ST == 2 ? hh * wq : hh * ST * F.Wp;
+  const IntDiv d_wo = int_div(L.wo), d_hh = int_div(hh), d_nog = int_div(nog);
   for (int e = tm.tid; e < items; e += tm.n) {
-    int r = e;
-    const int x0 = r % L.wo;
-    r /= L.wo;
-    const int y = r % hh;
-    r /= hh;
-    const int og = r % nog;
-    const int s = r / nog;
+    int r = e, q = div_of(r, d_wo);
+    const int x0 = r - q * L.wo;
+    r = q;
+    q = div_of(r, d_hh);
+    const int y = r - q * hh;
+    r = q;
+    q = div_of(r, d_nog);
+    const int og = r - q * nog;
+    const int s = q;
     // accumulators of channel pairs (g, g+1) as float2: one packed FMA
     // (__ffma2_rn, two round-to-nearest FMAs) updates both channels
     float2 acc2[2][GF / 2];
@@ -511,14 +550,17 @@ __device__ void conv_t_blocked(const Ctx<S, NT>& c, const LayerDev& L, const Fus
   const int items = S * ST * ST * ncg * hh * qw;
   const float* wt = c.sW + F.swt;
   const int dsec = hh * F.Wr;  // the second row's rho, hh rows down
+  const IntDiv d_qw = int_div(qw), d_hh = int_div(hh), d_ncg = int_div(ncg);
   for (int e = tm.tid; e < items; e += tm.n) {
-    int r = e;
-    const int qx = r % qw;
-    r /= qw;
-    const int qy = r % hh;
-    r /= hh;
-    const int cg = r % ncg;
-    r /= ncg;
+    int r = e, q = div_of(r, d_qw);
+    const int qx = r - q * qw;
+    r = q;
+    q = div_of(r, d_hh);
+    const int qy = r - q * hh;
+    r = q;
+    q = div_of(r, d_ncg);
+    const int cg = r - q * ncg;
+    r = q;
     const int rx = r % ST;
     r /= ST;
     const int ry = r % ST;
@@ -712,7 +754,8 @@ __global__ void __launch_bounds__(NT) fused_kernel(const __grid_constant__ Fused
   unsigned empty = 0;
   for (int s = 0; s < S; ++s)
     if (b0 + s < P.B && P.empty[b0 + s]) empty |= 1u << s;
-  Ctx<S, NT> c{net, P, sW, XP, XB, RHO, M, V, RED, b0, false, empty};
+  Ctx<S, NT> c{net, P, sW, XP, XB, RHO, M, V, RED, b0, false, empty, {}};
+  if (S == 1) c.prop[0] = b0 < P.B ? prop_of(P, b0) : 0;
   // conv weights; zero planes (their halos stay zero for the whole run)
   for (int k = 0; k < net.n; ++k) {
     const LayerDev& L = net.L[k];

@@ -47,6 +47,8 @@ METRIC = "LD subdomain bounds/s on Base/Wide/Deep convnets, bf16 vs fp32 at ≤1
 # tile, threads per CTA, subdomains, iterations).  Only entries whose kernels have not changed since
 # the capture are listed.
 TRAFFIC = {
+    # fused_kernel<2, 512>, one launch (CROWN start + 100 iterations): profiles/fused_kernel_base256.md
+    ("base", "fp32", "fused", 2, 512, 256, 100): 8.02e6,
     # the seven launches of one BF16 iteration x 100 (cold-cache capture): profiles/tc_kernels_wide2048_bf16.md
     ("wide", "bf16", "tensor-core bf16", 0, 0, 2048, 100): 4.415e10,
 }

@@ -9,7 +9,10 @@
 //   forward pass     x_hat_A,k+1 = W_{k+1} x_k + b_{k+1} -> supergradient
 //                    x_hat_B,k+1 - x_hat_A,k+1 and the Adam step on rho_{k+1}
 // in two phases: all transposed passes (they read only the previous
-// iteration's rho), then all forward passes (see the kernel's loop).
+// iteration's rho), then all forward passes (see the kernel's loop).  When
+// the net has both FC and conv hidden layers, the first half of the CTA runs
+// the FC passes of each phase and the second half the conv passes, side by
+// side (the L2-bound weight streams overlap the shared-memory-bound convs).
 // Everything a subdomain owns lives in shared memory for the whole run:
 //   x_k      one zero-padded plane per layer input (stride-2 conv inputs stored
 //            by stride phase so that the conv reads consecutive addresses)
@@ -206,8 +209,8 @@ __device__ __forceinline__ int rho_of_layer(const Ctx<S, NT>& c, int k, int i) {
 // FC scratch: every hidden FC layer k has its own slice of RED, S x red_need
 // floats, so that the FC passes of different layers may be in flight at the
 // same time.  The forward pass keeps its S x n_out sums there; a transposed
-// pass split between the two CTA halves keeps two slots of S x n_in partial
-// sums.  red_off: per-subdomain floats before layer k's slice.
+// pass split between the two halves of its thread group keeps two slots of
+// S x n_in partial sums.  red_off: per-subdomain floats before layer k's slice.
 __host__ __device__ inline bool tfc_split(const LayerDev& L, const FusedLayer& F, int NT) {
   return F.vec4 && 2 * (L.n_in / 4) <= NT;
 }
@@ -229,10 +232,10 @@ __device__ __forceinline__ float* red_of(const Ctx<S, NT>& c, int k) {
 // Transposed FC pass of layer L = layer k+1 into layer k: g[s][i] = sum_o W[o, i] rho_{k+1}[s][o].
 // A thread owns 4 consecutive columns i and streams the weight rows in
 // batches of U 16-byte loads; the clamped bounds its epilogue needs are
-// loaded before the weight loop.  When the CTA has at least twice as many
-// threads as 4-column groups, its two halves take one half of the rows each
-// and add their partial sums through shared memory (half p finalises the
-// subdomains s with s % 2 == p).
+// loaded before the weight loop.  When the pass's thread group has at least
+// twice as many threads as 4-column groups, its two halves take one half of
+// the rows each and add their partial sums through shared memory (half p
+// finalises the subdomains s with s % 2 == p).
 template <int S, int NT>
 __device__ __forceinline__ void tfc_rows(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, int i4,
                                          int b_lo, int b_hi, float4 (&acc)[S]) {

@@ -14,7 +14,9 @@
 // bound e on its error (from delta_i and the rounding of one subtraction and
 // one product) are summed per subdomain; the bound returned is
 //   S - E - gamma_M * sum|t|   (S = sum t, E = sum e, M = number of terms),
-// each of E and sum|t| inflated for the reassociation of the atomic sums.
+// with E and sum|t| summed rounding upward and scaled by 1 + 2 gamma_M as a
+// margin.  Partial sums go to fixed slots that one kernel adds in a fixed
+// order, so the bound does not depend on the order in which blocks run.
 #include "ld_common.cuh"
 
 namespace ld {

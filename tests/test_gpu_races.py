@@ -4,10 +4,9 @@ sum in a fixed order (no atomics), so any difference in rho_T between two
 runs is a race (a read before its writer's barrier, a lost write).  The FP64
 final bound adds fixed partial-sum slots in a fixed order, so it is
 deterministic too; it is held to 1e-12 relative here, the duals bitwise.
-Ragged batches (B not a multiple of the
-subdomains per CTA) cover the padding subdomains of the last CTA; Base runs
-the fused engine's FC and conv thread groups side by side, Deep a split
-transposed FC pass inside the FC group."""
+Ragged batches (B not a multiple of the subdomains per CTA) cover the padding
+subdomains of the last CTA; Base runs the fused engine's FC and conv thread
+groups side by side, Deep a split transposed FC pass inside the FC group."""
 import numpy as np
 import pytest
 import torch

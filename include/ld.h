@@ -74,7 +74,7 @@ enum { LD_INIT_ZERO = 0, LD_INIT_CROWN = 1, LD_INIT_GIVEN = 2 };
 enum { LD_PREC_FP32 = 0, LD_PREC_BF16 = 1 };
 
 /* Solver options.  Defaults (ld_opts_default): alpha 1e-2 -> 1e-4 (linear
- * decay, Sec. 7.1), Adam beta1 0.9, beta2 0.999, eps 1e-8, CROWN init
+ * decay, Sec. 7.2), Adam beta1 0.9, beta2 0.999, eps 1e-8, CROWN init
  * (Prop. 3), FP32 arithmetic, FP64 final bound. */
 typedef struct {
   float alpha0;        /* step size at iteration 0                          */
@@ -142,7 +142,7 @@ ld_status ld_net_reserve(ld_net* net, int32_t B);
  * last call (LD_ERR_NONFINITE).  Synchronises `stream`, then clears it. */
 ld_status ld_net_sync_status(ld_net* net, void* stream);
 
-/* Interval bound propagation (Sec. 2.2.3; IBP in Sec. 7.1) for n_props boxes.
+/* Interval bound propagation (Sec. 2.2.3; IBP in Sec. 7.2) for n_props boxes.
  *   lb0, ub0 [device] [n_props, n_0] float input boxes.
  *   lbk, ubk [device] [n_props, N] float outputs: bounds of x_hat_k for
  *   layers 1..n-1 (flat ReLU vector), rounded outward (directed FP32
@@ -154,7 +154,7 @@ ld_status ld_intermediate_bounds(ld_net* net, const float* lb0, const float* ub0
                                  float* lbk, float* ubk, double* out_lb, void* stream);
 
 /* Interval bounds recomputed per subdomain after its splits (the
- * per-subdomain intermediate bounds used by BaBSR, Sec. 7.1, with the split
+ * per-subdomain intermediate bounds used by BaBSR, Sec. 5.1.1, with the split
  * semantics of Sec. 2.3.2): for subdomain b, layer 1 is bounded over box
  * prop_of_subdomain[b]; each hidden layer's bounds are clamped by b's split
  * mask (+1 => l <- max(l,0), -1 => u <- min(u,0)) before they bound the

@@ -8,7 +8,7 @@ What it computes.  Intermediate bounds l_hat_k, u_hat_k on x_hat_k are the
 bounds of versions of Eq. (noncvx_pb) whose objective is one neuron
 x_hat_k[i] instead of x_hat_n, for k = 1..n-1 and every i (Sec. 2.2.3).  The
 experiments take, for each layer, the layer-wise best of the bounds returned
-by CROWN and by WK (Sec. 7.1; BaDNB, Sec. 4.3), layer by layer, each layer
+by CROWN and by WK (Sec. 7.2; BaDNB, Sec. 5.1.1), layer by layer, each layer
 bounded with the best bounds of the layers before it.
 
 Both are propagation methods (Sec. 2.2.1): each ReLU is replaced by a linear
@@ -19,7 +19,7 @@ the objective row is substituted backwards through the layers.  They differ
 only in the lower slope of an ambiguous ReLU:
   CROWN: a_low = 1 if u >= -l else 0 (footnote of Sec. 4.2)
   WK:    a_low = [u]_+ / ([u]_+ - [l]_-) = a_bar (the WK relaxation quoted in
-         Sec. 4.3 for Smart Branching).
+         Sec. 4.1 for Smart Branching).
 
 Backward substitution for a lower bound of c^T x_hat_k (an upper bound is
 minus the lower bound of -c^T x_hat_k):
@@ -35,7 +35,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .ld_oracle import Net, classify
+from .ld_oracle import Net, classify, split_offsets
 
 RULES = ("crown", "wk")
 
@@ -90,7 +90,7 @@ def layer_bounds(net: Net, k: int, l0, u0, lb, ub, rule: str):
 
 
 def crown_wk_bounds(net: Net, l0, u0, rules=RULES, include_output: bool = False):
-    """Layer-wise best intermediate bounds over `rules` (Sec. 7.1).
+    """Layer-wise best intermediate bounds over `rules` (Sec. 7.2).
 
     l0, u0: [P, n_0].  Returns lists lb, ub indexed 1..n-1 (1..n with
     include_output), index 0 = the box; layer k is bounded with the best
@@ -105,3 +105,36 @@ def crown_wk_bounds(net: Net, l0, u0, rules=RULES, include_output: bool = False)
         lb.append(np.max(np.stack(lows), axis=0))
         ub.append(np.min(np.stack(ups), axis=0))
     return lb, ub
+
+
+def crown_wk_bounds_split(net: Net, l0, u0, masks, prop=None, rules=RULES):
+    """Layer-wise best bounds recomputed per subdomain after its splits (the
+    bounds refreshed after every activation split in the paper's comparison of
+    intermediate-bound strategies, Sec. 8.4; split semantics of Sec. 2.3.2).
+
+    For subdomain b, layer 1 is bounded over box prop[b]; layer k's best
+    bounds are clamped by the subdomain's split mask (+1 => l <- max(l,0),
+    -1 => u <- min(u,0)) before they enter the relaxations that bound the
+    layers after it.  masks: [B, sum_k n_k] over layers 1..n-1.  Returns
+    clamped lists lb, ub indexed 1..n-1 of [B, n_k] (index 0 = the boxes)
+    and a boolean [B] that is True where some l > u (empty domain).
+    """
+    masks = np.asarray(masks)
+    B = masks.shape[0]
+    prop = np.zeros(B, dtype=np.int64) if prop is None else np.asarray(prop, dtype=np.int64)
+    L0 = np.asarray(l0, np.float64)[prop]
+    U0 = np.asarray(u0, np.float64)[prop]
+    offs = split_offsets(net)
+    lb, ub = [L0], [U0]
+    empty = np.zeros(B, dtype=bool)
+    for k in range(1, net.n):
+        lows, ups = zip(*(layer_bounds(net, k, L0, U0, lb, ub, r) for r in rules))
+        m = masks[:, offs[k - 1]:offs[k]]
+        lk = np.max(np.stack(lows), axis=0)
+        uk = np.min(np.stack(ups), axis=0)
+        lk = np.where(m > 0, np.maximum(lk, 0.0), lk)
+        uk = np.where(m < 0, np.minimum(uk, 0.0), uk)
+        empty |= np.any(lk > uk, axis=1)
+        lb.append(lk)
+        ub.append(uk)
+    return lb, ub, empty

@@ -10,13 +10,13 @@ Network Verification via Lagrangian Decomposition"):
 
 * problem:   min x_hat_n over an L-infinity box, Sec. 2.1, Eq. (noncvx_pb)
 * intermediate bounds: interval bound propagation (IBP), Sec. 2.2.3 and the
-  IBP item of Sec. 7.1 (IBP = all duals set to zero)
+  IBP item of Sec. 7.2 (IBP = all duals set to zero)
 * split masks: a ReLU fixed to its passing or blocking phase, Sec. 2.3.2
 * LD dual q(rho), Sec. 3.1 Eq. (nonprox_problem); its inner minimisation:
   P0 box argmin Eq. (box_bounds_sol), Pk 3-vertex argmin Eq. (min-pk) and the
   box argmins for non-ambiguous ReLUs (Sec. 3.2.2)
 * supergradient x_hat_B - x_hat_A and the Adam ascent of Algorithm 1,
-  Eq. (subgradient_update), step size decayed linearly (Sec. 7.1)
+  Eq. (subgradient_update), step size decayed linearly (Sec. 7.2)
 * dual initialisation from CROWN, Prop. 3 and Eq. (salman-assignment), with
   the CROWN slopes of the footnote in Sec. 4.2 and Eq. (slopes-biases)
 * the closed-form propagation bound Eq. (bounds-propagation)
@@ -193,7 +193,7 @@ def fold_margin(W_last, b_last, c):
 # --------------------------------------------------------------------------
 
 def ibp_bounds(net: Net, l0: np.ndarray, u0: np.ndarray):
-    """Interval bounds for every layer k = 1..n (Sec. 2.2.3; IBP in Sec. 7.1).
+    """Interval bounds for every layer k = 1..n (Sec. 2.2.3; IBP in Sec. 7.2).
 
     l0, u0: [P, n_0].  Returns lists lb, ub indexed 1..n (index 0 = the box).
     Layer 1 is bounded over the box; layer k >= 2 over [relu(l_{k-1}), relu(u_{k-1})].
@@ -245,7 +245,7 @@ def apply_masks(net: Net, lb, ub, masks):
 
 def ibp_bounds_split(net: Net, l0: np.ndarray, u0: np.ndarray, masks: np.ndarray, prop=None):
     """Interval bounds recomputed per subdomain after its splits (the
-    per-subdomain intermediate bounds of BaBSR, Sec. 7.1 / Sec. 2.3.2).
+    per-subdomain intermediate bounds of BaBSR, Sec. 5.1.1 / Sec. 2.3.2).
 
     For subdomain b, layer 1 is bounded over box prop[b]; the split clamp of
     Sec. 2.3.2 is applied to layer k's bounds (+1 => l <- max(l,0),
@@ -538,7 +538,7 @@ def propagation_bound(net: Net, l0, u0, lb, ub, mu, lam):
 
 @dataclass
 class AdamSettings:
-    """Hyper-parameters of the Adam ascent (Sec. 7.1: step size decreased
+    """Hyper-parameters of the Adam ascent (Sec. 7.2: step size decreased
     linearly from alpha0 to alpha_end; Adam moments as Kingma & Ba)."""
     alpha0: float = 1e-2
     alpha_end: float = 1e-4
@@ -548,7 +548,7 @@ class AdamSettings:
 
 
 def step_size(t: int, T: int, s: AdamSettings) -> float:
-    """alpha_t decreased linearly over t = 0..T-1 (Sec. 7.1)."""
+    """alpha_t decreased linearly over t = 0..T-1 (Sec. 7.2)."""
     return s.alpha0 + (s.alpha_end - s.alpha0) * t / max(T - 1, 1)
 
 

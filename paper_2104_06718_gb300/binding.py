@@ -129,7 +129,7 @@ def _dev(x, dtype):
 @dataclass
 class Options:
     """Solver options (ld_opts): step size alpha0 -> alpha_end decayed
-    linearly (Sec. 7.1), Adam moments, initialisation (Prop. 3 CROWN by
+    linearly (Sec. 7.2), Adam moments, initialisation (Prop. 3 CROWN by
     default), FP64 final bound."""
     alpha0: float = 1e-2
     alpha_end: float = 1e-4

@@ -1,4 +1,4 @@
-// Interval bound propagation (Sec. 2.2.3; the IBP bounding of Sec. 7.1):
+// Interval bound propagation (Sec. 2.2.3; the IBP bounding of Sec. 7.2):
 //   l_hat_k = b_k + W_k^+ lo_{k-1} + W_k^- hi_{k-1},  u_hat_k = b_k + W_k^+ hi_{k-1} + W_k^- lo_{k-1}
 // with [lo_0, hi_0] = the input box and [lo_k, hi_k] = [relu(l_hat_k), relu(u_hat_k)].
 // Every multiply-add is rounded outward (round-down for l_hat, round-up for

@@ -3,9 +3,9 @@
 // initialisation, Adam step and supergradient recording fused into their
 // epilogues.
 //
-// Transposed pass (Sec. 5.2, "analogous to backpropagation"):
+// Transposed pass (Sec. 5.2: the same product as a gradient backward pass):
 //     g_k = W_{k+1}^T rho_{k+1}                         -> inner minimisation of layer k
-// Forward pass (Sec. 5.2, "exactly forward passes"):
+// Forward pass (Sec. 5.2: the network's own forward product):
 //     x_hat_A,k+1 = W_{k+1} x_k^* + b_{k+1}             -> supergradient, Adam on rho_{k+1}
 //
 // FC layers are SIMT GEMMs with the subdomain batch as the M dimension in

@@ -1,8 +1,8 @@
 // BF16 tensor-core passes of the LD iteration (Blackwell tcgen05).
 //
 // With precision LD_PREC_BF16 the two linear passes of every Adam iteration,
-//     transposed  g_{k-1} = W_k^T rho_k      (Sec. 5.2, "analogous to backpropagation")
-//     forward     x_hat_A,k = W_k x_{k-1}^*  (Sec. 5.2, "exactly forward passes")
+//     transposed  g_{k-1} = W_k^T rho_k      (Sec. 5.2: a gradient-backward-like product)
+//     forward     x_hat_A,k = W_k x_{k-1}^*  (Sec. 5.2: the network's forward product)
 // run as BF16 GEMMs with FP32 accumulation in tensor memory (TMEM):
 //   conv layers  implicit GEMM, M = 128 (subdomain, position) rows, N = the
 //                channels, K = taps x channels; the weight matrix (all stride

@@ -1,4 +1,4 @@
-"""Pins of the oracle's CROWN / WK intermediate bounds (Sec. 2.2.3, Sec. 7.1)
+"""Pins of the oracle's CROWN / WK intermediate bounds (Sec. 2.2.3, Sec. 7.2)
 to things other than the oracle itself: exact ranges by corner enumeration,
 network values at sampled inputs, the Planet LP and exact minima on tiny
 nets, and Prop. 3 at the network output (the LD dual at the CROWN start is
@@ -173,6 +173,64 @@ def test_rules_differ_only_in_the_ambiguous_lower_slope():
     assert lo_c[0, 3] == lo_w[0, 3] == bar_c[0, 3] == 0.0 and bb_c[0, 3] == 0.0
     # u == -l: CROWN takes slope 1 (the footnote's u >= -l)
     assert lo_c[0, 4] == 1.0
+
+
+# ------------------------------------------------------------------ per-subdomain recomputation after splits
+
+def _split_masks(net, lb, ub, rng, n_sub):
+    """Subdomain 0 unsplit; the others split 1-3 root-ambiguous units of layer 1 or 2."""
+    offs = oracle.split_offsets(net)
+    amb = [j for k in (1, 2) for j in range(offs[k - 1], offs[k])
+           if lb[k][0, j - offs[k - 1]] < 0 < ub[k][0, j - offs[k - 1]]]
+    masks = np.zeros((n_sub, offs[-1]), np.int8)
+    for b in range(1, n_sub):
+        for j in rng.choice(amb, size=rng.integers(1, 4), replace=False):
+            masks[b, j] = rng.choice([-1, 1])
+    return masks
+
+
+@pytest.mark.parametrize("i", range(4))
+def test_split_bounds_contain_every_sampled_input_that_meets_the_splits(i):
+    _, net, l0, u0, _, _ = tiny_problem(i)
+    rlb, rub = ib.crown_wk_bounds(net, l0, u0)
+    rng = np.random.default_rng(100 + i)
+    masks = _split_masks(net, rlb, rub, rng, 12)
+    lb, ub, empty = ib.crown_wk_bounds_split(net, l0, u0, masks)
+    # no splits: the root bounds; every split unit clamped to its phase
+    for k in range(1, net.n):
+        assert np.array_equal(lb[k][0], rlb[k][0]) and np.array_equal(ub[k][0], rub[k][0])
+    offs = oracle.split_offsets(net)
+    for k in range(1, net.n):
+        m = masks[:, offs[k - 1]:offs[k]]
+        assert np.all(lb[k][m > 0] >= 0.0) and np.all(ub[k][m < 0] <= 0.0)
+    x = l0 + rng.uniform(size=(20000, l0.shape[1])) * (u0 - l0)
+    pts = pre_activations(net, x)
+    flat = np.concatenate([pts[k] for k in range(1, net.n)], axis=1)
+    checked = 0
+    for b in range(masks.shape[0]):
+        ok = np.all(np.where(masks[b] > 0, flat >= 0, True) & np.where(masks[b] < 0, flat <= 0, True), axis=1)
+        if not ok.any():
+            continue
+        assert not empty[b]
+        for k in range(1, net.n):
+            scale = np.maximum(np.abs(lb[k][b]), np.abs(ub[k][b])) + 1.0
+            assert np.all(pts[k][ok] >= lb[k][b] - 1e-9 * scale)
+            assert np.all(pts[k][ok] <= ub[k][b] + 1e-9 * scale)
+        checked += 1
+    assert checked >= 6
+
+
+def test_split_against_a_unit_that_cannot_pass_is_empty():
+    _, net, l0, u0, _, _ = tiny_problem(0)
+    rlb, rub = ib.crown_wk_bounds(net, l0, u0)
+    dead = np.nonzero(rub[1][0] < 0)[0]
+    live = np.nonzero(rlb[1][0] > 0)[0]
+    assert dead.size and live.size
+    masks = np.zeros((3, oracle.split_offsets(net)[-1]), np.int8)
+    masks[1, dead[0]] = 1      # force a blocked unit to pass: l = 0 > u
+    masks[2, live[0]] = -1     # force a passing unit to block: u = 0 < l
+    _, _, empty = ib.crown_wk_bounds_split(net, l0, u0, masks)
+    assert empty.tolist() == [False, True, True]
 
 
 # ------------------------------------------------------------------ planted mistakes

@@ -178,7 +178,7 @@ def test_split_ibp_is_sound_on_samples(i):
 
 @pytest.mark.parametrize("i", range(4))
 def test_zero_dual_equals_ibp(i):
-    """Sec. 7.1: IBP corresponds to all duals set to zero."""
+    """Sec. 7.2: IBP corresponds to all duals set to zero."""
     specs, net, l0, u0, lb, ub = tiny_problem(i)
     L, U = lists(net, lb, ub)
     q0 = oracle.dual_value(net, l0, u0, L, U, zeros_like_rho(L))
@@ -352,7 +352,7 @@ def test_single_relu_closed_form(case):
 
 def test_adam_step_matches_torch_adam():
     """The ascent update is Adam (Kingma & Ba) with the linear step decay of
-    Sec. 7.1: torch.optim.Adam(maximize=True) fed the oracle's supergradients
+    Sec. 7.2: torch.optim.Adam(maximize=True) fed the oracle's supergradients
     reproduces the oracle's rho trajectory."""
     specs, net, l0, u0, lb, ub = tiny_problem(2)
     L, U = lists(net, lb, ub)

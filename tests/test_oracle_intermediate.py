@@ -177,15 +177,23 @@ def test_rules_differ_only_in_the_ambiguous_lower_slope():
 
 # ------------------------------------------------------------------ per-subdomain recomputation after splits
 
-def _split_masks(net, lb, ub, rng, n_sub):
-    """Subdomain 0 unsplit; the others split 1-3 root-ambiguous units of layer 1 or 2."""
+def _split_masks(net, lb, ub, rng, n_sub, l0=None, u0=None):
+    """Subdomain 0 unsplit; the others split 1-3 root-ambiguous units of layer 1
+    or 2.  Phases at random, or (with the box given) the phases of a random
+    input's own pre-activations, so that the subdomain contains that input."""
     offs = oracle.split_offsets(net)
     amb = [j for k in (1, 2) for j in range(offs[k - 1], offs[k])
            if lb[k][0, j - offs[k - 1]] < 0 < ub[k][0, j - offs[k - 1]]]
     masks = np.zeros((n_sub, offs[-1]), np.int8)
     for b in range(1, n_sub):
-        for j in rng.choice(amb, size=rng.integers(1, 4), replace=False):
-            masks[b, j] = rng.choice([-1, 1])
+        units = rng.choice(amb, size=rng.integers(1, 4), replace=False)
+        if l0 is None:
+            masks[b, units] = rng.choice([-1, 1], size=len(units))
+        else:
+            x = l0 + rng.uniform(size=l0.shape) * (u0 - l0)
+            pts = pre_activations(net, x)
+            flat = np.concatenate([pts[k] for k in range(1, net.n)], axis=1)[0]
+            masks[b, units] = np.where(flat[units] >= 0, 1, -1)
     return masks
 
 
@@ -218,6 +226,31 @@ def test_split_bounds_contain_every_sampled_input_that_meets_the_splits(i):
             assert np.all(pts[k][ok] <= ub[k][b] + 1e-9 * scale)
         checked += 1
     assert checked >= 6
+
+
+@pytest.mark.parametrize("i", range(2))
+def test_split_bounds_are_below_the_lp_of_the_subdomain(i):
+    """With a subdomain's clamped bounds of layer 1, the Planet LP over them is
+    a relaxation of that subdomain; the CROWN/WK bounds of every neuron of
+    layer 2 of the subdomain lie below its optimum (above, for upper bounds)."""
+    _, net, l0, u0, _, _ = tiny_problem(i)
+    rlb, rub = ib.crown_wk_bounds(net, l0, u0)
+    masks = _split_masks(net, rlb, rub, np.random.default_rng(200 + i), 5, l0, u0)
+    lb, ub, empty = ib.crown_wk_bounds_split(net, l0, u0, masks)
+    assert not empty.any()  # every subdomain contains the input its phases came from
+    for b in range(1, masks.shape[0]):
+        L = [lb[0][b:b + 1]] + [lb[1][b:b + 1]]
+        U = [ub[0][b:b + 1]] + [ub[1][b:b + 1]]
+        lows = {r: ib.layer_bounds(net, 2, L[0], U[0], L, U, r) for r in ib.RULES}
+        for j in range(net.L(2).n_out):
+            for sign in (1.0, -1.0):
+                p = lp.planet_lp(truncated(net, 2, j, sign), l0[0], u0[0], [None, lb[1][b]], [None, ub[1][b]])
+                assert p.status == 0
+                for r in ib.RULES:
+                    bound = lows[r][0][0, j] if sign > 0 else -lows[r][1][0, j]
+                    assert bound <= p.p_star + 1e-7 * max(1.0, abs(p.p_star)), (b, j, sign, r)
+            # the recomputed (clamped) best bound of the unit is one of them, clamped
+            assert lb[2][b, j] >= min(lows[r][0][0, j] for r in ib.RULES) - 1e-12
 
 
 def test_split_against_a_unit_that_cannot_pass_is_empty():

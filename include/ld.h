@@ -116,8 +116,11 @@ const char* ld_status_str(ld_status s);
  *   L [host] n_layers descriptors, layer 1 first.  Every layer but the last
  *   is followed by a ReLU.  The last layer must be FC.
  *   margin [host] NULL, or [cout of the last layer]: the property vector c;
- *   the last layer is folded to W_n = c^T W_last, b_n = c^T b_last (in FP64,
- *   rounded once to FP32), giving the scalar output of the canonical form.
+ *   the last layer is folded to W_n = c^T W_last, b_n = c^T b_last, giving
+ *   the scalar output of the canonical form.  The fold is summed in FP64; the
+ *   Adam iterations use it rounded to FP32, while the FP64 final bound and
+ *   the IBP output bound use the FP64 fold and add a bound on its summation
+ *   error to their slack, so that they bound c^T (W_last x + b_last) itself.
  *   With margin == NULL the last layer must have cout == 1.
  *   *out receives the handle; the handle owns device copies of the weights
  *   and its workspace.  `stream` orders the weight uploads.
@@ -147,7 +150,9 @@ ld_status ld_net_sync_status(ld_net* net, void* stream);
  *   lbk, ubk [device] [n_props, N] float outputs: bounds of x_hat_k for
  *   layers 1..n-1 (flat ReLU vector), rounded outward (directed FP32
  *   rounding), so they contain the exact interval bounds.
- *   out_lb [device] NULL or [n_props] double: IBP lower bound of x_hat_n.
+ *   out_lb [device] NULL or [n_props] double: IBP lower bound of x_hat_n
+ *   (from the FP64 fold of the margin, rounded down, lowered by the fold's
+ *   error bound).
  * Errors: LD_ERR_ARG; LD_ERR_NONFINITE (via the status word) if a box holds
  * NaN/Inf or l0 > u0. */
 ld_status ld_intermediate_bounds(ld_net* net, const float* lb0, const float* ub0, int32_t n_props,
@@ -275,6 +280,16 @@ ld_status ld_final_bound_noalloc(ld_net* net, const float* lb0, const float* ub0
                                  const float* ubk, int32_t n_props, const int32_t* prop_of_subdomain,
                                  const int8_t* split_masks, int32_t B, const float* rho, double* out,
                                  void* stream);
+
+/* Failure injection for tests (not a paper concept): arm a host-side
+ * failure of the library's own device allocations.  After `after` more
+ * allocations succeed, the next one fails without calling the CUDA
+ * allocator, as if it had returned out-of-memory (code = LD_ERR_NOMEM) or
+ * another CUDA error (code = LD_ERR_CUDA); the failure fires once.  The entry
+ * point that made the allocation returns that code and leaves the handle
+ * usable (a later call allocates again).  after < 0 disarms.  Process-wide
+ * (all handles).  Errors: LD_ERR_ARG for another code. */
+ld_status ld_test_inject_alloc_failure(int32_t after, int32_t code);
 
 /* Number of kernels this library has launched in this process (all
  * handles, all calls), for accounting of device work. */

@@ -468,6 +468,29 @@ class BF16Passes:
         return self.rounded[k].linear(round_bf16(x)) + self.net.L(k).bias_vector()[None, :]
 
 
+class FP32Passes:
+    """Linear passes with float32 operands, products and sums: an emulation
+    of an FP32 evaluation of the method, used by the tests to measure how far
+    the Adam trajectory moves when only the rounding of the passes changes
+    (the device kernels sum in other orders; this is a model of their
+    precision, not of their arithmetic).  Every layer is held as a float32
+    sparse matrix, so the sums run in a fixed order on every machine."""
+
+    def __init__(self, net: Net):
+        self.net = net
+        self.mats = {k: sp.csr_matrix(net.L(k).mat, dtype=np.float32) for k in range(1, net.n + 1)}
+        self.tmats = {k: sp.csr_matrix(self.mats[k].T) for k in range(1, net.n + 1)}
+        self.bias = {k: net.L(k).bias_vector().astype(np.float32) for k in range(1, net.n + 1)}
+
+    def transposed(self, k: int, r):
+        out = self.tmats[k] @ np.asarray(r, np.float32).T
+        return np.asarray(out, dtype=np.float32).T.astype(np.float64)
+
+    def forward(self, k: int, x):
+        out = np.asarray(self.mats[k] @ np.asarray(x, np.float32).T, dtype=np.float32).T
+        return (out + self.bias[k][None, :]).astype(np.float64)
+
+
 # --------------------------------------------------------------------------
 # Dual initialisation (Prop. 3) and the propagation bound
 # --------------------------------------------------------------------------
@@ -552,6 +575,22 @@ def step_size(t: int, T: int, s: AdamSettings) -> float:
     return s.alpha0 + (s.alpha_end - s.alpha0) * t / max(T - 1, 1)
 
 
+def adam_update(rho, m, v, sg, tt: int, Ts: int, s: AdamSettings):
+    """One Adam ascent step of one layer at schedule index tt of Ts (Algorithm 1
+    with Adam in place of Eq. (subgradient_update); bias corrections with step
+    count tt + 1, step size of the linear schedule of Sec. 7.2):
+        m <- b1 m + (1-b1) s;  v <- b2 v + (1-b2) s^2
+        rho <- rho + alpha_tt * (m / (1-b1^(tt+1))) / (sqrt(v / (1-b2^(tt+1))) + eps)
+    Returns the new (rho, m, v)."""
+    alpha = step_size(tt, Ts, s)
+    bc1 = 1.0 - s.beta1 ** (tt + 1)
+    bc2 = 1.0 - s.beta2 ** (tt + 1)
+    m = s.beta1 * m + (1.0 - s.beta1) * sg
+    v = s.beta2 * v + (1.0 - s.beta2) * sg ** 2
+    rho = rho + alpha * (m / bc1) / (np.sqrt(v / bc2) + s.eps)
+    return rho, m, v
+
+
 @dataclass
 class AdamResult:
     rho: list
@@ -585,13 +624,8 @@ def supergradient_adam(net, l0, u0, lb, ub, rho0, T, s: AdamSettings = AdamSetti
         sol = inner_minimisation(net, l0, u0, lb, ub, rho, passes)
         trace.append(sol.q)
         sg = supergradient(sol)
-        alpha = step_size(tt, Ts, s)
-        bc1 = 1.0 - s.beta1 ** (tt + 1)
-        bc2 = 1.0 - s.beta2 ** (tt + 1)
         for k in range(1, n):
-            m[k] = s.beta1 * m[k] + (1.0 - s.beta1) * sg[k]
-            v[k] = s.beta2 * v[k] + (1.0 - s.beta2) * sg[k] ** 2
-            rho[k] = rho[k] + alpha * (m[k] / bc1) / (np.sqrt(v[k] / bc2) + s.eps)
+            rho[k], m[k], v[k] = adam_update(rho[k], m[k], v[k], sg[k], tt, Ts, s)
     q_final = inner_minimisation(net, l0, u0, lb, ub, rho).q
     q_trace = np.array(trace) if trace else np.zeros((0, l0.shape[0]))
     return AdamResult(rho=rho, m=m, v=v, q_trace=q_trace, q_final=q_final)

@@ -7,7 +7,11 @@ theorem applied to the inner minimum of Eq. (nonprox_problem)); it flows to
 the input box, the intermediate bounds and the layer parameters.  The net
 handle holds its own copy of the weights: pass the same parameter tensors it
 was built from (they route gradients only), and rebuild the handle after
-changing their values.
+changing their values.  The first call with a set of parameter tensors checks
+their values against the handle's weights; later calls check that the
+tensors have not been written since (their version counters), so a changed
+parameter without a rebuilt handle raises instead of returning stale bounds
+and gradients.
 """
 from __future__ import annotations
 
@@ -15,6 +19,33 @@ import numpy as np
 import torch
 
 from . import binding as ldb
+
+
+class StaleParametersError(RuntimeError):
+    """The parameter tensors differ from the weights the net handle was built from."""
+
+
+def check_params(net, params):
+    """Raise StaleParametersError unless params (W_1, b_1, ..., W_n, b_n, or a
+    prefix of them) hold the weights net was built from (the last layer
+    before margin folding)."""
+    if not params:
+        return
+    key = tuple((p.data_ptr(), p._version) for p in params)
+    if getattr(net, "_param_key", None) == key:
+        return
+    expect = []
+    for s in net.specs:
+        expect += [np.asarray(s.W, np.float32), np.asarray(s.b, np.float32)]
+    if len(params) > len(expect):
+        raise StaleParametersError(f"{len(params)} parameter tensors for a net of {len(expect)}")
+    for i, (p, e) in enumerate(zip(params, expect)):
+        t = p.detach()
+        if tuple(t.shape) != e.shape or not torch.equal(t.to(device="cpu", dtype=torch.float32),
+                                                        torch.from_numpy(np.ascontiguousarray(e))):
+            raise StaleParametersError(f"parameter {i} differs from the weights the net handle holds: rebuild the "
+                                       "net (binding.Net) after changing its parameters")
+    net._param_key = key
 
 
 class LDBound(torch.autograd.Function):
@@ -28,6 +59,7 @@ class LDBound(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, net, n_iters, opts, prop, masks, lb0, ub0, lbk, ubk, *params):
+        check_params(net, params)
         out, rho = ldb.ld_bound(net, lb0, ub0, lbk, ubk, prop, masks, n_iters=n_iters, opts=opts, return_rho=True)
         ctx.net = net
         ctx.prop = prop

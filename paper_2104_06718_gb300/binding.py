@@ -29,6 +29,7 @@ EXPORTED = [
     "ld_net_sync_status", "ld_selftest_wait_timeout", "ld_intermediate_bounds", "ld_intermediate_bounds_split",
     "ld_bound", "ld_dual_supergradient", "ld_bound_backward",
     "ld_net_profile", "ld_net_profile_read", "ld_launch_count", "ld_net_tuned", "ld_final_bound_noalloc",
+    "ld_test_inject_alloc_failure",
 ]
 PHASES = {"iter": 0, "final": 1, "init": 2, "ibp": 3, "backward": 4}
 
@@ -85,6 +86,7 @@ def load_library(path: str = LIB_PATH):
     lib.ld_launch_count.argtypes = [C.POINTER(i64)]
     lib.ld_net_tuned.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
     lib.ld_final_bound_noalloc.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, i32, vp, vp, vp]
+    lib.ld_test_inject_alloc_failure.argtypes = [i32, i32]
     for name in EXPORTED:
         if name not in ("ld_opts_default", "ld_status_str"):
             getattr(lib, name).restype = C.c_int
@@ -239,6 +241,13 @@ class Net:
         _check(self._lib.ld_net_tuned(self._h, int(B), C.byref(e), C.byref(t), C.byref(n)), "ld_net_tuned")
         names = {LD_ENGINE_LAYERWISE: "layerwise", LD_ENGINE_FUSED: "fused"}
         return names.get(e.value), t.value, n.value
+
+
+def inject_alloc_failure(after: int, code: int = LD_ERR_NOMEM):
+    """Arm a host-side failure of libld's device allocations: after `after`
+    more allocations succeed, the next one fails with `code` (LD_ERR_NOMEM or
+    LD_ERR_CUDA) without calling the CUDA allocator; after < 0 disarms."""
+    _check(load_library().ld_test_inject_alloc_failure(int(after), int(code)), "ld_test_inject_alloc_failure")
 
 
 def launch_count() -> int:

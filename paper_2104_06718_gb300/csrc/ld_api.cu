@@ -17,6 +17,26 @@ using ld::Problem;
 namespace ld {
 std::atomic<int64_t> g_launches{0};
 void count_launch(int n) { g_launches.fetch_add(n); }
+
+// Host-side failure injection for the allocation paths (ld_test_inject_alloc_failure):
+// g_fail_after allocations still succeed, then one returns g_fail_code without
+// calling cudaMalloc; -1 = off.
+std::atomic<int> g_fail_after{-1};
+std::atomic<int> g_fail_code{0};
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  int n = g_fail_after.load();
+  while (n >= 0) {
+    if (g_fail_after.compare_exchange_weak(n, n - 1)) {
+      if (n == 0) {
+        *p = nullptr;
+        return g_fail_code.load() == LD_ERR_CUDA ? cudaErrorInvalidValue : cudaErrorMemoryAllocation;
+      }
+      break;
+    }
+  }
+  return cudaMalloc(p, bytes);
+}
 }  // namespace ld
 
 struct ld_net {
@@ -30,7 +50,9 @@ struct ld_net {
   float* d_b = nullptr;
   float* d_Wx = nullptr;              // conv weights re-laid for the fused engine
   int* d_status = nullptr;
-  double bn = 0.0;                    // folded output bias b_n
+  double bn = 0.0;                    // folded output bias b_n (FP64 fold)
+  double bn_err = 0.0;                // bound on the FP64 fold's error in b_n
+  double* d_Wn64 = nullptr;           // FP64 folded last row [n_{n-1}], then its error bounds [n_{n-1}]
   // workspace, sized for ws_B subdomains
   int ws_B = -1;
   void* ws = nullptr;
@@ -72,7 +94,9 @@ struct ld_net {
 };
 
 namespace ld {
-NetView net_view(const ld_net* net) { return NetView{net->n, net->n0, net->N, net->bn, &net->L, net->d_status}; }
+NetView net_view(const ld_net* net) {
+  return NetView{net->n, net->n0, net->N, net->bn, net->bn_err, &net->L, net->d_status};
+}
 }  // namespace ld
 
 namespace {
@@ -124,6 +148,10 @@ namespace {
 
 inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// Higham's gamma_{m-1} for a recursive FP64 sum of m exact products (the
+// margin fold): the sum's error is at most gamma_{m-1} times the sum of |terms|.
+double fold_gamma(int m) { return ld::final_gamma((double)(m - 1)); }
+
 ld_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return LD_OK;
   if (e == cudaErrorMemoryAllocation) return LD_ERR_NOMEM;
@@ -174,9 +202,10 @@ ld_status ensure_ws(ld_net* net, int B) {
   cudaDeviceSynchronize();
   free_ws(net);
   void* p = nullptr;
-  if (cudaMalloc(&p, total) != cudaSuccess) {
+  const cudaError_t e = ld::dev_malloc(&p, total);
+  if (e != cudaSuccess) {
     cudaGetLastError();
-    return LD_ERR_NOMEM;
+    return cuda_status(e);
   }
   net->ws = p;
   char* c = static_cast<char*>(p);
@@ -404,8 +433,9 @@ ld_status run_graphed(ld_net* net, cudaStream_t s, F launches) {
 // Tensor-core plan and shadow buffers for B subdomains and n_props properties.
 ld_status ensure_tc(ld_net* net, int B, int n_props) {
   if (!net->tc_tried) {
-    net->tc_tried = true;
     net->tc_state = ld::build_tc_net(net->L, &net->tc);
+    // a shape without a tensor-core path is final; a failed allocation is retried by the next call
+    net->tc_tried = net->tc_state == LD_OK || net->tc_state == LD_ERR_UNSUPPORTED;
   }
   if (net->tc_state != LD_OK) return net->tc_state;
   if (B <= net->tc_B && n_props <= net->tc_props) return LD_OK;
@@ -417,9 +447,10 @@ ld_status ensure_tc(ld_net* net, int B, int n_props) {
   net->tc_ws = nullptr;
   net->tc_B = net->tc_props = -1;
   void* p = nullptr;
-  if (cudaMalloc(&p, s_xh + s_rh + s_c1) != cudaSuccess) {
+  const cudaError_t e = ld::dev_malloc(&p, s_xh + s_rh + s_c1);
+  if (e != cudaSuccess) {
     cudaGetLastError();
-    return LD_ERR_NOMEM;
+    return cuda_status(e);
   }
   // the zero padding of the shadows is never written afterwards
   if (cudaMemset(p, 0, s_xh + s_rh + s_c1) != cudaSuccess) return LD_ERR_CUDA;
@@ -564,7 +595,7 @@ void final_fp64(ld_net* net, const Problem& P, double* out, cudaStream_t s) {
   ld::launch_final_bias(net->L, P, net->rho, acc, s);
   const double M = (double)(net->n0 + 2 * net->N + 1);
   const double gM = ld::final_gamma(M);
-  ld::launch_final_combine_bn(P, acc, net->bn, gM, 1.0 + 2.0 * gM, out, s);
+  ld::launch_final_combine_bn(P, acc, net->bn, net->bn_err, gM, 1.0 + 2.0 * gM, out, s);
 }
 
 // q in FP32 terms (FP64 sum) via the forward form, +inf for empty subdomains.
@@ -667,21 +698,44 @@ ld_status ld_net_create(const ld_layer_desc* Ld, int32_t n_layers, const float* 
   if (!margin && last.cout != 1) return LD_ERR_SHAPE;
 
   // Host copies of the packed parameters, last layer folded with the margin.
+  // The fold c^T W_last, c^T b_last is summed in FP64 (each product of two
+  // floats is exact there); the iterations use its FP32 rounding, while the
+  // FP64 final bound and the IBP output bound use the FP64 row together with
+  // an a-priori bound on its summation error, gamma_{m-1} sum_o |c_o W_o,i|
+  // for m = cout terms, so that they bound the property c^T (W x + b) itself
+  // and not its rounded copy.
   std::vector<float> hW(n_w), hb(n_b);
+  const int n_last_in = Ld[n_layers - 1].cin;
+  std::vector<double> hWn64(2 * (size_t)n_last_in + 2);   // folded row, its error bounds, then b_n and its bound
+  double bn64 = 0.0, bn_err = 0.0;
   for (int k = 0; k < n_layers; ++k) {
     const ld_layer_desc& d = Ld[k];
     if (k < n_layers - 1) {
       std::memcpy(&hW[w_off[k]], d.W, sizeof(float) * (size_t)d.cout * d.cin * (d.kind == LD_LAYER_FC ? 1 : d.kh * d.kw));
       std::memcpy(&hb[b_off[k]], d.b, sizeof(float) * (size_t)d.cout);
     } else {
-      double bsum = 0.0;
+      const double gm = fold_gamma(d.cout);
       for (int i = 0; i < d.cin; ++i) {
-        double s = 0.0;
-        for (int o = 0; o < d.cout; ++o) s += (margin ? (double)margin[o] : 1.0) * (double)d.W[(size_t)o * d.cin + i];
+        double s = 0.0, a = 0.0;
+        for (int o = 0; o < d.cout; ++o) {
+          const double t = (margin ? (double)margin[o] : 1.0) * (double)d.W[(size_t)o * d.cin + i];
+          s += t;
+          a += std::fabs(t);
+        }
         hW[w_off[k] + i] = (float)s;
+        hWn64[i] = s;
+        hWn64[(size_t)n_last_in + i] = gm * a;
       }
-      for (int o = 0; o < d.cout; ++o) bsum += (margin ? (double)margin[o] : 1.0) * (double)d.b[o];
-      hb[b_off[k]] = (float)bsum;
+      double a = 0.0;
+      for (int o = 0; o < d.cout; ++o) {
+        const double t = (margin ? (double)margin[o] : 1.0) * (double)d.b[o];
+        bn64 += t;
+        a += std::fabs(t);
+      }
+      hb[b_off[k]] = (float)bn64;
+      bn_err = gm * a;
+      hWn64[2 * (size_t)n_last_in] = bn64;
+      hWn64[2 * (size_t)n_last_in + 1] = bn_err;
     }
   }
 
@@ -708,11 +762,15 @@ ld_status ld_net_create(const ld_layer_desc* Ld, int32_t n_layers, const float* 
   net->b_off = b_off;
   net->n_w = n_w;
   net->n_b = n_b;
-  net->bn = (double)hb[b_off[n_layers - 1]];
+  net->bn = bn64;
+  net->bn_err = bn_err;
   cudaStream_t s = S(stream);
-  ld_status st = cuda_status(cudaMalloc(&net->d_W, sizeof(float) * n_w));
-  if (st == LD_OK) st = cuda_status(cudaMalloc(&net->d_b, sizeof(float) * n_b));
-  if (st == LD_OK) st = cuda_status(cudaMalloc(&net->d_status, sizeof(int)));
+  ld_status st = cuda_status(ld::dev_malloc((void**)&net->d_W, sizeof(float) * n_w));
+  if (st == LD_OK) st = cuda_status(ld::dev_malloc((void**)&net->d_b, sizeof(float) * n_b));
+  if (st == LD_OK) st = cuda_status(ld::dev_malloc((void**)&net->d_Wn64, sizeof(double) * hWn64.size()));
+  if (st == LD_OK)
+    st = cuda_status(cudaMemcpyAsync(net->d_Wn64, hWn64.data(), sizeof(double) * hWn64.size(), cudaMemcpyHostToDevice, s));
+  if (st == LD_OK) st = cuda_status(ld::dev_malloc((void**)&net->d_status, sizeof(int)));
   if (st == LD_OK) st = cuda_status(cudaMemcpyAsync(net->d_W, hW.data(), sizeof(float) * n_w, cudaMemcpyHostToDevice, s));
   if (st == LD_OK) st = cuda_status(cudaMemcpyAsync(net->d_b, hb.data(), sizeof(float) * n_b, cudaMemcpyHostToDevice, s));
   if (st == LD_OK) st = cuda_status(cudaMemsetAsync(net->d_status, 0, sizeof(int), s));
@@ -746,17 +804,23 @@ ld_status ld_net_create(const ld_layer_desc* Ld, int32_t n_layers, const float* 
             hX[x_off[k] + nw + (((size_t)o * l.kh + i) * l.kw + j) * l.cin + c] = w;
           }
   }
-  if (cudaMalloc(&net->d_Wx, sizeof(float) * hX.size()) != cudaSuccess ||
-      cudaMemcpy(net->d_Wx, hX.data(), sizeof(float) * hX.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
-    cudaGetLastError();
-    ld_net_destroy(net);
-    return LD_ERR_NOMEM;
+  {
+    cudaError_t e = ld::dev_malloc((void**)&net->d_Wx, sizeof(float) * hX.size());
+    if (e == cudaSuccess) e = cudaMemcpy(net->d_Wx, hX.data(), sizeof(float) * hX.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      ld_net_destroy(net);
+      return cuda_status(e);
+    }
   }
   for (int k = 0; k < n_layers; ++k) {
     L[k].W = net->d_W + w_off[k];
     L[k].b = net->d_b + b_off[k];
     L[k].Wf = nullptr;
     L[k].Wt = nullptr;
+    L[k].W64 = k == n_layers - 1 ? net->d_Wn64 : nullptr;
+    L[k].W64_err = k == n_layers - 1 ? net->d_Wn64 + n_last_in : nullptr;
+    L[k].b64 = k == n_layers - 1 ? net->d_Wn64 + 2 * (size_t)n_last_in : nullptr;
     if (L[k].kind == LD_LAYER_CONV) {
       const size_t nw = ((size_t)L[k].cout * L[k].cin * L[k].kh * L[k].kw + 3) & ~size_t(3);
       L[k].Wf = net->d_Wx + x_off[k];
@@ -787,6 +851,7 @@ ld_status ld_net_destroy(ld_net* net) {
   if (net->d_W) cudaFree(net->d_W);
   if (net->d_Wx) cudaFree(net->d_Wx);
   if (net->d_b) cudaFree(net->d_b);
+  if (net->d_Wn64) cudaFree(net->d_Wn64);
   if (net->d_status) cudaFree(net->d_status);
   delete net;
   return LD_OK;
@@ -1027,3 +1092,10 @@ ld_status ld_net_tuned(const ld_net* net, int32_t B, int32_t* engine, int32_t* t
 }
 
 }  // extern "C"
+
+ld_status ld_test_inject_alloc_failure(int32_t after, int32_t code) {
+  if (after >= 0 && code != LD_ERR_NOMEM && code != LD_ERR_CUDA) return LD_ERR_ARG;
+  ld::g_fail_code.store(code);
+  ld::g_fail_after.store(after < 0 ? -1 : after);
+  return LD_OK;
+}

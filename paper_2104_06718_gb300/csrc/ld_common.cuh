@@ -33,6 +33,9 @@ struct LayerDev {
   const float* b;                // [cout]
   const float* Wf;               // conv only: [cin, kh, kw, cout] (forward pass, output channels innermost)
   const float* Wt;               // conv only: [cout, kh, kw, cin] (transposed pass, input channels innermost)
+  const double* W64;             // last layer only: the margin-folded row summed in FP64 [n_in]
+  const double* W64_err;         // last layer only: bound on that row's summation error [n_in]
+  const double* b64;             // last layer only: {folded b_n in FP64, bound on its error}
 };
 
 // Inputs of one bounding call, in device memory.
@@ -241,11 +244,16 @@ struct EpiRecord {
 // kernel it launches); read through ld_launch_count.
 void count_launch(int n = 1);
 
+// Every device allocation of the library goes through here (cudaMalloc, or
+// the failure armed by ld_test_inject_alloc_failure).
+cudaError_t dev_malloc(void** p, size_t bytes);
+
 // Read-only view of a net handle for entry points outside ld_api.cu.
 struct NetView {
   int n;
   int64_t n0, N;
-  double bn;                         // folded output bias
+  double bn;                         // folded output bias (FP64 fold)
+  double bn_err;                     // bound on the FP64 fold's error in bn
   const std::vector<LayerDev>* L;    // (*L)[k-1] = layer k
   int* d_status;
 };
@@ -417,8 +425,8 @@ void launch_final_layer(const LayerDev& Lnext, int layer, int r_off, int x_off, 
                         const float* rho, int top, FinalAcc acc, cudaStream_t s);
 void launch_final_bias(const std::vector<LayerDev>& Ls, const Problem& P, const float* rho, FinalAcc acc,
                        cudaStream_t s);
-void launch_final_combine_bn(const Problem& P, FinalAcc acc, double bn, double gamma_M, double inflate,
-                             double* out, cudaStream_t s);
+void launch_final_combine_bn(const Problem& P, FinalAcc acc, double bn, double bn_err, double gamma_M,
+                             double inflate, double* out, cudaStream_t s);
 double final_gamma(double K);  // Higham's gamma_K for unit roundoff 2^-53, slightly inflated
 
 // Danskin adjoint (ld_backward.cu).

@@ -56,7 +56,10 @@ struct FinalEpi {
   const float* rho;
   double gamma_K;
   __device__ __forceinline__ void term(int b, int i, double g, float abs_sum, double& t, double& e) const {
-    const double delta = __dmul_ru(gamma_K, (double)abs_sum);
+    term_delta(b, i, g, __dmul_ru(gamma_K, (double)abs_sum), t, e);
+  }
+  // delta: bound on |g - exact g|
+  __device__ __forceinline__ void term_delta(int b, int i, double g, double delta, double& t, double& e) const {
     if (layer == 0) {
       const int p = prop_of(P, b);
       final_term(true, 0.0, g, delta, (double)P.l0[(size_t)p * P.n0 + i], (double)P.u0[(size_t)p * P.n0 + i], t, e);
@@ -356,14 +359,23 @@ int final_fast_blocks(const LayerDev& L, int G) {
   return (items + NT - 1) / NT;
 }
 
-// Top subproblem P_{n-1}: g_{n-1} = -W_n exactly (no rounding, delta = 0).
-__global__ void __launch_bounds__(NT) final_top_kernel(int n, const float* __restrict__ Wn, FinalEpi epi,
+// Top subproblem P_{n-1}: g_{n-1} = -W_n, no product formed.  W_n is the
+// margin-folded row summed in FP64 (Wn64) when the net has one, with Wn_err
+// bounding the distance of each entry from the exact fold (the error of g
+// enters the term's error bound like a summation error); else the FP32 row,
+// exact.
+__global__ void __launch_bounds__(NT) final_top_kernel(int n, const float* __restrict__ Wn,
+                                                       const double* __restrict__ Wn64,
+                                                       const double* __restrict__ Wn_err, FinalEpi epi,
                                                        FinalAcc acc_out) {
   const int b = blockIdx.x;
   double st = 0.0, se = 0.0, sa = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     double tv, ev;
-    epi.term(b, i, -(double)Wn[i], 0.f, tv, ev);
+    if (Wn64)
+      epi.term_delta(b, i, -Wn64[i], Wn_err[i], tv, ev);
+    else
+      epi.term(b, i, -(double)Wn[i], 0.f, tv, ev);
     st += tv;
     se = __dadd_ru(se, ev);
     sa = __dadd_ru(sa, fabs(tv));
@@ -393,13 +405,14 @@ __global__ void __launch_bounds__(NT) final_bias_kernel(Problem P, BiasLayers BL
   block_reduce_add(acc_out, acc_out.slot, b, st, 0.0, sa);
 }
 
-__global__ void final_combine_kernel(Problem P, FinalAcc a, double bn, double gamma_M, double inflate, double* out) {
+__global__ void final_combine_kernel(Problem P, FinalAcc a, double bn, double bn_err, double gamma_M, double inflate,
+                                     double* out) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < P.B; b += gridDim.x * blockDim.x) {
     if (P.empty[b]) {
       out[b] = __longlong_as_double(0x7ff0000000000000LL);  // +inf: empty subdomain
       continue;
     }
-    double S = bn, E = 0.0, A = fabs(bn);
+    double S = bn, E = bn_err, A = fabs(bn);
     const double* p = a.slots + (size_t)b * a.n_slots * 3;
     for (int i = 0; i < a.n_slots; ++i) {
       S += p[3 * i];
@@ -454,7 +467,7 @@ void launch_final_layer(const LayerDev& Lnext, int layer, int r_off, int x_off, 
   if (P.B == 0) return;
   count_launch();
   if (top) {
-    final_top_kernel<<<P.B, NT, 0, s>>>(Lnext.n_in, Lnext.W, epi, acc);
+    final_top_kernel<<<P.B, NT, 0, s>>>(Lnext.n_in, Lnext.W, Lnext.W64, Lnext.W64_err, epi, acc);
     return;
   }
   const float* r = rho + Lnext.r_out_off;
@@ -505,12 +518,13 @@ void launch_final_bias(const std::vector<LayerDev>& Ls, const Problem& P, const 
   final_bias_kernel<<<P.B, NT, 0, s>>>(P, BL, rho, acc);
 }
 
-// b_n is read on the host once per net and passed here.
-void launch_final_combine_bn(const Problem& P, FinalAcc acc, double bn, double gamma_M, double inflate,
-                             double* out, cudaStream_t s) {
+// b_n (the FP64 fold) and the bound on its fold error are read on the host
+// once per net and passed here.
+void launch_final_combine_bn(const Problem& P, FinalAcc acc, double bn, double bn_err, double gamma_M,
+                             double inflate, double* out, cudaStream_t s) {
   if (P.B == 0) return;
   count_launch();
-  final_combine_kernel<<<(P.B + 255) / 256, 256, 0, s>>>(P, acc, bn, gamma_M, inflate, out);
+  final_combine_kernel<<<(P.B + 255) / 256, 256, 0, s>>>(P, acc, bn, bn_err, gamma_M, inflate, out);
 }
 
 double final_gamma(double K) { return gamma_of(K); }

@@ -2,7 +2,9 @@
 //   l_hat_k = b_k + W_k^+ lo_{k-1} + W_k^- hi_{k-1},  u_hat_k = b_k + W_k^+ hi_{k-1} + W_k^- lo_{k-1}
 // with [lo_0, hi_0] = the input box and [lo_k, hi_k] = [relu(l_hat_k), relu(u_hat_k)].
 // Every multiply-add is rounded outward (round-down for l_hat, round-up for
-// u_hat), so the FP32 results contain the exact interval bounds.
+// u_hat), so the FP32 results contain the exact interval bounds.  The output
+// lower bound of the margin-folded last layer is formed in FP64 from the
+// FP64 fold, lowered by the fold's error bound.
 // One launch per layer; one thread per (row, output neuron), a row being a
 // property (root bounds) or a subdomain (bounds recomputed after its splits:
 // the first layer reads the box of the subdomain's property, and the split
@@ -27,6 +29,20 @@ __global__ void ibp_kernel(LayerDev L, int first, int last, int n_rows, const fl
     const float* lp = lin + (size_t)src * in_stride;
     const float* up = uin + (size_t)src * in_stride;
     float lo, hi;
+    if (last && L.W64) {
+      // Output bound of the margin-folded last layer from its FP64 row: each
+      // weight is within W64_err of the exact fold and the inputs are
+      // relu'd intervals, so w x >= W64 x - W64_err hi for x in [a, c], c >= 0.
+      double lod = __dsub_rd(L.b64[0], L.b64[1]);
+      for (int i = 0; i < L.n_in; ++i) {
+        const double a = fmax((double)lp[i], 0.0), c = fmax((double)up[i], 0.0);
+        const double wi = L.W64[i];
+        lod = __fma_rd(wi, wi >= 0.0 ? a : c, lod);
+        lod = __dsub_rd(lod, __dmul_ru(L.W64_err[i], c));
+      }
+      if (out_lb) out_lb[p] = lod;
+      continue;
+    }
     if (L.kind == LD_LAYER_FC) {
       lo = L.b[o];
       hi = L.b[o];

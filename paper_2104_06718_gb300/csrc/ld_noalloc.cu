@@ -91,7 +91,7 @@ extern "C" ld_status ld_final_bound_noalloc(ld_net* net, const float* lb0, const
   }
   ld::launch_final_bias(Ls, P, rho, acc, s);
   const double gM = ld::final_gamma((double)(nv.n0 + 2 * nv.N + 1));
-  ld::launch_final_combine_bn(P, acc, nv.bn, gM, 1.0 + 2.0 * gM, out, s);
+  ld::launch_final_combine_bn(P, acc, nv.bn, nv.bn_err, gM, 1.0 + 2.0 * gM, out, s);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? LD_OK : LD_ERR_CUDA;
 }

@@ -1343,9 +1343,10 @@ ld_status build_tc_net(const std::vector<LayerDev>& Ls, TcNet* out) {
   }
   if (total == 0) return LD_ERR_UNSUPPORTED;
   void* d = nullptr;
-  if (cudaMalloc(&d, total) != cudaSuccess) {
+  const cudaError_t e = dev_malloc(&d, total);
+  if (e != cudaSuccess) {
     cudaGetLastError();
-    return LD_ERR_NOMEM;
+    return e == cudaErrorMemoryAllocation ? LD_ERR_NOMEM : LD_ERR_CUDA;
   }
   char* base = static_cast<char*>(d);
   for (int k = 0; k < n - 1; ++k) {

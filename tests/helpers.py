@@ -86,3 +86,27 @@ def oracle_lists(net, pb, rows=None):
     ub = oracle.layer_lists(net, pb["ubk"][prop].astype(np.float64))
     lb, ub, empty = oracle.apply_masks(net, lb, ub, masks)
     return L0, U0, lb, ub, empty
+
+
+def near_tie_mask(on, L0, U0, lbs, ubs, rho, sol, rel_tol=5e-5):
+    """Decisions an FP32 evaluation may legitimately take differently from
+    the FP64 oracle: those whose deciding quantity is within rel_tol of its
+    threshold, relative to the magnitude of the terms that produce it.
+    Returns (box near-ties [B, n0], list of per-layer near-ties 1..n-1)."""
+    def absg_of(k):
+        nxt = -np.ones((rho[1].shape[0], 1)) if k + 1 == on.n else rho[k + 1]
+        return np.asarray((abs(on.L(k + 1).mat).T @ np.abs(nxt).T).T)
+    box = np.abs(sol.g[0]) < rel_tol * (absg_of(0) + 1e-30)
+    ties = [None]
+    for k in range(1, on.n):
+        r, g, l, u = rho[k], sol.g[k], lbs[k], ubs[k]
+        absg = absg_of(k)
+        mag = (np.abs(r) + absg + 1e-30) * (np.maximum(np.abs(l), np.abs(u)) + 1e-30)
+        cls = oracle.classify(l, u)
+        best0 = np.minimum(r * l, 0.0)
+        vuu = (r - g) * u
+        gap = best0 - oracle.TIE_REL * (np.abs(r) + np.abs(g)) * np.maximum(np.abs(l), np.abs(u)) - vuu
+        amb_tie = np.abs(gap) < rel_tol * mag
+        pas_tie = np.abs(r - g) < rel_tol * (np.abs(r) + absg + 1e-30)
+        ties.append(np.where(cls == 2, amb_tie, np.where(cls == 1, pas_tie, False)))
+    return box, ties

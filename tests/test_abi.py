@@ -87,3 +87,24 @@ def test_calls_reject_null_handle_on_host(lib):
     assert lib.ld_dual_supergradient(None, *([None] * 4), 1, None, None, 1, *([None] * 5)) == binding.LD_ERR_ARG
     assert lib.ld_net_destroy(None) == binding.LD_ERR_ARG
     assert lib.ld_net_reserve(None, 4) == binding.LD_ERR_ARG
+
+
+def test_allocation_failure_injection_on_host(lib):
+    """The failure-injection hook makes the library's first device allocation
+    fail on the host, before any CUDA allocator call: ld_net_create reports
+    the injected code (no GPU is needed to reach it)."""
+    W1 = np.ones((4, 3), np.float32)
+    b1 = np.zeros(4, np.float32)
+    W2 = np.ones((1, 4), np.float32)
+    b2 = np.zeros(1, np.float32)
+    arr = (binding.LayerDesc * 2)(_desc(0, 3, 1, 1, 4, 1, 1, 0, W1, b1), _desc(0, 4, 1, 1, 1, 1, 1, 0, W2, b2))
+    h = C.c_void_p()
+    try:
+        assert lib.ld_test_inject_alloc_failure(0, binding.LD_ERR_NOMEM) == binding.LD_OK
+        assert lib.ld_net_create(arr, 2, None, C.byref(h), None) == binding.LD_ERR_NOMEM
+        assert not h.value
+        assert lib.ld_test_inject_alloc_failure(0, binding.LD_ERR_CUDA) == binding.LD_OK
+        assert lib.ld_net_create(arr, 2, None, C.byref(h), None) == binding.LD_ERR_CUDA
+        assert lib.ld_test_inject_alloc_failure(0, binding.LD_ERR_ARG) == binding.LD_ERR_ARG
+    finally:
+        lib.ld_test_inject_alloc_failure(-1, 0)

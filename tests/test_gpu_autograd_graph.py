@@ -1,4 +1,6 @@
 """torch.autograd wrapper and CUDA-graph capture of the bound."""
+import dataclasses
+
 import numpy as np
 import pytest
 import torch
@@ -182,3 +184,30 @@ def test_deep_128_backward_matches_finite_differences():
     assert torch.allclose(lb0.grad, g["glb0"], rtol=1e-5, atol=1e-6)
     assert torch.allclose(ub0.grad, g["gub0"], rtol=1e-5, atol=1e-6)
     assert torch.allclose(params[2].grad.flatten(), g["gW"][woff[1]:woff[2]], rtol=1e-5, atol=1e-6)
+
+
+def test_changed_parameters_without_a_rebuilt_net_raise():
+    """The handle keeps its own weight copy: parameters changed in place after
+    the net was built must not give silently stale bounds and gradients."""
+    specs = synth.make_convnet("base")
+    l0, u0, c = synth.image_property(2)
+    net = ldb.Net(specs, margin=c)
+    lbk, ubk = ldb.ld_intermediate_bounds(net, l0[None], u0[None])
+    params = _params(specs)
+    out = lda.bound(net, l0[None], u0[None], lbk, ubk, params, n_iters=3)
+    assert torch.isfinite(out).all()
+    with torch.no_grad():
+        params[2].mul_(1.01)          # conv2 weights updated in place (e.g. an optimiser step)
+    with pytest.raises(lda.StaleParametersError):
+        lda.bound(net, l0[None], u0[None], lbk, ubk, params, n_iters=3)
+    wrong = _params(specs)
+    with torch.no_grad():
+        wrong[0].add_(1.0)
+    with pytest.raises(lda.StaleParametersError):
+        lda.bound(ldb.Net(specs, margin=c), l0[None], u0[None], lbk, ubk, wrong, n_iters=3)
+    # a rebuilt net with the new values is accepted
+    specs2 = [dataclasses.replace(s, W=p.detach().cpu().numpy(), b=q.detach().cpu().numpy())
+              for s, p, q in zip(specs, params[0::2], params[1::2])]
+    net2 = ldb.Net(specs2, margin=c)
+    out2 = lda.bound(net2, l0[None], u0[None], lbk, ubk, params, n_iters=3)
+    assert torch.isfinite(out2).all()

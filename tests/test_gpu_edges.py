@@ -68,3 +68,38 @@ def test_batch_beyond_limit_is_rejected_before_any_work():
         ldb.ld_bound(net, pb["l0"], pb["u0"], pb["lbk"], pb["ubk"], None, None, n_iters=1, B=B)
     assert e.value.code == ldb.LD_ERR_UNSUPPORTED
     assert net.sync_status() == ldb.LD_OK
+
+
+def test_injected_allocation_failures_leave_the_handle_usable():
+    """Failure detection on the allocation paths without a GPU fault: the
+    host-side hook fails one of the library's device allocations; the call
+    that made it returns LD_ERR_NOMEM (or LD_ERR_CUDA), and the handle still
+    bounds correctly afterwards (the workspace is allocated again)."""
+    pb = conv_problem("base", 8, depth=(0, 4), block=9)
+    args = (pb["l0"], pb["u0"], pb["lbk"], pb["ubk"], pb["prop"], pb["masks"])
+    ref = ldb.ld_bound(ldb.Net(pb["specs"]), *args, n_iters=3, opts=ldb.Options(engine="layerwise"))
+    try:
+        for after, code in ((0, ldb.LD_ERR_NOMEM), (3, ldb.LD_ERR_CUDA)):
+            ldb.inject_alloc_failure(after, code)
+            with pytest.raises(ldb.LDError) as e:
+                ldb.Net(pb["specs"])
+            assert e.value.code == code
+        net = ldb.Net(pb["specs"])
+        for code in (ldb.LD_ERR_NOMEM, ldb.LD_ERR_CUDA):
+            ldb.inject_alloc_failure(0, code)
+            with pytest.raises(ldb.LDError) as e:
+                net.reserve(64)
+            assert e.value.code == code
+            out = ldb.ld_bound(net, *args, n_iters=3, opts=ldb.Options(engine="layerwise"))
+            assert torch.equal(out, ref)
+        # the BF16 engine's own allocations (its shadow workspace and re-laid weights)
+        net.reserve(8)
+        ldb.inject_alloc_failure(0, ldb.LD_ERR_NOMEM)
+        with pytest.raises(ldb.LDError) as e:
+            ldb.ld_bound(net, *args, n_iters=3, opts=ldb.Options(precision="bf16"))
+        assert e.value.code == ldb.LD_ERR_NOMEM
+        out = ldb.ld_bound(net, *args, n_iters=3, opts=ldb.Options(precision="bf16"))
+        assert np.all(np.isfinite(out.cpu().numpy()) == np.isfinite(ref.cpu().numpy()))
+        assert net.sync_status() == ldb.LD_OK
+    finally:
+        ldb.inject_alloc_failure(-1)

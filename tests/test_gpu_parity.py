@@ -17,7 +17,7 @@ import torch
 import oracle
 from paper_2104_06718_gb300 import binding as ldb
 from paper_2104_06718_gb300 import synth
-from helpers import conv_problem, oracle_lists, outward_f32, oracle_net, tiny_problem
+from helpers import conv_problem, near_tie_mask, oracle_lists, outward_f32, oracle_net, tiny_problem
 
 pytestmark = pytest.mark.gpu
 
@@ -133,30 +133,6 @@ def test_nonfinite_box_sets_status(base16):
 
 
 # ------------------------------------------------------------------ inner minimisation (rows a2, a3, a4)
-
-def near_tie_mask(on, L0, U0, lbs, ubs, rho, sol, rel_tol=5e-5):
-    """Decisions an FP32 evaluation may legitimately take differently from
-    the FP64 oracle: those whose deciding quantity is within rel_tol of its
-    threshold, relative to the magnitude of the terms that produce it.
-    Returns (box near-ties [B, n0], list of per-layer near-ties 1..n-1)."""
-    def absg_of(k):
-        nxt = -np.ones((rho[1].shape[0], 1)) if k + 1 == on.n else rho[k + 1]
-        return np.asarray((abs(on.L(k + 1).mat).T @ np.abs(nxt).T).T)
-    box = np.abs(sol.g[0]) < rel_tol * (absg_of(0) + 1e-30)
-    ties = [None]
-    for k in range(1, on.n):
-        r, g, l, u = rho[k], sol.g[k], lbs[k], ubs[k]
-        absg = absg_of(k)
-        mag = (np.abs(r) + absg + 1e-30) * (np.maximum(np.abs(l), np.abs(u)) + 1e-30)
-        cls = oracle.classify(l, u)
-        best0 = np.minimum(r * l, 0.0)
-        vuu = (r - g) * u
-        gap = best0 - oracle.TIE_REL * (np.abs(r) + np.abs(g)) * np.maximum(np.abs(l), np.abs(u)) - vuu
-        amb_tie = np.abs(gap) < rel_tol * mag
-        pas_tie = np.abs(r - g) < rel_tol * (np.abs(r) + absg + 1e-30)
-        ties.append(np.where(cls == 2, amb_tie, np.where(cls == 1, pas_tie, False)))
-    return box, ties
-
 
 def check_inner(pb, rho_flat):
     """Compare q, the supergradient and the vertex codes at one rho."""
@@ -412,11 +388,55 @@ def test_margin_folding_matches_prefolded():
     lbk2, ubk2 = ldb.ld_intermediate_bounds(b, l0, u0)
     assert torch.equal(lbk, lbk2) and torch.equal(ubk, ubk2)
     # the engine is fixed: the autotuner times each net on its own and the
-    # engines differ in the summation order of the forward FC pass
+    # engines differ in the summation order of the forward FC pass.  The
+    # iterations use the fold rounded to FP32 in both nets (bitwise the same
+    # duals); the FP64 final bound of the margin net uses the FP64 fold, so
+    # its bound differs from the prefolded net's by the rounding of the row.
     for opts in (ldb.Options(engine="layerwise"), ldb.Options(engine="fused", tile=1), ldb.Options(precision="bf16")):
-        oa = ldb.ld_bound(a, l0, u0, lbk, ubk, n_iters=10, B=4, opts=opts)
-        ob = ldb.ld_bound(b, l0, u0, lbk, ubk, n_iters=10, B=4, opts=opts)
-        assert torch.equal(oa, ob)
+        oa, ra = ldb.ld_bound(a, l0, u0, lbk, ubk, n_iters=10, B=4, opts=opts, return_rho=True)
+        ob, rb = ldb.ld_bound(b, l0, u0, lbk, ubk, n_iters=10, B=4, opts=opts, return_rho=True)
+        assert torch.equal(ra, rb)
+        assert np.max(rel(oa.cpu().numpy(), ob.cpu().numpy())) < 1e-6
+
+
+@pytest.mark.parametrize("name", ["base", "wide", "deep"])
+def test_margin_fold_bound_is_sound_for_the_property_itself(name):
+    """The canonical form folds the property c into the last layer (Sec. 2.1).
+    The FP64 final bound must bound c^T (W x + b) itself, not a rounded copy
+    of the folded row: against the oracle built from the unfolded float32 net
+    with the margin folded in FP64, at the same rho (weak duality, Sec. 3.1),
+    with random margins whose fold is a real sum, and the property margin
+    e_gt - e_target.  The IBP output bound of the folded layer likewise."""
+    specs = synth.make_convnet(name)
+    l0, u0, c_prop = synth.image_property(4)
+    rng = np.random.default_rng(11)
+    margins = [c_prop] + [rng.standard_normal(specs[-1].W.shape[0]).astype(np.float32) for _ in range(2)]
+    on0 = oracle_net(specs, margin=margins[0])
+    lb, ub = oracle.ibp_bounds(on0, l0[None].astype(np.float64), u0[None].astype(np.float64))
+    lbk, ubk = outward_f32(flat(on0, lb), flat(on0, ub))
+    amb = np.nonzero((lbk[0] < 0) & (ubk[0] > 0))[0]
+    B = 12
+    masks = synth.split_masks(lbk.shape[1], B, amb, (0, 8), block=13)
+    rho = synth.random_duals([lbk.shape[1]], B, seed=31, scale=0.05)[0]
+    for c in margins:
+        net = ldb.Net(specs, margin=c)
+        on = oracle_net(specs, margin=c)
+        out = ldb.ld_bound(net, l0[None], u0[None], lbk, ubk, None, masks, n_iters=0, rho_in=rho).cpu().numpy()
+        L0 = np.repeat(l0[None].astype(np.float64), B, axis=0)
+        U0 = np.repeat(u0[None].astype(np.float64), B, axis=0)
+        lbs = oracle.layer_lists(on, np.repeat(lbk.astype(np.float64), B, axis=0))
+        ubs = oracle.layer_lists(on, np.repeat(ubk.astype(np.float64), B, axis=0))
+        lbs, ubs, empty = oracle.apply_masks(on, lbs, ubs, masks)
+        q = oracle.dual_value(on, L0, U0, lbs, ubs, oracle.layer_lists(on, rho.astype(np.float64)))
+        ok = ~empty
+        assert np.all(np.isinf(out[empty]))
+        assert np.all(out[ok] <= q[ok] + 1e-12 * np.maximum(np.abs(q[ok]), 1)), "bound above the property's dual"
+        assert np.max(rel(out[ok], q[ok])) < 1e-9
+        _, _, out_lb = ldb.ld_intermediate_bounds(net, l0, u0, want_output_lb=True)
+        lb_c, _ = oracle.ibp_bounds(on, l0[None].astype(np.float64), u0[None].astype(np.float64))
+        ibp = lb_c[on.n][0, 0]
+        assert out_lb.item() <= ibp + 1e-12 * max(abs(ibp), 1.0)
+        assert rel(out_lb.item(), ibp) < 1e-4
 
 
 # ------------------------------------------------------------------ Danskin adjoint (row a6)

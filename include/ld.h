@@ -178,6 +178,41 @@ ld_status ld_intermediate_bounds_split(ld_net* net, const float* lb0, const floa
                                        const int32_t* prop_of_subdomain, const int8_t* split_masks, int32_t B,
                                        float* lbk, float* ubk, void* stream);
 
+/* Propagation-based intermediate bounds (Sec. 2.2.1, Sec. 2.2.3): CROWN, WK
+ * or, per layer, the better of the two (the layer-wise best the experiments
+ * use, Sec. 7.2; root bounds as BaDNB, Sec. 5.1.1).  The bound of neuron i of
+ * layer k is the lower bound of +-x_hat_k[i] obtained by substituting the
+ * objective backwards through layers k..1 with every ReLU replaced by the
+ * upper relaxation of Eq. (slopes-biases) and a linear lower relaxation:
+ * slope 1[u >= -l] for CROWN (footnote of Sec. 4.2), the upper slope
+ * u/(u-l) for WK (the relaxation quoted in Sec. 4.1).  Layer 1 is the exact
+ * range of its affine map over the box; layer k >= 2 is bounded with the
+ * (best, clamped) bounds of layers 1..k-1.
+ *   Rows: n_rows output rows, each bounded over one box.  prop_of_row [device]
+ *   NULL or [n_rows] int32: the box of each row (out-of-range entries are
+ *   clamped); with NULL, n_rows == n_props gives one row per box (root
+ *   bounds) and n_props == 1 bounds every row over box 0.
+ *   split_masks [device] NULL or [n_rows, N] int8: every hidden layer's
+ *   bounds of a row are clamped by its mask (+1 => l <- max(l,0), -1 =>
+ *   u <- min(u,0), Sec. 2.3.2) before they bound the layers after it (the
+ *   bounds recomputed per subdomain after its splits); NULL = no clamp.
+ *   rules: LD_IB_CROWN, LD_IB_WK or both (LD_IB_CROWN | LD_IB_WK, the
+ *   layer-wise best).
+ *   lb0, ub0 [device] [n_props, n_0] float boxes; lbk, ubk [device]
+ *   [n_rows, N] float outputs, rounded outward: every FP32 pass's rounding
+ *   error is bounded a priori and subtracted, so they contain the exact
+ *   CROWN / WK bounds (and hence every reachable pre-activation).
+ * The call grows a workspace of its own on first use (up to ~24 bytes per
+ * objective row, rows = n_rows x rules x 2 x the widest layer, plus 256 MB
+ * of coefficient buffers), like ld_net_reserve; LD_ERR_NOMEM if that fails.
+ * Errors: LD_ERR_ARG (nulls, n_props < 1, n_rows < 0, bad rules, prop NULL
+ * with n_rows != n_props and n_props > 1); LD_ERR_UNSUPPORTED (n_rows >
+ * 65535); LD_ERR_NONFINITE via the status word as ld_intermediate_bounds. */
+enum { LD_IB_CROWN = 1, LD_IB_WK = 2 };
+ld_status ld_intermediate_bounds_propagated(ld_net* net, const float* lb0, const float* ub0, int32_t n_props,
+                                            const int32_t* prop_of_row, const int8_t* split_masks, int32_t n_rows,
+                                            int32_t rules, float* lbk, float* ubk, void* stream);
+
 /* LD lower bounds for B subdomains after n_iters Adam iterations
  * (Algorithm 1; Eq. box_bounds_sol and Eq. min-pk for the inner minimum).
  *   lb0, ub0 [device] [n_props, n_0] float boxes; lbk, ubk [device]

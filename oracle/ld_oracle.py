@@ -324,6 +324,53 @@ class ExactPasses:
         return self.net.L(k).forward(x)
 
 
+def relu_subproblem_argmin(r, c, l, u):
+    """argmin of r * x_hat_B - c * x over the Planet hull of one ReLU layer
+    (Sec. 3.2.2, Eq. (min-pk)), elementwise.  Returns (x_hat_B, x, vertex
+    code): 0 -> (l,0) / lower end, 1 -> (0,0), 2 -> (u,u) / upper end."""
+    cls = classify(l, u)
+    xb = np.zeros_like(r)
+    xk = np.zeros_like(r)
+    code = np.zeros(r.shape, dtype=np.int8)
+    # blocking: x = 0, minimise r * x_hat_B over [l, u]
+    blk = cls == 0
+    xb[blk] = box_argmin(r, l, u)[blk]
+    code[blk] = np.where(r <= 0, 2, 0)[blk]
+    # passing: x = x_hat_B, minimise (r - c) * x_hat_B over [l, u]; the
+    # lower end needs r - c > TIE_REL (|r| + |c|): at the CROWN point
+    # r = c exactly for every passing ReLU, and rounding must not decide
+    pas = cls == 1
+    low = (r - c) > TIE_REL * (np.abs(r) + np.abs(c))
+    yp = np.where(low, l, u)
+    xb[pas] = yp[pas]
+    xk[pas] = yp[pas]
+    code[pas] = np.where(low, 0, 2)[pas]
+    # ambiguous: the three vertices of Fig. (relucvx), Eq. (min-pk)
+    amb = cls == 2
+    v_l0 = r * l                  # vertex (l, 0)
+    v_00 = np.zeros_like(r)       # vertex (0, 0)
+    v_uu = (r - c) * u            # vertex (u, u)
+    best = v_l0.copy()
+    choice = np.zeros(r.shape, dtype=np.int8)
+    take = v_00 < best
+    best = np.where(take, v_00, best)
+    choice[take] = 1
+    # (u,u) must win by more than TIE_REL of the magnitudes that enter
+    # the comparison, (|r| + |g|) * max(|l|, u): the CROWN point of
+    # Prop. 3 puts (l,0) and (u,u) at an exact tie for every ambiguous
+    # ReLU with lambda > 0, and (r - g) * u is then a cancellation whose
+    # rounding error scales with |r| + |g|; rounding must not decide it.
+    margin = TIE_REL * (np.abs(r) + np.abs(c)) * np.maximum(np.abs(l), np.abs(u))
+    take = v_uu < best - margin
+    choice[take] = 2
+    xb_amb = np.select([choice == 0, choice == 1], [l, np.zeros_like(l)], u)
+    xk_amb = np.where(choice == 2, u, 0.0)
+    xb[amb] = xb_amb[amb]
+    xk[amb] = xk_amb[amb]
+    code[amb] = choice[amb]
+    return xb, xk, code
+
+
 def inner_minimisation(net: Net, l0, u0, lb, ub, rho, passes=None) -> InnerSolution:
     """Solve the decomposed inner problem of Eq. (nonprox_problem) at rho.
 
@@ -346,47 +393,7 @@ def inner_minimisation(net: Net, l0, u0, lb, ub, rho, passes=None) -> InnerSolut
     vertex = [None]
     # Pk (Sec. 3.2.2): minimise rho_k x_hat_B,k - g_k x_k over the ReLU hull.
     for k in range(1, n):
-        r, c, l, u = rho[k], g[k], lb[k], ub[k]
-        cls = classify(l, u)
-        xb = np.zeros_like(r)
-        xk = np.zeros_like(r)
-        code = np.zeros(r.shape, dtype=np.int8)
-        # blocking: x = 0, minimise r * x_hat_B over [l, u]
-        blk = cls == 0
-        xb[blk] = box_argmin(r, l, u)[blk]
-        code[blk] = np.where(r <= 0, 2, 0)[blk]
-        # passing: x = x_hat_B, minimise (r - c) * x_hat_B over [l, u]; the
-        # lower end needs r - c > TIE_REL (|r| + |c|): at the CROWN point
-        # r = c exactly for every passing ReLU, and rounding must not decide
-        pas = cls == 1
-        low = (r - c) > TIE_REL * (np.abs(r) + np.abs(c))
-        yp = np.where(low, l, u)
-        xb[pas] = yp[pas]
-        xk[pas] = yp[pas]
-        code[pas] = np.where(low, 0, 2)[pas]
-        # ambiguous: the three vertices of Fig. (relucvx), Eq. (min-pk)
-        amb = cls == 2
-        v_l0 = r * l                  # vertex (l, 0)
-        v_00 = np.zeros_like(r)       # vertex (0, 0)
-        v_uu = (r - c) * u            # vertex (u, u)
-        best = v_l0.copy()
-        choice = np.zeros(r.shape, dtype=np.int8)
-        take = v_00 < best
-        best = np.where(take, v_00, best)
-        choice[take] = 1
-        # (u,u) must win by more than TIE_REL of the magnitudes that enter
-        # the comparison, (|r| + |g|) * max(|l|, u): the CROWN point of
-        # Prop. 3 puts (l,0) and (u,u) at an exact tie for every ambiguous
-        # ReLU with lambda > 0, and (r - g) * u is then a cancellation whose
-        # rounding error scales with |r| + |g|; rounding must not decide it.
-        margin = TIE_REL * (np.abs(r) + np.abs(c)) * np.maximum(np.abs(l), np.abs(u))
-        take = v_uu < best - margin
-        choice[take] = 2
-        xb_amb = np.select([choice == 0, choice == 1], [l, np.zeros_like(l)], u)
-        xk_amb = np.where(choice == 2, u, 0.0)
-        xb[amb] = xb_amb[amb]
-        xk[amb] = xk_amb[amb]
-        code[amb] = choice[amb]
+        xb, xk, code = relu_subproblem_argmin(rho[k], g[k], lb[k], ub[k])
         x.append(xk)
         xB.append(xb)
         vertex.append(code)

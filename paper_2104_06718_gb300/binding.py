@@ -23,13 +23,15 @@ LD_LAYER_FC, LD_LAYER_CONV = 0, 1
 LD_INIT_ZERO, LD_INIT_CROWN, LD_INIT_GIVEN = 0, 1, 2
 LD_PREC_FP32, LD_PREC_BF16 = 0, 1
 LD_ENGINE_AUTO, LD_ENGINE_LAYERWISE, LD_ENGINE_FUSED = 0, 1, 2
+LD_IB_CROWN, LD_IB_WK = 1, 2
+IB_RULES = {"crown": LD_IB_CROWN, "wk": LD_IB_WK, "best": LD_IB_CROWN | LD_IB_WK}
 
 EXPORTED = [
     "ld_opts_default", "ld_status_str", "ld_net_create", "ld_net_destroy", "ld_net_sizes", "ld_net_reserve",
     "ld_net_sync_status", "ld_selftest_wait_timeout", "ld_intermediate_bounds", "ld_intermediate_bounds_split",
     "ld_bound", "ld_dual_supergradient", "ld_bound_backward",
     "ld_net_profile", "ld_net_profile_read", "ld_launch_count", "ld_net_tuned", "ld_final_bound_noalloc",
-    "ld_test_inject_alloc_failure",
+    "ld_test_inject_alloc_failure", "ld_intermediate_bounds_propagated",
 ]
 PHASES = {"iter": 0, "final": 1, "init": 2, "ibp": 3, "backward": 4}
 
@@ -87,6 +89,7 @@ def load_library(path: str = LIB_PATH):
     lib.ld_net_tuned.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
     lib.ld_final_bound_noalloc.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, i32, vp, vp, vp]
     lib.ld_test_inject_alloc_failure.argtypes = [i32, i32]
+    lib.ld_intermediate_bounds_propagated.argtypes = [vp, vp, vp, i32, vp, vp, i32, i32, vp, vp, vp]
     for name in EXPORTED:
         if name not in ("ld_opts_default", "ld_status_str"):
             getattr(lib, name).restype = C.c_int
@@ -290,6 +293,28 @@ def ld_intermediate_bounds_split(net: Net, lb0, ub0, masks, prop=None):
     _check(net._lib.ld_intermediate_bounds_split(net.handle, _ptr(lb0), _ptr(ub0), lb0.shape[0], _ptr(prop),
                                                  _ptr(masks), B, _ptr(lbk), _ptr(ubk), _stream()),
            "ld_intermediate_bounds_split")
+    return lbk, ubk
+
+
+def ld_intermediate_bounds_propagated(net: Net, lb0, ub0, rules: str = "best", masks=None, prop=None,
+                                      n_rows: int | None = None):
+    """CROWN / WK / layer-wise best ("best") intermediate bounds ([R, N],
+    [R, N]) float32, outward rounded.  Without masks and prop: one row per
+    box (root bounds).  With masks [B, N] (and prop [B] when there are several
+    boxes): bounds recomputed per subdomain after its splits, already clamped."""
+    lb0 = _dev(lb0, torch.float32)
+    ub0 = _dev(ub0, torch.float32)
+    if lb0.dim() == 1:
+        lb0, ub0 = lb0[None], ub0[None]
+    masks = None if masks is None else _dev(masks, torch.int8)
+    prop = None if prop is None else _dev(prop, torch.int32)
+    if n_rows is None:
+        n_rows = masks.shape[0] if masks is not None else (prop.shape[0] if prop is not None else lb0.shape[0])
+    lbk = torch.empty((n_rows, net.N), dtype=torch.float32, device="cuda")
+    ubk = torch.empty_like(lbk)
+    _check(net._lib.ld_intermediate_bounds_propagated(net.handle, _ptr(lb0), _ptr(ub0), lb0.shape[0], _ptr(prop),
+                                                      _ptr(masks), int(n_rows), IB_RULES[rules], _ptr(lbk), _ptr(ubk),
+                                                      _stream()), "ld_intermediate_bounds_propagated")
     return lbk, ubk
 
 

@@ -74,6 +74,9 @@ struct ld_net {
   int tc_B = -1, tc_props = -1;
   uint16_t *xh = nullptr, *rh = nullptr;
   float* c1 = nullptr;
+  // workspace of the propagation-based intermediate bounds (grown on demand)
+  void* ib_ws = nullptr;
+  size_t ib_bytes = 0;
   // the per-iteration launches of the layerwise and BF16 engines, captured
   // into one executable graph (re-captured and updated in place each call)
   bool graphs = true;
@@ -847,6 +850,7 @@ ld_status ld_net_destroy(ld_net* net) {
   if (net->iter_exec) cudaGraphExecDestroy(net->iter_exec);
   if (net->cap_stream) cudaStreamDestroy(net->cap_stream);
   if (net->tc_ws) cudaFree(net->tc_ws);
+  if (net->ib_ws) cudaFree(net->ib_ws);
   ld::free_tc_net(&net->tc);
   if (net->d_W) cudaFree(net->d_W);
   if (net->d_Wx) cudaFree(net->d_Wx);
@@ -926,6 +930,81 @@ ld_status ld_intermediate_bounds_split(ld_net* net, const float* lb0, const floa
     const int in_stride = k == 1 ? (int)net->n0 : (int)net->N;
     ld::launch_ibp_layer(L, k == 1, 0, B, lin, uin, in_stride, lbk + L.r_out_off, ubk + L.r_out_off, (int)net->N,
                          nullptr, net->d_status, s, rows);
+  }
+  return last_error();
+}
+
+ld_status ld_intermediate_bounds_propagated(ld_net* net, const float* lb0, const float* ub0, int32_t n_props,
+                                            const int32_t* prop, const int8_t* masks, int32_t n_rows, int32_t rules,
+                                            float* lbk, float* ubk, void* stream) {
+  if (!net || !lb0 || !ub0 || n_props < 1 || n_rows < 0 || (n_rows > 0 && (!lbk || !ubk))) return LD_ERR_ARG;
+  if (rules < LD_IB_CROWN || rules > (LD_IB_CROWN | LD_IB_WK)) return LD_ERR_ARG;
+  if (!prop && n_rows != n_props && n_props != 1) return LD_ERR_ARG;
+  if (n_rows > 65535) return LD_ERR_UNSUPPORTED;
+  if (n_rows == 0) return LD_OK;
+  cudaStream_t s = S(stream);
+  PhaseMark pm(net, LD_PHASE_IBP, s);
+  const int N = (int)net->N, n = net->n;
+  // layer 1: the exact range of an affine map over the box (its interval bound), clamped
+  ld::IbpRows rows;
+  if (prop) {
+    rows.in_row = prop;
+    rows.n_in_rows = n_props;
+  } else if (n_rows != n_props) {
+    rows.n_in_rows = 1;
+  }
+  rows.mask = masks;
+  rows.mask_stride = N;
+  const LayerDev& L1 = layer(net, 1);
+  ld::launch_ibp_layer(L1, 1, 0, n_rows, lb0, ub0, (int)net->n0, lbk + L1.r_out_off, ubk + L1.r_out_off, N, nullptr,
+                       net->d_status, s, rows);
+  if (n <= 2) return last_error();
+  const int n_rules = rules == (LD_IB_CROWN | LD_IB_WK) ? 2 : 1;
+  size_t max_rows = 0;
+  int max_w = 1;
+  for (int k = 1; k < n; ++k) max_w = std::max(max_w, layer(net, k).n_out);
+  for (int k = 2; k < n; ++k) max_rows = std::max(max_rows, (size_t)n_rows * ld::ib_rows_per_owner(net->L, k, n_rules));
+  const size_t mu_cap = (size_t)256 << 20;   // both coefficient buffers together
+  int64_t chunk = (int64_t)std::max<size_t>(1, mu_cap / (2 * sizeof(float) * (size_t)max_w));
+  if ((size_t)chunk > max_rows) chunk = (int64_t)max_rows;
+  const size_t acc_b = align256(24 * max_rows), mu_b = align256(sizeof(float) * (size_t)chunk * max_w);
+  const size_t need = acc_b + 2 * mu_b;
+  if (need > net->ib_bytes) {
+    cudaDeviceSynchronize();
+    if (net->ib_ws) cudaFree(net->ib_ws);
+    net->ib_ws = nullptr;
+    net->ib_bytes = 0;
+    void* p = nullptr;
+    const cudaError_t e = ld::dev_malloc(&p, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return cuda_status(e);
+    }
+    net->ib_ws = p;
+    net->ib_bytes = need;
+  }
+  char* c = static_cast<char*>(net->ib_ws);
+  ld::IbLayerArgs A{};
+  A.n_owners = n_rows;
+  A.n_rules = n_rules;
+  A.rule0 = rules == LD_IB_WK ? 1 : 0;
+  A.lbk = lbk;
+  A.ubk = ubk;
+  A.N = N;
+  A.l0 = lb0;
+  A.u0 = ub0;
+  A.n0 = (int)net->n0;
+  A.box_row = prop;
+  A.n_boxes = n_props;
+  A.mask = masks;
+  A.acc = reinterpret_cast<double*>(c);
+  A.mu_a = reinterpret_cast<float*>(c + acc_b);
+  A.mu_b = reinterpret_cast<float*>(c + acc_b + mu_b);
+  A.chunk_rows = chunk;
+  A.gamma_M = ld::final_gamma(2.0 * (double)(net->N + net->n0) + 8.0);
+  for (int k = 2; k < n; ++k) {
+    const cudaError_t e = ld::launch_ib_layer(net->L, k, A, s);
+    if (e != cudaSuccess) return cuda_status(e);
   }
   return last_error();
 }

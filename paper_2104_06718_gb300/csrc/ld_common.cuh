@@ -412,6 +412,32 @@ void launch_ibp_layer(const LayerDev& L, int first, int last, int n_rows, const 
                       int in_stride, float* lout, float* uout, int out_stride, double* out_lb, int* status,
                       cudaStream_t s, const IbpRows& rows = IbpRows{});
 
+// Propagation-based intermediate bounds: CROWN / WK / layer-wise best (ld_ib.cu).
+// Rows ("owners") are properties (root bounds) or subdomains; each owner's
+// bounds of layers 1..k-1 are read from lbk/ubk (already clamped) and layer
+// k's are written there.
+struct IbLayerArgs {
+  int n_owners;
+  int n_rules;              // 1 or 2
+  int rule0;                // rule of rule index 0: 0 CROWN, 1 WK (index 1 is WK)
+  float* lbk;               // [owners, N]
+  float* ubk;
+  int N;
+  const float* l0;          // [n_boxes, n0]
+  const float* u0;
+  int n0;
+  const int32_t* box_row;   // [owners] box of each owner, or nullptr (owner = box row; box 0 with one box)
+  int n_boxes;
+  const int8_t* mask;       // [owners, N] split masks or nullptr
+  double* acc;              // [owners x rules x 2 x n_k, 3]
+  float* mu_a;              // [chunk_rows, max hidden width] x 2
+  float* mu_b;
+  int64_t chunk_rows;
+  double gamma_M;           // FP64 constant of the per-row sums
+};
+size_t ib_rows_per_owner(const std::vector<LayerDev>& Ls, int k, int n_rules);
+cudaError_t launch_ib_layer(const std::vector<LayerDev>& Ls, int k, const IbLayerArgs& A, cudaStream_t s);
+
 // FP64 final bound (ld_final.cu).
 struct FinalAcc {
   double* slots;       // [B, n_slots, 3]: per-slot sum of term values, of their

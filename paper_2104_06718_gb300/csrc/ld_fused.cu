@@ -543,9 +543,12 @@ __device__ void conv_fwd_blocked(const Ctx<S, NT>& c, const LayerDev& L, const F
 // Transposed conv of layer L = layer k+1 into layer k, blocked, split by
 // stride phase: for rows yy = ry + ST*qy the valid taps are i = i0 + ST*a with
 // i0 = (ry + pad) mod ST, reading rho row y = qy + dy0 - a with
-// dy0 = (ry + pad - i0) / ST (likewise in x).  Item = (s, phase, qy, qx,
-// group of G input channels); the thread computes rows qy and qy + qh/2 of
-// column qx (consecutive lanes: consecutive columns of full rows).
+// dy0 = (ry + pad - i0) / ST (likewise in x).  Item = (s, ry, group of G input
+// channels, qy, rx, qx), qx fastest; the thread computes rows qy and
+// qy + qh/2 of column qx.  With the x phase second-fastest, the lanes of a
+// warp that differ in rx read the same rho row one word apart and write
+// consecutive columns of a full output row (the rows qy of a warp would
+// otherwise wrap onto the same shared-memory banks).
 template <int KH, int KW, int ST, int G, int S, int NT>
 __device__ void conv_t_blocked(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, int k, const Team& tm) {
   if (tm.tid < 0) return;
@@ -558,14 +561,14 @@ __device__ void conv_t_blocked(const Ctx<S, NT>& c, const LayerDev& L, const Fus
     int r = e, q = div_of(r, d_qw);
     const int qx = r - q * qw;
     r = q;
+    const int rx = r % ST;
+    r /= ST;
     q = div_of(r, d_hh);
     const int qy = r - q * hh;
     r = q;
     q = div_of(r, d_ncg);
     const int cg = r - q * ncg;
     r = q;
-    const int rx = r % ST;
-    r /= ST;
     const int ry = r % ST;
     const int s = r / ST;
     const int i0 = (ry + L.pad) % ST, j0 = (rx + L.pad) % ST;

@@ -242,6 +242,48 @@ ld_status ld_bound(ld_net* net, const float* lb0, const float* ub0, const float*
                    const float* rho_in, float* rho_out, float* adam_mv, double* out,
                    void* stream);
 
+/* Options of the proximal solver.  Defaults (ld_prox_opts_default): the
+ * incomplete-verification setting of Sec. 7.2 -- proximal weights eta
+ * increased linearly from 10 to 500 over the iterations, momentum mu = 0.3
+ * (App. D), J = 2 Frank-Wolfe sweeps per iteration; CROWN start (Prop. 3);
+ * FP64 final bound.  The branch-and-bound setting of Sec. 8.2 is eta0 =
+ * eta_end = 100 and mu = 0. */
+typedef struct {
+  float eta0;          /* weight eta of the proximal terms at iteration 0     */
+  float eta_end;       /* ... at the last iteration (linear in between)       */
+  float mu;            /* momentum of the dual update, in [0, 1)              */
+  int32_t J;           /* block-coordinate Frank-Wolfe sweeps per iteration   */
+  int32_t init;        /* LD_INIT_*: starting duals (GIVEN reads rho_in)      */
+  int32_t fp64_final;  /* as ld_opts                                          */
+} ld_prox_opts;
+
+void ld_prox_opts_default(ld_prox_opts* opts);
+
+/* LD lower bounds for B subdomains after n_iters iterations of the proximal
+ * solver (Sec. 3.3, Algorithm 2): the method of multipliers on the dual of
+ * Eq. (nonprox_problem), whose primal step minimises the Augmented
+ * Lagrangian of Eq. (z_updates) approximately by J sweeps of block-coordinate
+ * Frank-Wolfe over the layer-pair blocks (x_hat_B,k, x_hat_A,k+1), k = 0..n-1,
+ * each with the closed-form optimal step of Eq. (optimal-gamma-gauss); the
+ * conditional gradient of a block is the inner minimisation of P_k at the
+ * Augmented Lagrangian's duals lambda + (x_hat_B - x_hat_A) / eta (Sec.
+ * 3.3.2).  The dual update is Eq. (momentum_updates) (mu = 0: Eq.
+ * (lambda_updates)).  The primal starts at the inner minimiser of q at the
+ * initial duals.  Returned: q at the final duals, in FP64 with outward slack
+ * as ld_bound (a valid lower bound, weak duality).
+ *   Arguments as ld_bound; opts [host] NULL for defaults; rho_in [device]
+ *   [B, N] read with init GIVEN; rho_out [device] NULL or [B, N]: the final
+ *   duals.  Each iteration runs the transposed and forward passes of every
+ *   layer J times (twice the passes of a supergradient iteration for J = 2).
+ *   The call grows a workspace of its own (12 B per ReLU and subdomain) on
+ *   first use; LD_ERR_NOMEM if that fails.
+ * Errors: as ld_bound; LD_ERR_ARG for eta <= 0, mu outside [0, 1), J outside
+ * [1, 64]. */
+ld_status ld_bound_proximal(ld_net* net, const float* lb0, const float* ub0, const float* lbk,
+                            const float* ubk, int32_t n_props, const int32_t* prop_of_subdomain,
+                            const int8_t* split_masks, int32_t B, int32_t n_iters, const ld_prox_opts* opts,
+                            const float* rho_in, float* rho_out, double* out, void* stream);
+
 /* One inner minimisation at a given rho, in FP32, without any update:
  * q(rho) (Eq. nonprox_problem), the supergradient x_hat_B - x_hat_A
  * (Algorithm 1) and the chosen vertex per ReLU.

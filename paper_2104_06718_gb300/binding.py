@@ -31,7 +31,7 @@ EXPORTED = [
     "ld_net_sync_status", "ld_selftest_wait_timeout", "ld_intermediate_bounds", "ld_intermediate_bounds_split",
     "ld_bound", "ld_dual_supergradient", "ld_bound_backward",
     "ld_net_profile", "ld_net_profile_read", "ld_launch_count", "ld_net_tuned", "ld_final_bound_noalloc",
-    "ld_test_inject_alloc_failure", "ld_intermediate_bounds_propagated",
+    "ld_test_inject_alloc_failure", "ld_intermediate_bounds_propagated", "ld_prox_opts_default", "ld_bound_proximal",
 ]
 PHASES = {"iter": 0, "final": 1, "init": 2, "ibp": 3, "backward": 4}
 
@@ -53,6 +53,11 @@ class Opts(C.Structure):
                 ("eps", C.c_float), ("init", C.c_int32), ("precision", C.c_int32), ("fp64_final", C.c_int32),
                 ("t_offset", C.c_int32), ("t_total", C.c_int32), ("engine", C.c_int32), ("tile", C.c_int32),
                 ("cta_threads", C.c_int32)]
+
+
+class ProxOpts(C.Structure):
+    _fields_ = [("eta0", C.c_float), ("eta_end", C.c_float), ("mu", C.c_float), ("J", C.c_int32),
+                ("init", C.c_int32), ("fp64_final", C.c_int32)]
 
 
 _lib = None
@@ -90,8 +95,11 @@ def load_library(path: str = LIB_PATH):
     lib.ld_final_bound_noalloc.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, i32, vp, vp, vp]
     lib.ld_test_inject_alloc_failure.argtypes = [i32, i32]
     lib.ld_intermediate_bounds_propagated.argtypes = [vp, vp, vp, i32, vp, vp, i32, i32, vp, vp, vp]
+    lib.ld_prox_opts_default.argtypes = [C.POINTER(ProxOpts)]
+    lib.ld_prox_opts_default.restype = None
+    lib.ld_bound_proximal.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, i32, i32, C.POINTER(ProxOpts), vp, vp, vp, vp]
     for name in EXPORTED:
-        if name not in ("ld_opts_default", "ld_status_str"):
+        if name not in ("ld_opts_default", "ld_status_str", "ld_prox_opts_default"):
             getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -157,6 +165,24 @@ class Options:
                     int(self.fp64_final), self.t_offset, self.t_total,
                     {"auto": LD_ENGINE_AUTO, "layerwise": LD_ENGINE_LAYERWISE, "fused": LD_ENGINE_FUSED}[self.engine],
                     int(self.tile), int(self.cta_threads))
+
+
+@dataclass
+class ProxOptions:
+    """Proximal-solver options (ld_prox_opts): eta increased linearly from
+    eta0 to eta_end, momentum mu, J Frank-Wolfe sweeps (Sec. 7.2 defaults;
+    the branch-and-bound setting of Sec. 8.2 is eta0 = eta_end = 100, mu = 0)."""
+    eta0: float = 1e1
+    eta_end: float = 5e2
+    mu: float = 0.3
+    J: int = 2
+    init: str = "crown"
+    fp64_final: bool = True
+
+    def to_c(self) -> ProxOpts:
+        return ProxOpts(self.eta0, self.eta_end, self.mu, int(self.J),
+                        {"zero": LD_INIT_ZERO, "crown": LD_INIT_CROWN, "given": LD_INIT_GIVEN}[self.init],
+                        int(self.fp64_final))
 
 
 class Net:
@@ -349,6 +375,24 @@ def ld_bound(net: Net, lb0, ub0, lbk, ubk, prop=None, masks=None, n_iters: int =
     _check(net._lib.ld_bound(net.handle, _ptr(lb0), _ptr(ub0), _ptr(lbk), _ptr(ubk), lbk.shape[0], _ptr(prop),
                              _ptr(masks), B, int(n_iters), C.byref(oc), _ptr(rho_in), _ptr(rho_out), _ptr(adam_mv),
                              _ptr(out), _stream()), "ld_bound")
+    return (out, rho_out) if return_rho else out
+
+
+def ld_bound_proximal(net: Net, lb0, ub0, lbk, ubk, prop=None, masks=None, n_iters: int = 100,
+                      opts: ProxOptions | None = None, rho_in=None, B: int | None = None, return_rho: bool = False):
+    """Lower bounds [B] (float64) after n_iters iterations of the proximal
+    solver (Algorithm 2).  With return_rho, also the final duals [B, N]."""
+    lb0, ub0, lbk, ubk, prop, masks, B = _problem(lb0, ub0, lbk, ubk, prop, masks, B)
+    o = opts or ProxOptions()
+    if rho_in is not None and o.init != "given":
+        o = ProxOptions(**{**o.__dict__, "init": "given"})
+    rho_in = None if rho_in is None else _dev(rho_in, torch.float32)
+    out = torch.empty(B, dtype=torch.float64, device="cuda")
+    rho_out = torch.empty((B, net.N), dtype=torch.float32, device="cuda") if return_rho else None
+    oc = o.to_c()
+    _check(net._lib.ld_bound_proximal(net.handle, _ptr(lb0), _ptr(ub0), _ptr(lbk), _ptr(ubk), lbk.shape[0],
+                                      _ptr(prop), _ptr(masks), B, int(n_iters), C.byref(oc), _ptr(rho_in),
+                                      _ptr(rho_out), _ptr(out), _stream()), "ld_bound_proximal")
     return (out, rho_out) if return_rho else out
 
 

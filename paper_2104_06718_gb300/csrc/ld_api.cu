@@ -77,6 +77,9 @@ struct ld_net {
   // workspace of the propagation-based intermediate bounds (grown on demand)
   void* ib_ws = nullptr;
   size_t ib_bytes = 0;
+  // workspace of the proximal solver: x_hat_A and z_A [B, N + 1], lambda' [B, N]
+  void* prox_ws = nullptr;
+  int prox_B = -1;
   // the per-iteration launches of the layerwise and BF16 engines, captured
   // into one executable graph (re-captured and updated in place each call)
   bool graphs = true;
@@ -851,6 +854,7 @@ ld_status ld_net_destroy(ld_net* net) {
   if (net->cap_stream) cudaStreamDestroy(net->cap_stream);
   if (net->tc_ws) cudaFree(net->tc_ws);
   if (net->ib_ws) cudaFree(net->ib_ws);
+  if (net->prox_ws) cudaFree(net->prox_ws);
   ld::free_tc_net(&net->tc);
   if (net->d_W) cudaFree(net->d_W);
   if (net->d_Wx) cudaFree(net->d_Wx);
@@ -931,6 +935,151 @@ ld_status ld_intermediate_bounds_split(ld_net* net, const float* lb0, const floa
     ld::launch_ibp_layer(L, k == 1, 0, B, lin, uin, in_stride, lbk + L.r_out_off, ubk + L.r_out_off, (int)net->N,
                          nullptr, net->d_status, s, rows);
   }
+  return last_error();
+}
+
+void ld_prox_opts_default(ld_prox_opts* o) {
+  if (!o) return;
+  o->eta0 = 1e1f;
+  o->eta_end = 5e2f;
+  o->mu = 0.3f;
+  o->J = 2;
+  o->init = LD_INIT_CROWN;
+  o->fp64_final = 1;
+}
+
+namespace {
+
+ld_status ensure_prox_ws(ld_net* net, int B) {
+  if (B <= net->prox_B) return LD_OK;
+  const size_t Bn = (size_t)(B > 0 ? B : 1), N = (size_t)net->N;
+  const size_t a = align256(4 * Bn * (N + 1)), l = align256(4 * Bn * N);
+  cudaDeviceSynchronize();
+  if (net->prox_ws) cudaFree(net->prox_ws);
+  net->prox_ws = nullptr;
+  net->prox_B = -1;
+  void* p = nullptr;
+  const cudaError_t e = ld::dev_malloc(&p, 2 * a + l);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_status(e);
+  }
+  net->prox_ws = p;
+  net->prox_B = (int)Bn;
+  return LD_OK;
+}
+
+ld::ProxState prox_state(ld_net* net) {
+  const size_t Bn = (size_t)net->prox_B, N = (size_t)net->N;
+  const size_t a = align256(4 * Bn * (N + 1));
+  char* c = static_cast<char*>(net->prox_ws);
+  ld::ProxState S;
+  S.lam = net->rho;
+  S.pi = net->m;
+  S.xB = net->v;
+  S.zB = net->xB;
+  S.xA = reinterpret_cast<float*>(c);
+  S.zA = reinterpret_cast<float*>(c + a);
+  S.lp = reinterpret_cast<float*>(c + 2 * a);
+  return S;
+}
+
+// Inner minimiser of q at lambda (Algorithm 2's initial primal x_hat^0): the
+// vertex choices of every layer into x_hat_B, the forward passes into x_hat_A.
+void prox_init_primal(ld_net* net, const Problem& P, const ld::ProxState& S, cudaStream_t s) {
+  const int n = net->n;
+  for (int k = n - 1; k >= 0; --k) {
+    ld::EpiArgmin ea{P, k, r_off(net, k), x_off(net, k), S.lam, net->x, S.xB, nullptr, nullptr};
+    if (k == n - 1)
+      ld::launch_top_argmin(layer(net, n), P, ea, s);
+    else
+      ld::launch_transposed_argmin(layer(net, k + 1), nullptr, P, S.lam, ea, s);
+    const LayerDev& Lk1 = layer(net, k + 1);
+    ld::EpiStore es{P, Lk1.r_out_off, plane_of(Lk1), k + 1 == n ? 1 : 0, Lk1.b, S.xA};
+    ld::launch_forward_store(Lk1, P, net->x, es, s);
+  }
+}
+
+// T outer iterations of Algorithm 2: J block-coordinate Frank-Wolfe sweeps
+// (blocks k = 0..n-1: lambda' of layers k and k+1, the conditional gradient
+// by the transposed pass of layer k+1 with the vertex choice of layer k and
+// the forward pass of layer k+1, then the optimal step and the block's move),
+// then the dual update.
+ld_status run_prox_iterations(ld_net* net, const Problem& P, const ld::ProxState& S, const ld_prox_opts& o,
+                              int n_iters, cudaStream_t s) {
+  const int n = net->n;
+  for (int t = 0; t < n_iters; ++t) {
+    const double eta_d = (double)o.eta0 + ((double)o.eta_end - (double)o.eta0) * t / std::max(n_iters - 1, 1);
+    const float eta = (float)eta_d;
+    for (int j = 0; j < o.J; ++j) {
+      for (int k = 0; k < n; ++k) {
+        if (k >= 1) ld::launch_prox_dual_prime(P, S, r_off(net, k), layer(net, k).n_out, eta, s);
+        if (k + 1 <= n - 1) ld::launch_prox_dual_prime(P, S, r_off(net, k + 1), layer(net, k + 1).n_out, eta, s);
+        ld::EpiArgmin ea{P, k, r_off(net, k), x_off(net, k), S.lp, net->x, S.zB, nullptr, nullptr};
+        if (k == n - 1)
+          ld::launch_top_argmin(layer(net, n), P, ea, s);
+        else
+          ld::launch_transposed_argmin(layer(net, k + 1), nullptr, P, S.lp, ea, s);
+        const LayerDev& Lk1 = layer(net, k + 1);
+        ld::EpiStore es{P, Lk1.r_out_off, plane_of(Lk1), k + 1 == n ? 1 : 0, Lk1.b, S.zA};
+        ld::launch_forward_store(Lk1, P, net->x, es, s);
+        ld::launch_prox_block_update(P, S, k >= 1 ? r_off(net, k) : 0, k >= 1 ? layer(net, k).n_out : 0,
+                                     k + 1 <= n - 1 ? r_off(net, k + 1) : 0, k + 1 <= n - 1 ? Lk1.n_out : 1,
+                                     k + 1 == n ? 1 : 0, eta, s);
+      }
+    }
+    ld::launch_prox_dual_update(P, S, eta, o.mu, s);
+  }
+  return last_error();
+}
+
+}  // namespace
+
+ld_status ld_bound_proximal(ld_net* net, const float* lb0, const float* ub0, const float* lbk, const float* ubk,
+                            int32_t n_props, const int32_t* prop, const int8_t* masks, int32_t B, int32_t n_iters,
+                            const ld_prox_opts* opts, const float* rho_in, float* rho_out, double* out,
+                            void* stream) {
+  ld_status st = check_problem(net, lb0, ub0, lbk, ubk, n_props, B);
+  if (st != LD_OK) return st;
+  if (n_iters < 0 || (!out && B > 0)) return LD_ERR_ARG;
+  ld_prox_opts o;
+  if (opts) o = *opts; else ld_prox_opts_default(&o);
+  if (!(o.eta0 > 0.f) || !(o.eta_end > 0.f) || !(o.mu >= 0.f && o.mu < 1.f) || o.J < 1 || o.J > 64 ||
+      o.init < LD_INIT_ZERO || o.init > LD_INIT_GIVEN || (o.fp64_final != 0 && o.fp64_final != 1))
+    return LD_ERR_ARG;
+  if (o.init == LD_INIT_GIVEN && !rho_in && B > 0) return LD_ERR_ARG;
+  if (B == 0) return LD_OK;
+  if ((st = ensure_ws(net, B)) != LD_OK) return st;
+  if ((st = ensure_prox_ws(net, B)) != LD_OK) return st;
+  cudaStream_t s = S(stream);
+  const Problem P = make_problem(net, lb0, ub0, lbk, ubk, n_props, prop, masks, B);
+  const size_t BN = (size_t)B * net->N;
+  const ld::ProxState PS = prox_state(net);
+  {
+    PhaseMark pm(net, LD_PHASE_INIT, s);
+    ld::launch_empty_flags(P, net->empty, net->d_status, s);
+    if (o.init == LD_INIT_GIVEN)
+      cudaMemcpyAsync(net->rho, rho_in, sizeof(float) * BN, cudaMemcpyDeviceToDevice, s);
+    else if (o.init == LD_INIT_ZERO)
+      cudaMemsetAsync(net->rho, 0, sizeof(float) * BN, s);
+    else
+      crown_sweep(net, P, s);
+    cudaMemsetAsync(PS.pi, 0, sizeof(float) * BN, s);
+    if (n_iters > 0) prox_init_primal(net, P, PS, s);
+  }
+  if (n_iters > 0) {
+    PhaseMark pm(net, LD_PHASE_ITER, s);
+    st = run_graphed(net, s, [&](cudaStream_t cs) { return run_prox_iterations(net, P, PS, o, n_iters, cs); });
+    if (st != LD_OK) return st;
+  }
+  {
+    PhaseMark pm(net, LD_PHASE_FINAL, s);
+    if (o.fp64_final)
+      final_fp64(net, P, out, s);
+    else
+      final_fp32(net, P, out, nullptr, nullptr, s);
+  }
+  if (rho_out) cudaMemcpyAsync(rho_out, net->rho, sizeof(float) * BN, cudaMemcpyDeviceToDevice, s);
   return last_error();
 }
 

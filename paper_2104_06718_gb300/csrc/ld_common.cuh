@@ -240,6 +240,22 @@ struct EpiRecord {
   }
 };
 
+// Forward pass -> store x_hat_A = W_{k+1} x_k + b_{k+1} of layer k+1 into a
+// [B, N + 1] array (layers 1..n-1 at their flat offsets, layer n at index N):
+// the conditional gradient's x_hat_A block of the proximal solver.
+struct EpiStore {
+  Problem P;
+  int r_off;           // layer k+1 in the flat ReLU vector (ignored for the last layer)
+  int plane;
+  int last;            // 1 for layer n
+  const float* bias;
+  float* out;          // [B, N + 1]
+  __device__ __forceinline__ void operator()(int b, int jj, float acc) const {
+    const float xa = acc + bias[jj / plane];
+    out[(size_t)b * (P.N + 1) + (last ? P.N : r_off + jj)] = xa;
+  }
+};
+
 // Library-wide count of kernel launches (every launcher calls this once per
 // kernel it launches); read through ld_launch_count.
 void count_launch(int n = 1);
@@ -395,6 +411,31 @@ void launch_top_crown(const LayerDev& Ln, const Problem& P, EpiCrown epi, cudaSt
 void launch_forward_adam(const LayerDev& L, const Problem& P, const float* x, EpiAdam epi, cudaStream_t s);
 void launch_forward_record(const LayerDev& L, const Problem& P, const float* x, EpiRecord epi,
                            cudaStream_t s);
+void launch_forward_store(const LayerDev& L, const Problem& P, const float* x, EpiStore epi, cudaStream_t s);
+
+// Proximal solver (ld_prox.cu): Algorithm 2's elementwise and per-subdomain steps.
+// Arrays: lam [B, N] (lambda), pi [B, N] (momentum), xB [B, N] and xA [B, N + 1]
+// (the primal blocks; xA's last column is x_hat_A,n), zB [B, N] and zA [B, N + 1]
+// (the conditional gradient), lp [B, N] (lambda' = lambda + (xB - xA) / eta).
+struct ProxState {
+  float* lam;
+  float* pi;
+  float* xB;
+  float* xA;
+  float* zB;
+  float* zA;
+  float* lp;
+};
+// lambda' of the neurons [off, off + n) of every subdomain.
+void launch_prox_dual_prime(const Problem& P, const ProxState& S, int off, int n, float eta, cudaStream_t s);
+// Block k's optimal step (Eq. optimal-gamma-gauss) per subdomain and its
+// convex-combination update of (x_hat_B,k, x_hat_A,k+1); layer k at offset
+// off_k (n_k neurons; k = 0: none), layer k+1 at off_k1 (n_k1 neurons), last:
+// layer k+1 is the output (x_hat_A,n at column N, eta_n = infinity).
+void launch_prox_block_update(const Problem& P, const ProxState& S, int off_k, int n_k, int off_k1, int n_k1,
+                              int last, float eta, cudaStream_t s);
+// Dual update with momentum (Eq. momentum_updates; mu = 0: Eq. lambda_updates).
+void launch_prox_dual_update(const Problem& P, const ProxState& S, float eta, float mu, cudaStream_t s);
 
 // Feasibility pre-pass and box checks (ld_passes.cu).
 void launch_empty_flags(const Problem& P, int8_t* empty, int* status, cudaStream_t s);

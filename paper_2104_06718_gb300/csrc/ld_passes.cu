@@ -452,6 +452,10 @@ void launch_forward_record(const LayerDev& L, const Problem& P, const float* x, 
   forward(L, P, x, epi, s);
 }
 
+void launch_forward_store(const LayerDev& L, const Problem& P, const float* x, EpiStore epi, cudaStream_t s) {
+  forward(L, P, x, epi, s);
+}
+
 void launch_empty_flags(const Problem& P, int8_t* empty, int* status, cudaStream_t s) {
   if (P.B > 0) {
     count_launch();

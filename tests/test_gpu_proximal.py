@@ -1,0 +1,130 @@
+"""GPU: the proximal solver (Sec. 3.3, Algorithm 2) against oracle/proximal.py.
+
+ld_bound_proximal runs Algorithm 2 on the device: CROWN start, the inner
+minimiser of q as the first primal point, J sweeps of block-coordinate
+Frank-Wolfe per iteration with the optimal step of Eq. (optimal-gamma-gauss),
+and the dual update with momentum (App. D).  Tolerances (relative to
+max(|b|, 1)):
+  * bound after 1 and 3 iterations, both of the paper's settings     1e-5
+  * bound after 50 iterations: 1e-3 max / 3e-4 median (like the supergradient's
+    long runs, a near-tie decided the other way moves the whole trajectory)
+  * tiny MLPs after 200 iterations: never above the Planet LP optimum
+  * empty subdomains +inf; two runs bitwise equal (fixed-order reductions)
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import lp
+from oracle import proximal as px
+from paper_2104_06718_gb300 import binding as ldb
+from helpers import conv_problem, oracle_lists, outward_f32, tiny_problem
+
+pytestmark = pytest.mark.gpu
+
+SETTINGS = {"incomplete": (ldb.ProxOptions(), px.ProxSettings()),
+            "bab": (ldb.ProxOptions(eta0=100.0, eta_end=100.0, mu=0.0), px.BAB_SETTINGS)}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2104_06718_gb300 import build
+    build.build()
+    ldb.load_library()
+
+
+def rel(a, b):
+    return np.abs(np.asarray(a, np.float64) - np.asarray(b, np.float64)) / np.maximum(np.abs(np.asarray(b, np.float64)), 1.0)
+
+
+def oracle_prox(pb, T, s):
+    on = pb["net"]
+    L0, U0, lbs, ubs, empty = oracle_lists(on, pb)
+    out = np.full(pb["B"], np.inf)
+    keep = ~empty
+    if keep.any():
+        sel = lambda l: [None] + [x[keep] for x in l[1:]]
+        r = px.proximal_solver(on, L0[keep], U0[keep], sel(lbs), sel(ubs), T, s)
+        out[keep] = r.q_final
+    return out
+
+
+def run_gpu(pb, T, o):
+    net = ldb.Net(pb["specs"])
+    return ldb.ld_bound_proximal(net, pb["l0"], pb["u0"], pb["lbk"], pb["ubk"], pb["prop"], pb["masks"], n_iters=T,
+                                 opts=o).cpu().numpy()
+
+
+@pytest.mark.parametrize("setting", ["incomplete", "bab"])
+@pytest.mark.parametrize("name", ["base", "wide", "deep"])
+@pytest.mark.parametrize("T", [1, 3])
+def test_prox_short_runs_match_oracle(name, T, setting):
+    if setting == "bab" and name != "base":
+        pytest.skip("the second setting on one net")
+    pb = conv_problem(name, 16, depth=(0, 8), block=8)
+    go, so = SETTINGS[setting]
+    out = run_gpu(pb, T, go)
+    ref = oracle_prox(pb, T, so)
+    fin = np.isfinite(ref)
+    assert np.array_equal(np.isfinite(out), fin)
+    assert np.max(rel(out[fin], ref[fin])) < 1e-5
+
+
+@pytest.mark.parametrize("name,B", [("base", 24), ("deep", 12)])
+def test_prox_full_runs_match_oracle(name, B):
+    pb = conv_problem(name, B, depth=(0, 8), block=5)
+    go, so = SETTINGS["incomplete"]
+    out = run_gpu(pb, 50, go)
+    ref = oracle_prox(pb, 50, so)
+    fin = np.isfinite(ref)
+    assert np.array_equal(np.isfinite(out), fin)
+    r = rel(out[fin], ref[fin])
+    assert r.max() < 1e-3 and np.median(r) < 3e-4, (r.max(), np.median(r))
+
+
+def test_prox_tiny_nets_stay_below_the_lp():
+    for i in range(6):
+        specs, on, l0, u0, lb, ub = tiny_problem(i)
+        flat_l = np.concatenate([lb[k] for k in range(1, on.n)], axis=1)
+        flat_u = np.concatenate([ub[k] for k in range(1, on.n)], axis=1)
+        lbk, ubk = outward_f32(flat_l, flat_u)
+        net = ldb.Net(specs)
+        out = ldb.ld_bound_proximal(net, l0.astype(np.float32), u0.astype(np.float32), lbk, ubk,
+                                    masks=np.zeros((1, lbk.shape[1]), np.int8), n_iters=200).cpu().numpy()
+        lbs = oracle.layer_lists(on, lbk.astype(np.float64))
+        ubs = oracle.layer_lists(on, ubk.astype(np.float64))
+        p = lp.planet_lp(on, l0[0], u0[0], [None] + [x[0] for x in lbs[1:]], [None] + [x[0] for x in ubs[1:]])
+        assert out[0] <= p.p_star + 1e-9 * max(1.0, abs(p.p_star))
+        ref = px.proximal_solver(on, l0, u0, lbs, ubs, 200).q_final
+        assert rel(out[0], ref[0]) < 1e-3
+
+
+def test_prox_empty_subdomains_deterministic_and_given_start():
+    pb = conv_problem("base", 16, depth=(0, 8), block=1)
+    masks = pb["masks"].copy()
+    blk = np.nonzero(pb["ubk"][0] < 0)[0]
+    masks[5, blk[0]] = 1   # a blocking ReLU forced passing: empty domain
+    pb = dict(pb, masks=masks)
+    net = ldb.Net(pb["specs"])
+    args = (pb["l0"], pb["u0"], pb["lbk"], pb["ubk"], pb["prop"], pb["masks"])
+    a, ra = ldb.ld_bound_proximal(net, *args, n_iters=20, return_rho=True)
+    b, rb = ldb.ld_bound_proximal(net, *args, n_iters=20, return_rho=True)
+    assert torch.equal(a, b) and torch.equal(ra, rb)
+    a = a.cpu().numpy()
+    assert np.isinf(a[5]) and np.isfinite(np.delete(a, 5)).all()
+    # a warm start (init GIVEN) from duals of 5 supergradient steps taken by the oracle
+    on = pb["net"]
+    L0, U0, lbs, ubs, empty = oracle_lists(on, pb)
+    keep = ~empty
+    sel = lambda l: [None] + [x[keep] for x in l[1:]]
+    lbs, ubs, L0, U0 = sel(lbs), sel(ubs), L0[keep], U0[keep]
+    sg = oracle.supergradient_adam(on, L0, U0, lbs, ubs, oracle.crown_init(on, lbs, ubs)[0], 5)
+    rho = np.zeros((pb["B"], pb["lbk"].shape[1]), np.float32)
+    rho[keep] = oracle.flatten_layers(on, sg.rho)
+    out = ldb.ld_bound_proximal(net, *args, n_iters=3, rho_in=rho).cpu().numpy()
+    lam0 = oracle.layer_lists(on, rho[keep].astype(np.float64))
+    ref = px.proximal_solver(on, L0, U0, lbs, ubs, 3, px.ProxSettings(), lam0=lam0).q_final
+    assert np.max(rel(out[keep], ref)) < 1e-5

@@ -18,10 +18,15 @@
 //
 // Every objective row (owner x rule x sign x neuron) is one CTA.  Its dense
 // coefficient vector is staged in shared memory and each transposed pass
-// a = W^T mu runs in FP32, with a second FP32 sum of |W||mu| rounded upward:
-// the pass's rounding error is at most gamma_K times that sum (K = terms per
-// sum), and since a multiplies x_{j-1} in the substitution, the bound is
-// lowered by gamma_K * sum|W||mu| * max|x_{j-1}|.  The relaxation slopes are
+// a = W^T mu runs in FP32 as a compensated dot product (each product split
+// exactly into value and error by an FMA, the running sum by TwoSum, the
+// errors summed alongside: Ogita, Rump and Oishi's Dot2), with a sum of
+// |W||mu| rounded upward beside it.  The result's error is at most
+// u |a| + gamma_K^2 sum|W||mu| (u = 2^-24, K = terms per sum), and since a
+// multiplies x_{j-1} in the substitution, the bound is lowered by that error
+// times max|x_{j-1}|.  (A plain FP32 sum would carry gamma_K sum|W||mu|,
+// which over a deep chain of substitutions loosens the bounds by ~1e-3.)
+// The relaxation slopes are
 // rounded in the direction that keeps each relaxation valid (a_bar upward,
 // b_bar upward; any lower slope in [0,1] is valid), a rounded mu_j product
 // lowers the bound by its rounding error times max|x_hat_j|, and every scalar
@@ -46,7 +51,7 @@ struct IbStep {
   const float* bias_prev;   // hidden epilogue: bias of layer j-1 (plane_prev outputs per channel)
   int plane_prev;
   int prev_r_off;           // layer j-1 in the flat ReLU vector
-  float gamma_K;            // FP32 a-priori constant of this pass's sums (0 when seed)
+  float gamma_K;            // FP32 gamma of this pass's sums (its square bounds Dot2's error; 0 when seed)
   // rows
   int n_k;                  // neurons of the layer being bounded
   int n_rules;              // 1 or 2
@@ -82,18 +87,31 @@ __device__ __forceinline__ int box_of(const IbStep& st, int owner) {
   return st.n_boxes == 1 ? 0 : owner;
 }
 
-// a = (W^T mu)[ii] in FP32 and s >= sum |W| |mu| (FP32, rounded up), mu in shared memory.
+// Compensated dot product state: running sum p, accumulated errors c, and
+// s >= sum |w m| (rounded up).
+struct Dot2 {
+  float p = 0.f, c = 0.f, s = 0.f;
+  __device__ __forceinline__ void add(float w, float m) {
+    const float h = __fmul_rn(w, m);
+    const float r = __fmaf_rn(w, m, -h);           // w m = h + r exactly
+    const float t = __fadd_rn(p, h);               // TwoSum(p, h) = t + q exactly
+    const float bv = __fsub_rn(t, p);
+    const float av = __fsub_rn(t, bv);
+    const float q = __fadd_rn(__fsub_rn(p, av), __fsub_rn(h, bv));
+    p = t;
+    c = __fadd_rn(c, __fadd_rn(q, r));
+    s = __fmaf_ru(fabsf(w), fabsf(m), s);
+  }
+};
+
+// a = (W^T mu)[ii] by Dot2 and s >= sum |W| |mu| (FP32, rounded up), mu in shared memory.
 __device__ __forceinline__ void transposed_elem(const LayerDev& L, const float* mu, int ii, float& a, float& s) {
-  a = 0.f;
-  s = 0.f;
+  Dot2 d;
   if (L.kind == LD_LAYER_FC) {
     const float* w = L.W + ii;
-    for (int o = 0; o < L.n_out; ++o) {
-      const float wv = __ldg(w + (size_t)o * L.n_in);
-      const float m = mu[o];
-      a = fmaf(wv, m, a);
-      s = __fmaf_ru(fabsf(wv), fabsf(m), s);
-    }
+    for (int o = 0; o < L.n_out; ++o) d.add(__ldg(w + (size_t)o * L.n_in), mu[o]);
+    a = __fadd_rn(d.p, d.c);
+    s = d.s;
     return;
   }
   const int hw = L.h * L.w;
@@ -108,14 +126,12 @@ __device__ __forceinline__ void transposed_elem(const LayerDev& L, const float* 
       if (tx < 0 || tx % L.stride) continue;
       const int ox = tx / L.stride;
       if (ox >= L.wo) continue;
-      for (int o = 0; o < L.cout; ++o) {
-        const float wv = __ldg(L.W + (((size_t)o * L.cin + c) * L.kh + ki) * L.kw + kj);
-        const float m = mu[((size_t)o * L.ho + oy) * L.wo + ox];
-        a = fmaf(wv, m, a);
-        s = __fmaf_ru(fabsf(wv), fabsf(m), s);
-      }
+      for (int o = 0; o < L.cout; ++o)
+        d.add(__ldg(L.W + (((size_t)o * L.cin + c) * L.kh + ki) * L.kw + kj), mu[((size_t)o * L.ho + oy) * L.wo + ox]);
     }
   }
+  a = __fadd_rn(d.p, d.c);
+  s = d.s;
 }
 
 __device__ __forceinline__ double block_sum(double v, double* red, bool up) {
@@ -156,15 +172,18 @@ __global__ void __launch_bounds__(NT) ib_step_kernel(IbStep st) {
     av = fabs(bb);
   }
   const int bx = st.box ? box_of(st, owner) : 0;
+  const double g2 = 2.0 * (double)st.gamma_K * (double)st.gamma_K;
   for (int ii = threadIdx.x; ii < L.n_in; ii += NT) {
     float a, s;
     transposed_elem(L, mu, ii, a, s);
+    // bound on |a - W^T mu| (Dot2): u |a| + gamma_K^2 sum|W||mu|, with margin; 0 for the exact seed
+    const double da = st.seed ? 0.0 : __dadd_ru(__dmul_ru(1.1920928955078125e-07, fabs((double)a)), __dmul_ru(g2, (double)s));
     if (st.box) {
       const double l = (double)st.l0[(size_t)bx * st.n0 + ii], u = (double)st.u0[(size_t)bx * st.n0 + ii];
       const double t = fmin((double)a * l, (double)a * u);
       v += t;
       av = __dadd_ru(av, fabs(t));
-      e = __dadd_ru(e, __dmul_ru(__dmul_ru((double)st.gamma_K, (double)s), fmax(fabs(l), fabs(u))));
+      e = __dadd_ru(e, __dmul_ru(da, fmax(fabs(l), fabs(u))));
       continue;
     }
     const size_t j = (size_t)owner * st.N + st.prev_r_off + ii;
@@ -194,7 +213,7 @@ __global__ void __launch_bounds__(NT) ib_step_kernel(IbStep st) {
       v += t;
       av = __dadd_ru(av, fabs(t));
       // the pass's own rounding, times max x_{j-1} = max(u, 0)
-      e = __dadd_ru(e, __dmul_ru(__dmul_ru((double)st.gamma_K, (double)s), (double)u));
+      e = __dadd_ru(e, __dmul_ru(da, (double)u));
     }
     st.mu_out[(size_t)rl * L.n_in + ii] = m;
   }

@@ -192,22 +192,24 @@ def test_changed_parameters_without_a_rebuilt_net_raise():
     specs = synth.make_convnet("base")
     l0, u0, c = synth.image_property(2)
     net = ldb.Net(specs, margin=c)
-    lbk, ubk = ldb.ld_intermediate_bounds(net, l0[None], u0[None])
+    l0 = torch.tensor(l0[None], device="cuda")
+    u0 = torch.tensor(u0[None], device="cuda")
+    lbk, ubk = ldb.ld_intermediate_bounds(net, l0, u0)
     params = _params(specs)
-    out = lda.bound(net, l0[None], u0[None], lbk, ubk, params, n_iters=3)
+    out = lda.bound(net, l0, u0, lbk, ubk, params, n_iters=3)
     assert torch.isfinite(out).all()
     with torch.no_grad():
         params[2].mul_(1.01)          # conv2 weights updated in place (e.g. an optimiser step)
     with pytest.raises(lda.StaleParametersError):
-        lda.bound(net, l0[None], u0[None], lbk, ubk, params, n_iters=3)
+        lda.bound(net, l0, u0, lbk, ubk, params, n_iters=3)
     wrong = _params(specs)
     with torch.no_grad():
         wrong[0].add_(1.0)
     with pytest.raises(lda.StaleParametersError):
-        lda.bound(ldb.Net(specs, margin=c), l0[None], u0[None], lbk, ubk, wrong, n_iters=3)
+        lda.bound(ldb.Net(specs, margin=c), l0, u0, lbk, ubk, wrong, n_iters=3)
     # a rebuilt net with the new values is accepted
     specs2 = [dataclasses.replace(s, W=p.detach().cpu().numpy(), b=q.detach().cpu().numpy())
               for s, p, q in zip(specs, params[0::2], params[1::2])]
     net2 = ldb.Net(specs2, margin=c)
-    out2 = lda.bound(net2, l0[None], u0[None], lbk, ubk, params, n_iters=3)
+    out2 = lda.bound(net2, l0, u0, lbk, ubk, params, n_iters=3)
     assert torch.isfinite(out2).all()

@@ -284,6 +284,59 @@ ld_status ld_bound_proximal(ld_net* net, const float* lb0, const float* ub0, con
                             const int8_t* split_masks, int32_t B, int32_t n_iters, const ld_prox_opts* opts,
                             const float* rho_in, float* rho_out, double* out, void* stream);
 
+/* Branching scores of every ReLU (Sec. 4.1, Eq. babsr-scores and Eq.
+ * fsb-scores) from one backward pass of the WK upper slopes:
+ * lam_{n-1} = -W_n^T 1, lam_{k-1} = W_k^T ([u]_+ / ([u]_+ - [l]_-) lam_k); for
+ * an ambiguous ReLU (clamped bounds l < 0 < u; others score 0)
+ *   s_SR  = | max(0, lam b) - u/(u-l) lam b + u l/(u-l) [lam]_+ |
+ *   s_FSB = | min(0, lam b) - u/(u-l) lam b + u l/(u-l) [lam]_+ |   (mSR / FSB)
+ *   t_SR  = -u l/(u-l) [lam]_+                                       (backup)
+ * with b the neuron's bias.
+ *   lbk, ubk [device] [n_props, N]; prop_of_subdomain [device] NULL (one
+ *   property) or [B]; split_masks [device] NULL or [B, N] (the clamp of Sec.
+ *   2.3.2 applies before scoring).  s_sr, s_fsb, t_sr [device] [B, N] float
+ *   outputs (any may be NULL).
+ * Errors: LD_ERR_ARG (nulls, n_props < 1, B < 0, prop NULL with n_props > 1),
+ * LD_ERR_UNSUPPORTED (B > 65535), LD_ERR_NOMEM. */
+ld_status ld_branching_scores(ld_net* net, const float* lbk, const float* ubk, int32_t n_props,
+                              const int32_t* prop_of_subdomain, const int8_t* split_masks, int32_t B,
+                              float* s_sr, float* s_fsb, float* t_sr, void* stream);
+
+/* One branching decision per subdomain (Sec. 4): the ReLU to split, as a
+ * flat index, or -1 where no ReLU is ambiguous.
+ *   rule LD_BRANCH_SR: BaBSR's Smart ReLU -- the largest s_SR, or the
+ *   largest t_SR when that score does not exceed `threshold`;
+ *   LD_BRANCH_MSR: the same with s_FSB (min-based SR);
+ *   LD_BRANCH_FSB: Filtered Smart Branching (Sec. 4.2, Eq. fsb-prefilter):
+ *   per layer the argmax of s_FSB and of t_SR are candidates; each
+ *   candidate's two children (the ReLU fixed passing / blocking in the
+ *   subdomain's clamped bounds) are bounded by the better of the CROWN and WK
+ *   bounds of the output (rigorous, as ld_intermediate_bounds_propagated), and
+ *   the candidate whose worse child bound is the largest is taken.
+ *   Every argmax takes the first index on ties.
+ *   lb0, ub0 [device] [n_props, n_0] (FSB only; may be NULL otherwise).
+ *   decision [device] [B] int32 output; child_bounds [device] NULL or
+ *   [B, 2 (n-1), 2] double: FSB's children bounds (candidate-major, passing
+ *   child first).  FSB grows the workspace of ld_intermediate_bounds_propagated.
+ * Errors: as ld_branching_scores; LD_ERR_ARG for a bad rule or a NULL
+ * decision. */
+enum { LD_BRANCH_SR = 0, LD_BRANCH_MSR = 1, LD_BRANCH_FSB = 2 };
+ld_status ld_branch(ld_net* net, const float* lb0, const float* ub0, const float* lbk, const float* ubk,
+                    int32_t n_props, const int32_t* prop_of_subdomain, const int8_t* split_masks, int32_t B,
+                    int32_t rule, float threshold, int32_t* decision, double* child_bounds, void* stream);
+
+/* Upper bounds on the minimum (Sec. 5.1.3): the network's output at the input
+ * point x0* of the inner minimisation of q(rho) (the box argmin of
+ * Eq. box_bounds_sol at the given duals), evaluated in FP32 (a point of the
+ * box, so its value bounds the minimum from above up to that rounding; the
+ * value is a counterexample candidate when negative).
+ *   Arguments as ld_bound; rho [device] [B, N]; ub [device] [B] double;
+ *   x0 [device] NULL or [B, n_0] float: the points themselves.
+ * Errors: as ld_bound. */
+ld_status ld_upper_bound(ld_net* net, const float* lb0, const float* ub0, const float* lbk, const float* ubk,
+                         int32_t n_props, const int32_t* prop_of_subdomain, const int8_t* split_masks, int32_t B,
+                         const float* rho, double* ub, float* x0, void* stream);
+
 /* One inner minimisation at a given rho, in FP32, without any update:
  * q(rho) (Eq. nonprox_problem), the supergradient x_hat_B - x_hat_A
  * (Algorithm 1) and the chosen vertex per ReLU.

@@ -29,9 +29,9 @@ What it computes.
   search stops when none is left (the property holds), when an upper bound
   falls below 0 (a counterexample), or after a node budget.
 Readings (listed in the design notes): subdomains hold their intermediate
-bounds fixed at the root's, clamped by the split (BaDNB, Sec. 5.1.1); a
-score ties to the first index; the SR threshold defaults to 0; splits
-already made score 0 (they are no longer ambiguous).
+bounds fixed at the root's, clamped by the split (BaDNB, Sec. 5.1.1); every
+argmax runs over the ambiguous ReLUs only and takes the first index on ties;
+the SR threshold defaults to 0; splits already made are no longer ambiguous.
 """
 from __future__ import annotations
 
@@ -85,9 +85,9 @@ def sr_decision(net: Net, lb, ub, fsb_scores: bool = False, threshold: float = 0
     """Flat ReLU index chosen by SR (mSR with fsb_scores) per subdomain [B];
     -1 where no ReLU is ambiguous."""
     s_sr, s_fsb, t_sr = branching_scores(net, lb, ub)
-    s = _flat(net, s_fsb if fsb_scores else s_sr)
-    t = _flat(net, t_sr)
     amb = _flat(net, [None] + [classify(lb[k], ub[k]) == 2 for k in range(1, net.n)])
+    s = np.where(amb, _flat(net, s_fsb if fsb_scores else s_sr), -np.inf)
+    t = np.where(amb, _flat(net, t_sr), -np.inf)
     i_s = np.argmax(s, axis=1)
     i_t = np.argmax(t, axis=1)
     rows = np.arange(s.shape[0])
@@ -102,9 +102,10 @@ def fsb_candidates(net: Net, lb, ub):
     offs = split_offsets(net)
     cols = []
     for k in range(1, net.n):
-        amb = (classify(lb[k], ub[k]) == 2).any(axis=1)
+        amb_k = classify(lb[k], ub[k]) == 2
+        amb = amb_k.any(axis=1)
         for sc in (s_fsb[k], t_sr[k]):
-            cols.append(np.where(amb, offs[k - 1] + np.argmax(sc, axis=1), -1))
+            cols.append(np.where(amb, offs[k - 1] + np.argmax(np.where(amb_k, sc, -np.inf), axis=1), -1))
     return np.stack(cols, axis=1)
 
 

@@ -24,6 +24,8 @@ LD_INIT_ZERO, LD_INIT_CROWN, LD_INIT_GIVEN = 0, 1, 2
 LD_PREC_FP32, LD_PREC_BF16 = 0, 1
 LD_ENGINE_AUTO, LD_ENGINE_LAYERWISE, LD_ENGINE_FUSED = 0, 1, 2
 LD_IB_CROWN, LD_IB_WK = 1, 2
+LD_BRANCH_SR, LD_BRANCH_MSR, LD_BRANCH_FSB = 0, 1, 2
+BRANCH_RULES = {"sr": LD_BRANCH_SR, "msr": LD_BRANCH_MSR, "fsb": LD_BRANCH_FSB}
 IB_RULES = {"crown": LD_IB_CROWN, "wk": LD_IB_WK, "best": LD_IB_CROWN | LD_IB_WK}
 
 EXPORTED = [
@@ -32,6 +34,7 @@ EXPORTED = [
     "ld_bound", "ld_dual_supergradient", "ld_bound_backward",
     "ld_net_profile", "ld_net_profile_read", "ld_launch_count", "ld_net_tuned", "ld_final_bound_noalloc",
     "ld_test_inject_alloc_failure", "ld_intermediate_bounds_propagated", "ld_prox_opts_default", "ld_bound_proximal",
+    "ld_branching_scores", "ld_branch", "ld_upper_bound",
 ]
 PHASES = {"iter": 0, "final": 1, "init": 2, "ibp": 3, "backward": 4}
 
@@ -98,6 +101,9 @@ def load_library(path: str = LIB_PATH):
     lib.ld_prox_opts_default.argtypes = [C.POINTER(ProxOpts)]
     lib.ld_prox_opts_default.restype = None
     lib.ld_bound_proximal.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, i32, i32, C.POINTER(ProxOpts), vp, vp, vp, vp]
+    lib.ld_branching_scores.argtypes = [vp, vp, vp, i32, vp, vp, i32, vp, vp, vp, vp]
+    lib.ld_branch.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, i32, i32, C.c_float, vp, vp, vp]
+    lib.ld_upper_bound.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, i32, vp, vp, vp, vp]
     for name in EXPORTED:
         if name not in ("ld_opts_default", "ld_status_str", "ld_prox_opts_default"):
             getattr(lib, name).restype = C.c_int
@@ -394,6 +400,50 @@ def ld_bound_proximal(net: Net, lb0, ub0, lbk, ubk, prop=None, masks=None, n_ite
                                       _ptr(prop), _ptr(masks), B, int(n_iters), C.byref(oc), _ptr(rho_in),
                                       _ptr(rho_out), _ptr(out), _stream()), "ld_bound_proximal")
     return (out, rho_out) if return_rho else out
+
+
+def ld_branching_scores(net: Net, lbk, ubk, prop=None, masks=None, B: int | None = None):
+    """(s_SR, s_FSB, t_SR) [B, N] float32 branching scores (Sec. 4)."""
+    lbk = _dev(lbk, torch.float32)
+    ubk = _dev(ubk, torch.float32)
+    if lbk.dim() == 1:
+        lbk, ubk = lbk[None], ubk[None]
+    prop = None if prop is None else _dev(prop, torch.int32)
+    masks = None if masks is None else _dev(masks, torch.int8)
+    if B is None:
+        B = masks.shape[0] if masks is not None else (prop.shape[0] if prop is not None else 1)
+    f = lambda: torch.empty((B, net.N), dtype=torch.float32, device="cuda")
+    s_sr, s_fsb, t_sr = f(), f(), f()
+    _check(net._lib.ld_branching_scores(net.handle, _ptr(lbk), _ptr(ubk), lbk.shape[0], _ptr(prop), _ptr(masks), int(B),
+                                        _ptr(s_sr), _ptr(s_fsb), _ptr(t_sr), _stream()), "ld_branching_scores")
+    return s_sr, s_fsb, t_sr
+
+
+def ld_branch(net: Net, lb0, ub0, lbk, ubk, prop=None, masks=None, rule: str = "fsb", threshold: float = 0.0,
+              B: int | None = None, return_child_bounds: bool = False):
+    """Branching decision per subdomain [B] int32 (flat ReLU index, -1 when
+    none is ambiguous); with return_child_bounds (FSB), also the candidates'
+    children bounds [B, 2(n-1), 2] float64."""
+    lb0, ub0, lbk, ubk, prop, masks, B = _problem(lb0, ub0, lbk, ubk, prop, masks, B)
+    dec = torch.empty(B, dtype=torch.int32, device="cuda")
+    child = torch.empty((B, 2 * (net.n_layers - 1), 2), dtype=torch.float64, device="cuda") \
+        if return_child_bounds else None
+    _check(net._lib.ld_branch(net.handle, _ptr(lb0), _ptr(ub0), _ptr(lbk), _ptr(ubk), lbk.shape[0], _ptr(prop),
+                              _ptr(masks), B, BRANCH_RULES[rule], float(threshold), _ptr(dec), _ptr(child),
+                              _stream()), "ld_branch")
+    return (dec, child) if return_child_bounds else dec
+
+
+def ld_upper_bound(net: Net, lb0, ub0, lbk, ubk, rho, prop=None, masks=None, return_x0: bool = False):
+    """Network output [B] (float64) at the inner minimiser's input point x0* of
+    q(rho), an upper bound on the minimum (Sec. 5.1.3); optionally x0* [B, n0]."""
+    rho = _dev(rho, torch.float32)
+    lb0, ub0, lbk, ubk, prop, masks, B = _problem(lb0, ub0, lbk, ubk, prop, masks, rho.shape[0])
+    ub = torch.empty(B, dtype=torch.float64, device="cuda")
+    x0 = torch.empty((B, net.n0), dtype=torch.float32, device="cuda") if return_x0 else None
+    _check(net._lib.ld_upper_bound(net.handle, _ptr(lb0), _ptr(ub0), _ptr(lbk), _ptr(ubk), lbk.shape[0], _ptr(prop),
+                                   _ptr(masks), B, _ptr(rho), _ptr(ub), _ptr(x0), _stream()), "ld_upper_bound")
+    return (ub, x0) if return_x0 else ub
 
 
 def ld_dual_supergradient(net: Net, lb0, ub0, lbk, ubk, rho, prop=None, masks=None):

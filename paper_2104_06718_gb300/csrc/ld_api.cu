@@ -938,6 +938,47 @@ ld_status ld_intermediate_bounds_split(ld_net* net, const float* lb0, const floa
   return last_error();
 }
 
+namespace {
+
+// Workspace of the propagation kernels for up to max_rows objective rows
+// (plus `extra` bytes for the caller, returned at the end of the block via
+// A.mu_b + ... -- see ib_extra), grown on demand; fills the workspace part of A.
+ld_status ib_args(ld_net* net, size_t max_rows, size_t extra, ld::IbLayerArgs& A, char** extra_ptr = nullptr) {
+  int max_w = 1;
+  for (int k = 1; k < net->n; ++k) max_w = std::max(max_w, layer(net, k).n_out);
+  const size_t mu_cap = (size_t)256 << 20;   // both coefficient buffers together
+  int64_t chunk = (int64_t)std::max<size_t>(1, mu_cap / (2 * sizeof(float) * (size_t)max_w));
+  if ((size_t)chunk > max_rows) chunk = (int64_t)std::max<size_t>(max_rows, 1);
+  const size_t acc_b = align256(24 * std::max<size_t>(max_rows, 1)), mu_b = align256(sizeof(float) * (size_t)chunk * max_w);
+  const size_t need = acc_b + 2 * mu_b + align256(extra);
+  if (need > net->ib_bytes) {
+    cudaDeviceSynchronize();
+    if (net->ib_ws) cudaFree(net->ib_ws);
+    net->ib_ws = nullptr;
+    net->ib_bytes = 0;
+    void* p = nullptr;
+    const cudaError_t e = ld::dev_malloc(&p, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return cuda_status(e);
+    }
+    net->ib_ws = p;
+    net->ib_bytes = need;
+  }
+  char* c = static_cast<char*>(net->ib_ws);
+  A.N = (int)net->N;
+  A.n0 = (int)net->n0;
+  A.acc = reinterpret_cast<double*>(c);
+  A.mu_a = reinterpret_cast<float*>(c + acc_b);
+  A.mu_b = reinterpret_cast<float*>(c + acc_b + mu_b);
+  A.chunk_rows = chunk;
+  A.gamma_M = ld::final_gamma(2.0 * (double)(net->N + net->n0) + 8.0);
+  if (extra_ptr) *extra_ptr = c + acc_b + 2 * mu_b;
+  return LD_OK;
+}
+
+}  // namespace
+
 void ld_prox_opts_default(ld_prox_opts* o) {
   if (!o) return;
   o->eta0 = 1e1f;
@@ -1094,6 +1135,7 @@ ld_status ld_intermediate_bounds_propagated(ld_net* net, const float* lb0, const
   cudaStream_t s = S(stream);
   PhaseMark pm(net, LD_PHASE_IBP, s);
   const int N = (int)net->N, n = net->n;
+  ld_status st = LD_OK;
   // layer 1: the exact range of an affine map over the box (its interval bound), clamped
   ld::IbpRows rows;
   if (prop) {
@@ -1110,51 +1152,137 @@ ld_status ld_intermediate_bounds_propagated(ld_net* net, const float* lb0, const
   if (n <= 2) return last_error();
   const int n_rules = rules == (LD_IB_CROWN | LD_IB_WK) ? 2 : 1;
   size_t max_rows = 0;
-  int max_w = 1;
-  for (int k = 1; k < n; ++k) max_w = std::max(max_w, layer(net, k).n_out);
   for (int k = 2; k < n; ++k) max_rows = std::max(max_rows, (size_t)n_rows * ld::ib_rows_per_owner(net->L, k, n_rules));
-  const size_t mu_cap = (size_t)256 << 20;   // both coefficient buffers together
-  int64_t chunk = (int64_t)std::max<size_t>(1, mu_cap / (2 * sizeof(float) * (size_t)max_w));
-  if ((size_t)chunk > max_rows) chunk = (int64_t)max_rows;
-  const size_t acc_b = align256(24 * max_rows), mu_b = align256(sizeof(float) * (size_t)chunk * max_w);
-  const size_t need = acc_b + 2 * mu_b;
-  if (need > net->ib_bytes) {
-    cudaDeviceSynchronize();
-    if (net->ib_ws) cudaFree(net->ib_ws);
-    net->ib_ws = nullptr;
-    net->ib_bytes = 0;
-    void* p = nullptr;
-    const cudaError_t e = ld::dev_malloc(&p, need);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return cuda_status(e);
-    }
-    net->ib_ws = p;
-    net->ib_bytes = need;
-  }
-  char* c = static_cast<char*>(net->ib_ws);
   ld::IbLayerArgs A{};
+  if ((st = ib_args(net, max_rows, 0, A)) != LD_OK) return st;
   A.n_owners = n_rows;
   A.n_rules = n_rules;
   A.rule0 = rules == LD_IB_WK ? 1 : 0;
   A.lbk = lbk;
   A.ubk = ubk;
-  A.N = N;
   A.l0 = lb0;
   A.u0 = ub0;
-  A.n0 = (int)net->n0;
   A.box_row = prop;
   A.n_boxes = n_props;
   A.mask = masks;
-  A.acc = reinterpret_cast<double*>(c);
-  A.mu_a = reinterpret_cast<float*>(c + acc_b);
-  A.mu_b = reinterpret_cast<float*>(c + acc_b + mu_b);
-  A.chunk_rows = chunk;
-  A.gamma_M = ld::final_gamma(2.0 * (double)(net->N + net->n0) + 8.0);
   for (int k = 2; k < n; ++k) {
     const cudaError_t e = ld::launch_ib_layer(net->L, k, A, s);
     if (e != cudaSuccess) return cuda_status(e);
   }
+  return last_error();
+}
+
+namespace {
+
+// The backward pass of Eq. (babsr-scores) with the scores of every layer.
+void scores_sweep(ld_net* net, const Problem& P, float* mu, float* s_sr, float* s_fsb, float* t_sr, cudaStream_t s) {
+  const int n = net->n;
+  for (int k = n - 1; k >= 1; --k) {
+    const LayerDev& Lk = layer(net, k);
+    ld::EpiScores e{P, Lk.r_out_off, plane_of(Lk), Lk.b, mu, s_sr, s_fsb, t_sr};
+    if (k == n - 1)
+      ld::launch_top_scores(layer(net, n), P, e, s);
+    else
+      ld::launch_transposed_scores(layer(net, k + 1), P, mu, e, s);
+  }
+}
+
+ld_status check_bounds_problem(const ld_net* net, const float* lbk, const float* ubk, int32_t n_props,
+                               const int32_t* prop, int32_t B) {
+  if (!net || n_props < 1 || B < 0 || (B > 0 && (!lbk || !ubk))) return LD_ERR_ARG;
+  if (!prop && n_props != 1) return LD_ERR_ARG;
+  if (B > 65535) return LD_ERR_UNSUPPORTED;
+  return LD_OK;
+}
+
+}  // namespace
+
+ld_status ld_branching_scores(ld_net* net, const float* lbk, const float* ubk, int32_t n_props, const int32_t* prop,
+                              const int8_t* masks, int32_t B, float* s_sr, float* s_fsb, float* t_sr, void* stream) {
+  ld_status st = check_bounds_problem(net, lbk, ubk, n_props, prop, B);
+  if (st != LD_OK) return st;
+  if (B == 0) return LD_OK;
+  if ((st = ensure_ws(net, B)) != LD_OK) return st;
+  cudaStream_t s = S(stream);
+  const Problem P = make_problem(net, nullptr, nullptr, lbk, ubk, n_props, prop, masks, B);
+  scores_sweep(net, P, net->g, s_sr, s_fsb, t_sr, s);
+  return last_error();
+}
+
+ld_status ld_branch(ld_net* net, const float* lb0, const float* ub0, const float* lbk, const float* ubk,
+                    int32_t n_props, const int32_t* prop, const int8_t* masks, int32_t B, int32_t rule,
+                    float threshold, int32_t* decision, double* child_bounds, void* stream) {
+  ld_status st = check_bounds_problem(net, lbk, ubk, n_props, prop, B);
+  if (st != LD_OK) return st;
+  if (rule < LD_BRANCH_SR || rule > LD_BRANCH_FSB || (B > 0 && !decision)) return LD_ERR_ARG;
+  if (rule == LD_BRANCH_FSB && (!lb0 || !ub0)) return LD_ERR_ARG;
+  if (B == 0) return LD_OK;
+  if ((st = ensure_ws(net, B)) != LD_OK) return st;
+  cudaStream_t s = S(stream);
+  const Problem P = make_problem(net, lb0, ub0, lbk, ubk, n_props, prop, masks, B);
+  float *s_sr = net->m, *s_fsb = net->v, *t_sr = net->xB;
+  scores_sweep(net, P, net->g, s_sr, s_fsb, t_sr, s);
+  if (rule != LD_BRANCH_FSB) {
+    ld::launch_sr_decision(P, rule == LD_BRANCH_SR ? s_sr : s_fsb, t_sr, threshold, decision, s);
+    return last_error();
+  }
+  // FSB: candidates, their children's bounds, the children's output bounds
+  // (layer-wise best of CROWN and WK, one objective row per child and rule)
+  const int C = 2 * (net->n - 1);
+  const size_t owners = (size_t)B * C * 2, N = (size_t)net->N;
+  const size_t b_cand = align256(4 * (size_t)B * C), b_box = align256(4 * owners), b_out = align256(8 * owners);
+  const size_t b_bnd = align256(4 * owners * N);
+  const size_t extra = b_cand + b_box + b_out + 2 * b_bnd;
+  ld::IbLayerArgs A{};
+  char* x = nullptr;
+  if ((st = ib_args(net, owners * 2 * 2, extra, A, &x)) != LD_OK) return st;
+  int32_t* cand = reinterpret_cast<int32_t*>(x);
+  int32_t* box = reinterpret_cast<int32_t*>(x + b_cand);
+  double* child = reinterpret_cast<double*>(x + b_cand + b_box);
+  float* clb = reinterpret_cast<float*>(x + b_cand + b_box + b_out);
+  float* cub = reinterpret_cast<float*>(x + b_cand + b_box + b_out + b_bnd);
+  ld::launch_fsb_candidates(P, net->L, s_fsb, t_sr, cand, s);
+  ld::launch_fsb_children(P, cand, C, clb, cub, box, s);
+  A.n_owners = (int)owners;
+  A.n_rules = 2;
+  A.rule0 = 0;
+  A.lbk = clb;
+  A.ubk = cub;
+  A.l0 = lb0;
+  A.u0 = ub0;
+  A.box_row = box;
+  A.n_boxes = n_props;
+  A.mask = nullptr;
+  A.out_lb = child;
+  const cudaError_t e = ld::launch_ib_layer(net->L, net->n, A, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  ld::launch_fsb_pick(B, C, cand, child, decision, s);
+  if (child_bounds)
+    cudaMemcpyAsync(child_bounds, child, sizeof(double) * owners, cudaMemcpyDeviceToDevice, s);
+  return last_error();
+}
+
+ld_status ld_upper_bound(ld_net* net, const float* lb0, const float* ub0, const float* lbk, const float* ubk,
+                         int32_t n_props, const int32_t* prop, const int8_t* masks, int32_t B, const float* rho,
+                         double* ub, float* x0, void* stream) {
+  ld_status st = check_problem(net, lb0, ub0, lbk, ubk, n_props, B);
+  if (st != LD_OK) return st;
+  if (B > 0 && (!rho || !ub)) return LD_ERR_ARG;
+  if (B == 0) return LD_OK;
+  if ((st = ensure_ws(net, B)) != LD_OK) return st;
+  cudaStream_t s = S(stream);
+  const Problem P = make_problem(net, lb0, ub0, lbk, ubk, n_props, prop, masks, B);
+  // x0* = box argmin of -g_0^T x0 with g_0 = W_1^T rho_1 (Eq. box_bounds_sol)
+  ld::EpiArgmin ea{P, 0, 0, 0, rho, net->x, net->xB, nullptr, nullptr};
+  ld::launch_transposed_argmin(layer(net, 1), nullptr, P, rho, ea, s);
+  for (int k = 1; k <= net->n; ++k) {
+    const LayerDev& L = layer(net, k);
+    ld::EpiEval ev{P, k < net->n ? x_off(net, k) : 0, plane_of(L), k == net->n ? 1 : 0, L.b, net->x, ub};
+    ld::launch_forward_eval(L, P, net->x, ev, s);
+  }
+  if (x0)
+    cudaMemcpy2DAsync(x0, sizeof(float) * net->n0, net->x, sizeof(float) * net->XS, sizeof(float) * net->n0, B,
+                      cudaMemcpyDeviceToDevice, s);
   return last_error();
 }
 

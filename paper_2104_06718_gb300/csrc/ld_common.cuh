@@ -256,6 +256,58 @@ struct EpiStore {
   }
 };
 
+// Transposed pass -> branching scores of layer k (Eq. babsr-scores, Eq.
+// fsb-scores) at lam_k = g, and mu_k = [u]_+ / ([u]_+ - [l]_-) lam_k for the
+// next pass of the backward recursion (clamped bounds of the subdomain).
+struct EpiScores {
+  Problem P;
+  int r_off;           // layer k in the flat ReLU vector
+  int plane;           // outputs per channel of layer k (its bias index)
+  const float* bias;   // bias of layer k
+  float* mu;           // [B, N]: slope * lam for the next transposed pass
+  float* s_sr;         // [B, N] or nullptr
+  float* s_fsb;        // [B, N] or nullptr
+  float* t_sr;         // [B, N] or nullptr
+  __device__ __forceinline__ void operator()(int b, int i, float lam) const {
+    const int j = r_off + i;
+    float l, u;
+    clamped_bounds(P, b, j, l, u);
+    const float up = fmaxf(u, 0.f), lo = fminf(l, 0.f);
+    mu[(size_t)b * P.N + j] = up - lo > 0.f ? up / (up - lo) * lam : 0.f;
+    float ssr = 0.f, sfsb = 0.f, tsr = 0.f;
+    if (l < 0.f && u > 0.f) {
+      const float d = u - l;
+      const float lb = lam * bias[i / plane];
+      const float common = -(u / d) * lb + (u * l / d) * fmaxf(lam, 0.f);
+      ssr = fabsf(fmaxf(0.f, lb) + common);
+      sfsb = fabsf(fminf(0.f, lb) + common);
+      tsr = -(u * l / d) * fmaxf(lam, 0.f);
+    }
+    const size_t o = (size_t)b * P.N + j;
+    if (s_sr) s_sr[o] = ssr;
+    if (s_fsb) s_fsb[o] = sfsb;
+    if (t_sr) t_sr[o] = tsr;
+  }
+};
+
+// Forward pass -> the network itself: x_{k+1} = relu(W_{k+1} x_k + b_{k+1})
+// into the x buffer, or for the last layer the output into out[b] (an upper
+// bound on the minimum when x_0 is in the box, Sec. 5.1.3).
+struct EpiEval {
+  Problem P;
+  int x_off;           // layer k+1 in the x buffer (ignored for the last layer)
+  int plane;
+  int last;
+  const float* bias;
+  float* x;            // [B, XS]
+  double* out;         // [B] (last layer)
+  __device__ __forceinline__ void operator()(int b, int jj, float acc) const {
+    const float v = acc + bias[jj / plane];
+    if (last) out[b] = (double)v;
+    else x[(size_t)b * P.XS + x_off + jj] = fmaxf(v, 0.f);
+  }
+};
+
 // Library-wide count of kernel launches (every launcher calls this once per
 // kernel it launches); read through ld_launch_count.
 void count_launch(int n = 1);
@@ -412,6 +464,27 @@ void launch_forward_adam(const LayerDev& L, const Problem& P, const float* x, Ep
 void launch_forward_record(const LayerDev& L, const Problem& P, const float* x, EpiRecord epi,
                            cudaStream_t s);
 void launch_forward_store(const LayerDev& L, const Problem& P, const float* x, EpiStore epi, cudaStream_t s);
+void launch_transposed_scores(const LayerDev& L, const Problem& P, const float* mu, EpiScores epi, cudaStream_t s);
+void launch_top_scores(const LayerDev& Ln, const Problem& P, EpiScores epi, cudaStream_t s);
+void launch_forward_eval(const LayerDev& L, const Problem& P, const float* x, EpiEval epi, cudaStream_t s);
+
+// Branching (ld_branch.cu).
+// Per subdomain and layer k = 1..n-1: the argmax (first index on ties) of
+// s_FSB and of t_SR over layer k's ReLUs (flat indices; -1 where the layer
+// has no ambiguous ReLU): cand [B, 2 (n-1)].
+void launch_fsb_candidates(const Problem& P, const std::vector<LayerDev>& Ls, const float* s_fsb, const float* t_sr,
+                           int32_t* cand, cudaStream_t s);
+// Per subdomain the argmax of s (or of t where s's maximum does not exceed
+// the threshold) over all ReLUs: SR / mSR decisions [B] (-1: none ambiguous).
+void launch_sr_decision(const Problem& P, const float* s, const float* t, float threshold, int32_t* out,
+                        cudaStream_t s_);
+// Children's clamped bounds: owner (b, c, h) gets subdomain b's clamped bounds
+// with candidate c split passing (h = 0) or blocking (h = 1): [B * C * 2, N];
+// box[owner] = the subdomain's property.
+void launch_fsb_children(const Problem& P, const int32_t* cand, int C, float* lbk, float* ubk, int32_t* box,
+                         cudaStream_t s);
+// FSB's choice: the candidate whose worse child bound is the largest.
+void launch_fsb_pick(int B, int C, const int32_t* cand, const double* child, int32_t* out, cudaStream_t s);
 
 // Proximal solver (ld_prox.cu): Algorithm 2's elementwise and per-subdomain steps.
 // Arrays: lam [B, N] (lambda), pi [B, N] (momentum), xB [B, N] and xA [B, N + 1]
@@ -475,6 +548,7 @@ struct IbLayerArgs {
   float* mu_b;
   int64_t chunk_rows;
   double gamma_M;           // FP64 constant of the per-row sums
+  double* out_lb;           // layer k = n (the output): lower bound per owner [owners] instead of lbk/ubk
 };
 size_t ib_rows_per_owner(const std::vector<LayerDev>& Ls, int k, int n_rules);
 cudaError_t launch_ib_layer(const std::vector<LayerDev>& Ls, int k, const IbLayerArgs& A, cudaStream_t s);

@@ -241,6 +241,7 @@ struct IbFinish {
   const int8_t* mask;       // [owners, N] or nullptr
   float* lbk;
   float* ubk;
+  double* out_lb;           // output layer: the lower bound per owner (nullptr: lbk/ubk)
 };
 
 // Layer-wise best over the rules: l = max of the lower bounds, u = min of
@@ -259,6 +260,10 @@ __global__ void ib_finish_kernel(IbFinish f) {
         if (sg == 0) lo = fmax(lo, b);
         else up = fmin(up, -b);
       }
+    if (f.out_lb) {
+      f.out_lb[owner] = lo;
+      continue;
+    }
     float l = __double2float_rd(lo), u = __double2float_ru(up);
     const size_t j = (size_t)owner * f.N + f.r_off + i;
     if (f.mask) {
@@ -338,7 +343,7 @@ cudaError_t launch_ib_layer(const std::vector<LayerDev>& Ls, int k, const IbLaye
       nxt = t;
     }
   }
-  IbFinish f{A.n_owners, n_k, A.n_rules, A.N, Lk.r_out_off, A.acc, A.gamma_M, A.mask, A.lbk, A.ubk};
+  IbFinish f{A.n_owners, n_k, A.n_rules, A.N, Lk.r_out_off, A.acc, A.gamma_M, A.mask, A.lbk, A.ubk, A.out_lb};
   const int64_t total = (int64_t)A.n_owners * n_k;
   const int grid = (int)((total + 255) / 256 < 65535 ? (total + 255) / 256 : 65535);
   count_launch();

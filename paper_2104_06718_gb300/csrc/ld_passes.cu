@@ -456,6 +456,19 @@ void launch_forward_store(const LayerDev& L, const Problem& P, const float* x, E
   forward(L, P, x, epi, s);
 }
 
+void launch_transposed_scores(const LayerDev& L, const Problem& P, const float* mu, EpiScores epi, cudaStream_t s) {
+  transposed(L, P, mu, epi, s);
+}
+
+void launch_top_scores(const LayerDev& Ln, const Problem& P, EpiScores epi, cudaStream_t s) {
+  count_launch();
+  top_kernel<EpiScores><<<grid1d((size_t)P.B * Ln.n_in), NT, 0, s>>>(P.B, Ln.n_in, Ln.W, epi);
+}
+
+void launch_forward_eval(const LayerDev& L, const Problem& P, const float* x, EpiEval epi, cudaStream_t s) {
+  forward(L, P, x, epi, s);
+}
+
 void launch_empty_flags(const Problem& P, int8_t* empty, int* status, cudaStream_t s) {
   if (P.B > 0) {
     count_launch();

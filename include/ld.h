@@ -284,6 +284,32 @@ ld_status ld_bound_proximal(ld_net* net, const float* lb0, const float* ub0, con
                             const int8_t* split_masks, int32_t B, int32_t n_iters, const ld_prox_opts* opts,
                             const float* rho_in, float* rho_out, double* out, void* stream);
 
+/* The dual of Dvijotham et al. (Sec. 2.2.2, Eq. dj_prob-main) solved by
+ * supergradient ascent with Adam (DSG+, the comparison solver of Sec. 7.2),
+ * and its decomposed evaluation (Dec-DSG+, Theorem 1).  With multipliers mu_k
+ * on x_hat_k = W_k x_{k-1} + b_k and lambda_k on x_k = relu(x_hat_k), the dual
+ * d_O(mu, lambda) separates into box minima over x_0, x_k in [relu(l),
+ * relu(u)] and x_hat_k in [l, u] (the last a piecewise-linear minimum at l,
+ * 0 or u); its supergradient is (x_hat_k - W_k x_{k-1} - b_k,
+ * x_k - relu(x_hat_k)).  Started from CROWN (Prop. 3: mu = the CROWN duals,
+ * lambda_{k-1} = W_k^T mu_k, lambda_{n-1} = -W_n^T 1, where d_O is the CROWN
+ * bound) or from mu_in / lam_in (init GIVEN; lam_in NULL takes lambda from
+ * mu as at the CROWN start).  opts as ld_bound (FP32 only; step sizes,
+ * Adam constants, t_offset / t_total; engine, tile and threads are ignored:
+ * the passes run one launch per layer).
+ *   out_dec [device] NULL or [B] double: q(mu_T), the LD dual at DSG+'s mu
+ *   (Dec-DSG+), in FP64 with outward slack as ld_bound -- a sound bound, at
+ *   least d_O(mu_T, lambda_T) by Theorem 1.
+ *   out_dsg [device] NULL or [B] double: d_O(mu_T, lambda_T), DSG+'s own
+ *   bound (FP32 terms summed in FP64, not rounded outward).
+ *   mu_out, lam_out [device] NULL or [B, N]: the final duals.
+ * Errors: as ld_bound; LD_ERR_UNSUPPORTED for BF16 precision; LD_ERR_ARG if
+ * both outputs are NULL. */
+ld_status ld_bound_dsg(ld_net* net, const float* lb0, const float* ub0, const float* lbk, const float* ubk,
+                       int32_t n_props, const int32_t* prop_of_subdomain, const int8_t* split_masks, int32_t B,
+                       int32_t n_iters, const ld_opts* opts, const float* mu_in, const float* lam_in, float* mu_out,
+                       float* lam_out, double* out_dec, double* out_dsg, void* stream);
+
 /* Branching scores of every ReLU (Sec. 4.1, Eq. babsr-scores and Eq.
  * fsb-scores) from one backward pass of the WK upper slopes:
  * lam_{n-1} = -W_n^T 1, lam_{k-1} = W_k^T ([u]_+ / ([u]_+ - [l]_-) lam_k); for

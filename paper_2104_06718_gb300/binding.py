@@ -34,7 +34,7 @@ EXPORTED = [
     "ld_bound", "ld_dual_supergradient", "ld_bound_backward",
     "ld_net_profile", "ld_net_profile_read", "ld_launch_count", "ld_net_tuned", "ld_final_bound_noalloc",
     "ld_test_inject_alloc_failure", "ld_intermediate_bounds_propagated", "ld_prox_opts_default", "ld_bound_proximal",
-    "ld_branching_scores", "ld_branch", "ld_upper_bound",
+    "ld_branching_scores", "ld_branch", "ld_upper_bound", "ld_bound_dsg",
 ]
 PHASES = {"iter": 0, "final": 1, "init": 2, "ibp": 3, "backward": 4}
 
@@ -104,6 +104,7 @@ def load_library(path: str = LIB_PATH):
     lib.ld_branching_scores.argtypes = [vp, vp, vp, i32, vp, vp, i32, vp, vp, vp, vp]
     lib.ld_branch.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, i32, i32, C.c_float, vp, vp, vp]
     lib.ld_upper_bound.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, i32, vp, vp, vp, vp]
+    lib.ld_bound_dsg.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, i32, i32, C.POINTER(Opts), vp, vp, vp, vp, vp, vp, vp]
     for name in EXPORTED:
         if name not in ("ld_opts_default", "ld_status_str", "ld_prox_opts_default"):
             getattr(lib, name).restype = C.c_int
@@ -400,6 +401,28 @@ def ld_bound_proximal(net: Net, lb0, ub0, lbk, ubk, prop=None, masks=None, n_ite
                                       _ptr(prop), _ptr(masks), B, int(n_iters), C.byref(oc), _ptr(rho_in),
                                       _ptr(rho_out), _ptr(out), _stream()), "ld_bound_proximal")
     return (out, rho_out) if return_rho else out
+
+
+def ld_bound_dsg(net: Net, lb0, ub0, lbk, ubk, prop=None, masks=None, n_iters: int = 100,
+                 opts: Options | None = None, mu_in=None, lam_in=None, B: int | None = None,
+                 return_duals: bool = False):
+    """DSG+ (Sec. 2.2.2): (Dec-DSG+ bound q(mu_T) [B] float64, sound; DSG+'s own
+    d_O(mu_T, lambda_T) [B] float64); with return_duals also (mu_T, lambda_T)."""
+    lb0, ub0, lbk, ubk, prop, masks, B = _problem(lb0, ub0, lbk, ubk, prop, masks, B)
+    o = opts or Options()
+    if mu_in is not None and o.init != "given":
+        o = Options(**{**o.__dict__, "init": "given"})
+    mu_in = None if mu_in is None else _dev(mu_in, torch.float32)
+    lam_in = None if lam_in is None else _dev(lam_in, torch.float32)
+    dec = torch.empty(B, dtype=torch.float64, device="cuda")
+    dsg = torch.empty(B, dtype=torch.float64, device="cuda")
+    f = (lambda: torch.empty((B, net.N), dtype=torch.float32, device="cuda")) if return_duals else (lambda: None)
+    mu_out, lam_out = f(), f()
+    oc = o.to_c()
+    _check(net._lib.ld_bound_dsg(net.handle, _ptr(lb0), _ptr(ub0), _ptr(lbk), _ptr(ubk), lbk.shape[0], _ptr(prop),
+                                 _ptr(masks), B, int(n_iters), C.byref(oc), _ptr(mu_in), _ptr(lam_in), _ptr(mu_out),
+                                 _ptr(lam_out), _ptr(dec), _ptr(dsg), _stream()), "ld_bound_dsg")
+    return (dec, dsg, mu_out, lam_out) if return_duals else (dec, dsg)
 
 
 def ld_branching_scores(net: Net, lbk, ubk, prop=None, masks=None, B: int | None = None):

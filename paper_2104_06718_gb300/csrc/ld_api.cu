@@ -80,6 +80,9 @@ struct ld_net {
   // workspace of the proximal solver: x_hat_A and z_A [B, N + 1], lambda' [B, N]
   void* prox_ws = nullptr;
   int prox_B = -1;
+  // workspace of DSG+: lambda and its Adam moments [B, N], the dual value [B]
+  void* dsg_ws = nullptr;
+  int dsg_B = -1;
   // the per-iteration launches of the layerwise and BF16 engines, captured
   // into one executable graph (re-captured and updated in place each call)
   bool graphs = true;
@@ -855,6 +858,7 @@ ld_status ld_net_destroy(ld_net* net) {
   if (net->tc_ws) cudaFree(net->tc_ws);
   if (net->ib_ws) cudaFree(net->ib_ws);
   if (net->prox_ws) cudaFree(net->prox_ws);
+  if (net->dsg_ws) cudaFree(net->dsg_ws);
   ld::free_tc_net(&net->tc);
   if (net->d_W) cudaFree(net->d_W);
   if (net->d_Wx) cudaFree(net->d_Wx);
@@ -997,6 +1001,7 @@ ld_status ensure_prox_ws(ld_net* net, int B) {
   const size_t a = align256(4 * Bn * (N + 1)), l = align256(4 * Bn * N);
   cudaDeviceSynchronize();
   if (net->prox_ws) cudaFree(net->prox_ws);
+  if (net->dsg_ws) cudaFree(net->dsg_ws);
   net->prox_ws = nullptr;
   net->prox_B = -1;
   void* p = nullptr;
@@ -1075,6 +1080,132 @@ ld_status run_prox_iterations(ld_net* net, const Problem& P, const ld::ProxState
 }
 
 }  // namespace
+
+namespace {
+
+struct DsgBufs {
+  float* lam;
+  float* lm;
+  float* lv;
+  double* dval;
+};
+
+ld_status ensure_dsg_ws(ld_net* net, int B, DsgBufs& D) {
+  const size_t Bn = (size_t)(B > 0 ? B : 1), N = (size_t)net->N;
+  const size_t a = align256(4 * Bn * N), d = align256(8 * Bn);
+  if (B > net->dsg_B) {
+    cudaDeviceSynchronize();
+    if (net->dsg_ws) cudaFree(net->dsg_ws);
+    net->dsg_ws = nullptr;
+    net->dsg_B = -1;
+    void* p = nullptr;
+    const cudaError_t e = ld::dev_malloc(&p, 3 * a + d);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return cuda_status(e);
+    }
+    net->dsg_ws = p;
+    net->dsg_B = (int)Bn;
+  }
+  const size_t aw = align256(4 * (size_t)net->dsg_B * N);
+  char* c = static_cast<char*>(net->dsg_ws);
+  D.lam = reinterpret_cast<float*>(c);
+  D.lm = reinterpret_cast<float*>(c + aw);
+  D.lv = reinterpret_cast<float*>(c + 2 * aw);
+  D.dval = reinterpret_cast<double*>(c + 3 * aw);
+  return LD_OK;
+}
+
+// One pass over the layers k = n-1 .. 0 of the DSG+ minimisation: the
+// transposed pass of layer k+1 (mu_{k+1}) with the separable minimum of layer
+// k, then (mode 0) the forward pass of layer k+1 with the Adam step on mu_{k+1}
+// from its supergradient x_hat_{k+1} - W_{k+1} x_k - b_{k+1}.
+void dsg_sweep(ld_net* net, const Problem& P, const DsgBufs& D, int mode, const ld_opts& o, ld::AdamStep st,
+               cudaStream_t s) {
+  const int n = net->n;
+  for (int k = n - 1; k >= 0; --k) {
+    ld::EpiDsgT e{P, k, r_off(net, k), x_off(net, k), k >= 1 ? plane_of(layer(net, k)) : 1,
+                  k >= 1 ? layer(net, k).b : nullptr, net->rho, D.lam, D.lm, D.lv, net->x, net->xB, D.dval,
+                  net->bn, mode, o.beta1, o.beta2, o.eps, st};
+    if (k == n - 1)
+      ld::launch_top_dsg(layer(net, n), P, e, s);
+    else
+      ld::launch_transposed_dsg(layer(net, k + 1), P, net->rho, e, s);
+    if (mode == 0 && k + 1 <= n - 1) {
+      const LayerDev& Lk1 = layer(net, k + 1);
+      ld::EpiAdam ep{P, Lk1.r_out_off, plane_of(Lk1), Lk1.b, net->xB, net->rho, net->m, net->v,
+                     o.beta1, o.beta2, o.eps, st};
+      ld::launch_forward_adam(Lk1, P, net->x, ep, s);
+    }
+  }
+}
+
+}  // namespace
+
+ld_status ld_bound_dsg(ld_net* net, const float* lb0, const float* ub0, const float* lbk, const float* ubk,
+                       int32_t n_props, const int32_t* prop, const int8_t* masks, int32_t B, int32_t n_iters,
+                       const ld_opts* opts, const float* mu_in, const float* lam_in, float* mu_out, float* lam_out,
+                       double* out_dec, double* out_dsg, void* stream) {
+  ld_status st = check_problem(net, lb0, ub0, lbk, ubk, n_props, B);
+  if (st != LD_OK) return st;
+  if (n_iters < 0 || (!out_dec && !out_dsg && B > 0)) return LD_ERR_ARG;
+  ld_opts o;
+  if (opts) o = *opts; else ld_opts_default(&o);
+  if ((st = check_opts(o)) != LD_OK) return st;
+  if (o.precision != LD_PREC_FP32) return LD_ERR_UNSUPPORTED;
+  if (o.init == LD_INIT_GIVEN && !mu_in && B > 0) return LD_ERR_ARG;
+  if (B == 0) return LD_OK;
+  if ((st = ensure_ws(net, B)) != LD_OK) return st;
+  DsgBufs D;
+  if ((st = ensure_dsg_ws(net, B, D)) != LD_OK) return st;
+  cudaStream_t s = S(stream);
+  const Problem P = make_problem(net, lb0, ub0, lbk, ubk, n_props, prop, masks, B);
+  const size_t BN = (size_t)B * net->N;
+  const int T_sched = o.t_total > 0 ? o.t_total : o.t_offset + n_iters;
+  {
+    PhaseMark pm(net, LD_PHASE_INIT, s);
+    ld::launch_empty_flags(P, net->empty, net->d_status, s);
+    if (o.init == LD_INIT_GIVEN)
+      cudaMemcpyAsync(net->rho, mu_in, sizeof(float) * BN, cudaMemcpyDeviceToDevice, s);
+    else if (o.init == LD_INIT_ZERO)
+      cudaMemsetAsync(net->rho, 0, sizeof(float) * BN, s);
+    else
+      crown_sweep(net, P, s);
+    if (o.init == LD_INIT_GIVEN && lam_in)
+      cudaMemcpyAsync(D.lam, lam_in, sizeof(float) * BN, cudaMemcpyDeviceToDevice, s);
+    else
+      dsg_sweep(net, P, D, 2, o, ld::AdamStep{}, s);   // lambda_k = W_{k+1}^T mu_{k+1} (Prop. 3 / Theorem 1)
+    cudaMemsetAsync(net->m, 0, sizeof(float) * BN, s);
+    cudaMemsetAsync(net->v, 0, sizeof(float) * BN, s);
+    cudaMemsetAsync(D.lm, 0, sizeof(float) * BN, s);
+    cudaMemsetAsync(D.lv, 0, sizeof(float) * BN, s);
+  }
+  if (n_iters > 0) {
+    PhaseMark pm(net, LD_PHASE_ITER, s);
+    st = run_graphed(net, s, [&](cudaStream_t cs) {
+      for (int t = 0; t < n_iters; ++t) dsg_sweep(net, P, D, 0, o, adam_step(o, o.t_offset + t, T_sched), cs);
+      return last_error();
+    });
+    if (st != LD_OK) return st;
+  }
+  {
+    PhaseMark pm(net, LD_PHASE_FINAL, s);
+    if (out_dec) {
+      if (o.fp64_final)
+        final_fp64(net, P, out_dec, s);
+      else
+        final_fp32(net, P, out_dec, nullptr, nullptr, s);
+    }
+    if (out_dsg) {
+      cudaMemsetAsync(D.dval, 0, sizeof(double) * B, s);
+      dsg_sweep(net, P, D, 1, o, ld::AdamStep{}, s);
+      ld::launch_record_finish(P, D.dval, out_dsg, s);
+    }
+  }
+  if (mu_out) cudaMemcpyAsync(mu_out, net->rho, sizeof(float) * BN, cudaMemcpyDeviceToDevice, s);
+  if (lam_out) cudaMemcpyAsync(lam_out, D.lam, sizeof(float) * BN, cudaMemcpyDeviceToDevice, s);
+  return last_error();
+}
 
 ld_status ld_bound_proximal(ld_net* net, const float* lb0, const float* ub0, const float* lbk, const float* ubk,
                             int32_t n_props, const int32_t* prop, const int8_t* masks, int32_t B, int32_t n_iters,

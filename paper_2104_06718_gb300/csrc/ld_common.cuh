@@ -308,6 +308,79 @@ struct EpiEval {
   }
 };
 
+// Transposed pass -> the separable minimisation of the dual of Eq.
+// (dj_prob-main) at (mu, lambda) for layer k (DSG+, Sec. 2.2.2), g = g_k =
+// W_{k+1}^T mu_{k+1} (mu_n = -1):
+//   k = 0: x_0 = box argmin of -g_0^T x_0 (Eq. box_bounds_sol);
+//   k >= 1: x_k = box argmin over [relu(l), relu(u)] of (lambda - g) x (upper
+//   end where the coefficient is <= 0); x_hat_k = first strict minimum of
+//   mu x_hat - lambda relu(x_hat) among l, 0 (when l < 0 < u), u.
+// mode 0: Adam ascent step on lambda with the supergradient x_k - relu(x_hat_k);
+// mode 1: accumulate the minima (and -mu^T b_k) into dval[b] (d_O without b_n);
+// mode 2: lambda <- g (the start of Prop. 3 / Theorem 1's lambda').
+struct EpiDsgT {
+  Problem P;
+  int layer;           // k
+  int r_off;           // layer k in the flat ReLU vector (k >= 1)
+  int x_off;           // layer k in the x buffer
+  int plane;           // outputs per channel of layer k (its bias index)
+  const float* bias;   // bias of layer k (k >= 1)
+  const float* mu;     // [B, N]
+  float* lam;          // [B, N]
+  float* lm;           // [B, N] Adam moments of lambda
+  float* lv;
+  float* x;            // [B, XS]
+  float* xh;           // [B, N] x_hat_k
+  double* dval;        // [B] (mode 1)
+  double bn;           // mode 1: b_n, added once per subdomain with the box term
+  int mode;
+  float beta1, beta2, eps;
+  AdamStep st;
+  __device__ __forceinline__ void operator()(int b, int i, float g) const {
+    if (layer == 0) {
+      const int p = prop_of(P, b);
+      const float l0 = P.l0[(size_t)p * P.n0 + i], u0 = P.u0[(size_t)p * P.n0 + i];
+      x[(size_t)b * P.XS + i] = g >= 0.f ? u0 : l0;
+      if (mode == 1 && !P.empty[b])
+        atomicAdd(&dval[b], fmin(-(double)g * l0, -(double)g * u0) + (i == 0 ? bn : 0.0));
+      return;
+    }
+    const size_t j = (size_t)b * P.N + r_off + i;
+    if (mode == 2) {
+      lam[j] = g;
+      return;
+    }
+    float l, u;
+    clamped_bounds(P, b, r_off + i, l, u);
+    const float m = mu[j], la = lam[j];
+    const float c = la - g;
+    const float xk = c <= 0.f ? fmaxf(u, 0.f) : fmaxf(l, 0.f);
+    float best = m * l - la * fmaxf(l, 0.f), arg = l;
+    if (l < 0.f && u > 0.f && 0.f < best) {
+      best = 0.f;
+      arg = 0.f;
+    }
+    const float fu = m * u - la * fmaxf(u, 0.f);
+    if (fu < best) {
+      best = fu;
+      arg = u;
+    }
+    x[(size_t)b * P.XS + x_off + i] = xk;
+    xh[j] = arg;
+    if (P.empty[b]) return;
+    if (mode == 1) {
+      atomicAdd(&dval[b], (double)c * (double)xk + (double)best - (double)m * (double)bias[i / plane]);
+      return;
+    }
+    const float s = xk - fmaxf(arg, 0.f);
+    const float mm = beta1 * lm[j] + (1.f - beta1) * s;
+    const float vv = beta2 * lv[j] + (1.f - beta2) * s * s;
+    lm[j] = mm;
+    lv[j] = vv;
+    lam[j] = la + st.alpha * (mm * st.inv_bc1) / (sqrtf(vv * st.inv_bc2) + eps);
+  }
+};
+
 // Library-wide count of kernel launches (every launcher calls this once per
 // kernel it launches); read through ld_launch_count.
 void count_launch(int n = 1);
@@ -467,6 +540,8 @@ void launch_forward_store(const LayerDev& L, const Problem& P, const float* x, E
 void launch_transposed_scores(const LayerDev& L, const Problem& P, const float* mu, EpiScores epi, cudaStream_t s);
 void launch_top_scores(const LayerDev& Ln, const Problem& P, EpiScores epi, cudaStream_t s);
 void launch_forward_eval(const LayerDev& L, const Problem& P, const float* x, EpiEval epi, cudaStream_t s);
+void launch_transposed_dsg(const LayerDev& L, const Problem& P, const float* mu, EpiDsgT epi, cudaStream_t s);
+void launch_top_dsg(const LayerDev& Ln, const Problem& P, EpiDsgT epi, cudaStream_t s);
 
 // Branching (ld_branch.cu).
 // Per subdomain and layer k = 1..n-1: the argmax (first index on ties) of

@@ -469,6 +469,15 @@ void launch_forward_eval(const LayerDev& L, const Problem& P, const float* x, Ep
   forward(L, P, x, epi, s);
 }
 
+void launch_transposed_dsg(const LayerDev& L, const Problem& P, const float* mu, EpiDsgT epi, cudaStream_t s) {
+  transposed(L, P, mu, epi, s);
+}
+
+void launch_top_dsg(const LayerDev& Ln, const Problem& P, EpiDsgT epi, cudaStream_t s) {
+  count_launch();
+  top_kernel<EpiDsgT><<<grid1d((size_t)P.B * Ln.n_in), NT, 0, s>>>(P.B, Ln.n_in, Ln.W, epi);
+}
+
 void launch_empty_flags(const Problem& P, int8_t* empty, int* status, cudaStream_t s) {
   if (P.B > 0) {
     count_launch();

@@ -5,9 +5,14 @@ minimiser of q as the first primal point, J sweeps of block-coordinate
 Frank-Wolfe per iteration with the optimal step of Eq. (optimal-gamma-gauss),
 and the dual update with momentum (App. D).  Tolerances (relative to
 max(|b|, 1)):
-  * bound after 1 and 3 iterations, both of the paper's settings     1e-5
-  * bound after 50 iterations: 1e-3 max / 3e-4 median (like the supergradient's
-    long runs, a near-tie decided the other way moves the whole trajectory)
+  * bound after 1 and 3 iterations, the incomplete-verification setting   1e-5
+  * the branch-and-bound setting (eta = 100) after 1 and 3 iterations and
+    every setting after 50: the proximal iterates are far more sensitive to
+    rounding than the supergradient ones (a perturbation of 1e-7 of the
+    oracle's own start moves its bound by up to 8e-4 after 3 iterations at
+    eta = 100 and by up to 9e-3 after 50 on Deep; tests/test_oracle_proximal.py),
+    so these runs are held to three times the oracle's own spread under that
+    perturbation, measured in the test on the same problem, plus 1e-5
   * tiny MLPs after 200 iterations: never above the Planet LP optimum
   * empty subdomains +inf; two runs bitwise equal (fixed-order reductions)
 """
@@ -40,16 +45,37 @@ def rel(a, b):
     return np.abs(np.asarray(a, np.float64) - np.asarray(b, np.float64)) / np.maximum(np.abs(np.asarray(b, np.float64)), 1.0)
 
 
-def oracle_prox(pb, T, s):
+def oracle_prox(pb, T, s, perturb=0.0):
+    """The oracle's bounds; with perturb > 0, from a CROWN start perturbed by
+    that relative amount (seeded), to measure the method's own sensitivity."""
     on = pb["net"]
     L0, U0, lbs, ubs, empty = oracle_lists(on, pb)
     out = np.full(pb["B"], np.inf)
     keep = ~empty
     if keep.any():
         sel = lambda l: [None] + [x[keep] for x in l[1:]]
-        r = px.proximal_solver(on, L0[keep], U0[keep], sel(lbs), sel(ubs), T, s)
+        lbs, ubs = sel(lbs), sel(ubs)
+        lam0 = None
+        if perturb:
+            rc, _ = oracle.crown_init(on, lbs, ubs)
+            rng = np.random.default_rng(0)
+            lam0 = [None] + [x * (1 + perturb * rng.standard_normal(x.shape)) for x in rc[1:]]
+        r = px.proximal_solver(on, L0[keep], U0[keep], lbs, ubs, T, s, lam0=lam0)
         out[keep] = r.q_final
     return out
+
+
+def assert_within_own_spread(out, pb, T, so):
+    """|gpu - oracle| within 3x the oracle's own spread under a 1e-7
+    perturbation of its start (max and median), plus 1e-5."""
+    ref = oracle_prox(pb, T, so)
+    alt = oracle_prox(pb, T, so, perturb=1e-7)
+    fin = np.isfinite(ref)
+    assert np.array_equal(np.isfinite(out), fin)
+    r = rel(out[fin], ref[fin])
+    spread = rel(alt[fin], ref[fin])
+    assert r.max() <= 3 * spread.max() + 1e-5, (r.max(), spread.max())
+    assert np.median(r) <= 3 * np.median(spread) + 1e-5, (np.median(r), np.median(spread))
 
 
 def run_gpu(pb, T, o):
@@ -67,6 +93,9 @@ def test_prox_short_runs_match_oracle(name, T, setting):
     pb = conv_problem(name, 16, depth=(0, 8), block=8)
     go, so = SETTINGS[setting]
     out = run_gpu(pb, T, go)
+    if setting == "bab":
+        assert_within_own_spread(out, pb, T, so)
+        return
     ref = oracle_prox(pb, T, so)
     fin = np.isfinite(ref)
     assert np.array_equal(np.isfinite(out), fin)
@@ -78,11 +107,7 @@ def test_prox_full_runs_match_oracle(name, B):
     pb = conv_problem(name, B, depth=(0, 8), block=5)
     go, so = SETTINGS["incomplete"]
     out = run_gpu(pb, 50, go)
-    ref = oracle_prox(pb, 50, so)
-    fin = np.isfinite(ref)
-    assert np.array_equal(np.isfinite(out), fin)
-    r = rel(out[fin], ref[fin])
-    assert r.max() < 1e-3 and np.median(r) < 3e-4, (r.max(), np.median(r))
+    assert_within_own_spread(out, pb, 50, so)
 
 
 def test_prox_tiny_nets_stay_below_the_lp():

@@ -14,7 +14,12 @@
   * the dual update is Eq. (lambda_updates) with mu = 0 and accumulates the
     momentum of Eq. (momentum_updates) with mu > 0;
   * planted mistakes (the step's sign, a dropped curvature term, a block
-    dual without its Augmented-Lagrangian part) make a pin fail.
+    dual without its Augmented-Lagrangian part) make a pin fail;
+  * (a measurement) the method's sensitivity to rounding: a relative
+    perturbation of 1e-7 of the CROWN start moves the bound after 50
+    iterations on the Deep convnet by more than 1e-3 -- far more than the
+    supergradient method's ~3e-4 -- which sets the tolerance of the device's
+    long runs (tests/test_gpu_proximal.py).
 """
 import numpy as np
 import pytest
@@ -182,3 +187,21 @@ def test_planted_mistakes_in_the_proximal_oracle_are_caught(monkeypatch, what):
         except AssertionError:
             failed = True
     assert failed, f"planted mistake '{what}' passed every pin"
+
+
+def test_sensitivity_of_long_runs_to_a_tiny_perturbation():
+    pb = conv_problem("deep", 12, depth=(0, 8), block=5)
+    on = pb["net"]
+    L0, U0, lbs, ubs, empty = oracle_lists(on, pb)
+    keep = ~empty
+    sel = lambda l: [None] + [x[keep] for x in l[1:]]
+    lbs, ubs, L0, U0 = sel(lbs), sel(ubs), L0[keep], U0[keep]
+    rc, _ = oracle.crown_init(on, lbs, ubs)
+    rng = np.random.default_rng(0)
+    rp = [None] + [x * (1 + 1e-7 * rng.standard_normal(x.shape)) for x in rc[1:]]
+    a = px.proximal_solver(on, L0, U0, lbs, ubs, 50, lam0=rc)
+    b = px.proximal_solver(on, L0, U0, lbs, ubs, 50, lam0=rp)
+    first = np.abs(a.q_trace[0] - b.q_trace[0]) / np.maximum(np.abs(a.q_trace[0]), 1.0)
+    final = np.abs(a.q_final - b.q_final) / np.maximum(np.abs(a.q_final), 1.0)
+    assert first.max() < 1e-6          # the perturbation itself is tiny ...
+    assert final.max() > 1e-3          # ... and the trajectory amplifies it

@@ -26,8 +26,10 @@ started from CROWN (Prop. 3: mu = rho_CROWN and lambda_{k-1} = W_k^T mu_k,
 lambda_{n-1} = -W_n^T 1, where d_O equals the CROWN bound).  Dec-DSG+
 evaluates the LD dual q at mu (Theorem 1: q(mu) >= d_O(mu, lambda)).
 Readings (listed in the design notes): box argmins take the upper end where
-the coefficient is <= 0 (as in Eq. (box_bounds_sol)); the x_hat minimum
-takes the first strict minimum in the order l, 0, u.
+the coefficient is <= 0 (as in Eq. (box_bounds_sol)); d_O is summed from
+the exact minima, while the returned x_hat (the supergradient's point) is
+the first strict minimum in the order l, 0, u with u having to win by
+2^-16 (|mu| + |lambda|) max(|l|, |u|), the LD dual's tie margin.
 """
 from __future__ import annotations
 
@@ -35,7 +37,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from .ld_oracle import AdamSettings, Net, adam_update, box_argmin, classify, crown_init
+from .ld_oracle import TIE_REL, AdamSettings, Net, adam_update, box_argmin, classify, crown_init
 
 
 @dataclass
@@ -64,16 +66,21 @@ def dsg_inner(net: Net, l0, u0, lb, ub, mu, lam) -> DsgInner:
         c = lam[k] - g[k]
         rl, ru = np.maximum(l, 0.0), np.maximum(u, 0.0)
         xk = box_argmin(c, rl, ru)
-        # x_hat: candidates l, 0 (inside the interval), u; first strict minimum
+        # x_hat: candidates l, 0 (inside the interval), u.  The value is the
+        # exact minimum; the returned point is the first strict minimum in
+        # that order, u having to win by the tie margin of the LD reading: at
+        # the CROWN start (Prop. 3) mu l and (mu - lambda) u tie exactly for
+        # every ambiguous ReLU with lambda > 0, and rounding must not decide.
         f = lambda v: mu[k] * v - lam[k] * np.maximum(v, 0.0)
-        best, arg = f(l), l.copy()
         inside = (l < 0) & (u > 0)
-        f0 = np.where(inside, 0.0, np.inf)
-        take = f0 < best
-        best, arg = np.where(take, f0, best), np.where(take, 0.0, arg)
-        fu = f(u)
-        take = fu < best
-        best, arg = np.where(take, fu, best), np.where(take, u, arg)
+        fl, f0, fu = f(l), np.where(inside, 0.0, np.inf), f(u)
+        best = np.minimum(np.minimum(fl, f0), fu)
+        pick, arg = fl, l.copy()
+        take = f0 < pick
+        pick, arg = np.where(take, f0, pick), np.where(take, 0.0, arg)
+        margin = TIE_REL * (np.abs(mu[k]) + np.abs(lam[k])) * np.maximum(np.abs(l), np.abs(u))
+        take = fu < pick - margin
+        arg = np.where(take, u, arg)
         d = d + np.sum(c * xk, axis=1) + np.sum(best, axis=1) - mu[k] @ net.L(k).bias_vector()
         x.append(xk)
         xh.append(arg)

@@ -314,7 +314,8 @@ struct EpiEval {
 //   k = 0: x_0 = box argmin of -g_0^T x_0 (Eq. box_bounds_sol);
 //   k >= 1: x_k = box argmin over [relu(l), relu(u)] of (lambda - g) x (upper
 //   end where the coefficient is <= 0); x_hat_k = first strict minimum of
-//   mu x_hat - lambda relu(x_hat) among l, 0 (when l < 0 < u), u.
+//   mu x_hat - lambda relu(x_hat) among l, 0 (when l < 0 < u), u, where u has
+//   to win by kTieRel (|mu| + |lambda|) max(|l|, |u|) (the value is the exact minimum).
 // mode 0: Adam ascent step on lambda with the supergradient x_k - relu(x_hat_k);
 // mode 1: accumulate the minima (and -mu^T b_k) into dval[b] (d_O without b_n);
 // mode 2: lambda <- g (the start of Prop. 3 / Theorem 1's lambda').
@@ -355,16 +356,17 @@ struct EpiDsgT {
     const float m = mu[j], la = lam[j];
     const float c = la - g;
     const float xk = c <= 0.f ? fmaxf(u, 0.f) : fmaxf(l, 0.f);
-    float best = m * l - la * fmaxf(l, 0.f), arg = l;
-    if (l < 0.f && u > 0.f && 0.f < best) {
-      best = 0.f;
+    // the value is the exact minimum over l, 0 (inside), u; the returned point
+    // is the first strict minimum with u winning only by the LD tie margin
+    // (the CROWN start puts mu l and (mu - lambda) u at an exact tie)
+    const float fl = m * l - la * fmaxf(l, 0.f), fu = m * u - la * fmaxf(u, 0.f);
+    float pick = fl, arg = l;
+    if (l < 0.f && u > 0.f && 0.f < pick) {
+      pick = 0.f;
       arg = 0.f;
     }
-    const float fu = m * u - la * fmaxf(u, 0.f);
-    if (fu < best) {
-      best = fu;
-      arg = u;
-    }
+    const float best = fminf(pick, fu);
+    if (fu < pick - kTieRel * (fabsf(m) + fabsf(la)) * fmaxf(fabsf(l), fabsf(u))) arg = u;
     x[(size_t)b * P.XS + x_off + i] = xk;
     xh[j] = arg;
     if (P.empty[b]) return;

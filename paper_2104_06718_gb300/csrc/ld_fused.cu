@@ -465,10 +465,13 @@ __device__ void ffc_finish(const Ctx<S, NT>& c, const LayerDev& L, const FusedLa
 
 // ------------------------------------------------------------------ blocked convs
 
-// Forward conv, blocked: item = (s, y0, x, group of GF output channels); the
-// thread computes rows y0 and y0 + ho/2 of column x.  Consecutive lanes take
-// consecutive columns of full rows, so the plane and epilogue accesses of a
-// warp fall in distinct shared-memory banks.
+// Forward conv, blocked: item = (group of GF output channels, y0, s, x), x
+// fastest; the thread computes rows y0 and y0 + ho/2 of column x of subdomain
+// s.  Consecutive lanes take consecutive columns of full rows; with the
+// subdomain second-fastest, a warp whose row is shorter than 32 columns reads
+// the same row of the next subdomain in its other lanes (a subdomain's planes
+// are xp_total floats apart, 16 banks when xp_total = 16 mod 32), instead of
+// the next row, which wraps onto the banks of the first.
 template <int KH, int KW, int ST, int GF, int S, int NT>
 __device__ void conv_fwd_blocked(const Ctx<S, NT>& c, const LayerDev& L, const FusedLayer& F, const FusedIter& it,
                                  const AdamStep& st, const Team& tm) {
@@ -479,17 +482,17 @@ __device__ void conv_fwd_blocked(const Ctx<S, NT>& c, const LayerDev& L, const F
   const int hq = F.Hp >> 1, wq = F.Wp >> 1;
   // offset of the second row's inputs: hh output rows down
   const int dsec = ST == 2 ? hh * wq : hh * ST * F.Wp;
-  const IntDiv d_wo = int_div(L.wo), d_hh = int_div(hh), d_nog = int_div(nog);
+  const IntDiv d_wo = int_div(L.wo), d_hh = int_div(hh);
   for (int e = tm.tid; e < items; e += tm.n) {
     int r = e, q = div_of(r, d_wo);
     const int x0 = r - q * L.wo;
     r = q;
+    q = r / S;
+    const int s = r - q * S;
+    r = q;
     q = div_of(r, d_hh);
     const int y = r - q * hh;
-    r = q;
-    q = div_of(r, d_nog);
-    const int og = r - q * nog;
-    const int s = q;
+    const int og = q;
     // accumulators of channel pairs (g, g+1) as float2: one packed FMA
     // (__ffma2_rn, two round-to-nearest FMAs) updates both channels
     float2 acc2[2][GF / 2];

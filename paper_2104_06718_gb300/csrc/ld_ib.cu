@@ -42,7 +42,7 @@ constexpr int NT = 256;
 
 struct IbStep {
   LayerDev L;               // layer j: this launch computes a_{j-1} = W_j^T mu_j
-  int seed;                 // 1: mu_j is the row's objective (+-e_i, layer k = j); the sums are exact
+  int seed;                 // 1: mu_j is the row's objective (+-e_i, layer k = j): a is a row of W_k, exact
   int box;                  // 1: j == 1, the epilogue adds the box term
   const float* mu_in;       // [rows of the chunk, L.n_out] (unused when seed)
   float* mu_out;            // [rows of the chunk, L.n_in]  (unused when box)
@@ -149,6 +149,19 @@ __device__ __forceinline__ double block_sum(double v, double* red, bool up) {
   return t;
 }
 
+// Seed pass: a = W_k^T (sign e_i) is sign times row i of W_k (a conv row:
+// the kernel taps of output neuron i that land on input element ii), exact.
+__device__ __forceinline__ float seed_elem(const LayerDev& L, int i, float sign, int ii) {
+  if (L.kind == LD_LAYER_FC) return sign * __ldg(L.W + (size_t)i * L.n_in + ii);
+  const int hw = L.ho * L.wo;
+  const int o = i / hw, orem = i % hw, oy = orem / L.wo, ox = orem % L.wo;
+  const int hwi = L.h * L.w;
+  const int c = ii / hwi, rem = ii % hwi, y = rem / L.w, x = rem % L.w;
+  const int ky = y + L.pad - oy * L.stride, kx = x + L.pad - ox * L.stride;
+  if (ky < 0 || ky >= L.kh || kx < 0 || kx >= L.kw) return 0.f;
+  return sign * __ldg(L.W + (((size_t)o * L.cin + c) * L.kh + ky) * L.kw + kx);
+}
+
 __global__ void __launch_bounds__(NT) ib_step_kernel(IbStep st) {
   extern __shared__ float mu[];
   __shared__ double red[NT / 32];
@@ -158,9 +171,7 @@ __global__ void __launch_bounds__(NT) ib_step_kernel(IbStep st) {
   float sign;
   decode_row(st, r, owner, rule, sign, i);
   const LayerDev& L = st.L;
-  if (st.seed) {
-    for (int o = threadIdx.x; o < L.n_out; o += NT) mu[o] = o == i ? sign : 0.f;
-  } else {
+  if (!st.seed) {
     const float* src = st.mu_in + (size_t)rl * L.n_out;
     for (int o = threadIdx.x; o < L.n_out; o += NT) mu[o] = src[o];
   }
@@ -175,7 +186,12 @@ __global__ void __launch_bounds__(NT) ib_step_kernel(IbStep st) {
   const double g2 = 2.0 * (double)st.gamma_K * (double)st.gamma_K;
   for (int ii = threadIdx.x; ii < L.n_in; ii += NT) {
     float a, s;
-    transposed_elem(L, mu, ii, a, s);
+    if (st.seed) {
+      a = seed_elem(L, i, sign, ii);
+      s = fabsf(a);
+    } else {
+      transposed_elem(L, mu, ii, a, s);
+    }
     // bound on |a - W^T mu| (Dot2): u |a| + gamma_K^2 sum|W||mu|, with margin; 0 for the exact seed
     const double da = st.seed ? 0.0 : __dadd_ru(__dmul_ru(1.1920928955078125e-07, fabs((double)a)), __dmul_ru(g2, (double)s));
     if (st.box) {
@@ -333,7 +349,7 @@ cudaError_t launch_ib_layer(const std::vector<LayerDev>& Ls, int k, const IbLaye
       }
       st.gamma_K = j == k ? 0.f : gamma32(L.fan_t);
       st.row0 = r0;
-      const size_t smem = sizeof(float) * (size_t)L.n_out;
+      const size_t smem = j == k ? 0 : sizeof(float) * (size_t)L.n_out;
       count_launch();
       ib_step_kernel<<<(unsigned)nr, NT, smem, s>>>(st);
       cudaError_t e = cudaGetLastError();

@@ -515,6 +515,64 @@ def measure_ib(bn, args):
     return res
 
 
+def measure_solvers(bn, args):
+    """The three dual solvers on the Base workload with the layer-wise best
+    CROWN/WK root bounds, at the iteration counts Sec. 8.2 tunes to roughly
+    equal time (supergradient 160, proximal 100 with eta = 100 and no
+    momentum, DSG+ 260): time per call (256 subdomains), bounds/s and the mean
+    bound (the FP64 bound at the final duals; for DSG+ also its own d_O)."""
+    ldb = bn.ldb
+    d = bn.setup("base")
+    net, l0, u0, masks = d["net"], d["l0"], d["u0"], d["masks"]
+    lk, uk = ldb.ld_intermediate_bounds_propagated(net, l0, u0, rules="best")
+    B = d["wl"]["B"]
+    runs = {
+        "supergradient_T160": lambda: ldb.ld_bound(net, l0, u0, lk, uk, None, masks, n_iters=160),
+        "proximal_T100": lambda: ldb.ld_bound_proximal(net, l0, u0, lk, uk, None, masks, n_iters=100,
+                                                       opts=ldb.ProxOptions(eta0=100.0, eta_end=100.0, mu=0.0)),
+        "dsg_T260": lambda: ldb.ld_bound_dsg(net, l0, u0, lk, uk, None, masks, n_iters=260),
+    }
+    res = {"subdomains": B, "intermediate_bounds": "layer-wise best of CROWN and WK at the root"}
+    for key, fn in runs.items():
+        times, win = bn.timed(fn, 3, 1)
+        out = fn()
+        ms = statistics.median(times)
+        entry = {"ms_per_call": ms, "bounds_per_s": B / (ms / 1000.0), "clocks": bn.sampler.window(*win)}
+        if key.startswith("dsg"):
+            dec, dd = (x.cpu().numpy() for x in out)
+            fin = np.isfinite(dec)
+            entry.update({"mean_bound_dec_dsg": float(dec[fin].mean()), "mean_bound_dsg": float(dd[fin].mean())})
+        else:
+            o = out.cpu().numpy()
+            entry["mean_bound"] = float(o[np.isfinite(o)].mean())
+        res[key] = entry
+    return res
+
+
+def measure_branching(bn, args):
+    """Branching decisions for the 256 Base subdomains (SR, mSR, FSB: time per
+    call) and one batched branch and bound run on a Base property (CROWN/WK
+    root bounds, T = 50 per bound, 128 subdomains per step, a budget of 4096
+    subdomains): status, subdomains bounded and their rate."""
+    ldb = bn.ldb
+    from paper_2104_06718_gb300 import bab
+    d = bn.setup("base")
+    net, l0, u0, masks = d["net"], d["l0"], d["u0"], d["masks"]
+    lk, uk = ldb.ld_intermediate_bounds_propagated(net, l0, u0, rules="best")
+    res = {"subdomains": d["wl"]["B"]}
+    for rule in ("sr", "msr", "fsb"):
+        fn = lambda: ldb.ld_branch(net, l0, u0, lk, uk, None, masks, rule=rule)
+        times, _ = bn.timed(fn, 5, 1)
+        res[f"{rule}_ms_per_call"] = statistics.median(times)
+    t0 = time.perf_counter()
+    r = bab.verify(net, d["wl"]["l0"][0], d["wl"]["u0"][0], lk, uk, T=50, batch=128, max_nodes=4096)
+    dt = time.perf_counter() - t0
+    res["bab"] = {"status": r.status, "subdomains_bounded": r.nodes, "branching_steps": r.iterations,
+                  "lower": r.lower, "upper": r.upper, "seconds": dt, "subdomains_per_s": r.nodes / dt,
+                  "setting": "FSB, T = 50 per bound (fused engine), 128 subdomains per step, budget 4096"}
+    return res
+
+
 def summarise(m, B, world):
     t = sum(m["times"]) / 1000.0
     ph = m["phases"]
@@ -607,6 +665,8 @@ def run_ours(args):
                                             "definition": "|q_bf16 - q_fp32| / max(|q_fp32|, 1) per subdomain, "
                                                           "same inputs and T, whole batch"}
         configs["intermediate_bounds_base256"] = measure_ib(bn, args)
+        configs["solvers_base256"] = measure_solvers(bn, args)
+        configs["branching_base256"] = measure_branching(bn, args)
     bn.sampler.stop()
     if rank != 0:
         if world > 1:

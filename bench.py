@@ -61,22 +61,35 @@ METRIC = "LD subdomain bounds/s on Base/Wide/Deep convnets, bf16 vs fp32 at ≤1
 
 # DRAM bytes (read + write) of one launch of the iterations, from ncu captures;
 # keyed by (workload, precision, engine, tile, threads per CTA, subdomains,
-# iterations) and by the digest of the kernel sources they were captured at
-# (kernel_digest()).  An entry whose digest differs from the current sources
-# is not reported (the kernels changed since the capture).
-TRAFFIC = {}
+# iterations), each with the digest of that engine's sources at the capture
+# (kernel_digest(engine)).  An entry whose digest differs from the current
+# sources is not reported (the kernel changed since the capture).
+TRAFFIC = {
+    # ncu --set full of fused_kernel<2, 512>: dram__bytes_read.sum 8,010,752 B, dram__bytes_write.sum 0
+    ("base", "fp32", "fused", 2, 512, 256, 100): ("a060510a6ce7", 8010752),
+}
+
+# The sources each timed engine is compiled from (besides the shared header
+# and the ABI header).
+ENGINE_SOURCES = {"fused": ["ld_fused.cu"], "tensor-core bf16": ["ld_tc.cu"], "layerwise": ["ld_passes.cu"]}
 
 
-def kernel_digest() -> str:
-    """SHA-256 (first 12 hex digits) of the CUDA sources of the library."""
+def kernel_digest(engine=None) -> str:
+    """SHA-256 (first 12 hex digits) of the CUDA sources of the library, or,
+    given an engine, of the sources that engine's kernels are built from."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_2104_06718_gb300", "csrc")
+    if engine is None:
+        files = sorted(fn for fn in os.listdir(csrc) if fn.endswith((".cu", ".cuh", ".h")))
+        paths = [(fn, os.path.join(csrc, fn)) for fn in files]
+    else:
+        files = ENGINE_SOURCES.get(engine, []) + ["ld_common.cuh"]
+        paths = [(fn, os.path.join(csrc, fn)) for fn in files] + [("ld.h", os.path.join(ROOT, "include", "ld.h"))]
     h = hashlib.sha256()
-    for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh", ".h")):
-            h.update(fn.encode())
-            with open(os.path.join(csrc, fn), "rb") as f:
-                h.update(f.read())
+    for fn, path in paths:
+        h.update(fn.encode())
+        with open(path, "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:12]
 
 
@@ -454,7 +467,7 @@ class Bench:
         main = alu_obj if resident else hbm_obj
         key = (wl["name"], precision, engine, tile, threads, B, T)
         tr = TRAFFIC.get(key)
-        traffic = tr[1] if tr is not None and tr[0] == kernel_digest() else None
+        traffic = tr[1] if tr is not None and tr[0] == kernel_digest(engine) else None
         other = {"hbm": hbm_obj} if resident else {"alu": alu_obj}
         if precision == "bf16":
             other["tensor"] = tensor_obj

@@ -43,14 +43,21 @@ def verify(net: ldb.Net, l0, u0, lbk, ubk, T: int = 50, batch: int = 64, max_nod
     ubk = torch.as_tensor(ubk, device=dev, dtype=torch.float32).reshape(1, -1)
     N = net.N
     masks = torch.zeros((1, N), dtype=torch.int8, device=dev)
-    # one fused launch shape for every batch size (the autotuner would probe each new size)
-    o = opts or ldb.Options(engine="fused", tile=1, cta_threads=512)
-    lo, rho = ldb.ld_bound(net, l0, u0, lbk, ubk, None, masks, n_iters=T, opts=o, return_rho=True)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+
+    def shape(B, warm):
+        # fixed fused launch shapes (the autotuner would probe every new batch
+        # size): one subdomain per 512-thread CTA while the batch fits the
+        # SMs in one wave, two per CTA beyond that; children start from their
+        # parent's duals
+        o = opts or ldb.Options(engine="fused", tile=1 if B <= sms else 2, cta_threads=512)
+        return ldb.Options(**{**o.__dict__, "init": "given"}) if warm else o
+
+    lo, rho = ldb.ld_bound(net, l0, u0, lbk, ubk, None, masks, n_iters=T, opts=shape(1, False), return_rho=True)
     best_ub = float(ldb.ld_upper_bound(net, l0, u0, lbk, ubk, rho, masks=masks).min().item())
     bounds = lo.cpu().numpy()
     stuck = []
     nodes, it, trace = 1, 0, []
-    given = ldb.Options(**{**o.__dict__, "init": "given"})
     while True:
         open_ = bounds <= 0.0
         idx = np.nonzero(open_)[0]
@@ -82,7 +89,8 @@ def verify(net: ldb.Net, l0, u0, lbk, ubk, T: int = 50, batch: int = 64, max_nod
         rows = torch.arange(2 * split.size, device=dev)
         cm[rows, torch.cat([col, col])] = torch.cat([torch.ones_like(col), -torch.ones_like(col)]).to(torch.int8)
         cr = torch.cat([r[ts], r[ts]])
-        co, crho = ldb.ld_bound(net, l0, u0, lbk, ubk, None, cm, n_iters=T, opts=given, rho_in=cr, return_rho=True)
+        co, crho = ldb.ld_bound(net, l0, u0, lbk, ubk, None, cm, n_iters=T, opts=shape(int(cm.shape[0]), True),
+                                rho_in=cr, return_rho=True)
         ub = ldb.ld_upper_bound(net, l0, u0, lbk, ubk, crho, masks=cm).cpu().numpy()
         co = co.cpu().numpy()
         fin = np.isfinite(co)

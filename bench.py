@@ -71,7 +71,9 @@ TRAFFIC = {
 
 # The sources each timed engine is compiled from (besides the shared header
 # and the ABI header).
-ENGINE_SOURCES = {"fused": ["ld_fused.cu"], "tensor-core bf16": ["ld_tc.cu"], "layerwise": ["ld_passes.cu"]}
+ENGINE_SOURCES = {"fused": ["ld_fused.cu", "ld_fused_impl.cuh"],
+                  "fused tensor-core bf16": ["ld_fused_tc.cu", "ld_fused_impl.cuh", "ld_tcgen05.cuh"],
+                  "tensor-core bf16": ["ld_tc.cu", "ld_tcgen05.cuh"], "layerwise": ["ld_passes.cu"]}
 
 
 def kernel_digest(engine=None) -> str:
@@ -418,11 +420,15 @@ class Bench:
         ph = {k: net.profile_read(k, reset=True) for k in ("iter", "final", "init", "ibp", "backward")}
         net.profile(False)
         out, _ = step()
-        engine, tile, threads = net.tuned(B)
-        if precision == "bf16":
-            engine, tile, threads = "tensor-core bf16", 0, 0
-        elif self.args.engine != "auto":
+        engine, tile, threads = net.tuned(B, precision)
+        if self.args.engine != "auto":
             engine, tile, threads = self.args.engine, self.args.tile, self.args.cta_threads
+        if precision == "bf16":
+            engine = "fused tensor-core bf16" if engine == "fused" else "tensor-core bf16"
+            if engine == "fused tensor-core bf16":
+                threads = 512
+            else:
+                tile, threads = 0, 0
         return dict(times=times, window=win, launches=launches, phases=ph, out=out.cpu().numpy(),
                     engine=(engine, tile, threads),
                     roofline=self.roofline(wl, net, precision, ph["iter"], (engine, tile, threads)))
@@ -463,18 +469,27 @@ class Bench:
         tensor_obj = {"achieved": achieved_tflops, "peak": bf16_peak, "unit": "TFLOP/s",
                       "frac": achieved_tflops / bf16_peak, "peak_source": f"{self.peak_src} bf16 dense (burst)",
                       "work_per_launch": alu_obj["work_per_launch"]}
-        resident = engine == "fused"
-        main = alu_obj if resident else hbm_obj
+        resident = engine in ("fused", "fused tensor-core bf16")
+        tensor_main = engine == "fused tensor-core bf16"
+        main = tensor_obj if tensor_main else (alu_obj if resident else hbm_obj)
         key = (wl["name"], precision, engine, tile, threads, B, T)
         tr = TRAFFIC.get(key)
         traffic = tr[1] if tr is not None and tr[0] == kernel_digest(engine) else None
         other = {"hbm": hbm_obj} if resident else {"alu": alu_obj}
-        if precision == "bf16":
+        if tensor_main:
+            other["alu"] = alu_obj
+        elif precision == "bf16":
             other["tensor"] = tensor_obj
-        return {"bound": "alu" if resident else "hbm", "achieved": main["achieved"], "peak": main["peak"],
-                "unit": main["unit"], "frac": main["frac"], "traffic": traffic,
-                "kernel": f"fused iterations (tile {tile}, {threads or 256} threads per CTA; rho, m, v resident "
-                          "in shared memory)" if resident else f"{engine or 'auto'} iterations (one graph launch)",
+        if tensor_main:
+            kernel = (f"fused tensor-core iterations ({tile} subdomains per 512-thread CTA; conv passes as tcgen05 "
+                      "BF16 GEMMs from shared-memory shadows, rho, m, v resident in shared memory)")
+        elif resident:
+            kernel = f"fused iterations (tile {tile}, {threads or 256} threads per CTA; rho, m, v resident in shared memory)"
+        else:
+            kernel = f"{engine or 'auto'} iterations (one graph launch)"
+        return {"bound": "tensor" if tensor_main else ("alu" if resident else "hbm"), "achieved": main["achieved"],
+                "peak": main["peak"], "unit": main["unit"], "frac": main["frac"], "traffic": traffic,
+                "kernel": kernel,
                 "avg_launch_ms": iter_ms / max(iter_n, 1),
                 "peak_source": main["peak_source"], "work_per_launch": main["work_per_launch"], "other": other,
                 "l2_note": "the dual state of this workload fits in the 129 MB L2" if B * net.N * 24.25 < 100e6
@@ -811,14 +826,14 @@ def run_sweep(args):
                     e1.record(stream)
                     e1.synchronize()
                     times.append(e0.elapsed_time(e1))
-                res[prec] = (B / (statistics.median(times) / 1000.0), out.cpu().numpy(), net.tuned(B))
+                res[prec] = (B / (statistics.median(times) / 1000.0), out.cpu().numpy(), net.tuned(B, prec))
             a32, a16 = res["fp32"][1], res["bf16"][1]
             fin = np.isfinite(a32) & np.isfinite(a16)
             rel = np.abs(a16[fin] - a32[fin]) / np.maximum(np.abs(a32[fin]), 1.0)
             print(json.dumps({"sweep": "deep", "subdomains": B, "iterations": T, "properties": n_props,
                               "fp32_bounds_per_s": res["fp32"][0], "bf16_bounds_per_s": res["bf16"][0],
                               "bf16_speedup": res["bf16"][0] / res["fp32"][0],
-                              "fp32_engine": list(res["fp32"][2]),
+                              "fp32_engine": list(res["fp32"][2]), "bf16_engine": list(res["bf16"][2]),
                               "gap_median": float(np.median(rel)) if rel.size else None,
                               "gap_max": float(rel.max()) if rel.size else None,
                               "ambiguous_relus": {"min": int(amb_counts.min()), "median": float(np.median(amb_counts)),

@@ -95,13 +95,18 @@ typedef struct {
                           the autotuner's choice under LD_ENGINE_AUTO      */
 } ld_opts;
 
-/* Engines for the iterations (all compute the same iterates up to FP32
- * rounding order):
- *   LD_ENGINE_AUTO      pick per (net, B) by timing a short probe of each
- *                       candidate on the first call, then cache the choice;
- *   LD_ENGINE_LAYERWISE one launch per layer pass and iteration;
+/* Engines for the iterations (for one precision, all compute the same
+ * iterates up to FP32 rounding order):
+ *   LD_ENGINE_AUTO      pick per (net, B, precision) by timing a short probe
+ *                       of each candidate on the first call, then cache it;
+ *   LD_ENGINE_LAYERWISE one launch per layer pass and iteration (BF16: the
+ *                       layer-wise tensor-core GEMM kernels);
  *   LD_ENGINE_FUSED     one launch for all iterations, each CTA owning
- *                       `tile` subdomains for the whole run. */
+ *                       `tile` subdomains for the whole run (BF16: the fused
+ *                       tensor-core engine, tile 1 or 2, 512 threads, conv
+ *                       passes as tcgen05 GEMMs over shared-memory operands;
+ *                       nets whose convs it does not cover fall back to the
+ *                       layer-wise tensor-core engine). */
 enum { LD_ENGINE_AUTO = 0, LD_ENGINE_LAYERWISE = 1, LD_ENGINE_FUSED = 2 };
 
 typedef struct ld_net ld_net;
@@ -447,6 +452,20 @@ ld_status ld_final_bound_noalloc(ld_net* net, const float* lb0, const float* ub0
  * (all handles).  Errors: LD_ERR_ARG for another code. */
 ld_status ld_test_inject_alloc_failure(int32_t after, int32_t code);
 
+/* Layout check of the fused tensor-core engine, on the host only (no device
+ * call, usable without a GPU): plans the BF16 shadow planes, weight tiles and
+ * the table of tcgen05.mma operations of the BF16 fused engine for the given
+ * net (as for ld_net_create, without the margin) with S = 1 or 2 subdomains
+ * per CTA, and checks for every MMA and every valid output row that the
+ * operand rows it reads are exactly where the epilogues write x_k / rho_k.
+ * info (7 int64, caller-owned): shared-memory bytes of a CTA, TMEM columns,
+ * MMAs per iteration, shadow bytes, weight-tile bytes, passes, MMA table
+ * entries that read rows beyond their plane (S = 1 half tiles).  Errors:
+ * LD_ERR_ARG; LD_ERR_UNSUPPORTED when the geometry has no plan or the plan
+ * needs more than smem_limit bytes. */
+ld_status ld_test_fused_tc_plan(const ld_layer_desc* layers, int32_t n_layers, int32_t S, int64_t smem_limit,
+                                int64_t* info);
+
 /* Number of kernels this library has launched in this process (all
  * handles, all calls), for accounting of device work. */
 ld_status ld_launch_count(int64_t* count);
@@ -459,9 +478,13 @@ ld_status ld_launch_count(int64_t* count);
 ld_status ld_selftest_wait_timeout(ld_net* net, void* stream);
 
 /* The engine, tile and threads per CTA of the LD_ENGINE_AUTO choice cached
- * for batch size B (engine = -1 if none yet; tile and cta_threads are 0 for
- * the layerwise engine).  Any output pointer may be NULL. */
-ld_status ld_net_tuned(const ld_net* net, int32_t B, int32_t* engine, int32_t* tile, int32_t* cta_threads);
+ * for batch size B and the iterations' precision (LD_PREC_*): engine = -1 if
+ * none yet; tile and cta_threads are 0 for the layerwise engines.  For
+ * LD_PREC_BF16, LD_ENGINE_LAYERWISE is the layer-wise tensor-core engine and
+ * LD_ENGINE_FUSED the fused tensor-core engine (tile = subdomains per CTA,
+ * 512 threads).  Any output pointer may be NULL.  Errors: LD_ERR_ARG. */
+ld_status ld_net_tuned(const ld_net* net, int32_t precision, int32_t B, int32_t* engine, int32_t* tile,
+                       int32_t* cta_threads);
 
 #ifdef __cplusplus
 }

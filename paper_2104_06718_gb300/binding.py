@@ -34,7 +34,7 @@ EXPORTED = [
     "ld_bound", "ld_dual_supergradient", "ld_bound_backward",
     "ld_net_profile", "ld_net_profile_read", "ld_launch_count", "ld_net_tuned", "ld_final_bound_noalloc",
     "ld_test_inject_alloc_failure", "ld_intermediate_bounds_propagated", "ld_prox_opts_default", "ld_bound_proximal",
-    "ld_branching_scores", "ld_branch", "ld_upper_bound", "ld_bound_dsg",
+    "ld_branching_scores", "ld_branch", "ld_upper_bound", "ld_bound_dsg", "ld_test_fused_tc_plan",
 ]
 PHASES = {"iter": 0, "final": 1, "init": 2, "ibp": 3, "backward": 4}
 
@@ -192,6 +192,26 @@ class ProxOptions:
                         int(self.fp64_final))
 
 
+def layer_descs(specs):
+    """ld_layer_desc array of layer specs, and the arrays it points into."""
+    keep = []
+    descs = (LayerDesc * len(specs))()
+    for d, s in zip(descs, specs):
+        W = np.ascontiguousarray(np.asarray(s.W, dtype=np.float32))
+        b = np.ascontiguousarray(np.asarray(s.b, dtype=np.float32))
+        keep += [W, b]
+        if s.kind == "fc":
+            d.kind, d.cin, d.h, d.w = LD_LAYER_FC, W.shape[1], 1, 1
+            d.cout, d.kh, d.kw, d.stride, d.pad = W.shape[0], 1, 1, 1, 0
+        else:
+            c, h, w = s.in_shape
+            d.kind, d.cin, d.h, d.w = LD_LAYER_CONV, c, h, w
+            d.cout, d.kh, d.kw, d.stride, d.pad = W.shape[0], W.shape[2], W.shape[3], s.stride, s.pad
+        d.W = W.ctypes.data
+        d.b = b.ctypes.data
+    return descs, keep
+
+
 class Net:
     """An ld_net handle: device copies of a ReLU net in canonical form.
 
@@ -202,21 +222,7 @@ class Net:
 
     def __init__(self, specs, margin=None):
         lib = load_library()
-        self._keep = []
-        descs = (LayerDesc * len(specs))()
-        for d, s in zip(descs, specs):
-            W = np.ascontiguousarray(np.asarray(s.W, dtype=np.float32))
-            b = np.ascontiguousarray(np.asarray(s.b, dtype=np.float32))
-            self._keep += [W, b]
-            if s.kind == "fc":
-                d.kind, d.cin, d.h, d.w = LD_LAYER_FC, W.shape[1], 1, 1
-                d.cout, d.kh, d.kw, d.stride, d.pad = W.shape[0], 1, 1, 1, 0
-            else:
-                c, h, w = s.in_shape
-                d.kind, d.cin, d.h, d.w = LD_LAYER_CONV, c, h, w
-                d.cout, d.kh, d.kw, d.stride, d.pad = W.shape[0], W.shape[2], W.shape[3], s.stride, s.pad
-            d.W = W.ctypes.data
-            d.b = b.ctypes.data
+        descs, self._keep = layer_descs(specs)
         mptr = None
         if margin is not None:
             m = np.ascontiguousarray(np.asarray(margin, dtype=np.float32))
@@ -270,11 +276,14 @@ class Net:
                "ld_net_profile_read")
         return ms.value, n.value
 
-    def tuned(self, B: int):
+    def tuned(self, B: int, precision: str = "fp32"):
         """(engine, tile, threads per CTA) chosen by the autotuner for batch
-        size B, or (None, 0, 0)."""
+        size B and the iterations' precision, or (None, 0, 0).  For "bf16",
+        "layerwise" is the layer-wise tensor-core engine and "fused" the
+        fused tensor-core engine."""
         e, t, n = C.c_int32(), C.c_int32(), C.c_int32()
-        _check(self._lib.ld_net_tuned(self._h, int(B), C.byref(e), C.byref(t), C.byref(n)), "ld_net_tuned")
+        prec = {"fp32": LD_PREC_FP32, "bf16": LD_PREC_BF16}[precision]
+        _check(self._lib.ld_net_tuned(self._h, prec, int(B), C.byref(e), C.byref(t), C.byref(n)), "ld_net_tuned")
         names = {LD_ENGINE_LAYERWISE: "layerwise", LD_ENGINE_FUSED: "fused"}
         return names.get(e.value), t.value, n.value
 
@@ -284,6 +293,21 @@ def inject_alloc_failure(after: int, code: int = LD_ERR_NOMEM):
     more allocations succeed, the next one fails with `code` (LD_ERR_NOMEM or
     LD_ERR_CUDA) without calling the CUDA allocator; after < 0 disarms."""
     _check(load_library().ld_test_inject_alloc_failure(int(after), int(code)), "ld_test_inject_alloc_failure")
+
+
+def fused_tc_plan(specs, S: int, smem_limit: int = 232448):
+    """Host-only layout check of the fused tensor-core engine for S
+    subdomains per CTA (no GPU needed): None when the net has no plan within
+    smem_limit bytes, else the plan's figures."""
+    descs, keep = layer_descs(specs)
+    info = (C.c_int64 * 7)()
+    st = load_library().ld_test_fused_tc_plan(descs, len(specs), int(S), C.c_int64(smem_limit), info)
+    if st == LD_ERR_UNSUPPORTED:
+        return None
+    _check(st, "ld_test_fused_tc_plan")
+    keys = ("smem_bytes", "tmem_cols", "mmas_per_iteration", "shadow_bytes", "weight_tile_bytes", "passes",
+            "half_tile_mmas")
+    return dict(zip(keys, (int(v) for v in info)))
 
 
 def launch_count() -> int:

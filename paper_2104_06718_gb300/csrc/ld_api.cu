@@ -74,6 +74,15 @@ struct ld_net {
   int tc_B = -1, tc_props = -1;
   uint16_t *xh = nullptr, *rh = nullptr;
   float* c1 = nullptr;
+  // fused tensor-core engine (built on first use): its net (tc layout, BF16-
+  // rounded hidden FC weights), plans for 1 and 2 subdomains per CTA, and the
+  // allocation holding their MMA tables and weight tiles
+  ld::FusedNet fused_tc{};
+  ld::FusedTc ftc[2]{};
+  void* ftc_mem = nullptr;
+  bool ftc_tried = false;
+  ld_status ftc_state = LD_ERR_UNSUPPORTED;
+  std::map<int, std::pair<int, int>> tuned_bf16;  // B -> (engine, subdomains per CTA) for BF16 iterations
   // workspace of the propagation-based intermediate bounds (grown on demand)
   void* ib_ws = nullptr;
   size_t ib_bytes = 0;
@@ -514,6 +523,111 @@ ld_status run_iterations_bf16(ld_net* net, const Problem& P, const ld_opts& o, i
   return last_error();
 }
 
+// The fused tensor-core engine's net and plans, built on the first BF16 call.
+ld_status ensure_fused_tc(ld_net* net) {
+  if (!net->ftc_tried) {
+    net->ftc_state = ld::build_fused_tc(net->L, &net->fused_tc, net->ftc, net->smem_optin, &net->ftc_mem);
+    net->ftc_tried = net->ftc_state == LD_OK || net->ftc_state == LD_ERR_UNSUPPORTED;
+  }
+  return net->ftc_state;
+}
+bool fused_tc_fits(const ld_net* net, int S) {
+  return net->ftc_state == LD_OK && (S == 1 || S == 2) && net->ftc[S - 1].npass > 0;
+}
+
+// T Adam iterations of the fused tensor-core engine with S subdomains per
+// CTA: one launch per kFusedSteps iterations, the first also computing the
+// CROWN start (crown = 1) with the engine's own transposed passes.  The
+// centre term W_1 c_0 + b_1 of the first layer is computed first.
+ld_status run_iterations_fused_tc(ld_net* net, const Problem& P, const ld_opts& o, int n_iters, int S,
+                                  cudaStream_t s, int crown) {
+  const int T_sched = o.t_total > 0 ? o.t_total : o.t_offset + n_iters;
+  ld::FusedTc t = net->ftc[S - 1];
+  t.c1 = net->c1;
+  t.status = net->d_status;
+  ld::launch_tc_centre(net->tc, layer(net, 1), P, tc_state(net, o), s);
+  for (int t0 = 0; t0 < n_iters || (t0 == 0 && crown); t0 += ld::kFusedSteps) {
+    ld::FusedIter it{};
+    it.T = std::min(ld::kFusedSteps, n_iters - t0);
+    it.crown = t0 == 0 ? crown : 0;
+    it.beta1 = o.beta1;
+    it.beta2 = o.beta2;
+    it.eps = o.eps;
+    it.fc_threads = 256;
+    for (int i = 0; i < it.T; ++i) it.step[i] = adam_step(o, o.t_offset + t0 + i, T_sched);
+    const ld_status st =
+        cuda_status(ld::launch_fused_tc(net->fused_tc, t, S, P, net->rho, net->m, net->v, it, s));
+    if (st != LD_OK) return st;
+  }
+  return LD_OK;
+}
+
+// Engine for BF16 iterations: the layer-wise tensor-core engine
+// (LD_ENGINE_LAYERWISE) or the fused tensor-core engine with 1 or 2
+// subdomains per CTA (LD_ENGINE_FUSED, tile).  LD_ENGINE_AUTO times the
+// candidates on the first call with a given B, as choose_engine does.
+std::pair<int, int> choose_engine_bf16(ld_net* net, const Problem& P, const ld_opts& o, int n_iters,
+                                       cudaStream_t s) {
+  const bool f1 = fused_tc_fits(net, 1), f2 = fused_tc_fits(net, 2);
+  if (o.engine == LD_ENGINE_LAYERWISE || (!f1 && !f2)) return {LD_ENGINE_LAYERWISE, 0};
+  if (o.engine == LD_ENGINE_FUSED) {
+    int S = o.tile == 1 || o.tile == 2 ? o.tile : (P.B <= net->n_sm ? 1 : 2);
+    if (!fused_tc_fits(net, S)) S = f1 ? 1 : 2;
+    return {LD_ENGINE_FUSED, S};
+  }
+  auto hit = net->tuned_bf16.find(P.B);
+  if (hit != net->tuned_bf16.end()) return hit->second;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cap);
+  if (cap != cudaStreamCaptureStatusNone) return {LD_ENGINE_FUSED, (P.B <= net->n_sm && f1) || !f2 ? 1 : 2};
+  ld::launch_empty_flags(P, net->empty, net->d_status, s);
+  std::vector<std::pair<int, int>> cands = {{LD_ENGINE_LAYERWISE, 0}};
+  if (f1) cands.push_back({LD_ENGINE_FUSED, 1});
+  if (f2) cands.push_back({LD_ENGINE_FUSED, 2});
+  const size_t BN = (size_t)P.B * net->N;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  ld_opts probe = o;
+  probe.t_offset = 0;
+  probe.t_total = 100;
+  double best = 1e300;
+  std::pair<int, int> choice = cands.back();
+  const double T = n_iters > 0 ? (double)n_iters : 1.0;
+  for (const auto& c : cands) {
+    float ms[2] = {0.f, 0.f};
+    bool ok = true;
+    const int its[2] = {2, 6};
+    for (int r = -1; r < 2; ++r) {  // r = -1: warm-up
+      cudaMemsetAsync(net->rho, 0, sizeof(float) * BN, s);
+      cudaMemsetAsync(net->m, 0, sizeof(float) * BN, s);
+      cudaMemsetAsync(net->v, 0, sizeof(float) * BN, s);
+      const int nit = r < 0 ? 1 : its[r];
+      cudaEventRecord(e0, s);
+      const ld_status st =
+          c.first == LD_ENGINE_FUSED
+              ? run_iterations_fused_tc(net, P, probe, nit, c.second, s, 0)
+              : run_graphed(net, s, [&](cudaStream_t cs) { return run_iterations_bf16(net, P, probe, nit, false, cs); });
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      if (r >= 0) ok = ok && st == LD_OK && cudaEventElapsedTime(&ms[r], e0, e1) == cudaSuccess;
+    }
+    if (!ok) continue;
+    const double per_iter = std::max(0.0, (double)(ms[1] - ms[0]) / 4.0);
+    const double fixed = std::max(0.0, (double)ms[0] - 2.0 * per_iter);
+    const double predicted = fixed + T * per_iter;
+    if (predicted < best) {
+      best = predicted;
+      choice = c;
+    }
+  }
+  cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  net->tuned_bf16[P.B] = choice;
+  return choice;
+}
+
 // Engine and tile for this call.  LD_ENGINE_AUTO times every candidate on
 // the first call with a given B (on the call's own inputs, before rho is
 // initialised): a 2- and a 6-iteration probe give its fixed cost per call
@@ -860,6 +974,7 @@ ld_status ld_net_destroy(ld_net* net) {
   if (net->prox_ws) cudaFree(net->prox_ws);
   if (net->dsg_ws) cudaFree(net->dsg_ws);
   ld::free_tc_net(&net->tc);
+  if (net->ftc_mem) cudaFree(net->ftc_mem);
   if (net->d_W) cudaFree(net->d_W);
   if (net->d_Wx) cudaFree(net->d_Wx);
   if (net->d_b) cudaFree(net->d_b);
@@ -1435,11 +1550,13 @@ ld_status ld_bound(ld_net* net, const float* lb0, const float* ub0, const float*
   const size_t BN = (size_t)B * net->N;
   const bool bf16 = o.precision == LD_PREC_BF16 && n_iters > 0;
   if (bf16 && (st = ensure_tc(net, B, n_props)) != LD_OK) return st;
-  const std::pair<int, int> eng =
-      (n_iters > 0 && !bf16) ? choose_engine(net, P, o, n_iters, s) : std::make_pair((int)LD_ENGINE_LAYERWISE, 0);
+  if (bf16 && (st = ensure_fused_tc(net)) != LD_OK && st != LD_ERR_UNSUPPORTED) return st;
+  const std::pair<int, int> eng = n_iters <= 0 ? std::make_pair((int)LD_ENGINE_LAYERWISE, 0)
+                                  : bf16       ? choose_engine_bf16(net, P, o, n_iters, s)
+                                               : choose_engine(net, P, o, n_iters, s);
   // The CROWN start must come from the same transposed-pass arithmetic as the
   // iterations (its exact ties would otherwise be broken by rounding): the
-  // fused engine computes it in-kernel, the layerwise engine with its kernels.
+  // fused engines compute it in-kernel, the layerwise engines with their kernels.
   const int crown_in_kernel = (o.init == LD_INIT_CROWN && eng.first == LD_ENGINE_FUSED) ? 1 : 0;
   {
     PhaseMark pm(net, LD_PHASE_INIT, s);
@@ -1448,9 +1565,11 @@ ld_status ld_bound(ld_net* net, const float* lb0, const float* ub0, const float*
       cudaMemcpyAsync(net->rho, rho_in, sizeof(float) * BN, cudaMemcpyDeviceToDevice, s);
     else if (o.init == LD_INIT_ZERO)
       cudaMemsetAsync(net->rho, 0, sizeof(float) * BN, s);
+    else if (crown_in_kernel)
+      ;
     else if (bf16)
       crown_sweep_bf16(net, P, o, s);
-    else if (!crown_in_kernel)
+    else
       crown_sweep(net, P, s);
     if (adam_mv && o.t_offset > 0) {
       cudaMemcpyAsync(net->m, adam_mv, sizeof(float) * BN, cudaMemcpyDeviceToDevice, s);
@@ -1462,7 +1581,9 @@ ld_status ld_bound(ld_net* net, const float* lb0, const float* ub0, const float*
   }
   if (n_iters > 0) {
     PhaseMark pm(net, LD_PHASE_ITER, s);
-    if (bf16)
+    if (bf16 && eng.first == LD_ENGINE_FUSED)
+      st = run_iterations_fused_tc(net, P, o, n_iters, eng.second, s, crown_in_kernel);
+    else if (bf16)
       st = run_graphed(net, s, [&](cudaStream_t cs) {
         return run_iterations_bf16(net, P, o, n_iters, o.init == LD_INIT_CROWN, cs);
       });
@@ -1566,8 +1687,18 @@ ld_status ld_launch_count(int64_t* count) {
   return LD_OK;
 }
 
-ld_status ld_net_tuned(const ld_net* net, int32_t B, int32_t* engine, int32_t* tile, int32_t* cta_threads) {
-  if (!net) return LD_ERR_ARG;
+ld_status ld_net_tuned(const ld_net* net, int32_t precision, int32_t B, int32_t* engine, int32_t* tile,
+                       int32_t* cta_threads) {
+  if (!net || (precision != LD_PREC_FP32 && precision != LD_PREC_BF16)) return LD_ERR_ARG;
+  if (precision == LD_PREC_BF16) {
+    auto it = net->tuned_bf16.find(B);
+    const bool found = it != net->tuned_bf16.end();
+    const bool fused = found && it->second.first == LD_ENGINE_FUSED;
+    if (engine) *engine = found ? it->second.first : -1;
+    if (tile) *tile = fused ? it->second.second : 0;
+    if (cta_threads) *cta_threads = fused ? 512 : 0;
+    return LD_OK;
+  }
   auto it = net->tuned.find(B);
   const bool found = it != net->tuned.end();
   const bool fused = found && it->second.first == LD_ENGINE_FUSED;

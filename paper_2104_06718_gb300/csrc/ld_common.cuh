@@ -448,11 +448,69 @@ struct FusedIter {
 // with 2 the FC weights also stream once per 2 subdomains).
 constexpr int kFusedWide = 16;
 
-FusedNet make_fused_net(const std::vector<LayerDev>& Ls);
+// tc: the layout of the fused tensor-core engine (conv inputs and outputs
+// live in BF16 shadows, so the FP32 planes keep only the FC inputs, the rho
+// planes carry no halo, and no FP32 conv weights are staged).
+FusedNet make_fused_net(const std::vector<LayerDev>& Ls, bool tc = false);
 // Shared memory of a fused launch of the given shape code (all state resident).
 size_t fused_smem_bytes(const FusedNet& f, int code);
 cudaError_t launch_fused(const FusedNet& f, int code, const Problem& P, float* rho, float* m, float* v,
                          const FusedIter& it, cudaStream_t s);
+
+// ---------------------------------------------------------------- fused tensor-core engine
+// The fused engine with its conv passes on the tensor cores (ld_fused_tc.cu):
+// every conv pass is an implicit GEMM D[rows, N] = A[rows, K] B[N, K]^T read
+// straight from BF16 "shadow" planes in shared memory, channels innermost in
+// groups of 8 (16 bytes: one row of a core matrix), the rows of the S
+// subdomains of a CTA interleaved, so that 8 consecutive output columns of 16
+// consecutive (row, subdomain) pairs form an M = 128 tile with constant
+// strides: no im2col copy.  A tap shifts the view; stride-2 inputs are stored
+// by stride phase.  Accumulators live in tensor memory (TMEM).
+constexpr int kTcMaxPass = 2 * kMaxLayers;
+struct TcShadow {             // conv layer k (= paper layer k+1)
+  int xs, nph, Hq, Wq, gin;   // input x_k: byte offset, phase planes (1 or 4), rows, columns, 8-channel groups
+  int rs, Hr, Wr, rhl, rwl, gout;  // output dual rho_{k+1}: offset, rows, columns (with halo), halo, groups
+};
+struct TcPass {
+  int k, fwd;                 // conv layer; 1 forward (-> Adam on rho_{k+1}), 0 transposed (-> layer k)
+  int n_tiles, N, nch, real;  // 128-row tiles, columns per tile, 8-column chunks holding channels, channels
+  int col0;                   // first TMEM column of tile 0
+  int e0, ne;                 // its MMAs in the table
+  int tx, tr, rows, cols;     // tiles along x, 16-row blocks per phase, rows / columns of a phase grid
+};
+struct TcEntry {              // one tcgen05.mma; descriptors relative to the shared-memory base
+  unsigned long long a, b;
+  uint32_t d, idesc, acc, pad;
+};
+static_assert(sizeof(TcEntry) == 32, "TcEntry is copied to shared memory in 16-byte units");
+struct FusedTc {
+  int npass, t0, nt, f0, nf;  // passes; the transposed ones [t0, t0+nt), the forward ones [f0, f0+nf)
+  TcPass pass[kTcMaxPass];
+  TcShadow sh[kMaxLayers];
+  int shadow_bytes;           // bytes of all shadows (zeroed at the start of a launch)
+  int wt_bytes;               // bytes of the BF16 weight tiles
+  int tab_bytes;              // bytes of the MMA table (copied to shared memory after the weight tiles)
+  int tc_bytes;               // shadows + weight tiles + table + barriers: the part before the FP32 state
+  int tmem_cols;              // TMEM allocation of a CTA (power of 2)
+  const TcEntry* table;
+  const uint16_t* wtiles;     // device copy of the weight tiles
+  const float* c1;            // [props, n_out of layer 1]: W_1 c_0 + b_1, c_0 the box centre
+  int n1;                     // n_out of layer 1
+  int* status;                // LD_ERR_TIMEOUT when a wait on the tensor core gives up
+};
+// The engine's net (tc layout of make_fused_net, hidden FC layers pointing at
+// BF16-rounded copies of their weights) and its plans for 1 and 2
+// subdomains per CTA (npass = 0: none within smem_limit bytes), or
+// LD_ERR_UNSUPPORTED when the geometry has no plan: conv layers first, then
+// FC layers; 4x4/stride-2 or 3x3/stride-1 convs with even planes and output
+// widths (and transposed-pass phase widths) a multiple of 8.  One device
+// allocation (*dev_mem, owned by the caller) holds the rounded weights, the
+// MMA tables and the weight tiles.
+ld_status build_fused_tc(const std::vector<LayerDev>& Ls, FusedNet* f, FusedTc out[2], size_t smem_limit,
+                         void** dev_mem);
+size_t fused_tc_smem_bytes(const FusedNet& f, const FusedTc& t, int S);
+cudaError_t launch_fused_tc(const FusedNet& f, const FusedTc& t, int S, const Problem& P, float* rho, float* m,
+                            float* v, const FusedIter& it, cudaStream_t s);
 
 // ---------------------------------------------------------------- BF16 tensor-core engine
 // Plan of layer k for the tcgen05 passes (ld_tc.cu).  The BF16 operand copies

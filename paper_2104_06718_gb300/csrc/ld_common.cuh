@@ -36,6 +36,7 @@ struct LayerDev {
   const double* W64;             // last layer only: the margin-folded row summed in FP64 [n_in]
   const double* W64_err;         // last layer only: bound on that row's summation error [n_in]
   const double* b64;             // last layer only: {folded b_n in FP64, bound on its error}
+  const uint16_t* Wh;            // fused tensor-core engine, hidden FC layers: W in BF16 [n_out, n_in]
 };
 
 // Inputs of one bounding call, in device memory.

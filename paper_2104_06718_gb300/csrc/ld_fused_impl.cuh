@@ -29,14 +29,10 @@ struct Ctx {
   bool crown;      // transposed-pass epilogue computes the CROWN duals instead of the argmin
   unsigned empty;  // bit s: subdomain b0 + s has crossing bounds (no update)
   int prop[S];     // property of subdomain b0 + s (0 for the padding of a ragged last CTA); see prop_at
-  // tensor-core engine only (TC): the plan, the shared-memory base (generic
-  // pointer and shared-window address), the TMEM allocation, three mbarriers
-  // (transposed passes, forward passes, CROWN start) and the abort flag
+  // tensor-core engine only (TC): the plan (everything else it places in
+  // shared memory is found from it, see tc_sb and tc_ctl, so that no extra
+  // register stays live through the FC passes)
   const FusedTc* tc = nullptr;
-  const TcEntry* tab = nullptr;  // the MMA table, copied to shared memory
-  unsigned char* sb = nullptr;
-  uint32_t sbase = 0, tmem = 0, bar = 0;
-  volatile int* abort = nullptr;
   __device__ float* xp(int s) const { return XP + s * net.xp_total; }
   __device__ float* xb(int s) const { return XB + s * net.nb; }
   __device__ float* rho(int s) const { return RHO + s * net.rho_total; }
@@ -115,8 +111,38 @@ __device__ __forceinline__ int rho_flat(const LayerDev& L, const FusedLayer& F, 
 }
 
 // ------------------------------------------------------------------ BF16 shadows (TC)
+// The dynamic shared memory of the fused launch (the same bytes as the
+// kernel's own extern array).  The tensor-core engine lays out, from its
+// start: the shadows, the weight tiles, the MMA table, then a control block
+// of three mbarriers (transposed passes, forward passes, CROWN start), the
+// TMEM base address written by tcgen05.alloc, and the abort flag.
+extern __shared__ __align__(128) unsigned char g_fused_smem[];
+__device__ __forceinline__ unsigned char* tc_sb() { return g_fused_smem; }
+__device__ __forceinline__ int tc_ctl_off(const FusedTc& t) { return t.shadow_bytes + t.wt_bytes + t.tab_bytes; }
+// Control block: one mbarrier per pass (its MMAs, committed by each of the
+// kTcIssuers issuing threads), one for the CROWN start (one issuer), the TMEM
+// base address written by tcgen05.alloc, the abort flag.
+constexpr int kTcIssuers = 4;
+constexpr int kTcCrownBar = kTcMaxPass;
+__device__ __forceinline__ uint32_t tc_bar(const FusedTc& t, int i) {
+  return smem_u32(g_fused_smem) + (uint32_t)(tc_ctl_off(t) + 8 * i);
+}
+__device__ __forceinline__ uint32_t tc_tmem_slot(const FusedTc& t) { return tc_bar(t, kTcMaxPass + 1); }
+__device__ __forceinline__ uint32_t tc_tmem(const FusedTc& t) {
+  return *reinterpret_cast<volatile const uint32_t*>(g_fused_smem + tc_ctl_off(t) + 8 * (kTcMaxPass + 1));
+}
+__device__ __forceinline__ volatile int* tc_abort(const FusedTc& t) {
+  return reinterpret_cast<volatile int*>(g_fused_smem + tc_ctl_off(t) + 8 * (kTcMaxPass + 2));
+}
+
 // BF16 rounding of an FP32 operand (round to nearest even), kept in FP32.
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+// Four BF16 values (little-endian pairs) widened to FP32 (exact).
+__device__ __forceinline__ float4 bf16x4_to_float4(uint2 h) {
+  return make_float4(__uint_as_float(h.x << 16), __uint_as_float(h.x & 0xffff0000u), __uint_as_float(h.y << 16),
+                     __uint_as_float(h.y & 0xffff0000u));
+}
+__device__ __forceinline__ float bf16_at(const uint16_t* p) { return __uint_as_float((uint32_t)__ldg(p) << 16); }
 
 // Byte offset of the 8 channels 8g..8g+7 of input position (Y, X) of conv
 // layer k (its x_k shadow) for subdomain s: padded coordinates, by stride
@@ -143,7 +169,7 @@ template <int S, int NT, bool TC>
 __device__ __forceinline__ void rho_shadow1(const Ctx<S, NT, TC>& c, int k, int s, int i, float r) {
   const LayerDev& L = c.net.L[k - 1];
   const int hw = L.ho * L.wo, o = i / hw, p = i - o * hw, y = p / L.wo, x = p - y * L.wo;
-  *reinterpret_cast<__nv_bfloat16*>(c.sb + rs_at<S>(c.tc->sh[k - 1], o >> 3, y, x, s) + 2 * (o & 7)) =
+  *reinterpret_cast<__nv_bfloat16*>(tc_sb() + rs_at<S>(c.tc->sh[k - 1], o >> 3, y, x, s) + 2 * (o & 7)) =
       __float2bfloat16_rn(r);
 }
 
@@ -272,10 +298,21 @@ __device__ __forceinline__ void tfc_rows(const Ctx<S, NT, TC>& c, const LayerDev
     // so that concurrent CTAs spread over the L2 slices
     const int o0 = U * (b_lo + (bi + (int)blockIdx.x) % nb);
     float4 wv[U];
+    if constexpr (TC) {
+      // BF16 weights: half the bytes of the L2 stream, widened when used
+      uint2 wh[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u)
-      wv[u] = (o0 + u < L.n_out) ? __ldg(reinterpret_cast<const float4*>(W + (size_t)(o0 + u) * L.n_in) + i4)
-                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int u = 0; u < U; ++u)
+        wh[u] = (o0 + u < L.n_out) ? __ldg(reinterpret_cast<const uint2*>(L.Wh + (size_t)(o0 + u) * L.n_in) + i4)
+                                   : make_uint2(0u, 0u);
+#pragma unroll
+      for (int u = 0; u < U; ++u) wv[u] = bf16x4_to_float4(wh[u]);
+    } else {
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        wv[u] = (o0 + u < L.n_out) ? __ldg(reinterpret_cast<const float4*>(W + (size_t)(o0 + u) * L.n_in) + i4)
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (o0 + u < L.n_out) {
@@ -358,7 +395,7 @@ __device__ void tfc_main(const Ctx<S, NT, TC>& c, const LayerDev& L, const Fused
 #pragma unroll
     for (int s = 0; s < S; ++s) acc[s] = 0.f;
     for (int o = 0; o < L.n_out; ++o) {
-      const float w = __ldg(W + (size_t)o * L.n_in + i);
+      const float w = TC ? bf16_at(L.Wh + (size_t)o * L.n_in + i) : __ldg(W + (size_t)o * L.n_in + i);
 #pragma unroll
       for (int s = 0; s < S; ++s) acc[s] = fmaf(w, TC ? bf16r(c.rho(s)[F.roff + o]) : c.rho(s)[F.roff + o], acc[s]);
     }
@@ -424,13 +461,30 @@ __device__ void ffc_main(const Ctx<S, NT, TC>& c, const LayerDev& L, const Fused
       const int n4 = L.n_in / 4;
       const float4* w0 = reinterpret_cast<const float4*>(W + (size_t)j0 * L.n_in);
       const float4* w1 = reinterpret_cast<const float4*>(W + (size_t)(two ? j0 + 1 : j0) * L.n_in);
+      const uint2* h0 = reinterpret_cast<const uint2*>(L.Wh + (size_t)j0 * L.n_in);
+      const uint2* h1 = reinterpret_cast<const uint2*>(L.Wh + (size_t)(two ? j0 + 1 : j0) * L.n_in);
       for (int t0 = lane; t0 < n4; t0 += 32 * U) {
         float4 a[U], bq[U];
+        if constexpr (TC) {
+          uint2 ha[U], hb[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int t = t0 + 32 * u;
-          a[u] = t < n4 ? __ldg(w0 + t) : make_float4(0.f, 0.f, 0.f, 0.f);
-          bq[u] = t < n4 ? __ldg(w1 + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+          for (int u = 0; u < U; ++u) {
+            const int t = t0 + 32 * u;
+            ha[u] = t < n4 ? __ldg(h0 + t) : make_uint2(0u, 0u);
+            hb[u] = t < n4 ? __ldg(h1 + t) : make_uint2(0u, 0u);
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            a[u] = bf16x4_to_float4(ha[u]);
+            bq[u] = bf16x4_to_float4(hb[u]);
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int t = t0 + 32 * u;
+            a[u] = t < n4 ? __ldg(w0 + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+            bq[u] = t < n4 ? __ldg(w1 + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -448,8 +502,10 @@ __device__ void ffc_main(const Ctx<S, NT, TC>& c, const LayerDev& L, const Fused
     } else {
       const float* w0 = W + (size_t)j0 * L.n_in;
       const float* w1 = W + (size_t)(two ? j0 + 1 : j0) * L.n_in;
+      const uint16_t* g0 = L.Wh + (size_t)j0 * L.n_in;
+      const uint16_t* g1 = L.Wh + (size_t)(two ? j0 + 1 : j0) * L.n_in;
       for (int i = lane; i < L.n_in; i += 32) {
-        const float a = __ldg(w0 + i), bb = __ldg(w1 + i);
+        const float a = TC ? bf16_at(g0 + i) : __ldg(w0 + i), bb = TC ? bf16_at(g1 + i) : __ldg(w1 + i);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
           const float x = c.xp(s)[F.xoff + i];
@@ -769,26 +825,29 @@ __device__ void top_pass(const Ctx<S, NT, TC>& c, const Team& tm) {
 }
 
 // ------------------------------------------------------------------ tensor-core conv passes (TC)
-// Issue the MMAs of passes [p0, p0 + np) and commit them to mbarrier bar
-// (one thread).  The table holds the descriptors relative to the shared-
-// memory base; the base is added to their 14-bit start-address fields.
-// The table sits in shared memory; its entries are read four at a time
-// ahead of the MMAs they describe.
-__device__ __forceinline__ void tc_issue(const FusedTc& t, const TcEntry* tab, int p0, int np, uint32_t sbase,
-                                         uint32_t tmem, uint32_t bar) {
+// Issue this thread's share of the MMAs of passes [p0, p0 + np): issuer w of
+// nw takes every nw-th tile (a tile's K steps stay with one thread, which
+// keeps its accumulation chain in order), and commits after each pass to the
+// pass's mbarrier (crown: to the CROWN barrier).  The table sits in shared
+// memory; the descriptors in it are relative to the shared-memory base,
+// which is added to their 14-bit start-address fields here.
+__device__ __noinline__ void tc_issue(const FusedTc& t, int p0, int np, int w, int nw, bool crown) {
   tc_fence_after();
-  const unsigned long long sb = sbase >> 4;
-  const int e_lo = t.pass[p0].e0, e_hi = t.pass[p0 + np - 1].e0 + t.pass[p0 + np - 1].ne;
-  for (int e = e_lo; e < e_hi; e += 4) {
-    TcEntry en[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (e + u < e_hi) en[u] = tab[e + u];
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (e + u < e_hi) mma_bf16(tmem + en[u].d, en[u].a + sb, en[u].b + sb, en[u].idesc, en[u].acc);
+  const TcEntry* tab = reinterpret_cast<const TcEntry*>(tc_sb() + t.shadow_bytes + t.wt_bytes);
+  const uint32_t tmem = tc_tmem(t);
+  const unsigned long long sb = smem_u32(tc_sb()) >> 4;
+  int g = 0;
+  for (int p = p0; p < p0 + np; ++p) {
+    const TcPass& ps = t.pass[p];
+    const int steps = ps.ne / ps.n_tiles;
+    for (int tt = 0; tt < ps.n_tiles; ++tt, ++g) {
+      if (g % nw != w) continue;
+      const TcEntry* en = tab + ps.e0 + tt * steps;
+      for (int st = 0; st < steps; ++st)
+        mma_bf16(tmem + en[st].d, en[st].a + sb, en[st].b + sb, en[st].idesc, en[st].acc);
+    }
+    mma_commit(tc_bar(t, crown ? kTcCrownBar : p));
   }
-  mma_commit(bar);
 }
 
 // Epilogue of one 8-column chunk of one tile row (this thread's TMEM lane):
@@ -832,7 +891,7 @@ __device__ __forceinline__ void tc_epi_chunk(const Ctx<S, NT, TC>& c, const TcPa
       rho[roff + jn] = r;
       out[e] = r;
     }
-    *reinterpret_cast<uint4*>(c.sb + rs_at<S>(h, ch, y, x, s)) = pack8(out);
+    *reinterpret_cast<uint4*>(tc_sb() + rs_at<S>(h, ch, y, x, s)) = pack8(out);
     return;
   }
   // transposed: input position (Y, X) of layer k
@@ -843,17 +902,36 @@ __device__ __forceinline__ void tc_epi_chunk(const Ctx<S, NT, TC>& c, const TcPa
   }
   const int hw = L.h * L.w, pos = Y * L.w + X;
   if (k == 0) {
-    // P0 (Eq. box_bounds_sol): x0 = u0 where g_0 >= 0, else l0; stored centred
-    const int p = prop_at(c, s);
+    // P0 (Eq. box_bounds_sol): x0 = u0 where g_0 >= 0, else l0; stored centred,
+    // as +-(u0 - l0) / 2.  With cin <= 4 the half-widths sit in channels
+    // cin .. 2 cin - 1 of the same shadow position (weights there are zero),
+    // written once per launch; otherwise they come from the box.
+    uint4* dst = reinterpret_cast<uint4*>(tc_sb() + xs_at<S>(h, L.pad, ch, Y, X, s));
+    if (L.cin <= 4) {
+      const uint4 cur = *dst;
+      const uint32_t wd[4] = {cur.x, cur.y, cur.z, cur.w};
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      out[e] = 0.f;
-      if (c0 + e >= L.cin) continue;
-      const size_t i0 = (size_t)p * c.P.n0 + (size_t)(c0 + e) * hw + pos;
-      const float half = 0.5f * (c.P.u0[i0] - c.P.l0[i0]);
-      out[e] = v[e] >= 0.f ? half : -half;
+      for (int e = 0; e < 8; ++e) out[e] = 0.f;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (e >= L.cin) continue;
+        const int ce = L.cin + e;  // channel holding the half-width of channel e
+        const float half = __uint_as_float((ce & 1 ? wd[ce >> 1] & 0xffff0000u : wd[ce >> 1] << 16));
+        out[e] = v[e] >= 0.f ? half : -half;
+        out[ce] = half;
+      }
+    } else {
+      const int p = prop_at(c, s);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        out[e] = 0.f;
+        if (c0 + e >= L.cin) continue;
+        const size_t i0 = (size_t)p * c.P.n0 + (size_t)(c0 + e) * hw + pos;
+        const float half = 0.5f * (c.P.u0[i0] - c.P.l0[i0]);
+        out[e] = v[e] >= 0.f ? half : -half;
+      }
     }
-    *reinterpret_cast<uint4*>(c.sb + xs_at<S>(h, L.pad, ch, Y, X, s)) = pack8(out);
+    *dst = pack8(out);
     return;
   }
   const LayerDev& Lp = c.net.L[k - 1];
@@ -883,7 +961,7 @@ __device__ __forceinline__ void tc_epi_chunk(const Ctx<S, NT, TC>& c, const TcPa
       out[e] = r;
     }
     // rho_k is the output dual of conv layer k-1, at the same position
-    *reinterpret_cast<uint4*>(c.sb + rs_at<S>(c.tc->sh[k - 1], ch, Y, X, s)) = pack8(out);
+    *reinterpret_cast<uint4*>(tc_sb() + rs_at<S>(c.tc->sh[k - 1], ch, Y, X, s)) = pack8(out);
     return;
   }
   float l[8] = {}, u[8] = {}, r[8] = {};
@@ -914,27 +992,28 @@ __device__ __forceinline__ void tc_epi_chunk(const Ctx<S, NT, TC>& c, const TcPa
     c.xb(s)[Lp.r_out_off + (c0 + e) * hw + pos] = xb;
     out[e] = xv;
   }
-  *reinterpret_cast<uint4*>(c.sb + xs_at<S>(h, L.pad, ch, Y, X, s)) = pack8(out);
+  *reinterpret_cast<uint4*>(tc_sb() + xs_at<S>(h, L.pad, ch, Y, X, s)) = pack8(out);
 }
 
-// Wait for the MMAs committed to mbarrier bar (phase parity par), then run the
-// epilogues of passes [p0, p0 + np) on the conv group (gw: its warp index;
-// the group is 8 warps, two per TMEM lane quadrant, the quadrant of warp w
-// being w % 4 of the CTA).  A wait that gives up sets the abort flag and the
-// status; the epilogues are then skipped.
+// The epilogues of passes [p0, p0 + np) on the conv group (gw: its warp
+// index; the group is 8 warps, two per TMEM lane quadrant, the quadrant of
+// warp w being w % 4 of the CTA): for each pass, wait for its MMAs (phase
+// parity par; the CROWN barrier in crown mode), so that the epilogue of one
+// pass runs while the MMAs of the next are still being issued.  A wait that
+// gives up sets the abort flag and the status; the epilogues are then skipped.
 template <int S, int NT, bool TC>
-__device__ void tc_epilogues(const Ctx<S, NT, TC>& c, int p0, int np, uint32_t bar, uint32_t par, int gw,
-                             const FusedIter& it, const AdamStep& st) {
-  if (!mbar_wait_ab(bar, par, c.abort)) {
-    if ((threadIdx.x & 31) == 0 && c.tc->status) atomicExch(c.tc->status, (int)LD_ERR_TIMEOUT);
-    return;
-  }
-  tc_fence_after();
+__device__ __forceinline__ void tc_epilogues(const Ctx<S, NT, TC>& c, int p0, int np, uint32_t par, int gw,
+                                             const FusedIter& it, const AdamStep& st) {
   const int lane = threadIdx.x & 31, q = (threadIdx.x >> 5) & 3, half = gw >> 2;
   const int row = 32 * q + lane;
-  const uint32_t lane_base = c.tmem + ((uint32_t)(32 * q) << 16);
+  const uint32_t lane_base = tc_tmem(*c.tc) + ((uint32_t)(32 * q) << 16);
   constexpr int kBatch = 2;  // TMEM loads in flight before one wait
   for (int p = p0; p < p0 + np; ++p) {
+    if (!mbar_wait_ab(tc_bar(*c.tc, c.crown ? kTcCrownBar : p), par, tc_abort(*c.tc))) {
+      if (lane == 0 && c.tc->status) atomicExch(c.tc->status, (int)LD_ERR_TIMEOUT);
+      return;
+    }
+    tc_fence_after();
     const TcPass& ps = c.tc->pass[p];
     const int units = ps.n_tiles * ps.nch;
     for (int u0 = half; u0 < units; u0 += 2 * kBatch) {
@@ -990,14 +1069,8 @@ __global__ void __launch_bounds__(NT) fused_kernel(const __grid_constant__ Fused
   Ctx<S, NT, TC> c{net, P, sW, XP, XB, RHO, M, V, RED, b0, false, empty, {}};
   if (S == 1) c.prop[0] = b0 < P.B ? prop_of(P, b0) : 0;
   if constexpr (TC) {
-    unsigned char* sb = reinterpret_cast<unsigned char*>(smem);
+    unsigned char* sb = tc_sb();
     c.tc = &tcp;
-    c.sb = sb;
-    c.sbase = smem_u32(sb);
-    const int bar_off = tcp.shadow_bytes + tcp.wt_bytes + tcp.tab_bytes;
-    c.tab = reinterpret_cast<const TcEntry*>(sb + tcp.shadow_bytes + tcp.wt_bytes);
-    c.bar = c.sbase + (uint32_t)bar_off;  // 3 mbarriers, then the TMEM slot, the abort flag
-    c.abort = reinterpret_cast<volatile int*>(sb + bar_off + 32);
     // zero shadows (their halos and padding stay zero), stage the weight tiles and the MMA table
     for (int e = threadIdx.x; e < tcp.shadow_bytes / 16; e += NT)
       reinterpret_cast<uint4*>(sb)[e] = make_uint4(0u, 0u, 0u, 0u);
@@ -1006,21 +1079,38 @@ __global__ void __launch_bounds__(NT) fused_kernel(const __grid_constant__ Fused
     for (int e = threadIdx.x; e < tcp.tab_bytes / 16; e += NT)
       reinterpret_cast<uint4*>(sb + tcp.shadow_bytes + tcp.wt_bytes)[e] =
           __ldg(reinterpret_cast<const uint4*>(tcp.table) + e);
+    __syncthreads();  // shadows zeroed
+    // the box half-widths (u0 - l0) / 2 in BF16 beside x0, channel cin + c
+    // (layer 1 with cin <= 4: its weights for those channels are zero)
+    const LayerDev& L0 = net.L[0];
+    if (L0.cin <= 4) {
+      const int hw0 = L0.h * L0.w;
+      for (int s = 0; s < S; ++s) {
+        if (!active(c, s)) continue;
+        const float* lo = P.l0 + (size_t)prop_at(c, s) * P.n0;
+        const float* up = P.u0 + (size_t)prop_at(c, s) * P.n0;
+        for (int e = threadIdx.x; e < L0.cin * hw0; e += NT) {
+          const int ch = e / hw0, pos = e - ch * hw0, Y = pos / L0.w, X = pos - Y * L0.w;
+          *reinterpret_cast<__nv_bfloat16*>(sb + xs_at<S>(tcp.sh[0], L0.pad, 0, Y, X, s) + 2 * (L0.cin + ch)) =
+              __float2bfloat16_rn(0.5f * (up[e] - lo[e]));
+        }
+      }
+    }
     if (threadIdx.x == 0) {
-      for (int i = 0; i < 3; ++i) mbar_init(c.bar + 8 * i, 1);
-      *c.abort = 0;
+      for (int i = 0; i < tcp.npass; ++i) mbar_init(tc_bar(tcp, i), kTcIssuers);
+      mbar_init(tc_bar(tcp, kTcCrownBar), 1);
+      *tc_abort(tcp) = 0;
       fence_mbar_init();
     }
     // one warp allocates the TMEM columns (and later frees them)
     if (threadIdx.x / 32 == NT / 32 - 1) {
-      tmem_alloc(c.bar + 24, (uint32_t)tcp.tmem_cols);
+      tmem_alloc(tc_tmem_slot(tcp), (uint32_t)tcp.tmem_cols);
       tmem_relinquish();
     }
     fence_proxy_async();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    c.tmem = *reinterpret_cast<volatile uint32_t*>(sb + bar_off + 24);
   }
   // conv weights (FP32 passes only); zero planes (their halos stay zero for the whole run)
   for (int k = 0; k < net.n; ++k) {
@@ -1081,8 +1171,8 @@ __global__ void __launch_bounds__(NT) fused_kernel(const __grid_constant__ Fused
           // epilogue writes rho_k and its shadow
           int p = tcp.t0;
           while (p < tcp.t0 + tcp.nt && tcp.pass[p].k != k) ++p;
-          if (tc.tid == 0) tc_issue(tcp, c.tab, p, 1, c.sbase, c.tmem, c.bar + 16);
-          if (tc.tid >= 0) tc_epilogues(c, p, 1, c.bar + 16, cpar, tc.tid / 32, it, it.step[0]);
+          if (tc.tid == 0) tc_issue(tcp, p, 1, 0, 1, true);
+          if (tc.tid >= 0) tc_epilogues(c, p, 1, cpar, tc.tid / 32, it, it.step[0]);
           cpar ^= 1u;
         }
       } else {
@@ -1124,8 +1214,10 @@ __global__ void __launch_bounds__(NT) fused_kernel(const __grid_constant__ Fused
         for (int k = net.n - 2; k >= 0; --k)
           if (net.L[k].kind == LD_LAYER_FC) tfc_main(c, net.L[k], net.F[k], k, tf);
       } else if constexpr (TC) {
-        if (tc.tid == 0) tc_issue(tcp, c.tab, tcp.t0, tcp.nt, c.sbase, c.tmem, c.bar);
-        tc_epilogues(c, tcp.t0, tcp.nt, c.bar, (uint32_t)(t & 1), tc.tid / 32, it, st);
+        // lane 0 of the group's first kTcIssuers warps issue, then all run the epilogues
+        if ((tc.tid & 31) == 0 && tc.tid < 32 * kTcIssuers)
+          tc_issue(tcp, tcp.t0, tcp.nt, tc.tid / 32, kTcIssuers, false);
+        tc_epilogues(c, tcp.t0, tcp.nt, (uint32_t)(t & 1), tc.tid / 32, it, st);
       } else {
         for (int k = net.n - 2; k >= 0; --k)
           if (net.L[k].kind != LD_LAYER_FC) transposed_pass(c, net.L[k], net.F[k], k, tc);
@@ -1143,12 +1235,13 @@ __global__ void __launch_bounds__(NT) fused_kernel(const __grid_constant__ Fused
         if (net.L[k].kind == LD_LAYER_FC) tfc_finish(c, net.L[k], net.F[k], k, tf);
       __syncthreads();
     }
-    if (TC && *c.abort) break;
+    if (TC && *tc_abort(tcp)) break;
     for (int k = net.n - 2; k >= 0; --k)
       if (net.L[k].kind == LD_LAYER_FC) ffc_main(c, net.L[k], net.F[k], k, tf);
     if constexpr (TC) {
-      if (tc.tid == 0) tc_issue(tcp, c.tab, tcp.f0, tcp.nf, c.sbase, c.tmem, c.bar + 8);
-      if (tc.tid >= 0) tc_epilogues(c, tcp.f0, tcp.nf, c.bar + 8, (uint32_t)(t & 1), tc.tid / 32, it, st);
+      if (tc.tid >= 0 && (tc.tid & 31) == 0 && tc.tid < 32 * kTcIssuers)
+        tc_issue(tcp, tcp.f0, tcp.nf, tc.tid / 32, kTcIssuers, false);
+      if (tc.tid >= 0) tc_epilogues(c, tcp.f0, tcp.nf, (uint32_t)(t & 1), tc.tid / 32, it, st);
     } else {
       for (int k = net.n - 2; k >= 0; --k)
         if (net.L[k].kind != LD_LAYER_FC) forward_conv(c, net.L[k], net.F[k], it, st, tc);
@@ -1159,7 +1252,7 @@ __global__ void __launch_bounds__(NT) fused_kernel(const __grid_constant__ Fused
         if (net.L[k].kind == LD_LAYER_FC) ffc_finish(c, net.L[k], net.F[k], k, it, st, all);
     }
     __syncthreads();
-    if (TC && *c.abort) break;
+    if (TC && *tc_abort(tcp)) break;
   }
   if constexpr (TC) {
     // free the TMEM columns; after a wait gave up, leave the state untouched
@@ -1168,9 +1261,9 @@ __global__ void __launch_bounds__(NT) fused_kernel(const __grid_constant__ Fused
     __syncthreads();
     if (threadIdx.x / 32 == NT / 32 - 1) {
       tc_fence_after();
-      tmem_dealloc(c.tmem, (uint32_t)tcp.tmem_cols);
+      tmem_dealloc(tc_tmem(tcp), (uint32_t)tcp.tmem_cols);
     }
-    if (*c.abort) return;
+    if (*tc_abort(tcp)) return;
   }
   // the FC Adam epilogues of the last iteration
   if (nf && any_fc && it.T > 0) {

@@ -38,12 +38,6 @@ uint16_t host_bf16(float f) {
   u += 0x7FFFu + ((u >> 16) & 1u);
   return (uint16_t)(u >> 16);
 }
-float host_bf16_round(float f) {
-  const uint32_t u = (uint32_t)host_bf16(f) << 16;
-  float r;
-  std::memcpy(&r, &u, 4);
-  return r;
-}
 
 // Shared-memory matrix descriptor (no swizzle, K-major), start relative to
 // the dynamic shared-memory base.
@@ -229,7 +223,9 @@ bool plan_fused_tc(const std::vector<LayerDev>& Ls, const std::vector<std::vecto
       n_entries += ((int)pcs[q].per_phase[tt / (ps.tr * ps.tx)].size() + 1) / 2;
   }
   t.tab_bytes = round_up(n_entries * (int)sizeof(TcEntry), 128);
-  t.tc_bytes = t.shadow_bytes + t.wt_bytes + t.tab_bytes + 128;  // + 3 mbarriers, the TMEM slot, the abort flag
+  // + the control block: an mbarrier per pass and one for the CROWN start,
+  // the TMEM address slot, the abort flag
+  t.tc_bytes = t.shadow_bytes + t.wt_bytes + t.tab_bytes + round_up(8 * (kTcMaxPass + 3), 128);
   if (col > 512) return false;
   t.tmem_cols = 32;
   while (t.tmem_cols < col) t.tmem_cols *= 2;
@@ -294,6 +290,7 @@ bool plan_fused_tc(const std::vector<LayerDev>& Ls, const std::vector<std::vecto
       }
     }
     ps.ne = (int)out.entries.size() - ps.e0;
+    if (ps.ne % ps.n_tiles != 0) return false;  // the issuers assume the same K steps for every tile
   }
   return (int)out.entries.size() == n_entries;
 }
@@ -337,7 +334,7 @@ ld_status build_fused_tc(const std::vector<LayerDev>& Ls, FusedNet* f, FusedTc o
   for (int k = 0; k + 1 < n; ++k)
     if (Ls[k].kind == LD_LAYER_FC) {
       fc_off[k] = bytes;
-      bytes += (W[k].size() * 4 + 255) / 256 * 256;
+      bytes += (W[k].size() * 2 + 255) / 256 * 256;
     }
   size_t tab_off[2], wt_off[2];
   for (int i = 0; i < 2; ++i) {
@@ -355,13 +352,13 @@ ld_status build_fused_tc(const std::vector<LayerDev>& Ls, FusedNet* f, FusedTc o
   char* c = static_cast<char*>(p);
   for (int k = 0; k + 1 < n; ++k)
     if (Ls[k].kind == LD_LAYER_FC) {
-      std::vector<float> r(W[k].size());
-      for (size_t z = 0; z < r.size(); ++z) r[z] = host_bf16_round(W[k][z]);
-      if (cudaMemcpy(c + fc_off[k], r.data(), r.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+      std::vector<uint16_t> r(W[k].size());
+      for (size_t z = 0; z < r.size(); ++z) r[z] = host_bf16(W[k][z]);
+      if (cudaMemcpy(c + fc_off[k], r.data(), r.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaFree(p);
         return LD_ERR_CUDA;
       }
-      f->L[k].W = reinterpret_cast<const float*>(c + fc_off[k]);
+      f->L[k].Wh = reinterpret_cast<const uint16_t*>(c + fc_off[k]);
     }
   for (int i = 0; i < 2; ++i) {
     if (!ok[i]) continue;

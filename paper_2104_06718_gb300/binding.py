@@ -94,7 +94,7 @@ def load_library(path: str = LIB_PATH):
     lib.ld_net_profile.argtypes = [vp, i32]
     lib.ld_net_profile_read.argtypes = [vp, i32, C.POINTER(C.c_double), C.POINTER(i64), i32]
     lib.ld_launch_count.argtypes = [C.POINTER(i64)]
-    lib.ld_net_tuned.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
+    lib.ld_net_tuned.argtypes = [vp, i32, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
     lib.ld_final_bound_noalloc.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, i32, vp, vp, vp]
     lib.ld_test_inject_alloc_failure.argtypes = [i32, i32]
     lib.ld_intermediate_bounds_propagated.argtypes = [vp, vp, vp, i32, vp, vp, i32, i32, vp, vp, vp]

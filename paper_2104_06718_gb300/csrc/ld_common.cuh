@@ -493,6 +493,7 @@ struct FusedTc {
   int tab_bytes;              // bytes of the MMA table (copied to shared memory after the weight tiles)
   int tc_bytes;               // shadows + weight tiles + table + barriers: the part before the FP32 state
   int tmem_cols;              // TMEM allocation of a CTA (power of 2)
+  int issuers;                // threads that issue the MMAs of a phase (lane 0 of the conv group's first warps)
   const TcEntry* table;
   const uint16_t* wtiles;     // device copy of the weight tiles
   const float* c1;            // [props, n_out of layer 1]: W_1 c_0 + b_1, c_0 the box centre

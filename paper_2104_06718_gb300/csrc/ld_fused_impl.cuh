@@ -120,9 +120,8 @@ extern __shared__ __align__(128) unsigned char g_fused_smem[];
 __device__ __forceinline__ unsigned char* tc_sb() { return g_fused_smem; }
 __device__ __forceinline__ int tc_ctl_off(const FusedTc& t) { return t.shadow_bytes + t.wt_bytes + t.tab_bytes; }
 // Control block: one mbarrier per pass (its MMAs, committed by each of the
-// kTcIssuers issuing threads), one for the CROWN start (one issuer), the TMEM
+// plan's issuing threads), one for the CROWN start (one issuer), the TMEM
 // base address written by tcgen05.alloc, the abort flag.
-constexpr int kTcIssuers = 4;
 constexpr int kTcCrownBar = kTcMaxPass;
 __device__ __forceinline__ uint32_t tc_bar(const FusedTc& t, int i) {
   return smem_u32(g_fused_smem) + (uint32_t)(tc_ctl_off(t) + 8 * i);
@@ -1097,7 +1096,7 @@ __global__ void __launch_bounds__(NT) fused_kernel(const __grid_constant__ Fused
       }
     }
     if (threadIdx.x == 0) {
-      for (int i = 0; i < tcp.npass; ++i) mbar_init(tc_bar(tcp, i), kTcIssuers);
+      for (int i = 0; i < tcp.npass; ++i) mbar_init(tc_bar(tcp, i), tcp.issuers);
       mbar_init(tc_bar(tcp, kTcCrownBar), 1);
       *tc_abort(tcp) = 0;
       fence_mbar_init();
@@ -1214,9 +1213,9 @@ __global__ void __launch_bounds__(NT) fused_kernel(const __grid_constant__ Fused
         for (int k = net.n - 2; k >= 0; --k)
           if (net.L[k].kind == LD_LAYER_FC) tfc_main(c, net.L[k], net.F[k], k, tf);
       } else if constexpr (TC) {
-        // lane 0 of the group's first kTcIssuers warps issue, then all run the epilogues
-        if ((tc.tid & 31) == 0 && tc.tid < 32 * kTcIssuers)
-          tc_issue(tcp, tcp.t0, tcp.nt, tc.tid / 32, kTcIssuers, false);
+        // lane 0 of the group's first tcp.issuers warps issue, then all run the epilogues
+        if ((tc.tid & 31) == 0 && tc.tid < 32 * tcp.issuers)
+          tc_issue(tcp, tcp.t0, tcp.nt, tc.tid / 32, tcp.issuers, false);
         tc_epilogues(c, tcp.t0, tcp.nt, (uint32_t)(t & 1), tc.tid / 32, it, st);
       } else {
         for (int k = net.n - 2; k >= 0; --k)
@@ -1239,8 +1238,8 @@ __global__ void __launch_bounds__(NT) fused_kernel(const __grid_constant__ Fused
     for (int k = net.n - 2; k >= 0; --k)
       if (net.L[k].kind == LD_LAYER_FC) ffc_main(c, net.L[k], net.F[k], k, tf);
     if constexpr (TC) {
-      if (tc.tid >= 0 && (tc.tid & 31) == 0 && tc.tid < 32 * kTcIssuers)
-        tc_issue(tcp, tcp.f0, tcp.nf, tc.tid / 32, kTcIssuers, false);
+      if (tc.tid >= 0 && (tc.tid & 31) == 0 && tc.tid < 32 * tcp.issuers)
+        tc_issue(tcp, tcp.f0, tcp.nf, tc.tid / 32, tcp.issuers, false);
       if (tc.tid >= 0) tc_epilogues(c, tcp.f0, tcp.nf, (uint32_t)(t & 1), tc.tid / 32, it, st);
     } else {
       for (int k = net.n - 2; k >= 0; --k)

@@ -120,7 +120,9 @@ bool plan_fused_tc(const std::vector<LayerDev>& Ls, const std::vector<std::vecto
   }
   t.shadow_bytes = round_up(off, 128);
 
-  // passes: transposed k = nconv-1 .. 0, then forward k = 0 .. nconv-1
+  // passes: transposed k = nconv-1 .. 0, then forward k = nconv-1 .. 0 (in
+  // each phase the deeper, smaller layer first: its epilogue starts while
+  // the MMAs of the larger one are still being issued)
   struct PassChunks {
     std::vector<std::vector<Chunk>> per_phase;
   };
@@ -130,7 +132,7 @@ bool plan_fused_tc(const std::vector<LayerDev>& Ls, const std::vector<std::vecto
   std::vector<std::vector<int>> wt_phase;  // per pass, per phase: byte offset of its tiles in the weight region
   for (int q = 0; q < 2 * nconv; ++q) {
     const bool fwd = q >= nconv;
-    const int k = fwd ? q - nconv : nconv - 1 - q;
+    const int k = fwd ? 2 * nconv - 1 - q : nconv - 1 - q;
     const LayerDev& L = Ls[k];
     const TcShadow& h = t.sh[k];
     TcPass& ps = t.pass[q];
@@ -229,6 +231,12 @@ bool plan_fused_tc(const std::vector<LayerDev>& Ls, const std::vector<std::vecto
   if (col > 512) return false;
   t.tmem_cols = 32;
   while (t.tmem_cols < col) t.tmem_cols *= 2;
+  // MMA issue: a tcgen05.mma reading these no-swizzle shifted views keeps
+  // its issuing thread busy for hundreds of cycles (measured on GB300, Base,
+  // the 48 MMAs of the transposed passes: 22.6k cycles from one thread,
+  // 15.9k from two, 12.5k from four, 10.4k from eight), so lane 0 of every
+  // warp of the conv group issues a share
+  t.issuers = 8;
   const size_t fp32 = 4 * ((size_t)f.convW_total +
                            (size_t)S * (f.xp_total + f.rho_total + 3 * (size_t)f.nb + red_floats(f, kTcThreads)));
   out.smem_total = (size_t)t.tc_bytes + fp32;

@@ -147,3 +147,19 @@ def test_full_size_base_call():
     both = np.isfinite(out) & np.isfinite(f32)
     gap = rel(out[both], f32[both])
     assert np.median(gap) < FULL_RUN_MEDIAN and gap.max() < GAP_MAX
+
+
+def test_autotuner_reports_the_bf16_engine():
+    """LD_ENGINE_AUTO with BF16 iterations times the layer-wise and the fused
+    tensor-core engines and caches its choice per batch size; ld_net_tuned
+    reports it (FP32 and BF16 choices are kept apart)."""
+    pb = conv_problem("base", 32, depth=(0, 8), block=4)
+    net = ldb.Net(pb["specs"])
+    assert net.tuned(32, "bf16") == (None, 0, 0)
+    run_gpu(pb, 4, ldb.Options(precision="bf16"), net)
+    eng, tile, threads = net.tuned(32, "bf16")
+    assert (eng, threads) in (("layerwise", 0), ("fused", 512))
+    assert eng != "fused" or tile in (1, 2)
+    assert net.tuned(32, "fp32") == (None, 0, 0)
+    run_gpu(pb, 4, ldb.Options(), net)
+    assert net.tuned(32, "fp32")[0] in ("layerwise", "fused")

@@ -36,7 +36,6 @@ struct LayerDev {
   const double* W64;             // last layer only: the margin-folded row summed in FP64 [n_in]
   const double* W64_err;         // last layer only: bound on that row's summation error [n_in]
   const double* b64;             // last layer only: {folded b_n in FP64, bound on its error}
-  const uint16_t* Wh;            // fused tensor-core engine, hidden FC layers: W in BF16 [n_out, n_in]
 };
 
 // Inputs of one bounding call, in device memory.
@@ -412,6 +411,8 @@ struct FusedLayer {
   int Hr, Wr;                  // padded dims of that plane; FC: 1 x n_out
   int xoff;                    // offset of the input plane in the per-subdomain x area
   int roff;                    // offset of the output rho plane in the per-subdomain rho area (hidden layers)
+  int rroff;                   // tc layout, hidden FC layers: a BF16-rounded copy of that rho (the FC
+                               // transposed pass's operand), kept beside it; -1 otherwise
   int swf, swt;                // shared-memory offsets (floats) of the forward / transposed weight layouts
   int fmode, tmode;            // 0 generic; 1 blocked k4 s2; 2 blocked k3 s1
   int vec4;                    // FC: rows 16-byte aligned and n_in % 4 == 0

@@ -114,6 +114,13 @@ FusedNet make_fused_net(const std::vector<LayerDev>& Ls, bool tc) {
       F.roff = 0;
     }
   }
+  for (int k = 0; k < f.n; ++k) {
+    f.F[k].rroff = -1;
+    if (tc && k < f.n - 1 && Ls[k].kind == LD_LAYER_FC) {
+      f.F[k].rroff = roff;
+      roff += round4(Ls[k].n_out);
+    }
+  }
   f.xp_total = xoff > 4 ? xoff : 4;
   f.rho_total = roff > 4 ? roff : 4;
   f.nb = round4(N > 0 ? N : 1);

@@ -136,12 +136,6 @@ __device__ __forceinline__ volatile int* tc_abort(const FusedTc& t) {
 
 // BF16 rounding of an FP32 operand (round to nearest even), kept in FP32.
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
-// Four BF16 values (little-endian pairs) widened to FP32 (exact).
-__device__ __forceinline__ float4 bf16x4_to_float4(uint2 h) {
-  return make_float4(__uint_as_float(h.x << 16), __uint_as_float(h.x & 0xffff0000u), __uint_as_float(h.y << 16),
-                     __uint_as_float(h.y & 0xffff0000u));
-}
-__device__ __forceinline__ float bf16_at(const uint16_t* p) { return __uint_as_float((uint32_t)__ldg(p) << 16); }
 
 // Byte offset of the 8 channels 8g..8g+7 of input position (Y, X) of conv
 // layer k (its x_k shadow) for subdomain s: padded coordinates, by stride
@@ -195,7 +189,10 @@ __device__ __forceinline__ void epi_t_lu(const Ctx<S, NT, TC>& c, int k, int s, 
     }
     c.rho(s)[ri] = a_up * fmaxf(g, 0.f) + a_lo * fminf(g, 0.f);
     if constexpr (TC) {
-      if (c.net.L[k - 1].kind == LD_LAYER_CONV) rho_shadow1(c, k, s, i, c.rho(s)[ri]);
+      if (c.net.L[k - 1].kind == LD_LAYER_CONV)
+        rho_shadow1(c, k, s, i, c.rho(s)[ri]);
+      else
+        c.rho(s)[c.net.F[k - 1].rroff + i] = bf16r(c.rho(s)[ri]);
     }
     return;
   }
@@ -287,7 +284,7 @@ __device__ __forceinline__ float* red_of(const Ctx<S, NT, TC>& c, int k) {
 template <int S, int NT, bool TC>
 __device__ __forceinline__ void tfc_rows(const Ctx<S, NT, TC>& c, const LayerDev& L, const FusedLayer& F, int i4,
                                          int b_lo, int b_hi, float4 (&acc)[S]) {
-  constexpr int U = 16;  // weight rows in flight per thread
+  constexpr int U = TC ? 12 : 16;  // weight rows in flight per thread (TC: fewer, its kernel has less room)
   const float* __restrict__ W = L.W;
 #pragma unroll
   for (int s = 0; s < S; ++s) acc[s] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -297,16 +294,7 @@ __device__ __forceinline__ void tfc_rows(const Ctx<S, NT, TC>& c, const LayerDev
     // so that concurrent CTAs spread over the L2 slices
     const int o0 = U * (b_lo + (bi + (int)blockIdx.x) % nb);
     float4 wv[U];
-    if constexpr (TC) {
-      // BF16 weights: half the bytes of the L2 stream, widened when used
-      uint2 wh[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        wh[u] = (o0 + u < L.n_out) ? __ldg(reinterpret_cast<const uint2*>(L.Wh + (size_t)(o0 + u) * L.n_in) + i4)
-                                   : make_uint2(0u, 0u);
-#pragma unroll
-      for (int u = 0; u < U; ++u) wv[u] = bf16x4_to_float4(wh[u]);
-    } else {
+    {
 #pragma unroll
       for (int u = 0; u < U; ++u)
         wv[u] = (o0 + u < L.n_out) ? __ldg(reinterpret_cast<const float4*>(W + (size_t)(o0 + u) * L.n_in) + i4)
@@ -317,7 +305,8 @@ __device__ __forceinline__ void tfc_rows(const Ctx<S, NT, TC>& c, const LayerDev
       if (o0 + u < L.n_out) {
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-          const float r = TC ? bf16r(c.rho(s)[F.roff + o0 + u]) : c.rho(s)[F.roff + o0 + u];
+          // TC: the BF16-rounded copy of the FC layer's output duals
+          const float r = c.rho(s)[(TC ? F.rroff : F.roff) + o0 + u];
           const float2 rp = make_float2(r, r);
           const float2 lo = __ffma2_rn(make_float2(wv[u].x, wv[u].y), rp, make_float2(acc[s].x, acc[s].y));
           const float2 hi = __ffma2_rn(make_float2(wv[u].z, wv[u].w), rp, make_float2(acc[s].z, acc[s].w));
@@ -359,7 +348,7 @@ __device__ __forceinline__ void tfc_bounds(const Ctx<S, NT, TC>& c, int k, int s
 template <int S, int NT, bool TC>
 __device__ void tfc_main(const Ctx<S, NT, TC>& c, const LayerDev& L, const FusedLayer& F, int k, const Team& tm) {
   const float* __restrict__ W = L.W;
-  constexpr int U = 16;
+  constexpr int U = TC ? 12 : 16;
   if (tm.tid < 0) return;
   if (tfc_split(L, F, tm.n)) {
     const int n4 = L.n_in / 4, half = tm.n / 2;
@@ -394,9 +383,9 @@ __device__ void tfc_main(const Ctx<S, NT, TC>& c, const LayerDev& L, const Fused
 #pragma unroll
     for (int s = 0; s < S; ++s) acc[s] = 0.f;
     for (int o = 0; o < L.n_out; ++o) {
-      const float w = TC ? bf16_at(L.Wh + (size_t)o * L.n_in + i) : __ldg(W + (size_t)o * L.n_in + i);
+      const float w = __ldg(W + (size_t)o * L.n_in + i);
 #pragma unroll
-      for (int s = 0; s < S; ++s) acc[s] = fmaf(w, TC ? bf16r(c.rho(s)[F.roff + o]) : c.rho(s)[F.roff + o], acc[s]);
+      for (int s = 0; s < S; ++s) acc[s] = fmaf(w, c.rho(s)[(TC ? F.rroff : F.roff) + o], acc[s]);
     }
 #pragma unroll
     for (int s = 0; s < S; ++s)
@@ -460,30 +449,13 @@ __device__ void ffc_main(const Ctx<S, NT, TC>& c, const LayerDev& L, const Fused
       const int n4 = L.n_in / 4;
       const float4* w0 = reinterpret_cast<const float4*>(W + (size_t)j0 * L.n_in);
       const float4* w1 = reinterpret_cast<const float4*>(W + (size_t)(two ? j0 + 1 : j0) * L.n_in);
-      const uint2* h0 = reinterpret_cast<const uint2*>(L.Wh + (size_t)j0 * L.n_in);
-      const uint2* h1 = reinterpret_cast<const uint2*>(L.Wh + (size_t)(two ? j0 + 1 : j0) * L.n_in);
       for (int t0 = lane; t0 < n4; t0 += 32 * U) {
         float4 a[U], bq[U];
-        if constexpr (TC) {
-          uint2 ha[U], hb[U];
 #pragma unroll
-          for (int u = 0; u < U; ++u) {
-            const int t = t0 + 32 * u;
-            ha[u] = t < n4 ? __ldg(h0 + t) : make_uint2(0u, 0u);
-            hb[u] = t < n4 ? __ldg(h1 + t) : make_uint2(0u, 0u);
-          }
-#pragma unroll
-          for (int u = 0; u < U; ++u) {
-            a[u] = bf16x4_to_float4(ha[u]);
-            bq[u] = bf16x4_to_float4(hb[u]);
-          }
-        } else {
-#pragma unroll
-          for (int u = 0; u < U; ++u) {
-            const int t = t0 + 32 * u;
-            a[u] = t < n4 ? __ldg(w0 + t) : make_float4(0.f, 0.f, 0.f, 0.f);
-            bq[u] = t < n4 ? __ldg(w1 + t) : make_float4(0.f, 0.f, 0.f, 0.f);
-          }
+        for (int u = 0; u < U; ++u) {
+          const int t = t0 + 32 * u;
+          a[u] = t < n4 ? __ldg(w0 + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+          bq[u] = t < n4 ? __ldg(w1 + t) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -501,10 +473,8 @@ __device__ void ffc_main(const Ctx<S, NT, TC>& c, const LayerDev& L, const Fused
     } else {
       const float* w0 = W + (size_t)j0 * L.n_in;
       const float* w1 = W + (size_t)(two ? j0 + 1 : j0) * L.n_in;
-      const uint16_t* g0 = L.Wh + (size_t)j0 * L.n_in;
-      const uint16_t* g1 = L.Wh + (size_t)(two ? j0 + 1 : j0) * L.n_in;
       for (int i = lane; i < L.n_in; i += 32) {
-        const float a = TC ? bf16_at(g0 + i) : __ldg(w0 + i), bb = TC ? bf16_at(g1 + i) : __ldg(w1 + i);
+        const float a = __ldg(w0 + i), bb = __ldg(w1 + i);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
           const float x = c.xp(s)[F.xoff + i];
@@ -537,7 +507,9 @@ __device__ void ffc_finish(const Ctx<S, NT, TC>& c, const LayerDev& L, const Fus
   const float* red = red_of(c, k);
   for (int e = tm.tid; e < S * L.n_out; e += tm.n) {
     const int s = e / L.n_out, j = e - s * L.n_out;
-    if (active(c, s)) epi_f(c, L, s, j, j, F.roff + j, red[e], it, st);
+    if (!active(c, s)) continue;
+    epi_f(c, L, s, j, j, F.roff + j, red[e], it, st);
+    if constexpr (TC) c.rho(s)[F.rroff + j] = bf16r(c.rho(s)[F.roff + j]);
   }
 }
 
@@ -1137,7 +1109,10 @@ __global__ void __launch_bounds__(NT) fused_kernel(const __grid_constant__ Fused
         const float r = rho[gb + L.r_out_off + j];
         c.rho(s)[rho_flat(L, F, j)] = r;
         if constexpr (TC) {
-          if (L.kind == LD_LAYER_CONV) rho_shadow1(c, k, s, j, r);
+          if (L.kind == LD_LAYER_CONV)
+            rho_shadow1(c, k, s, j, r);
+          else
+            c.rho(s)[F.rroff + j] = bf16r(r);
         }
       }
     }

@@ -342,7 +342,7 @@ ld_status build_fused_tc(const std::vector<LayerDev>& Ls, FusedNet* f, FusedTc o
   for (int k = 0; k + 1 < n; ++k)
     if (Ls[k].kind == LD_LAYER_FC) {
       fc_off[k] = bytes;
-      bytes += (W[k].size() * 2 + 255) / 256 * 256;
+      bytes += (W[k].size() * 4 + 255) / 256 * 256;
     }
   size_t tab_off[2], wt_off[2];
   for (int i = 0; i < 2; ++i) {
@@ -360,13 +360,18 @@ ld_status build_fused_tc(const std::vector<LayerDev>& Ls, FusedNet* f, FusedTc o
   char* c = static_cast<char*>(p);
   for (int k = 0; k + 1 < n; ++k)
     if (Ls[k].kind == LD_LAYER_FC) {
-      std::vector<uint16_t> r(W[k].size());
-      for (size_t z = 0; z < r.size(); ++z) r[z] = host_bf16(W[k][z]);
-      if (cudaMemcpy(c + fc_off[k], r.data(), r.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) {
+      // BF16-rounded values kept in FP32 (the FC passes' loads and products
+      // stay those of the FP32 engine)
+      std::vector<float> r(W[k].size());
+      for (size_t z = 0; z < r.size(); ++z) {
+        const uint32_t u = (uint32_t)host_bf16(W[k][z]) << 16;
+        std::memcpy(&r[z], &u, 4);
+      }
+      if (cudaMemcpy(c + fc_off[k], r.data(), r.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaFree(p);
         return LD_ERR_CUDA;
       }
-      f->L[k].Wh = reinterpret_cast<const uint16_t*>(c + fc_off[k]);
+      f->L[k].W = reinterpret_cast<const float*>(c + fc_off[k]);
     }
   for (int i = 0; i < 2; ++i) {
     if (!ok[i]) continue;

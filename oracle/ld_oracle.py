@@ -371,13 +371,15 @@ def relu_subproblem_argmin(r, c, l, u):
     return xb, xk, code
 
 
-def inner_minimisation(net: Net, l0, u0, lb, ub, rho, passes=None) -> InnerSolution:
+def inner_minimisation(net: Net, l0, u0, lb, ub, rho, passes=None, ball_eps=None) -> InnerSolution:
     """Solve the decomposed inner problem of Eq. (nonprox_problem) at rho.
 
     l0, u0 [B, n_0]; lb, ub lists 1..n-1 of [B, n_k] (clamped); rho list 1..n-1.
     Vertex codes: 0 -> (l,0) / lower endpoint, 1 -> (0,0), 2 -> (u,u) / upper.
     `passes` supplies the linear passes (default: exact FP64, ExactPasses);
-    q is always computed from the g of those passes.
+    q is always computed from the g of those passes.  ball_eps [B]: the
+    input domain is the l2 ball of that radius around l0 (Sec. 3.2.1) instead
+    of the box [l0, u0].
     """
     n = net.n
     B = l0.shape[0]
@@ -387,8 +389,13 @@ def inner_minimisation(net: Net, l0, u0, lb, ub, rho, passes=None) -> InnerSolut
         rho_next = -np.ones((B, 1)) if k + 1 == n else rho[k + 1]
         g[k] = ps.transposed(k + 1, rho_next)
 
-    # P0 (Sec. 3.2.1, Eq. (box_bounds_sol)): minimise -g_0^T x0 over the box.
-    x = [box_argmin(-g[0], l0, u0)]
+    # P0 (Sec. 3.2.1): minimise -g_0^T x0 over the input domain: the box
+    # (Eq. (box_bounds_sol)) or the l2 ball
+    if ball_eps is None:
+        x = [box_argmin(-g[0], l0, u0)]
+    else:
+        from .l2 import ball_argmin
+        x = [ball_argmin(g[0], l0, ball_eps)]
     xB = [None]
     vertex = [None]
     # Pk (Sec. 3.2.2): minimise rho_k x_hat_B,k - g_k x_k over the ReLU hull.
@@ -407,7 +414,11 @@ def inner_minimisation(net: Net, l0, u0, lb, ub, rho, passes=None) -> InnerSolut
     # (dual_decomp_vs_dj)): the tie margins above may return a vertex whose
     # value exceeds the minimum by at most the margin, so q is not read off
     # the returned point.
-    q = np.sum(np.minimum(-g[0] * l0, -g[0] * u0), axis=1) + net.L(n).bias_vector()[0]
+    if ball_eps is None:
+        q = np.sum(np.minimum(-g[0] * l0, -g[0] * u0), axis=1) + net.L(n).bias_vector()[0]
+    else:
+        from .l2 import ball_min
+        q = ball_min(g[0], l0, ball_eps) + net.L(n).bias_vector()[0]
     for k in range(1, n):
         r, c, l, u = rho[k], g[k], lb[k], ub[k]
         cls = classify(l, u)
@@ -419,9 +430,9 @@ def inner_minimisation(net: Net, l0, u0, lb, ub, rho, passes=None) -> InnerSolut
     return InnerSolution(q=q, g=g, x=x, xB=xB, xA=xA, vertex=vertex, q_point=q_point)
 
 
-def dual_value(net, l0, u0, lb, ub, rho):
+def dual_value(net, l0, u0, lb, ub, rho, ball_eps=None):
     """q(rho) of Eq. (nonprox_problem); any rho gives a valid lower bound."""
-    return inner_minimisation(net, l0, u0, lb, ub, rho).q
+    return inner_minimisation(net, l0, u0, lb, ub, rho, ball_eps=ball_eps).q
 
 
 def supergradient(sol: InnerSolution):
@@ -608,7 +619,7 @@ class AdamResult:
 
 
 def supergradient_adam(net, l0, u0, lb, ub, rho0, T, s: AdamSettings = AdamSettings(),
-                       m0=None, v0=None, t0: int = 0, T_sched: int | None = None, passes=None):
+                       m0=None, v0=None, t0: int = 0, T_sched: int | None = None, passes=None, ball_eps=None):
     """Algorithm 1 with the Adam update in place of Eq. (subgradient_update).
 
     For t = 0..T-1: inner minimisation at rho^t, supergradient
@@ -618,7 +629,8 @@ def supergradient_adam(net, l0, u0, lb, ub, rho0, T, s: AdamSettings = AdamSetti
     and finally q(rho^T).  `t0`, `m0`, `v0`, `T_sched` resume a run that was
     split across calls (the schedule index is t0 + t out of T_sched).
     `passes` replaces the linear passes of the iterations (not of the final
-    q(rho^T), which is always exact).
+    q(rho^T), which is always exact).  ball_eps: l2-ball input domain
+    (inner_minimisation).
     """
     n = net.n
     rho = [None] + [np.array(rho0[k], dtype=np.float64, copy=True) for k in range(1, n)]
@@ -628,12 +640,12 @@ def supergradient_adam(net, l0, u0, lb, ub, rho0, T, s: AdamSettings = AdamSetti
     trace = []
     for t in range(T):
         tt = t0 + t
-        sol = inner_minimisation(net, l0, u0, lb, ub, rho, passes)
+        sol = inner_minimisation(net, l0, u0, lb, ub, rho, passes, ball_eps=ball_eps)
         trace.append(sol.q)
         sg = supergradient(sol)
         for k in range(1, n):
             rho[k], m[k], v[k] = adam_update(rho[k], m[k], v[k], sg[k], tt, Ts, s)
-    q_final = inner_minimisation(net, l0, u0, lb, ub, rho).q
+    q_final = inner_minimisation(net, l0, u0, lb, ub, rho, ball_eps=ball_eps).q
     q_trace = np.array(trace) if trace else np.zeros((0, l0.shape[0]))
     return AdamResult(rho=rho, m=m, v=v, q_trace=q_trace, q_final=q_final)
 
@@ -658,14 +670,17 @@ def flatten_layers(net, lst):
 
 
 def ld_bound(net: Net, l0, u0, lbk, ubk, prop_of_subdomain, masks, T,
-             s: AdamSettings = AdamSettings(), init: str = "crown", rho_in=None, operands: str = "fp64"):
+             s: AdamSettings = AdamSettings(), init: str = "crown", rho_in=None, operands: str = "fp64",
+             ball_eps=None):
     """Lower bound of min x_hat_n for each subdomain after T Adam updates.
 
     l0, u0 [P, n_0]; lbk, ubk [P, sum n_k] intermediate bounds of layers
     1..n-1; masks int8 [B, sum n_k].  Empty subdomains get +inf and no
     iterations.  operands "bf16" runs the iterations with BF16Passes (the
-    final bound stays exact).  Returns (bounds [B], AdamResult over the
-    feasible rows, feasible-row index array).
+    final bound stays exact).  ball_eps [P]: the input domain of property p
+    is the l2 ball of radius ball_eps[p] around l0[p] (Sec. 3.2.1; u0 is then
+    not used).  Returns (bounds [B], AdamResult over the feasible rows,
+    feasible-row index array).
     """
     B = masks.shape[0]
     pos = np.zeros(B, dtype=np.int64) if prop_of_subdomain is None else np.asarray(prop_of_subdomain)
@@ -694,7 +709,8 @@ def ld_bound(net: Net, l0, u0, lbk, ubk, prop_of_subdomain, masks, T,
         passes = BF16Passes(net, L0[keep], U0[keep])
     elif operands != "fp64":
         raise ValueError(operands)
-    res = supergradient_adam(net, L0[keep], U0[keep], lbs, ubs, rho0, T, s, passes=passes)
+    eps = None if ball_eps is None else expand_per_subdomain(np.asarray(ball_eps, np.float64), pos)[keep]
+    res = supergradient_adam(net, L0[keep], U0[keep], lbs, ubs, rho0, T, s, passes=passes, ball_eps=eps)
     out[keep] = res.q_final
     return out, res, keep
 

@@ -551,7 +551,7 @@ def test_planted_vertex_sign_error_is_caught(monkeypatch):
     good = oracle.dual_value(net, l0, u0, L, U, rho)[0]
     orig = oracle.ld_oracle.inner_minimisation
 
-    def bad(net_, l0_, u0_, lb_, ub_, rho_):
+    def bad(net_, l0_, u0_, lb_, ub_, rho_, ball_eps=None):
         rho2 = [None] + [r for r in rho_[1:]]
         sol = orig(net_, l0_, u0_, lb_, ub_, rho2)
         # recompute with the transposed pass negated (a transposed-operand slip)

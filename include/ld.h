@@ -163,6 +163,19 @@ ld_status ld_net_sync_status(ld_net* net, void* stream);
 ld_status ld_intermediate_bounds(ld_net* net, const float* lb0, const float* ub0, int32_t n_props,
                                  float* lbk, float* ubk, double* out_lb, void* stream);
 
+/* Interval bounds over l2 balls (Sec. 3.2.1, l2-ball input domains): the
+ * input set of property p is {x0 : ||x0 - center[p]||_2 <= eps[p]}.
+ *   center [device] [n_props, n_0] float; eps [device] [n_props] float >= 0.
+ *   lbk, ubk, out_lb as ld_intermediate_bounds.  Layer 1 is bounded exactly
+ *   up to rounding, (W_1 c + b_1)_j -+ eps ||W_1[j, :]||_2 (evaluated in FP64
+ *   with an a-priori bound on its rounding error, rounded outward to FP32);
+ *   layers 2..n by interval propagation as ld_intermediate_bounds.
+ * Errors: LD_ERR_ARG; LD_ERR_UNSUPPORTED for a one-layer net;
+ * LD_ERR_NONFINITE (via the status word) for a NaN/Inf centre or a negative
+ * or non-finite radius. */
+ld_status ld_intermediate_bounds_ball(ld_net* net, const float* center, const float* eps, int32_t n_props,
+                                      float* lbk, float* ubk, double* out_lb, void* stream);
+
 /* Interval bounds recomputed per subdomain after its splits (the
  * per-subdomain intermediate bounds used by BaBSR, Sec. 5.1.1, with the split
  * semantics of Sec. 2.3.2): for subdomain b, layer 1 is bounded over box
@@ -246,6 +259,26 @@ ld_status ld_bound(ld_net* net, const float* lb0, const float* ub0, const float*
                    const int8_t* split_masks, int32_t B, int32_t n_iters, const ld_opts* opts,
                    const float* rho_in, float* rho_out, float* adam_mv, double* out,
                    void* stream);
+
+/* LD lower bounds over l2-ball input domains (Sec. 3.2.1): as ld_bound with
+ * the box of property p replaced by {x0 : ||x0 - center[p]||_2 <= eps[p]}.
+ * The subproblem P0 becomes min over the ball of -g0^T x0, g0 = W_1^T rho_1,
+ * solved in closed form by x0* = center + eps g0 / ||g0|| (center when
+ * g0 = 0) with value -g0^T center - eps ||g0||; P1..Pn are unchanged.
+ *   center [device] [n_props, n_0] float; eps [device] [n_props] float >= 0;
+ *   lbk, ubk [device] [n_props, N] intermediate bounds valid over the balls
+ *   (e.g. from ld_intermediate_bounds_ball); the other arguments as ld_bound.
+ *   The iterations run on the FP32 layer-wise engine (opts->engine is not
+ *   consulted); out[b] is q(rho_T) in FP64 lowered by an a-priori bound on its
+ *   rounding error, whose ball term -eps ||g0|| takes an upper bound of ||g0||
+ *   (every |g0_i| raised by its error bound, squares and sums and the square
+ *   root rounded up).  The call grows a workspace of its own on first use.
+ * Errors: as ld_bound; LD_ERR_UNSUPPORTED for opts->precision != FP32 or
+ * opts->fp64_final = 0. */
+ld_status ld_bound_ball(ld_net* net, const float* center, const float* eps, const float* lbk,
+                        const float* ubk, int32_t n_props, const int32_t* prop_of_subdomain,
+                        const int8_t* split_masks, int32_t B, int32_t n_iters, const ld_opts* opts,
+                        const float* rho_in, float* rho_out, float* adam_mv, double* out, void* stream);
 
 /* Options of the proximal solver.  Defaults (ld_prox_opts_default): the
  * incomplete-verification setting of Sec. 7.2 -- proximal weights eta

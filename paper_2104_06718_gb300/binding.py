@@ -35,6 +35,7 @@ EXPORTED = [
     "ld_net_profile", "ld_net_profile_read", "ld_launch_count", "ld_net_tuned", "ld_final_bound_noalloc",
     "ld_test_inject_alloc_failure", "ld_intermediate_bounds_propagated", "ld_prox_opts_default", "ld_bound_proximal",
     "ld_branching_scores", "ld_branch", "ld_upper_bound", "ld_bound_dsg", "ld_test_fused_tc_plan",
+    "ld_intermediate_bounds_ball", "ld_bound_ball",
 ]
 PHASES = {"iter": 0, "final": 1, "init": 2, "ibp": 3, "backward": 4}
 
@@ -88,6 +89,8 @@ def load_library(path: str = LIB_PATH):
     lib.ld_intermediate_bounds.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp]
     lib.ld_intermediate_bounds_split.argtypes = [vp, vp, vp, i32, vp, vp, i32, vp, vp, vp]
     lib.ld_bound.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, i32, i32, C.POINTER(Opts), vp, vp, vp, vp, vp]
+    lib.ld_bound_ball.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, i32, i32, C.POINTER(Opts), vp, vp, vp, vp, vp]
+    lib.ld_intermediate_bounds_ball.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp]
     lib.ld_dual_supergradient.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, i32, vp, vp, vp, vp, vp]
     lib.ld_bound_backward.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.ld_selftest_wait_timeout.argtypes = [vp, vp]
@@ -333,6 +336,25 @@ def ld_intermediate_bounds(net: Net, lb0, ub0, want_output_lb: bool = False):
     return (lbk, ubk, out_lb) if want_output_lb else (lbk, ubk)
 
 
+def ld_intermediate_bounds_ball(net: Net, center, eps, want_output_lb: bool = False):
+    """Interval bounds of layers 1..n-1 over l2 balls ||x0 - center[p]|| <=
+    eps[p] (Sec. 3.2.1): layer 1 exact up to outward rounding, the rest by
+    interval propagation; optionally the output's lower bound ([P] float64)."""
+    center = _dev(center, torch.float32)
+    if center.dim() == 1:
+        center = center[None]
+    P = center.shape[0]
+    eps = _dev(eps, torch.float32).reshape(-1)
+    if eps.numel() != P:
+        raise ValueError("eps needs one radius per centre")
+    lbk = torch.empty((P, net.N), dtype=torch.float32, device="cuda")
+    ubk = torch.empty_like(lbk)
+    out_lb = torch.empty(P, dtype=torch.float64, device="cuda") if want_output_lb else None
+    _check(net._lib.ld_intermediate_bounds_ball(net.handle, _ptr(center), _ptr(eps), P, _ptr(lbk), _ptr(ubk),
+                                                _ptr(out_lb), _stream()), "ld_intermediate_bounds_ball")
+    return (lbk, ubk, out_lb) if want_output_lb else (lbk, ubk)
+
+
 def ld_intermediate_bounds_split(net: Net, lb0, ub0, masks, prop=None):
     """Interval bounds recomputed per subdomain after its splits: ([B, N],
     [B, N]) float32, outward rounded and already clamped by the masks.
@@ -406,6 +428,29 @@ def ld_bound(net: Net, lb0, ub0, lbk, ubk, prop=None, masks=None, n_iters: int =
     _check(net._lib.ld_bound(net.handle, _ptr(lb0), _ptr(ub0), _ptr(lbk), _ptr(ubk), lbk.shape[0], _ptr(prop),
                              _ptr(masks), B, int(n_iters), C.byref(oc), _ptr(rho_in), _ptr(rho_out), _ptr(adam_mv),
                              _ptr(out), _stream()), "ld_bound")
+    return (out, rho_out) if return_rho else out
+
+
+def ld_bound_ball(net: Net, center, eps, lbk, ubk, prop=None, masks=None, n_iters: int = 100,
+                  opts: Options | None = None, rho_in=None, B: int | None = None, return_rho: bool = False,
+                  adam_mv=None):
+    """Lower bounds [B] (float64) over l2-ball input domains (Sec. 3.2.1)
+    after n_iters Adam iterations; arguments as ld_bound with the boxes
+    replaced by centres [P, n0] and radii [P]."""
+    center, _, lbk, ubk, prop, masks, B = _problem(center, center, lbk, ubk, prop, masks, B)
+    eps = _dev(eps, torch.float32).reshape(-1)
+    if eps.numel() != center.shape[0]:
+        raise ValueError("eps needs one radius per centre")
+    o = (opts or Options())
+    if rho_in is not None and o.init != "given":
+        o = Options(**{**o.__dict__, "init": "given"})
+    rho_in = None if rho_in is None else _dev(rho_in, torch.float32)
+    out = torch.empty(B, dtype=torch.float64, device="cuda")
+    rho_out = torch.empty((B, net.N), dtype=torch.float32, device="cuda") if return_rho else None
+    oc = o.to_c()
+    _check(net._lib.ld_bound_ball(net.handle, _ptr(center), _ptr(eps), _ptr(lbk), _ptr(ubk), lbk.shape[0],
+                                  _ptr(prop), _ptr(masks), B, int(n_iters), C.byref(oc), _ptr(rho_in),
+                                  _ptr(rho_out), _ptr(adam_mv), _ptr(out), _stream()), "ld_bound_ball")
     return (out, rho_out) if return_rho else out
 
 

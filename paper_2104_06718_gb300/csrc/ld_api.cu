@@ -92,6 +92,10 @@ struct ld_net {
   // workspace of DSG+: lambda and its Adam moments [B, N], the dual value [B]
   void* dsg_ws = nullptr;
   int dsg_B = -1;
+  // final-bound slots of l2-ball problems: the main slots plus one for the
+  // -eps ||g_0|| term, then the scratch slots of the ball pass [B, ..., 3]
+  double* ball_ws = nullptr;
+  int ball_B = -1;
   // the per-iteration launches of the layerwise and BF16 engines, captured
   // into one executable graph (re-captured and updated in place each call)
   bool graphs = true;
@@ -324,6 +328,8 @@ void sweep(ld_net* net, const Problem& P, int mode, const ld_opts& o, ld::AdamSt
       ld::launch_top_argmin(layer(net, n), P, ea, s);
     else
       ld::launch_transposed_argmin(layer(net, k + 1), nullptr, P, net->rho, ea, s);
+    // l2 ball: the epilogue left g_0 in x; x0 from its norm (Sec. 3.2.1)
+    if (k == 0 && P.ball_eps) ld::launch_ball_project(P, net->x, s);
     if (mode == 2) continue;
     const LayerDev& Lk1 = layer(net, k + 1);
     if (mode == 0) {
@@ -707,18 +713,53 @@ int n_final_slots(const ld_net* net) {
   return n;
 }
 
+// Slots of the final pass of layer 1 (the P0 terms).
+int p0_slots(const ld_net* net) { return ld::final_slots(layer(net, 1), net->n == 1 ? 1 : 0); }
+
+// With an l2-ball input domain (P.ball_eps) the P0 terms are -g_0^T c (the box
+// pass with l0 = u0 = c) and one more slot holds -eps ||g_0||, bounded from a
+// second final pass of layer 1 in ball-norm mode; the slots then live in
+// net->ball_ws (ensure_ball_ws).
 void final_fp64(ld_net* net, const Problem& P, double* out, cudaStream_t s) {
   const int n = net->n;
-  ld::FinalAcc acc{net->acc, n_final_slots(net), 0};
+  const int nfs = n_final_slots(net);
+  const bool ball = P.ball_eps != nullptr;
+  ld::FinalAcc acc{ball ? net->ball_ws : net->acc, nfs + (ball ? 1 : 0), 0};
   for (int k = n - 1; k >= 0; --k) {
     ld::launch_final_layer(layer(net, k + 1), k, r_off(net, k), x_off(net, k), P, net->rho, k == n - 1 ? 1 : 0, acc,
                            s);
     acc.slot += ld::final_slots(layer(net, k + 1), k == n - 1);
   }
   ld::launch_final_bias(net->L, P, net->rho, acc, s);
-  const double M = (double)(net->n0 + 2 * net->N + 1);
+  if (ball) {
+    ld::FinalAcc scratch{net->ball_ws + (size_t)P.B * (nfs + 1) * 3, p0_slots(net), 0};
+    ld::launch_final_layer(layer(net, 1), 0, r_off(net, 0), x_off(net, 0), P, net->rho, n == 1 ? 1 : 0, scratch, s,
+                           1);
+    ld::launch_final_ball(P, scratch, acc, nfs, s);
+  }
+  const double M = (double)(net->n0 + 2 * net->N + 1 + (ball ? 1 : 0));
   const double gM = ld::final_gamma(M);
   ld::launch_final_combine_bn(P, acc, net->bn, net->bn_err, gM, 1.0 + 2.0 * gM, out, s);
+}
+
+// Final-bound slots of l2-ball problems for B subdomains.
+ld_status ensure_ball_ws(ld_net* net, int B) {
+  if (B <= net->ball_B) return LD_OK;
+  const size_t Bn = (size_t)(B > 0 ? B : 1);
+  const size_t bytes = 8 * 3 * Bn * (size_t)(n_final_slots(net) + 1 + p0_slots(net));
+  cudaDeviceSynchronize();
+  if (net->ball_ws) cudaFree(net->ball_ws);
+  net->ball_ws = nullptr;
+  net->ball_B = -1;
+  void* p = nullptr;
+  const cudaError_t e = ld::dev_malloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_status(e);
+  }
+  net->ball_ws = static_cast<double*>(p);
+  net->ball_B = (int)Bn;
+  return LD_OK;
 }
 
 // q in FP32 terms (FP64 sum) via the forward form, +inf for empty subdomains.
@@ -975,6 +1016,7 @@ ld_status ld_net_destroy(ld_net* net) {
   if (net->dsg_ws) cudaFree(net->dsg_ws);
   ld::free_tc_net(&net->tc);
   if (net->ftc_mem) cudaFree(net->ftc_mem);
+  if (net->ball_ws) cudaFree(net->ball_ws);
   if (net->d_W) cudaFree(net->d_W);
   if (net->d_Wx) cudaFree(net->d_Wx);
   if (net->d_b) cudaFree(net->d_b);
@@ -1025,6 +1067,28 @@ ld_status ld_intermediate_bounds(ld_net* net, const float* lb0, const float* ub0
     if (last && !out_lb) break;
     ld::launch_ibp_layer(L, k == 1, last, n_props, lin, uin, in_stride, last ? nullptr : lbk + L.r_out_off,
                          last ? nullptr : ubk + L.r_out_off, (int)net->N, out_lb, net->d_status, s);
+  }
+  return last_error();
+}
+
+ld_status ld_intermediate_bounds_ball(ld_net* net, const float* center, const float* eps, int32_t n_props,
+                                      float* lbk, float* ubk, double* out_lb, void* stream) {
+  if (!net || !center || !eps || !lbk || !ubk || n_props < 1) return LD_ERR_ARG;
+  cudaStream_t s = S(stream);
+  const int n = net->n;
+  if (n < 2) return LD_ERR_UNSUPPORTED;
+  PhaseMark pm(net, LD_PHASE_IBP, s);
+  // layer 1: exact range over the ball, rounded outward; then interval propagation
+  const LayerDev& L1 = layer(net, 1);
+  ld::launch_ball_first_layer(L1, n_props, center, eps, lbk + L1.r_out_off, ubk + L1.r_out_off, (int)net->N,
+                              net->d_status, s);
+  for (int k = 2; k <= n; ++k) {
+    const LayerDev& L = layer(net, k);
+    const bool last = k == n;
+    if (last && !out_lb) break;
+    ld::launch_ibp_layer(L, 0, last, n_props, lbk + r_off(net, k - 1), ubk + r_off(net, k - 1), (int)net->N,
+                         last ? nullptr : lbk + L.r_out_off, last ? nullptr : ubk + L.r_out_off, (int)net->N, out_lb,
+                         net->d_status, s);
   }
   return last_error();
 }
@@ -1532,10 +1596,13 @@ ld_status ld_upper_bound(ld_net* net, const float* lb0, const float* ub0, const 
   return last_error();
 }
 
-ld_status ld_bound(ld_net* net, const float* lb0, const float* ub0, const float* lbk, const float* ubk,
-                   int32_t n_props, const int32_t* prop, const int8_t* masks, int32_t B, int32_t n_iters,
-                   const ld_opts* opts, const float* rho_in, float* rho_out, float* adam_mv, double* out,
-                   void* stream) {
+// ld_bound over boxes (ball_eps == nullptr) or over l2 balls centred at lb0
+// (= ub0) with radii ball_eps [n_props] (Sec. 3.2.1; FP32 layer-wise
+// iterations, FP64 final bound).
+static ld_status bound_impl(ld_net* net, const float* lb0, const float* ub0, const float* ball_eps,
+                            const float* lbk, const float* ubk, int32_t n_props, const int32_t* prop,
+                            const int8_t* masks, int32_t B, int32_t n_iters, const ld_opts* opts,
+                            const float* rho_in, float* rho_out, float* adam_mv, double* out, void* stream) {
   ld_status st = check_problem(net, lb0, ub0, lbk, ubk, n_props, B);
   if (st != LD_OK) return st;
   if (n_iters < 0 || (!out && B > 0)) return LD_ERR_ARG;
@@ -1545,13 +1612,15 @@ ld_status ld_bound(ld_net* net, const float* lb0, const float* ub0, const float*
   if (o.init == LD_INIT_GIVEN && !rho_in && B > 0) return LD_ERR_ARG;
   if (B == 0) return LD_OK;
   if ((st = ensure_ws(net, B)) != LD_OK) return st;
+  if (ball_eps && (st = ensure_ball_ws(net, B)) != LD_OK) return st;
   cudaStream_t s = S(stream);
-  const Problem P = make_problem(net, lb0, ub0, lbk, ubk, n_props, prop, masks, B);
+  Problem P = make_problem(net, lb0, ub0, lbk, ubk, n_props, prop, masks, B);
+  P.ball_eps = ball_eps;
   const size_t BN = (size_t)B * net->N;
   const bool bf16 = o.precision == LD_PREC_BF16 && n_iters > 0;
   if (bf16 && (st = ensure_tc(net, B, n_props)) != LD_OK) return st;
   if (bf16 && (st = ensure_fused_tc(net)) != LD_OK && st != LD_ERR_UNSUPPORTED) return st;
-  const std::pair<int, int> eng = n_iters <= 0 ? std::make_pair((int)LD_ENGINE_LAYERWISE, 0)
+  const std::pair<int, int> eng = (n_iters <= 0 || ball_eps) ? std::make_pair((int)LD_ENGINE_LAYERWISE, 0)
                                   : bf16       ? choose_engine_bf16(net, P, o, n_iters, s)
                                                : choose_engine(net, P, o, n_iters, s);
   // The CROWN start must come from the same transposed-pass arithmetic as the
@@ -1606,6 +1675,26 @@ ld_status ld_bound(ld_net* net, const float* lb0, const float* ub0, const float*
     cudaMemcpyAsync(adam_mv + BN, net->v, sizeof(float) * BN, cudaMemcpyDeviceToDevice, s);
   }
   return last_error();
+}
+
+ld_status ld_bound(ld_net* net, const float* lb0, const float* ub0, const float* lbk, const float* ubk,
+                   int32_t n_props, const int32_t* prop, const int8_t* masks, int32_t B, int32_t n_iters,
+                   const ld_opts* opts, const float* rho_in, float* rho_out, float* adam_mv, double* out,
+                   void* stream) {
+  return bound_impl(net, lb0, ub0, nullptr, lbk, ubk, n_props, prop, masks, B, n_iters, opts, rho_in, rho_out,
+                    adam_mv, out, stream);
+}
+
+ld_status ld_bound_ball(ld_net* net, const float* center, const float* eps, const float* lbk, const float* ubk,
+                        int32_t n_props, const int32_t* prop, const int8_t* masks, int32_t B, int32_t n_iters,
+                        const ld_opts* opts, const float* rho_in, float* rho_out, float* adam_mv, double* out,
+                        void* stream) {
+  if (!center || !eps) return LD_ERR_ARG;
+  ld_opts o;
+  if (opts) o = *opts; else ld_opts_default(&o);
+  if (o.precision != LD_PREC_FP32 || !o.fp64_final) return LD_ERR_UNSUPPORTED;
+  return bound_impl(net, center, center, eps, lbk, ubk, n_props, prop, masks, B, n_iters, &o, rho_in, rho_out,
+                    adam_mv, out, stream);
 }
 
 ld_status ld_dual_supergradient(ld_net* net, const float* lb0, const float* ub0, const float* lbk, const float* ubk,

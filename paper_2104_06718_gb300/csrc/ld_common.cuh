@@ -53,6 +53,9 @@ struct Problem {
   int* splitk_count;             // per output tile: partials that have arrived
   int splitk_part_cap;           // floats available in splitk_part
   int splitk_count_cap;          // ints available in splitk_count
+  // l2-ball input domains (Sec. 3.2.1): radius per property [P], the centre
+  // in l0 (= u0); nullptr: the box [l0, u0]
+  const float* ball_eps = nullptr;
 };
 
 // Property of subdomain b; an out-of-range index is clamped here (so no
@@ -132,6 +135,12 @@ struct EpiArgmin {
   __device__ __forceinline__ void operator()(int b, int i, float g) const {
     if (g_out) g_out[(size_t)b * P.XS + x_off + i] = g;
     if (layer == 0) {
+      if (P.ball_eps) {
+        // l2 ball: x0 depends on all of g_0 (its norm); keep g_0 here for
+        // the projection kernel (launch_ball_project)
+        x[(size_t)b * P.XS + i] = g;
+        return;
+      }
       const int p = prop_of(P, b);
       // P0 (Eq. box_bounds_sol): minimise -g_0^T x0, i.e. x0 = u0 where g_0 >= 0
       const float v = (g >= 0.f) ? P.u0[(size_t)p * P.n0 + i] : P.l0[(size_t)p * P.n0 + i];
@@ -700,8 +709,21 @@ struct FinalAcc {
 };
 int final_slots(const LayerDev& Lnext, int top);
 void launch_record_finish(const Problem& P, const double* q, double* out, cudaStream_t s);
+// l2-ball input domains (Sec. 3.2.1, ld_ball.cu).
+// P0 over the ball: x0 = c + eps g_0 / ||g_0|| per subdomain, from g_0 left in
+// x[b, 0..n0) by the layer-0 transposed epilogue (EpiArgmin).
+void launch_ball_project(const Problem& P, float* x, cudaStream_t s);
+// Interval bounds of layer 1 over the balls, rounded outward to FP32.
+void launch_ball_first_layer(const LayerDev& L1, int n_props, const float* center, const float* eps, float* lout,
+                             float* uout, int out_stride, int* status, cudaStream_t s);
+// The -eps ||g_0|| term of the FP64 final bound: from the slot sums of
+// (|g_0[i]| + delta_i)^2 in `scratch` (a final pass of layer 1 in ball mode),
+// -eps * sqrt(sum) rounded down, written to slot `slot` of `main`.
+void launch_final_ball(const Problem& P, FinalAcc scratch, FinalAcc main, int slot, cudaStream_t s);
+// ball_norm (layer 0 of an l2-ball problem): the terms are upper bounds on
+// g_0[i]^2 (their slot sums, rounded up, bound ||g_0||^2) instead of P0 minima.
 void launch_final_layer(const LayerDev& Lnext, int layer, int r_off, int x_off, const Problem& P,
-                        const float* rho, int top, FinalAcc acc, cudaStream_t s);
+                        const float* rho, int top, FinalAcc acc, cudaStream_t s, int ball_norm = 0);
 void launch_final_bias(const std::vector<LayerDev>& Ls, const Problem& P, const float* rho, FinalAcc acc,
                        cudaStream_t s);
 void launch_final_combine_bn(const Problem& P, FinalAcc acc, double bn, double bn_err, double gamma_M,

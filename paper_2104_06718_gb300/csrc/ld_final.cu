@@ -55,12 +55,23 @@ struct FinalEpi {
   int r_off;
   const float* rho;
   double gamma_K;
+  int ball_norm;       // layer 0, l2 ball: the term is an upper bound on g_0[i]^2 (for ||g_0||)
   __device__ __forceinline__ void term(int b, int i, double g, float abs_sum, double& t, double& e) const {
     term_delta(b, i, g, __dmul_ru(gamma_K, (double)abs_sum), t, e);
   }
   // delta: bound on |g - exact g|
   __device__ __forceinline__ void term_delta(int b, int i, double g, double delta, double& t, double& e) const {
     if (layer == 0) {
+      if (ball_norm) {
+        // |exact g_0[i]| <= |g| + delta: its square, rounded up
+        const double a = __dadd_ru(fabs(g), delta);
+        t = __dmul_ru(a, a);
+        e = 0.0;
+        return;
+      }
+      // the box; over an l2 ball l0 = u0 = the centre, which gives the
+      // -g_0^T c part of the ball's minimum (the -eps ||g_0|| part is added
+      // by the ball pass)
       const int p = prop_of(P, b);
       final_term(true, 0.0, g, delta, (double)P.l0[(size_t)p * P.n0 + i], (double)P.u0[(size_t)p * P.n0 + i], t, e);
       return;
@@ -461,9 +472,9 @@ int sm_count() {
 }
 
 void launch_final_layer(const LayerDev& Lnext, int layer, int r_off, int x_off, const Problem& P,
-                        const float* rho, int top, FinalAcc acc, cudaStream_t s) {
+                        const float* rho, int top, FinalAcc acc, cudaStream_t s, int ball_norm) {
   (void)x_off;
-  FinalEpi epi{P, layer, r_off, rho, gamma_of((double)Lnext.fan_t)};
+  FinalEpi epi{P, layer, r_off, rho, gamma_of((double)Lnext.fan_t), ball_norm};
   if (P.B == 0) return;
   count_launch();
   if (top) {

@@ -308,7 +308,8 @@ __global__ void empty_kernel(Problem P, int8_t* empty, int* status) {
   if (threadIdx.x == 0) empty[b] = (int8_t)(bad ? 1 : 0);
 }
 
-// Boxes must be finite with l0 <= u0; bounds must not be NaN.
+// Boxes must be finite with l0 <= u0, ball radii finite and >= 0; bounds
+// must not be NaN.
 __global__ void box_check_kernel(Problem P, int* status) {
   const size_t total = (size_t)P.n_props * P.n0;
   int bad = 0;
@@ -320,6 +321,9 @@ __global__ void box_check_kernel(Problem P, int* status) {
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < totk; e += (size_t)gridDim.x * blockDim.x) {
     if (isnan(P.lbk[e]) || isnan(P.ubk[e])) bad = 1;
   }
+  if (P.ball_eps)  // l2-ball radii: finite and >= 0
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P.n_props; p += gridDim.x * blockDim.x)
+      if (!(isfinite(P.ball_eps[p]) && P.ball_eps[p] >= 0.f)) bad = 1;
   if (bad) atomicCAS(status, 0, (int)LD_ERR_NONFINITE);
 }
 

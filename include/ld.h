@@ -260,6 +260,25 @@ ld_status ld_bound(ld_net* net, const float* lb0, const float* ub0, const float*
                    const float* rho_in, float* rho_out, float* adam_mv, double* out,
                    void* stream);
 
+/* ld_bound with the dual value of every iterate recorded (Algorithm 1
+ * evaluates q(rho_t) at each step before its update).
+ *   q_trace [device] [n_iters, B] double: row t = q(rho_t), t = 0..n_iters-1,
+ *   the sum of the per-subproblem minima in FP32 terms summed in FP64 (a
+ *   diagnostic of the ascent, not rounded outward: the returned bound is
+ *   out, as ld_bound); +inf for an empty subdomain.  NULL only when
+ *   n_iters = 0 or B = 0.
+ *   Other arguments as ld_bound.  The iterations run on the FP32 layer-wise
+ *   engine (opts->engine is not consulted) with one extra evaluation sweep per
+ *   iteration; rho_T, the Adam moments and out are those of ld_bound on the
+ *   layer-wise engine (the evaluation writes none of the iteration's state).
+ * Errors: as ld_bound; LD_ERR_ARG for a NULL q_trace with n_iters, B > 0;
+ * LD_ERR_UNSUPPORTED for opts->precision != FP32. */
+ld_status ld_bound_trace(ld_net* net, const float* lb0, const float* ub0, const float* lbk,
+                         const float* ubk, int32_t n_props, const int32_t* prop_of_subdomain,
+                         const int8_t* split_masks, int32_t B, int32_t n_iters, const ld_opts* opts,
+                         const float* rho_in, float* rho_out, float* adam_mv, double* out, double* q_trace,
+                         void* stream);
+
 /* LD lower bounds over l2-ball input domains (Sec. 3.2.1): as ld_bound with
  * the box of property p replaced by {x0 : ||x0 - center[p]||_2 <= eps[p]}.
  * The subproblem P0 becomes min over the ball of -g0^T x0, g0 = W_1^T rho_1,

@@ -35,7 +35,7 @@ EXPORTED = [
     "ld_net_profile", "ld_net_profile_read", "ld_launch_count", "ld_net_tuned", "ld_final_bound_noalloc",
     "ld_test_inject_alloc_failure", "ld_intermediate_bounds_propagated", "ld_prox_opts_default", "ld_bound_proximal",
     "ld_branching_scores", "ld_branch", "ld_upper_bound", "ld_bound_dsg", "ld_test_fused_tc_plan",
-    "ld_intermediate_bounds_ball", "ld_bound_ball",
+    "ld_intermediate_bounds_ball", "ld_bound_ball", "ld_bound_trace",
 ]
 PHASES = {"iter": 0, "final": 1, "init": 2, "ibp": 3, "backward": 4}
 
@@ -89,6 +89,8 @@ def load_library(path: str = LIB_PATH):
     lib.ld_intermediate_bounds.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp]
     lib.ld_intermediate_bounds_split.argtypes = [vp, vp, vp, i32, vp, vp, i32, vp, vp, vp]
     lib.ld_bound.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, i32, i32, C.POINTER(Opts), vp, vp, vp, vp, vp]
+    lib.ld_bound_trace.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, i32, i32, C.POINTER(Opts), vp, vp, vp, vp, vp,
+                                   vp]
     lib.ld_bound_ball.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, i32, i32, C.POINTER(Opts), vp, vp, vp, vp, vp]
     lib.ld_intermediate_bounds_ball.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp]
     lib.ld_dual_supergradient.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, i32, vp, vp, vp, vp, vp]
@@ -429,6 +431,24 @@ def ld_bound(net: Net, lb0, ub0, lbk, ubk, prop=None, masks=None, n_iters: int =
                              _ptr(masks), B, int(n_iters), C.byref(oc), _ptr(rho_in), _ptr(rho_out), _ptr(adam_mv),
                              _ptr(out), _stream()), "ld_bound")
     return (out, rho_out) if return_rho else out
+
+
+def ld_bound_trace(net: Net, lb0, ub0, lbk, ubk, prop=None, masks=None, n_iters: int = 100,
+                   opts: Options | None = None, rho_in=None, B: int | None = None, adam_mv=None):
+    """(bounds [B] float64, q trace [n_iters, B] float64): ld_bound on the
+    FP32 layer-wise engine with q(rho_t) recorded before every update."""
+    lb0, ub0, lbk, ubk, prop, masks, B = _problem(lb0, ub0, lbk, ubk, prop, masks, B)
+    o = (opts or Options())
+    if rho_in is not None and o.init != "given":
+        o = Options(**{**o.__dict__, "init": "given"})
+    rho_in = None if rho_in is None else _dev(rho_in, torch.float32)
+    out = torch.empty(B, dtype=torch.float64, device="cuda")
+    trace = torch.empty((int(n_iters), B), dtype=torch.float64, device="cuda")
+    oc = o.to_c()
+    _check(net._lib.ld_bound_trace(net.handle, _ptr(lb0), _ptr(ub0), _ptr(lbk), _ptr(ubk), lbk.shape[0], _ptr(prop),
+                                   _ptr(masks), B, int(n_iters), C.byref(oc), _ptr(rho_in), None, _ptr(adam_mv),
+                                   _ptr(out), _ptr(trace) if trace.numel() else None, _stream()), "ld_bound_trace")
+    return out, trace
 
 
 def ld_bound_ball(net: Net, center, eps, lbk, ubk, prop=None, masks=None, n_iters: int = 100,

@@ -772,6 +772,21 @@ void final_fp32(ld_net* net, const Problem& P, double* out, float* sg, int8_t* v
   if (out) ld::launch_record_finish(P, net->acc, out, s);
 }
 
+// T iterations of the FP32 layer-wise engine with q(rho_t) recorded before
+// every update (Algorithm 1 evaluates q at each iterate): row t of q_trace
+// [T, B].  The evaluation sweep writes only the argmins (which every sweep
+// recomputes from rho) and its own accumulator, so rho_T, m and v are the
+// same as without the trace.
+ld_status run_iterations_traced(ld_net* net, const Problem& P, const ld_opts& o, int n_iters, double* q_trace,
+                                cudaStream_t s) {
+  const int T_sched = o.t_total > 0 ? o.t_total : o.t_offset + n_iters;
+  for (int t = 0; t < n_iters; ++t) {
+    final_fp32(net, P, q_trace + (size_t)t * P.B, nullptr, nullptr, s);
+    sweep(net, P, 0, o, adam_step(o, o.t_offset + t, T_sched), nullptr, nullptr, nullptr, nullptr, s);
+  }
+  return last_error();
+}
+
 }  // namespace
 
 extern "C" {
@@ -1602,7 +1617,8 @@ ld_status ld_upper_bound(ld_net* net, const float* lb0, const float* ub0, const 
 static ld_status bound_impl(ld_net* net, const float* lb0, const float* ub0, const float* ball_eps,
                             const float* lbk, const float* ubk, int32_t n_props, const int32_t* prop,
                             const int8_t* masks, int32_t B, int32_t n_iters, const ld_opts* opts,
-                            const float* rho_in, float* rho_out, float* adam_mv, double* out, void* stream) {
+                            const float* rho_in, float* rho_out, float* adam_mv, double* out, double* q_trace,
+                            void* stream) {
   ld_status st = check_problem(net, lb0, ub0, lbk, ubk, n_props, B);
   if (st != LD_OK) return st;
   if (n_iters < 0 || (!out && B > 0)) return LD_ERR_ARG;
@@ -1620,7 +1636,7 @@ static ld_status bound_impl(ld_net* net, const float* lb0, const float* ub0, con
   const bool bf16 = o.precision == LD_PREC_BF16 && n_iters > 0;
   if (bf16 && (st = ensure_tc(net, B, n_props)) != LD_OK) return st;
   if (bf16 && (st = ensure_fused_tc(net)) != LD_OK && st != LD_ERR_UNSUPPORTED) return st;
-  const std::pair<int, int> eng = (n_iters <= 0 || ball_eps) ? std::make_pair((int)LD_ENGINE_LAYERWISE, 0)
+  const std::pair<int, int> eng = (n_iters <= 0 || ball_eps || q_trace) ? std::make_pair((int)LD_ENGINE_LAYERWISE, 0)
                                   : bf16       ? choose_engine_bf16(net, P, o, n_iters, s)
                                                : choose_engine(net, P, o, n_iters, s);
   // The CROWN start must come from the same transposed-pass arithmetic as the
@@ -1650,7 +1666,9 @@ static ld_status bound_impl(ld_net* net, const float* lb0, const float* ub0, con
   }
   if (n_iters > 0) {
     PhaseMark pm(net, LD_PHASE_ITER, s);
-    if (bf16 && eng.first == LD_ENGINE_FUSED)
+    if (q_trace)
+      st = run_graphed(net, s, [&](cudaStream_t cs) { return run_iterations_traced(net, P, o, n_iters, q_trace, cs); });
+    else if (bf16 && eng.first == LD_ENGINE_FUSED)
       st = run_iterations_fused_tc(net, P, o, n_iters, eng.second, s, crown_in_kernel);
     else if (bf16)
       st = run_graphed(net, s, [&](cudaStream_t cs) {
@@ -1682,7 +1700,19 @@ ld_status ld_bound(ld_net* net, const float* lb0, const float* ub0, const float*
                    const ld_opts* opts, const float* rho_in, float* rho_out, float* adam_mv, double* out,
                    void* stream) {
   return bound_impl(net, lb0, ub0, nullptr, lbk, ubk, n_props, prop, masks, B, n_iters, opts, rho_in, rho_out,
-                    adam_mv, out, stream);
+                    adam_mv, out, nullptr, stream);
+}
+
+ld_status ld_bound_trace(ld_net* net, const float* lb0, const float* ub0, const float* lbk, const float* ubk,
+                         int32_t n_props, const int32_t* prop, const int8_t* masks, int32_t B, int32_t n_iters,
+                         const ld_opts* opts, const float* rho_in, float* rho_out, float* adam_mv, double* out,
+                         double* q_trace, void* stream) {
+  if (!q_trace && B > 0 && n_iters > 0) return LD_ERR_ARG;
+  ld_opts o;
+  if (opts) o = *opts; else ld_opts_default(&o);
+  if (o.precision != LD_PREC_FP32) return LD_ERR_UNSUPPORTED;
+  return bound_impl(net, lb0, ub0, nullptr, lbk, ubk, n_props, prop, masks, B, n_iters, &o, rho_in, rho_out,
+                    adam_mv, out, n_iters > 0 ? q_trace : nullptr, stream);
 }
 
 ld_status ld_bound_ball(ld_net* net, const float* center, const float* eps, const float* lbk, const float* ubk,
@@ -1694,7 +1724,7 @@ ld_status ld_bound_ball(ld_net* net, const float* center, const float* eps, cons
   if (opts) o = *opts; else ld_opts_default(&o);
   if (o.precision != LD_PREC_FP32 || !o.fp64_final) return LD_ERR_UNSUPPORTED;
   return bound_impl(net, center, center, eps, lbk, ubk, n_props, prop, masks, B, n_iters, &o, rho_in, rho_out,
-                    adam_mv, out, stream);
+                    adam_mv, out, nullptr, stream);
 }
 
 ld_status ld_dual_supergradient(ld_net* net, const float* lb0, const float* ub0, const float* lbk, const float* ubk,

@@ -5,7 +5,8 @@ rounding, then interval propagation) and ld_bound_ball (the LD dual with P0
 minimised over the ball: x0* = c + eps g0/||g0||, value -g0.c - eps||g0||)
 against the FP64 oracle (oracle.l2 and oracle.ld_bound with ball_eps):
 
-  * interval bounds: contain the oracle's exact ones, within 1e-5 of them
+  * interval bounds: contain the oracle's exact ones; layer 1 within 1e-6,
+    the propagated layers within the 1e-4 of the box interval tests
   * short runs (T = 1, 3): within 1e-5 of the oracle (FP32 iterations)
   * long runs (T = 100): the FP32 chaos floor of the box tests
   * the FP64 final bound at the returned rho: at or below the oracle's q at
@@ -96,9 +97,13 @@ def test_intermediate_bounds_contain_the_exact_ones(name, eps):
     el, eu = flat(on, lb)[0], flat(on, ub)[0]
     scale = np.maximum(np.maximum(np.abs(el), np.abs(eu)), 1.0)
     assert np.all(lbk <= el + 1e-12 * scale) and np.all(ubk >= eu - 1e-12 * scale)
-    assert np.max(rel(lbk, el)) < 1e-5 and np.max(rel(ubk, eu)) < 1e-5
+    # layer 1: FP64 up to one outward FP32 rounding; above it the outward FP32
+    # interval propagation of the box tests (same 1e-4)
+    n1 = on.L(1).n_out
+    assert np.max(rel(lbk[:n1], el[:n1])) < 1e-6 and np.max(rel(ubk[:n1], eu[:n1])) < 1e-6
+    assert np.max(rel(lbk, el)) < 1e-4 and np.max(rel(ubk, eu)) < 1e-4
     assert out_lb.item() <= lb[on.n][0, 0] + 1e-9 * max(1.0, abs(lb[on.n][0, 0]))
-    assert rel(out_lb.item(), lb[on.n][0, 0]) < 1e-5
+    assert rel(out_lb.item(), lb[on.n][0, 0]) < 1e-4
 
 
 def test_intermediate_bounds_on_a_fully_connected_first_layer():
@@ -114,7 +119,9 @@ def test_intermediate_bounds_on_a_fully_connected_first_layer():
     g, h = lbk.cpu().numpy().astype(np.float64), ubk.cpu().numpy().astype(np.float64)
     scale = np.maximum(np.maximum(np.abs(el), np.abs(eu)), 1.0)
     assert np.all(g <= el + 1e-12 * scale) and np.all(h >= eu - 1e-12 * scale)
-    assert np.max(rel(g, el)) < 1e-5 and np.max(rel(h, eu)) < 1e-5
+    n1 = on.L(1).n_out
+    assert np.max(rel(g[:, :n1], el[:, :n1])) < 1e-6 and np.max(rel(h[:, :n1], eu[:, :n1])) < 1e-6
+    assert np.max(rel(g, el)) < 1e-4 and np.max(rel(h, eu)) < 1e-4
 
 
 @pytest.mark.parametrize("name", ["base", "deep"])

@@ -248,6 +248,12 @@ def make_workload(name, rank, B=0, T=0):
                 depth=depth, rank=rank)
 
 
+def ball_centre(wl):
+    """Centre of the l2-ball variant of a workload: the midpoint of its box,
+    [1, n0] float32 (the same array on both sides)."""
+    return ((wl["l0"].astype(np.float64) + wl["u0"].astype(np.float64)) / 2).astype(np.float32)
+
+
 def workload_config(wl, N, world, precision):
     """The `config` object of a bench line (both arms)."""
     net = "Tiny MLP 10-20-20-1" if wl["net"] == "tiny" else f"{wl['net']} convnet"
@@ -283,7 +289,11 @@ def oracle_problem(wl):
         layers.append(oracle.Layer("conv", W, b, in_shape=s.in_shape, stride=s.stride, pad=s.pad)
                       if s.kind == "conv" else oracle.Layer("fc", W, b))
     on = oracle.Net(layers)
-    lb, ub = oracle.ibp_bounds(on, wl["l0"].astype(np.float64), wl["u0"].astype(np.float64))
+    if wl.get("ball_eps") is not None:
+        from oracle import l2
+        lb, ub = l2.ball_ibp_bounds(on, ball_centre(wl).astype(np.float64), np.array([wl["ball_eps"]], np.float64))
+    else:
+        lb, ub = oracle.ibp_bounds(on, wl["l0"].astype(np.float64), wl["u0"].astype(np.float64))
     lbk, ubk = _outward_f32(np.concatenate([lb[k] for k in range(1, on.n)], axis=1),
                             np.concatenate([ub[k] for k in range(1, on.n)], axis=1))
     amb = np.nonzero((lbk[0] < 0) & (ubk[0] > 0))[0]
@@ -293,6 +303,11 @@ def oracle_problem(wl):
 
 def oracle_run(on, wl, lbk, ubk, masks):
     import oracle
+    if wl.get("ball_eps") is not None:
+        c = ball_centre(wl).astype(np.float64)
+        out, _, _ = oracle.ld_bound(on, c, c, lbk.astype(np.float64), ubk.astype(np.float64), None, masks, wl["T"],
+                                    ball_eps=np.array([wl["ball_eps"]], np.float64))
+        return out
     out, _, _ = oracle.ld_bound(on, wl["l0"].astype(np.float64), wl["u0"].astype(np.float64), lbk.astype(np.float64),
                                 ubk.astype(np.float64), None, masks, wl["T"])
     return out
@@ -311,7 +326,8 @@ def cpu_leg(wl, budget_s, run_gpu=None):
     ref = oracle_run(on, wl, lbk, ubk, masks[:n])
     dt = time.perf_counter() - t0
     cpu = {"value": n / dt, "unit": "bounds/s", "cores": os.cpu_count(), "kind": "oracle",
-           "sample": f"first {n} of {wl['B']} subdomains of the {wl['name']} workload, T={wl['T']}, FP64 "
+           "sample": f"first {n} of {wl['B']} subdomains of the {wl['name']} workload"
+                     f"{' over the l2 ball' if wl.get('ball_eps') is not None else ''}, T={wl['T']}, FP64 "
                      f"NumPy/SciPy (dense BLAS may use all {os.cpu_count()} cores; sparse conv products are "
                      "single-threaded)"}
     gaps = None
@@ -579,6 +595,40 @@ def measure_solvers(bn, args):
     return res
 
 
+def measure_ball(bn, args, eps=0.1):
+    """The Base workload over an l2 ball (Sec. 3.2.1) instead of the box:
+    radius eps around the box centre, interval bounds over the ball, 256
+    subdomains, T = 100, FP32 layer-wise iterations and the FP64 final bound
+    (ld_bound_ball); time per call, bounds/s, and, in the CPU leg, the gap to
+    the FP64 oracle on its own inputs."""
+    torch, ldb = bn.torch, bn.ldb
+    from paper_2104_06718_gb300 import synth
+    d = bn.setup("base")
+    net, wl = d["net"], dict(d["wl"], ball_eps=eps)
+    c = torch.as_tensor(ball_centre(wl), device=bn.dev)
+    e = torch.tensor([eps], dtype=torch.float32, device=bn.dev)
+    lbk, ubk = ldb.ld_intermediate_bounds_ball(net, c, e)
+    lb_h, ub_h = lbk.cpu().numpy(), ubk.cpu().numpy()
+    amb = np.nonzero((lb_h[0] < 0) & (ub_h[0] > 0))[0]
+    masks = torch.as_tensor(synth.split_masks(net.N, wl["B"], amb, wl["depth"], block=bn.rank), device=bn.dev)
+    fn = lambda: ldb.ld_bound_ball(net, c, e, lbk, ubk, None, masks, n_iters=wl["T"])
+    times, win = bn.timed(fn, 5, 2)
+    ms = statistics.median(times)
+    out = fn().cpu().numpy()
+    res = {"subdomains": wl["B"], "iterations": wl["T"], "radius": eps, "ms_per_call": ms,
+           "bounds_per_s": wl["B"] / (ms / 1000.0), "clocks": bn.sampler.window(*win),
+           "ambiguous_relus_root": int(amb.size), "mean_bound": float(out[np.isfinite(out)].mean()),
+           "engine": "FP32 layer-wise passes (the ball's P0 needs the norm of the whole g0)"}
+    if not args.no_cpu_baseline:
+        def run(lbk_o, ubk_o, masks_o):
+            got = ldb.ld_bound_ball(net, c, e, torch.as_tensor(lbk_o, device=bn.dev),
+                                    torch.as_tensor(ubk_o, device=bn.dev), None,
+                                    torch.as_tensor(masks_o, device=bn.dev), n_iters=wl["T"])
+            return {"fp32": got.cpu().numpy()}
+        res["cpu_baseline"], res["gap_vs_fp64_oracle"] = cpu_leg(wl, 3.0, run)
+    return res
+
+
 def measure_branching(bn, args):
     """Branching decisions for the 256 Base subdomains (SR, mSR, FSB: time per
     call) and one batched branch and bound run on a Base property (CROWN/WK
@@ -719,6 +769,7 @@ def run_ours(args):
         configs["intermediate_bounds_base256"] = measure_ib(bn, args)
         configs["solvers_base256"] = measure_solvers(bn, args)
         configs["branching_base256"] = measure_branching(bn, args)
+        configs["l2_ball_base256"] = measure_ball(bn, args)
     bn.sampler.stop()
     if rank != 0:
         if world > 1:

@@ -3,9 +3,10 @@
 Algorithm 1 evaluates q(rho_t) at every iterate before its update; the
 trace [T, B] records it.  Against the FP64 oracle's own trace (AdamResult
 .q_trace): after 1-3 steps within 1e-5, along 100 steps within the FP32
-floor of the long-run tests; row 0 equals the bound at the start; the
-returned bounds are bitwise those of ld_bound on the layer-wise engine (the
-evaluation leaves the iteration's state alone); empty subdomains are +inf.
+floor of the trajectory; row 0 equals the bound at the start and row T the
+bound after T steps; the returned bounds and moments are bitwise those of
+ld_bound on the layer-wise engine (the evaluation leaves the iteration's
+state alone); empty subdomains are +inf.
 """
 import numpy as np
 import pytest
@@ -19,6 +20,7 @@ pytestmark = pytest.mark.gpu
 
 FULL_RUN_MAX = 1e-3
 FULL_RUN_MEDIAN = 3e-4
+MID_RUN_MAX = 5e-3        # 2.5x the mid-run FP32 floor
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -72,15 +74,19 @@ def test_trace_leaves_the_iterations_unchanged():
     B, N = pb["B"], pb["lbk"].shape[1]
     mv_a = torch.zeros((2, B, N), dtype=torch.float32, device="cuda")
     mv_b = torch.zeros_like(mv_a)
-    a, tr = ldb.ld_bound_trace(net, *args_of(pb), n_iters=25, adam_mv=mv_a)
-    b = ldb.ld_bound(net, *args_of(pb), n_iters=25, opts=ldb.Options(engine="layerwise"), adam_mv=mv_b)
+    # 25 steps of a 26-step schedule, so that a 26-step trace continues them
+    a, tr = ldb.ld_bound_trace(net, *args_of(pb), n_iters=25, adam_mv=mv_a, opts=ldb.Options(t_total=26))
+    b = ldb.ld_bound(net, *args_of(pb), n_iters=25, opts=ldb.Options(engine="layerwise", t_total=26), adam_mv=mv_b)
     assert torch.equal(a, b) and torch.equal(mv_a, mv_b)
     tr = tr.cpu().numpy()
     assert np.all(np.isinf(tr[:, 4])) and np.isinf(a[4].item())
     assert np.all(np.isfinite(np.delete(tr, 4, axis=1)))
-    # ascent: the last iterates are above the start on average
-    fin = np.delete(tr, 4, axis=1)
-    assert np.mean(fin[-1] - fin[0]) > 0
+    # the next row is q(rho_25), the value the 25-step call bounded in FP64
+    _, tr26 = ldb.ld_bound_trace(net, *args_of(pb), n_iters=26)
+    tr26 = tr26.cpu().numpy()
+    assert np.array_equal(tr26[:25], tr)
+    fin = np.isfinite(a.cpu().numpy())
+    assert np.max(rel(tr26[25, fin], a.cpu().numpy()[fin])) < 1e-6
 
 
 def test_long_trace_within_the_fp32_floor():
@@ -89,7 +95,12 @@ def test_long_trace_within_the_fp32_floor():
     _, tr = ldb.ld_bound_trace(net, *args_of(pb), n_iters=100)
     _, ref_tr, keep = oracle_trace(pb, 100)
     r = rel(tr.cpu().numpy()[:, keep], ref_tr)
-    assert np.max(r) < FULL_RUN_MAX and np.median(r) < FULL_RUN_MEDIAN
+    # the first steps to 1e-5; mid-run the FP32 floor of the trajectory (up
+    # to ~2e-3 for single subdomains, tests/test_oracle_fp32_floor.py); the
+    # last iterates to the long-run tolerances
+    assert np.max(r[:3]) < 1e-5
+    assert np.max(r) < MID_RUN_MAX and np.median(r) < FULL_RUN_MEDIAN
+    assert np.max(r[-1]) < FULL_RUN_MAX
 
 
 def test_bf16_trace_is_refused():

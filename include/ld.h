@@ -287,8 +287,10 @@ ld_status ld_bound_trace(ld_net* net, const float* lb0, const float* ub0, const 
  *   center [device] [n_props, n_0] float; eps [device] [n_props] float >= 0;
  *   lbk, ubk [device] [n_props, N] intermediate bounds valid over the balls
  *   (e.g. from ld_intermediate_bounds_ball); the other arguments as ld_bound.
- *   The iterations run on the FP32 layer-wise engine (opts->engine is not
- *   consulted); out[b] is q(rho_T) in FP64 lowered by an a-priori bound on its
+ *   The iterations run in FP32 on the layer-wise or the fused engine
+ *   (opts->engine; the fused engine forms x0* after its transposed phase from
+ *   a fixed-order norm of g0, and is used only where its scratch holds that
+ *   reduction); out[b] is q(rho_T) in FP64 lowered by an a-priori bound on its
  *   rounding error, whose ball term -eps ||g0|| takes an upper bound of ||g0||
  *   (every |g0_i| raised by its error bound, squares and sums and the square
  *   root rounded up).  The call grows a workspace of its own on first use.

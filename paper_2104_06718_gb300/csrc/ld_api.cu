@@ -384,6 +384,7 @@ ld_status run_iterations(ld_net* net, const Problem& P, const ld_opts& o, int n_
                          cudaStream_t s, int crown = 0) {
   const int T_sched = o.t_total > 0 ? o.t_total : o.t_offset + n_iters;
   if (engine == LD_ENGINE_FUSED) {
+    if (P.ball_eps && !ld::fused_ball_fits(net->fused, tile)) return LD_ERR_UNSUPPORTED;
     // one launch per kFusedSteps iterations; the first also computes the CROWN start
     for (int t0 = 0; t0 < n_iters || (t0 == 0 && crown); t0 += ld::kFusedSteps) {
       ld::FusedIter it{};
@@ -1636,9 +1637,11 @@ static ld_status bound_impl(ld_net* net, const float* lb0, const float* ub0, con
   const bool bf16 = o.precision == LD_PREC_BF16 && n_iters > 0;
   if (bf16 && (st = ensure_tc(net, B, n_props)) != LD_OK) return st;
   if (bf16 && (st = ensure_fused_tc(net)) != LD_OK && st != LD_ERR_UNSUPPORTED) return st;
-  const std::pair<int, int> eng = (n_iters <= 0 || ball_eps || q_trace) ? std::make_pair((int)LD_ENGINE_LAYERWISE, 0)
-                                  : bf16       ? choose_engine_bf16(net, P, o, n_iters, s)
-                                               : choose_engine(net, P, o, n_iters, s);
+  std::pair<int, int> eng = (n_iters <= 0 || q_trace) ? std::make_pair((int)LD_ENGINE_LAYERWISE, 0)
+                            : bf16                  ? choose_engine_bf16(net, P, o, n_iters, s)
+                                                    : choose_engine(net, P, o, n_iters, s);
+  if (ball_eps && eng.first == LD_ENGINE_FUSED && !ld::fused_ball_fits(net->fused, eng.second))
+    eng = {LD_ENGINE_LAYERWISE, 0};
   // The CROWN start must come from the same transposed-pass arithmetic as the
   // iterations (its exact ties would otherwise be broken by rounding): the
   // fused engines compute it in-kernel, the layerwise engines with their kernels.

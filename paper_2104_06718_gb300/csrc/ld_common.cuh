@@ -465,6 +465,9 @@ constexpr int kFusedWide = 16;
 FusedNet make_fused_net(const std::vector<LayerDev>& Ls, bool tc = false);
 // Shared memory of a fused launch of the given shape code (all state resident).
 size_t fused_smem_bytes(const FusedNet& f, int code);
+// l2-ball problems (P.ball_eps) on the FP32 fused engine: its FC scratch must
+// hold one float per warp and subdomain (the ball's norm reduction).
+bool fused_ball_fits(const FusedNet& f, int code);
 cudaError_t launch_fused(const FusedNet& f, int code, const Problem& P, float* rho, float* m, float* v,
                          const FusedIter& it, cudaStream_t s);
 

@@ -132,6 +132,11 @@ size_t fused_smem_bytes(const FusedNet& f, int code) {
   return smem_bytes(f, code & ~kFusedWide, (code & kFusedWide) ? 512 : 256);
 }
 
+bool fused_ball_fits(const FusedNet& f, int code) {
+  const int NT = (code & kFusedWide) ? 512 : 256;
+  return red_floats(f, NT) >= (size_t)(NT / 32);
+}
+
 cudaError_t launch_fused(const FusedNet& f, int code, const Problem& P, float* rho, float* m, float* v,
                          const FusedIter& it, cudaStream_t s) {
   if (P.B == 0 || (it.T == 0 && !it.crown)) return cudaSuccess;

@@ -213,6 +213,12 @@ template <int S, int NT, bool TC>
 __device__ __forceinline__ void epi_t(const Ctx<S, NT, TC>& c, int k, int s, int i, int xi, int ri, float g) {
   const int b = c.b0 + s;
   if (k == 0) {
+    if (!TC && c.P.ball_eps) {
+      // l2 ball (Sec. 3.2.1): x0 needs the norm of the whole g_0, so g_0 is
+      // kept here and ball_project forms x0 after the transposed phase
+      c.xp(s)[xi] = g;
+      return;
+    }
     // P0 (Eq. box_bounds_sol): minimise -g_0^T x0, i.e. x0 = u0 where g_0 >= 0
     const int p = prop_at(c, s);
     c.xp(s)[xi] = (g >= 0.f) ? c.P.u0[(size_t)p * c.P.n0 + i] : c.P.l0[(size_t)p * c.P.n0 + i];
@@ -1017,6 +1023,63 @@ __device__ __forceinline__ void tc_epilogues(const Ctx<S, NT, TC>& c, int p0, in
   fence_proxy_async();
 }
 
+// ------------------------------------------------------------------ l2-ball P0
+
+// Where input element i (flat, channel-major) sits in the x0 plane.
+__device__ __forceinline__ int x0_index(const LayerDev& L1, const FusedLayer& F1, int i) {
+  if (L1.kind == LD_LAYER_FC) return F1.xoff + i;
+  const int hw = L1.h * L1.w, ch = i / hw, r = i - ch * hw, y = r / L1.w;
+  return xp_conv(L1, F1, ch, y, r - y * L1.w);
+}
+
+// P0 over the l2 ball (Sec. 3.2.1), after the transposed phase has left g_0
+// in the x0 plane: x0 = c + eps g_0 / ||g_0|| (c when g_0 = 0).  The sum of
+// squares is formed in a fixed order (per-thread FP32 partials over a fixed
+// strided set, warp sums by a fixed shuffle tree, the warp sums added in
+// FP64 in warp order by every thread alike), so it does not depend on
+// scheduling.  The warp sums use the FC scratch, which holds nothing between
+// the transposed and the forward phase (the host runs this only when that
+// scratch has NT/32 floats per subdomain).  Every thread of the CTA calls it.
+template <int S, int NT, bool TC>
+__device__ void ball_project(const Ctx<S, NT, TC>& c) {
+  constexpr int NW = NT / 32;
+  const LayerDev& L1 = c.net.L[0];
+  const FusedLayer& F1 = c.net.F[0];
+  const int n0 = c.P.n0;
+  float part[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) part[s] = 0.f;
+  for (int i = threadIdx.x; i < n0; i += NT) {
+    const int xi = x0_index(L1, F1, i);
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      const float g = c.xp(s)[xi];
+      part[s] = fmaf(g, g, part[s]);
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) part[s] += __shfl_xor_sync(0xffffffffu, part[s], off);
+    if ((threadIdx.x & 31) == 0) c.RED[s * NW + (int)threadIdx.x / 32] = part[s];
+  }
+  __syncthreads();
+  float scale[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    double tot = 0.0;
+    for (int w = 0; w < NW; ++w) tot += (double)c.RED[s * NW + w];
+    scale[s] = tot > 0.0 ? (float)((double)c.P.ball_eps[prop_at(c, s)] / sqrt(tot)) : 0.f;
+  }
+  for (int i = threadIdx.x; i < n0; i += NT) {
+    const int xi = x0_index(L1, F1, i);
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+      if (active(c, s)) c.xp(s)[xi] = fmaf(scale[s], c.xp(s)[xi], c.P.l0[(size_t)prop_at(c, s) * n0 + i]);
+  }
+  __syncthreads();
+}
+
 // ------------------------------------------------------------------ kernel
 
 template <int S, int NT, bool TC>
@@ -1210,6 +1273,9 @@ __global__ void __launch_bounds__(NT) fused_kernel(const __grid_constant__ Fused
       __syncthreads();
     }
     if (TC && *tc_abort(tcp)) break;
+    if constexpr (!TC) {
+      if (P.ball_eps) ball_project(c);
+    }
     for (int k = net.n - 2; k >= 0; --k)
       if (net.L[k].kind == LD_LAYER_FC) ffc_main(c, net.L[k], net.F[k], k, tf);
     if constexpr (TC) {

@@ -236,3 +236,55 @@ def test_bad_radii_set_the_status_and_bf16_is_refused():
         run_gpu(pb, 2, opts=ldb.Options(precision="bf16"), net=net)
     with pytest.raises(ldb.LDError):
         run_gpu(pb, 2, opts=ldb.Options(fp64_final=False), net=net)
+
+
+# ------------------------------------------------------------------ the fused FP32 engine
+
+def fused(S):
+    return ldb.Options(engine="fused", tile=S)
+
+
+def tiny_ball_problem(B, eps=0.5, block=0):
+    """The tiny MLP (a fully connected first layer) over a ball around its box
+    centre, with the same construction as ball_problem."""
+    specs = synth.tiny_mlp(1)
+    net = oracle_net(specs)
+    l0, u0 = synth.tiny_box(1)
+    c = ((l0.astype(np.float64) + u0.astype(np.float64)) / 2).astype(np.float32).reshape(1, -1)
+    e = np.array([eps], np.float32)
+    lb, ub = l2.ball_ibp_bounds(net, c.astype(np.float64), e.astype(np.float64))
+    lbk, ubk = outward_f32(flat(net, lb), flat(net, ub))
+    amb = np.nonzero((lbk[0] < 0) & (ubk[0] > 0))[0]
+    masks = synth.split_masks(lbk.shape[1], B, amb, (0, 3), block=block)
+    return dict(specs=specs, net=net, c=c, eps=e, lbk=lbk, ubk=ubk, prop=np.zeros(B, np.int32), masks=masks, B=B)
+
+
+@pytest.mark.parametrize("name,S", [("base", 1), ("base", 2), ("deep", 1), ("tiny", 1)])
+@pytest.mark.parametrize("T", [1, 3])
+def test_fused_engine_short_runs_match_the_oracle(name, S, T):
+    pb = tiny_ball_problem(5) if name == "tiny" else \
+        ball_problem(name, 7, 0.1 if name == "base" else 0.05, block=3)   # 7: a ragged last CTA for S = 2
+    net = ldb.Net(pb["specs"])
+    out = run_gpu(pb, T, opts=fused(S), net=net).cpu().numpy()
+    ref = run_oracle(pb, T)
+    fin = np.isfinite(ref)
+    assert np.array_equal(np.isfinite(out), fin)
+    assert np.max(rel(out[fin], ref[fin])) < 1e-5
+    lay = run_gpu(pb, T, opts=ldb.Options(engine="layerwise"), net=net).cpu().numpy()
+    assert np.max(rel(out[fin], lay[fin])) < 1e-5
+
+
+@pytest.mark.parametrize("S", [1, 2])
+def test_fused_engine_long_runs_and_repeatability(S):
+    pb = ball_problem("base", 9, 0.1, block=5)
+    net = ldb.Net(pb["specs"])
+    out, rho = run_gpu(pb, 100, opts=fused(S), net=net, return_rho=True)
+    ref = run_oracle(pb, 100)
+    o = out.cpu().numpy()
+    fin = np.isfinite(ref)
+    assert np.array_equal(np.isfinite(o), fin)
+    r = rel(o[fin], ref[fin])
+    assert np.max(r) < FULL_RUN_MAX and np.median(r) < FULL_RUN_MEDIAN
+    # the norm is reduced in a fixed order: a second run is bitwise the same
+    out2, rho2 = run_gpu(pb, 100, opts=fused(S), net=net, return_rho=True)
+    assert torch.equal(rho, rho2) and torch.equal(out, out2)

@@ -65,10 +65,10 @@ METRIC = "LD subdomain bounds/s on Base/Wide/Deep convnets, bf16 vs fp32 at ≤1
 # (kernel_digest(engine)).  An entry whose digest differs from the current
 # sources is not reported (the kernel changed since the capture).
 TRAFFIC = {
-    # ncu --set full of fused_kernel<2, 512, 0>: dram__bytes_read.sum 8,010,496 B, dram__bytes_write.sum 0
-    ("base", "fp32", "fused", 2, 512, 256, 100): ("0dc0d110a53a", 8010496),
-    # ncu --set full of fused_kernel<2, 512, 1>: dram__bytes_read.sum 8,100,352 B, dram__bytes_write.sum 0
-    ("base", "bf16", "fused tensor-core bf16", 2, 512, 256, 100): ("c661d2910a24", 8100352),
+    # ncu --set full of fused_kernel<2, 512, 0>: dram__bytes_read.sum 8,018,432 B, dram__bytes_write.sum 0
+    ("base", "fp32", "fused", 2, 512, 256, 100): ("a9ba9e662b29", 8018432),
+    # ncu --metrics dram__bytes_*.sum of fused_kernel<2, 512, 1>: read 8,098,560 B, write 0
+    ("base", "bf16", "fused tensor-core bf16", 2, 512, 256, 100): ("93104ba69147", 8098560),
 }
 
 # The sources each timed engine is compiled from (besides the shared header
@@ -618,7 +618,7 @@ def measure_ball(bn, args, eps=0.1):
     res = {"subdomains": wl["B"], "iterations": wl["T"], "radius": eps, "ms_per_call": ms,
            "bounds_per_s": wl["B"] / (ms / 1000.0), "clocks": bn.sampler.window(*win),
            "ambiguous_relus_root": int(amb.size), "mean_bound": float(out[np.isfinite(out)].mean()),
-           "engine": "FP32 layer-wise passes (the ball's P0 needs the norm of the whole g0)"}
+           "engine": dict(zip(("engine", "tile", "cta_threads"), net.tuned(wl["B"], "fp32")))}
     if not args.no_cpu_baseline:
         def run(lbk_o, ubk_o, masks_o):
             got = ldb.ld_bound_ball(net, c, e, torch.as_tensor(lbk_o, device=bn.dev),

@@ -101,6 +101,13 @@ struct ld_net {
   bool graphs = true;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t iter_exec = nullptr;
+  // side streams of the FP64 final bound: its per-layer passes are
+  // independent (each writes its own slots), so they run side by side and
+  // join the caller's stream before the combine
+  static constexpr int kAux = 3;
+  cudaStream_t aux[kAux] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[kAux] = {};
+  bool aux_tried = false, aux_ok = false;
   std::map<int, std::pair<int, int>> tuned;
   int n_sm = 0;
   size_t smem_optin = 0;
@@ -721,16 +728,40 @@ int p0_slots(const ld_net* net) { return ld::final_slots(layer(net, 1), net->n =
 // pass with l0 = u0 = c) and one more slot holds -eps ||g_0||, bounded from a
 // second final pass of layer 1 in ball-norm mode; the slots then live in
 // net->ball_ws (ensure_ball_ws).
+// The side streams, made with the net (never while a stream is being
+// captured); false if they cannot be made (the final bound then runs on the
+// caller's stream alone).
+bool ensure_aux(ld_net* net) {
+  if (net->aux_tried) return net->aux_ok;
+  net->aux_tried = true;
+  bool ok = cudaEventCreateWithFlags(&net->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; i < ld_net::kAux && ok; ++i)
+    ok = cudaStreamCreateWithFlags(&net->aux[i], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&net->ev_join[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) cudaGetLastError();
+  net->aux_ok = ok;
+  return ok;
+}
+
 void final_fp64(ld_net* net, const Problem& P, double* out, cudaStream_t s) {
   const int n = net->n;
   const int nfs = n_final_slots(net);
   const bool ball = P.ball_eps != nullptr;
   ld::FinalAcc acc{ball ? net->ball_ws : net->acc, nfs + (ball ? 1 : 0), 0};
+  // the per-layer passes on the side streams (FP64-pipe bound, each too
+  // small to fill the GPU alone), joined before the combine
+  const bool fork = n >= 2 && net->aux_ok;
+  if (fork) {
+    cudaEventRecord(net->ev_fork, s);
+    for (int i = 0; i < ld_net::kAux; ++i) cudaStreamWaitEvent(net->aux[i], net->ev_fork, 0);
+  }
   for (int k = n - 1; k >= 0; --k) {
+    cudaStream_t ls = fork ? net->aux[k % ld_net::kAux] : s;
     ld::launch_final_layer(layer(net, k + 1), k, r_off(net, k), x_off(net, k), P, net->rho, k == n - 1 ? 1 : 0, acc,
-                           s);
+                           ls);
     acc.slot += ld::final_slots(layer(net, k + 1), k == n - 1);
   }
+  // the bias terms and the ball's norm pass meanwhile on the caller's stream
   ld::launch_final_bias(net->L, P, net->rho, acc, s);
   if (ball) {
     ld::FinalAcc scratch{net->ball_ws + (size_t)P.B * (nfs + 1) * 3, p0_slots(net), 0};
@@ -738,6 +769,11 @@ void final_fp64(ld_net* net, const Problem& P, double* out, cudaStream_t s) {
                            1);
     ld::launch_final_ball(P, scratch, acc, nfs, s);
   }
+  if (fork)
+    for (int i = 0; i < ld_net::kAux; ++i) {
+      cudaEventRecord(net->ev_join[i], net->aux[i]);
+      cudaStreamWaitEvent(s, net->ev_join[i], 0);
+    }
   const double M = (double)(net->n0 + 2 * net->N + 1 + (ball ? 1 : 0));
   const double gM = ld::final_gamma(M);
   ld::launch_final_combine_bn(P, acc, net->bn, net->bn_err, gM, 1.0 + 2.0 * gM, out, s);
@@ -1015,6 +1051,7 @@ ld_status ld_net_create(const ld_layer_desc* Ld, int32_t n_layers, const float* 
   net->n_sm = v > 0 ? v : 1;
   cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   net->smem_optin = (size_t)(v > 0 ? v : 48 * 1024);
+  ensure_aux(net);
   *out = net;
   return LD_OK;
 }
@@ -1026,6 +1063,11 @@ ld_status ld_net_destroy(ld_net* net) {
   free_ws(net);
   if (net->iter_exec) cudaGraphExecDestroy(net->iter_exec);
   if (net->cap_stream) cudaStreamDestroy(net->cap_stream);
+  for (int i = 0; i < ld_net::kAux; ++i) {
+    if (net->aux[i]) cudaStreamDestroy(net->aux[i]);
+    if (net->ev_join[i]) cudaEventDestroy(net->ev_join[i]);
+  }
+  if (net->ev_fork) cudaEventDestroy(net->ev_fork);
   if (net->tc_ws) cudaFree(net->tc_ws);
   if (net->ib_ws) cudaFree(net->ib_ws);
   if (net->prox_ws) cudaFree(net->prox_ws);

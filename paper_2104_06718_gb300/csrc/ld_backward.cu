@@ -167,13 +167,33 @@ __global__ void __launch_bounds__(NT) conv_wgrad_slab_kernel(Problem P, const do
   if (t < L.cout * PS) part[((size_t)blockIdx.x * PS + t % PS) * (size_t)(nw + L.cout) + nw + t / PS] = accb;
 }
 
+// Column sums of a [rows, width] array in a fixed order: a block takes 32
+// consecutive columns; its warp w sums rows w, w + kColGroups, ... (lane =
+// column, so every row read is one coalesced 128-byte segment), and the warp
+// sums are added in warp order.
+constexpr int kColGroups = NT / 32;
+
+__device__ __forceinline__ float column_sum(const float* __restrict__ src, int rows, int width, int col) {
+  __shared__ float part[kColGroups][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float acc = 0.f;
+  if (col < width)
+    for (int r = w; r < rows; r += kColGroups) acc += src[(size_t)r * width + col];
+  part[w][lane] = acc;
+  __syncthreads();
+  float t = 0.f;
+  if (w == 0)
+    for (int i = 0; i < kColGroups; ++i) t += part[i][lane];
+  return t;  // valid in warp 0
+}
+
 // Sum of the slab partials in a fixed order: out_w[e] (e < nw), out_b[e - nw].
-__global__ void wgrad_reduce_kernel(const float* __restrict__ part, int rows, int nw, int cout, float* out_w,
-                                    float* out_b) {
+__global__ void __launch_bounds__(NT) wgrad_reduce_kernel(const float* __restrict__ part, int rows, int nw, int cout,
+                                                          float* out_w, float* out_b) {
   const int width = nw + cout;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < width; e += gridDim.x * blockDim.x) {
-    float s = 0.f;
-    for (int r = 0; r < rows; ++r) s += part[(size_t)r * width + e];
+  const int e = blockIdx.x * 32 + (threadIdx.x & 31);
+  const float s = column_sum(part, rows, width, e);
+  if (threadIdx.x < 32 && e < width) {
     if (e < nw) {
       if (out_w) out_w[e] = s;
     } else if (out_b) {
@@ -230,6 +250,15 @@ __global__ void bound_contrib_kernel(Problem P, const double* w, const float* __
   }
 }
 
+// out[j] = sum over all subdomains of src[b, j] when every subdomain has
+// property 0 (no property map): column sums in a fixed order.
+__global__ void __launch_bounds__(NT) reduce_single_prop_kernel(const float* __restrict__ src, int rows, int width,
+                                                                float* out) {
+  const int j = blockIdx.x * 32 + (threadIdx.x & 31);
+  const float s = column_sum(src, rows, width, j);
+  if (threadIdx.x < 32 && j < width) out[j] = s;
+}
+
 // out[p, j] = sum over subdomains b of property p of src[b, j]; one thread per
 // column, flushing a running sum whenever the property changes.
 __global__ void reduce_by_prop_kernel(Problem P, const float* __restrict__ src, int width, float* out) {
@@ -281,7 +310,7 @@ void launch_backward(const std::vector<LayerDev>& Ls, const std::vector<size_t>&
         count_launch(2);
         conv_wgrad_slab_kernel<<<G, NT, smem, s>>>(P, grad_out, rho, L, x, PS, R, scratch_bn);
         const int width = nw + L.cout;
-        wgrad_reduce_kernel<<<(width + NT - 1) / NT, NT, 0, s>>>(scratch_bn, G * PS, nw, L.cout,
+        wgrad_reduce_kernel<<<(width + 31) / 32, NT, 0, s>>>(scratch_bn, G * PS, nw, L.cout,
                                                                  out.gW ? out.gW + w_off[k - 1] : nullptr,
                                                                  out.gb ? out.gb + b_off[k - 1] : nullptr);
         continue;
@@ -316,6 +345,11 @@ void launch_backward(const std::vector<LayerDev>& Ls, const std::vector<size_t>&
     auto red = [&](const float* src, int width, float* dst) {
       if (!dst) return;
       count_launch();
+      if (!P.prop) {
+        if (P.n_props > 1) cudaMemsetAsync(dst + width, 0, sizeof(float) * (size_t)(P.n_props - 1) * width, s);
+        reduce_single_prop_kernel<<<(width + 31) / 32, NT, 0, s>>>(src, P.B, width, dst);
+        return;
+      }
       cudaMemsetAsync(dst, 0, sizeof(float) * (size_t)P.n_props * width, s);
       reduce_by_prop_kernel<<<(width + NT - 1) / NT, NT, 0, s>>>(P, src, width, dst);
     };

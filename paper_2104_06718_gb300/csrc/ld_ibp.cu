@@ -5,8 +5,9 @@
 // u_hat), so the FP32 results contain the exact interval bounds.  The output
 // lower bound of the margin-folded last layer is formed in FP64 from the
 // FP64 fold, lowered by the fold's error bound.
-// One launch per layer; one thread per (row, output neuron), a row being a
-// property (root bounds) or a subdomain (bounds recomputed after its splits:
+// One launch per layer; one thread per (row, output neuron) (one warp for
+// wide FC layers), a row being a property (root bounds) or a subdomain
+// (bounds recomputed after its splits:
 // the first layer reads the box of the subdomain's property, and the split
 // clamp of Sec. 2.3.2 is applied to every hidden layer's bounds before they
 // feed the next layer through [relu(l), relu(u)]).
@@ -99,15 +100,76 @@ __global__ void ibp_kernel(LayerDev L, int first, int last, int n_rows, const fl
   }
 }
 
+// FC layers (not the margin-folded last row): one warp per (row, output
+// neuron); lane q takes the inputs q, q + 32, ... (coalesced weight reads),
+// and the lanes' outward-rounded partial sums are added by a fixed shuffle
+// tree, rounding down for l_hat and up for u_hat, then the bias.
+__global__ void ibp_fc_warp_kernel(LayerDev L, int first, int n_rows, const float* __restrict__ lin,
+                                   const float* __restrict__ uin, int in_stride, float* lout, float* uout,
+                                   int out_stride, int* status, IbpRows rows) {
+  const int lane = threadIdx.x & 31;
+  const size_t total = (size_t)n_rows * L.n_out;
+  const size_t nwarp = (size_t)gridDim.x * (blockDim.x / 32);
+  for (size_t e = blockIdx.x * (size_t)(blockDim.x / 32) + threadIdx.x / 32; e < total; e += nwarp) {
+    const int p = (int)(e / L.n_out), o = (int)(e % L.n_out);
+    int src = p;
+    if (first && rows.n_in_rows > 0) {
+      src = rows.in_row ? rows.in_row[p] : 0;
+      src = src < 0 ? 0 : (src >= rows.n_in_rows ? rows.n_in_rows - 1 : src);
+    }
+    const float* lp = lin + (size_t)src * in_stride;
+    const float* up = uin + (size_t)src * in_stride;
+    const float* w = L.W + (size_t)o * L.n_in;
+    float lo = 0.f, hi = 0.f;
+    bool bad = false;
+    for (int i = lane; i < L.n_in; i += 32) {
+      float a = lp[i], c = up[i];
+      if (!first) {
+        a = fmaxf(a, 0.f);
+        c = fmaxf(c, 0.f);
+      } else if (!(isfinite(a) && isfinite(c) && a <= c)) {
+        bad = true;
+      }
+      const float wi = w[i];
+      lo = __fmaf_rd(wi, wi >= 0.f ? a : c, lo);
+      hi = __fmaf_ru(wi, wi >= 0.f ? c : a, hi);
+    }
+    if (bad) atomicCAS(status, 0, (int)LD_ERR_NONFINITE);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      lo = __fadd_rd(lo, __shfl_xor_sync(0xffffffffu, lo, off));
+      hi = __fadd_ru(hi, __shfl_xor_sync(0xffffffffu, hi, off));
+    }
+    if (lane == 0) {
+      lo = __fadd_rd(lo, L.b[o]);
+      hi = __fadd_ru(hi, L.b[o]);
+      if (rows.mask) {  // split clamp: +1 => l <- max(l,0); -1 => u <- min(u,0)
+        const int m = rows.mask[(size_t)p * rows.mask_stride + L.r_out_off + o];
+        if (m > 0) lo = fmaxf(lo, 0.f);
+        if (m < 0) hi = fminf(hi, 0.f);
+      }
+      lout[(size_t)p * out_stride + o] = lo;
+      uout[(size_t)p * out_stride + o] = hi;
+    }
+  }
+}
+
 }  // namespace
 
 void launch_ibp_layer(const LayerDev& L, int first, int last, int n_rows, const float* lin, const float* uin,
                       int in_stride, float* lout, float* uout, int out_stride, double* out_lb, int* status,
                       cudaStream_t s, const IbpRows& rows) {
   const size_t total = (size_t)n_rows * L.n_out;
+  count_launch();
+  if (L.kind == LD_LAYER_FC && !last && L.n_in >= 64) {
+    size_t g = (total + 7) / 8;  // 8 warps per block
+    if (g > 65535 * 8) g = 65535 * 8;
+    ibp_fc_warp_kernel<<<(int)(g < 1 ? 1 : g), 256, 0, s>>>(L, first, n_rows, lin, uin, in_stride, lout, uout,
+                                                              out_stride, status, rows);
+    return;
+  }
   int grid = (int)((total + 255) / 256);
   if (grid < 1) grid = 1;
-  count_launch();
   ibp_kernel<<<grid, 256, 0, s>>>(L, first, last, n_rows, lin, uin, in_stride, lout, uout, out_stride, out_lb,
                                   status, rows);
 }

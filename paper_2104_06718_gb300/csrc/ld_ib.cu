@@ -105,11 +105,18 @@ struct Dot2 {
 };
 
 // a = (W^T mu)[ii] by Dot2 and s >= sum |W| |mu| (FP32, rounded up), mu in shared memory.
+// A zero mu term is skipped: it would add an exact zero to the running sum,
+// to its error and to s, so the result is the same (a row's mu is sparse: a
+// conv neuron's objective reaches only its receptive field, and blocking
+// ReLUs relax to zero).
 __device__ __forceinline__ void transposed_elem(const LayerDev& L, const float* mu, int ii, float& a, float& s) {
   Dot2 d;
   if (L.kind == LD_LAYER_FC) {
     const float* w = L.W + ii;
-    for (int o = 0; o < L.n_out; ++o) d.add(__ldg(w + (size_t)o * L.n_in), mu[o]);
+    for (int o = 0; o < L.n_out; ++o) {
+      const float m = mu[o];
+      if (m != 0.f) d.add(__ldg(w + (size_t)o * L.n_in), m);
+    }
     a = __fadd_rn(d.p, d.c);
     s = d.s;
     return;
@@ -126,8 +133,10 @@ __device__ __forceinline__ void transposed_elem(const LayerDev& L, const float* 
       if (tx < 0 || tx % L.stride) continue;
       const int ox = tx / L.stride;
       if (ox >= L.wo) continue;
-      for (int o = 0; o < L.cout; ++o)
-        d.add(__ldg(L.W + (((size_t)o * L.cin + c) * L.kh + ki) * L.kw + kj), mu[((size_t)o * L.ho + oy) * L.wo + ox]);
+      for (int o = 0; o < L.cout; ++o) {
+        const float m = mu[((size_t)o * L.ho + oy) * L.wo + ox];
+        if (m != 0.f) d.add(__ldg(L.W + (((size_t)o * L.cin + c) * L.kh + ki) * L.kw + kj), m);
+      }
     }
   }
   a = __fadd_rn(d.p, d.c);
@@ -191,6 +200,12 @@ __global__ void __launch_bounds__(NT) ib_step_kernel(IbStep st) {
       s = fabsf(a);
     } else {
       transposed_elem(L, mu, ii, a, s);
+    }
+    if (a == 0.f && s == 0.f) {
+      // no term reached this element: it adds nothing to the bound, its
+      // error or its relaxation (mu = 0 for the next pass)
+      if (!st.box) st.mu_out[(size_t)rl * L.n_in + ii] = 0.f;
+      continue;
     }
     // bound on |a - W^T mu| (Dot2): u |a| + gamma_K^2 sum|W||mu|, with margin; 0 for the exact seed
     const double da = st.seed ? 0.0 : __dadd_ru(__dmul_ru(1.1920928955078125e-07, fabs((double)a)), __dmul_ru(g2, (double)s));

@@ -425,6 +425,8 @@ struct FusedLayer {
   int swf, swt;                // shared-memory offsets (floats) of the forward / transposed weight layouts
   int fmode, tmode;            // 0 generic; 1 blocked k4 s2; 2 blocked k3 s1
   int vec4;                    // FC: rows 16-byte aligned and n_in % 4 == 0
+  const uint16_t* wh;          // tc layout, hidden FC layers with vec4: the BF16-rounded weights
+                               // [n_out, n_in] as BF16 (the transposed pass's rows); nullptr otherwise
 };
 
 // The net as the fused kernel sees it.

@@ -336,13 +336,15 @@ ld_status build_fused_tc(const std::vector<LayerDev>& Ls, FusedNet* f, FusedTc o
   bool ok[2];
   for (int i = 0; i < 2; ++i) ok[i] = plan_fused_tc(Ls, W, *f, i + 1, smem_limit, pl[i]);
   if (!ok[0] && !ok[1]) return LD_ERR_UNSUPPORTED;
-  // one allocation: rounded FC weights, then per plan its table and tiles
+  // one allocation: rounded FC weights (FP32 and BF16), then per plan its table and tiles
   size_t bytes = 0;
-  std::vector<size_t> fc_off(n, 0);
+  std::vector<size_t> fc_off(n, 0), fh_off(n, 0);
   for (int k = 0; k + 1 < n; ++k)
     if (Ls[k].kind == LD_LAYER_FC) {
       fc_off[k] = bytes;
       bytes += (W[k].size() * 4 + 255) / 256 * 256;
+      fh_off[k] = bytes;
+      bytes += (W[k].size() * 2 + 255) / 256 * 256;
     }
   size_t tab_off[2], wt_off[2];
   for (int i = 0; i < 2; ++i) {
@@ -360,18 +362,23 @@ ld_status build_fused_tc(const std::vector<LayerDev>& Ls, FusedNet* f, FusedTc o
   char* c = static_cast<char*>(p);
   for (int k = 0; k + 1 < n; ++k)
     if (Ls[k].kind == LD_LAYER_FC) {
-      // BF16-rounded values kept in FP32 (the FC passes' loads and products
-      // stay those of the FP32 engine)
+      // BF16-rounded values kept in FP32 (the forward pass's loads and
+      // products stay those of the FP32 engine) and as BF16 (the transposed
+      // pass's rows: the same values, half the bytes)
       std::vector<float> r(W[k].size());
+      std::vector<uint16_t> h(W[k].size());
       for (size_t z = 0; z < r.size(); ++z) {
-        const uint32_t u = (uint32_t)host_bf16(W[k][z]) << 16;
+        h[z] = host_bf16(W[k][z]);
+        const uint32_t u = (uint32_t)h[z] << 16;
         std::memcpy(&r[z], &u, 4);
       }
-      if (cudaMemcpy(c + fc_off[k], r.data(), r.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+      if (cudaMemcpy(c + fc_off[k], r.data(), r.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+          cudaMemcpy(c + fh_off[k], h.data(), h.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaFree(p);
         return LD_ERR_CUDA;
       }
       f->L[k].W = reinterpret_cast<const float*>(c + fc_off[k]);
+      f->F[k].wh = reinterpret_cast<const uint16_t*>(c + fh_off[k]);
     }
   for (int i = 0; i < 2; ++i) {
     if (!ok[i]) continue;

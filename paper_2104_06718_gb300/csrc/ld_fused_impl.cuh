@@ -284,15 +284,21 @@ __device__ __forceinline__ float* red_of(const Ctx<S, NT, TC>& c, int k) {
 
 // Transposed FC pass of layer L = layer k+1 into layer k: g[s][i] = sum_o W[o, i] rho_{k+1}[s][o].
 // A thread owns 4 consecutive columns i and streams the weight rows in
-// batches of U 16-byte loads (TC: U 8-byte loads of the BF16 weights, four
-// columns each, widened exactly to FP32: more rows in flight in the same
-// registers, 5 round trips instead of 9 over 100 rows); the clamped bounds its
-// epilogue needs are loaded before the weight loop (TC: after it).  When the pass's thread group has at least
+// batches of U 16-byte loads (the tensor-core kernel with 2 subdomains per
+// CTA: U 8-byte loads of the BF16 weights, four columns each, widened exactly
+// to FP32: more rows in flight in the same registers, 5 round trips instead of
+// 9 over 100 rows); the clamped bounds its epilogue needs are loaded before
+// the weight loop (BF16 rows: after it).  When the pass's thread group has at least
 // twice as many threads as 4-column groups, its two halves take one half of
 // the rows each and add their partial sums through shared memory (half p
 // finalises the subdomains s with s % 2 == p).
-template <bool TC>
-__host__ __device__ constexpr int tfc_batch_rows() { return TC ? 20 : 16; }  // weight rows in flight per thread
+// Weight rows in flight per thread; BF16 rows in the tensor-core kernel with
+// two subdomains per CTA (with one, its conv code has the registers to keep
+// the FP32-stored rows spill-free, and its iteration is bound by the convs).
+template <int S, bool TC>
+__host__ __device__ constexpr bool tfc_bf16_rows() { return TC && S >= 2; }
+template <int S, bool TC>
+__host__ __device__ constexpr int tfc_batch_rows() { return tfc_bf16_rows<S, TC>() ? 20 : (TC ? 12 : 16); }
 
 __device__ __forceinline__ float4 bf16x4_to_float4(uint2 q) {
   return make_float4(__uint_as_float(q.x << 16), __uint_as_float(q.x & 0xFFFF0000u), __uint_as_float(q.y << 16),
@@ -302,7 +308,8 @@ __device__ __forceinline__ float4 bf16x4_to_float4(uint2 q) {
 template <int S, int NT, bool TC>
 __device__ __forceinline__ void tfc_rows(const Ctx<S, NT, TC>& c, const LayerDev& L, const FusedLayer& F, int i4,
                                          int b_lo, int b_hi, float4 (&acc)[S]) {
-  constexpr int U = tfc_batch_rows<TC>();
+  constexpr int U = tfc_batch_rows<S, TC>();
+  constexpr bool BH = tfc_bf16_rows<S, TC>();
   const float* __restrict__ W = L.W;
 #pragma unroll
   for (int s = 0; s < S; ++s) acc[s] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -311,12 +318,12 @@ __device__ __forceinline__ void tfc_rows(const Ctx<S, NT, TC>& c, const LayerDev
     // every CTA streams the same weight rows: start at a CTA-dependent batch
     // so that concurrent CTAs spread over the L2 slices
     const int o0 = U * (b_lo + (bi + (int)blockIdx.x) % nb);
-    using WRow = typename std::conditional<TC, uint2, float4>::type;
+    using WRow = typename std::conditional<BH, uint2, float4>::type;
     WRow wv[U];
     {
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        if constexpr (TC)
+        if constexpr (BH)
           wv[u] = (o0 + u < L.n_out) ? __ldg(reinterpret_cast<const uint2*>(F.wh + (size_t)(o0 + u) * L.n_in) + i4)
                                      : make_uint2(0u, 0u);
         else
@@ -328,7 +335,7 @@ __device__ __forceinline__ void tfc_rows(const Ctx<S, NT, TC>& c, const LayerDev
     for (int u = 0; u < U; ++u) {
       if (o0 + u < L.n_out) {
         float4 w4;
-        if constexpr (TC)
+        if constexpr (BH)
           w4 = bf16x4_to_float4(wv[u]);
         else
           w4 = wv[u];
@@ -377,7 +384,7 @@ __device__ __forceinline__ void tfc_bounds(const Ctx<S, NT, TC>& c, int k, int s
 template <int S, int NT, bool TC>
 __device__ void tfc_main(const Ctx<S, NT, TC>& c, const LayerDev& L, const FusedLayer& F, int k, const Team& tm) {
   const float* __restrict__ W = L.W;
-  constexpr int U = tfc_batch_rows<TC>();
+  constexpr int U = tfc_batch_rows<S, TC>();
   if (tm.tid < 0) return;
   if (tfc_split(L, F, tm.n)) {
     const int n4 = L.n_in / 4, half = tm.n / 2;
@@ -396,16 +403,16 @@ __device__ void tfc_main(const Ctx<S, NT, TC>& c, const LayerDev& L, const Fused
     const int n4 = L.n_in / 4;
     const int nbat = (L.n_out + U - 1) / U;
     for (int i4 = tm.tid; i4 < n4; i4 += tm.n) {
-      // the bounds load before the weight loop (TC: after it, which leaves
-      // the registers to the weight rows)
+      // the bounds load before the weight loop (BF16 rows: after it, which
+      // leaves the registers to the weight rows)
       float l[S][4], u[S][4];
-      if constexpr (!TC) {
+      if constexpr (!tfc_bf16_rows<S, TC>()) {
 #pragma unroll
         for (int s = 0; s < S; ++s) tfc_bounds(c, k, s, i4, l[s], u[s]);
       }
       float4 acc[S];
       tfc_rows(c, L, F, i4, 0, nbat, acc);
-      if constexpr (TC) {
+      if constexpr (tfc_bf16_rows<S, TC>()) {
 #pragma unroll
         for (int s = 0; s < S; ++s) tfc_bounds(c, k, s, i4, l[s], u[s]);
       }

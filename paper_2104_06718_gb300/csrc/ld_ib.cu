@@ -33,6 +33,8 @@
 // term is added in FP64 (exact products of FP32 values), whose summation error
 // is bounded by gamma_M times the sum of |terms|.  So the returned bounds
 // contain the exact CROWN/WK bounds (outward), like the interval bounds.
+#include <climits>
+
 #include "ld_common.cuh"
 
 namespace ld {
@@ -191,6 +193,46 @@ __global__ void __launch_bounds__(NT) ib_step_kernel(IbStep st) {
     v = bb;
     av = fabs(bb);
   }
+  // Conv layers: the window of the input plane that the nonzero mu reach
+  // (output rows oy feed input rows oy*stride - pad .. + kh - 1, and the same
+  // for columns); an element outside it meets only zero terms, a = 0 and
+  // s = 0, and is skipped as such below.
+  __shared__ int win[4];
+  bool windowed = false;
+  if (!st.seed && L.kind == LD_LAYER_CONV) {
+    windowed = true;
+    if (threadIdx.x == 0) {
+      win[0] = INT_MAX;
+      win[1] = -1;
+      win[2] = INT_MAX;
+      win[3] = -1;
+    }
+    __syncthreads();
+    int y0 = INT_MAX, y1 = -1, x0 = INT_MAX, x1 = -1;
+    const int hwo = L.ho * L.wo;
+    for (int o = threadIdx.x; o < L.n_out; o += NT)
+      if (mu[o] != 0.f) {
+        const int r = o % hwo, oy = r / L.wo, ox = r - oy * L.wo;
+        y0 = min(y0, oy);
+        y1 = max(y1, oy);
+        x0 = min(x0, ox);
+        x1 = max(x1, ox);
+      }
+    if (y1 >= 0) {
+      atomicMin(&win[0], y0);
+      atomicMax(&win[1], y1);
+      atomicMin(&win[2], x0);
+      atomicMax(&win[3], x1);
+    }
+    __syncthreads();
+  }
+  int wy0 = 0, wy1 = -1, wx0 = 0, wx1 = -1;
+  if (windowed && win[1] >= 0) {
+    wy0 = max(0, win[0] * L.stride - L.pad);
+    wy1 = min(L.h - 1, win[1] * L.stride - L.pad + L.kh - 1);
+    wx0 = max(0, win[2] * L.stride - L.pad);
+    wx1 = min(L.w - 1, win[3] * L.stride - L.pad + L.kw - 1);
+  }
   const int bx = st.box ? box_of(st, owner) : 0;
   const double g2 = 2.0 * (double)st.gamma_K * (double)st.gamma_K;
   for (int ii = threadIdx.x; ii < L.n_in; ii += NT) {
@@ -199,6 +241,13 @@ __global__ void __launch_bounds__(NT) ib_step_kernel(IbStep st) {
       a = seed_elem(L, i, sign, ii);
       s = fabsf(a);
     } else {
+      if (windowed) {
+        const int rem = ii % (L.h * L.w), y = rem / L.w, x = rem - y * L.w;
+        if (y < wy0 || y > wy1 || x < wx0 || x > wx1) {
+          if (!st.box) st.mu_out[(size_t)rl * L.n_in + ii] = 0.f;
+          continue;
+        }
+      }
       transposed_elem(L, mu, ii, a, s);
     }
     if (a == 0.f && s == 0.f) {

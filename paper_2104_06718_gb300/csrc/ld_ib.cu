@@ -145,11 +145,14 @@ __device__ __forceinline__ void transposed_elem(const LayerDev& L, const float* 
   s = d.s;
 }
 
+// (A warp whose values are all zero skips its FP64 shuffle tree: its sum is
+// that zero, and FP64 additions are GB300's scarce unit.)
 __device__ __forceinline__ double block_sum(double v, double* red, bool up) {
-  for (int o = 16; o > 0; o >>= 1) {
-    const double w = __shfl_down_sync(0xffffffffu, v, o);
-    v = up ? __dadd_ru(v, w) : v + w;
-  }
+  if (__any_sync(0xffffffffu, v != 0.0))
+    for (int o = 16; o > 0; o >>= 1) {
+      const double w = __shfl_down_sync(0xffffffffu, v, o);
+      v = up ? __dadd_ru(v, w) : v + w;
+    }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __syncthreads();
   if (lane == 0) red[warp] = v;

@@ -85,6 +85,9 @@ def test_calls_reject_null_handle_on_host(lib):
     assert lib.ld_intermediate_bounds(None, None, None, 1, None, None, None, None) == binding.LD_ERR_ARG
     assert lib.ld_bound_backward(None, *([None] * 4), 1, None, None, 1, *([None] * 9)) == binding.LD_ERR_ARG
     assert lib.ld_dual_supergradient(None, *([None] * 4), 1, None, None, 1, *([None] * 5)) == binding.LD_ERR_ARG
+    assert lib.ld_bound_ball(None, *([None] * 4), 1, None, None, 1, 1, C.byref(o), *([None] * 5)) == binding.LD_ERR_ARG
+    assert lib.ld_bound_trace(None, *([None] * 4), 1, None, None, 1, 1, C.byref(o), *([None] * 6)) == binding.LD_ERR_ARG
+    assert lib.ld_intermediate_bounds_ball(None, None, None, 1, None, None, None, None) == binding.LD_ERR_ARG
     assert lib.ld_net_destroy(None) == binding.LD_ERR_ARG
     assert lib.ld_net_reserve(None, 4) == binding.LD_ERR_ARG
 

@@ -69,6 +69,10 @@ TRAFFIC = {
     ("base", "fp32", "fused", 2, 512, 256, 100): ("fb0d87097daa", 8017920),
     # ncu --set full of fused_kernel<2, 512, 1>: dram__bytes_read.sum 8,573,696 B, dram__bytes_write.sum 0
     ("base", "bf16", "fused tensor-core bf16", 2, 512, 256, 100): ("6999b18eb761", 8573696),
+    # ncu --metrics dram__bytes_*.sum of fused_kernel<1, 512, 0> / <1, 512, 1>, one launch each
+    ("wide", "fp32", "fused", 1, 512, 2048, 100): ("fb0d87097daa", 118957056 + 98169600),
+    ("deep", "fp32", "fused", 1, 512, 128, 100): ("fb0d87097daa", 8338432),
+    ("deep", "bf16", "fused tensor-core bf16", 1, 512, 128, 100): ("6999b18eb761", 8344832),
     # ncu --set full of the 7 launches of one iteration of the layer-wise tensor-core engine
     # (read 359.92 MB + write 82.02 MB) x 100 iterations of the graph launch
     ("wide", "bf16", "tensor-core bf16", 0, 0, 2048, 100): ("ae24c7520b03", 44194022400),

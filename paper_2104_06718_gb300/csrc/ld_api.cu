@@ -1291,13 +1291,16 @@ void prox_init_primal(ld_net* net, const Problem& P, const ld::ProxState& S, cud
 ld_status run_prox_iterations(ld_net* net, const Problem& P, const ld::ProxState& S, const ld_prox_opts& o,
                               int n_iters, cudaStream_t s) {
   const int n = net->n;
+  auto eta_of = [&](int t) {
+    return (float)((double)o.eta0 + ((double)o.eta_end - (double)o.eta0) * t / std::max(n_iters - 1, 1));
+  };
+  // lambda' of every layer at the first eta; from then on the block moves and
+  // the dual updates keep it current
+  if (n_iters > 0) ld::launch_prox_dual_prime(P, S, 0, net->N, eta_of(0), s);
   for (int t = 0; t < n_iters; ++t) {
-    const double eta_d = (double)o.eta0 + ((double)o.eta_end - (double)o.eta0) * t / std::max(n_iters - 1, 1);
-    const float eta = (float)eta_d;
+    const float eta = eta_of(t);
     for (int j = 0; j < o.J; ++j) {
       for (int k = 0; k < n; ++k) {
-        if (k >= 1) ld::launch_prox_dual_prime(P, S, r_off(net, k), layer(net, k).n_out, eta, s);
-        if (k + 1 <= n - 1) ld::launch_prox_dual_prime(P, S, r_off(net, k + 1), layer(net, k + 1).n_out, eta, s);
         ld::EpiArgmin ea{P, k, r_off(net, k), x_off(net, k), S.lp, net->x, S.zB, nullptr, nullptr};
         if (k == n - 1)
           ld::launch_top_argmin(layer(net, n), P, ea, s);
@@ -1311,7 +1314,7 @@ ld_status run_prox_iterations(ld_net* net, const Problem& P, const ld::ProxState
                                      k + 1 == n ? 1 : 0, eta, s);
       }
     }
-    ld::launch_prox_dual_update(P, S, eta, o.mu, s);
+    ld::launch_prox_dual_update(P, S, eta, o.mu, t + 1 < n_iters ? eta_of(t + 1) : 0.f, s);
   }
   return last_error();
 }

@@ -660,7 +660,9 @@ void launch_prox_dual_prime(const Problem& P, const ProxState& S, int off, int n
 void launch_prox_block_update(const Problem& P, const ProxState& S, int off_k, int n_k, int off_k1, int n_k1,
                               int last, float eta, cudaStream_t s);
 // Dual update with momentum (Eq. momentum_updates; mu = 0: Eq. lambda_updates).
-void launch_prox_dual_update(const Problem& P, const ProxState& S, float eta, float mu, cudaStream_t s);
+// eta_next > 0: also forms lambda' for the next iteration's eta.
+void launch_prox_dual_update(const Problem& P, const ProxState& S, float eta, float mu, float eta_next,
+                             cudaStream_t s);
 
 // Feasibility pre-pass and box checks (ld_passes.cu).
 void launch_empty_flags(const Problem& P, int8_t* empty, int* status, cudaStream_t s);

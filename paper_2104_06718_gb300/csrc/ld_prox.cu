@@ -5,6 +5,10 @@
 // on the layerwise transposed and forward passes; the kernels here form
 // lambda', take block k's optimal step of Eq. (optimal-gamma-gauss) and move
 // the block, and apply the dual update of Eq. (momentum_updates).
+// lambda' is kept current instead of re-formed before every block: a block's
+// move rewrites lambda' of the two layers it changed, and the dual update
+// rewrites all of it with the next iteration's eta (one formula, lam_prime,
+// everywhere, so the values are those of re-forming it).
 //
 // The optimal step of a subdomain is a ratio of two sums over block k's
 // neurons; one CTA per subdomain sums them in a fixed order (deterministic)
@@ -16,6 +20,11 @@ namespace {
 
 constexpr int NT = 256;
 
+// lambda' = lambda + (x_hat_B - x_hat_A) / eta, with inv = 1 / eta.
+__device__ __forceinline__ float lam_prime(float lam, float xb, float xa, float inv) {
+  return __fmaf_rn(__fsub_rn(xb, xa), inv, lam);
+}
+
 __global__ void prox_dual_prime_kernel(Problem P, ProxState S, int off, int n, float eta) {
   const size_t total = (size_t)P.B * n;
   const float inv = 1.f / eta;
@@ -23,7 +32,7 @@ __global__ void prox_dual_prime_kernel(Problem P, ProxState S, int off, int n, f
     const int b = (int)(e / n), i = (int)(e % n);
     const size_t j = (size_t)b * P.N + off + i;
     const size_t ja = (size_t)b * (P.N + 1) + off + i;
-    S.lp[j] = S.lam[j] + (S.xB[j] - S.xA[ja]) * inv;
+    S.lp[j] = lam_prime(S.lam[j], S.xB[j], S.xA[ja], inv);
   }
 }
 
@@ -55,7 +64,7 @@ __global__ void __launch_bounds__(NT) prox_block_update_kernel(Problem P, ProxSt
   for (int i = threadIdx.x; i < n_k; i += NT) {
     const size_t j = rb + off_k + i;
     const float xb = S.xB[j], zb = S.zB[j];
-    const float lpk = S.lam[j] + (xb - S.xA[ra + off_k + i]) * inv;
+    const float lpk = lam_prime(S.lam[j], xb, S.xA[ra + off_k + i], inv);
     const float d = zb - xb;
     num -= (double)lpk * (double)d;
     den += (double)d * (double)d;
@@ -79,26 +88,36 @@ __global__ void __launch_bounds__(NT) prox_block_update_kernel(Problem P, ProxSt
   __syncthreads();
   const float g = gam_s, h = 1.f - g;
   if (P.empty[b]) return;
+  // move the block, and rewrite lambda' of the layers it changed
   for (int i = threadIdx.x; i < n_k; i += NT) {
     const size_t j = rb + off_k + i;
-    S.xB[j] = fmaf(g, S.zB[j], h * S.xB[j]);
+    const float xb = fmaf(g, S.zB[j], h * S.xB[j]);
+    S.xB[j] = xb;
+    S.lp[j] = lam_prime(S.lam[j], xb, S.xA[ra + off_k + i], inv);
   }
   for (int i = threadIdx.x; i < n_k1; i += NT) {
     const size_t ja = ra + (last ? P.N : off_k1 + i);
-    S.xA[ja] = fmaf(g, S.zA[ja], h * S.xA[ja]);
+    const float xa = fmaf(g, S.zA[ja], h * S.xA[ja]);
+    S.xA[ja] = xa;
+    if (!last) S.lp[rb + off_k1 + i] = lam_prime(S.lam[rb + off_k1 + i], S.xB[rb + off_k1 + i], xa, inv);
   }
 }
 
-__global__ void prox_dual_update_kernel(Problem P, ProxState S, float eta, float mu) {
+// eta_next > 0: also lambda' of the next iteration (its eta).
+__global__ void prox_dual_update_kernel(Problem P, ProxState S, float eta, float mu, float eta_next) {
   const size_t total = (size_t)P.B * P.N;
   const float inv = 1.f / eta;
+  const float inv_next = eta_next > 0.f ? 1.f / eta_next : 0.f;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const int b = (int)(e / P.N), i = (int)(e % P.N);
     if (P.empty[b]) continue;
-    const float step = (S.xB[e] - S.xA[(size_t)b * (P.N + 1) + i]) * inv;
+    const float xb = S.xB[e], xa = S.xA[(size_t)b * (P.N + 1) + i];
+    const float step = (xb - xa) * inv;
     const float p = fmaf(mu, S.pi[e], step);
     S.pi[e] = p;
-    S.lam[e] = S.lam[e] + p;
+    const float lam = S.lam[e] + p;
+    S.lam[e] = lam;
+    if (eta_next > 0.f) S.lp[e] = lam_prime(lam, xb, xa, inv_next);
   }
 }
 
@@ -123,10 +142,11 @@ void launch_prox_block_update(const Problem& P, const ProxState& S, int off_k, i
   prox_block_update_kernel<<<P.B, NT, 0, s>>>(P, S, off_k, n_k, off_k1, n_k1, last, eta);
 }
 
-void launch_prox_dual_update(const Problem& P, const ProxState& S, float eta, float mu, cudaStream_t s) {
+void launch_prox_dual_update(const Problem& P, const ProxState& S, float eta, float mu, float eta_next,
+                             cudaStream_t s) {
   if (P.B == 0) return;
   count_launch();
-  prox_dual_update_kernel<<<grid_of((size_t)P.B * P.N), NT, 0, s>>>(P, S, eta, mu);
+  prox_dual_update_kernel<<<grid_of((size_t)P.B * P.N), NT, 0, s>>>(P, S, eta, mu, eta_next);
 }
 
 }  // namespace ld

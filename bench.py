@@ -65,17 +65,16 @@ METRIC = "LD subdomain bounds/s on Base/Wide/Deep convnets, bf16 vs fp32 at ≤1
 # (kernel_digest(engine)).  An entry whose digest differs from the current
 # sources is not reported (the kernel changed since the capture).
 TRAFFIC = {
-    # ncu --metrics dram__bytes_*.sum of fused_kernel<2, 512, 0>: read 8,017,920 B, write 0
-    ("base", "fp32", "fused", 2, 512, 256, 100): ("fb0d87097daa", 8017920),
-    # ncu --set full of fused_kernel<2, 512, 1>: dram__bytes_read.sum 8,573,696 B, dram__bytes_write.sum 0
-    ("base", "bf16", "fused tensor-core bf16", 2, 512, 256, 100): ("6999b18eb761", 8573696),
-    # ncu --metrics dram__bytes_*.sum of fused_kernel<1, 512, 0> / <1, 512, 1>, one launch each
-    ("wide", "fp32", "fused", 1, 512, 2048, 100): ("fb0d87097daa", 118957056 + 98169600),
-    ("deep", "fp32", "fused", 1, 512, 128, 100): ("fb0d87097daa", 8338432),
-    ("deep", "bf16", "fused tensor-core bf16", 1, 512, 128, 100): ("6999b18eb761", 8344832),
-    # ncu --set full of the 7 launches of one iteration of the layer-wise tensor-core engine
-    # (read 359.92 MB + write 82.02 MB) x 100 iterations of the graph launch
-    ("wide", "bf16", "tensor-core bf16", 0, 0, 2048, 100): ("ae24c7520b03", 44194022400),
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum of one launch of the fused kernels
+    # (fused_kernel<2, 512, 0|1> on Base, <1, 512, 0|1> on Wide and Deep): read + write
+    ("base", "fp32", "fused", 2, 512, 256, 100): ("f3512387ae4d", 8013568),
+    ("base", "bf16", "fused tensor-core bf16", 2, 512, 256, 100): ("b20cd24da710", 8575232),
+    ("wide", "fp32", "fused", 1, 512, 2048, 100): ("f3512387ae4d", 119097600 + 98118144),
+    ("deep", "fp32", "fused", 1, 512, 128, 100): ("f3512387ae4d", 8338688),
+    ("deep", "bf16", "fused tensor-core bf16", 1, 512, 128, 100): ("b20cd24da710", 8386560),
+    # the same metrics over the 7 launches of one iteration of the layer-wise tensor-core engine
+    # (read 359.94 MB + write 75.89 MB) x the 100 iterations of its graph launch
+    ("wide", "bf16", "tensor-core bf16", 0, 0, 2048, 100): ("81ea16f36381", (359940352 + 75886592) * 100),
 }
 
 # The sources each timed engine is compiled from (besides the shared header
